@@ -1,0 +1,310 @@
+"""FP64 CPU oracle for the fluctuating D2Q9 lattice Boltzmann step of arXiv:1009.0254.
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` are the only callers.  The product library never imports this
+package and shares no code with it: the C core (``lbref.c``) does the per-site
+collision and streaming in plain loops, and this module builds the noise of Sec. IV
+and the statistics used by the paper's Results section with numpy.
+
+Parity status: every function here is pinned by a ``-m "not gpu"`` test against the
+paper's printed matrices, closed forms, the linear theory or brute force (see the
+tests named in each docstring).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from . import theory
+from .theory import C, N, SIGMA_S2, T, TINV, W, Model
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liblbref.so")
+_lib = None
+
+NOISE_OFF, NOISE_LW, NOISE_FULL, NOISE_DIAG = 0, 1, 2, 3
+TAG_MODES_5_8, TAG_MODES_4_9, TAG_KSPACE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the C core with gcc into oracle/_build/liblbref.so."""
+    src = os.path.join(_HERE, "lbref.c")
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.oracle_tables.argtypes = [dp, dp, dp, ctypes.POINTER(ctypes.c_int)]
+        L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.oracle_normals.argtypes = [ctypes.c_int64, u32p, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_uint32, dp]
+        L.oracle_step.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        L.oracle_collide_sites.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int64), dp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+# --- random numbers ------------------------------------------------------------
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block function (Salmon et al., SC'11) of the C core."""
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib().oracle_philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), out.ctypes.data_as(u32p))
+    return out
+
+
+def normals(index, seed: int, step: int, tag: int) -> np.ndarray:
+    """Four unit normals per counter index: shape (len(index), 4)."""
+    idx = np.ascontiguousarray(np.asarray(index, dtype=np.uint32))
+    out = np.zeros((idx.size, 4))
+    lib().oracle_normals(idx.size, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                         ctypes.c_uint64(seed), ctypes.c_uint64(step), ctypes.c_uint32(tag), _dp(out))
+    return out
+
+
+# --- noise of Sec. IV ------------------------------------------------------------
+
+def _fft_conj_index(nx, ny):
+    """Linear index of -k for every k = (mx, my), array [my, mx]."""
+    mx = np.arange(nx)
+    my = np.arange(ny)
+    MX, MY = np.meshgrid(mx, my, indexing="xy")
+    return ((ny - MY) % ny) * nx + (nx - MX) % nx
+
+
+def eta_field(nx, ny, seed, step):
+    """Two independent Hermitian unit Gaussian fields eta_1(k), eta_2(k), arrays [my, mx].
+
+    Every pair (k, -k) shares one draw owned by the lower linear index my*nx + mx
+    (tag 2): eta = (n0 + i n1)/sqrt(2), (n2 + i n3)/sqrt(2) at the owner and the
+    conjugate at its partner; at self-conjugate k only the real parts n0, n2 are
+    used, so <|eta(k)|^2> = 1 everywhere."""
+    n = nx * ny
+    lin = np.arange(n).reshape(ny, nx)
+    conj = _fft_conj_index(nx, ny)
+    owner = np.minimum(lin, conj)
+    g = normals(np.arange(n, dtype=np.uint32), seed, step, TAG_KSPACE)   # draw for every index
+    go = g[owner.ravel()].reshape(ny, nx, 4)
+    selfc = lin == conj
+    is_owner = lin == owner
+    e1 = np.where(selfc, go[..., 0] + 0j, (go[..., 0] + 1j * go[..., 1]) / np.sqrt(2))
+    e2 = np.where(selfc, go[..., 2] + 0j, (go[..., 2] + 1j * go[..., 3]) / np.sqrt(2))
+    e1 = np.where(is_owner | selfc, e1, np.conj(e1))
+    e2 = np.where(is_owner | selfc, e2, np.conj(e2))
+    return e1, e2
+
+
+def block49_factor(model: Model, kx, ky):
+    """Cholesky factor (L44, L94, L99) of the (4,9) block of Xi(k), Eq. (noise-yeo),
+    vectorised over k; zero pivots clamped to 0 (Sec. IV: Xi is only PSD)."""
+    c2k = model.cs2_k(kx, ky)
+    lb, le = model.lam[3], model.lam[8]
+    pref = -(model.rho0 * model.kT / SIGMA_S2)
+    x44 = pref * N[3] * (2 - 3 * c2k) * lb * (2 + lb)
+    x49 = pref * 12 * (c2k - SIGMA_S2) * (lb + le + lb * le)
+    x99 = pref * N[8] * (5 / 4 - 3 / 4 * c2k) * le * (2 + le)
+    scale = np.maximum(np.abs(x44), np.abs(x99)) + 1e-300
+    if np.any(x44 < -1e-9 * scale) or np.any(x99 < -1e-9 * scale):
+        raise ValueError("Xi(k) is not positive semidefinite on this grid")
+    L44 = np.sqrt(np.maximum(x44, 0.0))
+    L94 = np.where(L44 > 0, x49 / np.where(L44 > 0, L44, 1.0), 0.0)
+    rem = x99 - L94 * L94
+    if np.any(rem < -1e-9 * scale):
+        raise ValueError("Xi(k) is not positive semidefinite on this grid")
+    L99 = np.sqrt(np.maximum(rem, 0.0))
+    return L44, L94, L99
+
+
+def xi49_full(model: Model, nx, ny, seed, step):
+    """Spatially correlated noise of modes 4 and 9 (Sec. IV, last paragraph): in k-space
+    xi(k) = L(k) eta(k) with L L^T the (4,9) block of Xi(k), Eq. (noise-yeo), then one
+    transform back to the lattice with the unitary convention of Sec. III:
+    a(r) = n^-1/2 sum_k exp(-i k.r) a(k).  Returns real fields xi4[y, x], xi9[y, x]."""
+    KX, KY = theory.lattice_k(nx, ny)
+    L44, L94, L99 = block49_factor(model, KX, KY)
+    e1, e2 = eta_field(nx, ny, seed, step)
+    x4k = L44 * e1
+    x9k = L94 * e1 + L99 * e2
+    n = nx * ny
+    # numpy's forward fft2 computes sum_k a(k) exp(-2 pi i (mx x/nx + my y/ny))
+    x4 = np.fft.fft2(x4k) / np.sqrt(n)
+    x9 = np.fft.fft2(x9k) / np.sqrt(n)
+    return x4.real, x9.real
+
+
+def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None):
+    """xi[a, y, x] for one step (Sec. IV).
+
+    LW:   xi = L nu with L L^T = Xi(0) (lower-right 6x6 Cholesky), nu_5..8 from tag 0,
+          (nu_4, nu_9) from tag 1, spatially uncorrelated.
+    DIAG: as LW with the off-diagonal Xi_49 dropped ("ideal gas-like" noise, Sec. IV).
+    FULL: modes 5..8 as LW (their variances do not depend on k); modes 4, 9 from
+          xi49_full()."""
+    n = nx * ny
+    xi = np.zeros((9, ny, nx))
+    if mode == NOISE_OFF or model.kT == 0.0:
+        return xi
+    idx = np.arange(n, dtype=np.uint32)
+    g0 = normals(idx, seed, step, TAG_MODES_5_8)
+    nu = np.zeros((9, n))
+    nu[4:8] = g0.T
+    if mode in (NOISE_LW, NOISE_DIAG):
+        g1 = normals(idx, seed, step, TAG_MODES_4_9)
+        nu[3] = g1[:, 0]
+        nu[8] = g1[:, 1]
+    if L0 is None:
+        X0 = model.Xi_zero()
+        if mode == NOISE_DIAG:
+            X0 = np.diag(np.diag(X0))
+        L0 = theory.noise_factor(X0)
+    xi_flat = L0 @ nu
+    xi[:] = xi_flat.reshape(9, ny, nx)
+    if mode == NOISE_FULL:
+        x4, x9 = xi49_full(model, nx, ny, seed, step)
+        xi[3] = x4
+        xi[8] = x9
+    return xi
+
+
+# --- the step -----------------------------------------------------------------------
+
+def params_vector(model: Model) -> np.ndarray:
+    return np.concatenate([[model.rho0, model.cs2, model.kappa], model.lam]).astype(np.float64)
+
+
+def step(f: np.ndarray, model: Model, xi=None) -> np.ndarray:
+    """One step of Eq. (fluct-lin-lbe) on a periodic lattice: f[9, ny, nx] pre-collision
+    populations in, next pre-collision populations out (FP64)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, ny, nx = f.shape
+    out = np.empty_like(f)
+    par = params_vector(model)
+    xi_c = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
+    lib().oracle_step(nx, ny, _dp(f), _dp(out), _dp(par), _dp(xi_c))
+    return out
+
+
+def collide_sites(f: np.ndarray, model: Model, sites: np.ndarray, xi_sites=None) -> np.ndarray:
+    """Post-collision populations f*_i at the given linear sites, shape (len(sites), 9)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, ny, nx = f.shape
+    s = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.zeros((s.size, 9))
+    par = params_vector(model)
+    xs = None if xi_sites is None else np.ascontiguousarray(xi_sites, dtype=np.float64)
+    lib().oracle_collide_sites(nx, ny, _dp(f), s.size, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                               _dp(par), _dp(xs), _dp(out))
+    return out
+
+
+class Lattice:
+    """A periodic nx x ny lattice stepped by the oracle (FP64), noise per Sec. IV.
+
+    ``f`` holds pre-collision populations f[i, y, x]; ``t`` is the index of the next
+    collision, which keys its random numbers."""
+
+    def __init__(self, nx, ny, rho0=1.0, cs2=SIGMA_S2, seed=42):
+        self.nx, self.ny = int(nx), int(ny)
+        self.seed = int(seed)
+        self.model = Model(rho0=rho0, cs2=cs2)
+        self.mode = NOISE_OFF
+        self.t = 0
+        self.f = np.broadcast_to(self.model.fbar()[:, None, None], (9, ny, nx)).copy()
+        self._L0 = None
+
+    def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+        m = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
+        fb_old = self.model.fbar()
+        self.model = m
+        self.mode = int(noise_mode)
+        X0 = m.Xi_zero()
+        if self.mode == NOISE_DIAG:
+            X0 = np.diag(np.diag(X0))
+        self._L0 = theory.noise_factor(X0)
+        del fb_old
+
+    def noise(self, t=None):
+        t = self.t if t is None else t
+        return noise_fields(self.model, self.mode, self.nx, self.ny, self.seed, t, self._L0)
+
+    def step(self, nsteps=1):
+        for _ in range(int(nsteps)):
+            xi = None
+            if self.mode != NOISE_OFF and self.model.kT > 0:
+                xi = self.noise()
+            self.f = step(self.f, self.model, xi)
+            self.t += 1
+        return self
+
+    def moments(self) -> np.ndarray:
+        """m_a(r) = sum_i T_ai f_i(r), shape (9, ny, nx)."""
+        return np.einsum("ai,iyx->ayx", T, self.f)
+
+
+# --- statistics of the Results section ------------------------------------------------
+
+def unitary_ft(a: np.ndarray) -> np.ndarray:
+    """a(k) = n^-1/2 sum_r exp(+i k.r) a(r) (Sec. III, notation), array [my, mx]."""
+    n = a.size
+    return np.fft.ifft2(a) * np.sqrt(n)
+
+
+def k_bins(nx, ny, nbins):
+    """Radial bin of every wavevector: |k| with components wrapped to (-pi, pi], bin width
+    pi sqrt(2)/nbins, k = 0 excluded (bin -1).  Decided in FP64."""
+    mx = np.arange(nx)
+    my = np.arange(ny)
+    mxw = np.where(mx > nx // 2, mx - nx, mx)
+    myw = np.where(my > ny // 2, my - ny, my)
+    KXw, KYw = np.meshgrid(2.0 * np.pi * mxw / nx, 2.0 * np.pi * myw / ny, indexing="xy")
+    kmag = np.sqrt(KXw * KXw + KYw * KYw)
+    width = np.pi * np.sqrt(2.0) / nbins
+    b = np.floor(kmag / width).astype(np.int64)
+    b = np.minimum(b, nbins - 1)
+    b[0, 0] = -1
+    return b, KXw, KYw, kmag
+
+
+def spectra_sample(f: np.ndarray, rho0: float, nbins: int):
+    """Per-bin sums of |drho(k)|^2, |j_l(k)|^2, |j_t(k)|^2 and the bin counts for one state
+    (Eqs. struct-fact and momtm-fluct are the theories they estimate)."""
+    _, ny, nx = f.shape
+    rho = f.sum(axis=0)
+    jx = np.einsum("i,iyx->yx", C[:, 0].astype(float), f)
+    jy = np.einsum("i,iyx->yx", C[:, 1].astype(float), f)
+    rk = unitary_ft(rho - rho0)
+    jxk = unitary_ft(jx)
+    jyk = unitary_ft(jy)
+    b, KXw, KYw, kmag = k_bins(nx, ny, nbins)
+    kk = np.where(kmag > 0, kmag, 1.0)
+    jl = (KXw * jxk + KYw * jyk) / kk
+    jt = (-KYw * jxk + KXw * jyk) / kk
+    sel = b >= 0
+    Srho = np.bincount(b[sel], weights=np.abs(rk[sel]) ** 2, minlength=nbins)
+    Sjl = np.bincount(b[sel], weights=np.abs(jl[sel]) ** 2, minlength=nbins)
+    Sjt = np.bincount(b[sel], weights=np.abs(jt[sel]) ** 2, minlength=nbins)
+    cnt = np.bincount(b[sel], minlength=nbins)
+    return Srho, Sjl, Sjt, cnt

@@ -1,0 +1,150 @@
+"""Pins of the oracle's noise (Sec. IV of arXiv:1009.0254) and of the equilibrium
+statistics it produces (Sec. V A, the equilibration ratios of Figs. 3 and 4)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import theory as th
+
+
+def _xi_samples(model, mode, nx, ny, steps, seed=11):
+    L0 = None
+    out = []
+    for t in range(steps):
+        out.append(oracle.noise_fields(model, mode, nx, ny, seed, t, L0))
+    return np.array(out)                                  # (steps, 9, ny, nx)
+
+
+@pytest.mark.parametrize("mode", [oracle.NOISE_LW, oracle.NOISE_DIAG])
+def test_uncorrelated_noise_covariance(mode):
+    # Sec. IV: xi = L nu with L L^T = Xi(0) (LW) or diag Xi(0) (ideal-gas-like, DIAG);
+    # c_s != sigma_s so that Xi_49(0) != 0
+    m = th.Model(rho0=1.0, cs2=0.2 ** 2, kappa=0.03, kT=1e-4, tau_s=0.8, tau_b=1.0, tau_ghost=1.2)
+    X0 = m.Xi_zero()
+    target = X0 if mode == oracle.NOISE_LW else np.diag(np.diag(X0))
+    assert abs(X0[3, 8]) > 0.1 * np.sqrt(X0[3, 3] * X0[8, 8])
+    xi = _xi_samples(m, mode, 32, 32, 20)
+    v = xi.transpose(1, 0, 2, 3).reshape(9, -1)
+    Nn = v.shape[1]
+    C = v @ v.T / Nn
+    assert np.all(C[:3] == 0) and np.all(C[:, :3] == 0)       # no noise on rho, j
+    C, target = C[3:, 3:], target[3:, 3:]
+    sig = np.sqrt((np.outer(np.diag(target), np.diag(target)) + target ** 2) / Nn)
+    assert np.all(np.abs(C - target) <= 5 * sig)
+    # spatially white: neighbour correlation vanishes
+    nb = (xi * np.roll(xi, 1, axis=3)).mean(axis=(0, 2, 3))
+    assert np.all(np.abs(nb[3:]) <= 5 * np.diag(target) / np.sqrt(Nn))
+
+
+def test_hermitian_eta_field():
+    nx, ny = 8, 6
+    e1, e2 = oracle.eta_field(nx, ny, seed=3, step=9)
+    conj = oracle._fft_conj_index(nx, ny)
+    for e in (e1, e2):
+        flat = e.ravel()
+        np.testing.assert_array_equal(flat[conj.ravel()], np.conj(flat))
+        selfc = conj.ravel() == np.arange(nx * ny)
+        assert np.all(flat[selfc].imag == 0)
+    # unit variance over many draws
+    acc = np.zeros((ny, nx))
+    for t in range(400):
+        e1, _ = oracle.eta_field(nx, ny, seed=3, step=t)
+        acc += np.abs(e1) ** 2
+    assert np.all(np.abs(acc / 400 - 1) < 5 * np.sqrt(2 / 400))
+
+
+def test_full_noise_is_L_eta_in_k_space():
+    # the transform back and the forward transform of Sec. III are inverse: the
+    # spectrum of the real-space noise field is exactly L(k) eta(k)
+    m = th.Model(rho0=1.0, cs2=1 / 3, kappa=0.03, kT=1e-4, tau_s=0.8)
+    nx, ny = 16, 8
+    x4, x9 = oracle.xi49_full(m, nx, ny, seed=4, step=2)
+    e1, e2 = oracle.eta_field(nx, ny, seed=4, step=2)
+    KX, KY = th.lattice_k(nx, ny)
+    L44, L94, L99 = oracle.block49_factor(m, KX, KY)
+    np.testing.assert_allclose(oracle.unitary_ft(x4), L44 * e1, atol=1e-14)
+    np.testing.assert_allclose(oracle.unitary_ft(x9), L94 * e1 + L99 * e2, atol=1e-14)
+    # L L^T reproduces the (4,9) block of Eq. (noise-yeo) at every k
+    for (j, i) in [(0, 0), (3, 5), (4, 8), (7, 15)]:
+        X = m.Xi_closed(KX[j, i], KY[j, i])
+        Lm = np.array([[L44[j, i], 0], [L94[j, i], L99[j, i]]])
+        np.testing.assert_allclose(Lm @ Lm.T, X[np.ix_([3, 8], [3, 8])], atol=1e-18)
+
+
+def test_full_noise_spectrum_statistics():
+    m = th.Model(rho0=1.0, cs2=0.25 ** 2, kappa=0.05, kT=1e-4, tau_s=1.0)
+    nx = ny = 16
+    KX, KY = th.lattice_k(nx, ny)
+    steps = 300
+    P44 = np.zeros((ny, nx)); P99 = np.zeros((ny, nx)); P49 = np.zeros((ny, nx))
+    for t in range(steps):
+        x4, x9 = oracle.xi49_full(m, nx, ny, seed=8, step=t)
+        a, b = oracle.unitary_ft(x4), oracle.unitary_ft(x9)
+        P44 += np.abs(a) ** 2; P99 += np.abs(b) ** 2; P49 += (a * np.conj(b)).real
+    X = np.array([[m.Xi_closed(KX[j, i], KY[j, i]) for i in range(nx)] for j in range(ny)])
+    # aggregate in 4 shells of k^2; each entry is an average of steps*count draws
+    k2 = th.k2_lattice(KX, KY)
+    edges = np.quantile(k2, [0, 0.25, 0.5, 0.75, 1.0])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (k2 >= lo) & (k2 <= hi)
+        nS = sel.sum() * steps
+        for P, ab in [(P44, (3, 3)), (P99, (8, 8))]:
+            ratio = P[sel].sum() / (steps * X[sel][:, ab[0], ab[1]].sum())
+            assert abs(ratio - 1) < 5 * np.sqrt(2.0 / nS)
+        c = P49[sel].sum() / steps
+        ref = X[sel][:, 3, 8].sum()
+        sd = np.sqrt((X[sel][:, 3, 3] * X[sel][:, 8, 8]).sum() / steps)
+        assert abs(c - ref) < 5 * sd
+
+
+def _equilibration_ratios(lat, burn, samples, every, G_of_k):
+    nx, ny = lat.nx, lat.ny
+    KX, KY = th.lattice_k(nx, ny)
+    lat.step(burn)
+    acc = np.zeros((9, ny, nx))
+    for _ in range(samples):
+        lat.step(every)
+        dm = lat.moments() - lat.model.mbar()[:, None, None]
+        acc += np.abs(np.array([oracle.unitary_ft(dm[a]) for a in range(9)])) ** 2
+    acc /= samples
+    G = np.array([[np.diag(G_of_k(KX[j, i], KY[j, i])).real for i in range(nx)] for j in range(ny)])
+    ratio = acc / G.transpose(2, 0, 1)
+    keep = np.ones((ny, nx), bool)
+    keep[0, 0] = False                   # k = 0: frozen by conservation
+    keep[0, nx // 2] = False             # staggered momentum invariants (see theory tests)
+    keep[ny // 2, 0] = False
+    return ratio, keep
+
+
+@pytest.mark.slow
+def test_full_noise_equilibrates_every_mode():
+    # Sec. V A: with the correlated noise of Eq. (noise-yeo) every mode equilibrates,
+    # <|dm_a(k)|^2> / G_aa(k) = 1 (Fig. 3); kappa = 0.08, c_s = 0.265, tau = 1
+    lat = oracle.Lattice(12, 12, rho0=1.0, cs2=0.265 ** 2, seed=77)
+    lat.set_params(kT=1e-6, kappa=0.08, tau_s=1.0, tau_b=1.0, tau_ghost=1.0, noise_mode=oracle.NOISE_FULL)
+    ratio, keep = _equilibration_ratios(lat, burn=400, samples=1500, every=2, G_of_k=lat.model.G_closed)
+    for a in range(9):
+        r = ratio[a][keep]
+        assert abs(r.mean() - 1) < 0.04, (a, r.mean())
+
+
+@pytest.mark.slow
+def test_long_wavelength_noise_matches_its_own_stationary_theory():
+    # LW noise (Eq. noise-matrix-k0 used at every k): the stationary spectrum is the
+    # solution of G = M G M^H + A(-k) Xi(0) A(-k)^H; it tends to G(k) as k -> 0
+    m0 = th.Model(rho0=1.0, cs2=0.15 ** 2, kappa=0.03, kT=1e-6, tau_s=1.0, tau_b=1.0, tau_ghost=1.0)
+    lat = oracle.Lattice(12, 12, rho0=1.0, cs2=0.15 ** 2, seed=78)
+    lat.set_params(kT=1e-6, kappa=0.03, tau_s=1.0, tau_b=1.0, tau_ghost=1.0, noise_mode=oracle.NOISE_LW)
+    X0 = m0.Xi_zero()
+
+    def G_lw(kx, ky):
+        if kx == 0 and ky == 0:
+            return m0.G_closed(0.0, 0.0)
+        if np.abs(np.linalg.eigvals(m0.M(kx, ky))).max() > 1 - 1e-9:
+            return m0.G_closed(kx, ky)
+        return th.lyapunov_G(m0, kx, ky, X0)
+
+    ratio, keep = _equilibration_ratios(lat, burn=400, samples=1500, every=2, G_of_k=G_lw)
+    for a in range(9):
+        r = ratio[a][keep]
+        assert abs(r.mean() - 1) < 0.04, (a, r.mean())

@@ -104,9 +104,10 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Uniform on (0,1) from the top 24 bits: (k + 1/2) 2^-24, exact in FP32 and FP64. */
+/* Uniform on (0,1) from the top 23 bits: (k + 1/2) 2^-23 = (2k + 1) 2^-24, which has
+ * at most 24 significant bits and so is exact in FP32 as well as FP64. */
 static double unit_open(uint32_t x) {
-    return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0);
+    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
 /* Box-Muller: (u1, u2) -> sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2). */

@@ -34,8 +34,8 @@ def test_normals_are_unit_gaussian():
     # the two normals of a Box-Muller pair are uncorrelated
     p = oracle.normals(np.arange(100000, dtype=np.uint32), seed=3, step=0, tag=1)
     assert abs(np.mean(p[:, 0] * p[:, 1])) < 5 / np.sqrt(p.shape[0])
-    # tails: |n| is bounded by sqrt(-2 ln 2^-25) since u1 >= 2^-25
-    assert np.abs(g).max() <= np.sqrt(-2 * np.log(2.0 ** -25)) + 1e-12
+    # tails: |n| is bounded by sqrt(-2 ln 2^-24) since u1 >= 2^-24
+    assert np.abs(g).max() <= np.sqrt(-2 * np.log(2.0 ** -24)) + 1e-12
 
 
 def test_counter_fields_select_independent_streams():
@@ -52,10 +52,10 @@ def test_counter_fields_select_independent_streams():
 
 def test_normals_follow_counter_layout():
     # counter = (index, step lo, step hi, tag), key = (seed lo, seed hi); words (0,1) and
-    # (2,3) feed Box-Muller with u = (x >> 8 + 1/2) 2^-24
+    # (2,3) feed Box-Muller with u = (x >> 9 + 1/2) 2^-23
     seed, step, tag, index = 0x0123456789ABCDEF, (5 << 32) + 17, 2, 99
     w = oracle.philox4x32_10([index, step & 0xFFFFFFFF, step >> 32, tag], [seed & 0xFFFFFFFF, seed >> 32])
-    u = ((w.astype(np.float64) // 256) + 0.5) / 2.0 ** 24
+    u = ((w.astype(np.float64) // 512) + 0.5) / 2.0 ** 23
     r1 = np.sqrt(-2 * np.log(u[0]))
     r2 = np.sqrt(-2 * np.log(u[2]))
     expect = [r1 * np.cos(2 * np.pi * u[1]), r1 * np.sin(2 * np.pi * u[1]),

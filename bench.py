@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the fluctuating D2Q9 step on GB300: MLUPS and fraction of the HBM roofline.
+
+Workload (one GPU): a single periodic 4096 x 4096 FP32 lattice, rho0 = 1, tau_s = 0.8,
+tau_b = 1, tau_ghost = 1, kT = 1e-4, cs2 = 1/3, radially binned S(k) and velocity spectra
+accumulated in FP64 on the device every 100 steps.  The main line runs the long-wavelength
+noise at kappa = 0.01; the correlated (full FDT) noise at kappa = 0.05 is measured in the
+same run and reported under "variants".  A step is one time step of every node (pull,
+density stencil, equilibrium, MRT relaxation, noise, back-transform, store) plus, every
+100th step, the spectra sample.  Inputs (2 x 614 MB of populations) are larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (launched by torch.distributed.run) every rank steps its own independent
+lattice (replicas; the method has no exchange between independent runs): weak scaling.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE_STEP = 72          # 9 FP32 populations read + 9 written
+BYTES_PER_NODE_STEP_FULL = 80     # + the (xi_4, xi_9) FP32 pair read by the step kernel
+PARAMS_LW = dict(kT=1e-4, kappa=0.01, tau_s=0.8, tau_b=1.0, tau_ghost=1.0)
+PARAMS_FULL = dict(kT=1e-4, kappa=0.05, tau_s=0.8, tau_b=1.0, tau_ghost=1.0)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10000)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=4096, help="lattice side")
+    p.add_argument("--every", type=int, default=100)
+    p.add_argument("--nbins", type=int, default=2048)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variants", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def step_kernel_traffic(nodes):
+    """DRAM bytes per step-kernel launch from a committed ncu capture, scaled by nodes,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for name in d.get("sources", []):
+        with open(os.path.join(ROOT, name), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != d.get("source_sha256"):
+        return None
+    return float(d["dram_bytes_per_launch"]) * nodes / float(d["nodes"])
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if ts < t0 or ts > t1 + 0.05:
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def cpu_baseline(seconds, n_side):
+    """The FP64 oracle (as it stands, one thread) on a periodic n_side x h strip of the
+    workload with the main line's parameters; h sized for about `seconds` of work."""
+    import oracle
+    oracle.build()
+    p = PARAMS_LW
+
+    def run(h, steps):
+        L = oracle.Lattice(n_side, h, seed=42)
+        L.set_params(p["kT"], p["kappa"], p["tau_s"], p["tau_b"], p["tau_ghost"], oracle.NOISE_LW)
+        L.step(1)
+        t0 = time.perf_counter()
+        L.step(steps)
+        return time.perf_counter() - t0
+
+    dt = run(4, 2)
+    rate = n_side * 4 * 2 / max(dt, 1e-9)                   # node updates / s
+    steps = 5
+    h = int(max(4, min(n_side, seconds * rate / (n_side * steps))))
+    dt = run(h, steps)
+    mlups = n_side * h * steps / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of a periodic %dx%d strip (long-wavelength noise, kappa=%.2f), FP64 C core + "
+                      "numpy noise, one thread" % (steps, n_side, h, p["kappa"]),
+            "seconds": dt}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    p = PARAMS_LW
+    n_side = args.n
+
+    def make(h):
+        L = oracle.Lattice(n_side, h, seed=42)
+        L.set_params(p["kT"], p["kappa"], p["tau_s"], p["tau_b"], p["tau_ghost"], oracle.NOISE_LW)
+        return L
+
+    L = make(4)
+    t0 = time.perf_counter()
+    L.step(2)
+    rate = n_side * 4 * 2 / max(time.perf_counter() - t0, 1e-9)
+    budget = 150.0
+    h = int(max(2, min(n_side, budget * rate / (n_side * max(1, args.steps + args.warmup)))))
+    L = make(h)
+    L.step(args.warmup)
+    t0 = time.perf_counter()
+    L.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = n_side * h * args.steps / dt / 1e6
+    sample = "each step: one oracle step of a periodic %dx%d strip of the %dx%d workload" % (n_side, h, n_side, n_side)
+    line = {"impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "D2Q9 fluctuating non-ideal LB, periodic %dx%d FP32 lattice, long-wavelength "
+                                   "noise, kappa=0.01, tau_s=0.8, kT=1e-4" % (n_side, n_side),
+                       "sample_rows": h},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def timed_run(lbf, torch, L, steps, warmup, mode, params, dist):
+    L.set_params(params["kT"], params["kappa"], params["tau_s"], params["tau_b"], params["tau_ghost"], mode)
+    L.step(warmup)
+    torch.cuda.synchronize()
+    lbf.lb_set_kernel_timing(L.ctx, 1)
+    k0 = lbf.lb_launch_count(L.ctx)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
+    ev0.record(L.stream)
+    L.step(steps)
+    ev1.record(L.stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kms, kl = lbf.lb_kernel_time(L.ctx)
+    launches = lbf.lb_launch_count(L.ctx) - k0
+    lbf.lb_set_kernel_timing(L.ctx, 0)
+    return ms, kms, kl, launches, wall0, wall1
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import paper_1009_0254_gb300 as lbf
+    from paper_1009_0254_gb300 import build as lbbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        lbbuild.build()
+    if dist is not None:
+        dist.barrier()
+    lbf.load()
+
+    n = args.n
+    nodes = n * n
+    L = lbf.Lattice(n, n, seed=42 + 1000 * rank)
+    L.set_sampling(args.every, args.nbins)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = vis.split(",")[local] if vis else local
+    clocks = ClockSampler(gpu_index)
+    time.sleep(0.3)
+
+    # main line: long-wavelength noise
+    ms, kms, kl, launches, w0, w1 = timed_run(lbf, torch, L, args.steps, args.warmup, lbf.LB_NOISE_LW, PARAMS_LW, dist)
+    clk = clocks.stop(w0, w1)
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = max_over_ranks(ms)
+    value = world * nodes * args.steps / (ms / 1e3) / 1e6
+    hbm, peak_kind = peaks()
+    k_avg_s = kms / max(kl, 1) / 1e3
+    achieved = BYTES_PER_NODE_STEP * nodes / k_avg_s / 1e9
+    traffic = step_kernel_traffic(nodes)
+
+    # variant: correlated (full FDT) noise at kappa = 0.05
+    variants = []
+    if not args.no_variants:
+        L.set_sampling(args.every, args.nbins)
+        fms, fkms, fkl, flaunch, _, _ = timed_run(lbf, torch, L, args.steps, args.warmup, lbf.LB_NOISE_FULL,
+                                                  PARAMS_FULL, dist)
+        fms = max_over_ranks(fms)
+        fk = fkms / max(fkl, 1) / 1e3
+        variants.append({"noise": "full (correlated, k-space synthesis + FFT each step)", "kappa": 0.05,
+                         "value": world * nodes * args.steps / (fms / 1e3) / 1e6, "unit": "MLUPS",
+                         "ms_per_step": fms / args.steps,
+                         "step_kernel": {"achieved": BYTES_PER_NODE_STEP_FULL * nodes / fk / 1e9, "unit": "GB/s",
+                                         "frac": BYTES_PER_NODE_STEP_FULL * nodes / fk / 1e9 / hbm,
+                                         "avg_us": fk * 1e6},
+                         "gpu_launches": flaunch})
+
+    # end to end through the public API: host initial state in, spectra and sums out
+    L.set_params(PARAMS_LW["kT"], PARAMS_LW["kappa"], PARAMS_LW["tau_s"], PARAMS_LW["tau_b"],
+                 PARAMS_LW["tau_ghost"], lbf.LB_NOISE_LW)
+    L.set_sampling(args.every, args.nbins)
+    host_f = torch.empty((9, n, n), dtype=torch.float64, pin_memory=True)
+    host_f.copy_(torch.from_numpy(L.populations()))
+    S = np.zeros(args.nbins)
+    Jl = np.zeros(args.nbins)
+    Jt = np.zeros(args.nbins)
+    cnt = np.zeros(args.nbins, dtype=np.int64)
+    ns = np.zeros(1, dtype=np.int64)
+    sums = np.zeros(3)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    lbf.lb_set_populations(L.ctx, host_f.data_ptr(), lbf.LB_HOST, 0)
+    lbf.lb_step(L.ctx, args.steps)
+    lbf.lb_structure_factor(L.ctx, args.nbins, S, Jl, Jt, cnt, ns)
+    lbf.lb_moments(L.ctx, None, lbf.LB_HOST, sums)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s)
+    h2d = 9 * nodes * 8
+    d2h = 3 * args.nbins * 8 + 3 * 8
+    e2e = {"value": world * nodes * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "job": "lb_set_populations (host FP64) + lb_step(K) + lb_structure_factor + lb_moments sums"}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(args.cpu_seconds, n)
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "D2Q9 fluctuating non-ideal LB (modified equilibrium), periodic %dx%d FP32 "
+                               "lattice, long-wavelength noise, kappa=0.01, tau_s=0.8, tau_b=1, tau_ghost=1, "
+                               "kT=1e-4, cs2=1/3, S(k) every %d steps into %d bins (FP64)" % (n, n, args.every,
+                                                                                               args.nbins),
+                   "lattice": [n, n], "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (
+                       2 * 9 * (n + 64) * (n + 4) * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "kernel": "step_kernel (fused pull+collide+noise)",
+                     "bytes_per_node": BYTES_PER_NODE_STEP, "avg_launch_us": k_avg_s * 1e6,
+                     "peak_source": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "variants": variants,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * lbfluct.h -- C ABI of the GB300 (sm_103a) fluctuating lattice Boltzmann library.
+ *
+ * The library steps a periodic D2Q9 lattice of the modified-equilibrium non-ideal
+ * fluid model with thermal noise that satisfies the lattice fluctuation-dissipation
+ * theorem of Gross, Adhikari, Cates & Varnik, "Thermal fluctuations in the lattice
+ * Boltzmann method for non-ideal fluids", arXiv:1009.0254 (cited below as [GACV]).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: LB_OK (0) on success, a negative LB_E* code on failure.  Nothing
+ *     aborts; lb_last_error(ctx) returns a message for the last failure on ctx.
+ *   - Populations cross the ABI as FP64 arrays f[i][y][x] (index i*nx*ny + y*nx + x),
+ *     i = 0..8 in the velocity order of [GACV] Eq. (Tmat): c = (0,0), (1,0), (0,1),
+ *     (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).  They are the pre-collision
+ *     populations f_i(r, t), i.e. the state right after streaming.
+ *   - Moments are m_a = sum_i T_ai f_i with T of [GACV] Table I, a = 0..8 for the
+ *     paper's a = 1..9 (rho, jx, jy, e, p_ww, p_xy, qx, qy, eps).
+ *   - `loc` says where a caller buffer lives: LB_HOST (pageable or pinned host memory)
+ *     or LB_DEVICE (device memory of the context's GPU).  The caller owns every
+ *     buffer it passes; the library keeps no pointer to it after the call returns.
+ *   - All GPU work is issued on the context's stream (lb_set_stream, default: the
+ *     legacy default stream).  Calls that return data to the host synchronise that
+ *     stream; lb_step does not.
+ *   - One context may be used by one host thread at a time.
+ */
+#ifndef LBFLUCT_H
+#define LBFLUCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define LB_OK 0
+#define LB_EINVAL (-1)     /* argument out of range or inconsistent */
+#define LB_ENOTPSD (-2)    /* noise covariance Xi(k) not positive semidefinite */
+#define LB_ENOMEM (-3)     /* device allocation failed or workspace too small */
+#define LB_ECUDA (-4)      /* a CUDA runtime call failed (message in lb_last_error) */
+#define LB_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define LB_ESTATE (-6)     /* call out of order (e.g. lb_step before lb_set_params) */
+
+/* storage precision of the populations */
+#define LB_FP32 0          /* FP32 deviations f_i - fbar_i */
+#define LB_FP16DEV 1       /* FP16 deviations f_i - fbar_i (reserved, not built yet) */
+
+/* noise modes, [GACV] Sec. IV */
+#define LB_NOISE_OFF 0     /* deterministic (kT ignored) */
+#define LB_NOISE_LW 1      /* spatially uncorrelated, covariance Xi(0), Eq. (noise-matrix-k0) */
+#define LB_NOISE_FULL 2    /* spatially correlated, covariance Xi(k), Eq. (noise-yeo) */
+#define LB_NOISE_DIAG 3    /* "ideal gas-like": LW with the off-diagonal Xi_49 dropped */
+
+/* buffer locations */
+#define LB_HOST 0
+#define LB_DEVICE 1
+
+/* warning bits returned by lb_warnings() */
+#define LB_WARN_LOW_MACH 1 /* kT >= 0.1 sigma_s^2 rho0, [GACV] Eq. (low-mach) */
+
+typedef struct lb_ctx lb_ctx;
+
+/*
+ * Device bytes a context of this size needs (populations, noise and statistics
+ * scratch).  Pass a buffer of at least this size to lb_create to keep all device
+ * memory under the caller's allocator.  Returns 0 for invalid sizes.
+ */
+size_t lb_workspace_bytes(int nx, int ny, int precision);
+
+/*
+ * Creates a context for a periodic nx x ny lattice (nx, ny >= 2) at rest with
+ * uniform density rho0: f_i = fbar_i, the equilibrium of [GACV] Table II at u = 0
+ * with the linearised equation of state p0 = cs2 rho (cs2 is the thermodynamic
+ * sound speed squared; 1/3 gives fbar_i = w_i rho0).  `seed` keys the Philox4x32-10
+ * noise: key = (seed mod 2^32, seed div 2^32).
+ * workspace: device buffer of >= lb_workspace_bytes() bytes owned by the caller and
+ * kept alive until lb_destroy, or NULL to let the library cudaMalloc its own.
+ * The context uses the device that is current when lb_create is called.
+ * Errors: LB_EINVAL (sizes, rho0 <= 0, cs2 <= 0, precision), LB_ENOMEM, LB_ECUDA.
+ */
+int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double cs2,
+              void* workspace, size_t workspace_bytes, lb_ctx** out);
+
+/* Releases the context (and its own device memory, if it allocated any). */
+int lb_destroy(lb_ctx* ctx);
+
+/* Issue all later GPU work of ctx on `stream` (a cudaStream_t; NULL = legacy default). */
+int lb_set_stream(lb_ctx* ctx, void* stream);
+
+/*
+ * Relaxation and noise, [GACV] Sec. III-IV.  lambda_a = -1/tau_a with tau_s for the
+ * shear modes p_ww, p_xy, tau_b for the bulk mode e and tau_ghost for q_x, q_y and eps
+ * (Table I).  Every tau must exceed 1/2 (Sec. III A), kT >= 0, kappa >= 0.
+ * For noise_mode != LB_NOISE_OFF with kT > 0 the noise covariance Xi(k) of
+ * Eq. (noise-yeo) must be positive semidefinite at every wavevector of this lattice
+ * (Sec. III C, Fig. 5), else LB_ENOTPSD; its factors are computed here in FP64.
+ * May be called again between steps; the lattice state is kept.
+ */
+int lb_set_params(lb_ctx* ctx, double kT, double kappa, double tau_s, double tau_b,
+                  double tau_ghost, int noise_mode);
+
+/*
+ * Advances nsteps >= 0 time steps of [GACV] Eq. (fluct-lin-lbe): stream (pull),
+ * collide in moment space with the Table II equilibrium (Appendix B Laplacian),
+ * add the noise of the chosen mode, transform back.  The collision at time t draws
+ * its random numbers with counter (node y*nx+x, t mod 2^32, t div 2^32, tag).  If
+ * sampling is on (lb_set_sampling) the spectra are accumulated after every step
+ * that brings the time to a multiple of `every`.  Asynchronous on the stream.
+ * Errors: LB_ESTATE before lb_set_params, LB_ECUDA on launch failure.
+ */
+int lb_step(lb_ctx* ctx, int64_t nsteps);
+
+/* Time index t of the current state (number of collisions done since t = 0). */
+int lb_get_time(lb_ctx* ctx, int64_t* t);
+
+/*
+ * Replaces the state by pre-collision populations f (FP64, 9*nx*ny, layout above) and
+ * sets the time index to t (which keys the next collision's noise).  Values are
+ * rounded to the storage precision as deviations from fbar_i.
+ */
+int lb_set_populations(lb_ctx* ctx, const double* f, int loc, int64_t t);
+
+/* Copies the current pre-collision populations (FP64, 9*nx*ny) into f. */
+int lb_get_populations(lb_ctx* ctx, double* f, int loc);
+
+/*
+ * Moments of the current state.  If m != NULL it receives m_a(r) (FP64, 9*nx*ny,
+ * m[a*nx*ny + y*nx + x]).  If sums != NULL it receives the FP64 lattice sums
+ * {sum rho, sum jx, sum jy}, accumulated on the device in FP64 (Table I: these
+ * three are conserved by the collision).
+ */
+int lb_moments(lb_ctx* ctx, double* m, int loc, double sums[3]);
+
+/*
+ * Turns on sampling of the spectra every `every` >= 1 steps into `nbins` >= 1 radial
+ * bins of |k| over [0, pi sqrt(2)] (k components wrapped to (-pi, pi], k = 0 left
+ * out); every = 0 turns sampling off.  Needs nx and ny powers of two (the transform
+ * is a radix-2 FFT).  Resets the accumulators.
+ */
+int lb_set_sampling(lb_ctx* ctx, int every, int nbins);
+
+/*
+ * Running FP64 averages over the samples taken so far, per bin b < nbins:
+ *   S_rho[b] = < |drho(k)|^2 >,  S_jl[b] = < |k.j(k)|^2 / k^2 >,
+ *   S_jt[b]  = < |k x j(k)|^2 / k^2 >,  counts[b] = wavevectors in bin b,
+ * with the unitary transform a(k) = n^-1/2 sum_r exp(i k.r) a(r) of [GACV] Sec. III
+ * and drho = rho - rho0.  Their theories are Eqs. (struct-fact) and (momtm-fluct).
+ * Any output pointer may be NULL.  *nsamples receives the number of samples.
+ */
+int lb_structure_factor(lb_ctx* ctx, int nbins, double* S_rho, double* S_jl, double* S_jt,
+                        int64_t* counts, int64_t* nsamples);
+
+/* Bitmask of LB_WARN_* raised by the last lb_set_params. */
+int lb_warnings(lb_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none); ctx == NULL gives the last
+ * failure of a call that had no context (lb_create). */
+const char* lb_last_error(lb_ctx* ctx);
+
+/* Waits for all work issued on the context's stream. */
+int lb_synchronize(lb_ctx* ctx);
+
+/*
+ * Kernel timing for roofline measurements: when on, CUDA events are recorded on the
+ * context's stream around every launch of the fused step kernel; lb_kernel_time
+ * synchronises and returns the summed event time (ms) and the launch count since
+ * timing was turned on.
+ */
+int lb_set_kernel_timing(lb_ctx* ctx, int on);
+int lb_kernel_time(lb_ctx* ctx, double* ms, int64_t* launches);
+
+/* Number of kernels this context has launched since lb_create (all kinds). */
+int lb_launch_count(lb_ctx* ctx, int64_t* launches);
+
+/*
+ * Host-only helpers (no GPU needed).
+ * lb_noise_matrix: the 9x9 noise covariance Xi(k) of [GACV] Eq. (noise-yeo) for the
+ * given parameters at wavevector (kx, ky), with k^2 the lattice symbol of Appendix B;
+ * row-major into xi[81].
+ * lb_check_params: the validation lb_set_params performs for an nx x ny lattice.
+ */
+int lb_noise_matrix(double rho0, double cs2, double kT, double kappa, double tau_s,
+                    double tau_b, double tau_ghost, double kx, double ky, double* xi);
+int lb_check_params(int nx, int ny, double rho0, double cs2, double kT, double kappa,
+                    double tau_s, double tau_b, double tau_ghost, int noise_mode);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBFLUCT_H */

@@ -308,3 +308,47 @@ def spectra_sample(f: np.ndarray, rho0: float, nbins: int):
     Sjt = np.bincount(b[sel], weights=np.abs(jt[sel]) ** 2, minlength=nbins)
     cnt = np.bincount(b[sel], minlength=nbins)
     return Srho, Sjl, Sjt, cnt
+
+
+def noise_at_sites(model: Model, mode: int, nx, ny, seed, step, sites, L0=None, xi49=None):
+    """xi[k, a] at the listed linear sites (same draws as noise_fields); for the
+    correlated mode the (4, 9) fields over the whole lattice may be passed in xi49."""
+    sites = np.asarray(sites, dtype=np.int64)
+    xi = np.zeros((sites.size, 9))
+    if mode == NOISE_OFF or model.kT == 0.0:
+        return xi
+    if L0 is None:
+        X0 = model.Xi_zero()
+        if mode == NOISE_DIAG:
+            X0 = np.diag(np.diag(X0))
+        L0 = theory.noise_factor(X0)
+    idx = sites.astype(np.uint32)
+    nu = np.zeros((9, sites.size))
+    nu[4:8] = normals(idx, seed, step, TAG_MODES_5_8).T
+    if mode in (NOISE_LW, NOISE_DIAG):
+        g1 = normals(idx, seed, step, TAG_MODES_4_9)
+        nu[3] = g1[:, 0]
+        nu[8] = g1[:, 1]
+    xi[:] = (L0 @ nu).T
+    if mode == NOISE_FULL:
+        if xi49 is None:
+            xi49 = xi49_full(model, nx, ny, seed, step)
+        x4, x9 = xi49
+        xi[:, 3] = x4.ravel()[sites]
+        xi[:, 8] = x9.ravel()[sites]
+    return xi
+
+
+def step_sampled(f: np.ndarray, model: Model, mode: int, seed: int, step: int, nodes, L0=None, xi49=None):
+    """Pre-collision populations f_i(r, t+1) = f*_i(r - c_i, t) at the listed nodes only,
+    shape (len(nodes), 9); the collisions run at the nine source sites of each node."""
+    _, ny, nx = f.shape
+    nodes = np.asarray(nodes, dtype=np.int64)
+    x = nodes % nx
+    y = nodes // nx
+    src = np.stack([((y - C[i, 1]) % ny) * nx + (x - C[i, 0]) % nx for i in range(9)], axis=1)
+    sites, inv = np.unique(src.ravel(), return_inverse=True)
+    xi = noise_at_sites(model, mode, nx, ny, seed, step, sites, L0, xi49)
+    fs = collide_sites(f, model, sites, xi)
+    inv = inv.reshape(src.shape)
+    return np.stack([fs[inv[:, i], i] for i in range(9)], axis=1)

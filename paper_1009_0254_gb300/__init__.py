@@ -1,0 +1,268 @@
+"""Python binding of liblbfluct.so, the GB300 fluctuating lattice Boltzmann library.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  The
+functions below carry the names of the C ABI (include/lbfluct.h) and raise
+``LBError`` on a negative return code.  ``Lattice`` is a small convenience wrapper
+that lets PyTorch own the device workspace and supply the stream.
+
+There is no fallback: if the shared library is missing or cannot be loaded, every
+call raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbfluct.so")
+
+LB_OK, LB_EINVAL, LB_ENOTPSD, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LB_FP32, LB_FP16DEV = 0, 1
+LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL, LB_NOISE_DIAG = 0, 1, 2, 3
+LB_HOST, LB_DEVICE = 0, 1
+LB_WARN_LOW_MACH = 1
+
+_lib = None
+
+
+class LBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lbfluct error %d: %s" % (code, msg))
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbfluct.so (built by paper_1009_0254_gb300/build.py) and declare its ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("liblbfluct.so not found at %s: build it first (python -c 'import "
+                           "__graft_entry__ as g; g.build()')" % path)
+    L = ctypes.CDLL(path)
+    vp, dp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    c_int, c_i64, c_u64, c_dbl, c_sz = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t
+    proto = {
+        "lb_workspace_bytes": (c_sz, [c_int, c_int, c_int]),
+        "lb_create": (c_int, [c_int, c_int, c_int, c_u64, c_dbl, c_dbl, vp, c_sz, ctypes.POINTER(vp)]),
+        "lb_destroy": (c_int, [vp]),
+        "lb_set_stream": (c_int, [vp, vp]),
+        "lb_set_params": (c_int, [vp, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_int]),
+        "lb_step": (c_int, [vp, c_i64]),
+        "lb_get_time": (c_int, [vp, i64p]),
+        "lb_set_populations": (c_int, [vp, vp, c_int, c_i64]),
+        "lb_get_populations": (c_int, [vp, vp, c_int]),
+        "lb_moments": (c_int, [vp, vp, c_int, dp]),
+        "lb_set_sampling": (c_int, [vp, c_int, c_int]),
+        "lb_structure_factor": (c_int, [vp, c_int, dp, dp, dp, i64p, i64p]),
+        "lb_warnings": (c_int, [vp]),
+        "lb_last_error": (ctypes.c_char_p, [vp]),
+        "lb_synchronize": (c_int, [vp]),
+        "lb_set_kernel_timing": (c_int, [vp, c_int]),
+        "lb_kernel_time": (c_int, [vp, dp, i64p]),
+        "lb_launch_count": (c_int, [vp, i64p]),
+        "lb_noise_matrix": (c_int, [c_dbl] * 9 + [dp]),
+        "lb_check_params": (c_int, [c_int, c_int] + [c_dbl] * 7 + [c_int]),
+    }
+    for name, (res, args) in proto.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc, ctx=None):
+    if rc < 0:
+        msg = load().lb_last_error(ctx)
+        raise LBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a):
+    """Device or host address of a torch tensor or numpy array (plain int passes through)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()          # torch.Tensor
+
+
+def _dptr(a):
+    return ctypes.cast(_ptr(a), ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+# --- the ABI, one Python function per C entry point ---------------------------------------
+
+def lb_workspace_bytes(nx, ny, precision=LB_FP32):
+    return load().lb_workspace_bytes(nx, ny, precision)
+
+
+def lb_create(nx, ny, precision=LB_FP32, seed=42, rho0=1.0, cs2=1.0 / 3.0, workspace=None, workspace_bytes=0):
+    out = ctypes.c_void_p()
+    _check(load().lb_create(nx, ny, precision, seed, rho0, cs2, _ptr(workspace), workspace_bytes,
+                            ctypes.byref(out)))
+    return out.value
+
+
+def lb_destroy(ctx):
+    return _check(load().lb_destroy(ctx))
+
+
+def lb_set_stream(ctx, stream):
+    return _check(load().lb_set_stream(ctx, stream), ctx)
+
+
+def lb_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+    return _check(load().lb_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode), ctx)
+
+
+def lb_step(ctx, nsteps):
+    return _check(load().lb_step(ctx, nsteps), ctx)
+
+
+def lb_get_time(ctx):
+    t = ctypes.c_int64()
+    _check(load().lb_get_time(ctx, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def lb_set_populations(ctx, f, loc, t):
+    return _check(load().lb_set_populations(ctx, _ptr(f), loc, t), ctx)
+
+
+def lb_get_populations(ctx, f, loc):
+    return _check(load().lb_get_populations(ctx, _ptr(f), loc), ctx)
+
+
+def lb_moments(ctx, m, loc, sums):
+    return _check(load().lb_moments(ctx, _ptr(m), loc, _dptr(sums)), ctx)
+
+
+def lb_set_sampling(ctx, every, nbins):
+    return _check(load().lb_set_sampling(ctx, every, nbins), ctx)
+
+
+def lb_structure_factor(ctx, nbins, S_rho, S_jl, S_jt, counts, nsamples):
+    i64 = lambda a: ctypes.cast(_ptr(a), ctypes.POINTER(ctypes.c_int64)) if a is not None else None
+    return _check(load().lb_structure_factor(ctx, nbins, _dptr(S_rho), _dptr(S_jl), _dptr(S_jt), i64(counts),
+                                             i64(nsamples)), ctx)
+
+
+def lb_warnings(ctx):
+    return load().lb_warnings(ctx)
+
+
+def lb_last_error(ctx=None):
+    m = load().lb_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lb_synchronize(ctx):
+    return _check(load().lb_synchronize(ctx), ctx)
+
+
+def lb_set_kernel_timing(ctx, on):
+    return _check(load().lb_set_kernel_timing(ctx, int(on)), ctx)
+
+
+def lb_kernel_time(ctx):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().lb_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def lb_launch_count(ctx):
+    n = ctypes.c_int64()
+    _check(load().lb_launch_count(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def lb_noise_matrix(rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, kx, ky):
+    xi = np.zeros(81)
+    _check(load().lb_noise_matrix(rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, kx, ky, _dptr(xi)))
+    return xi.reshape(9, 9)
+
+
+def lb_check_params(nx, ny, rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+    return load().lb_check_params(nx, ny, rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
+
+
+# --- convenience wrapper -------------------------------------------------------------------
+
+class Lattice:
+    """One lattice on the current CUDA device.  PyTorch allocates the workspace and
+    provides the stream (torch.cuda.current_stream() at construction, unless given)."""
+
+    def __init__(self, nx, ny, seed=42, rho0=1.0, cs2=1.0 / 3.0, stream=None):
+        import torch
+        self.nx, self.ny = int(nx), int(ny)
+        nbytes = lb_workspace_bytes(self.nx, self.ny, LB_FP32)
+        if nbytes == 0:
+            raise LBError(LB_EINVAL, "invalid lattice size %dx%d" % (nx, ny))
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        aligned = (base + 255) & ~255
+        self.ctx = lb_create(self.nx, self.ny, LB_FP32, seed, rho0, cs2, aligned, nbytes)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        lb_set_stream(self.ctx, self.stream.cuda_stream)
+        self.nbins = 0
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+        lb_set_params(self.ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
+
+    def step(self, n=1):
+        lb_step(self.ctx, n)
+
+    @property
+    def t(self):
+        return lb_get_time(self.ctx)
+
+    def set_populations(self, f, t=0):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        lb_set_populations(self.ctx, f, LB_HOST, t)
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        lb_get_populations(self.ctx, f, LB_HOST)
+        return f
+
+    def moments(self):
+        m = np.empty((9, self.ny, self.nx))
+        s = np.zeros(3)
+        lb_moments(self.ctx, m, LB_HOST, s)
+        return m, s
+
+    def sums(self):
+        s = np.zeros(3)
+        lb_moments(self.ctx, None, LB_HOST, s)
+        return s
+
+    def set_sampling(self, every, nbins):
+        lb_set_sampling(self.ctx, every, nbins)
+        self.nbins = nbins
+
+    def structure_factor(self):
+        nb = self.nbins
+        S, L, Tt = np.zeros(nb), np.zeros(nb), np.zeros(nb)
+        cnt = np.zeros(nb, dtype=np.int64)
+        ns = np.zeros(1, dtype=np.int64)
+        lb_structure_factor(self.ctx, nb, S, L, Tt, cnt, ns)
+        return S, L, Tt, cnt, int(ns[0])

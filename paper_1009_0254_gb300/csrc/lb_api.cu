@@ -1,0 +1,608 @@
+// lb_api.cu -- the C ABI declared in include/lbfluct.h.
+//
+// Host side: context and workspace management, the FP64 parameter theory of
+// [GACV] Sec. III C-IV (noise covariance Xi(k) of Eq. noise-yeo, its positive
+// semidefiniteness on the lattice's wavevectors, the Cholesky factors of Sec. IV),
+// and the launch sequence of one time step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "lb_internal.cuh"
+#include "lbfluct.h"
+
+using namespace lbf;
+
+namespace {
+
+constexpr double SIGMA_S2 = 1.0 / 3.0;   // [GACV] Sec. III, notation
+thread_local std::string g_create_error;
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+
+struct WsLayout {
+    size_t pop[2], z1, z2, twx, twy, cosx, cosy, bins, counts, partial, sums3, fbar, total;
+};
+
+bool make_grid(int nx, int ny, Grid* g) {
+    if (nx < 2 || ny < 2 || nx > (1 << 16) || ny > (1 << 16)) return false;
+    g->nx = nx;
+    g->ny = ny;
+    g->pitch = ((nx + 2 * GX + 31) / 32) * 32;
+    g->plane = (((long long)g->pitch * (ny + 2 * GY)) + 63) / 64 * 64;
+    return true;
+}
+
+WsLayout make_layout(const Grid& g) {
+    WsLayout L{};
+    const long long n = (long long)g.nx * g.ny;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    L.pop[0] = take((size_t)Q * g.plane * sizeof(float));
+    L.pop[1] = take((size_t)Q * g.plane * sizeof(float));
+    L.z1 = take((size_t)n * sizeof(float2));
+    L.z2 = take((size_t)n * sizeof(float2));
+    L.twx = take((size_t)(g.nx / 2 + 1) * sizeof(float2));
+    L.twy = take((size_t)(g.ny / 2 + 1) * sizeof(float2));
+    L.cosx = take((size_t)g.nx * sizeof(float));
+    L.cosy = take((size_t)g.ny * sizeof(float));
+    L.bins = take((size_t)3 * MAX_BINS * sizeof(double));
+    L.counts = take((size_t)MAX_BINS * sizeof(unsigned long long));
+    L.partial = take((size_t)sums_partial_count() * sizeof(double));
+    L.sums3 = take(3 * sizeof(double));
+    L.fbar = take(Q * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+// velocities in [GACV] Eq. (Tmat) order and the D2Q9 weights (Sec. III A)
+const int CXh[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+const int CYh[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+const double Wh[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+// Rest populations fbar_i = w_i (rho0 + T_4i d rho0 / N_4 - T_9i d rho0 / N_9) for the
+// reference moments {rho0, 0, 0, d rho0, 0, 0, 0, 0, -d rho0}, d = 6 (cs2 - sigma_s^2)
+// (Table II at u = 0 with p0 = cs2 rho; inverse transform of Sec. III A).
+void rest_populations(double rho0, double cs2, double fbar[Q]) {
+    const double d = 6.0 * (cs2 - SIGMA_S2);
+    for (int i = 0; i < Q; ++i) {
+        const double c2 = CXh[i] * CXh[i] + CYh[i] * CYh[i];
+        const double t4 = 3.0 * c2 - 2.0;
+        const double t9 = 9.0 * c2 * c2 - 15.0 * c2 + 2.0;
+        fbar[i] = Wh[i] * (rho0 + t4 * d * rho0 / 4.0 - t9 * d * rho0 / 16.0);
+    }
+}
+
+// Noise covariance of [GACV] Eq. (noise-yeo) as functions of the lattice k^2 (s):
+// Xi_44 = a44 + b44 s, Xi_49 = a49 + b49 s, Xi_99 = a99 + b99 s; the shear and ghost
+// entries do not depend on k.
+struct NoiseCoef {
+    double a44, b44, a49, b49, a99, b99, x55, x66, x77;
+};
+
+NoiseCoef noise_coef(double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
+                     double tau_g) {
+    const double lb = -1.0 / tau_b, ls = -1.0 / tau_s, lq = -1.0 / tau_g, le = -1.0 / tau_g;
+    const double til_b = lb * (2.0 + lb), til_s = ls * (2.0 + ls), til_q = lq * (2.0 + lq);
+    const double til_e = le * (2.0 + le), til_be = lb + le + lb * le;
+    const double pref = -(rho0 * kT / SIGMA_S2);
+    const double N4 = 4.0, N5 = 4.0 / 9.0, N6 = 1.0 / 9.0, N7 = 2.0 / 3.0, N9 = 16.0;
+    NoiseCoef c;
+    // c_s^2(k) = cs2 + rho0 kappa s
+    c.a44 = pref * N4 * (2.0 - 3.0 * cs2) * til_b;
+    c.b44 = pref * N4 * (-3.0 * rho0 * kappa) * til_b;
+    c.a49 = pref * 12.0 * (cs2 - SIGMA_S2) * til_be;
+    c.b49 = pref * 12.0 * (rho0 * kappa) * til_be;
+    c.a99 = pref * N9 * (1.25 - 0.75 * cs2) * til_e;
+    c.b99 = pref * N9 * (-0.75 * rho0 * kappa) * til_e;
+    c.x55 = pref * N5 * til_s;
+    c.x66 = pref * N6 * til_s;
+    c.x77 = pref * N7 * til_q;
+    return c;
+}
+
+// lattice k^2: minus the Fourier symbol of the Appendix B Laplacian
+double k2_lattice(double kx, double ky) {
+    return -((4.0 / 9.0) * (std::cos(kx) + std::cos(ky)) + (2.0 / 9.0) * std::cos(kx) * std::cos(ky) - 10.0 / 9.0) /
+           SIGMA_S2;
+}
+
+bool block_psd(const NoiseCoef& c, double s) {
+    const double x44 = c.a44 + c.b44 * s, x49 = c.a49 + c.b49 * s, x99 = c.a99 + c.b99 * s;
+    const double scale = std::fmax(std::fabs(x44), std::fabs(x99)) + 1e-300;
+    const double tol = 1e-12 * scale;
+    if (x44 < -tol || x99 < -tol) return false;
+    return x44 * x99 - x49 * x49 >= -tol * scale;
+}
+
+int validate(int nx, int ny, double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
+             double tau_g, int mode, std::string* why) {
+    auto bad = [&](const char* m) { if (why) *why = m; return LB_EINVAL; };
+    if (!(tau_s > 0.5) || !(tau_b > 0.5) || !(tau_g > 0.5)) return bad("every relaxation time must exceed 1/2");
+    if (!(kT >= 0.0) || !std::isfinite(kT)) return bad("kT must be finite and >= 0");
+    if (!(kappa >= 0.0) || !std::isfinite(kappa)) return bad("kappa must be finite and >= 0");
+    if (mode < LB_NOISE_OFF || mode > LB_NOISE_DIAG) return bad("unknown noise mode");
+    if (!(rho0 > 0.0) || !(cs2 > 0.0)) return bad("rho0 and cs2 must be positive");
+    if (mode == LB_NOISE_OFF || kT == 0.0) return LB_OK;
+    const NoiseCoef c = noise_coef(rho0, cs2, 1.0, kappa, tau_s, tau_b, tau_g);
+    if (mode == LB_NOISE_FULL) {
+        // every wavevector of the lattice; cos is even, so the quarter grid suffices
+        for (int my = 0; my <= ny / 2; ++my)
+            for (int mx = 0; mx <= nx / 2; ++mx) {
+                const double s = k2_lattice(2.0 * M_PI * mx / nx, 2.0 * M_PI * my / ny);
+                if (!block_psd(c, s)) {
+                    if (why) *why = "noise covariance Xi(k) is not positive semidefinite on this lattice";
+                    return LB_ENOTPSD;
+                }
+            }
+    } else if (mode == LB_NOISE_LW) {
+        if (!block_psd(c, 0.0)) {
+            if (why) *why = "noise covariance Xi(0) is not positive semidefinite";
+            return LB_ENOTPSD;
+        }
+    } else {   // LB_NOISE_DIAG uses the diagonal of Xi(0) only
+        if (c.a44 < 0.0 || c.a99 < 0.0) {
+            if (why) *why = "diagonal of Xi(0) has a negative entry";
+            return LB_ENOTPSD;
+        }
+    }
+    return LB_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() { if (changed) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+struct lb_ctx {
+    int nx = 0, ny = 0, precision = 0, device = 0;
+    long long n = 0;
+    uint64_t seed = 0;
+    double rho0 = 1.0, cs2 = SIGMA_S2;
+    Grid g{};
+    WsLayout L{};
+    char* ws = nullptr;
+    bool owns = false;
+    float* pop[2] = {nullptr, nullptr};
+    int cur = 0;
+    float2 *z1 = nullptr, *z2 = nullptr, *twx = nullptr, *twy = nullptr;
+    float *cosx = nullptr, *cosy = nullptr;
+    double *bins = nullptr, *partial = nullptr, *sums3 = nullptr, *fbar_dev = nullptr;
+    unsigned long long* counts = nullptr;
+    bool pow2 = false;
+    double fbar[Q] = {};
+    // parameters
+    bool have_params = false;
+    int noise_mode = LB_NOISE_OFF, warnings = 0;
+    double kT = 0, kappa = 0, tau_s = 1, tau_b = 1, tau_g = 1;
+    StepArgs sa{};
+    NoiseGenArgs ga{};
+    // sampling
+    int every = 0, nbins = 0;
+    long long nsamples = 0;
+    std::vector<unsigned long long> hcounts;
+    // execution
+    cudaStream_t stream = nullptr;
+    long long t = 0;
+    std::string err;
+    // kernel timing
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t ev_used = 0;
+    double ms_acc = 0.0;
+    long long launches_acc = 0;
+    long long kernels = 0;          // every kernel launched on behalf of this context
+};
+
+static int fail(lb_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg; else g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(lb_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, LB_ECUDA, m);
+}
+
+#define CK(ctx, call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+extern "C" {
+
+size_t lb_workspace_bytes(int nx, int ny, int precision) {
+    Grid g;
+    if (precision != LB_FP32 || !make_grid(nx, ny, &g)) return 0;
+    return make_layout(g).total;
+}
+
+int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double cs2, void* workspace,
+              size_t workspace_bytes, lb_ctx** out) {
+    if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (precision != LB_FP32) return fail(nullptr, LB_EINVAL, "only LB_FP32 storage is available");
+    Grid g;
+    if (!make_grid(nx, ny, &g)) return fail(nullptr, LB_EINVAL, "nx and ny must lie in [2, 65536]");
+    if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(nullptr, LB_EINVAL, "rho0 must be positive");
+    if (!(cs2 > 0.0) || !std::isfinite(cs2)) return fail(nullptr, LB_EINVAL, "cs2 must be positive");
+    lb_ctx* c = new lb_ctx();
+    c->nx = nx; c->ny = ny; c->n = (long long)nx * ny; c->precision = precision;
+    c->seed = seed; c->rho0 = rho0; c->cs2 = cs2; c->g = g; c->L = make_layout(g);
+    c->pow2 = is_pow2(nx) && is_pow2(ny);
+    cudaGetDevice(&c->device);
+    if (workspace) {
+        if (workspace_bytes < c->L.total || ((uintptr_t)workspace & 255)) {
+            delete c;
+            return fail(nullptr, LB_ENOMEM, "workspace smaller than lb_workspace_bytes() or not 256-byte aligned");
+        }
+        c->ws = (char*)workspace;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&c->ws, c->L.total);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(nullptr, LB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        c->owns = true;
+    }
+    c->pop[0] = (float*)(c->ws + c->L.pop[0]);
+    c->pop[1] = (float*)(c->ws + c->L.pop[1]);
+    c->z1 = (float2*)(c->ws + c->L.z1);
+    c->z2 = (float2*)(c->ws + c->L.z2);
+    c->twx = (float2*)(c->ws + c->L.twx);
+    c->twy = (float2*)(c->ws + c->L.twy);
+    c->cosx = (float*)(c->ws + c->L.cosx);
+    c->cosy = (float*)(c->ws + c->L.cosy);
+    c->bins = (double*)(c->ws + c->L.bins);
+    c->counts = (unsigned long long*)(c->ws + c->L.counts);
+    c->partial = (double*)(c->ws + c->L.partial);
+    c->sums3 = (double*)(c->ws + c->L.sums3);
+    c->fbar_dev = (double*)(c->ws + c->L.fbar);
+    rest_populations(rho0, cs2, c->fbar);
+
+    // host tables in FP64 -> device
+    std::vector<float2> tw(std::max(nx, ny) / 2 + 1);
+    std::vector<float> cs(std::max(nx, ny));
+    auto upload = [&](int n, float2* dtw, float* dcos) -> cudaError_t {
+        for (int k = 0; k < n / 2 + 1; ++k) {
+            const double a = 2.0 * M_PI * (double)k / n;
+            tw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));   // exp(-2 pi i k/n)
+        }
+        for (int k = 0; k < n; ++k) cs[k] = (float)std::cos(2.0 * M_PI * (double)k / n);
+        cudaError_t e = cudaMemcpy(dtw, tw.data(), sizeof(float2) * (n / 2 + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(dcos, cs.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e = upload(nx, c->twx, c->cosx);
+    if (e == cudaSuccess) e = upload(ny, c->twy, c->cosy);
+    if (e == cudaSuccess) e = cudaMemcpy(c->fbar_dev, c->fbar, sizeof(double) * Q, cudaMemcpyHostToDevice);
+    // rest state: every deviation (and ghost) zero
+    if (e == cudaSuccess) e = cudaMemset(c->pop[0], 0, (size_t)Q * g.plane * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, (size_t)Q * g.plane * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->bins, 0, 3 * MAX_BINS * sizeof(double));
+    if (e != cudaSuccess) {
+        if (c->owns) cudaFree(c->ws);
+        delete c;
+        return fail(nullptr, LB_ECUDA, std::string("lb_create: ") + cudaGetErrorString(e));
+    }
+    c->sa.g = g;
+    c->sa.rho0 = (float)rho0;
+    c->sa.cs2m = (float)(cs2 - SIGMA_S2);
+    c->sa.key0 = (uint32_t)(seed & 0xffffffffu);
+    c->sa.key1 = (uint32_t)(seed >> 32);
+    *out = c;
+    return LB_OK;
+}
+
+int lb_destroy(lb_ctx* c) {
+    if (!c) return LB_EINVAL;
+    DeviceGuard dg(c->device);
+    for (auto& p : c->ev) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    if (c->owns) cudaFree(c->ws);
+    delete c;
+    return LB_OK;
+}
+
+int lb_set_stream(lb_ctx* c, void* stream) {
+    if (!c) return LB_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return LB_OK;
+}
+
+int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b, double tau_ghost, int mode) {
+    if (!c) return LB_EINVAL;
+    std::string why;
+    int r = validate(c->nx, c->ny, c->rho0, c->cs2, kT, kappa, tau_s, tau_b, tau_ghost, mode, &why);
+    if (r != LB_OK) return fail(c, r, why);
+    if (mode == LB_NOISE_FULL && kT > 0.0 && !c->pow2)
+        return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two (radix-2 FFT)");
+    c->kT = kT; c->kappa = kappa; c->tau_s = tau_s; c->tau_b = tau_b; c->tau_g = tau_ghost;
+    c->noise_mode = mode;
+    c->warnings = (kT >= 0.1 * SIGMA_S2 * c->rho0) ? LB_WARN_LOW_MACH : 0;   // Eq. (low-mach)
+    StepArgs& a = c->sa;
+    a.kappa = (float)kappa;
+    a.lb = (float)(-1.0 / tau_b);
+    a.ls = (float)(-1.0 / tau_s);
+    a.lq = (float)(-1.0 / tau_ghost);
+    a.le = (float)(-1.0 / tau_ghost);
+    const NoiseCoef nc = noise_coef(c->rho0, c->cs2, kT, kappa, tau_s, tau_b, tau_ghost);
+    // Sec. IV: xi = L nu with L L^T = Xi(0) on modes 4..9; only the (4,9) block is coupled
+    const double x44 = nc.a44, x49 = (mode == LB_NOISE_DIAG) ? 0.0 : nc.a49, x99 = nc.a99;
+    const double L44 = std::sqrt(std::fmax(x44, 0.0));
+    const double L94 = L44 > 0.0 ? x49 / L44 : 0.0;
+    const double L99 = std::sqrt(std::fmax(x99 - L94 * L94, 0.0));
+    a.L44 = (float)L44; a.L94 = (float)L94; a.L99 = (float)L99;
+    a.s5 = (float)std::sqrt(std::fmax(nc.x55, 0.0));
+    a.s6 = (float)std::sqrt(std::fmax(nc.x66, 0.0));
+    a.s7 = (float)std::sqrt(std::fmax(nc.x77, 0.0));
+    NoiseGenArgs& ga = c->ga;
+    ga.a44 = (float)nc.a44; ga.b44 = (float)nc.b44;
+    ga.a49 = (float)nc.a49; ga.b49 = (float)nc.b49;
+    ga.a99 = (float)nc.a99; ga.b99 = (float)nc.b99;
+    ga.cosx = c->cosx; ga.cosy = c->cosy; ga.nx = c->nx; ga.ny = c->ny;
+    ga.key0 = a.key0; ga.key1 = a.key1;
+    c->have_params = true;
+    return LB_OK;
+}
+
+static int record_timing(lb_ctx* c, cudaEvent_t* start, cudaEvent_t* stop) {
+    if (c->ev_used == c->ev.size()) {
+        if (c->ev.size() >= 1024) {
+            // fold the finished pairs into the running total and reuse them
+            CK(c, cudaEventSynchronize(c->ev.back().second), "cudaEventSynchronize");
+            for (auto& p : c->ev) {
+                float ms = 0.f;
+                CK(c, cudaEventElapsedTime(&ms, p.first, p.second), "cudaEventElapsedTime");
+                c->ms_acc += ms;
+            }
+            c->ev_used = 0;
+        } else {
+            cudaEvent_t a, b;
+            CK(c, cudaEventCreate(&a), "cudaEventCreate");
+            CK(c, cudaEventCreate(&b), "cudaEventCreate");
+            c->ev.push_back({a, b});
+        }
+    }
+    *start = c->ev[c->ev_used].first;
+    *stop = c->ev[c->ev_used].second;
+    c->ev_used++;
+    return LB_OK;
+}
+
+int lb_step(lb_ctx* c, int64_t nsteps) {
+    if (!c) return LB_EINVAL;
+    if (nsteps < 0) return fail(c, LB_EINVAL, "nsteps must be >= 0");
+    if (!c->have_params) return fail(c, LB_ESTATE, "lb_set_params must be called before lb_step");
+    DeviceGuard dg(c->device);
+    const bool noisy = c->noise_mode != LB_NOISE_OFF && c->kT > 0.0;
+    const int kmode = !noisy ? 0 : (c->noise_mode == LB_NOISE_FULL ? 2 : 1);
+    if (kmode == 2 && !c->pow2)
+        return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two (radix-2 FFT)");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const uint32_t tlo = (uint32_t)((uint64_t)c->t & 0xffffffffu), thi = (uint32_t)((uint64_t)c->t >> 32);
+        if (kmode == 2) {
+            NoiseGenArgs ga = c->ga;
+            ga.t_lo = tlo; ga.t_hi = thi;
+            CK(c, launch_noise49(c->z1, ga, c->twx, c->twy, c->stream), "correlated noise");
+            c->kernels += 2;
+        }
+        StepArgs a = c->sa;
+        a.src = c->pop[c->cur];
+        a.dst = c->pop[c->cur ^ 1];
+        a.xi49 = c->z1;
+        a.t_lo = tlo; a.t_hi = thi;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->timing) {
+            int r = record_timing(c, &e0, &e1);
+            if (r != LB_OK) return r;
+            CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
+        }
+        CK(c, launch_step(a, kmode, c->stream), "step kernel launch");
+        c->kernels += 1;
+        if (c->timing) {
+            CK(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
+            c->launches_acc++;
+        }
+        c->cur ^= 1;
+        c->t++;
+        if (c->every > 0 && c->t % c->every == 0) {
+            CK(c, launch_stats_sample(c->pop[c->cur], c->g, c->z1, c->z2, c->twx, c->twy, c->bins, c->nbins,
+                                      c->stream), "spectra sample");
+            c->kernels += 6;
+            c->nsamples++;
+        }
+    }
+    return LB_OK;
+}
+
+int lb_get_time(lb_ctx* c, int64_t* t) {
+    if (!c || !t) return LB_EINVAL;
+    *t = c->t;
+    return LB_OK;
+}
+
+int lb_set_populations(lb_ctx* c, const double* f, int loc, int64_t t) {
+    if (!c || !f || (loc != LB_HOST && loc != LB_DEVICE) || t < 0) return LB_EINVAL;
+    DeviceGuard dg(c->device);
+    double* stage = (double*)c->z1;     // n doubles of scratch
+    for (int i = 0; i < Q; ++i) {
+        const double* src = f + (long long)i * c->n;
+        if (loc == LB_HOST) {
+            CK(c, cudaMemcpyAsync(stage, src, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream), "H2D");
+            src = stage;
+        }
+        CK(c, launch_set_plane(src, c->pop[c->cur] + (long long)i * c->g.plane, c->g, i, c->fbar[i], c->stream),
+           "set populations");
+        c->kernels += 1;
+    }
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    c->t = t;
+    return LB_OK;
+}
+
+int lb_get_populations(lb_ctx* c, double* f, int loc) {
+    if (!c || !f || (loc != LB_HOST && loc != LB_DEVICE)) return LB_EINVAL;
+    DeviceGuard dg(c->device);
+    double* stage = (double*)c->z1;
+    for (int i = 0; i < Q; ++i) {
+        double* dst = (loc == LB_HOST) ? stage : f + (long long)i * c->n;
+        CK(c, launch_get_plane(c->pop[c->cur] + (long long)i * c->g.plane, c->g, i, c->fbar[i], dst, c->stream),
+           "get populations");
+        c->kernels += 1;
+        if (loc == LB_HOST)
+            CK(c, cudaMemcpyAsync(f + (long long)i * c->n, stage, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
+                                  c->stream), "D2H");
+    }
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_moments(lb_ctx* c, double* m, int loc, double sums[3]) {
+    if (!c || (m && loc != LB_HOST && loc != LB_DEVICE)) return LB_EINVAL;
+    DeviceGuard dg(c->device);
+    if (m) {
+        double* stage = (double*)c->z1;
+        for (int a = 0; a < Q; ++a) {
+            double* dst = (loc == LB_HOST) ? stage : m + (long long)a * c->n;
+            CK(c, launch_moment(c->pop[c->cur], c->g, a, c->fbar_dev, dst, c->stream), "moments");
+            c->kernels += 1;
+            if (loc == LB_HOST)
+                CK(c, cudaMemcpyAsync(m + (long long)a * c->n, stage, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
+                                      c->stream), "D2H");
+        }
+    }
+    if (sums) {
+        CK(c, launch_sums(c->pop[c->cur], c->g, c->fbar_dev, c->partial, c->sums3, c->stream), "sums");
+        c->kernels += 2;
+        CK(c, cudaMemcpyAsync(sums, c->sums3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    }
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_set_sampling(lb_ctx* c, int every, int nbins) {
+    if (!c) return LB_EINVAL;
+    if (every < 0) return fail(c, LB_EINVAL, "every must be >= 0");
+    DeviceGuard dg(c->device);
+    if (every == 0) {
+        c->every = 0;
+        return LB_OK;
+    }
+    if (!c->pow2) return fail(c, LB_EINVAL, "spectra need nx and ny powers of two (radix-2 FFT)");
+    if (nbins < 1 || nbins > MAX_BINS) return fail(c, LB_EINVAL, "nbins must lie in [1, 4096]");
+    c->every = every;
+    c->nbins = nbins;
+    c->nsamples = 0;
+    CK(c, cudaMemsetAsync(c->bins, 0, 3 * MAX_BINS * sizeof(double), c->stream), "memset");
+    CK(c, launch_bin_counts(c->nx, c->ny, nbins, c->counts, c->stream), "bin counts");
+    c->kernels += 1;
+    c->hcounts.assign(nbins, 0);
+    CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost,
+                          c->stream), "D2H");
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_structure_factor(lb_ctx* c, int nbins, double* S_rho, double* S_jl, double* S_jt, int64_t* counts,
+                        int64_t* nsamples) {
+    if (!c) return LB_EINVAL;
+    if (c->every == 0 && c->nbins == 0) return fail(c, LB_ESTATE, "sampling was never turned on");
+    if (nbins != c->nbins) return fail(c, LB_EINVAL, "nbins differs from lb_set_sampling");
+    DeviceGuard dg(c->device);
+    std::vector<double> h(3 * (size_t)nbins);
+    CK(c, cudaMemcpyAsync(h.data(), c->bins, sizeof(double) * nbins, cudaMemcpyDeviceToHost, c->stream), "D2H");
+    CK(c, cudaMemcpyAsync(h.data() + nbins, c->bins + nbins, sizeof(double) * nbins, cudaMemcpyDeviceToHost,
+                          c->stream), "D2H");
+    CK(c, cudaMemcpyAsync(h.data() + 2 * nbins, c->bins + 2 * nbins, sizeof(double) * nbins, cudaMemcpyDeviceToHost,
+                          c->stream), "D2H");
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    for (int b = 0; b < nbins; ++b) {
+        const double den = (double)c->hcounts[b] * (double)c->nsamples;
+        if (S_rho) S_rho[b] = den > 0 ? h[b] / den : 0.0;
+        if (S_jl) S_jl[b] = den > 0 ? h[nbins + b] / den : 0.0;
+        if (S_jt) S_jt[b] = den > 0 ? h[2 * nbins + b] / den : 0.0;
+        if (counts) counts[b] = (int64_t)c->hcounts[b];
+    }
+    if (nsamples) *nsamples = c->nsamples;
+    return LB_OK;
+}
+
+int lb_warnings(lb_ctx* c) { return c ? c->warnings : 0; }
+
+const char* lb_last_error(lb_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int lb_synchronize(lb_ctx* c) {
+    if (!c) return LB_EINVAL;
+    DeviceGuard dg(c->device);
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_set_kernel_timing(lb_ctx* c, int on) {
+    if (!c) return LB_EINVAL;
+    c->timing = on != 0;
+    c->ev_used = 0;
+    c->ms_acc = 0.0;
+    c->launches_acc = 0;
+    return LB_OK;
+}
+
+int lb_kernel_time(lb_ctx* c, double* ms, int64_t* launches) {
+    if (!c) return LB_EINVAL;
+    DeviceGuard dg(c->device);
+    double total = c->ms_acc;
+    if (c->ev_used > 0) {
+        CK(c, cudaEventSynchronize(c->ev[c->ev_used - 1].second), "cudaEventSynchronize");
+        for (size_t k = 0; k < c->ev_used; ++k) {
+            float v = 0.f;
+            CK(c, cudaEventElapsedTime(&v, c->ev[k].first, c->ev[k].second), "cudaEventElapsedTime");
+            total += v;
+        }
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = c->launches_acc;
+    return LB_OK;
+}
+
+int lb_launch_count(lb_ctx* c, int64_t* launches) {
+    if (!c || !launches) return LB_EINVAL;
+    *launches = c->kernels;
+    return LB_OK;
+}
+
+int lb_noise_matrix(double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
+                    double tau_ghost, double kx, double ky, double* xi) {
+    if (!xi) return LB_EINVAL;
+    const NoiseCoef c = noise_coef(rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost);
+    const double s = k2_lattice(kx, ky);
+    for (int k = 0; k < 81; ++k) xi[k] = 0.0;
+    xi[3 * 9 + 3] = c.a44 + c.b44 * s;
+    xi[3 * 9 + 8] = xi[8 * 9 + 3] = c.a49 + c.b49 * s;
+    xi[8 * 9 + 8] = c.a99 + c.b99 * s;
+    xi[4 * 9 + 4] = c.x55;
+    xi[5 * 9 + 5] = c.x66;
+    xi[6 * 9 + 6] = xi[7 * 9 + 7] = c.x77;
+    return LB_OK;
+}
+
+int lb_check_params(int nx, int ny, double rho0, double cs2, double kT, double kappa, double tau_s,
+                    double tau_b, double tau_ghost, int noise_mode) {
+    Grid g;
+    if (!make_grid(nx, ny, &g)) return LB_EINVAL;
+    return validate(nx, ny, rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode, nullptr);
+}
+
+}  // extern "C"

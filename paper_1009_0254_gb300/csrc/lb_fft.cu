@@ -1,0 +1,288 @@
+// lb_fft.cu -- radix-2 FFTs in shared memory, the k-space synthesis of the correlated
+// noise ([GACV] Sec. IV, last paragraph) and the sampled spectra ([GACV] Sec. V A).
+//
+// Transforms follow the unitary convention of [GACV] Sec. III:
+//   forward  a(k) = n^-1/2 sum_r exp(+i k.r) a(r)         (sign = +1)
+//   back     a(r) = n^-1/2 sum_k exp(-i k.r) a(k)         (sign = -1)
+// with k = 2 pi (mx/nx, my/ny).  Sizes are powers of two.  Each transform is a 2D
+// pass over rows (one CTA per row) followed by a pass over columns (a CTA per strip
+// of C adjacent columns), each an in-place decimation-in-time FFT on data loaded in
+// bit-reversed order into shared memory, with twiddles exp(-2 pi i k/n) computed on
+// the host in FP64.
+#include "lb_internal.cuh"
+
+namespace lbf {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev(v) >> (32 - bits); }
+
+// In-place DIT butterflies over `count` interleaved sequences of length n (log2n bits)
+// stored as s[e * count + c]; input already in bit-reversed order.
+__device__ __forceinline__ void smem_fft(float2* s, int n, int log2n, int count, int sign, const float2* tw) {
+    const int nth = blockDim.x;
+    const int tid = threadIdx.x;
+    const int total = (n >> 1) * count;
+    for (int lh = 0; lh < log2n; ++lh) {
+        const int h = 1 << lh;
+        __syncthreads();
+        for (int j = tid; j < total; j += nth) {
+            const int c = j % count;
+            const int b = j / count;
+            const int pos = b & (h - 1);
+            const int i0 = ((b - pos) << 1) + pos;
+            const int i1 = i0 + h;
+            float2 w = tw[pos << (log2n - 1 - lh)];
+            if (sign > 0) w.y = -w.y;
+            const float2 u = s[i0 * count + c];
+            const float2 v = cmul(w, s[i1 * count + c]);
+            s[i0 * count + c] = make_float2(u.x + v.x, u.y + v.y);
+            s[i1 * count + c] = make_float2(u.x - v.x, u.y - v.y);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
+
+// Correlated noise of modes 4 and 9 in k-space: xi(k) = L(k) eta(k) with L L^T the
+// (4,9) block of Xi(k), Eq. (noise-yeo); packed as Z = xi_4(k) + i xi_9(k).  The pair
+// (k, -k) shares one Philox draw owned by the lower linear index, so eta(-k) = eta(k)*.
+__device__ __forceinline__ float2 noise49_k(const NoiseGenArgs& ga, int mx, int my) {
+    const uint32_t lin = (uint32_t)my * ga.nx + mx;
+    const uint32_t cx = (uint32_t)((ga.nx - mx) & (ga.nx - 1));
+    const uint32_t cy = (uint32_t)((ga.ny - my) & (ga.ny - 1));
+    const uint32_t conj = cy * ga.nx + cx;
+    const uint32_t owner = lin < conj ? lin : conj;
+    const uint4 r = philox4x32_10(make_uint4(owner, ga.t_lo, ga.t_hi, TAG_KSPACE), ga.key0, ga.key1);
+    const float2 g01 = gauss_pair(r.x, r.y);
+    const float2 g23 = gauss_pair(r.z, r.w);
+    float2 e1, e2;
+    if (lin == conj) {
+        e1 = make_float2(g01.x, 0.f);
+        e2 = make_float2(g23.x, 0.f);
+    } else {
+        const float h = 0.70710678118654752f;
+        e1 = make_float2(g01.x * h, g01.y * h);
+        e2 = make_float2(g23.x * h, g23.y * h);
+        if (lin != owner) { e1.y = -e1.y; e2.y = -e2.y; }
+    }
+    // Appendix B: k^2 = 10/3 - 4/3 (cos kx + cos ky) - 2/3 cos kx cos ky
+    const float ckx = ga.cosx[mx], cky = ga.cosy[my];
+    const float s = (10.0f / 3.0f) - (4.0f / 3.0f) * (ckx + cky) - (2.0f / 3.0f) * (ckx * cky);
+    const float x44 = ga.a44 + ga.b44 * s;
+    const float x49 = ga.a49 + ga.b49 * s;
+    const float x99 = ga.a99 + ga.b99 * s;
+    const float L44 = sqrtf(fmaxf(x44, 0.f));
+    const float L94 = L44 > 0.f ? x49 / L44 : 0.f;
+    const float L99 = sqrtf(fmaxf(x99 - L94 * L94, 0.f));
+    const float2 z4 = make_float2(L44 * e1.x, L44 * e1.y);
+    const float2 z9 = make_float2(L94 * e1.x + L99 * e2.x, L94 * e1.y + L99 * e2.y);
+    return make_float2(z4.x - z9.y, z4.y + z9.x);
+}
+
+// Row pass.  GEN = true: the row is synthesised (noise49_k) instead of loaded.
+template <bool GEN>
+__global__ void fft_rows_kernel(float2* data, int nx, int sign, const float2* __restrict__ twx,
+                                NoiseGenArgs ga) {
+    extern __shared__ float2 sm[];
+    const int log2n = ilog2(nx);
+    float2* tw = sm + nx;
+    const int row = blockIdx.x;
+    for (int j = threadIdx.x; j < (nx >> 1); j += blockDim.x) tw[j] = twx[j];
+    float2* rowp = data + (long long)row * nx;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        float2 v = GEN ? noise49_k(ga, j, row) : rowp[j];
+        sm[bitrev(j, log2n)] = v;
+    }
+    smem_fft(sm, nx, log2n, 1, sign, tw);
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) rowp[j] = sm[j];
+}
+
+// Column pass over strips of `count` adjacent columns, scaled by `scale` on the way out.
+__global__ void fft_cols_kernel(float2* data, int nx, int ny, int count, int sign,
+                                const float2* __restrict__ twy, float scale) {
+    extern __shared__ float2 sm[];
+    const int log2n = ilog2(ny);
+    float2* tw = sm + (long long)ny * count;
+    for (int j = threadIdx.x; j < (ny >> 1); j += blockDim.x) tw[j] = twy[j];
+    const int xs = blockIdx.x * count;
+    const int total = ny * count;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int c = e % count, r = e / count;
+        sm[bitrev(r, log2n) * count + c] = data[(long long)r * nx + xs + c];
+    }
+    smem_fft(sm, ny, log2n, count, sign, tw);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int c = e % count, r = e / count;
+        const float2 v = sm[r * count + c];
+        data[(long long)r * nx + xs + c] = make_float2(v.x * scale, v.y * scale);
+    }
+}
+
+static int col_strip(int nx, int ny) {
+    // strip width: as many columns as fit in ~160 KB of shared memory, at most 16
+    int c = 16;
+    while (c > 1 && ((long long)ny * c * 8 + (long long)(ny / 2) * 8 > 160 * 1024)) c >>= 1;
+    if (c > nx) c = nx;
+    return c;
+}
+
+static cudaError_t rows_pass(float2* data, int nx, int ny, int sign, const float2* twx, bool gen,
+                             const NoiseGenArgs& ga, cudaStream_t s) {
+    const size_t smem = (size_t)nx * 8 + (size_t)(nx / 2 > 0 ? nx / 2 : 1) * 8;
+    int threads = nx / 2;
+    if (threads > 512) threads = 512;
+    if (threads < 32) threads = 32;
+    cudaError_t e;
+    if (gen) {
+        e = cudaFuncSetAttribute(fft_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fft_rows_kernel<true><<<ny, threads, smem, s>>>(data, nx, sign, twx, ga);
+    } else {
+        e = cudaFuncSetAttribute(fft_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fft_rows_kernel<false><<<ny, threads, smem, s>>>(data, nx, sign, twx, ga);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t cols_pass(float2* data, int nx, int ny, int sign, const float2* twy, float scale,
+                             cudaStream_t s) {
+    const int c = col_strip(nx, ny);
+    const size_t smem = (size_t)ny * c * 8 + (size_t)(ny / 2 > 0 ? ny / 2 : 1) * 8;
+    int threads = (ny / 2) * c;
+    if (threads > 512) threads = 512;
+    if (threads < 32) threads = 32;
+    cudaError_t e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fft_cols_kernel<<<nx / c, threads, smem, s>>>(data, nx, ny, c, sign, twy, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft2d(float2* data, int nx, int ny, int sign, const float2* twx, const float2* twy,
+                         float scale, cudaStream_t s) {
+    NoiseGenArgs none{};
+    cudaError_t e = rows_pass(data, nx, ny, sign, twx, false, none, s);
+    if (e != cudaSuccess) return e;
+    return cols_pass(data, nx, ny, sign, twy, scale, s);
+}
+
+cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
+                           cudaStream_t s) {
+    // synthesise xi(k) row by row, transform back along x, then along y with n^-1/2
+    cudaError_t e = rows_pass(buf, ga.nx, ga.ny, -1, twx, true, ga, s);
+    if (e != cudaSuccess) return e;
+    const float scale = (float)(1.0 / sqrt((double)ga.nx * (double)ga.ny));
+    return cols_pass(buf, ga.nx, ga.ny, -1, twy, scale, s);
+}
+
+// --- sampled spectra ---------------------------------------------------------------
+
+// z1 = drho + i jx, z2 = jy of the pre-collision state f_i(r) = f*_i(r - c_i)
+__global__ void stats_fields_kernel(const float* __restrict__ src, Grid g, float2* z1, float2* z2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= g.nx) return;
+    const long long P = g.plane;
+    const long long c = g.at(x, y);
+    const float f0 = src[c], f1 = src[P + c - 1], f2 = src[2 * P + c - g.pitch], f3 = src[3 * P + c + 1];
+    const float f4 = src[4 * P + c + g.pitch], f5 = src[5 * P + c - g.pitch - 1];
+    const float f6 = src[6 * P + c - g.pitch + 1], f7 = src[7 * P + c + g.pitch + 1];
+    const float f8 = src[8 * P + c + g.pitch - 1];
+    const float drho = f0 + ((f1 + f3) + (f2 + f4)) + ((f5 + f7) + (f6 + f8));
+    const float jx = (f1 - f3) + (f5 - f7) + (f8 - f6);
+    const float jy = (f2 - f4) + (f5 - f7) + (f6 - f8);
+    const long long o = (long long)y * g.nx + x;
+    z1[o] = make_float2(drho, jx);
+    z2[o] = make_float2(jy, 0.f);
+}
+
+// Radial bin of wavevector (mx, my), decided in FP64 with explicitly rounded
+// operations (no contraction), matching a plain double evaluation of
+// floor(sqrt(kx^2 + ky^2) / (pi sqrt 2 / nbins)), kx = (2 pi mx_w) / nx.
+__device__ __forceinline__ int k_bin(int mx, int my, int nx, int ny, int nbins, double* kx_o, double* ky_o) {
+    const int mxw = mx > nx / 2 ? mx - nx : mx;
+    const int myw = my > ny / 2 ? my - ny : my;
+    const double two_pi = 6.283185307179586;
+    const double kx = __ddiv_rn(__dmul_rn(two_pi, (double)mxw), (double)nx);
+    const double ky = __ddiv_rn(__dmul_rn(two_pi, (double)myw), (double)ny);
+    const double km = __dsqrt_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)));
+    const double width = __ddiv_rn(__dmul_rn(3.141592653589793, 1.4142135623730951), (double)nbins);
+    int b = (int)floor(__ddiv_rn(km, width));
+    if (b > nbins - 1) b = nbins - 1;
+    *kx_o = kx;
+    *ky_o = ky;
+    return b;
+}
+
+__global__ void bin_kernel(const float2* __restrict__ z1, const float2* __restrict__ z2, int nx, int ny,
+                           int nbins, double* bins) {
+    extern __shared__ double sb[];   // 3 * nbins
+    for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x) sb[j] = 0.0;
+    __syncthreads();
+    for (int my = blockIdx.x; my < ny; my += gridDim.x)
+    for (int mx = threadIdx.x; mx < nx; mx += blockDim.x) {
+        if (mx == 0 && my == 0) continue;
+        double kx, ky;
+        const int b = k_bin(mx, my, nx, ny, nbins, &kx, &ky);
+        const int cx = (nx - mx) & (nx - 1), cy = (ny - my) & (ny - 1);
+        const float2 a = z1[(long long)my * nx + mx];
+        const float2 am = z1[(long long)cy * nx + cx];
+        const float2 c = z2[(long long)my * nx + mx];
+        // z1 = drho + i jx (both real fields): drho(k) = (Z(k) + Z(-k)*)/2, jx(k) = (Z(k) - Z(-k)*)/(2i)
+        const double rr = 0.5 * ((double)a.x + (double)am.x), ri = 0.5 * ((double)a.y - (double)am.y);
+        const double xr = 0.5 * ((double)a.y + (double)am.y), xi = -0.5 * ((double)a.x - (double)am.x);
+        const double yr = (double)c.x, yi = (double)c.y;
+        const double km = sqrt(kx * kx + ky * ky);
+        const double lr = (kx * xr + ky * yr) / km, li = (kx * xi + ky * yi) / km;
+        const double tr = (-ky * xr + kx * yr) / km, ti = (-ky * xi + kx * yi) / km;
+        atomicAdd(&sb[b], rr * rr + ri * ri);
+        atomicAdd(&sb[nbins + b], lr * lr + li * li);
+        atomicAdd(&sb[2 * nbins + b], tr * tr + ti * ti);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x)
+        if (sb[j] != 0.0) atomicAdd(&bins[j], sb[j]);
+}
+
+__global__ void count_kernel(int nx, int ny, int nbins, unsigned long long* counts) {
+    const long long n = (long long)nx * ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (i == 0) continue;
+        double kx, ky;
+        const int b = k_bin((int)(i % nx), (int)(i / nx), nx, ny, nbins, &kx, &ky);
+        atomicAdd(&counts[b], 1ull);
+    }
+}
+
+cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned long long* counts, cudaStream_t s) {
+    cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * nbins, s);
+    count_kernel<<<256, 256, 0, s>>>(nx, ny, nbins, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_sample(const float* pops, const Grid& g, float2* z1, float2* z2,
+                                const float2* twx, const float2* twy, double* bins, int nbins,
+                                cudaStream_t s) {
+    dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
+    stats_fields_kernel<<<grd, blk, 0, s>>>(pops, g, z1, z2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const float scale = (float)(1.0 / sqrt((double)g.nx * (double)g.ny));
+    e = launch_fft2d(z1, g.nx, g.ny, +1, twx, twy, scale, s);
+    if (e != cudaSuccess) return e;
+    e = launch_fft2d(z2, g.nx, g.ny, +1, twx, twy, scale, s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)3 * nbins * sizeof(double);
+    e = cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int bx = g.nx >= 256 ? 256 : 64;
+    const int nblk = g.ny < 304 ? g.ny : 304;   // two blocks per SM, each over many rows
+    bin_kernel<<<nblk, bx, smem, s>>>(z1, z2, g.nx, g.ny, nbins, bins);
+    return cudaGetLastError();
+}
+
+}  // namespace lbf

@@ -83,7 +83,11 @@ def test_moments_and_sums_match_oracle():
     m, s = g.moments()
     mo = o.moments()
     np.testing.assert_allclose(m, mo, atol=4 * TOL)
-    np.testing.assert_allclose(s, mo[:3].sum(axis=(1, 2)), rtol=1e-9, atol=1e-9)
+    # the device FP64 reduction equals the sum of the device's own FP64 moments ...
+    np.testing.assert_allclose(s, m[:3].sum(axis=(1, 2)), rtol=1e-13, atol=1e-13)
+    # ... and the oracle's sums up to the FP32 rounding of n stored nodes (~1e-7 each)
+    n = 40 * 24
+    np.testing.assert_allclose(s, mo[:3].sum(axis=(1, 2)), rtol=0, atol=30 * 1e-7 * np.sqrt(n))
 
 
 def test_full_size_sampled_parity_and_conservation():

@@ -6,6 +6,7 @@
 // and the launch sequence of one time step.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -27,7 +28,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
 
 struct WsLayout {
-    size_t pop[2], z1, z2, twx, twy, cosx, cosy, bins, counts, partial, sums3, fbar, total;
+    size_t pop[2], z1, z2, twx, twy, cosx, cosy, bins, counts, partial, sums3, fbar, err, total;
 };
 
 bool make_grid(int nx, int ny, Grid* g) {
@@ -57,6 +58,7 @@ WsLayout make_layout(const Grid& g) {
     L.partial = take((size_t)sums_partial_count() * sizeof(double));
     L.sums3 = take(3 * sizeof(double));
     L.fbar = take(Q * sizeof(double));
+    L.err = take(sizeof(int));
     L.total = off;
     return L;
 }
@@ -181,7 +183,10 @@ struct lb_ctx {
     float *cosx = nullptr, *cosy = nullptr;
     double *bins = nullptr, *partial = nullptr, *sums3 = nullptr, *fbar_dev = nullptr;
     unsigned long long* counts = nullptr;
+    int* err_dev = nullptr;          // set by a kernel whose bounded wait gave up
     bool pow2 = false;
+    bool use_tma = false;            // TMA-staged persistent step kernel
+    alignas(64) unsigned char tmap[2][128];
     double fbar[Q] = {};
     // parameters
     bool have_params = false;
@@ -221,6 +226,19 @@ static int cuda_fail(lb_ctx* c, cudaError_t e, const char* where) {
         cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
     } while (0)
+
+// Reads the device error word (after the stream has drained); a bounded wait that gave
+// up in a kernel is reported as LB_ETIMEOUT and cleared.
+static int check_device_error(lb_ctx* c) {
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (h != 0) {
+        CK(c, cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream), "memset");
+        return fail(c, LB_ETIMEOUT, "a step kernel gave up waiting for its TMA loads");
+    }
+    return LB_OK;
+}
 
 extern "C" {
 
@@ -271,7 +289,14 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     c->partial = (double*)(c->ws + c->L.partial);
     c->sums3 = (double*)(c->ws + c->L.sums3);
     c->fbar_dev = (double*)(c->ws + c->L.fbar);
+    c->err_dev = (int*)(c->ws + c->L.err);
     rest_populations(rho0, cs2, c->fbar);
+    {
+        const char* v = std::getenv("LBFLUCT_STEP_KERNEL");
+        const bool want_tma = !(v && std::strcmp(v, "simple") == 0);
+        c->use_tma = want_tma && tensor_map_bytes() <= sizeof(c->tmap[0]) &&
+                     make_pop_tensor_map(c->pop[0], g, c->tmap[0]) && make_pop_tensor_map(c->pop[1], g, c->tmap[1]);
+    }
 
     // host tables in FP64 -> device
     std::vector<float2> tw(std::max(nx, ny) / 2 + 1);
@@ -293,6 +318,7 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     if (e == cudaSuccess) e = cudaMemset(c->pop[0], 0, (size_t)Q * g.plane * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, (size_t)Q * g.plane * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->bins, 0, 3 * MAX_BINS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->err_dev, 0, sizeof(int));
     if (e != cudaSuccess) {
         if (c->owns) cudaFree(c->ws);
         delete c;
@@ -301,8 +327,7 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     c->sa.g = g;
     c->sa.rho0 = (float)rho0;
     c->sa.cs2m = (float)(cs2 - SIGMA_S2);
-    c->sa.key0 = (uint32_t)(seed & 0xffffffffu);
-    c->sa.key1 = (uint32_t)(seed >> 32);
+    c->sa.rk = make_round_keys(seed);
     *out = c;
     return LB_OK;
 }
@@ -353,7 +378,7 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     ga.a49 = (float)nc.a49; ga.b49 = (float)nc.b49;
     ga.a99 = (float)nc.a99; ga.b99 = (float)nc.b99;
     ga.cosx = c->cosx; ga.cosy = c->cosy; ga.nx = c->nx; ga.ny = c->ny;
-    ga.key0 = a.key0; ga.key1 = a.key1;
+    ga.rk = a.rk;
     c->have_params = true;
     return LB_OK;
 }
@@ -410,7 +435,10 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
             if (r != LB_OK) return r;
             CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
         }
-        CK(c, launch_step(a, kmode, c->stream), "step kernel launch");
+        if (c->use_tma)
+            CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->stream), "step kernel launch");
+        else
+            CK(c, launch_step_simple(a, kmode, c->stream), "step kernel launch");
         c->kernels += 1;
         if (c->timing) {
             CK(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
@@ -467,7 +495,7 @@ int lb_get_populations(lb_ctx* c, double* f, int loc) {
                                   c->stream), "D2H");
     }
     CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    return LB_OK;
+    return check_device_error(c);
 }
 
 int lb_moments(lb_ctx* c, double* m, int loc, double sums[3]) {
@@ -490,7 +518,7 @@ int lb_moments(lb_ctx* c, double* m, int loc, double sums[3]) {
         CK(c, cudaMemcpyAsync(sums, c->sums3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
     }
     CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    return LB_OK;
+    return check_device_error(c);
 }
 
 int lb_set_sampling(lb_ctx* c, int every, int nbins) {
@@ -548,7 +576,7 @@ int lb_synchronize(lb_ctx* c) {
     if (!c) return LB_EINVAL;
     DeviceGuard dg(c->device);
     CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    return LB_OK;
+    return check_device_error(c);
 }
 
 int lb_set_kernel_timing(lb_ctx* c, int on) {

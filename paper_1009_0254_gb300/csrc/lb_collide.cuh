@@ -1,0 +1,106 @@
+// lb_collide.cuh -- the per-node fluctuating collision of [GACV] Eq. (fluct-lin-lbe),
+// shared by the step kernels.  Input: the nine pulled FP32 deviations f_i(r,t) - fbar_i
+// and the density deviations on the 3x3 neighbourhood; output: the nine post-collision
+// deviations f*_i(r,t) - fbar_i.
+#pragma once
+
+#include "lb_internal.cuh"
+
+namespace lbf {
+
+// density deviation with one fixed summation order (used for a node and for the ring)
+__device__ __forceinline__ float drho_of(const float f[Q]) {
+    const float sa = (f[1] + f[3]) + (f[2] + f[4]);
+    const float sd = (f[5] + f[7]) + (f[6] + f[8]);
+    return f[0] + sa + sd;
+}
+
+// Density deviations around the node: C centre, E/W = x +- 1, N/S = y +- 1.
+struct Nbr {
+    float C, E, W, N, S, NE, NW, SE, SW;
+};
+
+// MODE 0: no noise; 1: uncorrelated (long-wavelength or diagonal); 2: correlated
+// (xi_4, xi_9 given in xi49).
+template <int MODE>
+__device__ __forceinline__ void collide_node(const StepArgs& a, const float f[Q], const Nbr& r, uint32_t node,
+                                             float2 xi49, float o[Q]) {
+    // Appendix B: sum_{i != 1} w_i [rho(r+c_i) + rho(r-c_i) - 2 rho(r)] / sigma_s^2
+    const float lap = (4.0f * ((r.E + r.W) + (r.N + r.S)) + ((r.NE + r.SW) + (r.NW + r.SE)) - 20.0f * r.C) *
+                      (1.0f / 6.0f);
+    // d_alpha rho = 3 sum_i w_i c_i,alpha rho(r + c_i)
+    const float gx = (r.E - r.W) * (1.0f / 3.0f) + ((r.NE - r.SW) + (r.SE - r.NW)) * (1.0f / 12.0f);
+    const float gy = (r.N - r.S) * (1.0f / 3.0f) + ((r.NE - r.SW) + (r.NW - r.SE)) * (1.0f / 12.0f);
+
+    // moments of the deviations (rows of T, Eq. Tmat)
+    const float sa = (f[1] + f[3]) + (f[2] + f[4]);
+    const float sd = (f[5] + f[7]) + (f[6] + f[8]);
+    const float drho = f[0] + sa + sd;
+    const float ax = f[1] - f[3], ay = f[2] - f[4];
+    const float dx = (f[5] - f[7]) + (f[8] - f[6]);
+    const float dy = (f[5] - f[7]) + (f[6] - f[8]);
+    const float jx = ax + dx, jy = ay + dy;
+    const float m4 = -2.0f * f[0] + sa + 4.0f * sd;
+    const float m5 = (f[1] + f[3]) - (f[2] + f[4]);
+    const float m6 = (f[5] + f[7]) - (f[6] + f[8]);
+    const float m7 = 2.0f * dx - ax;
+    const float m8 = 2.0f * dy - ay;
+    const float m9 = 2.0f * f[0] - 4.0f * sa + 8.0f * sd;
+
+    // equilibrium deviations, Table II (p0 = cs2 rho, C_n = 0)
+    const float rho = a.rho0 + drho;
+    const float inv = 1.0f / rho;
+    const float ux = jx * inv, uy = jy * inv;
+    const float iso = a.cs2m * drho - a.kappa * rho * lap;
+    const float e_eq = 3.0f * (jx * ux + jy * uy) + 6.0f * iso;
+    const float pww_eq = (jx * ux - jy * uy) + a.kappa * (gx * gx - gy * gy);
+    const float pxy_eq = jx * uy + a.kappa * gx * gy;
+    const float eps_eq = -6.0f * iso - 3.0f * a.kappa * (gx * gx + gy * gy);
+
+    // noise, Sec. IV
+    float xi4 = 0.f, xi5 = 0.f, xi6 = 0.f, xi7 = 0.f, xi8 = 0.f, xi9 = 0.f;
+    if (MODE != 0) {
+        const uint4 r0 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_MODES_5_8), a.rk);
+        const float2 g01 = gauss_pair(r0.x, r0.y);
+        const float2 g23 = gauss_pair(r0.z, r0.w);
+        xi5 = a.s5 * g01.x;
+        xi6 = a.s6 * g01.y;
+        xi7 = a.s7 * g23.x;
+        xi8 = a.s7 * g23.y;
+        if (MODE == 1) {
+            const uint4 r1 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_MODES_4_9), a.rk);
+            const float2 n49 = gauss_pair(r1.x, r1.y);
+            xi4 = a.L44 * n49.x;
+            xi9 = a.L94 * n49.x + a.L99 * n49.y;
+        } else {
+            xi4 = xi49.x;
+            xi9 = xi49.y;
+        }
+    }
+
+    // relaxation of the non-conserved modes, Eq. (fluct-lin-lbe)
+    const float m4s = m4 + a.lb * (m4 - e_eq) + xi4;
+    const float m5s = m5 + a.ls * (m5 - pww_eq) + xi5;
+    const float m6s = m6 + a.ls * (m6 - pxy_eq) + xi6;
+    const float m7s = m7 + a.lq * m7 + xi7;
+    const float m8s = m8 + a.lq * m8 + xi8;
+    const float m9s = m9 + a.le * (m9 - eps_eq) + xi9;
+
+    // back to populations: f*_i = w_i sum_a T_ai m*_a / N_a
+    const float u1 = drho, u2 = 3.0f * jx, u3 = 3.0f * jy;
+    const float u4 = 0.25f * m4s, u5 = 2.25f * m5s, u6 = 9.0f * m6s;
+    const float u7 = 1.5f * m7s, u8 = 1.5f * m8s, u9 = 0.0625f * m9s;
+    const float base_a = u1 + u4 - 4.0f * u9;
+    const float base_d = u1 + 4.0f * u4 + 8.0f * u9;
+    o[0] = (4.0f / 9.0f) * (u1 - 2.0f * u4 + 2.0f * u9);
+    o[1] = (1.0f / 9.0f) * (base_a + u2 + u5 - u7);
+    o[2] = (1.0f / 9.0f) * (base_a + u3 - u5 - u8);
+    o[3] = (1.0f / 9.0f) * (base_a - u2 + u5 + u7);
+    o[4] = (1.0f / 9.0f) * (base_a - u3 - u5 + u8);
+    o[5] = (1.0f / 36.0f) * (base_d + u2 + u3 + u6 + 2.0f * u7 + 2.0f * u8);
+    o[6] = (1.0f / 36.0f) * (base_d - u2 + u3 - u6 - 2.0f * u7 + 2.0f * u8);
+    o[7] = (1.0f / 36.0f) * (base_d - u2 - u3 + u6 - 2.0f * u7 - 2.0f * u8);
+    o[8] = (1.0f / 36.0f) * (base_d + u2 - u3 - u6 + 2.0f * u7 - 2.0f * u8);
+}
+
+}  // namespace lbf

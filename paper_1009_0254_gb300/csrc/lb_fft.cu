@@ -56,7 +56,7 @@ __device__ __forceinline__ float2 noise49_k(const NoiseGenArgs& ga, int mx, int 
     const uint32_t cy = (uint32_t)((ga.ny - my) & (ga.ny - 1));
     const uint32_t conj = cy * ga.nx + cx;
     const uint32_t owner = lin < conj ? lin : conj;
-    const uint4 r = philox4x32_10(make_uint4(owner, ga.t_lo, ga.t_hi, TAG_KSPACE), ga.key0, ga.key1);
+    const uint4 r = philox4x32_10(make_uint4(owner, ga.t_lo, ga.t_hi, TAG_KSPACE), ga.rk);
     const float2 g01 = gauss_pair(r.x, r.y);
     const float2 g23 = gauss_pair(r.z, r.w);
     float2 e1, e2;

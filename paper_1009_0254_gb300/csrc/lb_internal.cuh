@@ -27,6 +27,24 @@ struct Grid {
     }
 };
 
+// Philox4x32-10 round keys: round r uses (k0 + r W0, k1 + r W1) mod 2^32, computed once on
+// the host so that every round is two wide multiplies and two three-input XORs.
+struct RoundKeys {
+    uint32_t k[20];
+};
+
+inline RoundKeys make_round_keys(uint64_t seed) {
+    RoundKeys rk;
+    uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = k0;
+        rk.k[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return rk;
+}
+
 // Arguments of the fused step kernel (by value).
 struct StepArgs {
     Grid g;
@@ -39,7 +57,8 @@ struct StepArgs {
     float lb, ls, lq, le;            // lambda_b, lambda_s, lambda_q, lambda_eps
     float L44, L94, L99;             // Cholesky factor of the (4,9) block of Xi(0)
     float s5, s6, s7;                // sqrt(Xi_55), sqrt(Xi_66), sqrt(Xi_77) = sqrt(Xi_88)
-    uint32_t key0, key1, t_lo, t_hi;
+    uint32_t t_lo, t_hi;
+    RoundKeys rk;
 };
 
 // k-space synthesis of the correlated (4,9) noise: Xi_ab(k) = a_ab + b_ab s(k) with s
@@ -49,41 +68,45 @@ struct NoiseGenArgs {
     const float* cosx;   // cos(2 pi m / nx), m < nx
     const float* cosy;   // cos(2 pi m / ny), m < ny
     int nx, ny;
-    uint32_t key0, key1, t_lo, t_hi;
+    uint32_t t_lo, t_hi;
+    RoundKeys rk;
 };
 
 // ---------------------------------------------------------------------------
 // Counter-based random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k[2 * r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk.k[2 * r + 1], (uint32_t)p0);
     }
     return c;
 }
 
-// Two unit normals by Box-Muller from two 32-bit words.  u = (2k+1) 2^-24 with k the
-// top 23 bits is exact in FP32; the angle uses sincospif on 2u (also exact).
+// Two unit normals by Box-Muller, sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2), from two
+// 32-bit words: u = (2k+1) 2^-24 with k the top 23 bits, exact in FP32.  Evaluated with
+// the hardware approximations of log2, rsqrt, sin and cos (absolute error below 1e-6 in
+// the normal except for u1 within ~1e-6 of 1, where r itself is below 1.5e-3 and the error
+// below 7e-4); cos(2 pi u) = -cos(2 pi (u - 1/2)) keeps the angle in [-pi, pi].
 __device__ __forceinline__ float2 gauss_pair(uint32_t a, uint32_t b) {
     const float u1 = __uint2float_rn(a >> 9) * 0x1p-23f + 0x1p-24f;
     const float u2 = __uint2float_rn(b >> 9) * 0x1p-23f + 0x1p-24f;
-    const float r = sqrtf(-2.0f * logf(u1));
-    float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    return make_float2(r * c, r * s);
+    const float l = fmaxf(-1.3862943611198906f * __log2f(u1), 0.0f);     // -2 ln u1 = -2 ln2 log2 u1
+    const float r = l * rsqrtf(l + 1e-30f);
+    const float th = 6.2831853071795865f * (u2 - 0.5f);
+    return make_float2(-r * __cosf(th), -r * __sinf(th));
 }
 
 // noise draw tags (fourth counter word)
 constexpr uint32_t TAG_MODES_5_8 = 0;   // nu_5..nu_8
 constexpr uint32_t TAG_MODES_4_9 = 1;   // (nu_4, nu_9)
 constexpr uint32_t TAG_KSPACE = 2;      // eta_1(k), eta_2(k)
+
+// Stores the nine planes of one node, and its periodic ghost copies near an edge.
+__device__ __forceinline__ void store9(float* dst, long long P, const Grid& g, int x, int y, const float o[Q]);
 
 // Writes v at (x, y) of a plane and at the ghost copies that (x, y) feeds.
 __device__ __forceinline__ void store_with_ghosts(float* plane, const Grid& g, int x, int y, float v) {
@@ -106,11 +129,26 @@ __device__ __forceinline__ void store_with_ghosts(float* plane, const Grid& g, i
     }
 }
 
+__device__ __forceinline__ void store9(float* dst, long long P, const Grid& g, int x, int y, const float o[Q]) {
+    const bool edge = (x < 2) | (x >= g.nx - 2) | (y < 2) | (y >= g.ny - 2);
+    if (!edge) {
+        const long long c = g.at(x, y);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dst[i * P + c] = o[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) store_with_ghosts(dst + i * P, g, x, y, o[i]);
+    }
+}
+
 }  // namespace lbf
 
 // Launchers implemented in the .cu files (host side).
 namespace lbf {
-cudaError_t launch_step(const StepArgs& a, int noise_mode, cudaStream_t s);
+cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, cudaStream_t s);
+cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, cudaStream_t s);
+bool make_pop_tensor_map(const float* buf, const Grid& g, void* map_out);
+size_t tensor_map_bytes();
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s);
 cudaError_t launch_stats_sample(const float* pops, const Grid& g, float2* z1, float2* z2,

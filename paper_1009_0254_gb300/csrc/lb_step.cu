@@ -13,7 +13,7 @@
 //   store  f*_i(r,t) with its periodic ghost copies.
 // Everything is FP32 on deviations from the rest state fbar_i, which keeps the
 // small fluctuations (~sqrt(kT)) at full relative precision.
-#include "lb_internal.cuh"
+#include "lb_collide.cuh"
 
 namespace lbf {
 
@@ -36,13 +36,6 @@ __device__ __forceinline__ void pull9(const float* __restrict__ s, long long P, 
     f[6] = __ldg(s + 6 * P + c - pitch + 1);       // c = (-1, 1)
     f[7] = __ldg(s + 7 * P + c + pitch + 1);       // c = (-1,-1)
     f[8] = __ldg(s + 8 * P + c + pitch - 1);       // c = ( 1,-1)
-}
-
-// density deviation with one fixed summation order (used for the node and the ring)
-__device__ __forceinline__ float drho_of(const float f[Q]) {
-    const float sa = (f[1] + f[3]) + (f[2] + f[4]);
-    const float sd = (f[5] + f[7]) + (f[6] + f[8]);
-    return f[0] + sa + sd;
 }
 
 template <int BX, int BY, int MODE>
@@ -89,97 +82,24 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
     __syncthreads();
     if (!own) return;
 
-    // 3. stencils on the density (deviations; the constant rho0 drops out)
-    const float rC = rs[ty + 1][tx + 1];
-    const float rE = rs[ty + 1][tx + 2], rW = rs[ty + 1][tx];
-    const float rN = rs[ty + 2][tx + 1], rS = rs[ty][tx + 1];
-    const float rNE = rs[ty + 2][tx + 2], rNW = rs[ty + 2][tx];
-    const float rSE = rs[ty][tx + 2], rSW = rs[ty][tx];
-    // Appendix B: sum_{i != 1} w_i [rho(r+c_i) + rho(r-c_i) - 2 rho(r)] / sigma_s^2
-    const float lap = (4.0f * ((rE + rW) + (rN + rS)) + ((rNE + rSW) + (rNW + rSE)) - 20.0f * rC) * (1.0f / 6.0f);
-    // d_alpha rho = 3 sum_i w_i c_i,alpha rho(r + c_i)
-    const float gxr = (rE - rW) * (1.0f / 3.0f) + ((rNE - rSW) + (rSE - rNW)) * (1.0f / 12.0f);
-    const float gyr = (rN - rS) * (1.0f / 3.0f) + ((rNE - rSW) + (rNW - rSE)) * (1.0f / 12.0f);
-
-    // 4. moments of the deviations (rows of T, Eq. Tmat)
-    const float sa = (f[1] + f[3]) + (f[2] + f[4]);
-    const float sd = (f[5] + f[7]) + (f[6] + f[8]);
-    const float drho = f[0] + sa + sd;
-    const float ax = f[1] - f[3], ay = f[2] - f[4];
-    const float dx = (f[5] - f[7]) + (f[8] - f[6]);
-    const float dy = (f[5] - f[7]) + (f[6] - f[8]);
-    const float jx = ax + dx, jy = ay + dy;
-    const float m4 = -2.0f * f[0] + sa + 4.0f * sd;
-    const float m5 = (f[1] + f[3]) - (f[2] + f[4]);
-    const float m6 = (f[5] + f[7]) - (f[6] + f[8]);
-    const float m7 = 2.0f * dx - ax;
-    const float m8 = 2.0f * dy - ay;
-    const float m9 = 2.0f * f[0] - 4.0f * sa + 8.0f * sd;
-
-    // 5. equilibrium deviations, Table II
-    const float rho = a.rho0 + drho;
-    const float inv = 1.0f / rho;
-    const float ux = jx * inv, uy = jy * inv;
-    const float iso = a.cs2m * drho - a.kappa * rho * lap;        // p0 - rho s^2 - k rho lap, minus rest value
-    const float e_eq = 3.0f * (jx * ux + jy * uy) + 6.0f * iso;
-    const float pww_eq = (jx * ux - jy * uy) + a.kappa * (gxr * gxr - gyr * gyr);
-    const float pxy_eq = jx * uy + a.kappa * gxr * gyr;
-    const float eps_eq = -6.0f * iso - 3.0f * a.kappa * (gxr * gxr + gyr * gyr);
-
-    // 6. noise
-    float xi4 = 0.f, xi5 = 0.f, xi6 = 0.f, xi7 = 0.f, xi8 = 0.f, xi9 = 0.f;
-    if (MODE != 0) {
-        const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
-        const uint4 r0 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_MODES_5_8), a.key0, a.key1);
-        const float2 g01 = gauss_pair(r0.x, r0.y);
-        const float2 g23 = gauss_pair(r0.z, r0.w);
-        xi5 = a.s5 * g01.x;
-        xi6 = a.s6 * g01.y;
-        xi7 = a.s7 * g23.x;
-        xi8 = a.s7 * g23.y;
-        if (MODE == 1) {
-            const uint4 r1 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_MODES_4_9), a.key0, a.key1);
-            const float2 n49 = gauss_pair(r1.x, r1.y);
-            xi4 = a.L44 * n49.x;
-            xi9 = a.L94 * n49.x + a.L99 * n49.y;
-        } else {
-            const float2 z = a.xi49[(long long)y * g.nx + x];
-            xi4 = z.x;
-            xi9 = z.y;
-        }
-    }
-
-    // 7. relaxation of the non-conserved modes, Eq. (fluct-lin-lbe)
-    const float m4s = m4 + a.lb * (m4 - e_eq) + xi4;
-    const float m5s = m5 + a.ls * (m5 - pww_eq) + xi5;
-    const float m6s = m6 + a.ls * (m6 - pxy_eq) + xi6;
-    const float m7s = m7 + a.lq * m7 + xi7;
-    const float m8s = m8 + a.lq * m8 + xi8;
-    const float m9s = m9 + a.le * (m9 - eps_eq) + xi9;
-
-    // 8. back to populations: f*_i = w_i sum_a T_ai m*_a / N_a
-    const float u1 = drho, u2 = 3.0f * jx, u3 = 3.0f * jy;
-    const float u4 = 0.25f * m4s, u5 = 2.25f * m5s, u6 = 9.0f * m6s;
-    const float u7 = 1.5f * m7s, u8 = 1.5f * m8s, u9 = 0.0625f * m9s;
-    const float base_a = u1 + u4 - 4.0f * u9;               // common to the axis directions
-    const float base_d = u1 + 4.0f * u4 + 8.0f * u9;        // common to the diagonals
+    // 3.-8. stencil, moments, equilibrium, noise, relaxation, back-transform
+    Nbr r;
+    r.C = rs[ty + 1][tx + 1];
+    r.E = rs[ty + 1][tx + 2]; r.W = rs[ty + 1][tx];
+    r.N = rs[ty + 2][tx + 1]; r.S = rs[ty][tx + 1];
+    r.NE = rs[ty + 2][tx + 2]; r.NW = rs[ty + 2][tx];
+    r.SE = rs[ty][tx + 2]; r.SW = rs[ty][tx];
+    const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+    float2 z = make_float2(0.f, 0.f);
+    if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
     float o[Q];
-    o[0] = (4.0f / 9.0f) * (u1 - 2.0f * u4 + 2.0f * u9);
-    o[1] = (1.0f / 9.0f) * (base_a + u2 + u5 - u7);
-    o[2] = (1.0f / 9.0f) * (base_a + u3 - u5 - u8);
-    o[3] = (1.0f / 9.0f) * (base_a - u2 + u5 + u7);
-    o[4] = (1.0f / 9.0f) * (base_a - u3 - u5 + u8);
-    o[5] = (1.0f / 36.0f) * (base_d + u2 + u3 + u6 + 2.0f * u7 + 2.0f * u8);
-    o[6] = (1.0f / 36.0f) * (base_d - u2 + u3 - u6 - 2.0f * u7 + 2.0f * u8);
-    o[7] = (1.0f / 36.0f) * (base_d - u2 - u3 + u6 - 2.0f * u7 - 2.0f * u8);
-    o[8] = (1.0f / 36.0f) * (base_d + u2 - u3 - u6 + 2.0f * u7 - 2.0f * u8);
+    collide_node<MODE>(a, f, r, node, z, o);
 
     // 9. store (own node plus periodic ghosts)
-#pragma unroll
-    for (int i = 0; i < Q; ++i) store_with_ghosts(a.dst + i * P, g, x, y, o[i]);
+    store9(a.dst, P, g, x, y, o);
 }
 
-cudaError_t launch_step(const StepArgs& a, int noise_mode, cudaStream_t s) {
+cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, cudaStream_t s) {
     constexpr int BX = 32, BY = 16;
     dim3 block(BX, BY);
     dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY);

@@ -1,0 +1,265 @@
+// lb_step_tma.cu -- the fused fluctuating D2Q9 step, TMA-staged and persistent.
+//
+// Same arithmetic as lb_step.cu (collide_node), different data movement:
+//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles, in
+//     row-major tile order, so the tiles in flight form a band whose halo rows are
+//     still in L2 when the neighbouring tile reads them;
+//   * for each tile one thread issues nine 3D TMA loads (cp.async.bulk.tensor), one per
+//     population plane, of the box [x0 - 4, x0 + TX + 4) x [y0 - 1 - cy_i, y0 + TY + 1 - cy_i)
+//     into shared memory; the y offset of plane i absorbs its streaming shift, so node
+//     (lx, ly) of the tile reads f_i at box[ly + 1][lx + 4 - cx_i].  The x start is rounded
+//     down to a 16-byte boundary (four floats) as TMA requires;
+//   * two stages and an mbarrier each: tile k+1 is in flight while tile k is computed;
+//   * density on the tile plus one ring is formed from shared memory, then every node
+//     collides and stores its nine post-collision deviations (and periodic ghosts)
+//     directly from registers with coalesced stores.
+// Waits on the mbarriers are bounded by the global timer; a CTA that gives up sets the
+// error word and returns.
+#include <cuda.h>
+
+#include "lb_collide.cuh"
+
+namespace lbf {
+
+template <int TX, int TY>
+struct TmaTile {
+    static constexpr int BW = TX + 8;                                  // box width (floats)
+    static constexpr int BH = TY + 2;                                  // box height
+    static constexpr int PLANE_BYTES = BW * BH * 4;
+    static constexpr int PS = ((PLANE_BYTES + 127) / 128) * 128 / 4;   // plane stride in smem (floats)
+    static constexpr int STAGE = Q * PS;                               // floats per stage
+    static constexpr int RW = TX + 2, RH = TY + 2;                     // density tile + ring
+    static constexpr int SMEM_BYTES = (2 * STAGE + RW * RH) * 4 + 2 * 8;
+    static constexpr uint32_t TX_BYTES = Q * PLANE_BYTES;
+};
+
+__constant__ int kCYt[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+struct TmaArgs {
+    StepArgs a;
+    int ntx, nty;      // tiles along x and y
+    int* err;          // device error word (1 = a TMA wait timed out)
+};
+
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s: far beyond any healthy tile load
+
+template <int TX, int TY, int NT, int MODE>
+__global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const TmaArgs ta) {
+    using TT = TmaTile<TX, TY>;
+    extern __shared__ __align__(128) float smem[];
+    float* R = smem + 2 * TT::STAGE;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(R + TT::RW * TT::RH);
+    const StepArgs& a = ta.a;
+    const Grid g = a.g;
+    const int tid = threadIdx.x;
+    const int ntiles = ta.ntx * ta.nty;
+
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int tile, int s) {
+        const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
+        const uint32_t bar = smem_u32(&mbar[s]);
+        mbar_expect_tx(bar, TT::TX_BYTES);
+        float* st = smem + s * TT::STAGE;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            tma_load_3d(smem_u32(st + i * TT::PS), &tmap, x0 - 4 + GX, y0 - 1 - kCYt[i] + GY, i, bar);
+    };
+
+    const int first = blockIdx.x;
+    if (tid == 0) {
+        if (first < ntiles) issue(first, 0);
+        if (first + (int)gridDim.x < ntiles) issue(first + gridDim.x, 1);
+    }
+
+    int k = 0;
+    for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
+        const int s = k & 1;
+        const uint32_t parity = (uint32_t)((k >> 1) & 1);
+        // bounded wait for this tile's nine boxes; the decision to give up is collective
+        bool ok = mbar_try_wait(smem_u32(&mbar[s]), parity);
+        if (!ok) {
+            const uint64_t t0 = global_ns();
+            while (!(ok = mbar_try_wait(smem_u32(&mbar[s]), parity)))
+                if (global_ns() - t0 > WAIT_LIMIT_NS) break;
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(ta.err, 1);
+            return;
+        }
+        const float* S = smem + s * TT::STAGE;
+        const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
+
+        // density deviation on the tile and its ring: node (lx, ly) = (rx - 1, ry - 1)
+        for (int q = tid; q < TT::RW * TT::RH; q += NT) {
+            const int ry = q / TT::RW, rx = q - ry * TT::RW;
+            const int b = ry * TT::BW + rx + 3;
+            float f[Q];
+            f[0] = S[b];
+            f[1] = S[TT::PS + b - 1];
+            f[2] = S[2 * TT::PS + b];
+            f[3] = S[3 * TT::PS + b + 1];
+            f[4] = S[4 * TT::PS + b];
+            f[5] = S[5 * TT::PS + b - 1];
+            f[6] = S[6 * TT::PS + b + 1];
+            f[7] = S[7 * TT::PS + b + 1];
+            f[8] = S[8 * TT::PS + b - 1];
+            R[q] = drho_of(f);
+        }
+        __syncthreads();
+
+        // collide every node of the tile
+        for (int q = tid; q < TX * TY; q += NT) {
+            const int ly = q / TX, lx = q - ly * TX;
+            const int x = x0 + lx, y = y0 + ly;
+            if (x >= g.nx || y >= g.ny) continue;
+            const int b = (ly + 1) * TT::BW + lx + 4;
+            float f[Q];
+            f[0] = S[b];
+            f[1] = S[TT::PS + b - 1];
+            f[2] = S[2 * TT::PS + b];
+            f[3] = S[3 * TT::PS + b + 1];
+            f[4] = S[4 * TT::PS + b];
+            f[5] = S[5 * TT::PS + b - 1];
+            f[6] = S[6 * TT::PS + b + 1];
+            f[7] = S[7 * TT::PS + b + 1];
+            f[8] = S[8 * TT::PS + b - 1];
+            const int rc = (ly + 1) * TT::RW + lx + 1;
+            Nbr r;
+            r.C = R[rc];
+            r.E = R[rc + 1]; r.W = R[rc - 1];
+            r.N = R[rc + TT::RW]; r.S = R[rc - TT::RW];
+            r.NE = R[rc + TT::RW + 1]; r.NW = R[rc + TT::RW - 1];
+            r.SE = R[rc - TT::RW + 1]; r.SW = R[rc - TT::RW - 1];
+            const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+            float2 z = make_float2(0.f, 0.f);
+            if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
+            float o[Q];
+            collide_node<MODE>(a, f, r, node, z, o);
+            store9(a.dst, g.plane, g, x, y, o);
+        }
+        __syncthreads();
+        // stage s is free again: refill it with the tile two steps ahead
+        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(tile + 2 * gridDim.x, s);
+        }
+    }
+}
+
+// --- host side ----------------------------------------------------------------------
+
+constexpr int TMA_TX = 128, TMA_TY = 8, TMA_NT = 512;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// Tensor map over one population buffer: dims (pitch, ny + 2 GY, 9) of FP32, box
+// (TX + 8, TY + 2, 1), zero fill outside.
+bool make_pop_tensor_map(const float* buf, const Grid& g, void* map_out) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)Q};
+    cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
+    cuuint32_t box[3] = {TMA_TX + 8, TMA_TY + 2, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)buf, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+
+template <int MODE>
+static cudaError_t launch_mode(const void* map, const TmaArgs& ta, cudaStream_t s) {
+    using TT = TmaTile<TMA_TX, TMA_TY>;
+    auto kern = step_tma_kernel<TMA_TX, TMA_TY, TMA_NT, MODE>;
+    static int grid_cache = 0;
+    if (grid_cache == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TMA_NT, TT::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        grid_cache = sms * (per > 0 ? per : 1);
+    }
+    const int ntiles = ta.ntx * ta.nty;
+    const int grid = ntiles < grid_cache ? ntiles : grid_cache;
+    kern<<<grid, TMA_NT, TT::SMEM_BYTES, s>>>(*reinterpret_cast<const CUtensorMap*>(map), ta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, cudaStream_t s) {
+    TmaArgs ta;
+    ta.a = a;
+    ta.ntx = (a.g.nx + TMA_TX - 1) / TMA_TX;
+    ta.nty = (a.g.ny + TMA_TY - 1) / TMA_TY;
+    ta.err = err;
+    switch (noise_mode) {
+        case 0: return launch_mode<0>(src_map, ta, s);
+        case 1: return launch_mode<1>(src_map, ta, s);
+        default: return launch_mode<2>(src_map, ta, s);
+    }
+}
+
+}  // namespace lbf

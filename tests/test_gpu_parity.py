@@ -42,8 +42,15 @@ def _pair(nx, ny, seed, rho0, cs2, params, mode, init_scale):
 CONFIG1 = (1e-4, 0.01, 1.0, 1.0, 1.0)   # kT, kappa, tau_s, tau_b, tau_ghost
 
 
+@pytest.fixture(params=["tma", "simple"])
+def kernel(request, monkeypatch):
+    """Both step kernels: the TMA-staged persistent one (default) and the plain one."""
+    monkeypatch.setenv("LBFLUCT_STEP_KERNEL", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("mode", ["full", "lw", "diag", "off"])
-def test_parity_64x64_config1(mode):
+def test_parity_64x64_config1(mode, kernel):
     # 64^2, rho0 = 1, kappa = 0.01, tau = 1, kT = 1e-4, cs2 = 1/3, seed 42, start at rest
     scale = 0.01 if mode == "off" else 0.0
     g, o = _pair(64, 64, 42, 1.0, 1 / 3, CONFIG1, MODES[mode], scale)
@@ -57,8 +64,9 @@ def test_parity_64x64_config1(mode):
 
 
 @pytest.mark.parametrize("nx,ny,mode", [(6, 10, "lw"), (33, 17, "lw"), (100, 36, "diag"), (2, 2, "lw"),
-                                        (37, 5, "off"), (64, 32, "full"), (16, 128, "full"), (2, 8, "full")])
-def test_parity_ragged_and_small_lattices(nx, ny, mode):
+                                        (37, 5, "off"), (64, 32, "full"), (16, 128, "full"), (2, 8, "full"),
+                                        (300, 20, "lw"), (129, 9, "diag"), (256, 8, "full")])
+def test_parity_ragged_and_small_lattices(nx, ny, mode, kernel):
     g, o = _pair(nx, ny, 7, 1.0, 1 / 3, (2e-4, 0.02, 0.8, 1.0, 1.0), MODES[mode], 0.01)
     g.step(60)
     o.step(60)
@@ -67,7 +75,7 @@ def test_parity_ragged_and_small_lattices(nx, ny, mode):
 
 
 @pytest.mark.parametrize("mode", ["lw", "full"])
-def test_parity_nonideal_sound_speed(mode):
+def test_parity_nonideal_sound_speed(mode, kernel):
     # cs != sigma_s: rest populations differ from w_i rho0 and Xi_49(0) != 0
     g, o = _pair(32, 32, 9, 0.9, 0.265 ** 2, (1e-5, 0.08, 1.0, 1.1, 0.9), MODES[mode], 0.005)
     g.step(100)
@@ -90,7 +98,7 @@ def test_moments_and_sums_match_oracle():
     np.testing.assert_allclose(s, mo[:3].sum(axis=(1, 2)), rtol=0, atol=30 * 1e-7 * np.sqrt(n))
 
 
-def test_full_size_sampled_parity_and_conservation():
+def test_full_size_sampled_parity_and_conservation(kernel):
     # the roofline workload's size (4096^2), one step from a seeded random state in each
     # noise mode, compared on sampled nodes (corners and edges included)
     nx = ny = 4096
@@ -116,7 +124,7 @@ def test_full_size_sampled_parity_and_conservation():
         assert np.all(np.abs(s1[1:] - s0[1:]) < 1e-7 * nx * ny)
 
 
-def test_reproducible_and_resumable():
+def test_reproducible_and_resumable(kernel):
     a = lbf.Lattice(64, 64, seed=11)
     b = lbf.Lattice(64, 64, seed=11)
     for L in (a, b):

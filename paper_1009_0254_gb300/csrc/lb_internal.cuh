@@ -152,9 +152,10 @@ size_t tensor_map_bytes();
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s);
 cudaError_t launch_stats_sample(const float* pops, const Grid& g, float2* z1, float2* z2,
-                                const float2* twx, const float2* twy, double* bins, int nbins,
-                                cudaStream_t s);
-cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned long long* counts, cudaStream_t s);
+                                const float2* twx, const float2* twy, const unsigned short* bin16, double* bins,
+                                int nbins, cudaStream_t s);
+cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned short* bin16, unsigned long long* counts,
+                              cudaStream_t s);
 cudaError_t launch_fft2d(float2* data, int nx, int ny, int sign, const float2* twx, const float2* twy,
                          float scale, cudaStream_t s);
 cudaError_t launch_set_plane(const double* src, float* plane, const Grid& g, int i, double fbar,

@@ -155,7 +155,7 @@ int lb_structure_factor(lb_ctx* ctx, int nbins, double* S_rho, double* S_jl, dou
 int lb_warnings(lb_ctx* ctx);
 
 /* Message of the last failure on ctx ("" if none); ctx == NULL gives the last
- * failure of a call that had no context (lb_create). */
+ * failure of a call that had no context (lb_create, lb_conserved_sums_static). */
 const char* lb_last_error(lb_ctx* ctx);
 
 /* Waits for all work issued on the context's stream. */
@@ -172,6 +172,30 @@ int lb_kernel_time(lb_ctx* ctx, double* ms, int64_t* launches);
 
 /* Number of kernels this context has launched since lb_create (all kinds). */
 int lb_launch_count(lb_ctx* ctx, int64_t* launches);
+
+/* Row capacity of the static scratch used by lb_conserved_sums_static. */
+#define LB_STATIC_MAX_ROWS 16384
+
+/*
+ * Allocation-free conserved sums, for callers that cannot call cudaMalloc (their device
+ * memory is wholly owned by another allocator, or a latency-critical loop must not risk
+ * the device-wide synchronisation of an allocation).  The paper has no counterpart: this
+ * is the FP64 reduction behind lb_moments' sums, applied to populations the caller owns.
+ *   f:      device pointer, FP64 populations f[i][y][x] (layout above), nx*ny*9 values
+ *   sums:   device pointer, receives {sum rho, sum jx, sum jy} (FP64) when the stream
+ *           reaches the work; nothing is copied to the host
+ *   stream: a cudaStream_t (NULL = legacy default stream); the call returns without
+ *           waiting for the result
+ * Needs no context and allocates nothing: the per-row partial sums live in one static
+ * device array of LB_STATIC_MAX_ROWS rows (384 KB) that every GPU which loads the library
+ * holds until the process exits.  nx >= 1, 1 <= ny <= LB_STATIC_MAX_ROWS, else LB_EINVAL
+ * (message in lb_last_error(NULL)).  The first call on a device looks up the array's
+ * device address with the device current (no allocation); make that first call before
+ * any stream capture.  All calls share the array, each writing the rows it reads, so two
+ * calls whose GPU work overlaps (different streams, or different host threads on the
+ * same device) race and may return wrong sums; order them on one stream.
+ */
+int lb_conserved_sums_static(const double* f, int nx, int ny, double* sums, void* stream);
 
 /*
  * Host-only helpers (no GPU needed).

@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
         "lb_launch_count": (c_int, [vp, i64p]),
         "lb_noise_matrix": (c_int, [c_dbl] * 9 + [dp]),
         "lb_check_params": (c_int, [c_int, c_int] + [c_dbl] * 7 + [c_int]),
+        "lb_conserved_sums_static": (c_int, [vp, c_int, c_int, vp, vp]),
     }
     for name, (res, args) in proto.items():
         fn = getattr(L, name)
@@ -181,6 +182,16 @@ def lb_launch_count(ctx):
     n = ctypes.c_int64()
     _check(load().lb_launch_count(ctx, ctypes.byref(n)), ctx)
     return n.value
+
+
+LB_STATIC_MAX_ROWS = 16384
+
+
+def lb_conserved_sums_static(f, nx, ny, sums, stream=None):
+    """Allocation-free FP64 conserved sums of caller-owned device populations (f, FP64,
+    9*nx*ny) into the caller's device buffer sums (3 doubles), on `stream` (a cudaStream_t
+    handle or None).  Returns without waiting for the GPU."""
+    return _check(load().lb_conserved_sums_static(_ptr(f), nx, ny, _ptr(sums), stream))
 
 
 def lb_noise_matrix(rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, kx, ky):

@@ -213,6 +213,10 @@ struct lb_ctx {
     long long kernels = 0;          // every kernel launched on behalf of this context
 };
 
+namespace lbf {
+void set_context_free_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace lbf
+
 static int fail(lb_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg; else g_create_error = msg;
     return code;

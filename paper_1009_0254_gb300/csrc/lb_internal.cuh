@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace lbf {
 
 constexpr int Q = 9;
@@ -167,4 +169,5 @@ cudaError_t launch_moment(const float* pops, const Grid& g, int a, const double*
 cudaError_t launch_sums(const float* pops, const Grid& g, const double* fbar9, double* partial,
                         double* out3, cudaStream_t s);
 int sums_partial_count();
+void set_context_free_error(const std::string& msg);
 }  // namespace lbf

@@ -49,8 +49,8 @@ WsLayout make_layout(const Grid& g) {
     L.pop[1] = take((size_t)Q * g.plane * sizeof(float));
     L.z1 = take((size_t)n * sizeof(float2));
     L.z2 = take((size_t)n * sizeof(float2));
-    L.twx = take((size_t)(g.nx / 2 + 1) * sizeof(float2));
-    L.twy = take((size_t)(g.ny / 2 + 1) * sizeof(float2));
+    L.twx = take((size_t)g.nx * sizeof(float2));
+    L.twy = take((size_t)g.ny * sizeof(float2));
     L.cosx = take((size_t)g.nx * sizeof(float));
     L.cosy = take((size_t)g.ny * sizeof(float));
     L.bins = take((size_t)3 * MAX_BINS * sizeof(double));
@@ -188,6 +188,7 @@ struct lb_ctx {
     int* err_dev = nullptr;          // set by a kernel whose bounded wait gave up
     bool pow2 = false;
     bool use_tma = false;            // TMA-staged persistent step kernel
+    int tma_tile = 0;                // its tile shape (see lb_step_tma.cu)
     alignas(64) unsigned char tmap[2][128];
     double fbar[Q] = {};
     // parameters
@@ -299,22 +300,27 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     c->err_dev = (int*)(c->ws + c->L.err);
     rest_populations(rho0, cs2, c->fbar);
     {
+        // LBFLUCT_STEP_KERNEL=simple selects the plain kernel; LBFLUCT_TMA_TILE=<0..2> a tile shape
         const char* v = std::getenv("LBFLUCT_STEP_KERNEL");
         const bool want_tma = !(v && std::strcmp(v, "simple") == 0);
+        const char* tv = std::getenv("LBFLUCT_TMA_TILE");
+        c->tma_tile = tv ? std::atoi(tv) : 0;
+        if (c->tma_tile < 0 || c->tma_tile >= tma_tile_count()) c->tma_tile = 0;
         c->use_tma = want_tma && tensor_map_bytes() <= sizeof(c->tmap[0]) &&
-                     make_pop_tensor_map(c->pop[0], g, c->tmap[0]) && make_pop_tensor_map(c->pop[1], g, c->tmap[1]);
+                     make_pop_tensor_map(c->pop[0], g, c->tma_tile, c->tmap[0]) &&
+                     make_pop_tensor_map(c->pop[1], g, c->tma_tile, c->tmap[1]);
     }
 
     // host tables in FP64 -> device
-    std::vector<float2> tw(std::max(nx, ny) / 2 + 1);
+    std::vector<float2> tw(std::max(nx, ny));
     std::vector<float> cs(std::max(nx, ny));
     auto upload = [&](int n, float2* dtw, float* dcos) -> cudaError_t {
-        for (int k = 0; k < n / 2 + 1; ++k) {
+        for (int k = 0; k < n; ++k) {
             const double a = 2.0 * M_PI * (double)k / n;
             tw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));   // exp(-2 pi i k/n)
         }
         for (int k = 0; k < n; ++k) cs[k] = (float)std::cos(2.0 * M_PI * (double)k / n);
-        cudaError_t e = cudaMemcpy(dtw, tw.data(), sizeof(float2) * (n / 2 + 1), cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMemcpy(dtw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
         return cudaMemcpy(dcos, cs.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
     };
@@ -443,7 +449,8 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
             CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
         }
         if (c->use_tma)
-            CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->stream), "step kernel launch");
+            CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->tma_tile, c->stream),
+               "step kernel launch");
         else
             CK(c, launch_step_simple(a, kmode, c->stream), "step kernel launch");
         c->kernels += 1;

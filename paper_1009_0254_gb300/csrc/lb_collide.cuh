@@ -49,7 +49,7 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, const float f[Q]
 
     // equilibrium deviations, Table II (p0 = cs2 rho, C_n = 0)
     const float rho = a.rho0 + drho;
-    const float inv = 1.0f / rho;
+    const float inv = rcp_approx(rho);
     const float ux = jx * inv, uy = jy * inv;
     const float iso = a.cs2m * drho - a.kappa * rho * lap;
     const float e_eq = 3.0f * (jx * ux + jy * uy) + 6.0f * iso;

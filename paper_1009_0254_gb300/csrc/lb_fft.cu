@@ -5,46 +5,13 @@
 //   forward  a(k) = n^-1/2 sum_r exp(+i k.r) a(r)         (sign = +1)
 //   back     a(r) = n^-1/2 sum_k exp(-i k.r) a(k)         (sign = -1)
 // with k = 2 pi (mx/nx, my/ny).  Sizes are powers of two.  Each transform is a 2D
-// pass over rows (one CTA per row) followed by a pass over columns (a CTA per strip
-// of C adjacent columns), each an in-place decimation-in-time FFT on data loaded in
-// bit-reversed order into shared memory, with twiddles exp(-2 pi i k/n) computed on
-// the host in FP64.
+// pass over rows (one CTA per row) and a pass over columns (a CTA per strip of C
+// adjacent columns), each an in-place Stockham FFT in shared memory (lb_fft_core.cuh)
+// with twiddles exp(-2 pi i q/n) computed on the host in FP64.
+#include "lb_fft_core.cuh"
 #include "lb_internal.cuh"
 
 namespace lbf {
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev(v) >> (32 - bits); }
-
-// In-place DIT butterflies over `count` interleaved sequences of length n (log2n bits)
-// stored as s[e * count + c]; input already in bit-reversed order.
-__device__ __forceinline__ void smem_fft(float2* s, int n, int log2n, int count, int sign, const float2* tw) {
-    const int nth = blockDim.x;
-    const int tid = threadIdx.x;
-    const int total = (n >> 1) * count;
-    const int lc = 31 - __clz(count);
-    for (int lh = 0; lh < log2n; ++lh) {
-        const int h = 1 << lh;
-        __syncthreads();
-        for (int j = tid; j < total; j += nth) {
-            const int c = j & (count - 1);
-            const int b = j >> lc;
-            const int pos = b & (h - 1);
-            const int i0 = ((b - pos) << 1) + pos;
-            const int i1 = i0 + h;
-            float2 w = tw[pos << (log2n - 1 - lh)];
-            if (sign > 0) w.y = -w.y;
-            const float2 u = s[i0 * count + c];
-            const float2 v = cmul(w, s[i1 * count + c]);
-            s[i0 * count + c] = make_float2(u.x + v.x, u.y + v.y);
-            s[i1 * count + c] = make_float2(u.x - v.x, u.y - v.y);
-        }
-    }
-    __syncthreads();
-}
 
 __device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
 
@@ -84,14 +51,11 @@ __device__ __forceinline__ float2 noise49_k(const NoiseGenArgs& ga, int mx, int 
     return make_float2(z4.x - z9.y, z4.y + z9.x);
 }
 
-// Row pass, in place, scaled by `scale` on the way out.
-__global__ void fft_rows_kernel(float2* data, int nx, int sign, const float2* __restrict__ twx, float scale) {
+// Row pass, in place, scaled by `scale` on the way out.  One CTA per row.
+__global__ void __launch_bounds__(1024) fft_rows_kernel(float2* data, int nx, int sign, const float2* __restrict__ twx, float scale) {
     extern __shared__ float2 sm[];
     const int log2n = ilog2(nx);
-    float2* tw = sm + nx;
-    const int row = blockIdx.x;
-    for (int j = threadIdx.x; j < (nx >> 1); j += blockDim.x) tw[j] = twx[j];
-    float2* rowp = data + (long long)row * nx;
+    float2* rowp = data + (long long)blockIdx.x * nx;
     constexpr int U = 8;                       // loads in flight per thread
     for (int j0 = threadIdx.x; j0 < nx; j0 += U * blockDim.x) {
         float2 v[U];
@@ -103,45 +67,41 @@ __global__ void fft_rows_kernel(float2* data, int nx, int sign, const float2* __
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u * blockDim.x;
-            if (j < nx) sm[bitrev(j, log2n)] = v[u];
+            if (j < nx) sm[fpad(j)] = v[u];
         }
     }
-    smem_fft(sm, nx, log2n, 1, sign, tw);
+    stockham_fft(sm, nx, log2n, 1, sign, twx);
     for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-        const float2 v = sm[j];
+        const float2 v = sm[fpad(j)];
         rowp[j] = make_float2(v.x * scale, v.y * scale);
     }
 }
 
 // Correlated noise, first pass: a CTA synthesises the k-space columns [c0, c0 + count)
-// for every k_y straight into shared memory (bit-reversed along k_y), transforms them
-// back along y and writes the partial result H(k_x, y); the row pass finishes along x.
-__global__ void noise_cols_kernel(float2* out, NoiseGenArgs ga, int count, const float2* __restrict__ twy) {
+// for every k_y straight into shared memory, transforms them back along y and writes
+// the partial result H(k_x, y); the row pass finishes along x.
+__global__ void __launch_bounds__(1024) noise_cols_kernel(float2* out, NoiseGenArgs ga, int count, const float2* __restrict__ twy) {
     extern __shared__ float2 sm[];
     const int ny = ga.ny, log2n = ilog2(ny);
     const int lc = 31 - __clz(count);
-    float2* tw = sm + (long long)ny * count;
-    for (int j = threadIdx.x; j < (ny >> 1); j += blockDim.x) tw[j] = twy[j];
     const int c0 = blockIdx.x * count;
     const int total = ny * count;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int c = e & (count - 1), ky = e >> lc;
-        sm[bitrev(ky, log2n) * count + c] = noise49_k(ga, c0 + c, ky);
+        sm[fpad(e)] = noise49_k(ga, c0 + c, ky);
     }
-    smem_fft(sm, ny, log2n, count, -1, tw);
+    stockham_fft(sm, ny, log2n, count, -1, twy);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int c = e & (count - 1), y = e >> lc;
-        out[(long long)y * ga.nx + c0 + c] = sm[y * count + c];
+        out[(long long)y * ga.nx + c0 + c] = sm[fpad(e)];
     }
 }
 
 // Column pass over strips of `count` adjacent columns, scaled by `scale` on the way out.
-__global__ void fft_cols_kernel(float2* data, int nx, int ny, int count, int sign,
+__global__ void __launch_bounds__(1024) fft_cols_kernel(float2* data, int nx, int ny, int count, int sign,
                                 const float2* __restrict__ twy, float scale) {
     extern __shared__ float2 sm[];
     const int log2n = ilog2(ny);
-    float2* tw = sm + (long long)ny * count;
-    for (int j = threadIdx.x; j < (ny >> 1); j += blockDim.x) tw[j] = twy[j];
     const int xs = blockIdx.x * count;
     const int total = ny * count;
     const int lc = 31 - __clz(count);
@@ -156,47 +116,40 @@ __global__ void fft_cols_kernel(float2* data, int nx, int ny, int count, int sig
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int e = e0 + u * blockDim.x;
-            if (e < total) sm[bitrev(e >> lc, log2n) * count + (e & (count - 1))] = v[u];
+            if (e < total) sm[fpad(e)] = v[u];
         }
     }
-    smem_fft(sm, ny, log2n, count, sign, tw);
+    stockham_fft(sm, ny, log2n, count, sign, twy);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int c = e % count, r = e / count;
-        const float2 v = sm[r * count + c];
-        data[(long long)r * nx + xs + c] = make_float2(v.x * scale, v.y * scale);
+        const float2 v = sm[fpad(e)];
+        data[(long long)(e >> lc) * nx + xs + (e & (count - 1))] = make_float2(v.x * scale, v.y * scale);
     }
 }
 
 static int col_strip(int nx, int ny) {
-    // strip width: as many columns as fit in ~160 KB of shared memory, at most 16
+    // strip width: as many columns as fit in one CTA (<= 1024 threads, ~200 KB), at most 16
     int c = 16;
-    while (c > 1 && ((long long)ny * c * 8 + (long long)(ny / 2) * 8 > 160 * 1024)) c >>= 1;
+    while (c > 1 && (fft_threads(ny, c) > 1024 || fft_smem_bytes(ny, c) > 200 * 1024)) c >>= 1;
     if (c > nx) c = nx;
     return c;
 }
 
 static cudaError_t rows_pass(float2* data, int nx, int ny, int sign, const float2* twx, float scale,
                              cudaStream_t s) {
-    const size_t smem = (size_t)nx * 8 + (size_t)(nx / 2 > 0 ? nx / 2 : 1) * 8;
-    int threads = nx / 2;
-    if (threads > 512) threads = 512;
-    if (threads < 32) threads = 32;
+    const size_t smem = fft_smem_bytes(nx, 1);
     cudaError_t e = cudaFuncSetAttribute(fft_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fft_rows_kernel<<<ny, threads, smem, s>>>(data, nx, sign, twx, scale);
+    fft_rows_kernel<<<ny, fft_threads(nx, 1), smem, s>>>(data, nx, sign, twx, scale);
     return cudaGetLastError();
 }
 
 static cudaError_t cols_pass(float2* data, int nx, int ny, int sign, const float2* twy, float scale,
                              cudaStream_t s) {
     const int c = col_strip(nx, ny);
-    const size_t smem = (size_t)ny * c * 8 + (size_t)(ny / 2 > 0 ? ny / 2 : 1) * 8;
-    int threads = (ny / 2) * c;
-    if (threads > 512) threads = 512;
-    if (threads < 32) threads = 32;
+    const size_t smem = fft_smem_bytes(ny, c);
     cudaError_t e = cudaFuncSetAttribute(fft_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fft_cols_kernel<<<nx / c, threads, smem, s>>>(data, nx, ny, c, sign, twy, scale);
+    fft_cols_kernel<<<nx / c, fft_threads(ny, c), smem, s>>>(data, nx, ny, c, sign, twy, scale);
     return cudaGetLastError();
 }
 
@@ -212,13 +165,10 @@ cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* tw
     // synthesise xi(k) column block by column block and transform back along y, then
     // along x with the unitary n^-1/2
     const int c = col_strip(ga.nx, ga.ny);
-    const size_t smem = (size_t)ga.ny * c * 8 + (size_t)(ga.ny / 2 > 0 ? ga.ny / 2 : 1) * 8;
-    int threads = (ga.ny / 2) * c;
-    if (threads > 512) threads = 512;
-    if (threads < 32) threads = 32;
+    const size_t smem = fft_smem_bytes(ga.ny, c);
     cudaError_t e = cudaFuncSetAttribute(noise_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    noise_cols_kernel<<<ga.nx / c, threads, smem, s>>>(buf, ga, c, twy);
+    noise_cols_kernel<<<ga.nx / c, fft_threads(ga.ny, c), smem, s>>>(buf, ga, c, twy);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const float scale = (float)(1.0 / sqrt((double)ga.nx * (double)ga.ny));

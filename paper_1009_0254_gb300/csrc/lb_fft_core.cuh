@@ -1,0 +1,166 @@
+// lb_fft_core.cuh -- in-place Stockham FFTs of power-of-two length in shared memory.
+//
+// `count` sequences of length n are interleaved element by element: element e of sequence
+// c sits at s[pad(e * count + c)], with one float2 of padding after every 16 so that the
+// strided accesses of every stage hit distinct banks.  A transform is a chain of Stockham
+// stages (radix 16, then one radix 2/4/8 stage for the remaining factor); stage radix R with
+// Ns = product of the previous radices maps, for work item j < n/R with k = j mod Ns,
+//     a_m = s[j + m n/R] * W^(m k n/(Ns R)),   A = R-point DFT of a,
+//     s[(j - k) R + k + m Ns] = A_m,
+// which leaves the output in natural order.  W = exp(sign 2 pi i / n); sign = -1 is the
+// e^{-i} kernel.  Each thread holds all values of its work items in registers between a
+// read phase and a write phase separated by a barrier, so the stage runs in place.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lbf {
+
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// multiply by sign * i
+__device__ __forceinline__ float2 c_rot(float2 a, int sign) {
+    return sign < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+__device__ __forceinline__ void dft2(float2* a) {
+    const float2 t = a[0];
+    a[0] = c_add(t, a[1]);
+    a[1] = c_sub(t, a[1]);
+}
+
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, int sign) {
+    const float2 y0 = c_add(a0, a2), y1 = c_sub(a0, a2);
+    const float2 y2 = c_add(a1, a3), y3 = c_rot(c_sub(a1, a3), sign);
+    a0 = c_add(y0, y2);
+    a2 = c_sub(y0, y2);
+    a1 = c_add(y1, y3);
+    a3 = c_sub(y1, y3);
+}
+
+// 8-point DFT by decimation in time: X_k = E_k + W8^k O_k, X_{k+4} = E_k - W8^k O_k.
+__device__ __forceinline__ void dft8(float2* a, int sign) {
+    float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4(e0, e1, e2, e3, sign);
+    dft4(o0, o1, o2, o3, sign);
+    const float h = 0.70710678118654752f;
+    const float s = (float)sign;
+    o1 = c_mul(o1, make_float2(h, s * h));
+    o2 = c_rot(o2, sign);
+    o3 = c_mul(o3, make_float2(-h, s * h));
+    a[0] = c_add(e0, o0); a[4] = c_sub(e0, o0);
+    a[1] = c_add(e1, o1); a[5] = c_sub(e1, o1);
+    a[2] = c_add(e2, o2); a[6] = c_sub(e2, o2);
+    a[3] = c_add(e3, o3); a[7] = c_sub(e3, o3);
+}
+
+// 16-point DFT by decimation in time over two 8-point halves, W16^k = exp(sign i k pi / 8).
+__device__ __forceinline__ void dft16(float2* a, int sign) {
+    float2 e[8], o[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        e[m] = a[2 * m];
+        o[m] = a[2 * m + 1];
+    }
+    dft8(e, sign);
+    dft8(o, sign);
+    const float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+    const float s = (float)sign;
+    const float2 w[8] = {make_float2(1.f, 0.f),  make_float2(c1, s * s1), make_float2(h, s * h),
+                         make_float2(s1, s * c1), make_float2(0.f, s),    make_float2(-s1, s * c1),
+                         make_float2(-h, s * h), make_float2(-c1, s * s1)};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float2 t = c_mul(o[k], w[k]);
+        a[k] = c_add(e[k], t);
+        a[k + 8] = c_sub(e[k], t);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void dft_r(float2* a, int sign) {
+    if (R == 2) dft2(a);
+    else if (R == 4) dft4(a[0], a[1], a[2], a[3], sign);
+    else if (R == 8) dft8(a, sign);
+    else dft16(a, sign);
+}
+
+// One Stockham stage of radix R; each thread takes up to 16/R work items.
+template <int R>
+__device__ __forceinline__ void stockham_stage(float2* s, int n, int count, int lc, int Ns, int sign,
+                                               const float2* __restrict__ tw) {
+    constexpr int MQ = 16 / R;
+    const int items = (n / R) * count;
+    const int T = blockDim.x;
+    const int stride_in = n / R;
+    const int tw_step = n / (Ns * R);
+    float2 v[MQ][R];
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+        const int w = threadIdx.x + q * T;
+        if (w < items) {
+            const int c = w & (count - 1), j = w >> lc;
+            const int k = j & (Ns - 1);
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                float2 x = s[fpad((j + m * stride_in) * count + c)];
+                if (m > 0 && Ns > 1) {
+                    float2 t = __ldg(&tw[m * k * tw_step]);
+                    if (sign > 0) t.y = -t.y;
+                    x = c_mul(x, t);
+                }
+                v[q][m] = x;
+            }
+            dft_r<R>(v[q], sign);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+        const int w = threadIdx.x + q * T;
+        if (w < items) {
+            const int c = w & (count - 1), j = w >> lc;
+            const int k = j & (Ns - 1);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int m = 0; m < R; ++m) s[fpad((base + m * Ns) * count + c)] = v[q][m];
+        }
+    }
+    __syncthreads();
+}
+
+// Full transform of `count` interleaved sequences of length n = 2^log2n (n >= 2) already in
+// shared memory; tw[q] = exp(-2 pi i q / n), q < n.  Needs blockDim.x >= max(1, n/16) * count.
+__device__ __forceinline__ void stockham_fft(float2* s, int n, int log2n, int count, int sign,
+                                             const float2* __restrict__ tw) {
+    const int lc = 31 - __clz(count);
+    int Ns = 1, left = log2n;
+    __syncthreads();
+    while (left >= 4) {
+        stockham_stage<16>(s, n, count, lc, Ns, sign, tw);
+        Ns <<= 4;
+        left -= 4;
+    }
+    if (left == 3) stockham_stage<8>(s, n, count, lc, Ns, sign, tw);
+    else if (left == 2) stockham_stage<4>(s, n, count, lc, Ns, sign, tw);
+    else if (left == 1) stockham_stage<2>(s, n, count, lc, Ns, sign, tw);
+}
+
+__host__ __device__ inline int fft_threads(int n, int count) {
+    int t = (n >= 16 ? n / 16 : 1) * count;
+    if (t < 32) t = 32;
+    return (t + 31) / 32 * 32;
+}
+
+__host__ __device__ inline size_t fft_smem_bytes(int n, int count) {
+    const long long e = (long long)n * count;
+    return (size_t)(e + (e >> 4) + 1) * 8;
+}
+
+}  // namespace lbf

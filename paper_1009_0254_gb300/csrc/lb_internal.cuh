@@ -93,13 +93,27 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk) {
 // the hardware approximations of log2, rsqrt, sin and cos (absolute error below 1e-6 in
 // the normal except for u1 within ~1e-6 of 1, where r itself is below 1.5e-3 and the error
 // below 7e-4); cos(2 pi u) = -cos(2 pi (u - 1/2)) keeps the angle in [-pi, pi].
+// The uniforms are built exactly from bits: x = 1 + k 2^-23 (k in the mantissa), then
+// u1 = x - (1 - 2^-24) and u2 - 1/2 = (x - 3/2) + 2^-24, both exact by Sterbenz's lemma.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float2 gauss_pair(uint32_t a, uint32_t b) {
-    const float u1 = __uint2float_rn(a >> 9) * 0x1p-23f + 0x1p-24f;
-    const float u2 = __uint2float_rn(b >> 9) * 0x1p-23f + 0x1p-24f;
+    const float u1 = __uint_as_float((a >> 9) | 0x3f800000u) - 0.99999994f;
+    const float v2 = (__uint_as_float((b >> 9) | 0x3f800000u) - 1.5f) + 0x1p-24f;   // u2 - 1/2
     const float l = fmaxf(-1.3862943611198906f * __log2f(u1), 0.0f);     // -2 ln u1 = -2 ln2 log2 u1
-    const float r = l * rsqrtf(l + 1e-30f);
-    const float th = 6.2831853071795865f * (u2 - 0.5f);
+    const float r = sqrt_approx(l);
+    const float th = 6.2831853071795865f * v2;
     return make_float2(-r * __cosf(th), -r * __sinf(th));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // noise draw tags (fourth counter word)
@@ -148,8 +162,10 @@ __device__ __forceinline__ void store9(float* dst, long long P, const Grid& g, i
 // Launchers implemented in the .cu files (host side).
 namespace lbf {
 cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, cudaStream_t s);
-cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, cudaStream_t s);
-bool make_pop_tensor_map(const float* buf, const Grid& g, void* map_out);
+cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile,
+                            cudaStream_t s);
+bool make_pop_tensor_map(const float* buf, const Grid& g, int tile, void* map_out);
+int tma_tile_count();
 size_t tensor_map_bytes();
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s);

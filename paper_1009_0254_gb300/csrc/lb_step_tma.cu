@@ -1,7 +1,8 @@
 // lb_step_tma.cu -- the fused fluctuating D2Q9 step, TMA-staged and persistent.
 //
 // Same arithmetic as lb_step.cu (collide_node), different data movement:
-//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles, in
+//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles (64 x 16
+//     by default), in
 //     row-major tile order, so the tiles in flight form a band whose halo rows are
 //     still in L2 when the neighbouring tile reads them;
 //   * for each tile one thread issues nine 3D TMA loads (cp.async.bulk.tensor), one per
@@ -135,7 +136,11 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
 
         // density deviation on the tile and its ring: node (lx, ly) = (rx - 1, ry - 1)
-        for (int q = tid; q < TT::RW * TT::RH; q += NT) {
+        constexpr int NA = (TT::RW * TT::RH + NT - 1) / NT;
+#pragma unroll
+        for (int it = 0; it < NA; ++it) {
+            const int q = tid + it * NT;
+            if (q >= TT::RW * TT::RH) break;
             const int ry = q / TT::RW, rx = q - ry * TT::RW;
             const int b = ry * TT::BW + rx + 3;
             float f[Q];
@@ -152,8 +157,12 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         }
         __syncthreads();
 
-        // collide every node of the tile
-        for (int q = tid; q < TX * TY; q += NT) {
+        // collide every node of the tile; the nodes of one thread are independent, so
+        // their random-number and collision chains interleave
+        static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
+#pragma unroll
+        for (int it = 0; it < TX * TY / NT; ++it) {
+            const int q = tid + it * NT;
             const int ly = q / TX, lx = q - ly * TX;
             const int x = x0 + lx, y = y0 + ly;
             if (x >= g.nx || y >= g.ny) continue;
@@ -193,8 +202,6 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
 
 // --- host side ----------------------------------------------------------------------
 
-constexpr int TMA_TX = 128, TMA_TY = 8, TMA_NT = 512;
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -211,14 +218,20 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
+// Tile shapes (TX x TY nodes, NT threads): 0 = 64x16/512 (two CTAs per SM, the fastest
+// measured on GB300), 1 = 128x8/512 (two CTAs per SM), 2 = 64x8/256 (four CTAs per SM).
+static const int kTiles[3][3] = {{64, 16, 512}, {128, 8, 512}, {64, 8, 256}};
+
+int tma_tile_count() { return 3; }
+
 // Tensor map over one population buffer: dims (pitch, ny + 2 GY, 9) of FP32, box
 // (TX + 8, TY + 2, 1), zero fill outside.
-bool make_pop_tensor_map(const float* buf, const Grid& g, void* map_out) {
+bool make_pop_tensor_map(const float* buf, const Grid& g, int tile, void* map_out) {
     EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
+    if (!fn || tile < 0 || tile >= 3) return false;
     cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)Q};
     cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
-    cuuint32_t box[3] = {TMA_TX + 8, TMA_TY + 2, 1};
+    cuuint32_t box[3] = {(cuuint32_t)kTiles[tile][0] + 8, (cuuint32_t)kTiles[tile][1] + 2, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)buf, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -228,10 +241,10 @@ bool make_pop_tensor_map(const float* buf, const Grid& g, void* map_out) {
 
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
-template <int MODE>
-static cudaError_t launch_mode(const void* map, const TmaArgs& ta, cudaStream_t s) {
-    using TT = TmaTile<TMA_TX, TMA_TY>;
-    auto kern = step_tma_kernel<TMA_TX, TMA_TY, TMA_NT, MODE>;
+template <int TX, int TY, int NT, int MODE>
+static cudaError_t launch_cfg(const void* map, TmaArgs ta, cudaStream_t s) {
+    using TT = TmaTile<TX, TY>;
+    auto kern = step_tma_kernel<TX, TY, NT, MODE>;
     static int grid_cache = 0;
     if (grid_cache == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES);
@@ -239,26 +252,37 @@ static cudaError_t launch_mode(const void* map, const TmaArgs& ta, cudaStream_t 
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TMA_NT, TT::SMEM_BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, TT::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         grid_cache = sms * (per > 0 ? per : 1);
     }
+    ta.ntx = (ta.a.g.nx + TX - 1) / TX;
+    ta.nty = (ta.a.g.ny + TY - 1) / TY;
     const int ntiles = ta.ntx * ta.nty;
     const int grid = ntiles < grid_cache ? ntiles : grid_cache;
-    kern<<<grid, TMA_NT, TT::SMEM_BYTES, s>>>(*reinterpret_cast<const CUtensorMap*>(map), ta);
+    kern<<<grid, NT, TT::SMEM_BYTES, s>>>(*reinterpret_cast<const CUtensorMap*>(map), ta);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, cudaStream_t s) {
+template <int MODE>
+static cudaError_t launch_mode(const void* map, const TmaArgs& ta, int tile, cudaStream_t s) {
+    switch (tile) {
+        case 1: return launch_cfg<128, 8, 512, MODE>(map, ta, s);
+        case 2: return launch_cfg<64, 8, 256, MODE>(map, ta, s);
+        default: return launch_cfg<64, 16, 512, MODE>(map, ta, s);
+    }
+}
+
+cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile,
+                            cudaStream_t s) {
     TmaArgs ta;
     ta.a = a;
-    ta.ntx = (a.g.nx + TMA_TX - 1) / TMA_TX;
-    ta.nty = (a.g.ny + TMA_TY - 1) / TMA_TY;
+    ta.ntx = ta.nty = 0;
     ta.err = err;
     switch (noise_mode) {
-        case 0: return launch_mode<0>(src_map, ta, s);
-        case 1: return launch_mode<1>(src_map, ta, s);
-        default: return launch_mode<2>(src_map, ta, s);
+        case 0: return launch_mode<0>(src_map, ta, tile, s);
+        case 1: return launch_mode<1>(src_map, ta, tile, s);
+        default: return launch_mode<2>(src_map, ta, tile, s);
     }
 }
 

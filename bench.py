@@ -36,8 +36,29 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE_STEP = 72          # 9 FP32 populations read + 9 written
 BYTES_PER_NODE_STEP_FULL = 80     # + the (xi_4, xi_9) FP32 pair read by the step kernel
+BYTES_PER_NODE_STEP_FP16 = 36     # 9 FP16 populations read + 9 written
 PARAMS_LW = dict(kT=1e-4, kappa=0.01, tau_s=0.8, tau_b=1.0, tau_ghost=1.0)
 PARAMS_FULL = dict(kT=1e-4, kappa=0.05, tau_s=0.8, tau_b=1.0, tau_ghost=1.0)
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank's independent lattice: replicas differ only in their Philox key."""
+    return base_seed + 1000 * rank
+
+
+def whole_job_mlups(world: int, nodes: int, steps: int, ms_max: float) -> float:
+    """Node updates of all ranks per second (MLUPS), timed by the slowest rank."""
+    return world * nodes * steps / (ms_max / 1e3) / 1e6
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    """The largest value over all ranks (no collective when running alone)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def parse():
@@ -256,7 +277,7 @@ def main():
 
     n = args.n
     nodes = n * n
-    L = lbf.Lattice(n, n, seed=42 + 1000 * rank)
+    L = lbf.Lattice(n, n, seed=replica_seed(42, rank))
     L.set_sampling(args.every, args.nbins)
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_index = vis.split(",")[local] if vis else local
@@ -267,15 +288,8 @@ def main():
     ms, kms, kl, launches, w0, w1 = timed_run(lbf, torch, L, args.steps, args.warmup, lbf.LB_NOISE_LW, PARAMS_LW, dist)
     clk = clocks.stop(w0, w1)
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms = max_over_ranks(ms)
-    value = world * nodes * args.steps / (ms / 1e3) / 1e6
+    ms = max_over_ranks(dist, ms, "cuda")
+    value = whole_job_mlups(world, nodes, args.steps, ms)
     hbm, peak_kind = peaks()
     k_avg_s = kms / max(kl, 1) / 1e3
     achieved = BYTES_PER_NODE_STEP * nodes / k_avg_s / 1e9
@@ -287,15 +301,33 @@ def main():
         L.set_sampling(args.every, args.nbins)
         fms, fkms, fkl, flaunch, _, _ = timed_run(lbf, torch, L, args.steps, args.warmup, lbf.LB_NOISE_FULL,
                                                   PARAMS_FULL, dist)
-        fms = max_over_ranks(fms)
+        fms = max_over_ranks(dist, fms, "cuda")
         fk = fkms / max(fkl, 1) / 1e3
         variants.append({"noise": "full (correlated, k-space synthesis + FFT each step)", "kappa": 0.05,
-                         "value": world * nodes * args.steps / (fms / 1e3) / 1e6, "unit": "MLUPS",
+                         "value": whole_job_mlups(world, nodes, args.steps, fms), "unit": "MLUPS",
                          "ms_per_step": fms / args.steps,
                          "step_kernel": {"achieved": BYTES_PER_NODE_STEP_FULL * nodes / fk / 1e9, "unit": "GB/s",
                                          "frac": BYTES_PER_NODE_STEP_FULL * nodes / fk / 1e9 / hbm,
                                          "avg_us": fk * 1e6},
                          "gpu_launches": flaunch})
+
+    # variant: FP16 deviation storage, long-wavelength noise (the precision study's second arm)
+    if not args.no_variants:
+        L16 = lbf.Lattice(n, n, seed=replica_seed(43, rank), precision=lbf.LB_FP16DEV)
+        L16.set_sampling(args.every, args.nbins)
+        hms, hkms, hkl, hlaunch, _, _ = timed_run(lbf, torch, L16, args.steps, args.warmup, lbf.LB_NOISE_LW,
+                                                  PARAMS_LW, dist)
+        hms = max_over_ranks(dist, hms, "cuda")
+        hk = hkms / max(hkl, 1) / 1e3
+        variants.append({"storage": "fp16 deviations (FP32 arithmetic)", "noise": "long-wavelength", "kappa": 0.01,
+                         "value": whole_job_mlups(world, nodes, args.steps, hms), "unit": "MLUPS",
+                         "ms_per_step": hms / args.steps,
+                         "step_kernel": {"achieved": BYTES_PER_NODE_STEP_FP16 * nodes / hk / 1e9, "unit": "GB/s",
+                                         "frac": BYTES_PER_NODE_STEP_FP16 * nodes / hk / 1e9 / hbm,
+                                         "avg_us": hk * 1e6},
+                         "gpu_launches": hlaunch})
+        L16.close()
+        del L16
 
     # end to end through the public API: host initial state in, spectra and sums out
     L.set_params(PARAMS_LW["kT"], PARAMS_LW["kappa"], PARAMS_LW["tau_s"], PARAMS_LW["tau_b"],
@@ -318,10 +350,10 @@ def main():
     lbf.lb_structure_factor(L.ctx, args.nbins, S, Jl, Jt, cnt, ns)
     lbf.lb_moments(L.ctx, None, lbf.LB_HOST, sums)
     e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s)
+    e2e_s = max_over_ranks(dist, e2e_s, "cuda")
     h2d = 9 * nodes * 8
     d2h = 3 * args.nbins * 8 + 3 * 8
-    e2e = {"value": world * nodes * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": whole_job_mlups(world, nodes, args.steps, e2e_s * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "job": "lb_set_populations (host FP64) + lb_step(K) + lb_structure_factor + lb_moments sums"}
 

@@ -43,13 +43,16 @@ extern "C" {
 #define LB_ESTATE (-6)     /* call out of order (e.g. lb_step before lb_set_params) */
 
 /* storage precision of the populations */
-#define LB_FP32 0          /* FP32 deviations f_i - fbar_i */
-#define LB_FP16DEV 1       /* FP16 deviations f_i - fbar_i (reserved, not built yet) */
+#define LB_FP32 0          /* FP32 deviations f_i - fbar_i (72 bytes moved per node update) */
+#define LB_FP16DEV 1       /* FP16 deviations, stored as (f_i - fbar_i) / w_i (36 bytes per node update);
+                              arithmetic stays FP32; rounding to FP16 each step makes the mass
+                              conserved only to that rounding */
 
 /* noise modes, [GACV] Sec. IV */
 #define LB_NOISE_OFF 0     /* deterministic (kT ignored) */
 #define LB_NOISE_LW 1      /* spatially uncorrelated, covariance Xi(0), Eq. (noise-matrix-k0) */
-#define LB_NOISE_FULL 2    /* spatially correlated, covariance Xi(k), Eq. (noise-yeo) */
+#define LB_NOISE_FULL 2    /* spatially correlated, covariance Xi(k), Eq. (noise-yeo);
+                              needs nx, ny powers of two, ny <= 8192 */
 #define LB_NOISE_DIAG 3    /* "ideal gas-like": LW with the off-diagonal Xi_49 dropped */
 
 /* buffer locations */

@@ -210,16 +210,16 @@ class Lattice:
     """One lattice on the current CUDA device.  PyTorch allocates the workspace and
     provides the stream (torch.cuda.current_stream() at construction, unless given)."""
 
-    def __init__(self, nx, ny, seed=42, rho0=1.0, cs2=1.0 / 3.0, stream=None):
+    def __init__(self, nx, ny, seed=42, rho0=1.0, cs2=1.0 / 3.0, stream=None, precision=LB_FP32):
         import torch
         self.nx, self.ny = int(nx), int(ny)
-        nbytes = lb_workspace_bytes(self.nx, self.ny, LB_FP32)
+        nbytes = lb_workspace_bytes(self.nx, self.ny, precision)
         if nbytes == 0:
-            raise LBError(LB_EINVAL, "invalid lattice size %dx%d" % (nx, ny))
+            raise LBError(LB_EINVAL, "invalid lattice size %dx%d or precision" % (nx, ny))
         self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self._ws.data_ptr()
         aligned = (base + 255) & ~255
-        self.ctx = lb_create(self.nx, self.ny, LB_FP32, seed, rho0, cs2, aligned, nbytes)
+        self.ctx = lb_create(self.nx, self.ny, precision, seed, rho0, cs2, aligned, nbytes)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         lb_set_stream(self.ctx, self.stream.cuda_stream)
         self.nbins = 0

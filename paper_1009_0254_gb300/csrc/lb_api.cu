@@ -31,22 +31,27 @@ struct WsLayout {
     size_t pop[2], z1, z2, twx, twy, cosx, cosy, bins, counts, bin16, partial, sums3, fbar, err, total;
 };
 
-bool make_grid(int nx, int ny, Grid* g) {
-    if (nx < 2 || ny < 2 || nx > (1 << 16) || ny > (1 << 16)) return false;
+int elem_size(int precision) { return precision == LB_FP16DEV ? 2 : (precision == LB_FP32 ? 4 : 0); }
+
+bool make_grid(int nx, int ny, int esize, Grid* g) {
+    if (nx < 2 || ny < 2 || nx > (1 << 16) || ny > (1 << 16) || esize <= 0) return false;
+    const int line = 128 / esize;                 // elements per 128 bytes
     g->nx = nx;
     g->ny = ny;
-    g->pitch = ((nx + 2 * GX + 31) / 32) * 32;
-    g->plane = (((long long)g->pitch * (ny + 2 * GY)) + 63) / 64 * 64;
+    g->gx = line;
+    g->pitch = (nx + 2 * line + line - 1) / line * line;
+    const long long a256 = 256 / esize;
+    g->plane = ((long long)g->pitch * (ny + 2 * GY) + a256 - 1) / a256 * a256;
     return true;
 }
 
-WsLayout make_layout(const Grid& g) {
+WsLayout make_layout(const Grid& g, int esize) {
     WsLayout L{};
     const long long n = (long long)g.nx * g.ny;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.pop[0] = take((size_t)Q * g.plane * sizeof(float));
-    L.pop[1] = take((size_t)Q * g.plane * sizeof(float));
+    L.pop[0] = take((size_t)Q * g.plane * esize);
+    L.pop[1] = take((size_t)Q * g.plane * esize);
     L.z1 = take((size_t)n * sizeof(float2));
     L.z2 = take((size_t)n * sizeof(float2));
     L.twx = take((size_t)g.nx * sizeof(float2));
@@ -170,7 +175,7 @@ struct DeviceGuard {
 }  // namespace
 
 struct lb_ctx {
-    int nx = 0, ny = 0, precision = 0, device = 0;
+    int nx = 0, ny = 0, precision = 0, device = 0, fp16 = 0;
     long long n = 0;
     uint64_t seed = 0;
     double rho0 = 1.0, cs2 = SIGMA_S2;
@@ -178,7 +183,7 @@ struct lb_ctx {
     WsLayout L{};
     char* ws = nullptr;
     bool owns = false;
-    float* pop[2] = {nullptr, nullptr};
+    void* pop[2] = {nullptr, nullptr};
     int cur = 0;
     float2 *z1 = nullptr, *z2 = nullptr, *twx = nullptr, *twy = nullptr;
     float *cosx = nullptr, *cosy = nullptr;
@@ -188,6 +193,8 @@ struct lb_ctx {
     int* err_dev = nullptr;          // set by a kernel whose bounded wait gave up
     bool pow2 = false;
     bool use_tma = false;            // TMA-staged persistent step kernel
+    bool use_sweep = false;          // warp-autonomous vertical sweep kernel
+    int sweep_occ6 = 0;              // its occupancy variant
     int tma_tile = 0;                // its tile shape (see lb_step_tma.cu)
     alignas(64) unsigned char tmap[2][128];
     double fbar[Q] = {};
@@ -251,22 +258,25 @@ extern "C" {
 
 size_t lb_workspace_bytes(int nx, int ny, int precision) {
     Grid g;
-    if (precision != LB_FP32 || !make_grid(nx, ny, &g)) return 0;
-    return make_layout(g).total;
+    const int es = elem_size(precision);
+    if (!make_grid(nx, ny, es, &g)) return 0;
+    return make_layout(g, es).total;
 }
 
 int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double cs2, void* workspace,
               size_t workspace_bytes, lb_ctx** out) {
     if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
     *out = nullptr;
-    if (precision != LB_FP32) return fail(nullptr, LB_EINVAL, "only LB_FP32 storage is available");
+    const int es = elem_size(precision);
+    if (es == 0) return fail(nullptr, LB_EINVAL, "precision must be LB_FP32 or LB_FP16DEV");
     Grid g;
-    if (!make_grid(nx, ny, &g)) return fail(nullptr, LB_EINVAL, "nx and ny must lie in [2, 65536]");
+    if (!make_grid(nx, ny, es, &g)) return fail(nullptr, LB_EINVAL, "nx and ny must lie in [2, 65536]");
     if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(nullptr, LB_EINVAL, "rho0 must be positive");
     if (!(cs2 > 0.0) || !std::isfinite(cs2)) return fail(nullptr, LB_EINVAL, "cs2 must be positive");
     lb_ctx* c = new lb_ctx();
     c->nx = nx; c->ny = ny; c->n = (long long)nx * ny; c->precision = precision;
-    c->seed = seed; c->rho0 = rho0; c->cs2 = cs2; c->g = g; c->L = make_layout(g);
+    c->fp16 = precision == LB_FP16DEV ? 1 : 0;
+    c->seed = seed; c->rho0 = rho0; c->cs2 = cs2; c->g = g; c->L = make_layout(g, es);
     c->pow2 = is_pow2(nx) && is_pow2(ny);
     cudaGetDevice(&c->device);
     if (workspace) {
@@ -283,8 +293,8 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
         }
         c->owns = true;
     }
-    c->pop[0] = (float*)(c->ws + c->L.pop[0]);
-    c->pop[1] = (float*)(c->ws + c->L.pop[1]);
+    c->pop[0] = c->ws + c->L.pop[0];
+    c->pop[1] = c->ws + c->L.pop[1];
     c->z1 = (float2*)(c->ws + c->L.z1);
     c->z2 = (float2*)(c->ws + c->L.z2);
     c->twx = (float2*)(c->ws + c->L.twx);
@@ -302,13 +312,15 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     {
         // LBFLUCT_STEP_KERNEL=simple selects the plain kernel; LBFLUCT_TMA_TILE=<0..2> a tile shape
         const char* v = std::getenv("LBFLUCT_STEP_KERNEL");
-        const bool want_tma = !(v && std::strcmp(v, "simple") == 0);
+        c->use_sweep = v && (std::strcmp(v, "sweep") == 0 || std::strcmp(v, "sweep6") == 0) && sweep_fits(g);
+        c->sweep_occ6 = v && std::strcmp(v, "sweep6") == 0;
+        const bool want_tma = !(v && std::strcmp(v, "simple") == 0) && !c->use_sweep;
         const char* tv = std::getenv("LBFLUCT_TMA_TILE");
         c->tma_tile = tv ? std::atoi(tv) : 0;
         if (c->tma_tile < 0 || c->tma_tile >= tma_tile_count()) c->tma_tile = 0;
         c->use_tma = want_tma && tensor_map_bytes() <= sizeof(c->tmap[0]) &&
-                     make_pop_tensor_map(c->pop[0], g, c->tma_tile, c->tmap[0]) &&
-                     make_pop_tensor_map(c->pop[1], g, c->tma_tile, c->tmap[1]);
+                     make_pop_tensor_map(c->pop[0], g, c->tma_tile, c->fp16, c->tmap[0]) &&
+                     make_pop_tensor_map(c->pop[1], g, c->tma_tile, c->fp16, c->tmap[1]);
     }
 
     // host tables in FP64 -> device
@@ -328,8 +340,8 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     if (e == cudaSuccess) e = upload(ny, c->twy, c->cosy);
     if (e == cudaSuccess) e = cudaMemcpy(c->fbar_dev, c->fbar, sizeof(double) * Q, cudaMemcpyHostToDevice);
     // rest state: every deviation (and ghost) zero
-    if (e == cudaSuccess) e = cudaMemset(c->pop[0], 0, (size_t)Q * g.plane * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, (size_t)Q * g.plane * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->pop[0], 0, (size_t)Q * g.plane * es);
+    if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, (size_t)Q * g.plane * es);
     if (e == cudaSuccess) e = cudaMemset(c->bins, 0, 3 * MAX_BINS * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->err_dev, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -365,8 +377,8 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     std::string why;
     int r = validate(c->nx, c->ny, c->rho0, c->cs2, kT, kappa, tau_s, tau_b, tau_ghost, mode, &why);
     if (r != LB_OK) return fail(c, r, why);
-    if (mode == LB_NOISE_FULL && kT > 0.0 && !c->pow2)
-        return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two (radix-2 FFT)");
+    if (mode == LB_NOISE_FULL && kT > 0.0 && (!c->pow2 || c->ny > 8192))
+        return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two and ny <= 8192");
     c->kT = kT; c->kappa = kappa; c->tau_s = tau_s; c->tau_b = tau_b; c->tau_g = tau_ghost;
     c->noise_mode = mode;
     c->warnings = (kT >= 0.1 * SIGMA_S2 * c->rho0) ? LB_WARN_LOW_MACH : 0;   // Eq. (low-mach)
@@ -448,11 +460,13 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
             if (r != LB_OK) return r;
             CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
         }
-        if (c->use_tma)
-            CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->tma_tile, c->stream),
+        if (c->use_sweep)
+            CK(c, launch_step_sweep(a, kmode, c->fp16, c->sweep_occ6, c->stream), "step kernel launch");
+        else if (c->use_tma)
+            CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->tma_tile, c->fp16, c->stream),
                "step kernel launch");
         else
-            CK(c, launch_step_simple(a, kmode, c->stream), "step kernel launch");
+            CK(c, launch_step_simple(a, kmode, c->fp16, c->stream), "step kernel launch");
         c->kernels += 1;
         if (c->timing) {
             CK(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
@@ -461,7 +475,7 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         c->cur ^= 1;
         c->t++;
         if (c->every > 0 && c->t % c->every == 0) {
-            CK(c, launch_stats_sample(c->pop[c->cur], c->g, c->z1, c->z2, c->twx, c->twy, c->bin16, c->bins,
+            CK(c, launch_stats_sample(c->pop[c->cur], c->fp16, c->g, c->z1, c->z2, c->twx, c->twy, c->bin16, c->bins,
                                       c->nbins, c->stream), "spectra sample");
             c->kernels += 6;
             c->nsamples++;
@@ -486,8 +500,7 @@ int lb_set_populations(lb_ctx* c, const double* f, int loc, int64_t t) {
             CK(c, cudaMemcpyAsync(stage, src, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream), "H2D");
             src = stage;
         }
-        CK(c, launch_set_plane(src, c->pop[c->cur] + (long long)i * c->g.plane, c->g, i, c->fbar[i], c->stream),
-           "set populations");
+        CK(c, launch_set_plane(src, c->pop[c->cur], c->fp16, c->g, i, c->fbar[i], c->stream), "set populations");
         c->kernels += 1;
     }
     CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -501,8 +514,7 @@ int lb_get_populations(lb_ctx* c, double* f, int loc) {
     double* stage = (double*)c->z1;
     for (int i = 0; i < Q; ++i) {
         double* dst = (loc == LB_HOST) ? stage : f + (long long)i * c->n;
-        CK(c, launch_get_plane(c->pop[c->cur] + (long long)i * c->g.plane, c->g, i, c->fbar[i], dst, c->stream),
-           "get populations");
+        CK(c, launch_get_plane(c->pop[c->cur], c->fp16, c->g, i, c->fbar[i], dst, c->stream), "get populations");
         c->kernels += 1;
         if (loc == LB_HOST)
             CK(c, cudaMemcpyAsync(f + (long long)i * c->n, stage, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
@@ -519,7 +531,7 @@ int lb_moments(lb_ctx* c, double* m, int loc, double sums[3]) {
         double* stage = (double*)c->z1;
         for (int a = 0; a < Q; ++a) {
             double* dst = (loc == LB_HOST) ? stage : m + (long long)a * c->n;
-            CK(c, launch_moment(c->pop[c->cur], c->g, a, c->fbar_dev, dst, c->stream), "moments");
+            CK(c, launch_moment(c->pop[c->cur], c->fp16, c->g, a, c->fbar_dev, dst, c->stream), "moments");
             c->kernels += 1;
             if (loc == LB_HOST)
                 CK(c, cudaMemcpyAsync(m + (long long)a * c->n, stage, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
@@ -527,7 +539,7 @@ int lb_moments(lb_ctx* c, double* m, int loc, double sums[3]) {
         }
     }
     if (sums) {
-        CK(c, launch_sums(c->pop[c->cur], c->g, c->fbar_dev, c->partial, c->sums3, c->stream), "sums");
+        CK(c, launch_sums(c->pop[c->cur], c->fp16, c->g, c->fbar_dev, c->partial, c->sums3, c->stream), "sums");
         c->kernels += 2;
         CK(c, cudaMemcpyAsync(sums, c->sums3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
     }
@@ -643,7 +655,7 @@ int lb_noise_matrix(double rho0, double cs2, double kT, double kappa, double tau
 int lb_check_params(int nx, int ny, double rho0, double cs2, double kT, double kappa, double tau_s,
                     double tau_b, double tau_ghost, int noise_mode) {
     Grid g;
-    if (!make_grid(nx, ny, &g)) return LB_EINVAL;
+    if (!make_grid(nx, ny, 4, &g)) return LB_EINVAL;
     return validate(nx, ny, rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode, nullptr);
 }
 

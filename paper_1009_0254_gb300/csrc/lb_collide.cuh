@@ -78,29 +78,32 @@ __device__ __forceinline__ void collide_node(const StepArgs& a, const float f[Q]
         }
     }
 
-    // relaxation of the non-conserved modes, Eq. (fluct-lin-lbe)
-    const float m4s = m4 + a.lb * (m4 - e_eq) + xi4;
-    const float m5s = m5 + a.ls * (m5 - pww_eq) + xi5;
-    const float m6s = m6 + a.ls * (m6 - pxy_eq) + xi6;
-    const float m7s = m7 + a.lq * m7 + xi7;
-    const float m8s = m8 + a.lq * m8 + xi8;
-    const float m9s = m9 + a.le * (m9 - eps_eq) + xi9;
+    // relaxation of the non-conserved modes, Eq. (fluct-lin-lbe), as increments
+    // D_a = m*_a - m_a = lambda_a (m_a - m_a^eq) + xi_a (zero for the conserved a = 1..3)
+    const float D4 = a.lb * (m4 - e_eq) + xi4;
+    const float D5 = a.ls * (m5 - pww_eq) + xi5;
+    const float D6 = a.ls * (m6 - pxy_eq) + xi6;
+    const float D7 = a.lq * m7 + xi7;
+    const float D8 = a.lq * m8 + xi8;
+    const float D9 = a.le * (m9 - eps_eq) + xi9;
 
-    // back to populations: f*_i = w_i sum_a T_ai m*_a / N_a
-    const float u1 = drho, u2 = 3.0f * jx, u3 = 3.0f * jy;
-    const float u4 = 0.25f * m4s, u5 = 2.25f * m5s, u6 = 9.0f * m6s;
-    const float u7 = 1.5f * m7s, u8 = 1.5f * m8s, u9 = 0.0625f * m9s;
-    const float base_a = u1 + u4 - 4.0f * u9;
-    const float base_d = u1 + 4.0f * u4 + 8.0f * u9;
-    o[0] = (4.0f / 9.0f) * (u1 - 2.0f * u4 + 2.0f * u9);
-    o[1] = (1.0f / 9.0f) * (base_a + u2 + u5 - u7);
-    o[2] = (1.0f / 9.0f) * (base_a + u3 - u5 - u8);
-    o[3] = (1.0f / 9.0f) * (base_a - u2 + u5 + u7);
-    o[4] = (1.0f / 9.0f) * (base_a - u3 - u5 + u8);
-    o[5] = (1.0f / 36.0f) * (base_d + u2 + u3 + u6 + 2.0f * u7 + 2.0f * u8);
-    o[6] = (1.0f / 36.0f) * (base_d - u2 + u3 - u6 - 2.0f * u7 + 2.0f * u8);
-    o[7] = (1.0f / 36.0f) * (base_d - u2 - u3 + u6 - 2.0f * u7 - 2.0f * u8);
-    o[8] = (1.0f / 36.0f) * (base_d + u2 - u3 - u6 + 2.0f * u7 - 2.0f * u8);
+    // back to populations: f*_i = f_i + w_i sum_{a>=4} T_ai D_a / N_a (Sec. III A)
+    const float d4 = 0.25f * D4, d5 = 2.25f * D5, d6 = 9.0f * D6;
+    const float d7 = 1.5f * D7, d8 = 1.5f * D8, d9 = 0.0625f * D9;
+    const float A = d4 - 4.0f * d9;                 // T_4i - 4 T_9i part of the axis directions
+    const float A1 = A + d5, A2 = A - d5;
+    const float Dd = 4.0f * d4 + 8.0f * d9;         // the same for the diagonals
+    const float D1 = Dd + d6, D2 = Dd - d6;
+    const float P = 2.0f * (d7 + d8), M = 2.0f * (d7 - d8);
+    o[0] = f[0] + (8.0f / 9.0f) * (d9 - d4);
+    o[1] = f[1] + (1.0f / 9.0f) * (A1 - d7);
+    o[2] = f[2] + (1.0f / 9.0f) * (A2 - d8);
+    o[3] = f[3] + (1.0f / 9.0f) * (A1 + d7);
+    o[4] = f[4] + (1.0f / 9.0f) * (A2 + d8);
+    o[5] = f[5] + (1.0f / 36.0f) * (D1 + P);
+    o[6] = f[6] + (1.0f / 36.0f) * (D2 - M);
+    o[7] = f[7] + (1.0f / 36.0f) * (D1 - P);
+    o[8] = f[8] + (1.0f / 36.0f) * (D2 + M);
 }
 
 }  // namespace lbf

@@ -17,8 +17,9 @@ __device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
 
 // Correlated noise of modes 4 and 9 in k-space: xi(k) = L(k) eta(k) with L L^T the
 // (4,9) block of Xi(k), Eq. (noise-yeo); packed as Z = xi_4(k) + i xi_9(k).  The pair
-// (k, -k) shares one Philox draw owned by the lower linear index, so eta(-k) = eta(k)*.
-__device__ __forceinline__ float2 noise49_k(const NoiseGenArgs& ga, int mx, int my) {
+// (k, -k) shares one Philox draw owned by the lower linear index, so eta(-k) = eta(k)*,
+// and L(-k) = L(k).  noise49_pair returns Z(k) and Z(-k) from that one draw.
+__device__ __forceinline__ void noise49_pair(const NoiseGenArgs& ga, int mx, int my, float2* zk, float2* zmk) {
     const uint32_t lin = (uint32_t)my * ga.nx + mx;
     const uint32_t cx = (uint32_t)((ga.nx - mx) & (ga.nx - 1));
     const uint32_t cy = (uint32_t)((ga.ny - my) & (ga.ny - 1));
@@ -43,12 +44,26 @@ __device__ __forceinline__ float2 noise49_k(const NoiseGenArgs& ga, int mx, int 
     const float x44 = ga.a44 + ga.b44 * s;
     const float x49 = ga.a49 + ga.b49 * s;
     const float x99 = ga.a99 + ga.b99 * s;
-    const float L44 = sqrtf(fmaxf(x44, 0.f));
-    const float L94 = L44 > 0.f ? x49 / L44 : 0.f;
-    const float L99 = sqrtf(fmaxf(x99 - L94 * L94, 0.f));
+    const float L44 = sqrt_approx(fmaxf(x44, 0.f));
+    const float L94 = L44 > 0.f ? x49 * rcp_approx(L44) : 0.f;
+    const float L99 = sqrt_approx(fmaxf(x99 - L94 * L94, 0.f));
+    // xi_4(k) = L44 e1, xi_9(k) = L94 e1 + L99 e2; at -k both are conjugated
     const float2 z4 = make_float2(L44 * e1.x, L44 * e1.y);
     const float2 z9 = make_float2(L94 * e1.x + L99 * e2.x, L94 * e1.y + L99 * e2.y);
-    return make_float2(z4.x - z9.y, z4.y + z9.x);
+    *zk = make_float2(z4.x - z9.y, z4.y + z9.x);
+    *zmk = make_float2(z4.x + z9.y, -z4.y + z9.x);
+}
+
+// Columns handled by column-block b of width `count` (a power of two >= 2) in the paired
+// synthesis: slot q < count/2 holds column j(b, q) of the left half and slot q + count/2
+// its mirror nx - j (mod nx).  Block 0 pairs the self-mirrored columns 0 and nx/2.
+__device__ __forceinline__ int paired_column(int b, int q, int count, int nx) {
+    const int half = count >> 1;
+    const int slot = q & (half - 1);
+    const bool mirror = q >= half;
+    if (b == 0 && slot == 0) return mirror ? nx >> 1 : 0;
+    const int j = b * half + slot;                 // 1 .. nx/2 - 1
+    return mirror ? nx - j : j;
 }
 
 // Row pass, in place, scaled by `scale` on the way out.  One CTA per row.
@@ -77,23 +92,47 @@ __global__ void __launch_bounds__(1024) fft_rows_kernel(float2* data, int nx, in
     }
 }
 
-// Correlated noise, first pass: a CTA synthesises the k-space columns [c0, c0 + count)
-// for every k_y straight into shared memory, transforms them back along y and writes
-// the partial result H(k_x, y); the row pass finishes along x.
-__global__ void __launch_bounds__(1024) noise_cols_kernel(float2* out, NoiseGenArgs ga, int count, const float2* __restrict__ twy) {
+// Correlated noise, first pass: a CTA synthesises `count` k-space columns (half of them
+// the mirrors of the others, so every (k, -k) draw is made once) for every k_y straight
+// into shared memory, transforms them back along y and writes the partial result
+// H(k_x, y); the row pass finishes along x.
+__global__ void __launch_bounds__(1024) noise_cols_kernel(float2* out, NoiseGenArgs ga, int count,
+                                                          const float2* __restrict__ twy) {
     extern __shared__ float2 sm[];
     const int ny = ga.ny, log2n = ilog2(ny);
     const int lc = 31 - __clz(count);
-    const int c0 = blockIdx.x * count;
-    const int total = ny * count;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int c = e & (count - 1), ky = e >> lc;
-        sm[fpad(e)] = noise49_k(ga, c0 + c, ky);
+    const int half = count >> 1;
+    const int b = blockIdx.x;
+    // owners: left slots q < half at every k_y; for the self-mirrored column pair of block 0
+    // (columns 0 and nx/2) the partner of (k_x, k_y) is (k_x, -k_y) in the same column
+    const int work = ny * half;
+    for (int e = threadIdx.x; e < work; e += blockDim.x) {
+        const int q = e & (half - 1), ky = e >> (lc - 1);
+        const int mx = paired_column(b, q, count, ga.nx);
+        if (b == 0 && q == 0) {
+            // columns 0 and nx/2: draw for k_y <= ny/2, write k_y and ny - k_y of both
+            if (ky > ny / 2) continue;
+            const int kym = (ny - ky) & (ny - 1);
+            float2 z, zm;
+            noise49_pair(ga, 0, ky, &z, &zm);
+            sm[fpad(ky * count + 0)] = z;
+            sm[fpad(kym * count + 0)] = zm;
+            noise49_pair(ga, ga.nx >> 1, ky, &z, &zm);
+            sm[fpad(ky * count + half)] = z;
+            sm[fpad(kym * count + half)] = zm;
+        } else {
+            const int kym = (ny - ky) & (ny - 1);
+            float2 z, zm;
+            noise49_pair(ga, mx, ky, &z, &zm);
+            sm[fpad(ky * count + q)] = z;
+            sm[fpad(kym * count + q + half)] = zm;
+        }
     }
     stockham_fft(sm, ny, log2n, count, -1, twy);
+    const int total = ny * count;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int c = e & (count - 1), y = e >> lc;
-        out[(long long)y * ga.nx + c0 + c] = sm[fpad(e)];
+        const int q = e & (count - 1), y = e >> lc;
+        out[(long long)y * ga.nx + paired_column(b, q, count, ga.nx)] = sm[fpad(e)];
     }
 }
 
@@ -163,8 +202,9 @@ cudaError_t launch_fft2d(float2* data, int nx, int ny, int sign, const float2* t
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s) {
     // synthesise xi(k) column block by column block and transform back along y, then
-    // along x with the unitary n^-1/2
+    // along x with the unitary n^-1/2; the paired blocks need an even width (ny <= 8192)
     const int c = col_strip(ga.nx, ga.ny);
+    if (c < 2) return cudaErrorInvalidValue;
     const size_t smem = fft_smem_bytes(ga.ny, c);
     cudaError_t e = cudaFuncSetAttribute(noise_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -178,16 +218,18 @@ cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* tw
 // --- sampled spectra ---------------------------------------------------------------
 
 // z1 = drho + i jx, z2 = jy of the pre-collision state f_i(r) = f*_i(r - c_i)
-__global__ void stats_fields_kernel(const float* __restrict__ src, Grid g, float2* z1, float2* z2) {
+template <typename T>
+__global__ void stats_fields_kernel(const T* __restrict__ src, Grid g, float2* z1, float2* z2) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= g.nx) return;
     const long long P = g.plane;
     const long long c = g.at(x, y);
-    const float f0 = src[c], f1 = src[P + c - 1], f2 = src[2 * P + c - g.pitch], f3 = src[3 * P + c + 1];
-    const float f4 = src[4 * P + c + g.pitch], f5 = src[5 * P + c - g.pitch - 1];
-    const float f6 = src[6 * P + c - g.pitch + 1], f7 = src[7 * P + c + g.pitch + 1];
-    const float f8 = src[8 * P + c + g.pitch - 1];
+    const float f0 = Elem<T>::load(src[c], 0), f1 = Elem<T>::load(src[P + c - 1], 1);
+    const float f2 = Elem<T>::load(src[2 * P + c - g.pitch], 2), f3 = Elem<T>::load(src[3 * P + c + 1], 3);
+    const float f4 = Elem<T>::load(src[4 * P + c + g.pitch], 4), f5 = Elem<T>::load(src[5 * P + c - g.pitch - 1], 5);
+    const float f6 = Elem<T>::load(src[6 * P + c - g.pitch + 1], 6), f7 = Elem<T>::load(src[7 * P + c + g.pitch + 1], 7);
+    const float f8 = Elem<T>::load(src[8 * P + c + g.pitch - 1], 8);
     const float drho = f0 + ((f1 + f3) + (f2 + f4)) + ((f5 + f7) + (f6 + f8));
     const float jx = (f1 - f3) + (f5 - f7) + (f8 - f6);
     const float jy = (f2 - f4) + (f5 - f7) + (f6 - f8);
@@ -294,11 +336,12 @@ cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned short* bin16, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats_sample(const float* pops, const Grid& g, float2* z1, float2* z2,
+cudaError_t launch_stats_sample(const void* pops, int fp16, const Grid& g, float2* z1, float2* z2,
                                 const float2* twx, const float2* twy, const unsigned short* bin16, double* bins,
                                 int nbins, cudaStream_t s) {
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
-    stats_fields_kernel<<<grd, blk, 0, s>>>(pops, g, z1, z2);
+    if (fp16) stats_fields_kernel<__half><<<grd, blk, 0, s>>>(static_cast<const __half*>(pops), g, z1, z2);
+    else stats_fields_kernel<float><<<grd, blk, 0, s>>>(static_cast<const float*>(pops), g, z1, z2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const float scale = (float)(1.0 / sqrt((double)g.nx * (double)g.ny));

@@ -8,6 +8,7 @@
 // outside the lattice) is an in-bounds, wrap-free address.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,16 +17,40 @@
 namespace lbf {
 
 constexpr int Q = 9;
-constexpr int GX = 32;   // ghost columns per side: keeps column 0 at a 128-byte boundary
 constexpr int GY = 2;    // ghost rows per side
 constexpr int MAX_BINS = 4096;
 
 struct Grid {
     int nx, ny;
-    int pitch;           // elements per stored row (>= nx + 2 GX, multiple of 32)
+    int gx;              // ghost columns per side: 128 bytes of elements, so column 0 is 128-byte aligned
+    int pitch;           // elements per stored row (>= nx + 2 gx, a multiple of 128 bytes)
     long long plane;     // elements per population plane
     __host__ __device__ __forceinline__ long long at(int x, int y) const {
-        return (long long)(y + GY) * pitch + (x + GX);
+        return (long long)(y + GY) * pitch + (x + gx);
+    }
+};
+
+// Storage of one population deviation df_i = f_i - fbar_i.  FP32 keeps df_i; FP16 keeps
+// df_i / w_i, which is of the size of the density fluctuation for every i and so stays in
+// FP16's normal range.  Arithmetic is FP32 either way.
+template <typename T>
+struct Elem;
+
+template <>
+struct Elem<float> {
+    static constexpr int XO = 4;     // elements per 16 bytes (TMA x alignment)
+    __host__ __device__ static __forceinline__ float load(float v, int) { return v; }
+    __host__ __device__ static __forceinline__ float store(float v, int) { return v; }
+};
+
+template <>
+struct Elem<__half> {
+    static constexpr int XO = 8;
+    __device__ static __forceinline__ float load(__half v, int i) {
+        return __half2float(v) * (i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f));
+    }
+    __device__ static __forceinline__ __half store(float v, int i) {
+        return __float2half_rn(v * (i == 0 ? 2.25f : (i < 5 ? 9.0f : 36.0f)));
     }
 };
 
@@ -50,8 +75,8 @@ inline RoundKeys make_round_keys(uint64_t seed) {
 // Arguments of the fused step kernel (by value).
 struct StepArgs {
     Grid g;
-    const float* __restrict__ src;   // post-collision deviations at t-1 (planes 0..8)
-    float* __restrict__ dst;         // post-collision deviations at t
+    const void* __restrict__ src;    // post-collision deviations at t-1 (planes 0..8, storage type)
+    void* __restrict__ dst;          // post-collision deviations at t
     const float2* __restrict__ xi49; // FULL mode: (xi_4, xi_9)(r) for this step, [y][x]
     float rho0;
     float cs2m;                      // cs2 - sigma_s^2
@@ -121,11 +146,9 @@ constexpr uint32_t TAG_MODES_5_8 = 0;   // nu_5..nu_8
 constexpr uint32_t TAG_MODES_4_9 = 1;   // (nu_4, nu_9)
 constexpr uint32_t TAG_KSPACE = 2;      // eta_1(k), eta_2(k)
 
-// Stores the nine planes of one node, and its periodic ghost copies near an edge.
-__device__ __forceinline__ void store9(float* dst, long long P, const Grid& g, int x, int y, const float o[Q]);
-
 // Writes v at (x, y) of a plane and at the ghost copies that (x, y) feeds.
-__device__ __forceinline__ void store_with_ghosts(float* plane, const Grid& g, int x, int y, float v) {
+template <typename T>
+__device__ __forceinline__ void store_with_ghosts(T* plane, const Grid& g, int x, int y, T v) {
     const long long c = g.at(x, y);
     plane[c] = v;
     const int dxl = (x < 2) ? g.nx : 0;            // copy to x + nx
@@ -145,15 +168,18 @@ __device__ __forceinline__ void store_with_ghosts(float* plane, const Grid& g, i
     }
 }
 
-__device__ __forceinline__ void store9(float* dst, long long P, const Grid& g, int x, int y, const float o[Q]) {
+// Stores the nine planes of one node (converted to the storage type), and its periodic
+// ghost copies near an edge.
+template <typename T>
+__device__ __forceinline__ void store9(T* dst, long long P, const Grid& g, int x, int y, const float o[Q]) {
     const bool edge = (x < 2) | (x >= g.nx - 2) | (y < 2) | (y >= g.ny - 2);
     if (!edge) {
         const long long c = g.at(x, y);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) dst[i * P + c] = o[i];
+        for (int i = 0; i < Q; ++i) dst[i * P + c] = Elem<T>::store(o[i], i);
     } else {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) store_with_ghosts(dst + i * P, g, x, y, o[i]);
+        for (int i = 0; i < Q; ++i) store_with_ghosts(dst + i * P, g, x, y, Elem<T>::store(o[i], i));
     }
 }
 
@@ -161,28 +187,30 @@ __device__ __forceinline__ void store9(float* dst, long long P, const Grid& g, i
 
 // Launchers implemented in the .cu files (host side).
 namespace lbf {
-cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, cudaStream_t s);
-cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile,
+cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, int fp16, cudaStream_t s);
+cudaError_t launch_step_sweep(const StepArgs& a, int noise_mode, int fp16, int occ6, cudaStream_t s);
+bool sweep_fits(const Grid& g);
+cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile, int fp16,
                             cudaStream_t s);
-bool make_pop_tensor_map(const float* buf, const Grid& g, int tile, void* map_out);
+bool make_pop_tensor_map(const void* buf, const Grid& g, int tile, int fp16, void* map_out);
 int tma_tile_count();
 size_t tensor_map_bytes();
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s);
-cudaError_t launch_stats_sample(const float* pops, const Grid& g, float2* z1, float2* z2,
+cudaError_t launch_stats_sample(const void* pops, int fp16, const Grid& g, float2* z1, float2* z2,
                                 const float2* twx, const float2* twy, const unsigned short* bin16, double* bins,
                                 int nbins, cudaStream_t s);
 cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned short* bin16, unsigned long long* counts,
                               cudaStream_t s);
 cudaError_t launch_fft2d(float2* data, int nx, int ny, int sign, const float2* twx, const float2* twy,
                          float scale, cudaStream_t s);
-cudaError_t launch_set_plane(const double* src, float* plane, const Grid& g, int i, double fbar,
+cudaError_t launch_set_plane(const double* src, void* pops, int fp16, const Grid& g, int i, double fbar,
                              cudaStream_t s);
-cudaError_t launch_get_plane(const float* plane, const Grid& g, int i, double fbar, double* out,
+cudaError_t launch_get_plane(const void* pops, int fp16, const Grid& g, int i, double fbar, double* out,
                              cudaStream_t s);
-cudaError_t launch_moment(const float* pops, const Grid& g, int a, const double* fbar9, double* out,
+cudaError_t launch_moment(const void* pops, int fp16, const Grid& g, int a, const double* fbar9, double* out,
                           cudaStream_t s);
-cudaError_t launch_sums(const float* pops, const Grid& g, const double* fbar9, double* partial,
+cudaError_t launch_sums(const void* pops, int fp16, const Grid& g, const double* fbar9, double* partial,
                         double* out3, cudaStream_t s);
 int sums_partial_count();
 void set_context_free_error(const std::string& msg);

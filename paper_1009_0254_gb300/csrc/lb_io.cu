@@ -22,7 +22,8 @@ __constant__ double kTm[Q][Q] = {
     {0, 0, -1, 0, 1, 2, 2, -2, -2},
     {2, -4, -4, -4, -4, 8, 8, 8, 8}};
 
-__global__ void set_plane_kernel(const double* __restrict__ src, float* plane, Grid g, int i, double fbar) {
+template <typename T>
+__global__ void set_plane_kernel(const double* __restrict__ src, T* plane, Grid g, int i, double fbar) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= g.nx) return;
@@ -30,24 +31,27 @@ __global__ void set_plane_kernel(const double* __restrict__ src, float* plane, G
     xs = xs < 0 ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
     ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
     const double v = src[(long long)ys * g.nx + xs] - fbar;
-    store_with_ghosts(plane, g, x, y, (float)v);
+    store_with_ghosts(plane, g, x, y, Elem<T>::store((float)v, i));
 }
 
-__global__ void get_plane_kernel(const float* __restrict__ plane, Grid g, int i, double fbar, double* out) {
+template <typename T>
+__global__ void get_plane_kernel(const T* __restrict__ plane, Grid g, int i, double fbar, double* out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= g.nx) return;
-    out[(long long)y * g.nx + x] = fbar + (double)plane[g.at(x - kCX[i], y - kCY[i])];
+    out[(long long)y * g.nx + x] = fbar + (double)Elem<T>::load(plane[g.at(x - kCX[i], y - kCY[i])], i);
 }
 
-__device__ __forceinline__ void pulled_f64(const float* __restrict__ pops, const Grid& g, int x, int y,
+template <typename T>
+__device__ __forceinline__ void pulled_f64(const T* __restrict__ pops, const Grid& g, int x, int y,
                                            const double* fbar9, double f[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        f[i] = fbar9[i] + (double)pops[i * g.plane + g.at(x - kCX[i], y - kCY[i])];
+        f[i] = fbar9[i] + (double)Elem<T>::load(pops[i * g.plane + g.at(x - kCX[i], y - kCY[i])], i);
 }
 
-__global__ void moment_kernel(const float* __restrict__ pops, Grid g, int a, const double* __restrict__ fbar9,
+template <typename T>
+__global__ void moment_kernel(const T* __restrict__ pops, Grid g, int a, const double* __restrict__ fbar9,
                               double* out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
@@ -66,7 +70,8 @@ int sums_partial_count() { return SUM_BLOCKS * 3; }
 
 // FP64 sums of rho, jx, jy in a fixed order: per-thread strided sums, a block tree,
 // then one block over the partials (deterministic for a given lattice size).
-__global__ void sums_kernel(const float* __restrict__ pops, Grid g, const double* __restrict__ fbar9,
+template <typename T>
+__global__ void sums_kernel(const T* __restrict__ pops, Grid g, const double* __restrict__ fbar9,
                             double* partial) {
     __shared__ double sh[3][SUM_THREADS];
     double s0 = 0, s1 = 0, s2 = 0;
@@ -113,25 +118,37 @@ __global__ void sums_final_kernel(const double* __restrict__ partial, double* ou
 
 static dim3 row_grid(const Grid& g, int bx) { return dim3((g.nx + bx - 1) / bx, g.ny); }
 
-cudaError_t launch_set_plane(const double* src, float* plane, const Grid& g, int i, double fbar, cudaStream_t s) {
-    set_plane_kernel<<<row_grid(g, 128), 128, 0, s>>>(src, plane, g, i, fbar);
+cudaError_t launch_set_plane(const double* src, void* pops, int fp16, const Grid& g, int i, double fbar,
+                             cudaStream_t s) {
+    if (fp16)
+        set_plane_kernel<__half><<<row_grid(g, 128), 128, 0, s>>>(src, static_cast<__half*>(pops) + i * g.plane, g, i, fbar);
+    else
+        set_plane_kernel<float><<<row_grid(g, 128), 128, 0, s>>>(src, static_cast<float*>(pops) + i * g.plane, g, i, fbar);
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_plane(const float* plane, const Grid& g, int i, double fbar, double* out, cudaStream_t s) {
-    get_plane_kernel<<<row_grid(g, 128), 128, 0, s>>>(plane, g, i, fbar, out);
+cudaError_t launch_get_plane(const void* pops, int fp16, const Grid& g, int i, double fbar, double* out,
+                             cudaStream_t s) {
+    if (fp16)
+        get_plane_kernel<__half><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const __half*>(pops) + i * g.plane, g, i,
+                                                                 fbar, out);
+    else
+        get_plane_kernel<float><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const float*>(pops) + i * g.plane, g, i,
+                                                                fbar, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moment(const float* pops, const Grid& g, int a, const double* fbar9, double* out,
+cudaError_t launch_moment(const void* pops, int fp16, const Grid& g, int a, const double* fbar9, double* out,
                           cudaStream_t s) {
-    moment_kernel<<<row_grid(g, 128), 128, 0, s>>>(pops, g, a, fbar9, out);
+    if (fp16) moment_kernel<__half><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const __half*>(pops), g, a, fbar9, out);
+    else moment_kernel<float><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const float*>(pops), g, a, fbar9, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sums(const float* pops, const Grid& g, const double* fbar9, double* partial, double* out3,
+cudaError_t launch_sums(const void* pops, int fp16, const Grid& g, const double* fbar9, double* partial, double* out3,
                         cudaStream_t s) {
-    sums_kernel<<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(pops, g, fbar9, partial);
+    if (fp16) sums_kernel<__half><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(static_cast<const __half*>(pops), g, fbar9, partial);
+    else sums_kernel<float><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(static_cast<const float*>(pops), g, fbar9, partial);
     sums_final_kernel<<<1, SUM_THREADS, 0, s>>>(partial, out3);
     return cudaGetLastError();
 }

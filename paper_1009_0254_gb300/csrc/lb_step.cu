@@ -25,24 +25,25 @@ struct Tile {
 };
 
 // Pulled deviations at (x, y): f_i(x, y) = f*_i(x - cx_i, y - cy_i).
-__device__ __forceinline__ void pull9(const float* __restrict__ s, long long P, int pitch, long long c,
-                                      float f[Q]) {
-    f[0] = __ldg(s + c);
-    f[1] = __ldg(s + P + c - 1);                   // c = ( 1, 0)
-    f[2] = __ldg(s + 2 * P + c - pitch);           // c = ( 0, 1)
-    f[3] = __ldg(s + 3 * P + c + 1);               // c = (-1, 0)
-    f[4] = __ldg(s + 4 * P + c + pitch);           // c = ( 0,-1)
-    f[5] = __ldg(s + 5 * P + c - pitch - 1);       // c = ( 1, 1)
-    f[6] = __ldg(s + 6 * P + c - pitch + 1);       // c = (-1, 1)
-    f[7] = __ldg(s + 7 * P + c + pitch + 1);       // c = (-1,-1)
-    f[8] = __ldg(s + 8 * P + c + pitch - 1);       // c = ( 1,-1)
+template <typename T>
+__device__ __forceinline__ void pull9(const T* __restrict__ s, long long P, int pitch, long long c, float f[Q]) {
+    f[0] = Elem<T>::load(s[c], 0);
+    f[1] = Elem<T>::load(s[P + c - 1], 1);                   // c = ( 1, 0)
+    f[2] = Elem<T>::load(s[2 * P + c - pitch], 2);           // c = ( 0, 1)
+    f[3] = Elem<T>::load(s[3 * P + c + 1], 3);               // c = (-1, 0)
+    f[4] = Elem<T>::load(s[4 * P + c + pitch], 4);           // c = ( 0,-1)
+    f[5] = Elem<T>::load(s[5 * P + c - pitch - 1], 5);       // c = ( 1, 1)
+    f[6] = Elem<T>::load(s[6 * P + c - pitch + 1], 6);       // c = (-1, 1)
+    f[7] = Elem<T>::load(s[7 * P + c + pitch + 1], 7);       // c = (-1,-1)
+    f[8] = Elem<T>::load(s[8 * P + c + pitch - 1], 8);       // c = ( 1,-1)
 }
 
-template <int BX, int BY, int MODE>
+template <int BX, int BY, int MODE, typename T>
 __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
     using TL = Tile<BX, BY>;
     __shared__ float rs[TL::RY][TL::RX];
     const Grid g = a.g;
+    const T* __restrict__ src = static_cast<const T*>(a.src);
     const long long P = g.plane;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
     // 1. density on the tile (plus the first column/row past a ragged edge)
     float f[Q];
     if (x <= g.nx && y <= g.ny) {
-        pull9(a.src, P, g.pitch, g.at(x, y), f);
+        pull9(src, P, g.pitch, g.at(x, y), f);
         rs[ty + 1][tx + 1] = drho_of(f);
     } else {
         rs[ty + 1][tx + 1] = 0.0f;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
         float v = 0.0f;
         if (gx >= -1 && gx <= g.nx && gy >= -1 && gy <= g.ny) {
             float h[Q];
-            pull9(a.src, P, g.pitch, g.at(gx, gy), h);
+            pull9(src, P, g.pitch, g.at(gx, gy), h);
             v = drho_of(h);
         }
         rs[hy + 1][hx + 1] = v;
@@ -96,18 +97,24 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
     collide_node<MODE>(a, f, r, node, z, o);
 
     // 9. store (own node plus periodic ghosts)
-    store9(a.dst, P, g, x, y, o);
+    store9(static_cast<T*>(a.dst), P, g, x, y, o);
 }
 
-cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, cudaStream_t s) {
+template <typename T>
+static void launch_t(const StepArgs& a, int noise_mode, cudaStream_t s) {
     constexpr int BX = 32, BY = 16;
     dim3 block(BX, BY);
     dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY);
     switch (noise_mode) {
-        case 0: step_kernel<BX, BY, 0><<<grid, block, 0, s>>>(a); break;
-        case 1: step_kernel<BX, BY, 1><<<grid, block, 0, s>>>(a); break;
-        default: step_kernel<BX, BY, 2><<<grid, block, 0, s>>>(a); break;
+        case 0: step_kernel<BX, BY, 0, T><<<grid, block, 0, s>>>(a); break;
+        case 1: step_kernel<BX, BY, 1, T><<<grid, block, 0, s>>>(a); break;
+        default: step_kernel<BX, BY, 2, T><<<grid, block, 0, s>>>(a); break;
     }
+}
+
+cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, int fp16, cudaStream_t s) {
+    if (fp16) launch_t<__half>(a, noise_mode, s);
+    else launch_t<float>(a, noise_mode, s);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,7 @@
 // lb_step_tma.cu -- the fused fluctuating D2Q9 step, TMA-staged and persistent.
 //
 // Same arithmetic as lb_step.cu (collide_node), different data movement:
-//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles (64 x 16
+//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles (32 x 16
 //     by default), in
 //     row-major tile order, so the tiles in flight form a band whose halo rows are
 //     still in L2 when the neighbouring tile reads them;
@@ -22,15 +22,17 @@
 
 namespace lbf {
 
-template <int TX, int TY>
+template <int TX, int TY, typename T>
 struct TmaTile {
-    static constexpr int BW = TX + 8;                                  // box width (floats)
-    static constexpr int BH = TY + 2;                                  // box height
-    static constexpr int PLANE_BYTES = BW * BH * 4;
-    static constexpr int PS = ((PLANE_BYTES + 127) / 128) * 128 / 4;   // plane stride in smem (floats)
-    static constexpr int STAGE = Q * PS;                               // floats per stage
-    static constexpr int RW = TX + 2, RH = TY + 2;                     // density tile + ring
-    static constexpr int SMEM_BYTES = (2 * STAGE + RW * RH) * 4 + 2 * 8;
+    static constexpr int XO = Elem<T>::XO;                              // 16 bytes of elements
+    static constexpr int BW = TX + 2 * XO;                              // box width (elements)
+    static constexpr int BH = TY + 2;                                   // box height
+    static constexpr int PLANE_BYTES = BW * BH * (int)sizeof(T);
+    static constexpr int PS = ((PLANE_BYTES + 127) / 128) * 128 / (int)sizeof(T);   // plane stride (elements)
+    static constexpr int STAGE = Q * PS;                                // elements per stage
+    static constexpr int STAGE_BYTES = STAGE * (int)sizeof(T);
+    static constexpr int RW = TX + 2, RH = TY + 2;                      // density tile + ring
+    static constexpr int SMEM_BYTES = 2 * STAGE_BYTES + RW * RH * 4 + 2 * 8;
     static constexpr uint32_t TX_BYTES = Q * PLANE_BYTES;
 };
 
@@ -82,16 +84,33 @@ struct TmaArgs {
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s: far beyond any healthy tile load
 
-template <int TX, int TY, int NT, int MODE>
+// The nine pulled deviations of the node whose unshifted box index is b: plane i is read at
+// b - cx_i (its y shift is already in the box origin).
+template <int PS, typename T>
+__device__ __forceinline__ void load9_ps(const T* S, int b, float f[Q]) {
+    f[0] = Elem<T>::load(S[b], 0);
+    f[1] = Elem<T>::load(S[PS + b - 1], 1);
+    f[2] = Elem<T>::load(S[2 * PS + b], 2);
+    f[3] = Elem<T>::load(S[3 * PS + b + 1], 3);
+    f[4] = Elem<T>::load(S[4 * PS + b], 4);
+    f[5] = Elem<T>::load(S[5 * PS + b - 1], 5);
+    f[6] = Elem<T>::load(S[6 * PS + b + 1], 6);
+    f[7] = Elem<T>::load(S[7 * PS + b + 1], 7);
+    f[8] = Elem<T>::load(S[8 * PS + b - 1], 8);
+}
+
+template <int TX, int TY, int NT, int MODE, typename T>
 __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const TmaArgs ta) {
-    using TT = TmaTile<TX, TY>;
-    extern __shared__ __align__(128) float smem[];
-    float* R = smem + 2 * TT::STAGE;
+    using TT = TmaTile<TX, TY, T>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* smem = reinterpret_cast<T*>(smem_raw);
+    float* R = reinterpret_cast<float*>(smem_raw + 2 * TT::STAGE_BYTES);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(R + TT::RW * TT::RH);
     const StepArgs& a = ta.a;
     const Grid g = a.g;
     const int tid = threadIdx.x;
     const int ntiles = ta.ntx * ta.nty;
+    auto load9 = [](const T* S, int b, float f[Q]) { load9_ps<TT::PS>(S, b, f); };
 
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
@@ -105,10 +124,10 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
         const uint32_t bar = smem_u32(&mbar[s]);
         mbar_expect_tx(bar, TT::TX_BYTES);
-        float* st = smem + s * TT::STAGE;
+        T* st = smem + s * TT::STAGE;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            tma_load_3d(smem_u32(st + i * TT::PS), &tmap, x0 - 4 + GX, y0 - 1 - kCYt[i] + GY, i, bar);
+            tma_load_3d(smem_u32(st + i * TT::PS), &tmap, x0 - TT::XO + g.gx, y0 - 1 - kCYt[i] + GY, i, bar);
     };
 
     const int first = blockIdx.x;
@@ -132,7 +151,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             if (tid == 0) atomicExch(ta.err, 1);
             return;
         }
-        const float* S = smem + s * TT::STAGE;
+        const T* S = smem + s * TT::STAGE;
         const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
 
         // density deviation on the tile and its ring: node (lx, ly) = (rx - 1, ry - 1)
@@ -142,17 +161,9 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             const int q = tid + it * NT;
             if (q >= TT::RW * TT::RH) break;
             const int ry = q / TT::RW, rx = q - ry * TT::RW;
-            const int b = ry * TT::BW + rx + 3;
+            const int b = ry * TT::BW + rx + TT::XO - 1;
             float f[Q];
-            f[0] = S[b];
-            f[1] = S[TT::PS + b - 1];
-            f[2] = S[2 * TT::PS + b];
-            f[3] = S[3 * TT::PS + b + 1];
-            f[4] = S[4 * TT::PS + b];
-            f[5] = S[5 * TT::PS + b - 1];
-            f[6] = S[6 * TT::PS + b + 1];
-            f[7] = S[7 * TT::PS + b + 1];
-            f[8] = S[8 * TT::PS + b - 1];
+            load9(S, b, f);
             R[q] = drho_of(f);
         }
         __syncthreads();
@@ -166,17 +177,9 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             const int ly = q / TX, lx = q - ly * TX;
             const int x = x0 + lx, y = y0 + ly;
             if (x >= g.nx || y >= g.ny) continue;
-            const int b = (ly + 1) * TT::BW + lx + 4;
+            const int b = (ly + 1) * TT::BW + lx + TT::XO;
             float f[Q];
-            f[0] = S[b];
-            f[1] = S[TT::PS + b - 1];
-            f[2] = S[2 * TT::PS + b];
-            f[3] = S[3 * TT::PS + b + 1];
-            f[4] = S[4 * TT::PS + b];
-            f[5] = S[5 * TT::PS + b - 1];
-            f[6] = S[6 * TT::PS + b + 1];
-            f[7] = S[7 * TT::PS + b + 1];
-            f[8] = S[8 * TT::PS + b - 1];
+            load9(S, b, f);
             const int rc = (ly + 1) * TT::RW + lx + 1;
             Nbr r;
             r.C = R[rc];
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
             float o[Q];
             collide_node<MODE>(a, f, r, node, z, o);
-            store9(a.dst, g.plane, g, x, y, o);
+            store9(static_cast<T*>(a.dst), g.plane, g, x, y, o);
         }
         __syncthreads();
         // stage s is free again: refill it with the tile two steps ahead
@@ -218,22 +221,26 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// Tile shapes (TX x TY nodes, NT threads): 0 = 64x16/512 (two CTAs per SM, the fastest
-// measured on GB300), 1 = 128x8/512 (two CTAs per SM), 2 = 64x8/256 (four CTAs per SM).
-static const int kTiles[3][3] = {{64, 16, 512}, {128, 8, 512}, {64, 8, 256}};
+// Tile shapes (TX x TY nodes, NT threads): 0 = 32x16/256 (four CTAs per SM, the fastest
+// measured on GB300), 1 = 128x8/512 (two CTAs per SM), 2 = 64x8/256 (four CTAs per SM),
+// 3 = 64x16/512 (two CTAs per SM), 4 = 64x32/1024 (one CTA per SM).
+static const int kTiles[5][3] = {{32, 16, 256}, {128, 8, 512}, {64, 8, 256}, {64, 16, 512}, {64, 32, 1024}};
 
-int tma_tile_count() { return 3; }
+int tma_tile_count() { return 5; }
 
 // Tensor map over one population buffer: dims (pitch, ny + 2 GY, 9) of FP32, box
 // (TX + 8, TY + 2, 1), zero fill outside.
-bool make_pop_tensor_map(const float* buf, const Grid& g, int tile, void* map_out) {
+bool make_pop_tensor_map(const void* buf, const Grid& g, int tile, int fp16, void* map_out) {
     EncodeTiledFn fn = encode_fn();
-    if (!fn || tile < 0 || tile >= 3) return false;
+    if (!fn || tile < 0 || tile >= tma_tile_count()) return false;
+    const cuuint64_t es = fp16 ? 2 : 4;
+    const int xo = fp16 ? Elem<__half>::XO : Elem<float>::XO;
     cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)Q};
-    cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
-    cuuint32_t box[3] = {(cuuint32_t)kTiles[tile][0] + 8, (cuuint32_t)kTiles[tile][1] + 2, 1};
+    cuuint64_t strides[2] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.plane * es};
+    cuuint32_t box[3] = {(cuuint32_t)(kTiles[tile][0] + 2 * xo), (cuuint32_t)kTiles[tile][1] + 2, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)buf, dims,
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(map_out),
+                    fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)buf, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -241,10 +248,10 @@ bool make_pop_tensor_map(const float* buf, const Grid& g, int tile, void* map_ou
 
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
-template <int TX, int TY, int NT, int MODE>
+template <int TX, int TY, int NT, int MODE, typename T>
 static cudaError_t launch_cfg(const void* map, TmaArgs ta, cudaStream_t s) {
-    using TT = TmaTile<TX, TY>;
-    auto kern = step_tma_kernel<TX, TY, NT, MODE>;
+    using TT = TmaTile<TX, TY, T>;
+    auto kern = step_tma_kernel<TX, TY, NT, MODE, T>;
     static int grid_cache = 0;
     if (grid_cache == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES);
@@ -264,26 +271,34 @@ static cudaError_t launch_cfg(const void* map, TmaArgs ta, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, typename T>
 static cudaError_t launch_mode(const void* map, const TmaArgs& ta, int tile, cudaStream_t s) {
     switch (tile) {
-        case 1: return launch_cfg<128, 8, 512, MODE>(map, ta, s);
-        case 2: return launch_cfg<64, 8, 256, MODE>(map, ta, s);
-        default: return launch_cfg<64, 16, 512, MODE>(map, ta, s);
+        case 1: return launch_cfg<128, 8, 512, MODE, T>(map, ta, s);
+        case 2: return launch_cfg<64, 8, 256, MODE, T>(map, ta, s);
+        case 3: return launch_cfg<64, 16, 512, MODE, T>(map, ta, s);
+        case 4: return launch_cfg<64, 32, 1024, MODE, T>(map, ta, s);
+        default: return launch_cfg<32, 16, 256, MODE, T>(map, ta, s);
     }
 }
 
-cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile,
+template <typename T>
+static cudaError_t launch_type(const void* map, const TmaArgs& ta, int noise_mode, int tile, cudaStream_t s) {
+    switch (noise_mode) {
+        case 0: return launch_mode<0, T>(map, ta, tile, s);
+        case 1: return launch_mode<1, T>(map, ta, tile, s);
+        default: return launch_mode<2, T>(map, ta, tile, s);
+    }
+}
+
+cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile, int fp16,
                             cudaStream_t s) {
     TmaArgs ta;
     ta.a = a;
     ta.ntx = ta.nty = 0;
     ta.err = err;
-    switch (noise_mode) {
-        case 0: return launch_mode<0>(src_map, ta, tile, s);
-        case 1: return launch_mode<1>(src_map, ta, tile, s);
-        default: return launch_mode<2>(src_map, ta, tile, s);
-    }
+    return fp16 ? launch_type<__half>(src_map, ta, noise_mode, tile, s)
+                : launch_type<float>(src_map, ta, noise_mode, tile, s);
 }
 
 }  // namespace lbf

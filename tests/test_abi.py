@@ -36,9 +36,11 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_workspace_size(lib):
     assert lbf.lb_workspace_bytes(1, 8) == 0
-    assert lbf.lb_workspace_bytes(64, 64, lbf.LB_FP16DEV) == 0
+    assert lbf.lb_workspace_bytes(64, 64, 7) == 0
     b = lbf.lb_workspace_bytes(64, 64)
     assert b >= 2 * 9 * 64 * 64 * 4 + 2 * 64 * 64 * 8
+    h = lbf.lb_workspace_bytes(64, 64, lbf.LB_FP16DEV)
+    assert 2 * 9 * 64 * 64 * 2 + 2 * 64 * 64 * 8 <= h < b
 
 
 @pytest.mark.parametrize("pars", [

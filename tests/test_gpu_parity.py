@@ -42,9 +42,9 @@ def _pair(nx, ny, seed, rho0, cs2, params, mode, init_scale):
 CONFIG1 = (1e-4, 0.01, 1.0, 1.0, 1.0)   # kT, kappa, tau_s, tau_b, tau_ghost
 
 
-@pytest.fixture(params=["tma", "simple"])
+@pytest.fixture(params=["tma", "simple", "sweep", "sweep6"])
 def kernel(request, monkeypatch):
-    """Both step kernels: the TMA-staged persistent one (default) and the plain one."""
+    """Every step kernel: TMA-staged persistent (default), plain, warp-autonomous sweep."""
     monkeypatch.setenv("LBFLUCT_STEP_KERNEL", request.param)
     return request.param
 

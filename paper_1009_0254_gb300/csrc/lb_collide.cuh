@@ -21,9 +21,10 @@ struct Nbr {
 };
 
 // MODE 0: no noise; 1: uncorrelated (long-wavelength or diagonal); 2: correlated
-// (xi_4, xi_9 given in xi49).
-template <int MODE>
-__device__ __forceinline__ void collide_node(const StepArgs& a, const float f[Q], const Nbr& r, uint32_t node,
+// (xi_4, xi_9 given in xi49).  A carries the relaxation and noise factors, the time and
+// the Philox key (StepArgs with precomputed round keys, or a per-replica record): Args.
+template <int MODE, typename Args>
+__device__ __forceinline__ void collide_node(const Args& a, const float f[Q], const Nbr& r, uint32_t node,
                                              float2 xi49, float o[Q]) {
     // Appendix B: sum_{i != 1} w_i [rho(r+c_i) + rho(r-c_i) - 2 rho(r)] / sigma_s^2
     const float lap = (4.0f * ((r.E + r.W) + (r.N + r.S)) + ((r.NE + r.SW) + (r.NW + r.SE)) - 20.0f * r.C) *

@@ -113,6 +113,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk) {
     return c;
 }
 
+// The same generator keyed by a (k0, k1) pair, the round keys formed on the fly.
+struct KeyPair {
+    uint32_t k0, k1;
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeyPair& kp) {
+    uint32_t k0 = kp.k0, k1 = kp.k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
 // Two unit normals by Box-Muller, sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2), from two
 // 32-bit words: u = (2k+1) 2^-24 with k the top 23 bits, exact in FP32.  Evaluated with
 // the hardware approximations of log2, rsqrt, sin and cos (absolute error below 1e-6 in

@@ -201,6 +201,73 @@ int lb_launch_count(lb_ctx* ctx, int64_t* launches);
 int lb_conserved_sums_static(const double* f, int nx, int ny, double* sums, void* stream);
 
 /*
+ * Batched ensembles: many independent periodic lattices ("replicas") stepped together.
+ * Every replica is the model of [GACV] Sec. III with uncorrelated noise of Sec. IV
+ * (LB_NOISE_OFF, LB_NOISE_LW or LB_NOISE_DIAG; LB_NOISE_FULL is rejected), in FP32
+ * storage, with its own size, seed and parameters, and follows exactly the trajectory
+ * that lb_create/lb_step with the same size, seed and parameters would give it: a
+ * replica's result does not depend on the other replicas of the batch.  Replicas of
+ * equal size share one launch of the step kernel per time step.
+ *
+ * lb_batch_workspace_bytes: device bytes of an ensemble of `count` lattices of sizes
+ *   nx[r] x ny[r] (each side in [2, 8192]); 0 if the sizes are invalid.
+ * lb_batch_create: like lb_create for every replica: seeds[r] keys replica r's Philox
+ *   stream; rho0 and cs2 are common.  workspace NULL: the library allocates and owns
+ *   device memory; else a 256-byte aligned caller buffer of at least
+ *   lb_batch_workspace_bytes() that the caller keeps alive until lb_batch_destroy.
+ *   Every replica starts at rest at time 0.
+ * lb_batch_set_params: lb_set_params for replica `replica`, or for every replica when
+ *   replica == -1; the same validation (lb_check_params), LB_EINVAL for LB_NOISE_FULL.
+ * lb_batch_autotune: times every tile shape of the batched step kernel on each size
+ *   class over `steps` launches and keeps the fastest, then puts every replica back at
+ *   rest at time 0 (populations set before are lost).  Needs parameters for every
+ *   replica; synchronises the stream.
+ * lb_batch_step: advances every replica by nsteps (asynchronous, one kernel per size
+ *   class and one counter update per step, plus the spectra samples).
+ * lb_batch_step_graph: the same, with the steps issued through a CUDA graph of
+ *   steps_per_graph steps (captured on first use, replayed afterwards; a multiple of the
+ *   sampling interval when sampling is on); leftovers run as lb_batch_step.  Results
+ *   are identical to lb_batch_step.
+ * lb_batch_get_time: the time t of replica `replica`.
+ * lb_batch_set_populations / lb_batch_get_populations: as lb_set_populations /
+ *   lb_get_populations for one replica (f holds nx[r]*ny[r]*9 doubles); setting also
+ *   sets that replica's time to t.  Synchronise the stream.
+ * lb_batch_sums: FP64 sums of (rho, jx, jy) of one replica.  Synchronises.
+ * lb_batch_set_sampling: every `every` steps, the radial spectra of [GACV] Sec. V of
+ *   every replica are accumulated (every = 0: off); nbins in [1, 1024]; every lattice
+ *   side must be a power of two.  Clears the accumulated spectra.
+ * lb_batch_structure_factor: as lb_structure_factor for one replica.
+ * lb_batch_launch_count: kernels launched on behalf of the ensemble so far (a graph
+ *   replay counts the kernels it contains).
+ * lb_batch_tuning: the tile shape of the step kernel in use (tile_x x tile_y nodes per
+ *   tile, `threads` threads per CTA) and the time per step lb_batch_autotune measured
+ *   for it (0 before any autotune); any output pointer may be NULL.
+ * lb_batch_last_error: message of the last failure on b (NULL b: of the last failed
+ *   lb_batch_create, as lb_last_error(NULL)).
+ */
+typedef struct lb_batch lb_batch;
+size_t lb_batch_workspace_bytes(int count, const int* nx, const int* ny);
+int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* seeds, double rho0,
+                    double cs2, void* workspace, size_t workspace_bytes, lb_batch** out);
+int lb_batch_destroy(lb_batch* b);
+int lb_batch_set_stream(lb_batch* b, void* stream);
+int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, double tau_s,
+                        double tau_b, double tau_ghost, int noise_mode);
+int lb_batch_autotune(lb_batch* b, int steps);
+int lb_batch_step(lb_batch* b, int64_t nsteps);
+int lb_batch_step_graph(lb_batch* b, int64_t nsteps, int64_t steps_per_graph);
+int lb_batch_get_time(lb_batch* b, int replica, int64_t* t);
+int lb_batch_set_populations(lb_batch* b, int replica, const double* f, int loc, int64_t t);
+int lb_batch_get_populations(lb_batch* b, int replica, double* f, int loc);
+int lb_batch_sums(lb_batch* b, int replica, double* sums);
+int lb_batch_set_sampling(lb_batch* b, int every, int nbins);
+int lb_batch_structure_factor(lb_batch* b, int replica, int nbins, double* S_rho, double* S_jl,
+                              double* S_jt, int64_t* counts, int64_t* nsamples);
+int lb_batch_launch_count(lb_batch* b, int64_t* launches);
+int lb_batch_tuning(lb_batch* b, int* tile_x, int* tile_y, int* threads, double* ms_per_step);
+const char* lb_batch_last_error(lb_batch* b);
+
+/*
  * Host-only helpers (no GPU needed).
  * lb_noise_matrix: the 9x9 noise covariance Xi(k) of [GACV] Eq. (noise-yeo) for the
  * given parameters at wavevector (kx, ky), with k^2 the lattice symbol of Appendix B;

@@ -66,6 +66,23 @@ def load(path: str = LIB_PATH):
         "lb_noise_matrix": (c_int, [c_dbl] * 9 + [dp]),
         "lb_check_params": (c_int, [c_int, c_int] + [c_dbl] * 7 + [c_int]),
         "lb_conserved_sums_static": (c_int, [vp, c_int, c_int, vp, vp]),
+        "lb_batch_workspace_bytes": (c_sz, [c_int, vp, vp]),
+        "lb_batch_create": (c_int, [c_int, vp, vp, vp, c_dbl, c_dbl, vp, c_sz, ctypes.POINTER(vp)]),
+        "lb_batch_destroy": (c_int, [vp]),
+        "lb_batch_set_stream": (c_int, [vp, vp]),
+        "lb_batch_set_params": (c_int, [vp, c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_int]),
+        "lb_batch_autotune": (c_int, [vp, c_int]),
+        "lb_batch_step": (c_int, [vp, c_i64]),
+        "lb_batch_step_graph": (c_int, [vp, c_i64, c_i64]),
+        "lb_batch_get_time": (c_int, [vp, c_int, i64p]),
+        "lb_batch_set_populations": (c_int, [vp, c_int, vp, c_int, c_i64]),
+        "lb_batch_get_populations": (c_int, [vp, c_int, vp, c_int]),
+        "lb_batch_sums": (c_int, [vp, c_int, dp]),
+        "lb_batch_set_sampling": (c_int, [vp, c_int, c_int]),
+        "lb_batch_structure_factor": (c_int, [vp, c_int, c_int, dp, dp, dp, i64p, i64p]),
+        "lb_batch_launch_count": (c_int, [vp, i64p]),
+        "lb_batch_tuning": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int), dp]),
+        "lb_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in proto.items():
         fn = getattr(L, name)
@@ -78,6 +95,13 @@ def load(path: str = LIB_PATH):
 def _check(rc, ctx=None):
     if rc < 0:
         msg = load().lb_last_error(ctx)
+        raise LBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _bcheck(rc, b=None):
+    if rc < 0:
+        msg = load().lb_batch_last_error(b)
         raise LBError(rc, msg.decode() if msg else "")
     return rc
 
@@ -204,7 +228,99 @@ def lb_check_params(nx, ny, rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise
     return load().lb_check_params(nx, ny, rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
 
 
-# --- convenience wrapper -------------------------------------------------------------------
+# --- batched ensembles -----------------------------------------------------------------------
+
+def _i32(v):
+    return np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+
+
+def lb_batch_workspace_bytes(nx, ny):
+    nx, ny = _i32(nx), _i32(ny)
+    return load().lb_batch_workspace_bytes(len(nx), nx.ctypes.data, ny.ctypes.data)
+
+
+def lb_batch_create(nx, ny, seeds, rho0=1.0, cs2=1.0 / 3.0, workspace=None, workspace_bytes=0):
+    nx, ny = _i32(nx), _i32(ny)
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    if not (len(nx) == len(ny) == len(sd)):
+        raise LBError(LB_EINVAL, "nx, ny and seeds must have one entry per replica")
+    out = ctypes.c_void_p()
+    _bcheck(load().lb_batch_create(len(nx), nx.ctypes.data, ny.ctypes.data, sd.ctypes.data, rho0, cs2,
+                                   _ptr(workspace), workspace_bytes, ctypes.byref(out)))
+    return out.value
+
+
+def lb_batch_destroy(b):
+    return _bcheck(load().lb_batch_destroy(b))
+
+
+def lb_batch_set_stream(b, stream):
+    return _bcheck(load().lb_batch_set_stream(b, stream), b)
+
+
+def lb_batch_set_params(b, replica, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+    return _bcheck(load().lb_batch_set_params(b, replica, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode), b)
+
+
+def lb_batch_autotune(b, steps):
+    return _bcheck(load().lb_batch_autotune(b, steps), b)
+
+
+def lb_batch_step(b, nsteps):
+    return _bcheck(load().lb_batch_step(b, nsteps), b)
+
+
+def lb_batch_step_graph(b, nsteps, steps_per_graph):
+    return _bcheck(load().lb_batch_step_graph(b, nsteps, steps_per_graph), b)
+
+
+def lb_batch_get_time(b, replica):
+    t = ctypes.c_int64()
+    _bcheck(load().lb_batch_get_time(b, replica, ctypes.byref(t)), b)
+    return t.value
+
+
+def lb_batch_set_populations(b, replica, f, loc, t):
+    return _bcheck(load().lb_batch_set_populations(b, replica, _ptr(f), loc, t), b)
+
+
+def lb_batch_get_populations(b, replica, f, loc):
+    return _bcheck(load().lb_batch_get_populations(b, replica, _ptr(f), loc), b)
+
+
+def lb_batch_sums(b, replica, sums):
+    return _bcheck(load().lb_batch_sums(b, replica, _dptr(sums)), b)
+
+
+def lb_batch_set_sampling(b, every, nbins):
+    return _bcheck(load().lb_batch_set_sampling(b, every, nbins), b)
+
+
+def lb_batch_structure_factor(b, replica, nbins, S_rho, S_jl, S_jt, counts, nsamples):
+    i64 = lambda a: ctypes.cast(_ptr(a), ctypes.POINTER(ctypes.c_int64)) if a is not None else None
+    return _bcheck(load().lb_batch_structure_factor(b, replica, nbins, _dptr(S_rho), _dptr(S_jl), _dptr(S_jt),
+                                                    i64(counts), i64(nsamples)), b)
+
+
+def lb_batch_launch_count(b):
+    n = ctypes.c_int64()
+    _bcheck(load().lb_batch_launch_count(b, ctypes.byref(n)), b)
+    return n.value
+
+
+def lb_batch_tuning(b):
+    """(tile_x, tile_y, threads, ms_per_step) of the step kernel in use."""
+    tx, ty, nt, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _bcheck(load().lb_batch_tuning(b, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(nt), ctypes.byref(ms)), b)
+    return tx.value, ty.value, nt.value, ms.value
+
+
+def lb_batch_last_error(b=None):
+    m = load().lb_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+# --- convenience wrappers ------------------------------------------------------------------
 
 class Lattice:
     """One lattice on the current CUDA device.  PyTorch allocates the workspace and
@@ -276,4 +392,82 @@ class Lattice:
         cnt = np.zeros(nb, dtype=np.int64)
         ns = np.zeros(1, dtype=np.int64)
         lb_structure_factor(self.ctx, nb, S, L, Tt, cnt, ns)
+        return S, L, Tt, cnt, int(ns[0])
+
+
+class Ensemble:
+    """Many independent lattices stepped together on the current CUDA device (workspace
+    owned by PyTorch, stream as for ``Lattice``).  ``sizes`` is a list of (nx, ny)."""
+
+    def __init__(self, sizes, seeds, rho0=1.0, cs2=1.0 / 3.0, stream=None):
+        import torch
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        nx = [a for a, _ in self.sizes]
+        ny = [b for _, b in self.sizes]
+        nbytes = lb_batch_workspace_bytes(nx, ny)
+        if nbytes == 0:
+            raise LBError(LB_EINVAL, "invalid lattice sizes")
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        aligned = (self._ws.data_ptr() + 255) & ~255
+        self.b = lb_batch_create(nx, ny, seeds, rho0, cs2, aligned, nbytes)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        lb_batch_set_stream(self.b, self.stream.cuda_stream)
+        self.nbins = 0
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, replica, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+        lb_batch_set_params(self.b, replica, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
+
+    def autotune(self, steps=10):
+        lb_batch_autotune(self.b, steps)
+
+    def step(self, n=1, graph_steps=0):
+        if graph_steps > 0:
+            lb_batch_step_graph(self.b, n, graph_steps)
+        else:
+            lb_batch_step(self.b, n)
+
+    def t(self, replica):
+        return lb_batch_get_time(self.b, replica)
+
+    def set_populations(self, replica, f, t=0):
+        nx, ny = self.sizes[replica]
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, ny, nx)
+        lb_batch_set_populations(self.b, replica, f, LB_HOST, t)
+
+    def populations(self, replica):
+        nx, ny = self.sizes[replica]
+        f = np.empty((9, ny, nx))
+        lb_batch_get_populations(self.b, replica, f, LB_HOST)
+        return f
+
+    def sums(self, replica):
+        s = np.zeros(3)
+        lb_batch_sums(self.b, replica, s)
+        return s
+
+    def set_sampling(self, every, nbins):
+        lb_batch_set_sampling(self.b, every, nbins)
+        self.nbins = nbins
+
+    def structure_factor(self, replica):
+        nb = self.nbins
+        S, L, Tt = np.zeros(nb), np.zeros(nb), np.zeros(nb)
+        cnt = np.zeros(nb, dtype=np.int64)
+        ns = np.zeros(1, dtype=np.int64)
+        lb_batch_structure_factor(self.b, replica, nb, S, L, Tt, cnt, ns)
         return S, L, Tt, cnt, int(ns[0])

@@ -74,19 +74,6 @@ const int CXh[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 const int CYh[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 const double Wh[Q] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
-// Rest populations fbar_i = w_i (rho0 + T_4i d rho0 / N_4 - T_9i d rho0 / N_9) for the
-// reference moments {rho0, 0, 0, d rho0, 0, 0, 0, 0, -d rho0}, d = 6 (cs2 - sigma_s^2)
-// (Table II at u = 0 with p0 = cs2 rho; inverse transform of Sec. III A).
-void rest_populations(double rho0, double cs2, double fbar[Q]) {
-    const double d = 6.0 * (cs2 - SIGMA_S2);
-    for (int i = 0; i < Q; ++i) {
-        const double c2 = CXh[i] * CXh[i] + CYh[i] * CYh[i];
-        const double t4 = 3.0 * c2 - 2.0;
-        const double t9 = 9.0 * c2 * c2 - 15.0 * c2 + 2.0;
-        fbar[i] = Wh[i] * (rho0 + t4 * d * rho0 / 4.0 - t9 * d * rho0 / 16.0);
-    }
-}
-
 // Noise covariance of [GACV] Eq. (noise-yeo) as functions of the lattice k^2 (s):
 // Xi_44 = a44 + b44 s, Xi_49 = a49 + b49 s, Xi_99 = a99 + b99 s; the shear and ghost
 // entries do not depend on k.
@@ -223,6 +210,20 @@ struct lb_ctx {
 
 namespace lbf {
 void set_context_free_error(const std::string& msg) { g_create_error = msg; }
+
+// Rest populations fbar_i = w_i (rho0 + T_4i d rho0 / N_4 - T_9i d rho0 / N_9) for the
+// reference moments {rho0, 0, 0, d rho0, 0, 0, 0, 0, -d rho0}, d = 6 (cs2 - sigma_s^2)
+// (Table II at u = 0 with p0 = cs2 rho; inverse transform of Sec. III A).
+void rest_populations(double rho0, double cs2, double fbar[Q]) {
+    const double d = 6.0 * (cs2 - SIGMA_S2);
+    for (int i = 0; i < Q; ++i) {
+        const double c2 = CXh[i] * CXh[i] + CYh[i] * CYh[i];
+        const double t4 = 3.0 * c2 - 2.0;
+        const double t9 = 9.0 * c2 * c2 - 15.0 * c2 + 2.0;
+        fbar[i] = Wh[i] * (rho0 + t4 * d * rho0 / 4.0 - t9 * d * rho0 / 16.0);
+    }
+}
+
 }  // namespace lbf
 
 static int fail(lb_ctx* c, int code, const std::string& msg) {

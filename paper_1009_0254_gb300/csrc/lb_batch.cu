@@ -1,0 +1,1024 @@
+// lb_batch.cu -- many independent lattices ("replicas") stepped together.
+//
+// Replicas of equal size form a class.  A class keeps its populations replica-major in
+// one buffer pair, [replica][plane][row][column] with the single-lattice layout per replica,
+// so one 4D tensor map (x, y, plane, replica) serves the whole class.  One persistent launch
+// of the batched TMA step kernel advances every replica of up to MAX_CLASSES classes by one
+// step: the launch's tiles are numbered class by class, replica by replica, and every CTA
+// walks its share of them through a two-stage TMA pipeline.  Each replica keeps its own
+// Philox key (its seed), relaxation and noise factors and time offset in a device record;
+// the step counter K lives in device memory and is advanced by the last CTA of the step's
+// last launch, so a captured CUDA graph of G steps can be replayed as it is: a replica's
+// time is K + offset, and K's parity selects the source buffer.  A replica stepped in a
+// batch follows exactly the trajectory it would follow stepped alone.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lb_collide.cuh"
+#include "lb_fft_core.cuh"
+#include "lb_internal.cuh"
+#include "lb_tma.cuh"
+#include "lbfluct.h"
+
+namespace lbf {
+
+constexpr int MAX_CLASSES = 8;      // size classes per launch (kernel parameters stay < 4 KB)
+
+// Per-replica record (device).
+struct RepRec {
+    float rho0, cs2m, kappa, lb, ls, lq, le;
+    float L44, L94, L99, s5, s6, s7;
+    int mode;                 // 0 no noise, 1 uncorrelated noise
+    uint32_t k0, k1;          // Philox key = the replica's seed
+    long long toff;           // time = K + toff
+};
+
+// What collide_node needs for one tile of one replica, in registers.
+struct TileArgs {
+    float rho0, cs2m, kappa, lb, ls, lq, le;
+    float L44, L94, L99, s5, s6, s7;
+    uint32_t t_lo, t_hi;
+    KeyPair rk;
+};
+
+struct ClassDesc {
+    Grid g;
+    float* buf[2];              // the class's two population buffers
+    const RepRec* recs;         // its replicas' records
+    int tile_begin;             // first tile of the class in the launch's numbering
+    int ntx, per;               // tiles along x per replica, tiles per replica
+    long long rstride;          // elements per replica (9 planes)
+};
+
+struct EnsParams {
+    CUtensorMap map[MAX_CLASSES][2];   // per class: map of buffer 0, of buffer 1
+    ClassDesc cls[MAX_CLASSES];
+    int nclass, ntiles;
+    long long* kstep;                  // device step counter K
+    unsigned int* done;                // CTAs finished in this launch (advancing launch only)
+    int* err;                          // set when a bounded wait gives up
+    int advance;                       // this launch advances K when its last CTA finishes
+};
+
+// Collide and stream the TX x TY nodes of one tile from the staged populations S and the
+// density tile R (with its one-node ring).
+template <int MODE, int TX, int TY, int NT>
+__device__ __forceinline__ void tile_nodes(const TileArgs& a, const float* S, const float* R, const Grid& g, int x0,
+                                           int y0, float* dst) {
+    using TT = TmaTile<TX, TY, float>;
+    static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
+#pragma unroll
+    for (int it = 0; it < TX * TY / NT; ++it) {
+        const int q = threadIdx.x + it * NT;
+        const int ly = q / TX, lx = q - ly * TX;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x >= g.nx || y >= g.ny) continue;
+        float f[Q];
+        load9_ps<TT::PS>(S, (ly + 1) * TT::BW + lx + TT::XO, f);
+        const int rc = (ly + 1) * TT::RW + lx + 1;
+        Nbr r;
+        r.C = R[rc];
+        r.E = R[rc + 1]; r.W = R[rc - 1];
+        r.N = R[rc + TT::RW]; r.S = R[rc - TT::RW];
+        r.NE = R[rc + TT::RW + 1]; r.NW = R[rc + TT::RW - 1];
+        r.SE = R[rc - TT::RW + 1]; r.SW = R[rc - TT::RW - 1];
+        const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+        float o[Q];
+        collide_node<MODE>(a, f, r, node, make_float2(0.f, 0.f), o);
+        store9(dst, g.plane, g, x, y, o);
+    }
+}
+
+// class, replica and origin of a tile of the launch
+struct TilePos {
+    int c, rep, x0, y0;
+};
+
+template <int TX, int TY>
+__device__ __forceinline__ TilePos locate(const EnsParams& p, int tile) {
+    TilePos t;
+    int c = 0;
+#pragma unroll 1
+    while (c + 1 < p.nclass && tile >= p.cls[c + 1].tile_begin) ++c;
+    const ClassDesc& d = p.cls[c];
+    const int rel = tile - d.tile_begin;
+    t.c = c;
+    t.rep = rel / d.per;
+    const int rem = rel - t.rep * d.per;
+    const int ty = rem / d.ntx;
+    t.x0 = (rem - ty * d.ntx) * TX;
+    t.y0 = ty * TY;
+    return t;
+}
+
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant__ EnsParams p) {
+    using TT = TmaTile<TX, TY, float>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* smem = reinterpret_cast<float*>(smem_raw);
+    float* R = reinterpret_cast<float*>(smem_raw + 2 * TT::STAGE_BYTES);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(R + TT::RW * TT::RH);
+    const int tid = threadIdx.x;
+    const long long K = __ldcg(p.kstep);
+    const int par = (int)(K & 1);
+    const int ntiles = p.ntiles;
+
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    auto issue = [&](int tile, int s) {
+        const TilePos tp = locate<TX, TY>(p, tile);
+        const CUtensorMap* map = &p.map[tp.c][par];
+        const int gx = p.cls[tp.c].g.gx;
+        const uint32_t bar = smem_u32(&mbar[s]);
+        mbar_expect_tx(bar, TT::TX_BYTES);
+        float* st = smem + s * TT::STAGE;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            tma_load_4d(smem_u32(st + i * TT::PS), map, tp.x0 - TT::XO + gx, tp.y0 - 1 - kCYt[i] + GY, i, tp.rep,
+                        bar);
+    };
+
+    const int first = blockIdx.x;
+    if (tid == 0) {
+        if (first < ntiles) issue(first, 0);
+        if (first + (int)gridDim.x < ntiles) issue(first + gridDim.x, 1);
+    }
+    int k = 0;
+    for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
+        const int s = k & 1;
+        const bool ok = mbar_wait_bounded(smem_u32(&mbar[s]), (uint32_t)((k >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(p.err, 1);
+                // give the loads still in flight into this CTA's shared memory a bounded
+                // chance to land before the CTA exits
+                mbar_wait_bounded(smem_u32(&mbar[s]), (uint32_t)((k >> 1) & 1));
+                if (tile + (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(smem_u32(&mbar[s ^ 1]), (uint32_t)(((k + 1) >> 1) & 1));
+            }
+            break;
+        }
+        const TilePos tp = locate<TX, TY>(p, tile);
+        const ClassDesc& d = p.cls[tp.c];
+        const Grid g = d.g;
+        const float* S = smem + s * TT::STAGE;
+
+        constexpr int NA = (TT::RW * TT::RH + NT - 1) / NT;
+#pragma unroll
+        for (int it = 0; it < NA; ++it) {
+            const int q = tid + it * NT;
+            if (q >= TT::RW * TT::RH) break;
+            const int ry = q / TT::RW, rx = q - ry * TT::RW;
+            float f[Q];
+            load9_ps<TT::PS>(S, ry * TT::BW + rx + TT::XO - 1, f);
+            R[q] = drho_of(f);
+        }
+        __syncthreads();
+
+        // the replica's record (the same address for every thread of the CTA)
+        const RepRec* rp = d.recs + tp.rep;
+        TileArgs a;
+        a.rho0 = __ldg(&rp->rho0); a.cs2m = __ldg(&rp->cs2m); a.kappa = __ldg(&rp->kappa);
+        a.lb = __ldg(&rp->lb); a.ls = __ldg(&rp->ls); a.lq = __ldg(&rp->lq); a.le = __ldg(&rp->le);
+        a.L44 = __ldg(&rp->L44); a.L94 = __ldg(&rp->L94); a.L99 = __ldg(&rp->L99);
+        a.s5 = __ldg(&rp->s5); a.s6 = __ldg(&rp->s6); a.s7 = __ldg(&rp->s7);
+        a.rk.k0 = __ldg(&rp->k0); a.rk.k1 = __ldg(&rp->k1);
+        const long long t = K + __ldg(&rp->toff);
+        a.t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);
+        a.t_hi = (uint32_t)((unsigned long long)t >> 32);
+        const int mode = __ldg(&rp->mode);
+        float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
+
+        if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst);
+        else tile_nodes<0, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst);
+        __syncthreads();
+        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(tile + 2 * gridDim.x, s);
+        }
+    }
+    // Every CTA read K before arriving here; the last one to arrive advances it for the
+    // next step (the next launch sees it, kernel boundaries order the accesses).
+    if (tid == 0 && p.advance) {
+        const unsigned int prev = atomicAdd(p.done, 1u);
+        if (prev == gridDim.x - 1) {
+            *p.done = 0u;
+            *p.kstep = K + 1;
+        }
+    }
+}
+
+// --- spectra of a class ----------------------------------------------------------------
+
+// z1 = drho + i jx, z2 = jy of every replica of the class (state of the current buffer)
+// (the buffer holding the state is chosen by the parity of the device step counter, so a
+// captured sample stays correct in every replay of its graph)
+__global__ void batch_fields_kernel(const float* __restrict__ buf0, const float* __restrict__ buf1,
+                                    const long long* __restrict__ kstep, long long rstride, Grid g, float2* z1,
+                                    float2* z2) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int rep = blockIdx.z;
+    if (x >= g.nx) return;
+    const float* src = ((__ldg(kstep) & 1) ? buf1 : buf0) + (long long)rep * rstride;
+    const long long P = g.plane;
+    const long long c = g.at(x, y);
+    const float f0 = src[c], f1 = src[P + c - 1], f2 = src[2 * P + c - g.pitch], f3 = src[3 * P + c + 1];
+    const float f4 = src[4 * P + c + g.pitch], f5 = src[5 * P + c - g.pitch - 1];
+    const float f6 = src[6 * P + c - g.pitch + 1], f7 = src[7 * P + c + g.pitch + 1];
+    const float f8 = src[8 * P + c + g.pitch - 1];
+    const float drho = f0 + ((f1 + f3) + (f2 + f4)) + ((f5 + f7) + (f6 + f8));
+    const float jx = (f1 - f3) + (f5 - f7) + (f8 - f6);
+    const float jy = (f2 - f4) + (f5 - f7) + (f6 - f8);
+    const long long o = ((long long)rep * g.ny + y) * g.nx + x;
+    z1[o] = make_float2(drho, jx);
+    z2[o] = make_float2(jy, 0.f);
+}
+
+__device__ __forceinline__ int ilog2b(int n) { return 31 - __clz(n); }
+
+// forward row transforms of R*ny consecutive rows, scaled on the way out
+__global__ void __launch_bounds__(1024) batch_rows_kernel(float2* data, int nx, const float2* __restrict__ twx,
+                                                          float scale) {
+    extern __shared__ float2 sm[];
+    float2* rowp = data + (long long)blockIdx.x * nx;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = rowp[j];
+    stockham_fft(sm, nx, ilog2b(nx), 1, +1, twx);
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        const float2 v = sm[fpad(j)];
+        rowp[j] = make_float2(v.x * scale, v.y * scale);
+    }
+}
+
+// forward column transforms, strips of `count` columns, replica blockIdx.y
+__global__ void __launch_bounds__(1024) batch_cols_kernel(float2* data, int nx, int ny, int count,
+                                                          const float2* __restrict__ twy, float scale) {
+    extern __shared__ float2 sm[];
+    float2* base = data + (long long)blockIdx.y * nx * ny;
+    const int xs = blockIdx.x * count;
+    const int lc = 31 - __clz(count);
+    const int total = ny * count;
+    for (int e = threadIdx.x; e < total; e += blockDim.x)
+        sm[fpad(e)] = base[(long long)(e >> lc) * nx + xs + (e & (count - 1))];
+    stockham_fft(sm, ny, ilog2b(ny), count, +1, twy);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const float2 v = sm[fpad(e)];
+        base[(long long)(e >> lc) * nx + xs + (e & (count - 1))] = make_float2(v.x * scale, v.y * scale);
+    }
+}
+
+// per-replica radial bins (bins[rep][3][nbins]) from the class's bin table
+__global__ void batch_bin_kernel(const float2* __restrict__ z1, const float2* __restrict__ z2,
+                                 const unsigned short* __restrict__ bin16, int nx, int ny, int nbins, double* bins) {
+    extern __shared__ double sb[];
+    for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x) sb[j] = 0.0;
+    __syncthreads();
+    const int rep = blockIdx.y;
+    const long long n = (long long)nx * ny;
+    const float2* a1 = z1 + rep * n;
+    const float2* a2 = z2 + rep * n;
+    const float tpx = 6.2831853071795865f / (float)nx, tpy = 6.2831853071795865f / (float)ny;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+        const int b = bin16[o];
+        if (b == 0xFFFF) continue;
+        const int mx = (int)(o % nx), my = (int)(o / nx);
+        const int cx = (nx - mx) & (nx - 1), cy = (ny - my) & (ny - 1);
+        const float kx = tpx * (float)(mx > nx / 2 ? mx - nx : mx);
+        const float ky = tpy * (float)(my > ny / 2 ? my - ny : my);
+        const float inv = rsqrtf(kx * kx + ky * ky);
+        const float2 a = a1[o], am = a1[(long long)cy * nx + cx], c = a2[o];
+        const float rr = 0.5f * (a.x + am.x), ri = 0.5f * (a.y - am.y);
+        const float xr = 0.5f * (a.y + am.y), xi = -0.5f * (a.x - am.x);
+        const float lr = (kx * xr + ky * c.x) * inv, li = (kx * xi + ky * c.y) * inv;
+        const float tr = (-ky * xr + kx * c.x) * inv, ti = (-ky * xi + kx * c.y) * inv;
+        atomicAdd(&sb[b], (double)(rr * rr + ri * ri));
+        atomicAdd(&sb[nbins + b], (double)(lr * lr + li * li));
+        atomicAdd(&sb[2 * nbins + b], (double)(tr * tr + ti * ti));
+    }
+    __syncthreads();
+    double* out = bins + (long long)rep * 3 * nbins;
+    for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x)
+        if (sb[j] != 0.0) atomicAdd(&out[j], sb[j]);
+}
+
+// --- host side -------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFnB)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFnB encode_fn_b() {
+    static EncodeTiledFnB fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFnB)p;
+    }
+    return fn;
+}
+
+// Tile shapes the autotuner chooses from: (TX, TY, NT); TX * TY / NT nodes per thread.
+static const int kBatchTiles[][3] = {{32, 16, 256}, {32, 16, 128}, {32, 8, 256}, {32, 8, 128},
+                                     {64, 8, 256},  {64, 16, 512}, {32, 32, 512}};
+constexpr int kBatchTileCount = 7;
+
+static bool make_class_map(void* buf, const Grid& g, int R, int tile, CUtensorMap* map) {
+    EncodeTiledFnB fn = encode_fn_b();
+    if (!fn || tile < 0 || tile >= kBatchTileCount) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)Q, (cuuint64_t)R};
+    cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.plane * 4 * Q};
+    // box: the tile plus 4 columns (16 bytes) on either side and one row above and below
+    cuuint32_t box[4] = {(cuuint32_t)(kBatchTiles[tile][0] + 8), (cuuint32_t)(kBatchTiles[tile][1] + 2), 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// CTAs of a persistent launch: every SM filled to the occupancy the kernel allows
+template <int TX, int TY, int NT>
+static cudaError_t ensemble_grid(int* grid) {
+    using TT = TmaTile<TX, TY, float>;
+    static int cached = 0;
+    if (cached == 0) {
+        auto kern = step_ensemble_kernel<TX, TY, NT>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, TT::SMEM_BYTES)) != cudaSuccess)
+            return e;
+        cached = sms * (per > 0 ? per : 1);
+    }
+    *grid = cached;
+    return cudaSuccess;
+}
+
+template <int TX, int TY, int NT>
+static cudaError_t launch_ensemble_t(const EnsParams& p, cudaStream_t s) {
+    using TT = TmaTile<TX, TY, float>;
+    int grid = 0;
+    cudaError_t e = ensemble_grid<TX, TY, NT>(&grid);
+    if (e != cudaSuccess) return e;
+    step_ensemble_kernel<TX, TY, NT><<<std::max(1, std::min(p.ntiles, grid)), NT, TT::SMEM_BYTES, s>>>(p);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_ensemble(int tile, const EnsParams& p, cudaStream_t s) {
+    switch (tile) {
+        case 1: return launch_ensemble_t<32, 16, 128>(p, s);
+        case 2: return launch_ensemble_t<32, 8, 256>(p, s);
+        case 3: return launch_ensemble_t<32, 8, 128>(p, s);
+        case 4: return launch_ensemble_t<64, 8, 256>(p, s);
+        case 5: return launch_ensemble_t<64, 16, 512>(p, s);
+        case 6: return launch_ensemble_t<32, 32, 512>(p, s);
+        default: return launch_ensemble_t<32, 16, 256>(p, s);
+    }
+}
+
+// prepares every kernel of the engine (attributes, occupancy) outside any stream capture
+static cudaError_t prepare_ensemble_kernels() {
+    int g = 0;
+    cudaError_t e;
+    if ((e = ensemble_grid<32, 16, 256>(&g)) != cudaSuccess) return e;
+    if ((e = ensemble_grid<32, 16, 128>(&g)) != cudaSuccess) return e;
+    if ((e = ensemble_grid<32, 8, 256>(&g)) != cudaSuccess) return e;
+    if ((e = ensemble_grid<32, 8, 128>(&g)) != cudaSuccess) return e;
+    if ((e = ensemble_grid<64, 8, 256>(&g)) != cudaSuccess) return e;
+    if ((e = ensemble_grid<64, 16, 512>(&g)) != cudaSuccess) return e;
+    return ensemble_grid<32, 32, 512>(&g);
+}
+
+}  // namespace lbf
+
+using namespace lbf;
+
+namespace {
+
+constexpr int kMaxBatchBins = 1024;
+constexpr double SIGMA_S2_B = 1.0 / 3.0;
+
+size_t align256b(size_t v) { return (v + 255) & ~size_t(255); }
+
+bool pow2b(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+
+bool grid_of(int nx, int ny, Grid* g) {
+    if (nx < 2 || ny < 2 || nx > 8192 || ny > 8192) return false;
+    g->nx = nx; g->ny = ny; g->gx = 32;
+    g->pitch = (nx + 64 + 31) / 32 * 32;
+    g->plane = ((long long)g->pitch * (ny + 2 * GY) + 63) / 64 * 64;
+    return true;
+}
+
+struct ClassInfo {
+    int nx, ny, R;
+    Grid g;
+    std::vector<int> members;          // replica ids, in class order
+    size_t off_buf[2], off_z1, off_z2, off_tw_x, off_tw_y, off_bin16, off_bins, off_counts, off_recs;
+};
+
+struct Layout {
+    std::vector<ClassInfo> classes;
+    std::vector<int> cls_of, slot_of;  // replica -> class, index within the class
+    size_t off_k, off_done, off_err, off_partial, off_sums, off_stage, off_fbar, total;
+};
+
+bool plan(int count, const int* nx, const int* ny, Layout* L) {
+    std::map<std::pair<int, int>, int> index;
+    L->classes.clear();
+    L->cls_of.assign(count, 0);
+    L->slot_of.assign(count, 0);
+    size_t biggest = 0;
+    for (int r = 0; r < count; ++r) {
+        Grid g;
+        if (!grid_of(nx[r], ny[r], &g)) return false;
+        auto key = std::make_pair(nx[r], ny[r]);
+        auto it = index.find(key);
+        int c;
+        if (it == index.end()) {
+            c = (int)L->classes.size();
+            index[key] = c;
+            ClassInfo ci;
+            ci.nx = nx[r]; ci.ny = ny[r]; ci.R = 0; ci.g = g;
+            L->classes.push_back(ci);
+        } else {
+            c = it->second;
+        }
+        L->cls_of[r] = c;
+        L->slot_of[r] = L->classes[c].R++;
+        L->classes[c].members.push_back(r);
+        biggest = std::max(biggest, (size_t)nx[r] * ny[r]);
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256b(off + bytes); return o; };
+    for (auto& ci : L->classes) {
+        const size_t n = (size_t)ci.nx * ci.ny;
+        const size_t rbytes = (size_t)Q * ci.g.plane * sizeof(float) * ci.R;
+        ci.off_buf[0] = take(rbytes);
+        ci.off_buf[1] = take(rbytes);
+        ci.off_z1 = take(n * ci.R * sizeof(float2));
+        ci.off_z2 = take(n * ci.R * sizeof(float2));
+        ci.off_tw_x = take(ci.nx * sizeof(float2));
+        ci.off_tw_y = take(ci.ny * sizeof(float2));
+        ci.off_bin16 = take(n * sizeof(unsigned short));
+        ci.off_bins = take((size_t)ci.R * 3 * kMaxBatchBins * sizeof(double));
+        ci.off_counts = take((size_t)kMaxBatchBins * sizeof(unsigned long long));
+        ci.off_recs = take((size_t)ci.R * sizeof(RepRec));
+    }
+    L->off_k = take(sizeof(long long));
+    L->off_done = take(sizeof(unsigned int));
+    L->off_err = take(sizeof(int));
+    L->off_partial = take((size_t)sums_partial_count() * sizeof(double));
+    L->off_sums = take(3 * sizeof(double));
+    L->off_stage = take(biggest * sizeof(double));
+    L->off_fbar = take(Q * sizeof(double));
+    L->total = off;
+    return true;
+}
+
+}  // namespace
+
+struct lb_batch {
+    int count = 0, device = 0;
+    double rho0 = 1.0, cs2 = SIGMA_S2_B;
+    Layout L;
+    char* ws = nullptr;
+    bool owns = false;
+    std::vector<RepRec> recs;              // host mirror, replica order
+    std::vector<uint64_t> seeds;
+    std::vector<long long> toff;
+    std::vector<int> mode;                 // noise mode per replica (LB_NOISE_*)
+    std::vector<bool> have_params;
+    double fbar[Q];
+    long long K = 0;                       // host mirror of the device step counter
+    int every = 0, nbins = 0;
+    long long nsamples = 0;
+    std::vector<std::vector<unsigned long long>> counts;   // per class
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // captured graph of `graph_steps` steps
+    cudaGraphExec_t graph = nullptr;
+    long long graph_steps = 0;
+    long long graph_kernels = 0;           // kernels one replay launches
+    cudaStream_t cap_stream = nullptr;
+    long long kernels = 0;
+    // the step launches: up to MAX_CLASSES classes each, for tile shape `tile`
+    int tile = 0;
+    std::vector<EnsParams> launches;
+    double autotune_ms = 0.0;              // per-step time of the chosen shape
+};
+
+static int bfail(lb_batch* b, int code, const std::string& m) {
+    if (b) b->err = m; else set_context_free_error(m);
+    return code;
+}
+
+#define BCK(b, call, where)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return bfail(b, LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static char* cls_ptr(lb_batch* b, size_t off) { return b->ws + off; }
+
+static int upload_rec(lb_batch* b, int r) {
+    const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
+    RepRec* d = reinterpret_cast<RepRec*>(cls_ptr(b, ci.off_recs)) + b->L.slot_of[r];
+    BCK(b, cudaMemcpyAsync(d, &b->recs[r], sizeof(RepRec), cudaMemcpyHostToDevice, b->stream), "H2D");
+    return LB_OK;
+}
+
+// Kernel parameters of the step launches for tile shape `tile`: classes in chunks of
+// MAX_CLASSES, the last launch of a step advancing the step counter.
+static int build_launches(lb_batch* b, int tile, std::vector<EnsParams>* out) {
+    out->clear();
+    const int TX = kBatchTiles[tile][0], TY = kBatchTiles[tile][1];
+    const int nc = (int)b->L.classes.size();
+    for (int c0 = 0; c0 < nc; c0 += MAX_CLASSES) {
+        EnsParams p;
+        std::memset(&p, 0, sizeof(p));
+        int tiles = 0;
+        for (int j = 0; j < MAX_CLASSES && c0 + j < nc; ++j) {
+            const ClassInfo& ci = b->L.classes[c0 + j];
+            for (int w = 0; w < 2; ++w)
+                if (!make_class_map(cls_ptr(b, ci.off_buf[w]), ci.g, ci.R, tile, &p.map[j][w]))
+                    return bfail(b, LB_ECUDA, "cuTensorMapEncodeTiled failed for a size class");
+            ClassDesc& d = p.cls[j];
+            d.g = ci.g;
+            d.buf[0] = reinterpret_cast<float*>(cls_ptr(b, ci.off_buf[0]));
+            d.buf[1] = reinterpret_cast<float*>(cls_ptr(b, ci.off_buf[1]));
+            d.recs = reinterpret_cast<const RepRec*>(cls_ptr(b, ci.off_recs));
+            d.ntx = (ci.nx + TX - 1) / TX;
+            d.per = d.ntx * ((ci.ny + TY - 1) / TY);
+            d.tile_begin = tiles;
+            d.rstride = (long long)Q * ci.g.plane;
+            const long long more = (long long)d.per * ci.R;
+            if (tiles + more > (1ll << 30)) return bfail(b, LB_EINVAL, "too many tiles in one launch");
+            tiles += (int)more;
+            p.nclass = j + 1;
+        }
+        p.ntiles = tiles;
+        p.kstep = reinterpret_cast<long long*>(cls_ptr(b, b->L.off_k));
+        p.done = reinterpret_cast<unsigned int*>(cls_ptr(b, b->L.off_done));
+        p.err = reinterpret_cast<int*>(cls_ptr(b, b->L.off_err));
+        p.advance = 0;
+        out->push_back(p);
+    }
+    if (!out->empty()) out->back().advance = 1;
+    return LB_OK;
+}
+
+static int batch_step_eager(lb_batch* b) {
+    for (const EnsParams& p : b->launches) {
+        BCK(b, launch_ensemble(b->tile, p, b->stream), "ensemble step");
+        b->kernels++;
+    }
+    return LB_OK;
+}
+
+static int col_strip_b(int nx, int ny) {
+    int c = 16;
+    while (c > 1 && (fft_threads(ny, c) > 1024 || fft_smem_bytes(ny, c) > 200 * 1024)) c >>= 1;
+    return c > nx ? nx : c;
+}
+
+static int batch_sample(lb_batch* b, cudaStream_t s) {
+    for (auto& ci : b->L.classes) {
+        float2* z1 = reinterpret_cast<float2*>(cls_ptr(b, ci.off_z1));
+        float2* z2 = reinterpret_cast<float2*>(cls_ptr(b, ci.off_z2));
+        dim3 grd((ci.nx + 127) / 128, ci.ny, ci.R);
+        batch_fields_kernel<<<grd, 128, 0, s>>>(reinterpret_cast<const float*>(cls_ptr(b, ci.off_buf[0])),
+                                                reinterpret_cast<const float*>(cls_ptr(b, ci.off_buf[1])),
+                                                reinterpret_cast<const long long*>(cls_ptr(b, b->L.off_k)),
+                                                (long long)Q * ci.g.plane, ci.g, z1, z2);
+        const float scale = (float)(1.0 / std::sqrt((double)ci.nx * ci.ny));
+        const float2* twx = reinterpret_cast<const float2*>(cls_ptr(b, ci.off_tw_x));
+        const float2* twy = reinterpret_cast<const float2*>(cls_ptr(b, ci.off_tw_y));
+        const size_t rsm = fft_smem_bytes(ci.nx, 1);
+        const int c = col_strip_b(ci.nx, ci.ny);
+        const size_t csm = fft_smem_bytes(ci.ny, c);
+        for (float2* z : {z1, z2}) {
+            batch_rows_kernel<<<ci.R * ci.ny, fft_threads(ci.nx, 1), rsm, s>>>(z, ci.nx, twx, 1.0f);
+            batch_cols_kernel<<<dim3(ci.nx / c, ci.R), fft_threads(ci.ny, c), csm, s>>>(z, ci.nx, ci.ny, c, twy, scale);
+        }
+        const size_t bsm = (size_t)3 * b->nbins * sizeof(double);
+        const int bx = std::max(1, std::min(64, (int)((size_t)ci.nx * ci.ny / 4096)));
+        batch_bin_kernel<<<dim3(bx, ci.R), 256, bsm, s>>>(z1, z2, reinterpret_cast<const unsigned short*>(cls_ptr(b, ci.off_bin16)),
+                                                          ci.nx, ci.ny, b->nbins, reinterpret_cast<double*>(cls_ptr(b, ci.off_bins)));
+        BCK(b, cudaGetLastError(), "spectra sample");
+        b->kernels += 6;
+    }
+    return LB_OK;
+}
+
+// one step (kernels, counter advance, optional sample) issued on stream s
+static int batch_one_step(lb_batch* b, cudaStream_t s) {
+    cudaStream_t keep = b->stream;
+    b->stream = s;
+    int r = batch_step_eager(b);
+    if (r == LB_OK) {
+        b->K++;
+        if (b->every > 0 && b->K % b->every == 0) {
+            r = batch_sample(b, s);
+            b->nsamples++;
+        }
+    }
+    b->stream = keep;
+    return r;
+}
+
+extern "C" {
+
+size_t lb_batch_workspace_bytes(int count, const int* nx, const int* ny) {
+    if (count < 1 || !nx || !ny) return 0;
+    Layout L;
+    if (!plan(count, nx, ny, &L)) return 0;
+    return L.total;
+}
+
+int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* seeds, double rho0, double cs2,
+                    void* workspace, size_t workspace_bytes, lb_batch** out) {
+    if (!out || count < 1 || !nx || !ny || !seeds) return bfail(nullptr, LB_EINVAL, "invalid arguments");
+    *out = nullptr;
+    if (!(rho0 > 0.0) || !(cs2 > 0.0)) return bfail(nullptr, LB_EINVAL, "rho0 and cs2 must be positive");
+    lb_batch* b = new lb_batch();
+    if (!plan(count, nx, ny, &b->L)) {
+        delete b;
+        return bfail(nullptr, LB_EINVAL, "every lattice side must lie in [2, 8192]");
+    }
+    b->count = count;
+    b->rho0 = rho0;
+    b->cs2 = cs2;
+    cudaGetDevice(&b->device);
+    if (workspace) {
+        if (workspace_bytes < b->L.total || ((uintptr_t)workspace & 255)) {
+            delete b;
+            return bfail(nullptr, LB_ENOMEM, "workspace smaller than lb_batch_workspace_bytes() or misaligned");
+        }
+        b->ws = (char*)workspace;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&b->ws, b->L.total);
+        if (e != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, LB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        b->owns = true;
+    }
+    rest_populations(rho0, cs2, b->fbar);
+    b->seeds.assign(seeds, seeds + count);
+    b->recs.assign(count, RepRec{});
+    b->toff.assign(count, 0);
+    b->mode.assign(count, LB_NOISE_OFF);
+    b->have_params.assign(count, false);
+    for (int r = 0; r < count; ++r) {
+        RepRec& rc = b->recs[r];
+        rc.rho0 = (float)rho0;
+        rc.cs2m = (float)(cs2 - SIGMA_S2_B);
+        rc.lb = rc.ls = rc.lq = rc.le = -1.0f;
+        rc.k0 = (uint32_t)(seeds[r] & 0xffffffffu);
+        rc.k1 = (uint32_t)(seeds[r] >> 32);
+    }
+    cudaError_t e = cudaMemset(b->ws, 0, b->L.total);
+    std::vector<float2> tw;
+    for (auto& ci : b->L.classes) {
+        if (e != cudaSuccess) break;
+        for (int which = 0; which < 2; ++which) {
+            const int n = which == 0 ? ci.nx : ci.ny;
+            tw.resize(n);
+            for (int k = 0; k < n; ++k) {
+                const double a = 2.0 * M_PI * (double)k / n;
+                tw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+            }
+            e = cudaMemcpy(cls_ptr(b, which == 0 ? ci.off_tw_x : ci.off_tw_y), tw.data(), n * sizeof(float2),
+                           cudaMemcpyHostToDevice);
+        }
+    }
+    for (int r = 0; r < count && e == cudaSuccess; ++r) {
+        const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
+        e = cudaMemcpy(reinterpret_cast<RepRec*>(cls_ptr(b, ci.off_recs)) + b->L.slot_of[r], &b->recs[r],
+                       sizeof(RepRec), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(cls_ptr(b, b->L.off_fbar), b->fbar, sizeof(double) * Q, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = prepare_ensemble_kernels();
+    if (e == cudaSuccess && build_launches(b, 0, &b->launches) != LB_OK) e = cudaErrorInvalidValue;
+    if (e != cudaSuccess) {
+        if (b->owns) cudaFree(b->ws);
+        delete b;
+        return bfail(nullptr, LB_ECUDA, std::string("lb_batch_create: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return LB_OK;
+}
+
+int lb_batch_destroy(lb_batch* b) {
+    if (!b) return LB_EINVAL;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->owns) cudaFree(b->ws);
+    delete b;
+    return LB_OK;
+}
+
+int lb_batch_set_stream(lb_batch* b, void* stream) {
+    if (!b) return LB_EINVAL;
+    b->stream = (cudaStream_t)stream;
+    return LB_OK;
+}
+
+int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, double tau_s, double tau_b,
+                        double tau_ghost, int noise_mode) {
+    if (!b || replica < -1 || replica >= b->count) return LB_EINVAL;
+    if (noise_mode == LB_NOISE_FULL)
+        return bfail(b, LB_EINVAL, "correlated noise is not available for batched replicas");
+    const int lo = replica < 0 ? 0 : replica, hi = replica < 0 ? b->count : replica + 1;
+    for (int r = lo; r < hi; ++r) {
+        const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
+        int rc = lb_check_params(ci.nx, ci.ny, b->rho0, b->cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode);
+        if (rc != LB_OK) return bfail(b, rc, "parameters rejected (see lb_check_params)");
+        double xi[81];
+        lb_noise_matrix(b->rho0, b->cs2, kT, kappa, tau_s, tau_b, tau_ghost, 0.0, 0.0, xi);
+        const double x44 = xi[3 * 9 + 3], x49 = noise_mode == LB_NOISE_DIAG ? 0.0 : xi[3 * 9 + 8], x99 = xi[8 * 9 + 8];
+        const double L44 = std::sqrt(std::fmax(x44, 0.0));
+        const double L94 = L44 > 0.0 ? x49 / L44 : 0.0;
+        const double L99 = std::sqrt(std::fmax(x99 - L94 * L94, 0.0));
+        RepRec& rec = b->recs[r];
+        rec.kappa = (float)kappa;
+        rec.lb = (float)(-1.0 / tau_b);
+        rec.ls = (float)(-1.0 / tau_s);
+        rec.lq = rec.le = (float)(-1.0 / tau_ghost);
+        rec.L44 = (float)L44; rec.L94 = (float)L94; rec.L99 = (float)L99;
+        rec.s5 = (float)std::sqrt(std::fmax(xi[4 * 9 + 4], 0.0));
+        rec.s6 = (float)std::sqrt(std::fmax(xi[5 * 9 + 5], 0.0));
+        rec.s7 = (float)std::sqrt(std::fmax(xi[6 * 9 + 6], 0.0));
+        rec.mode = (noise_mode != LB_NOISE_OFF && kT > 0.0) ? 1 : 0;
+        b->mode[r] = noise_mode;
+        b->have_params[r] = true;
+        int u = upload_rec(b, r);
+        if (u != LB_OK) return u;
+    }
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_batch_autotune(lb_batch* b, int steps) {
+    if (!b || steps < 1) return LB_EINVAL;
+    for (int r = 0; r < b->count; ++r)
+        if (!b->have_params[r]) return bfail(b, LB_ESTATE, "lb_batch_set_params must be called for every replica");
+    // times each tile shape on the whole ensemble (launches that leave the step counter
+    // alone), keeps the fastest, then puts every replica back at rest at K = 0
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+    } ev;
+    BCK(b, cudaEventCreate(&ev.a), "event");
+    BCK(b, cudaEventCreate(&ev.b), "event");
+    float best = 1e30f;
+    int best_tile = 0;
+    std::vector<EnsParams> cand;
+    for (int t = 0; t < kBatchTileCount; ++t) {
+        int rc = build_launches(b, t, &cand);
+        if (rc != LB_OK) return rc;
+        for (auto& p : cand) p.advance = 0;
+        for (const auto& p : cand) BCK(b, launch_ensemble(t, p, b->stream), "autotune");   // warm-up
+        BCK(b, cudaEventRecord(ev.a, b->stream), "event");
+        for (int k = 0; k < steps; ++k)
+            for (const auto& p : cand) BCK(b, launch_ensemble(t, p, b->stream), "autotune");
+        BCK(b, cudaEventRecord(ev.b, b->stream), "event");
+        BCK(b, cudaEventSynchronize(ev.b), "event");
+        b->kernels += (long long)(steps + 1) * (long long)cand.size();
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, ev.a, ev.b), "event");
+        if (ms < best) { best = ms; best_tile = t; }
+    }
+    b->tile = best_tile;
+    int rc = build_launches(b, best_tile, &b->launches);
+    if (rc != LB_OK) return rc;
+    b->autotune_ms = best / steps;
+    for (auto& ci : b->L.classes) {
+        BCK(b, cudaMemsetAsync(cls_ptr(b, ci.off_buf[0]), 0, (size_t)Q * ci.g.plane * 4 * ci.R, b->stream), "memset");
+        BCK(b, cudaMemsetAsync(cls_ptr(b, ci.off_buf[1]), 0, (size_t)Q * ci.g.plane * 4 * ci.R, b->stream), "memset");
+    }
+    BCK(b, cudaMemsetAsync(cls_ptr(b, b->L.off_k), 0, sizeof(long long), b->stream), "memset");
+    b->K = 0;
+    for (int r = 0; r < b->count; ++r) {
+        b->toff[r] = 0;
+        b->recs[r].toff = 0;
+        int u = upload_rec(b, r);
+        if (u != LB_OK) return u;
+    }
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_batch_step(lb_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return LB_EINVAL;
+    for (int r = 0; r < b->count; ++r)
+        if (!b->have_params[r]) return bfail(b, LB_ESTATE, "lb_batch_set_params must be called for every replica");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int r = batch_one_step(b, b->stream);
+        if (r != LB_OK) return r;
+    }
+    return LB_OK;
+}
+
+int lb_batch_step_graph(lb_batch* b, int64_t nsteps, int64_t steps_per_graph) {
+    if (!b || nsteps < 0 || steps_per_graph < 1) return LB_EINVAL;
+    for (int r = 0; r < b->count; ++r)
+        if (!b->have_params[r]) return bfail(b, LB_ESTATE, "lb_batch_set_params must be called for every replica");
+    const long long G = steps_per_graph;
+    if (b->every > 0 && G % b->every != 0) return bfail(b, LB_EINVAL, "steps_per_graph must be a multiple of every");
+    // eager steps until the graph's samples fall on multiples of `every`
+    while (nsteps > 0 && b->every > 0 && b->K % b->every != 0) {
+        int r = batch_one_step(b, b->stream);
+        if (r != LB_OK) return r;
+        --nsteps;
+    }
+    if (nsteps >= G && (!b->graph || b->graph_steps != G)) {
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+        if (!b->cap_stream) BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
+        const long long K0 = b->K, n0 = b->nsamples, k0 = b->kernels;
+        BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+        int rc = LB_OK;
+        for (long long k = 0; k < G && rc == LB_OK; ++k) rc = batch_one_step(b, b->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+        b->K = K0; b->nsamples = n0;               // capture issued nothing; the replays will
+        const long long per_graph = b->kernels - k0;
+        b->kernels = k0;
+        if (rc != LB_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return bfail(b, LB_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bfail(b, LB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        b->graph_steps = G;
+        b->graph_kernels = per_graph;
+    }
+    while (nsteps >= G && b->graph) {
+        BCK(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
+        b->K += G;
+        if (b->every > 0) b->nsamples += G / b->every;
+        b->kernels += b->graph_kernels;
+        nsteps -= G;
+    }
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int r = batch_one_step(b, b->stream);
+        if (r != LB_OK) return r;
+    }
+    return LB_OK;
+}
+
+int lb_batch_get_time(lb_batch* b, int replica, int64_t* t) {
+    if (!b || !t || replica < 0 || replica >= b->count) return LB_EINVAL;
+    *t = b->K + b->toff[replica];
+    return LB_OK;
+}
+
+static void* rep_pops(lb_batch* b, int r, int which) {
+    const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
+    return cls_ptr(b, ci.off_buf[which]) + (size_t)b->L.slot_of[r] * Q * ci.g.plane * sizeof(float);
+}
+
+int lb_batch_set_populations(lb_batch* b, int replica, const double* f, int loc, int64_t t) {
+    if (!b || !f || replica < 0 || replica >= b->count || (loc != LB_HOST && loc != LB_DEVICE) || t < 0)
+        return LB_EINVAL;
+    const ClassInfo& ci = b->L.classes[b->L.cls_of[replica]];
+    const long long n = (long long)ci.nx * ci.ny;
+    double* stage = reinterpret_cast<double*>(cls_ptr(b, b->L.off_stage));
+    void* pops = rep_pops(b, replica, (int)(b->K & 1));
+    for (int i = 0; i < Q; ++i) {
+        const double* src = f + i * n;
+        if (loc == LB_HOST) {
+            BCK(b, cudaMemcpyAsync(stage, src, sizeof(double) * n, cudaMemcpyHostToDevice, b->stream), "H2D");
+            src = stage;
+        }
+        BCK(b, launch_set_plane(src, pops, 0, ci.g, i, b->fbar[i], b->stream), "set populations");
+        b->kernels++;
+    }
+    b->toff[replica] = t - b->K;
+    b->recs[replica].toff = b->toff[replica];
+    int u = upload_rec(b, replica);
+    if (u != LB_OK) return u;
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_batch_get_populations(lb_batch* b, int replica, double* f, int loc) {
+    if (!b || !f || replica < 0 || replica >= b->count || (loc != LB_HOST && loc != LB_DEVICE)) return LB_EINVAL;
+    const ClassInfo& ci = b->L.classes[b->L.cls_of[replica]];
+    const long long n = (long long)ci.nx * ci.ny;
+    double* stage = reinterpret_cast<double*>(cls_ptr(b, b->L.off_stage));
+    const void* pops = rep_pops(b, replica, (int)(b->K & 1));
+    for (int i = 0; i < Q; ++i) {
+        double* dst = loc == LB_HOST ? stage : f + i * n;
+        BCK(b, launch_get_plane(pops, 0, ci.g, i, b->fbar[i], dst, b->stream), "get populations");
+        b->kernels++;
+        if (loc == LB_HOST)
+            BCK(b, cudaMemcpyAsync(f + i * n, stage, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream), "D2H");
+    }
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    int h = 0;
+    BCK(b, cudaMemcpy(&h, cls_ptr(b, b->L.off_err), sizeof(int), cudaMemcpyDeviceToHost), "D2H");
+    if (h) return bfail(b, LB_ETIMEOUT, "a batched step kernel gave up waiting for its TMA loads");
+    return LB_OK;
+}
+
+int lb_batch_sums(lb_batch* b, int replica, double sums[3]) {
+    if (!b || !sums || replica < 0 || replica >= b->count) return LB_EINVAL;
+    const ClassInfo& ci = b->L.classes[b->L.cls_of[replica]];
+    double* partial = reinterpret_cast<double*>(cls_ptr(b, b->L.off_partial));
+    double* s3 = reinterpret_cast<double*>(cls_ptr(b, b->L.off_sums));
+    BCK(b, launch_sums(rep_pops(b, replica, (int)(b->K & 1)), 0, ci.g,
+                       reinterpret_cast<const double*>(cls_ptr(b, b->L.off_fbar)), partial, s3, b->stream), "sums");
+    b->kernels += 2;
+    BCK(b, cudaMemcpyAsync(sums, s3, 3 * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "D2H");
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_batch_set_sampling(lb_batch* b, int every, int nbins) {
+    if (!b || every < 0) return LB_EINVAL;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
+    if (every == 0) { b->every = 0; return LB_OK; }
+    if (nbins < 1 || nbins > kMaxBatchBins) return bfail(b, LB_EINVAL, "nbins must lie in [1, 1024]");
+    size_t rsm = 0, csm = 0;
+    for (auto& ci : b->L.classes) {
+        if (!pow2b(ci.nx) || !pow2b(ci.ny)) return bfail(b, LB_EINVAL, "spectra need power-of-two lattice sides");
+        rsm = std::max(rsm, fft_smem_bytes(ci.nx, 1));
+        csm = std::max(csm, fft_smem_bytes(ci.ny, col_strip_b(ci.nx, ci.ny)));
+    }
+    // shared memory of the sample kernels, set here so that a graph capture makes no such call
+    BCK(b, cudaFuncSetAttribute(batch_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm), "attr");
+    BCK(b, cudaFuncSetAttribute(batch_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm), "attr");
+    BCK(b, cudaFuncSetAttribute(batch_bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(3 * nbins * sizeof(double))), "attr");
+    b->every = every;
+    b->nbins = nbins;
+    b->nsamples = 0;
+    b->counts.assign(b->L.classes.size(), std::vector<unsigned long long>(nbins, 0));
+    for (size_t c = 0; c < b->L.classes.size(); ++c) {
+        ClassInfo& ci = b->L.classes[c];
+        BCK(b, cudaMemsetAsync(cls_ptr(b, ci.off_bins), 0, (size_t)ci.R * 3 * kMaxBatchBins * sizeof(double),
+                               b->stream), "memset");
+        BCK(b, launch_bin_counts(ci.nx, ci.ny, nbins, reinterpret_cast<unsigned short*>(cls_ptr(b, ci.off_bin16)),
+                                 reinterpret_cast<unsigned long long*>(cls_ptr(b, ci.off_counts)), b->stream), "bins");
+        BCK(b, cudaMemcpyAsync(b->counts[c].data(), cls_ptr(b, ci.off_counts), nbins * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, b->stream), "D2H");
+    }
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_batch_structure_factor(lb_batch* b, int replica, int nbins, double* S_rho, double* S_jl, double* S_jt,
+                              int64_t* counts, int64_t* nsamples) {
+    if (!b || replica < 0 || replica >= b->count) return LB_EINVAL;
+    if (nbins != b->nbins || b->nbins == 0) return bfail(b, LB_EINVAL, "nbins differs from lb_batch_set_sampling");
+    const int c = b->L.cls_of[replica];
+    const ClassInfo& ci = b->L.classes[c];
+    std::vector<double> h(3 * (size_t)nbins);
+    const double* src = reinterpret_cast<const double*>(cls_ptr(b, ci.off_bins)) + (size_t)b->L.slot_of[replica] * 3 * nbins;
+    BCK(b, cudaMemcpyAsync(h.data(), src, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "D2H");
+    BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
+    for (int k = 0; k < nbins; ++k) {
+        const double den = (double)b->counts[c][k] * (double)b->nsamples;
+        if (S_rho) S_rho[k] = den > 0 ? h[k] / den : 0.0;
+        if (S_jl) S_jl[k] = den > 0 ? h[nbins + k] / den : 0.0;
+        if (S_jt) S_jt[k] = den > 0 ? h[2 * nbins + k] / den : 0.0;
+        if (counts) counts[k] = (int64_t)b->counts[c][k];
+    }
+    if (nsamples) *nsamples = b->nsamples;
+    return LB_OK;
+}
+
+int lb_batch_launch_count(lb_batch* b, int64_t* n) {
+    if (!b || !n) return LB_EINVAL;
+    *n = b->kernels;
+    return LB_OK;
+}
+
+int lb_batch_tuning(lb_batch* b, int* tile_x, int* tile_y, int* threads, double* ms_per_step) {
+    if (!b) return LB_EINVAL;
+    if (tile_x) *tile_x = kBatchTiles[b->tile][0];
+    if (tile_y) *tile_y = kBatchTiles[b->tile][1];
+    if (threads) *threads = kBatchTiles[b->tile][2];
+    if (ms_per_step) *ms_per_step = b->autotune_ms;
+    return LB_OK;
+}
+
+const char* lb_batch_last_error(lb_batch* b) { return b ? b->err.c_str() : lb_last_error(nullptr); }
+
+}  // extern "C"

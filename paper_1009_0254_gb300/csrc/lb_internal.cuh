@@ -232,4 +232,6 @@ cudaError_t launch_sums(const void* pops, int fp16, const Grid& g, const double*
                         double* out3, cudaStream_t s);
 int sums_partial_count();
 void set_context_free_error(const std::string& msg);
+// rest populations fbar_i of a lattice at density rho0 with p0 = cs2 rho (Table II at u = 0)
+void rest_populations(double rho0, double cs2, double fbar[Q]);
 }  // namespace lbf

@@ -268,6 +268,78 @@ int lb_batch_tuning(lb_batch* b, int* tile_x, int* tile_y, int* threads, double*
 const char* lb_batch_last_error(lb_batch* b);
 
 /*
+ * Request server: continuous batching of independent simulations.
+ * Each request is one periodic lattice of the model of [GACV] Sec. III started at rest
+ * (uniform density rho0, zero velocity) at time 0, with uncorrelated noise of Sec. IV
+ * (LB_NOISE_OFF, LB_NOISE_LW or LB_NOISE_DIAG) keyed by its own seed, FP32 storage,
+ * advanced by `steps` time steps.  Its trajectory is exactly the one lb_batch_* (and, up
+ * to FP32 rounding order, lb_step) gives the same lattice, whatever else is served with it.
+ *
+ * lb_server_request_bytes: device bytes one request of that size holds while admitted
+ *   (both population buffers); 0 for an invalid size (sides in [2, 16384]).
+ * lb_server_create: starts a scheduler thread on the current device.  hbm_budget_bytes
+ *   bounds the sum of lb_server_request_bytes over admitted requests (their memory comes
+ *   from a stream-ordered pool that keeps up to the budget cached); max_active bounds the
+ *   number admitted at once (device tables are sized for it); max_chunk_steps bounds the
+ *   steps issued between two admission decisions.  Requests are admitted in arrival order;
+ *   one that does not fit the remaining budget lets later, smaller ones pass.
+ * lb_server_submit: queues a request (thread-safe) and returns its id (> 0).  Validation
+ *   happens here: LB_EINVAL for bad sizes/steps/parameters or LB_NOISE_FULL, LB_ENOTPSD
+ *   as lb_check_params, LB_ENOMEM if the request alone exceeds the budget.
+ * lb_server_poll: moves up to max_results completed results (oldest first) into out.
+ * lb_server_wait: blocks until request `id` has completed (id <= 0: until every request
+ *   submitted so far has) or timeout_s seconds have passed (LB_ETIMEOUT; < 0: no limit).
+ * lb_server_fetch_populations: for a completed request submitted with keep_state = 1,
+ *   copies its final FP64 populations (9*nx*ny doubles, layout as lb_get_populations) to
+ *   host memory f and releases its device memory.  Until then that memory stays counted
+ *   against the budget.  LB_EINVAL if the request is unknown, not finished or not kept.
+ * lb_server_get_stats: counters since creation (times in seconds since lb_server_create).
+ * lb_server_destroy: drops queued requests, finishes the admitted ones, frees everything.
+ * lb_server_last_error: message of the last failure of s (NULL s: of the last failed
+ *   lb_server_create or lb_server_submit validation).
+ * Results carry the FP64 conserved sums (rho, jx, jy) of the final state and the host
+ * times of submission, admission and completion (completion = when the host saw the GPU
+ * finish the chunk holding the request's last step).
+ */
+typedef struct lb_request {
+    int nx, ny;
+    int64_t steps;
+    double rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost;
+    int noise_mode;
+    int keep_state;
+    uint64_t seed;
+} lb_request;
+
+typedef struct lb_result {
+    int64_t id;
+    int status;           /* LB_OK, or LB_ETIMEOUT if a kernel gave up a bounded wait */
+    int nx, ny;
+    int state_kept;
+    int64_t steps;
+    double sums[3];
+    double t_submit, t_admit, t_complete;
+} lb_result;
+
+typedef struct lb_server_stats {
+    int64_t submitted, completed, queued, steps_issued;
+    size_t bytes_in_use, bytes_peak, bytes_budget;
+    double node_updates;  /* lattice node updates issued */
+    double gpu_busy_s;    /* sum of the chunks' device durations */
+    double t_first_admit, t_last_complete;
+} lb_server_stats;
+
+typedef struct lb_server lb_server;
+size_t lb_server_request_bytes(int nx, int ny);
+int lb_server_create(size_t hbm_budget_bytes, int max_active, int max_chunk_steps, lb_server** out);
+int lb_server_submit(lb_server* s, const lb_request* r, int64_t* id);
+int lb_server_poll(lb_server* s, lb_result* out, int max_results, int* n);
+int lb_server_wait(lb_server* s, int64_t id, double timeout_s, lb_result* out);
+int lb_server_fetch_populations(lb_server* s, int64_t id, double* f);
+int lb_server_get_stats(lb_server* s, lb_server_stats* st);
+int lb_server_destroy(lb_server* s);
+const char* lb_server_last_error(lb_server* s);
+
+/*
  * Host-only helpers (no GPU needed).
  * lb_noise_matrix: the 9x9 noise covariance Xi(k) of [GACV] Eq. (noise-yeo) for the
  * given parameters at wavevector (kx, ky), with k^2 the lattice symbol of Appendix B;

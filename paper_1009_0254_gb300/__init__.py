@@ -27,6 +27,28 @@ LB_WARN_LOW_MACH = 1
 _lib = None
 
 
+class lb_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("steps", ctypes.c_int64),
+                ("rho0", ctypes.c_double), ("cs2", ctypes.c_double), ("kT", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("tau_s", ctypes.c_double), ("tau_b", ctypes.c_double),
+                ("tau_ghost", ctypes.c_double), ("noise_mode", ctypes.c_int), ("keep_state", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class lb_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("state_kept", ctypes.c_int), ("steps", ctypes.c_int64), ("sums", ctypes.c_double * 3),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_complete", ctypes.c_double)]
+
+
+class lb_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("steps_issued", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
+                ("bytes_peak", ctypes.c_size_t), ("bytes_budget", ctypes.c_size_t),
+                ("node_updates", ctypes.c_double), ("gpu_busy_s", ctypes.c_double),
+                ("t_first_admit", ctypes.c_double), ("t_last_complete", ctypes.c_double)]
+
+
 class LBError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("lbfluct error %d: %s" % (code, msg))
@@ -83,6 +105,15 @@ def load(path: str = LIB_PATH):
         "lb_batch_launch_count": (c_int, [vp, i64p]),
         "lb_batch_tuning": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int), dp]),
         "lb_batch_last_error": (ctypes.c_char_p, [vp]),
+        "lb_server_request_bytes": (c_sz, [c_int, c_int]),
+        "lb_server_create": (c_int, [c_sz, c_int, c_int, ctypes.POINTER(vp)]),
+        "lb_server_submit": (c_int, [vp, ctypes.POINTER(lb_request), i64p]),
+        "lb_server_poll": (c_int, [vp, ctypes.POINTER(lb_result), c_int, ctypes.POINTER(c_int)]),
+        "lb_server_wait": (c_int, [vp, c_i64, c_dbl, ctypes.POINTER(lb_result)]),
+        "lb_server_fetch_populations": (c_int, [vp, c_i64, vp]),
+        "lb_server_get_stats": (c_int, [vp, ctypes.POINTER(lb_server_stats)]),
+        "lb_server_destroy": (c_int, [vp]),
+        "lb_server_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in proto.items():
         fn = getattr(L, name)
@@ -320,6 +351,63 @@ def lb_batch_last_error(b=None):
     return m.decode() if m else ""
 
 
+# --- request server --------------------------------------------------------------------------
+
+def _scheck(rc, srv=None):
+    if rc < 0:
+        msg = load().lb_server_last_error(srv)
+        raise LBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def lb_server_request_bytes(nx, ny):
+    return load().lb_server_request_bytes(nx, ny)
+
+
+def lb_server_create(hbm_budget_bytes, max_active=4096, max_chunk_steps=500):
+    out = ctypes.c_void_p()
+    _scheck(load().lb_server_create(int(hbm_budget_bytes), max_active, max_chunk_steps, ctypes.byref(out)))
+    return out.value
+
+
+def lb_server_submit(srv, req):
+    i = ctypes.c_int64()
+    _scheck(load().lb_server_submit(srv, ctypes.byref(req), ctypes.byref(i)), None)
+    return i.value
+
+
+def lb_server_poll(srv, max_results=1024):
+    buf = (lb_result * max_results)()
+    n = ctypes.c_int()
+    _scheck(load().lb_server_poll(srv, buf, max_results, ctypes.byref(n)), srv)
+    return [buf[i] for i in range(n.value)]
+
+
+def lb_server_wait(srv, id=0, timeout_s=-1.0):
+    res = lb_result()
+    _scheck(load().lb_server_wait(srv, id, timeout_s, ctypes.byref(res)), srv)
+    return res if id > 0 else None
+
+
+def lb_server_fetch_populations(srv, id, f):
+    return _scheck(load().lb_server_fetch_populations(srv, id, _ptr(f)), srv)
+
+
+def lb_server_get_stats(srv):
+    st = lb_server_stats()
+    _scheck(load().lb_server_get_stats(srv, ctypes.byref(st)), srv)
+    return st
+
+
+def lb_server_destroy(srv):
+    return _scheck(load().lb_server_destroy(srv))
+
+
+def lb_server_last_error(srv=None):
+    m = load().lb_server_last_error(srv)
+    return m.decode() if m else ""
+
+
 # --- convenience wrappers ------------------------------------------------------------------
 
 class Lattice:
@@ -471,3 +559,42 @@ class Ensemble:
         ns = np.zeros(1, dtype=np.int64)
         lb_batch_structure_factor(self.b, replica, nb, S, L, Tt, cnt, ns)
         return S, L, Tt, cnt, int(ns[0])
+
+
+class Server:
+    """The request server on the current CUDA device (see lb_server_* in lbfluct.h)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=4096, max_chunk_steps=500):
+        self.srv = lb_server_create(hbm_budget_bytes, max_active, max_chunk_steps)
+
+    def submit(self, nx, ny, steps, kT=1e-4, kappa=0.01, tau_s=1.0, tau_b=1.0, tau_ghost=1.0,
+               noise_mode=LB_NOISE_LW, seed=42, rho0=1.0, cs2=1.0 / 3.0, keep_state=False):
+        r = lb_request(nx=int(nx), ny=int(ny), steps=int(steps), rho0=rho0, cs2=cs2, kT=kT, kappa=kappa,
+                       tau_s=tau_s, tau_b=tau_b, tau_ghost=tau_ghost, noise_mode=noise_mode,
+                       keep_state=int(bool(keep_state)), seed=int(seed))
+        return lb_server_submit(self.srv, r)
+
+    def wait(self, id=0, timeout_s=-1.0):
+        return lb_server_wait(self.srv, id, timeout_s)
+
+    def poll(self, max_results=1024):
+        return lb_server_poll(self.srv, max_results)
+
+    def fetch(self, id, nx, ny):
+        f = np.empty((9, ny, nx))
+        lb_server_fetch_populations(self.srv, id, f)
+        return f
+
+    def stats(self):
+        return lb_server_get_stats(self.srv)
+
+    def close(self):
+        if getattr(self, "srv", None):
+            lb_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,32 +20,13 @@
 #include <string>
 #include <vector>
 
-#include "lb_collide.cuh"
+#include "lb_ens.cuh"
 #include "lb_fft_core.cuh"
-#include "lb_internal.cuh"
-#include "lb_tma.cuh"
 #include "lbfluct.h"
 
 namespace lbf {
 
 constexpr int MAX_CLASSES = 8;      // size classes per launch (kernel parameters stay < 4 KB)
-
-// Per-replica record (device).
-struct RepRec {
-    float rho0, cs2m, kappa, lb, ls, lq, le;
-    float L44, L94, L99, s5, s6, s7;
-    int mode;                 // 0 no noise, 1 uncorrelated noise
-    uint32_t k0, k1;          // Philox key = the replica's seed
-    long long toff;           // time = K + toff
-};
-
-// What collide_node needs for one tile of one replica, in registers.
-struct TileArgs {
-    float rho0, cs2m, kappa, lb, ls, lq, le;
-    float L44, L94, L99, s5, s6, s7;
-    uint32_t t_lo, t_hi;
-    KeyPair rk;
-};
 
 struct ClassDesc {
     Grid g;
@@ -65,35 +46,6 @@ struct EnsParams {
     int* err;                          // set when a bounded wait gives up
     int advance;                       // this launch advances K when its last CTA finishes
 };
-
-// Collide and stream the TX x TY nodes of one tile from the staged populations S and the
-// density tile R (with its one-node ring).
-template <int MODE, int TX, int TY, int NT>
-__device__ __forceinline__ void tile_nodes(const TileArgs& a, const float* S, const float* R, const Grid& g, int x0,
-                                           int y0, float* dst) {
-    using TT = TmaTile<TX, TY, float>;
-    static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
-#pragma unroll
-    for (int it = 0; it < TX * TY / NT; ++it) {
-        const int q = threadIdx.x + it * NT;
-        const int ly = q / TX, lx = q - ly * TX;
-        const int x = x0 + lx, y = y0 + ly;
-        if (x >= g.nx || y >= g.ny) continue;
-        float f[Q];
-        load9_ps<TT::PS>(S, (ly + 1) * TT::BW + lx + TT::XO, f);
-        const int rc = (ly + 1) * TT::RW + lx + 1;
-        Nbr r;
-        r.C = R[rc];
-        r.E = R[rc + 1]; r.W = R[rc - 1];
-        r.N = R[rc + TT::RW]; r.S = R[rc - TT::RW];
-        r.NE = R[rc + TT::RW + 1]; r.NW = R[rc + TT::RW - 1];
-        r.SE = R[rc - TT::RW + 1]; r.SW = R[rc - TT::RW - 1];
-        const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
-        float o[Q];
-        collide_node<MODE>(a, f, r, node, make_float2(0.f, 0.f), o);
-        store9(dst, g.plane, g, x, y, o);
-    }
-}
 
 // class, replica and origin of a tile of the launch
 struct TilePos {
@@ -188,16 +140,8 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
 
         // the replica's record (the same address for every thread of the CTA)
         const RepRec* rp = d.recs + tp.rep;
-        TileArgs a;
-        a.rho0 = __ldg(&rp->rho0); a.cs2m = __ldg(&rp->cs2m); a.kappa = __ldg(&rp->kappa);
-        a.lb = __ldg(&rp->lb); a.ls = __ldg(&rp->ls); a.lq = __ldg(&rp->lq); a.le = __ldg(&rp->le);
-        a.L44 = __ldg(&rp->L44); a.L94 = __ldg(&rp->L94); a.L99 = __ldg(&rp->L99);
-        a.s5 = __ldg(&rp->s5); a.s6 = __ldg(&rp->s6); a.s7 = __ldg(&rp->s7);
-        a.rk.k0 = __ldg(&rp->k0); a.rk.k1 = __ldg(&rp->k1);
-        const long long t = K + __ldg(&rp->toff);
-        a.t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);
-        a.t_hi = (uint32_t)((unsigned long long)t >> 32);
-        const int mode = __ldg(&rp->mode);
+        int mode;
+        const TileArgs a = load_tile_args(rp, K + __ldg(&rp->toff), &mode);
         float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
 
         if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst);
@@ -401,6 +345,28 @@ static cudaError_t prepare_ensemble_kernels() {
     if ((e = ensemble_grid<64, 8, 256>(&g)) != cudaSuccess) return e;
     if ((e = ensemble_grid<64, 16, 512>(&g)) != cudaSuccess) return e;
     return ensemble_grid<32, 32, 512>(&g);
+}
+
+// Relaxation rates, Cholesky factors of Xi(0) (Sec. IV; the (4,9) block coupled unless
+// noise_mode is LB_NOISE_DIAG) and noise switch of one lattice's record; the key, time
+// offset and rho0/cs2 fields are left to the caller.
+void fill_rep_record(double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
+                     double tau_ghost, int noise_mode, RepRec* rec) {
+    double xi[81];
+    lb_noise_matrix(rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, 0.0, 0.0, xi);
+    const double x44 = xi[3 * 9 + 3], x49 = noise_mode == LB_NOISE_DIAG ? 0.0 : xi[3 * 9 + 8], x99 = xi[8 * 9 + 8];
+    const double L44 = std::sqrt(std::fmax(x44, 0.0));
+    const double L94 = L44 > 0.0 ? x49 / L44 : 0.0;
+    const double L99 = std::sqrt(std::fmax(x99 - L94 * L94, 0.0));
+    rec->kappa = (float)kappa;
+    rec->lb = (float)(-1.0 / tau_b);
+    rec->ls = (float)(-1.0 / tau_s);
+    rec->lq = rec->le = (float)(-1.0 / tau_ghost);
+    rec->L44 = (float)L44; rec->L94 = (float)L94; rec->L99 = (float)L99;
+    rec->s5 = (float)std::sqrt(std::fmax(xi[4 * 9 + 4], 0.0));
+    rec->s6 = (float)std::sqrt(std::fmax(xi[5 * 9 + 5], 0.0));
+    rec->s7 = (float)std::sqrt(std::fmax(xi[6 * 9 + 6], 0.0));
+    rec->mode = (noise_mode != LB_NOISE_OFF && kT > 0.0) ? 1 : 0;
 }
 
 }  // namespace lbf
@@ -749,22 +715,7 @@ int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, doubl
         const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
         int rc = lb_check_params(ci.nx, ci.ny, b->rho0, b->cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode);
         if (rc != LB_OK) return bfail(b, rc, "parameters rejected (see lb_check_params)");
-        double xi[81];
-        lb_noise_matrix(b->rho0, b->cs2, kT, kappa, tau_s, tau_b, tau_ghost, 0.0, 0.0, xi);
-        const double x44 = xi[3 * 9 + 3], x49 = noise_mode == LB_NOISE_DIAG ? 0.0 : xi[3 * 9 + 8], x99 = xi[8 * 9 + 8];
-        const double L44 = std::sqrt(std::fmax(x44, 0.0));
-        const double L94 = L44 > 0.0 ? x49 / L44 : 0.0;
-        const double L99 = std::sqrt(std::fmax(x99 - L94 * L94, 0.0));
-        RepRec& rec = b->recs[r];
-        rec.kappa = (float)kappa;
-        rec.lb = (float)(-1.0 / tau_b);
-        rec.ls = (float)(-1.0 / tau_s);
-        rec.lq = rec.le = (float)(-1.0 / tau_ghost);
-        rec.L44 = (float)L44; rec.L94 = (float)L94; rec.L99 = (float)L99;
-        rec.s5 = (float)std::sqrt(std::fmax(xi[4 * 9 + 4], 0.0));
-        rec.s6 = (float)std::sqrt(std::fmax(xi[5 * 9 + 5], 0.0));
-        rec.s7 = (float)std::sqrt(std::fmax(xi[6 * 9 + 6], 0.0));
-        rec.mode = (noise_mode != LB_NOISE_OFF && kT > 0.0) ? 1 : 0;
+        fill_rep_record(b->rho0, b->cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode, &b->recs[r]);
         b->mode[r] = noise_mode;
         b->have_params[r] = true;
         int u = upload_rec(b, r);

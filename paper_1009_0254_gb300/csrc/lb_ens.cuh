@@ -1,0 +1,77 @@
+// lb_ens.cuh -- device pieces shared by the engines that step many independent lattices
+// in one launch (batched ensembles, the request server): the per-lattice record, the
+// register copy of it that the collision reads, and the collision of one staged tile.
+#pragma once
+
+#include "lb_collide.cuh"
+#include "lb_internal.cuh"
+#include "lb_tma.cuh"
+
+namespace lbf {
+
+// Per-replica record (device).
+struct RepRec {
+    float rho0, cs2m, kappa, lb, ls, lq, le;
+    float L44, L94, L99, s5, s6, s7;
+    int mode;                 // 0 no noise, 1 uncorrelated noise
+    uint32_t k0, k1;          // Philox key = the replica's seed
+    long long toff;           // time = K + toff
+};
+
+// What collide_node needs for one tile of one replica, in registers.
+struct TileArgs {
+    float rho0, cs2m, kappa, lb, ls, lq, le;
+    float L44, L94, L99, s5, s6, s7;
+    uint32_t t_lo, t_hi;
+    KeyPair rk;
+};
+
+// The record of one lattice as collide_node reads it, for its time t; *mode = 0 without
+// noise, 1 with uncorrelated noise.
+__device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t, int* mode) {
+    TileArgs a;
+    a.rho0 = __ldg(&rp->rho0); a.cs2m = __ldg(&rp->cs2m); a.kappa = __ldg(&rp->kappa);
+    a.lb = __ldg(&rp->lb); a.ls = __ldg(&rp->ls); a.lq = __ldg(&rp->lq); a.le = __ldg(&rp->le);
+    a.L44 = __ldg(&rp->L44); a.L94 = __ldg(&rp->L94); a.L99 = __ldg(&rp->L99);
+    a.s5 = __ldg(&rp->s5); a.s6 = __ldg(&rp->s6); a.s7 = __ldg(&rp->s7);
+    a.rk.k0 = __ldg(&rp->k0); a.rk.k1 = __ldg(&rp->k1);
+    a.t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);
+    a.t_hi = (uint32_t)((unsigned long long)t >> 32);
+    *mode = __ldg(&rp->mode);
+    return a;
+}
+
+// Collide and stream the TX x TY nodes of one tile from the staged populations S and the
+// density tile R (with its one-node ring).
+template <int MODE, int TX, int TY, int NT>
+__device__ __forceinline__ void tile_nodes(const TileArgs& a, const float* S, const float* R, const Grid& g, int x0,
+                                           int y0, float* dst) {
+    using TT = TmaTile<TX, TY, float>;
+    static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
+#pragma unroll
+    for (int it = 0; it < TX * TY / NT; ++it) {
+        const int q = threadIdx.x + it * NT;
+        const int ly = q / TX, lx = q - ly * TX;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x >= g.nx || y >= g.ny) continue;
+        float f[Q];
+        load9_ps<TT::PS>(S, (ly + 1) * TT::BW + lx + TT::XO, f);
+        const int rc = (ly + 1) * TT::RW + lx + 1;
+        Nbr r;
+        r.C = R[rc];
+        r.E = R[rc + 1]; r.W = R[rc - 1];
+        r.N = R[rc + TT::RW]; r.S = R[rc - TT::RW];
+        r.NE = R[rc + TT::RW + 1]; r.NW = R[rc + TT::RW - 1];
+        r.SE = R[rc - TT::RW + 1]; r.SW = R[rc - TT::RW - 1];
+        const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+        float o[Q];
+        collide_node<MODE>(a, f, r, node, make_float2(0.f, 0.f), o);
+        store9(dst, g.plane, g, x, y, o);
+    }
+}
+
+// host: fills the parameter fields of a record (defined in lb_batch.cu)
+void fill_rep_record(double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
+                     double tau_ghost, int noise_mode, RepRec* rec);
+
+}  // namespace lbf

@@ -249,6 +249,135 @@ def timed_run(lbf, torch, L, steps, warmup, mode, params, dist):
     return ms, kms, kl, launches, wall0, wall1
 
 
+def batched_variant(lbf, torch, steps=2000, graph_steps=100, plain_steps=20):
+    """Batched ensemble: 512 replicas, 128 each of 32^2, 64^2, 128^2, 256^2, own seeds and kT
+    uniform in [5e-5, 2e-4], long-wavelength noise, one persistent launch per step replayed
+    from a CUDA graph of `graph_steps` steps, tile shape autotuned; against the plain path
+    (one lb_step per lattice per step) on the same replicas."""
+    rng = np.random.default_rng(2024)
+    sizes = [(L, L) for L in (32, 64, 128, 256) for _ in range(128)]
+    seeds = [int(x) for x in rng.integers(1, 2 ** 62, len(sizes))]
+    kT = rng.uniform(5e-5, 2e-4, len(sizes))
+    nodes = sum(a * b for a, b in sizes)
+    ens = lbf.Ensemble(sizes, seeds)
+    for r in range(len(sizes)):
+        ens.set_params(r, float(kT[r]), 0.01, 0.8, 1.0, 1.0, lbf.LB_NOISE_LW)
+    ens.autotune(5)
+    ens.set_sampling(100, 64)
+    ens.step(2 * graph_steps, graph_steps=graph_steps)        # warm-up, graph captured
+    torch.cuda.synchronize()
+    k0 = lbf.lb_batch_launch_count(ens.b)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(ens.stream)
+    ens.step(steps, graph_steps=graph_steps)
+    ev1.record(ens.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = lbf.lb_batch_launch_count(ens.b) - k0
+    tx, ty, nt, _ = lbf.lb_batch_tuning(ens.b)
+    ens.close()
+    del ens
+    # plain path: the same lattices as separate contexts, one step launch per lattice
+    lats = []
+    for r in range(len(sizes)):
+        L = lbf.Lattice(*sizes[r], seed=seeds[r])
+        L.set_params(float(kT[r]), 0.01, 0.8, 1.0, 1.0, lbf.LB_NOISE_LW)
+        lats.append(L)
+    for L in lats:
+        L.step(2)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(plain_steps):
+        for L in lats:
+            L.step(1)
+    ev1.record()
+    torch.cuda.synchronize()
+    pms = ev0.elapsed_time(ev1)
+    for L in lats:
+        L.close()
+    value = nodes * steps / (ms / 1e3) / 1e6
+    plain = nodes * plain_steps / (pms / 1e3) / 1e6
+    return {"workload": "batched ensemble: 512 FP32 replicas (128 each of 32^2, 64^2, 128^2, 256^2), own Philox "
+                        "seeds, kT uniform in [5e-5, 2e-4], kappa=0.01, tau_s=0.8, long-wavelength noise, "
+                        "%d steps, S(k) every 100 steps into 64 bins" % steps,
+            "value": value, "unit": "MLUPS", "ms_per_step": ms / steps,
+            "launch": "one persistent launch per step, CUDA graph of %d steps" % graph_steps,
+            "autotuned_tile": [tx, ty, nt], "gpu_launches": launches,
+            "plain_path": {"value": plain, "unit": "MLUPS", "steps": plain_steps,
+                           "how": "512 lb_step calls per step, one context per lattice"},
+            "speedup_vs_plain": value / plain,
+            "accuracy": "each replica steps exactly the trajectory it has alone (bitwise, tests/test_gpu_batch.py); "
+                        "replicas vs FP64 oracle <= 1e-5, per-replica S(k) vs oracle rtol 1e-4"}
+
+
+def served_variant(lbf, torch, n_requests=64, rate=200.0, budget=120 * 10 ** 9, chunk=200):
+    """Serving: a Poisson stream of requests at `rate`/s (a bounded sample of n_requests),
+    L uniform in {64, 128, 256, 512, 1024}, steps log-uniform in [1e3, 1e5], kT in
+    [5e-5, 2e-4], kappa in [0.005, 0.05], tau_s in [0.6, 1.5], FP32, admitted under an HBM
+    budget; latency = completion - submission on the host clock."""
+    rng = np.random.default_rng(11)
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    arrive = np.cumsum(gaps) - gaps[0]
+    side = rng.choice([64, 128, 256, 512, 1024], n_requests)
+    steps = np.exp(rng.uniform(np.log(1e3), np.log(1e5), n_requests)).astype(np.int64)
+    kT = rng.uniform(5e-5, 2e-4, n_requests)
+    kap = rng.uniform(0.005, 0.05, n_requests)
+    ts = rng.uniform(0.6, 1.5, n_requests)
+    srv = lbf.Server(budget, max_active=4096, max_chunk_steps=chunk)
+    t0 = time.perf_counter()
+    for k in range(n_requests):
+        d = arrive[k] - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        srv.submit(int(side[k]), int(side[k]), int(steps[k]), kT=float(kT[k]), kappa=float(kap[k]),
+                   tau_s=float(ts[k]), seed=1000 + k)
+    srv.wait(0)
+    res = srv.poll(n_requests + 8)
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r.t_complete - r.t_submit for r in res])
+    wall = st.t_last_complete - st.t_first_admit
+    value = st.node_updates / wall / 1e6
+    # plain path: each size alone through lb_step, measured; a FIFO server running one
+    # request at a time on it is then modelled from those service times
+    per_step = {}
+    for L in (64, 128, 256, 512, 1024):
+        lat_ = lbf.Lattice(L, L, seed=7)
+        lat_.set_params(1e-4, 0.01, 0.8, 1.0, 1.0, lbf.LB_NOISE_LW)
+        lat_.step(10)
+        torch.cuda.synchronize()
+        k = 400
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(lat_.stream)
+        lat_.step(k)
+        e1.record(lat_.stream)
+        torch.cuda.synchronize()
+        per_step[L] = e0.elapsed_time(e1) / 1e3 / k
+        lat_.close()
+    service = np.array([steps[k] * per_step[int(side[k])] for k in range(n_requests)])
+    done_t, free_at = np.zeros(n_requests), 0.0
+    for k in range(n_requests):
+        free_at = max(free_at, arrive[k]) + service[k]
+        done_t[k] = free_at
+    plain_lat = done_t - arrive
+    plain_mlups = float(np.sum(side.astype(float) ** 2 * steps)) / service.sum() / 1e6
+    return {"workload": "served: Poisson arrivals at %.0f/s (sample of %d requests), L in {64..1024}^2, steps "
+                        "log-uniform in [1e3, 1e5], kT in [5e-5, 2e-4], kappa in [0.005, 0.05], tau_s in [0.6, 1.5], "
+                        "FP32, HBM budget %.0f GB" % (rate, n_requests, budget / 1e9),
+            "value": value, "unit": "MLUPS (aggregate, first admission to last completion)",
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "completed": int(st.completed), "node_updates": st.node_updates, "wall_s": wall,
+            "gpu_busy_s": st.gpu_busy_s, "hbm_peak_gb": st.bytes_peak / 1e9,
+            "plain_path": {"value": plain_mlups, "unit": "MLUPS",
+                           "latency_s_modelled": {"p50": float(np.percentile(plain_lat, 50)),
+                                                  "p99": float(np.percentile(plain_lat, 99))},
+                           "how": "measured lb_step time per step for each size; FIFO one-at-a-time server "
+                                  "modelled from those service times"},
+            "accuracy": "each served result is bitwise the same alone and in the mix (tests/test_gpu_serve.py); "
+                        "served lattices vs FP64 oracle <= 1e-5"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -328,6 +457,11 @@ def main():
                          "gpu_launches": hlaunch})
         L16.close()
         del L16
+
+    # batched ensemble and request server (rank 0 of a single-GPU run)
+    if not args.no_variants and world == 1:
+        variants.append(batched_variant(lbf, torch))
+        variants.append(served_variant(lbf, torch))
 
     # end to end through the public API: host initial state in, spectra and sums out
     L.set_params(PARAMS_LW["kT"], PARAMS_LW["kappa"], PARAMS_LW["tau_s"], PARAMS_LW["tau_b"],

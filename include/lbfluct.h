@@ -41,6 +41,8 @@ extern "C" {
 #define LB_ECUDA (-4)      /* a CUDA runtime call failed (message in lb_last_error) */
 #define LB_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
 #define LB_ESTATE (-6)     /* call out of order (e.g. lb_step before lb_set_params) */
+#define LB_ENONFINITE (-7) /* a result holds NaN or infinity (served simulations) */
+#define LB_ECANCELED (-8)  /* the request was cancelled (served simulations) */
 
 /* storage precision of the populations */
 #define LB_FP32 0          /* FP32 deviations f_i - fbar_i (72 bytes moved per node update) */
@@ -294,12 +296,19 @@ const char* lb_batch_last_error(lb_batch* b);
  *   host memory f and releases its device memory.  Until then that memory stays counted
  *   against the budget.  LB_EINVAL if the request is unknown, not finished or not kept.
  * lb_server_get_stats: counters since creation (times in seconds since lb_server_create).
+ * lb_server_cancel: withdraws request `id`: a queued one at once, an admitted one at the
+ *   next chunk boundary (its memory is released); its result then has status
+ *   LB_ECANCELED.  LB_EINVAL if it is unknown or already completed.
+ * lb_server_inject_alloc_failures: fault injection on the host: the next `count`
+ *   admissions behave as if the device allocation failed; those requests complete with
+ *   status LB_ENOMEM without running, and the server carries on.
  * lb_server_destroy: drops queued requests, finishes the admitted ones, frees everything.
  * lb_server_last_error: message of the last failure of s (NULL s: of the last failed
  *   lb_server_create or lb_server_submit validation).
  * Results carry the FP64 conserved sums (rho, jx, jy) of the final state and the host
  * times of submission, admission and completion (completion = when the host saw the GPU
- * finish the chunk holding the request's last step).
+ * finish the chunk holding the request's last step).  A result whose sums are not finite
+ * (a diverged run) has status LB_ENONFINITE.
  */
 typedef struct lb_request {
     int nx, ny;
@@ -336,6 +345,8 @@ int lb_server_poll(lb_server* s, lb_result* out, int max_results, int* n);
 int lb_server_wait(lb_server* s, int64_t id, double timeout_s, lb_result* out);
 int lb_server_fetch_populations(lb_server* s, int64_t id, double* f);
 int lb_server_get_stats(lb_server* s, lb_server_stats* st);
+int lb_server_cancel(lb_server* s, int64_t id);
+int lb_server_inject_alloc_failures(lb_server* s, int count);
 int lb_server_destroy(lb_server* s);
 const char* lb_server_last_error(lb_server* s);
 
@@ -346,6 +357,14 @@ const char* lb_server_last_error(lb_server* s);
  * row-major into xi[81].
  * lb_check_params: the validation lb_set_params performs for an nx x ny lattice.
  */
+/*
+ * Self-test of the device-side timeout path (no fault involved): one CTA waits, with the
+ * bounded wait the TMA step kernels use and a limit of limit_s seconds (0 < limit_s <= 10),
+ * on an mbarrier armed for a transfer that is never issued.  Returns LB_ETIMEOUT and sets
+ * *gave_up = 1 when the wait gave up as designed; the CUDA context stays usable.
+ */
+int lb_selftest_bounded_wait(double limit_s, int* gave_up);
+
 int lb_noise_matrix(double rho0, double cs2, double kT, double kappa, double tau_s,
                     double tau_b, double tau_ghost, double kx, double ky, double* xi);
 int lb_check_params(int nx, int ny, double rho0, double cs2, double kT, double kappa,

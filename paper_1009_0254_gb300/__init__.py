@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbfluct.so")
 
 LB_OK, LB_EINVAL, LB_ENOTPSD, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LB_ENONFINITE, LB_ECANCELED = -7, -8
 LB_FP32, LB_FP16DEV = 0, 1
 LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL, LB_NOISE_DIAG = 0, 1, 2, 3
 LB_HOST, LB_DEVICE = 0, 1
@@ -113,6 +114,9 @@ def load(path: str = LIB_PATH):
         "lb_server_fetch_populations": (c_int, [vp, c_i64, vp]),
         "lb_server_get_stats": (c_int, [vp, ctypes.POINTER(lb_server_stats)]),
         "lb_server_destroy": (c_int, [vp]),
+        "lb_server_cancel": (c_int, [vp, c_i64]),
+        "lb_server_inject_alloc_failures": (c_int, [vp, c_int]),
+        "lb_selftest_bounded_wait": (c_int, [c_dbl, ctypes.POINTER(c_int)]),
         "lb_server_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in proto.items():
@@ -399,6 +403,21 @@ def lb_server_get_stats(srv):
     return st
 
 
+def lb_server_cancel(srv, id):
+    return _scheck(load().lb_server_cancel(srv, id), srv)
+
+
+def lb_server_inject_alloc_failures(srv, count):
+    return _scheck(load().lb_server_inject_alloc_failures(srv, count), srv)
+
+
+def lb_selftest_bounded_wait(limit_s):
+    """Runs the device-side timeout self-test; returns (return code, gave_up flag)."""
+    g = ctypes.c_int()
+    rc = load().lb_selftest_bounded_wait(limit_s, ctypes.byref(g))
+    return rc, g.value
+
+
 def lb_server_destroy(srv):
     return _scheck(load().lb_server_destroy(srv))
 
@@ -587,6 +606,9 @@ class Server:
 
     def stats(self):
         return lb_server_get_stats(self.srv)
+
+    def cancel(self, id):
+        lb_server_cancel(self.srv, id)
 
     def close(self):
         if getattr(self, "srv", None):

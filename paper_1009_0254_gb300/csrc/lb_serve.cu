@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -283,6 +284,8 @@ struct lb_server {
     double node_updates = 0.0, busy_ms = 0.0;
     double t_first_admit = -1.0, t_last_complete = -1.0;
     bool stop = false;
+    int inject_alloc_fail = 0;        // host-side fault injection: admissions left to fail
+    std::vector<int64_t> cancel_ids;  // admitted requests to withdraw at the next chunk boundary
     std::string err;                  // sticky worker error
     std::thread worker;
     Clock::time_point t0;
@@ -304,6 +307,58 @@ unsigned char* slot_stage(lb_server* s, int slot) { return s->h_slot + (size_t)s
             return false;                                                            \
         }                                                                            \
     } while (0)
+
+lb_result make_result(const lb_request& r, int64_t id, int status, double t_submit, double t_admit, double t_done) {
+    lb_result res;
+    std::memset(&res, 0, sizeof(res));
+    res.id = id;
+    res.status = status;
+    res.nx = r.nx;
+    res.ny = r.ny;
+    res.steps = r.steps;
+    res.t_submit = t_submit;
+    res.t_admit = t_admit;
+    res.t_complete = t_done;
+    return res;
+}
+
+// a request that leaves without (further) running: its budget and slot are returned
+void finish_unrun(lb_server* s, const Running& run, int status) {
+    const double t = now_s(s);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->in_use -= run.bytes;
+    s->free_slots.push_back(run.slot);
+    lb_result res = make_result(run.r, run.id, status, run.t_submit, t, t);
+    s->results.push_back(res);
+    s->all_results[run.id] = res;
+    s->completed++;
+    s->cv_done.notify_all();
+}
+
+// withdraw the admitted requests whose cancellation was asked for
+bool apply_cancellations(lb_server* s) {
+    std::vector<int64_t> ids;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        ids.swap(s->cancel_ids);
+    }
+    for (int64_t id : ids) {
+        for (auto it = s->running.begin(); it != s->running.end(); ++it) {
+            if (it->id != id) continue;
+            {
+                // the slot's staging copies and the chunks in flight must be done before
+                // the slot can be handed to another request (a rare path: synchronise)
+                std::lock_guard<std::mutex> gl(s->gpu);
+                SCK(s, cudaFreeAsync(it->mem, s->stream));
+                SCK(s, cudaStreamSynchronize(s->stream));
+            }
+            finish_unrun(s, *it, LB_ECANCELED);
+            s->running.erase(it);
+            break;
+        }
+    }
+    return true;
+}
 
 // admit pending requests (arrival order, smaller ones may pass a request that does not fit)
 bool admit(lb_server* s) {
@@ -338,6 +393,19 @@ bool admit(lb_server* s) {
         serve_grid(pr.r.nx, pr.r.ny, &run.g);
         run.bytes = slot_bytes(run.g);
         run.slot = slots[q];
+        bool injected = false;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->inject_alloc_fail > 0) {
+                s->inject_alloc_fail--;
+                injected = true;
+            }
+        }
+        if (injected) {
+            // behave as a failed allocation: the request completes with LB_ENOMEM, unrun
+            finish_unrun(s, run, LB_ENOMEM);
+            continue;
+        }
         void* mem = nullptr;
         SCK(s, cudaMallocFromPoolAsync(&mem, run.bytes, s->pool, s->stream));
         run.mem = (char*)mem;
@@ -406,6 +474,9 @@ bool complete_chunk(lb_server* s, int c) {
         res.ny = run.r.ny;
         res.steps = run.r.steps;
         for (int j = 0; j < 3; ++j) res.sums[j] = s->h_sums[3 * run.slot + j];
+        if (res.status == LB_OK && !(std::isfinite(res.sums[0]) && std::isfinite(res.sums[1]) &&
+                                     std::isfinite(res.sums[2])))
+            res.status = LB_ENONFINITE;
         res.t_submit = run.t_submit;
         res.t_admit = run.t_admit;
         res.t_complete = t;
@@ -509,6 +580,7 @@ void worker_main(lb_server* s) {
             if (s->stop && s->queue.empty() && s->running.empty() && !s->chunk_pending[0] && !s->chunk_pending[1])
                 break;
         }
+        if (!apply_cancellations(s)) break;
         if (!admit(s)) break;
         if (s->running.empty()) {
             // nothing admitted (budget or slots held by chunks in flight): finish those first
@@ -734,6 +806,33 @@ int lb_server_get_stats(lb_server* s, lb_server_stats* st) {
     st->t_last_complete = s->t_last_complete;
     st->steps_issued = s->K;
     return s->err.empty() ? LB_OK : LB_ECUDA;
+}
+
+int lb_server_cancel(lb_server* s, int64_t id) {
+    if (!s) return LB_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if (it->id != id) continue;
+        const double t = now_s(s);
+        lb_result res = make_result(it->r, id, LB_ECANCELED, it->t_submit, t, t);
+        s->results.push_back(res);
+        s->all_results[id] = res;
+        s->completed++;
+        s->queue.erase(it);
+        s->cv_done.notify_all();
+        return LB_OK;
+    }
+    if (id <= 0 || id >= s->next_id || s->all_results.count(id)) return LB_EINVAL;
+    s->cancel_ids.push_back(id);      // admitted (or being admitted): withdrawn by the worker
+    s->cv.notify_all();
+    return LB_OK;
+}
+
+int lb_server_inject_alloc_failures(lb_server* s, int count) {
+    if (!s || count < 0) return LB_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->inject_alloc_fail = count;
+    return LB_OK;
 }
 
 int lb_server_destroy(lb_server* s) {

@@ -72,16 +72,21 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s: far beyond any healthy tile load
 
-// Bounded wait on an mbarrier phase; the decision to give up is made by the caller
-// collectively (__syncthreads_or) so that no thread of the block is left at a barrier.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase (false once limit_ns have passed); the decision to give
+// up is made by the caller collectively (__syncthreads_or) so that no thread of the block
+// is left at a barrier.
+__device__ __forceinline__ bool mbar_wait_bounded_ns(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
     bool ok = mbar_try_wait(bar, parity);
     if (!ok) {
         const uint64_t t0 = global_ns();
         while (!(ok = mbar_try_wait(bar, parity)))
-            if (global_ns() - t0 > WAIT_LIMIT_NS) break;
+            if (global_ns() - t0 > limit_ns) break;
     }
     return ok;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    return mbar_wait_bounded_ns(bar, parity, WAIT_LIMIT_NS);
 }
 
 // The nine pulled deviations of the node whose unshifted box index is b: plane i is read at

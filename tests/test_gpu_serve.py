@@ -174,3 +174,59 @@ def test_submit_validation():
     with pytest.raises(lbf.LBError):               # not kept
         srv.fetch(i, 16, 16)
     srv.close()
+
+
+def test_cancel_queued_and_running_requests():
+    b = lbf.lb_server_request_bytes(256, 256)
+    srv = lbf.Server(b + b // 2, max_active=8, max_chunk_steps=20)     # one 256^2 at a time
+    long_id = srv.submit(256, 256, 200000, seed=1)                     # runs for seconds
+    queued = srv.submit(256, 256, 50, seed=2)                          # waits for the budget
+    srv.cancel(queued)
+    import time
+    time.sleep(0.2)
+    srv.cancel(long_id)
+    r_long = srv.wait(long_id, timeout_s=30)
+    r_q = srv.wait(queued, timeout_s=30)
+    assert r_q.status == lbf.LB_ECANCELED and r_long.status == lbf.LB_ECANCELED
+    after = srv.submit(64, 64, 30, seed=3)
+    r = srv.wait(after, timeout_s=30)
+    assert r.status == lbf.LB_OK
+    st = srv.stats()
+    assert st.bytes_in_use == 0 and st.completed == 3
+    with pytest.raises(lbf.LBError):
+        srv.cancel(after)                                              # already completed
+    srv.close()
+
+
+def test_injected_allocation_failures_leave_the_server_running():
+    srv = lbf.Server(1 << 30, max_active=16, max_chunk_steps=50)
+    lbf.lb_server_inject_alloc_failures(srv.srv, 2)
+    ids = [srv.submit(32, 32, 40, seed=s) for s in range(1, 6)]
+    srv.wait(0, timeout_s=60)
+    res = {r.id: r for r in srv.poll()}
+    status = [res[i].status for i in ids]
+    assert status.count(lbf.LB_ENOMEM) == 2 and status.count(lbf.LB_OK) == 3
+    assert srv.stats().bytes_in_use == 0
+    srv.close()
+
+
+def test_diverged_run_is_reported_not_finite():
+    # kT = 0.05 rho0 sigma_s^2 * 40: far beyond the low-Mach range, the run blows up
+    srv = lbf.Server(1 << 30, max_active=4, max_chunk_steps=100)
+    i = srv.submit(32, 32, 3000, kT=0.5, kappa=0.0, tau_s=0.51, tau_b=0.51, tau_ghost=0.51, seed=3)
+    r = srv.wait(i, timeout_s=60)
+    assert r.status in (lbf.LB_ENONFINITE, lbf.LB_OK)
+    if r.status == lbf.LB_OK:
+        assert np.all(np.isfinite(r.sums))
+    else:
+        assert not np.all(np.isfinite(r.sums))
+    srv.close()
+
+
+def test_device_wait_gives_up_and_context_survives():
+    rc, gave_up = lbf.lb_selftest_bounded_wait(0.05)
+    assert rc == lbf.LB_ETIMEOUT and gave_up == 1
+    L = lbf.Lattice(16, 16, seed=1)
+    L.set_params(1e-4, 0.01, 1.0, 1.0, 1.0, lbf.LB_NOISE_LW)
+    L.step(5)
+    assert L.t == 5 and np.all(np.isfinite(L.populations()))

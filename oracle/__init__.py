@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_BUILD, "liblbref.so")
 _lib = None
 
 NOISE_OFF, NOISE_LW, NOISE_FULL, NOISE_DIAG = 0, 1, 2, 3
-TAG_MODES_5_8, TAG_MODES_4_9, TAG_KSPACE = 0, 1, 2
+TAG_NODE, TAG_KSPACE = 0, 2
 
 
 def build(force: bool = False) -> str:
@@ -77,9 +77,10 @@ def philox4x32_10(ctr, key):
 
 
 def normals(index, seed: int, step: int, tag: int) -> np.ndarray:
-    """Four unit normals per counter index: shape (len(index), 4)."""
+    """Eight unit normals per counter index (one Box-Muller pair per Philox output word):
+    shape (len(index), 8)."""
     idx = np.ascontiguousarray(np.asarray(index, dtype=np.uint32))
-    out = np.zeros((idx.size, 4))
+    out = np.zeros((idx.size, 8))
     lib().oracle_normals(idx.size, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                          ctypes.c_uint64(seed), ctypes.c_uint64(step), ctypes.c_uint32(tag), _dp(out))
     return out
@@ -107,7 +108,7 @@ def eta_field(nx, ny, seed, step):
     conj = _fft_conj_index(nx, ny)
     owner = np.minimum(lin, conj)
     g = normals(np.arange(n, dtype=np.uint32), seed, step, TAG_KSPACE)   # draw for every index
-    go = g[owner.ravel()].reshape(ny, nx, 4)
+    go = g[owner.ravel()].reshape(ny, nx, 8)
     selfc = lin == conj
     is_owner = lin == owner
     e1 = np.where(selfc, go[..., 0] + 0j, (go[..., 0] + 1j * go[..., 1]) / np.sqrt(2))
@@ -158,8 +159,9 @@ def xi49_full(model: Model, nx, ny, seed, step):
 def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None):
     """xi[a, y, x] for one step (Sec. IV).
 
-    LW:   xi = L nu with L L^T = Xi(0) (lower-right 6x6 Cholesky), nu_5..8 from tag 0,
-          (nu_4, nu_9) from tag 1, spatially uncorrelated.
+    LW:   xi = L nu with L L^T = Xi(0) (lower-right 6x6 Cholesky); one draw per node
+          (tag 0): nu_5..8 from its words 0, 1 and (nu_4, nu_9) from word 2; spatially
+          uncorrelated.
     DIAG: as LW with the off-diagonal Xi_49 dropped ("ideal gas-like" noise, Sec. IV).
     FULL: modes 5..8 as LW (their variances do not depend on k); modes 4, 9 from
           xi49_full()."""
@@ -168,13 +170,12 @@ def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None):
     if mode == NOISE_OFF or model.kT == 0.0:
         return xi
     idx = np.arange(n, dtype=np.uint32)
-    g0 = normals(idx, seed, step, TAG_MODES_5_8)
+    g0 = normals(idx, seed, step, TAG_NODE)
     nu = np.zeros((9, n))
-    nu[4:8] = g0.T
+    nu[4:8] = g0[:, 0:4].T
     if mode in (NOISE_LW, NOISE_DIAG):
-        g1 = normals(idx, seed, step, TAG_MODES_4_9)
-        nu[3] = g1[:, 0]
-        nu[8] = g1[:, 1]
+        nu[3] = g0[:, 4]
+        nu[8] = g0[:, 5]
     if L0 is None:
         X0 = model.Xi_zero()
         if mode == NOISE_DIAG:
@@ -324,11 +325,11 @@ def noise_at_sites(model: Model, mode: int, nx, ny, seed, step, sites, L0=None, 
         L0 = theory.noise_factor(X0)
     idx = sites.astype(np.uint32)
     nu = np.zeros((9, sites.size))
-    nu[4:8] = normals(idx, seed, step, TAG_MODES_5_8).T
+    g0 = normals(idx, seed, step, TAG_NODE)
+    nu[4:8] = g0[:, 0:4].T
     if mode in (NOISE_LW, NOISE_DIAG):
-        g1 = normals(idx, seed, step, TAG_MODES_4_9)
-        nu[3] = g1[:, 0]
-        nu[8] = g1[:, 1]
+        nu[3] = g0[:, 4]
+        nu[8] = g0[:, 5]
     xi[:] = (L0 @ nu).T
     if mode == NOISE_FULL:
         if xi49 is None:

@@ -104,29 +104,29 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Uniform on (0,1) from the top 23 bits: (k + 1/2) 2^-23 = (2k + 1) 2^-24, which has
- * at most 24 significant bits and so is exact in FP32 as well as FP64. */
-static double unit_open(uint32_t x) {
-    return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
-}
-
-/* Box-Muller: (u1, u2) -> sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2). */
-static void box_muller(uint32_t a, uint32_t b, double* n0, double* n1) {
+/* One output word -> one Box-Muller pair.  The top 20 bits give the radius uniform
+ * u1 = (k + 1/2) 2^-20, the low 12 bits the angle uniform u2 = (j + 1/2) 2^-12; both are
+ * exact in FP32 as well as FP64.  Then (u1, u2) -> sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2):
+ * |n| <= sqrt(-2 ln 2^-21) = 5.39, and the 4096 equally spaced angles keep every moment of
+ * the pair below order 4096 exact. */
+static void box_muller_word(uint32_t w, double* n0, double* n1) {
     const double two_pi = 6.283185307179586476925286766559;
-    double u1 = unit_open(a), u2 = unit_open(b);
-    double r = sqrt(-2.0 * log(u1));
+    const double u1 = ((double)(w >> 12) + 0.5) * (1.0 / 1048576.0);
+    const double u2 = ((double)(w & 0xfffu) + 0.5) * (1.0 / 4096.0);
+    const double r = sqrt(-2.0 * log(u1));
     *n0 = r * cos(two_pi * u2);
     *n1 = r * sin(two_pi * u2);
 }
 
 /*
- * Four unit normals per entry of `index[]` for one (seed, step, tag):
+ * Eight unit normals per entry of `index[]` for one (seed, step, tag):
  *   key     = (seed & 0xffffffff, seed >> 32)
  *   counter = (index, step & 0xffffffff, step >> 32, tag)
- *   normals = Box-Muller of output words (0,1) and (2,3).
- * index is the node number y*nx + x (or a wavevector number), tag selects the
- * draw: 0 -> nu_5..nu_8, 1 -> (nu_4, nu_9) from words 0,1, 2 -> k-space eta.
- * out[4*j + q] receives normal q of entry j.
+ *   normals = the Box-Muller pairs of output words 0, 1, 2, 3 in that order.
+ * index is the node number y*nx + x (or a wavevector number), tag selects the draw:
+ * 0 -> per node: words 0, 1 -> nu_5..nu_8, word 2 -> (nu_4, nu_9);
+ * 2 -> k-space eta from words 0, 1.
+ * out[8*j + q] receives normal q of entry j.
  */
 void oracle_normals(int64_t count, const uint32_t* index, uint64_t seed, uint64_t step,
                     uint32_t tag, double* out) {
@@ -135,8 +135,7 @@ void oracle_normals(int64_t count, const uint32_t* index, uint64_t seed, uint64_
         uint32_t ctr[4] = {index[j], (uint32_t)(step & 0xffffffffu), (uint32_t)(step >> 32), tag};
         uint32_t r[4];
         oracle_philox4x32_10(ctr, key, r);
-        box_muller(r[0], r[1], &out[4 * j + 0], &out[4 * j + 1]);
-        box_muller(r[2], r[3], &out[4 * j + 2], &out[4 * j + 3]);
+        for (int q = 0; q < 4; ++q) box_muller_word(r[q], &out[8 * j + 2 * q], &out[8 * j + 2 * q + 1]);
     }
 }
 

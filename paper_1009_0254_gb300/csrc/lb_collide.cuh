@@ -61,16 +61,16 @@ __device__ __forceinline__ void collide_node(const Args& a, const float f[Q], co
     // noise, Sec. IV
     float xi4 = 0.f, xi5 = 0.f, xi6 = 0.f, xi7 = 0.f, xi8 = 0.f, xi9 = 0.f;
     if (MODE != 0) {
-        const uint4 r0 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_MODES_5_8), a.rk);
-        const float2 g01 = gauss_pair(r0.x, r0.y);
-        const float2 g23 = gauss_pair(r0.z, r0.w);
+        // one Philox draw per node and step: words 0, 1 -> nu_5..nu_8, word 2 -> (nu_4, nu_9)
+        const uint4 r0 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_NODE), a.rk);
+        const float2 g01 = gauss_pair(r0.x);
+        const float2 g23 = gauss_pair(r0.y);
         xi5 = a.s5 * g01.x;
         xi6 = a.s6 * g01.y;
         xi7 = a.s7 * g23.x;
         xi8 = a.s7 * g23.y;
         if (MODE == 1) {
-            const uint4 r1 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_MODES_4_9), a.rk);
-            const float2 n49 = gauss_pair(r1.x, r1.y);
+            const float2 n49 = gauss_pair(r0.z);
             xi4 = a.L44 * n49.x;
             xi9 = a.L94 * n49.x + a.L99 * n49.y;
         } else {

@@ -26,8 +26,8 @@ __device__ __forceinline__ void noise49_pair(const NoiseGenArgs& ga, int mx, int
     const uint32_t conj = cy * ga.nx + cx;
     const uint32_t owner = lin < conj ? lin : conj;
     const uint4 r = philox4x32_10(make_uint4(owner, ga.t_lo, ga.t_hi, TAG_KSPACE), ga.rk);
-    const float2 g01 = gauss_pair(r.x, r.y);
-    const float2 g23 = gauss_pair(r.z, r.w);
+    const float2 g01 = gauss_pair(r.x);
+    const float2 g23 = gauss_pair(r.y);
     float2 e1, e2;
     if (lin == conj) {
         e1 = make_float2(g01.x, 0.f);

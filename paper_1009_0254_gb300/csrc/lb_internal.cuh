@@ -133,22 +133,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeyPair& kp) {
     return c;
 }
 
-// Two unit normals by Box-Muller, sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2), from two
-// 32-bit words: u = (2k+1) 2^-24 with k the top 23 bits, exact in FP32.  Evaluated with
-// the hardware approximations of log2, rsqrt, sin and cos (absolute error below 1e-6 in
-// the normal except for u1 within ~1e-6 of 1, where r itself is below 1.5e-3 and the error
-// below 7e-4); cos(2 pi u) = -cos(2 pi (u - 1/2)) keeps the angle in [-pi, pi].
-// The uniforms are built exactly from bits: x = 1 + k 2^-23 (k in the mantissa), then
-// u1 = x - (1 - 2^-24) and u2 - 1/2 = (x - 3/2) + 2^-24, both exact by Sterbenz's lemma.
+// Box-Muller is evaluated with the hardware approximations of log2, sqrt, sin and cos
+// (absolute error below 1e-6 in the normal except for u1 within ~1e-6 of 1, where r itself
+// is below 1.5e-3 and the error below 7e-4).  The uniforms are built exactly from bits:
+// x = 1 + (k + 1/2) 2^-20 with k in the top mantissa bits, then u1 = x - 1, exact by
+// Sterbenz's lemma; likewise u2 - 1/2 = (1 + (j + 1/2) 2^-12) - 3/2.
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 
-__device__ __forceinline__ float2 gauss_pair(uint32_t a, uint32_t b) {
-    const float u1 = __uint_as_float((a >> 9) | 0x3f800000u) - 0.99999994f;
-    const float v2 = (__uint_as_float((b >> 9) | 0x3f800000u) - 1.5f) + 0x1p-24f;   // u2 - 1/2
+// One Philox output word -> one Box-Muller pair: the top 20 bits give the radius uniform
+// u1 = (k + 1/2) 2^-20, the low 12 bits the angle uniform u2 = (j + 1/2) 2^-12, both built
+// exactly from the bits; (n0, n1) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2), evaluated
+// as -r (cos, sin)(2 pi (u2 - 1/2)) so that the hardware sine and cosine see |x| < pi.
+__device__ __forceinline__ float2 gauss_pair(uint32_t w) {
+    const float u1 = __uint_as_float(((w >> 12) << 3) | 0x3f800004u) - 1.0f;
+    const float v2 = __uint_as_float(((w & 0xfffu) << 11) | 0x3f800400u) - 1.5f;
     const float l = fmaxf(-1.3862943611198906f * __log2f(u1), 0.0f);     // -2 ln u1 = -2 ln2 log2 u1
     const float r = sqrt_approx(l);
     const float th = 6.2831853071795865f * v2;
@@ -162,9 +164,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // noise draw tags (fourth counter word)
-constexpr uint32_t TAG_MODES_5_8 = 0;   // nu_5..nu_8
-constexpr uint32_t TAG_MODES_4_9 = 1;   // (nu_4, nu_9)
-constexpr uint32_t TAG_KSPACE = 2;      // eta_1(k), eta_2(k)
+constexpr uint32_t TAG_NODE = 0;     // per node: words 0, 1 -> nu_5..nu_8, word 2 -> (nu_4, nu_9)
+constexpr uint32_t TAG_KSPACE = 2;   // per wavevector pair: words 0, 1 -> eta_1(k), eta_2(k)
 
 // Writes v at (x, y) of a plane and at the ghost copies that (x, y) feeds.  Only columns
 // -2, -1, nx, nx+1 and rows -2, -1, ny, ny+1 are ever read, but the ghost columns are

@@ -147,10 +147,9 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// Tile shapes (TX x TY nodes, NT threads): 0 = 32x16/256 (four CTAs per SM, the fastest
-// measured on GB300), 1 = 128x8/512 (two CTAs per SM), 2 = 64x8/256 (four CTAs per SM),
-// 3 = 64x16/512 (two CTAs per SM), 4 = 64x32/1024 (one CTA per SM).
-static const int kTiles[5][3] = {{32, 16, 256}, {128, 8, 512}, {64, 8, 256}, {64, 16, 512}, {64, 32, 1024}};
+// Tile shapes (TX x TY nodes, NT threads): 0 = 32x16/256 (the fastest measured on GB300),
+// 1 = 32x32/256, 2 = 64x8/256, 3 = 64x16/512, 4 = 32x16/128.
+static const int kTiles[5][3] = {{32, 16, 256}, {32, 32, 256}, {64, 8, 256}, {64, 16, 512}, {32, 16, 128}};
 
 int tma_tile_count() { return 5; }
 
@@ -200,10 +199,10 @@ static cudaError_t launch_cfg(const void* map, TmaArgs ta, cudaStream_t s) {
 template <int MODE, typename T>
 static cudaError_t launch_mode(const void* map, const TmaArgs& ta, int tile, cudaStream_t s) {
     switch (tile) {
-        case 1: return launch_cfg<128, 8, 512, MODE, T>(map, ta, s);
+        case 1: return launch_cfg<32, 32, 256, MODE, T>(map, ta, s);
         case 2: return launch_cfg<64, 8, 256, MODE, T>(map, ta, s);
         case 3: return launch_cfg<64, 16, 512, MODE, T>(map, ta, s);
-        case 4: return launch_cfg<64, 32, 1024, MODE, T>(map, ta, s);
+        case 4: return launch_cfg<32, 16, 128, MODE, T>(map, ta, s);
         default: return launch_cfg<32, 16, 256, MODE, T>(map, ta, s);
     }
 }

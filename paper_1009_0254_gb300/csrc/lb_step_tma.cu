@@ -13,7 +13,9 @@
 //   * two stages and an mbarrier each: tile k+1 is in flight while tile k is computed;
 //   * density on the tile plus one ring is formed from shared memory, then every node
 //     collides and stores its nine post-collision deviations (and periodic ghosts)
-//     directly from registers with coalesced stores.
+//     directly from registers with coalesced stores.  Nodes beyond a ragged edge of the
+//     lattice take part in the density pass (their values are never used) but not in the
+//     collision pass.
 // Waits on the mbarriers are bounded by the global timer; a CTA that gives up sets the
 // error word and returns.
 #include <cuda.h>
@@ -80,32 +82,65 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         const T* S = smem + s * TT::STAGE;
         const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
 
-        // density deviation on the tile and its ring: node (lx, ly) = (rx - 1, ry - 1)
-        constexpr int NA = (TT::RW * TT::RH + NT - 1) / NT;
+        static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
+        constexpr int NN = TX * TY / NT;
+        // RES: each thread pulls its nodes' nine deviations once, keeps them in registers
+        // across the barrier and writes their density to the tile; the ring is formed
+        // separately.  Otherwise the density of tile and ring is formed in one pass and
+        // the nodes pull again in the collision pass (fewer live registers; measured
+        // faster for the uncorrelated noise in FP32 storage, slower for the others).
+        constexpr bool RES = !(MODE == 1 && sizeof(T) == 4);
+        float fr[RES ? NN : 1][Q];
+        if constexpr (RES) {
 #pragma unroll
-        for (int it = 0; it < NA; ++it) {
-            const int q = tid + it * NT;
-            if (q >= TT::RW * TT::RH) break;
-            const int ry = q / TT::RW, rx = q - ry * TT::RW;
-            const int b = ry * TT::BW + rx + TT::XO - 1;
-            float f[Q];
-            load9(S, b, f);
-            R[q] = drho_of(f);
+            for (int it = 0; it < NN; ++it) {
+                const int q = tid + it * NT;
+                const int ly = q / TX, lx = q - ly * TX;
+                load9(S, (ly + 1) * TT::BW + lx + TT::XO, fr[it]);
+                R[(ly + 1) * TT::RW + lx + 1] = drho_of(fr[it]);
+            }
+            // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
+            constexpr int NB = 2 * (TX + 2) + 2 * TY;
+            for (int j = tid; j < NB; j += NT) {
+                int rx, ry;
+                if (j < TX + 2) { rx = j; ry = 0; }
+                else if (j < 2 * (TX + 2)) { rx = j - (TX + 2); ry = TY + 1; }
+                else { const int u = j - 2 * (TX + 2); ry = 1 + (u >> 1); rx = (u & 1) ? TX + 1 : 0; }
+                float h[Q];
+                load9(S, ry * TT::BW + rx + TT::XO - 1, h);
+                R[ry * TT::RW + rx] = drho_of(h);
+            }
+        } else {
+            // density deviation on the tile and its ring: node (lx, ly) = (rx - 1, ry - 1)
+            constexpr int NA = (TT::RW * TT::RH + NT - 1) / NT;
+#pragma unroll
+            for (int it = 0; it < NA; ++it) {
+                const int q = tid + it * NT;
+                if (q >= TT::RW * TT::RH) break;
+                const int ry = q / TT::RW, rx = q - ry * TT::RW;
+                const int b = ry * TT::BW + rx + TT::XO - 1;
+                float f[Q];
+                load9(S, b, f);
+                R[q] = drho_of(f);
+            }
         }
         __syncthreads();
 
         // collide every node of the tile; the nodes of one thread are independent, so
         // their random-number and collision chains interleave
-        static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
 #pragma unroll
-        for (int it = 0; it < TX * TY / NT; ++it) {
+        for (int it = 0; it < NN; ++it) {
             const int q = tid + it * NT;
             const int ly = q / TX, lx = q - ly * TX;
             const int x = x0 + lx, y = y0 + ly;
             if (x >= g.nx || y >= g.ny) continue;
-            const int b = (ly + 1) * TT::BW + lx + TT::XO;
             float f[Q];
-            load9(S, b, f);
+            if constexpr (RES) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] = fr[it][i];
+            } else {
+                load9(S, (ly + 1) * TT::BW + lx + TT::XO, f);
+            }
             const int rc = (ly + 1) * TT::RW + lx + 1;
             Nbr r;
             r.C = R[rc];

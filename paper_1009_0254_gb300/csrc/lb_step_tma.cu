@@ -74,9 +74,17 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         const int s = k & 1;
         const uint32_t parity = (uint32_t)((k >> 1) & 1);
         // bounded wait for this tile's nine boxes; the decision to give up is collective
+        // (this barrier also orders the previous tile's reads of R before this tile's writes)
         const bool ok = mbar_wait_bounded(smem_u32(&mbar[s]), parity);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(ta.err, 1);
+            if (tid == 0) {
+                atomicExch(ta.err, 1);
+                // give the loads still in flight into this CTA's shared memory a bounded
+                // chance to land before the CTA exits
+                mbar_wait_bounded(smem_u32(&mbar[s]), parity);
+                if (tile + (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(smem_u32(&mbar[s ^ 1]), (uint32_t)(((k + 1) >> 1) & 1));
+            }
             return;
         }
         const T* S = smem + s * TT::STAGE;
@@ -125,6 +133,14 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             }
         }
         __syncthreads();
+        if constexpr (RES) {
+            // the collision pass reads no population from stage s: refill it now with the
+            // tile two steps ahead
+            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(tile + 2 * gridDim.x, s);
+            }
+        }
 
         // collide every node of the tile; the nodes of one thread are independent, so
         // their random-number and collision chains interleave
@@ -155,11 +171,15 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             collide_node<MODE>(a, f, r, node, z, o);
             store9(static_cast<T*>(a.dst), g.plane, g, x, y, o);
         }
-        __syncthreads();
-        // stage s is free again: refill it with the tile two steps ahead
-        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(tile + 2 * gridDim.x, s);
+        if constexpr (!RES) {
+            // stage s is free once every thread has pulled from it: refill it with the
+            // tile two steps ahead (a CTA barrier measured faster here than a
+            // last-warp-out release through a shared counter)
+            __syncthreads();
+            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(tile + 2 * gridDim.x, s);
+            }
         }
     }
 }

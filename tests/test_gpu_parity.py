@@ -124,6 +124,25 @@ def test_full_size_sampled_parity_and_conservation(kernel):
         assert np.all(np.abs(s1[1:] - s0[1:]) < 1e-7 * nx * ny)
 
 
+@pytest.mark.parametrize("mode", ["full", "lw"])
+def test_parity_64x64_config1_1000_steps(mode):
+    # the same configuration over its full 1000 steps (default step kernel): the FP32
+    # path stays within the population bar of the FP64 oracle, and both conserve mass
+    g, o = _pair(64, 64, 42, 1.0, 1 / 3, CONFIG1, MODES[mode], 0.0)
+    g.step(1000)
+    o.step(1000)
+    fg = g.populations()
+    err = np.abs(fg - o.f).max()
+    # conserved sums: the FP32 rounding of 9 n stored deviations per step (relative 2^-24
+    # each, independent) adds up as a random walk over nodes and steps
+    dmax = np.abs(o.f - o.model.fbar()[:, None, None]).max()
+    walk = np.sqrt(9 * 64 * 64 * 1000) * 2.0 ** -24 * dmax
+    ds = np.abs(g.sums() - o.moments()[:3].sum(axis=(1, 2))).max()
+    print("1000 steps %s: max |f - f_oracle| = %.3e, sums diff %.3e (walk %.3e)" % (mode, err, ds, walk))
+    assert err <= TOL, err
+    assert ds <= 10 * walk, (ds, walk)
+
+
 def test_reproducible_and_resumable(kernel):
     a = lbf.Lattice(64, 64, seed=11)
     b = lbf.Lattice(64, 64, seed=11)

@@ -57,6 +57,10 @@ extern "C" {
                               needs nx, ny powers of two, ny <= 8192 */
 #define LB_NOISE_DIAG 3    /* "ideal gas-like": LW with the off-diagonal Xi_49 dropped */
 
+/* factorisation of the noise matrix, [GACV] Sec. IV (xi = L nu with L L^T = Xi) */
+#define LB_FACTOR_CHOLESKY 0   /* Cholesky of the lower-right block (default) */
+#define LB_FACTOR_EIGEN 1      /* eigen-decomposition L = S diag(sqrt(e)) */
+
 /* buffer locations */
 #define LB_HOST 0
 #define LB_DEVICE 1
@@ -104,6 +108,17 @@ int lb_set_stream(lb_ctx* ctx, void* stream);
  */
 int lb_set_params(lb_ctx* ctx, double kT, double kappa, double tau_s, double tau_b,
                   double tau_ghost, int noise_mode);
+
+/*
+ * lb_set_noise_factor: how the noise matrix is factored, [GACV] Sec. IV: LB_FACTOR_CHOLESKY
+ * (default) or LB_FACTOR_EIGEN, L = S diag(sqrt(e)) with e the eigenvalues (largest first)
+ * and S = [[cos t, -sin t], [sin t, cos t]], t in [0, pi) with tan 2t = 2 Xi49 / (Xi44 -
+ * Xi99), of the coupled (4,9) block (Xi(0) for the uncorrelated modes, Xi(k) at
+ * every k for the correlated mode); the other modes are uncoupled.  Both give noise of
+ * covariance Xi; the realisations differ.  Applies to the current parameters and to later
+ * lb_set_params calls.  LB_EINVAL for an unknown factor.
+ */
+int lb_set_noise_factor(lb_ctx* ctx, int factor);
 
 /*
  * Advances nsteps >= 0 time steps of [GACV] Eq. (fluct-lin-lbe): stream (pull),

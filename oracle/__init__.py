@@ -118,9 +118,10 @@ def eta_field(nx, ny, seed, step):
     return e1, e2
 
 
-def block49_factor(model: Model, kx, ky):
-    """Cholesky factor (L44, L94, L99) of the (4,9) block of Xi(k), Eq. (noise-yeo),
-    vectorised over k; zero pivots clamped to 0 (Sec. IV: Xi is only PSD)."""
+def block49_factor(model: Model, kx, ky, factor: str = "cholesky"):
+    """Factor (L44, L49, L94, L99) of the (4,9) block of Xi(k), Eq. (noise-yeo), vectorised
+    over k: Cholesky (L49 = 0; zero pivots clamped to 0, Sec. IV: Xi is only PSD) or the
+    eigen-decomposition factor S diag(sqrt(e))."""
     c2k = model.cs2_k(kx, ky)
     lb, le = model.lam[3], model.lam[8]
     pref = -(model.rho0 * model.kT / SIGMA_S2)
@@ -130,24 +131,26 @@ def block49_factor(model: Model, kx, ky):
     scale = np.maximum(np.abs(x44), np.abs(x99)) + 1e-300
     if np.any(x44 < -1e-9 * scale) or np.any(x99 < -1e-9 * scale):
         raise ValueError("Xi(k) is not positive semidefinite on this grid")
+    if factor == "eigen":
+        return theory.eigen_factor_2x2(x44, x49, x99)
     L44 = np.sqrt(np.maximum(x44, 0.0))
     L94 = np.where(L44 > 0, x49 / np.where(L44 > 0, L44, 1.0), 0.0)
     rem = x99 - L94 * L94
     if np.any(rem < -1e-9 * scale):
         raise ValueError("Xi(k) is not positive semidefinite on this grid")
     L99 = np.sqrt(np.maximum(rem, 0.0))
-    return L44, L94, L99
+    return L44, np.zeros_like(L44), L94, L99
 
 
-def xi49_full(model: Model, nx, ny, seed, step):
+def xi49_full(model: Model, nx, ny, seed, step, factor: str = "cholesky"):
     """Spatially correlated noise of modes 4 and 9 (Sec. IV, last paragraph): in k-space
     xi(k) = L(k) eta(k) with L L^T the (4,9) block of Xi(k), Eq. (noise-yeo), then one
     transform back to the lattice with the unitary convention of Sec. III:
     a(r) = n^-1/2 sum_k exp(-i k.r) a(k).  Returns real fields xi4[y, x], xi9[y, x]."""
     KX, KY = theory.lattice_k(nx, ny)
-    L44, L94, L99 = block49_factor(model, KX, KY)
+    L44, L49, L94, L99 = block49_factor(model, KX, KY, factor)
     e1, e2 = eta_field(nx, ny, seed, step)
-    x4k = L44 * e1
+    x4k = L44 * e1 + L49 * e2
     x9k = L94 * e1 + L99 * e2
     n = nx * ny
     # numpy's forward fft2 computes sum_k a(k) exp(-2 pi i (mx x/nx + my y/ny))
@@ -156,7 +159,7 @@ def xi49_full(model: Model, nx, ny, seed, step):
     return x4.real, x9.real
 
 
-def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None):
+def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None, factor: str = "cholesky"):
     """xi[a, y, x] for one step (Sec. IV).
 
     LW:   xi = L nu with L L^T = Xi(0) (lower-right 6x6 Cholesky); one draw per node
@@ -180,11 +183,11 @@ def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None):
         X0 = model.Xi_zero()
         if mode == NOISE_DIAG:
             X0 = np.diag(np.diag(X0))
-        L0 = theory.noise_factor(X0)
+        L0 = theory.noise_factor(X0, factor)
     xi_flat = L0 @ nu
     xi[:] = xi_flat.reshape(9, ny, nx)
     if mode == NOISE_FULL:
-        x4, x9 = xi49_full(model, nx, ny, seed, step)
+        x4, x9 = xi49_full(model, nx, ny, seed, step, factor)
         xi[3] = x4
         xi[8] = x9
     return xi
@@ -235,8 +238,13 @@ class Lattice:
         self.t = 0
         self.f = np.broadcast_to(self.model.fbar()[:, None, None], (9, ny, nx)).copy()
         self._L0 = None
+        self.factor = "cholesky"
 
-    def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+    def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode, factor=None):
+        """factor: "cholesky" (default) or "eigen", the factorisation of the noise matrix
+        (Sec. IV); None keeps the current one."""
+        if factor is not None:
+            self.factor = factor
         m = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
         fb_old = self.model.fbar()
         self.model = m
@@ -244,12 +252,12 @@ class Lattice:
         X0 = m.Xi_zero()
         if self.mode == NOISE_DIAG:
             X0 = np.diag(np.diag(X0))
-        self._L0 = theory.noise_factor(X0)
+        self._L0 = theory.noise_factor(X0, self.factor)
         del fb_old
 
     def noise(self, t=None):
         t = self.t if t is None else t
-        return noise_fields(self.model, self.mode, self.nx, self.ny, self.seed, t, self._L0)
+        return noise_fields(self.model, self.mode, self.nx, self.ny, self.seed, t, self._L0, self.factor)
 
     def step(self, nsteps=1):
         for _ in range(int(nsteps)):
@@ -311,7 +319,8 @@ def spectra_sample(f: np.ndarray, rho0: float, nbins: int):
     return Srho, Sjl, Sjt, cnt
 
 
-def noise_at_sites(model: Model, mode: int, nx, ny, seed, step, sites, L0=None, xi49=None):
+def noise_at_sites(model: Model, mode: int, nx, ny, seed, step, sites, L0=None, xi49=None,
+                   factor: str = "cholesky"):
     """xi[k, a] at the listed linear sites (same draws as noise_fields); for the
     correlated mode the (4, 9) fields over the whole lattice may be passed in xi49."""
     sites = np.asarray(sites, dtype=np.int64)
@@ -333,14 +342,15 @@ def noise_at_sites(model: Model, mode: int, nx, ny, seed, step, sites, L0=None, 
     xi[:] = (L0 @ nu).T
     if mode == NOISE_FULL:
         if xi49 is None:
-            xi49 = xi49_full(model, nx, ny, seed, step)
+            xi49 = xi49_full(model, nx, ny, seed, step, factor)
         x4, x9 = xi49
         xi[:, 3] = x4.ravel()[sites]
         xi[:, 8] = x9.ravel()[sites]
     return xi
 
 
-def step_sampled(f: np.ndarray, model: Model, mode: int, seed: int, step: int, nodes, L0=None, xi49=None):
+def step_sampled(f: np.ndarray, model: Model, mode: int, seed: int, step: int, nodes, L0=None, xi49=None,
+                 factor: str = "cholesky"):
     """Pre-collision populations f_i(r, t+1) = f*_i(r - c_i, t) at the listed nodes only,
     shape (len(nodes), 9); the collisions run at the nine source sites of each node."""
     _, ny, nx = f.shape
@@ -349,7 +359,7 @@ def step_sampled(f: np.ndarray, model: Model, mode: int, seed: int, step: int, n
     y = nodes // nx
     src = np.stack([((y - C[i, 1]) % ny) * nx + (x - C[i, 0]) % nx for i in range(9)], axis=1)
     sites, inv = np.unique(src.ravel(), return_inverse=True)
-    xi = noise_at_sites(model, mode, nx, ny, seed, step, sites, L0, xi49)
+    xi = noise_at_sites(model, mode, nx, ny, seed, step, sites, L0, xi49, factor)
     fs = collide_sites(f, model, sites, xi)
     inv = inv.reshape(src.shape)
     return np.stack([fs[inv[:, i], i] for i in range(9)], axis=1)

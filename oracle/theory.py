@@ -242,11 +242,47 @@ def cholesky_psd(X: np.ndarray, rel_tol: float = 1e-12) -> np.ndarray:
     return L
 
 
-def noise_factor(Xi: np.ndarray) -> np.ndarray:
-    """9x9 factor L with xi = L nu: Cholesky of the lower-right 6x6 block (modes 4..9) of a
-    PSD noise matrix whose conserved rows vanish (Sec. IV); rows/columns 1..3 are zero."""
+def eigen_factor_2x2(a, b, c):
+    """Factor L = S diag(sqrt(e1), sqrt(e2)) of the symmetric PSD block [[a, b], [b, c]]
+    (Sec. IV, the eigen-decomposition alternative to Cholesky): e1 >= e2 its eigenvalues,
+    S = [[cos t, -sin t], [sin t, cos t]] their eigenvectors, t in [0, pi) with
+    tan 2t = 2b / (a - c), i.e. t = atan2(2b, a - c) / 2 shifted by pi when negative (the
+    first eigenvector's y component is >= 0; this keeps L continuous where b changes sign
+    while a < c, the case of the (4,9) block of this model).  Returns (L11, L12, L21, L22);
+    vectorised; a negative e2 that is zero up to rounding is clamped to 0."""
+    a, b, c = np.asarray(a, float), np.asarray(b, float), np.asarray(c, float)
+    half = 0.5 * (a + c)
+    rad = np.sqrt(0.25 * (a - c) ** 2 + b * b)
+    e1, e2 = half + rad, half - rad
+    scale = np.maximum(np.abs(a), np.abs(c)) + 1e-300
+    if np.any(e2 < -1e-9 * scale):
+        raise ValueError("matrix is not positive semidefinite")
+    t = 0.5 * np.arctan2(2.0 * b, a - c)
+    t = np.where(t < 0, t + np.pi, t)
+    r1, r2 = np.sqrt(np.maximum(e1, 0.0)), np.sqrt(np.maximum(e2, 0.0))
+    return np.cos(t) * r1, -np.sin(t) * r2, np.sin(t) * r1, np.cos(t) * r2
+
+
+def noise_factor(Xi: np.ndarray, factor: str = "cholesky") -> np.ndarray:
+    """9x9 factor L with xi = L nu and L L^T = Xi for a PSD noise matrix whose conserved
+    rows vanish (Sec. IV); rows/columns 1..3 are zero.  factor = "cholesky": Cholesky of
+    the lower-right 6x6 block (modes 4..9); "eigen": the eigen-decomposition factor
+    S diag(sqrt(e)) of every block of that matrix (the (4,9) block is the only one that is
+    not diagonal in this model)."""
     L = np.zeros((9, 9))
-    L[3:, 3:] = cholesky_psd(Xi[3:, 3:])
+    if factor == "cholesky":
+        L[3:, 3:] = cholesky_psd(Xi[3:, 3:])
+        return L
+    if factor != "eigen":
+        raise ValueError("unknown factor %r" % factor)
+    off = Xi[3:, 3:] - np.diag(np.diag(Xi[3:, 3:]))
+    off[0, 5] = off[5, 0] = 0.0
+    if np.any(np.abs(off) > 1e-12 * (np.abs(Xi).max() + 1e-300)):
+        raise ValueError("the eigen factor expects only the (4,9) block to be coupled")
+    for a in (4, 5, 6, 7):
+        L[a, a] = np.sqrt(max(Xi[a, a], 0.0))
+    l11, l12, l21, l22 = eigen_factor_2x2(Xi[3, 3], Xi[3, 8], Xi[8, 8])
+    L[3, 3], L[3, 8], L[8, 3], L[8, 8] = float(l11), float(l12), float(l21), float(l22)
     return L
 
 

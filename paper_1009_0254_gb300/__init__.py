@@ -22,6 +22,7 @@ LB_OK, LB_EINVAL, LB_ENOTPSD, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_ESTATE = 0, -
 LB_ENONFINITE, LB_ECANCELED = -7, -8
 LB_FP32, LB_FP16DEV = 0, 1
 LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL, LB_NOISE_DIAG = 0, 1, 2, 3
+LB_FACTOR_CHOLESKY, LB_FACTOR_EIGEN = 0, 1
 LB_HOST, LB_DEVICE = 0, 1
 LB_WARN_LOW_MACH = 1
 
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
         "lb_set_stream": (c_int, [vp, vp]),
         "lb_set_params": (c_int, [vp, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_int]),
         "lb_step": (c_int, [vp, c_i64]),
+        "lb_set_noise_factor": (c_int, [vp, c_int]),
         "lb_get_time": (c_int, [vp, i64p]),
         "lb_set_populations": (c_int, [vp, vp, c_int, c_i64]),
         "lb_get_populations": (c_int, [vp, vp, c_int]),
@@ -179,6 +181,10 @@ def lb_set_stream(ctx, stream):
 
 def lb_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
     return _check(load().lb_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode), ctx)
+
+
+def lb_set_noise_factor(ctx, factor):
+    return _check(load().lb_set_noise_factor(ctx, factor), ctx)
 
 
 def lb_step(ctx, nsteps):
@@ -460,6 +466,9 @@ class Lattice:
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
         lb_set_params(self.ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
+
+    def set_noise_factor(self, factor):
+        lb_set_noise_factor(self.ctx, factor)
 
     def step(self, n=1):
         lb_step(self.ctx, n)

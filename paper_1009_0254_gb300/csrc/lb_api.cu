@@ -116,6 +116,22 @@ bool block_psd(const NoiseCoef& c, double s) {
     return x44 * x99 - x49 * x49 >= -tol * scale;
 }
 
+// Factor L = S diag(sqrt e1, sqrt e2) of the PSD block [[a, b], [b, c]] (Sec. IV, the
+// eigen-decomposition alternative to Cholesky): e1 >= e2 its eigenvalues and
+// S = [[cos t, -sin t], [sin t, cos t]], t in [0, pi) with tan 2t = 2b / (a - c).
+void eigen_factor_2x2(double a, double b, double c, double* l11, double* l12, double* l21, double* l22) {
+    const double half = 0.5 * (a + c);
+    const double rad = std::sqrt(0.25 * (a - c) * (a - c) + b * b);
+    const double e1 = half + rad, e2 = std::fmax(half - rad, 0.0);
+    double t = 0.5 * std::atan2(2.0 * b, a - c);
+    if (t < 0.0) t += M_PI;
+    const double r1 = std::sqrt(std::fmax(e1, 0.0)), r2 = std::sqrt(e2);
+    *l11 = std::cos(t) * r1;
+    *l12 = -std::sin(t) * r2;
+    *l21 = std::sin(t) * r1;
+    *l22 = std::cos(t) * r2;
+}
+
 int validate(int nx, int ny, double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
              double tau_g, int mode, std::string* why) {
     auto bad = [&](const char* m) { if (why) *why = m; return LB_EINVAL; };
@@ -188,6 +204,7 @@ struct lb_ctx {
     // parameters
     bool have_params = false;
     int noise_mode = LB_NOISE_OFF, warnings = 0;
+    int factor = LB_FACTOR_CHOLESKY;
     double kT = 0, kappa = 0, tau_s = 1, tau_b = 1, tau_g = 1;
     StepArgs sa{};
     NoiseGenArgs ga{};
@@ -392,10 +409,15 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     const NoiseCoef nc = noise_coef(c->rho0, c->cs2, kT, kappa, tau_s, tau_b, tau_ghost);
     // Sec. IV: xi = L nu with L L^T = Xi(0) on modes 4..9; only the (4,9) block is coupled
     const double x44 = nc.a44, x49 = (mode == LB_NOISE_DIAG) ? 0.0 : nc.a49, x99 = nc.a99;
-    const double L44 = std::sqrt(std::fmax(x44, 0.0));
-    const double L94 = L44 > 0.0 ? x49 / L44 : 0.0;
-    const double L99 = std::sqrt(std::fmax(x99 - L94 * L94, 0.0));
-    a.L44 = (float)L44; a.L94 = (float)L94; a.L99 = (float)L99;
+    double L44, L49 = 0.0, L94, L99;
+    if (c->factor == LB_FACTOR_EIGEN) {
+        eigen_factor_2x2(x44, x49, x99, &L44, &L49, &L94, &L99);
+    } else {
+        L44 = std::sqrt(std::fmax(x44, 0.0));
+        L94 = L44 > 0.0 ? x49 / L44 : 0.0;
+        L99 = std::sqrt(std::fmax(x99 - L94 * L94, 0.0));
+    }
+    a.L44 = (float)L44; a.L49 = (float)L49; a.L94 = (float)L94; a.L99 = (float)L99;
     a.s5 = (float)std::sqrt(std::fmax(nc.x55, 0.0));
     a.s6 = (float)std::sqrt(std::fmax(nc.x66, 0.0));
     a.s7 = (float)std::sqrt(std::fmax(nc.x77, 0.0));
@@ -404,8 +426,18 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     ga.a49 = (float)nc.a49; ga.b49 = (float)nc.b49;
     ga.a99 = (float)nc.a99; ga.b99 = (float)nc.b99;
     ga.cosx = c->cosx; ga.cosy = c->cosy; ga.nx = c->nx; ga.ny = c->ny;
+    ga.eig = c->factor == LB_FACTOR_EIGEN ? 1 : 0;
     ga.rk = a.rk;
     c->have_params = true;
+    return LB_OK;
+}
+
+int lb_set_noise_factor(lb_ctx* c, int factor) {
+    if (!c) return LB_EINVAL;
+    if (factor != LB_FACTOR_CHOLESKY && factor != LB_FACTOR_EIGEN) return fail(c, LB_EINVAL, "unknown noise factor");
+    c->factor = factor;
+    if (c->have_params)
+        return lb_set_params(c, c->kT, c->kappa, c->tau_s, c->tau_b, c->tau_g, c->noise_mode);
     return LB_OK;
 }
 

@@ -362,7 +362,7 @@ void fill_rep_record(double rho0, double cs2, double kT, double kappa, double ta
     rec->lb = (float)(-1.0 / tau_b);
     rec->ls = (float)(-1.0 / tau_s);
     rec->lq = rec->le = (float)(-1.0 / tau_ghost);
-    rec->L44 = (float)L44; rec->L94 = (float)L94; rec->L99 = (float)L99;
+    rec->L44 = (float)L44; rec->L49 = 0.0f; rec->L94 = (float)L94; rec->L99 = (float)L99;
     rec->s5 = (float)std::sqrt(std::fmax(xi[4 * 9 + 4], 0.0));
     rec->s6 = (float)std::sqrt(std::fmax(xi[5 * 9 + 5], 0.0));
     rec->s7 = (float)std::sqrt(std::fmax(xi[6 * 9 + 6], 0.0));

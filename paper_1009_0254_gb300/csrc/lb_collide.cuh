@@ -71,7 +71,7 @@ __device__ __forceinline__ void collide_node(const Args& a, const float f[Q], co
         xi8 = a.s7 * g23.y;
         if (MODE == 1) {
             const float2 n49 = gauss_pair(r0.z);
-            xi4 = a.L44 * n49.x;
+            xi4 = a.L44 * n49.x + a.L49 * n49.y;
             xi9 = a.L94 * n49.x + a.L99 * n49.y;
         } else {
             xi4 = xi49.x;

@@ -12,7 +12,7 @@ namespace lbf {
 // Per-replica record (device).
 struct RepRec {
     float rho0, cs2m, kappa, lb, ls, lq, le;
-    float L44, L94, L99, s5, s6, s7;
+    float L44, L49, L94, L99, s5, s6, s7;
     int mode;                 // 0 no noise, 1 uncorrelated noise
     uint32_t k0, k1;          // Philox key = the replica's seed
     long long toff;           // time = K + toff
@@ -21,7 +21,7 @@ struct RepRec {
 // What collide_node needs for one tile of one replica, in registers.
 struct TileArgs {
     float rho0, cs2m, kappa, lb, ls, lq, le;
-    float L44, L94, L99, s5, s6, s7;
+    float L44, L49, L94, L99, s5, s6, s7;
     uint32_t t_lo, t_hi;
     KeyPair rk;
 };
@@ -32,7 +32,7 @@ __device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t
     TileArgs a;
     a.rho0 = __ldg(&rp->rho0); a.cs2m = __ldg(&rp->cs2m); a.kappa = __ldg(&rp->kappa);
     a.lb = __ldg(&rp->lb); a.ls = __ldg(&rp->ls); a.lq = __ldg(&rp->lq); a.le = __ldg(&rp->le);
-    a.L44 = __ldg(&rp->L44); a.L94 = __ldg(&rp->L94); a.L99 = __ldg(&rp->L99);
+    a.L44 = __ldg(&rp->L44); a.L49 = __ldg(&rp->L49); a.L94 = __ldg(&rp->L94); a.L99 = __ldg(&rp->L99);
     a.s5 = __ldg(&rp->s5); a.s6 = __ldg(&rp->s6); a.s7 = __ldg(&rp->s7);
     a.rk.k0 = __ldg(&rp->k0); a.rk.k1 = __ldg(&rp->k1);
     a.t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);

@@ -44,11 +44,26 @@ __device__ __forceinline__ void noise49_pair(const NoiseGenArgs& ga, int mx, int
     const float x44 = ga.a44 + ga.b44 * s;
     const float x49 = ga.a49 + ga.b49 * s;
     const float x99 = ga.a99 + ga.b99 * s;
-    const float L44 = sqrt_approx(fmaxf(x44, 0.f));
-    const float L94 = L44 > 0.f ? x49 * rcp_approx(L44) : 0.f;
-    const float L99 = sqrt_approx(fmaxf(x99 - L94 * L94, 0.f));
-    // xi_4(k) = L44 e1, xi_9(k) = L94 e1 + L99 e2; at -k both are conjugated
-    const float2 z4 = make_float2(L44 * e1.x, L44 * e1.y);
+    float L44, L49, L94, L99;
+    if (ga.eig) {
+        // L = S diag(sqrt e1, sqrt e2), S = [[cos t, -sin t], [sin t, cos t]], t in [0, pi)
+        // with tan 2t = 2 x49 / (x44 - x99), from the half-angle formulas (Sec. IV alternative)
+        const float hm = 0.5f * (x44 + x99), hd = 0.5f * (x44 - x99);
+        const float rad = sqrtf(hd * hd + x49 * x49);
+        const float e1 = hm + rad, e2 = fmaxf(hm - rad, 0.f);
+        const float c2t = rad > 0.f ? hd / rad : 1.f;
+        const float st = sqrtf(fmaxf(0.5f * (1.f - c2t), 0.f));
+        const float ct = copysignf(sqrtf(fmaxf(0.5f * (1.f + c2t), 0.f)), x49 == 0.f ? 1.f : x49);
+        const float r1 = sqrtf(fmaxf(e1, 0.f)), r2 = sqrtf(e2);
+        L44 = ct * r1; L49 = -st * r2; L94 = st * r1; L99 = ct * r2;
+    } else {
+        L44 = sqrt_approx(fmaxf(x44, 0.f));
+        L49 = 0.f;
+        L94 = L44 > 0.f ? x49 * rcp_approx(L44) : 0.f;
+        L99 = sqrt_approx(fmaxf(x99 - L94 * L94, 0.f));
+    }
+    // xi_4(k) = L44 e1 + L49 e2, xi_9(k) = L94 e1 + L99 e2; at -k both are conjugated
+    const float2 z4 = make_float2(L44 * e1.x + L49 * e2.x, L44 * e1.y + L49 * e2.y);
     const float2 z9 = make_float2(L94 * e1.x + L99 * e2.x, L94 * e1.y + L99 * e2.y);
     *zk = make_float2(z4.x - z9.y, z4.y + z9.x);
     *zmk = make_float2(z4.x + z9.y, -z4.y + z9.x);

@@ -84,7 +84,7 @@ struct StepArgs {
     float cs2m;                      // cs2 - sigma_s^2
     float kappa;
     float lb, ls, lq, le;            // lambda_b, lambda_s, lambda_q, lambda_eps
-    float L44, L94, L99;             // Cholesky factor of the (4,9) block of Xi(0)
+    float L44, L49, L94, L99;        // factor of the (4,9) block of Xi(0) (L49 = 0: Cholesky)
     float s5, s6, s7;                // sqrt(Xi_55), sqrt(Xi_66), sqrt(Xi_77) = sqrt(Xi_88)
     uint32_t t_lo, t_hi;
     RoundKeys rk;
@@ -94,6 +94,7 @@ struct StepArgs {
 // the lattice k^2 of [GACV] Appendix B, coefficients computed on the host in FP64.
 struct NoiseGenArgs {
     float a44, b44, a49, b49, a99, b99;
+    int eig;             // 0: Cholesky factor of the (4,9) block, 1: eigen-decomposition factor
     const float* cosx;   // cos(2 pi m / nx), m < nx
     const float* cosy;   // cos(2 pi m / ny), m < ny
     int nx, ny;

@@ -143,6 +143,33 @@ def test_parity_64x64_config1_1000_steps(mode):
     assert ds <= 10 * walk, (ds, walk)
 
 
+@pytest.mark.parametrize("mode,cs2,kappa", [("lw", 0.15 ** 2, 0.03), ("lw", 1 / 3, 0.01), ("full", 1 / 3, 0.03),
+                                           ("diag", 0.25 ** 2, 0.02)])
+def test_parity_eigen_noise_factor(mode, cs2, kappa):
+    # Sec. IV: the eigen-decomposition factor of the noise matrix instead of Cholesky
+    params = (1e-4, kappa, 1.0, 1.1, 0.9)
+    g = lbf.Lattice(64, 32, seed=13, cs2=cs2)
+    o = oracle.Lattice(64, 32, cs2=cs2, seed=13)
+    g.set_noise_factor(lbf.LB_FACTOR_EIGEN)
+    g.set_params(*params, MODES[mode])
+    o.set_params(*params, MODES[mode], factor="eigen")
+    pert = synth.gaussian_field((9, 32, 64), seed=77, scale=0.005)
+    f0 = o.model.fbar()[:, None, None] * (1.0 + pert)
+    o.f = f0.copy()
+    g.set_populations(f0, t=0)
+    g.step(60)
+    o.step(60)
+    err = np.abs(g.populations() - o.f).max()
+    assert err <= TOL, err
+    # and the realisation really differs from the Cholesky one where Xi49 != 0
+    if mode == "lw" and cs2 != 1 / 3:
+        c = oracle.Lattice(64, 32, cs2=cs2, seed=13)
+        c.set_params(*params, MODES[mode])
+        c.f = f0.copy()
+        c.step(60)
+        assert np.abs(c.f - o.f).max() > 100 * TOL
+
+
 def test_reproducible_and_resumable(kernel):
     a = lbf.Lattice(64, 64, seed=11)
     b = lbf.Lattice(64, 64, seed=11)

@@ -61,7 +61,8 @@ def test_full_noise_is_L_eta_in_k_space():
     x4, x9 = oracle.xi49_full(m, nx, ny, seed=4, step=2)
     e1, e2 = oracle.eta_field(nx, ny, seed=4, step=2)
     KX, KY = th.lattice_k(nx, ny)
-    L44, L94, L99 = oracle.block49_factor(m, KX, KY)
+    L44, L49, L94, L99 = oracle.block49_factor(m, KX, KY)
+    assert np.all(L49 == 0)
     np.testing.assert_allclose(oracle.unitary_ft(x4), L44 * e1, atol=1e-14)
     np.testing.assert_allclose(oracle.unitary_ft(x9), L94 * e1 + L99 * e2, atol=1e-14)
     # L L^T reproduces the (4,9) block of Eq. (noise-yeo) at every k
@@ -148,3 +149,45 @@ def test_long_wavelength_noise_matches_its_own_stationary_theory():
     for a in range(9):
         r = ratio[a][keep]
         assert abs(r.mean() - 1) < 0.04, (a, r.mean())
+
+
+@pytest.mark.parametrize("cs2,kappa", [(1 / 3, 0.03), (0.25 ** 2, 0.05), (0.265 ** 2, 0.08)])
+def test_eigen_factor_reproduces_the_noise_matrix(cs2, kappa):
+    # Sec. IV: L = S diag(sqrt(e)) with S the eigenvectors is the alternative to Cholesky;
+    # either must satisfy L L^T = Xi, at k = 0 (9x9) and for the (4,9) block at every k
+    m = th.Model(rho0=1.0, cs2=cs2, kappa=kappa, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    X0 = m.Xi_zero()
+    for factor in ("cholesky", "eigen"):
+        L = th.noise_factor(X0, factor)
+        np.testing.assert_allclose(L @ L.T, X0, atol=1e-14 * np.abs(X0).max(), rtol=0)
+    Le = th.noise_factor(X0, "eigen")
+    assert Le[3, 8] != 0.0 or X0[3, 8] == 0.0          # not triangular when Xi49 != 0
+    nx, ny = 16, 8
+    KX, KY = th.lattice_k(nx, ny)
+    l11, l12, l21, l22 = oracle.block49_factor(m, KX, KY, "eigen")
+    for (j, i) in [(0, 0), (3, 5), (4, 8), (7, 15), (2, 3)]:
+        X = m.Xi_closed(KX[j, i], KY[j, i])[np.ix_([3, 8], [3, 8])]
+        Lm = np.array([[l11[j, i], l12[j, i]], [l21[j, i], l22[j, i]]])
+        np.testing.assert_allclose(Lm @ Lm.T, X, atol=1e-14 * np.abs(X).max())
+        # the columns of L are eigenvectors scaled by sqrt(eigenvalues), largest first
+        e = np.linalg.eigvalsh(X)
+        np.testing.assert_allclose(np.sort(np.sum(Lm * Lm, axis=0)), np.sort(e), atol=1e-14 * np.abs(X).max())
+        assert np.sum(Lm[:, 0] ** 2) >= np.sum(Lm[:, 1] ** 2) - 1e-20
+
+
+def test_eigen_factor_lw_noise_statistics():
+    # the realisations differ from Cholesky but the covariance of xi is the same Xi(0)
+    m = th.Model(rho0=1.0, cs2=0.15 ** 2, kappa=0.03, kT=1e-4, tau_s=1.0)
+    nx = ny = 64
+    acc = np.zeros((9, 9))
+    steps = 40
+    for t in range(steps):
+        xi = oracle.noise_fields(m, oracle.NOISE_LW, nx, ny, seed=5, step=t, factor="eigen").reshape(9, -1)
+        acc += xi @ xi.T
+    C = acc / (steps * nx * ny)
+    X0 = m.Xi_zero()
+    ns = steps * nx * ny
+    for a in range(3, 9):
+        for b in range(3, 9):
+            sd = np.sqrt((X0[a, a] * X0[b, b] + X0[a, b] ** 2) / ns)
+            assert abs(C[a, b] - X0[a, b]) < 5 * sd + 1e-30, (a, b)

@@ -219,12 +219,14 @@ int lb_conserved_sums_static(const double* f, int nx, int ny, double* sums, void
 
 /*
  * Batched ensembles: many independent periodic lattices ("replicas") stepped together.
- * Every replica is the model of [GACV] Sec. III with uncorrelated noise of Sec. IV
- * (LB_NOISE_OFF, LB_NOISE_LW or LB_NOISE_DIAG; LB_NOISE_FULL is rejected), in FP32
- * storage, with its own size, seed and parameters, and follows exactly the trajectory
- * that lb_create/lb_step with the same size, seed and parameters would give it: a
- * replica's result does not depend on the other replicas of the batch.  Replicas of
- * equal size share one launch of the step kernel per time step.
+ * Every replica is the model of [GACV] Sec. III with the noise of Sec. IV (any noise mode;
+ * LB_NOISE_FULL needs nx, ny powers of two and ny <= 8192), in FP32 storage, with its own
+ * size, seed and parameters, and follows the trajectory that lb_create/lb_step with the
+ * same size, seed and parameters would give it (bitwise for a replica whatever the other
+ * replicas are; up to FP32 rounding order against lb_step).  The step kernel covers every
+ * replica in one persistent launch per time step; replicas with correlated noise add two
+ * launches per size class (k-space synthesis, transform back) before it.  The noise
+ * factor is Cholesky.
  *
  * lb_batch_workspace_bytes: device bytes of an ensemble of `count` lattices of sizes
  *   nx[r] x ny[r] (each side in [2, 8192]); 0 if the sizes are invalid.
@@ -234,7 +236,8 @@ int lb_conserved_sums_static(const double* f, int nx, int ny, double* sums, void
  *   lb_batch_workspace_bytes() that the caller keeps alive until lb_batch_destroy.
  *   Every replica starts at rest at time 0.
  * lb_batch_set_params: lb_set_params for replica `replica`, or for every replica when
- *   replica == -1; the same validation (lb_check_params), LB_EINVAL for LB_NOISE_FULL.
+ *   replica == -1; the same validation (lb_check_params), LB_EINVAL for LB_NOISE_FULL on
+ *   a lattice whose sides are not powers of two.
  * lb_batch_autotune: times every tile shape of the batched step kernel on each size
  *   class over `steps` launches and keeps the fastest, then puts every replica back at
  *   rest at time 0 (populations set before are lost).  Needs parameters for every

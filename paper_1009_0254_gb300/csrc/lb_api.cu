@@ -228,6 +228,12 @@ struct lb_ctx {
 namespace lbf {
 void set_context_free_error(const std::string& msg) { g_create_error = msg; }
 
+void noise_coefficients(double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
+                        double tau_ghost, double out[6]) {
+    const NoiseCoef c = noise_coef(rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost);
+    out[0] = c.a44; out[1] = c.b44; out[2] = c.a49; out[3] = c.b49; out[4] = c.a99; out[5] = c.b99;
+}
+
 // Rest populations fbar_i = w_i (rho0 + T_4i d rho0 / N_4 - T_9i d rho0 / N_9) for the
 // reference moments {rho0, 0, 0, d rho0, 0, 0, 0, 0, -d rho0}, d = 6 (cs2 - sigma_s^2)
 // (Table II at u = 0 with p0 = cs2 rho; inverse transform of Sec. III A).

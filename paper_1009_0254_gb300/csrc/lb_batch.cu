@@ -22,6 +22,7 @@
 
 #include "lb_ens.cuh"
 #include "lb_fft_core.cuh"
+#include "lb_noise.cuh"
 #include "lbfluct.h"
 
 namespace lbf {
@@ -35,6 +36,7 @@ struct ClassDesc {
     int tile_begin;             // first tile of the class in the launch's numbering
     int ntx, per;               // tiles along x per replica, tiles per replica
     long long rstride;          // elements per replica (9 planes)
+    const float2* xi;           // correlated noise (xi_4, xi_9) of the class, nx*ny per replica, or null
 };
 
 struct EnsParams {
@@ -144,8 +146,12 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
         const TileArgs a = load_tile_args(rp, K + __ldg(&rp->toff), &mode);
         float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
 
-        if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst);
-        else tile_nodes<0, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst);
+        if (mode == 2)
+            tile_nodes<2, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst, d.xi + (long long)tp.rep * g.nx * g.ny);
+        else if (mode)
+            tile_nodes<1, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst, nullptr);
+        else
+            tile_nodes<0, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst, nullptr);
         __syncthreads();
         if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -160,6 +166,47 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
             *p.done = 0u;
             *p.kstep = K + 1;
         }
+    }
+}
+
+// --- correlated noise of a class -------------------------------------------------------
+
+// First pass for every replica of the class in correlated mode (blockIdx.y = replica):
+// k-space synthesis with the replica's Xi(k) coefficients, seed and time, back along y.
+__global__ void __launch_bounds__(1024) batch_noise_cols_kernel(float2* out, const RepRec* __restrict__ recs,
+                                                                const long long* __restrict__ kstep, int nx, int ny,
+                                                                int count, const float2* __restrict__ twy,
+                                                                const float* __restrict__ cosx,
+                                                                const float* __restrict__ cosy) {
+    const RepRec* rp = recs + blockIdx.y;
+    if (__ldg(&rp->mode) != 2) return;
+    NoiseGenT<KeyPair> ga;
+    ga.a44 = __ldg(&rp->a44); ga.b44 = __ldg(&rp->b44);
+    ga.a49 = __ldg(&rp->a49); ga.b49 = __ldg(&rp->b49);
+    ga.a99 = __ldg(&rp->a99); ga.b99 = __ldg(&rp->b99);
+    ga.eig = 0;
+    ga.cosx = cosx; ga.cosy = cosy;
+    ga.nx = nx; ga.ny = ny;
+    const long long t = __ldcg(kstep) + __ldg(&rp->toff);
+    ga.t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);
+    ga.t_hi = (uint32_t)((unsigned long long)t >> 32);
+    ga.rk.k0 = __ldg(&rp->k0);
+    ga.rk.k1 = __ldg(&rp->k1);
+    noise_cols_block(out + (long long)blockIdx.y * nx * ny, ga, count, blockIdx.x, twy);
+}
+
+// Second pass: back along x (unitary scale), one CTA per row of a correlated replica.
+__global__ void __launch_bounds__(1024) batch_noise_rows_kernel(float2* data, const RepRec* __restrict__ recs,
+                                                                int nx, int ny, const float2* __restrict__ twx,
+                                                                float scale) {
+    if (__ldg(&recs[blockIdx.x / ny].mode) != 2) return;
+    extern __shared__ float2 sm[];
+    float2* rowp = data + (long long)blockIdx.x * nx;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = rowp[j];
+    stockham_fft(sm, nx, 31 - __clz(nx), 1, -1, twx);
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        const float2 v = sm[fpad(j)];
+        rowp[j] = make_float2(v.x * scale, v.y * scale);
     }
 }
 
@@ -366,7 +413,12 @@ void fill_rep_record(double rho0, double cs2, double kT, double kappa, double ta
     rec->s5 = (float)std::sqrt(std::fmax(xi[4 * 9 + 4], 0.0));
     rec->s6 = (float)std::sqrt(std::fmax(xi[5 * 9 + 5], 0.0));
     rec->s7 = (float)std::sqrt(std::fmax(xi[6 * 9 + 6], 0.0));
-    rec->mode = (noise_mode != LB_NOISE_OFF && kT > 0.0) ? 1 : 0;
+    double co[6];
+    noise_coefficients(rho0, cs2, kT, kappa, tau_s, tau_b, tau_ghost, co);
+    rec->a44 = (float)co[0]; rec->b44 = (float)co[1];
+    rec->a49 = (float)co[2]; rec->b49 = (float)co[3];
+    rec->a99 = (float)co[4]; rec->b99 = (float)co[5];
+    rec->mode = (noise_mode == LB_NOISE_OFF || kT <= 0.0) ? 0 : (noise_mode == LB_NOISE_FULL ? 2 : 1);
 }
 
 }  // namespace lbf
@@ -395,6 +447,8 @@ struct ClassInfo {
     Grid g;
     std::vector<int> members;          // replica ids, in class order
     size_t off_buf[2], off_z1, off_z2, off_tw_x, off_tw_y, off_bin16, off_bins, off_counts, off_recs;
+    size_t off_cosx, off_cosy;         // cos(2 pi m / n) tables of the correlated noise
+    bool any_full = false;             // some replica of the class has correlated noise
 };
 
 struct Layout {
@@ -444,6 +498,8 @@ bool plan(int count, const int* nx, const int* ny, Layout* L) {
         ci.off_bins = take((size_t)ci.R * 3 * kMaxBatchBins * sizeof(double));
         ci.off_counts = take((size_t)kMaxBatchBins * sizeof(unsigned long long));
         ci.off_recs = take((size_t)ci.R * sizeof(RepRec));
+        ci.off_cosx = take(ci.nx * sizeof(float));
+        ci.off_cosy = take(ci.ny * sizeof(float));
     }
     L->off_k = take(sizeof(long long));
     L->off_done = take(sizeof(unsigned int));
@@ -532,6 +588,7 @@ static int build_launches(lb_batch* b, int tile, std::vector<EnsParams>* out) {
             d.per = d.ntx * ((ci.ny + TY - 1) / TY);
             d.tile_begin = tiles;
             d.rstride = (long long)Q * ci.g.plane;
+            d.xi = reinterpret_cast<const float2*>(cls_ptr(b, ci.off_z1));
             const long long more = (long long)d.per * ci.R;
             if (tiles + more > (1ll << 30)) return bfail(b, LB_EINVAL, "too many tiles in one launch");
             tiles += (int)more;
@@ -548,18 +605,41 @@ static int build_launches(lb_batch* b, int tile, std::vector<EnsParams>* out) {
     return LB_OK;
 }
 
+static int col_strip_b(int nx, int ny) {
+    int c = 16;
+    while (c > 1 && (fft_threads(ny, c) > 1024 || fft_smem_bytes(ny, c) > 200 * 1024)) c >>= 1;
+    return c > nx ? nx : c;
+}
+
+// correlated noise (xi_4, xi_9) of every correlated replica of class ci for the coming step,
+// into the class's first spectra buffer (free between samples)
+static int batch_noise(lb_batch* b, const ClassInfo& ci) {
+    float2* xi = reinterpret_cast<float2*>(cls_ptr(b, ci.off_z1));
+    const RepRec* recs = reinterpret_cast<const RepRec*>(cls_ptr(b, ci.off_recs));
+    const int c = col_strip_b(ci.nx, ci.ny);
+    batch_noise_cols_kernel<<<dim3(ci.nx / c, ci.R), fft_threads(ci.ny, c), fft_smem_bytes(ci.ny, c), b->stream>>>(
+        xi, recs, reinterpret_cast<const long long*>(cls_ptr(b, b->L.off_k)), ci.nx, ci.ny, c,
+        reinterpret_cast<const float2*>(cls_ptr(b, ci.off_tw_y)), reinterpret_cast<const float*>(cls_ptr(b, ci.off_cosx)),
+        reinterpret_cast<const float*>(cls_ptr(b, ci.off_cosy)));
+    const float scale = (float)(1.0 / std::sqrt((double)ci.nx * ci.ny));
+    batch_noise_rows_kernel<<<ci.R * ci.ny, fft_threads(ci.nx, 1), fft_smem_bytes(ci.nx, 1), b->stream>>>(
+        xi, recs, ci.nx, ci.ny, reinterpret_cast<const float2*>(cls_ptr(b, ci.off_tw_x)), scale);
+    BCK(b, cudaGetLastError(), "correlated noise");
+    b->kernels += 2;
+    return LB_OK;
+}
+
 static int batch_step_eager(lb_batch* b) {
+    for (const ClassInfo& ci : b->L.classes)
+        if (ci.any_full) {
+            int r = batch_noise(b, ci);
+            if (r != LB_OK) return r;
+        }
     for (const EnsParams& p : b->launches) {
         BCK(b, launch_ensemble(b->tile, p, b->stream), "ensemble step");
         b->kernels++;
     }
     return LB_OK;
-}
-
-static int col_strip_b(int nx, int ny) {
-    int c = 16;
-    while (c > 1 && (fft_threads(ny, c) > 1024 || fft_smem_bytes(ny, c) > 200 * 1024)) c >>= 1;
-    return c > nx ? nx : c;
 }
 
 static int batch_sample(lb_batch* b, cudaStream_t s) {
@@ -660,6 +740,7 @@ int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* see
     }
     cudaError_t e = cudaMemset(b->ws, 0, b->L.total);
     std::vector<float2> tw;
+    size_t noise_csm = 0, noise_rsm = 0;
     for (auto& ci : b->L.classes) {
         if (e != cudaSuccess) break;
         for (int which = 0; which < 2; ++which) {
@@ -671,6 +752,17 @@ int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* see
             }
             e = cudaMemcpy(cls_ptr(b, which == 0 ? ci.off_tw_x : ci.off_tw_y), tw.data(), n * sizeof(float2),
                            cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) break;
+            std::vector<float> cs(n);
+            for (int k = 0; k < n; ++k) cs[k] = (float)std::cos(2.0 * M_PI * (double)k / n);
+            e = cudaMemcpy(cls_ptr(b, which == 0 ? ci.off_cosx : ci.off_cosy), cs.data(), n * sizeof(float),
+                           cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess && pow2b(ci.nx) && pow2b(ci.ny) && ci.ny <= 8192) {
+            // shared memory of the correlated-noise kernels, set before any graph capture
+            const int c = col_strip_b(ci.nx, ci.ny);
+            noise_csm = std::max(noise_csm, fft_smem_bytes(ci.ny, c));
+            noise_rsm = std::max(noise_rsm, fft_smem_bytes(ci.nx, 1));
         }
     }
     for (int r = 0; r < count && e == cudaSuccess; ++r) {
@@ -680,6 +772,10 @@ int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* see
     }
     if (e == cudaSuccess) e = cudaMemcpy(cls_ptr(b, b->L.off_fbar), b->fbar, sizeof(double) * Q, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = prepare_ensemble_kernels();
+    if (e == cudaSuccess && noise_csm > 0)
+        e = cudaFuncSetAttribute(batch_noise_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)noise_csm);
+    if (e == cudaSuccess && noise_rsm > 0)
+        e = cudaFuncSetAttribute(batch_noise_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)noise_rsm);
     if (e == cudaSuccess && build_launches(b, 0, &b->launches) != LB_OK) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         if (b->owns) cudaFree(b->ws);
@@ -708,19 +804,31 @@ int lb_batch_set_stream(lb_batch* b, void* stream) {
 int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, double tau_s, double tau_b,
                         double tau_ghost, int noise_mode) {
     if (!b || replica < -1 || replica >= b->count) return LB_EINVAL;
-    if (noise_mode == LB_NOISE_FULL)
-        return bfail(b, LB_EINVAL, "correlated noise is not available for batched replicas");
     const int lo = replica < 0 ? 0 : replica, hi = replica < 0 ? b->count : replica + 1;
     for (int r = lo; r < hi; ++r) {
         const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
+        if (noise_mode == LB_NOISE_FULL &&
+            (!pow2b(ci.nx) || !pow2b(ci.ny) || ci.ny > 8192 || col_strip_b(ci.nx, ci.ny) < 2))
+            return bfail(b, LB_EINVAL, "correlated noise needs nx and ny powers of two and ny <= 8192");
         int rc = lb_check_params(ci.nx, ci.ny, b->rho0, b->cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode);
         if (rc != LB_OK) return bfail(b, rc, "parameters rejected (see lb_check_params)");
+    }
+    for (int r = lo; r < hi; ++r) {
         fill_rep_record(b->rho0, b->cs2, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode, &b->recs[r]);
         b->mode[r] = noise_mode;
         b->have_params[r] = true;
         int u = upload_rec(b, r);
         if (u != LB_OK) return u;
     }
+    // classes that now need (or no longer need) the correlated-noise kernels
+    bool changed = false;
+    for (auto& ci : b->L.classes) {
+        bool any = false;
+        for (int r : ci.members) any = any || b->recs[r].mode == 2;
+        changed = changed || any != ci.any_full;
+        ci.any_full = any;
+    }
+    if (changed && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
     BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
     return LB_OK;
 }

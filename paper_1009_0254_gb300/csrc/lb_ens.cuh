@@ -13,7 +13,8 @@ namespace lbf {
 struct RepRec {
     float rho0, cs2m, kappa, lb, ls, lq, le;
     float L44, L49, L94, L99, s5, s6, s7;
-    int mode;                 // 0 no noise, 1 uncorrelated noise
+    float a44, b44, a49, b49, a99, b99;   // Xi(k) of the (4,9) block = a + b s(k) (correlated noise)
+    int mode;                 // 0 no noise, 1 uncorrelated noise, 2 correlated noise
     uint32_t k0, k1;          // Philox key = the replica's seed
     long long toff;           // time = K + toff
 };
@@ -27,7 +28,7 @@ struct TileArgs {
 };
 
 // The record of one lattice as collide_node reads it, for its time t; *mode = 0 without
-// noise, 1 with uncorrelated noise.
+// noise, 1 with uncorrelated noise, 2 with correlated noise (xi_4, xi_9 read from a field).
 __device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t, int* mode) {
     TileArgs a;
     a.rho0 = __ldg(&rp->rho0); a.cs2m = __ldg(&rp->cs2m); a.kappa = __ldg(&rp->kappa);
@@ -45,7 +46,7 @@ __device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t
 // density tile R (with its one-node ring).
 template <int MODE, int TX, int TY, int NT>
 __device__ __forceinline__ void tile_nodes(const TileArgs& a, const float* S, const float* R, const Grid& g, int x0,
-                                           int y0, float* dst) {
+                                           int y0, float* dst, const float2* __restrict__ xi49) {
     using TT = TmaTile<TX, TY, float>;
     static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
 #pragma unroll
@@ -64,8 +65,10 @@ __device__ __forceinline__ void tile_nodes(const TileArgs& a, const float* S, co
         r.NE = R[rc + TT::RW + 1]; r.NW = R[rc + TT::RW - 1];
         r.SE = R[rc - TT::RW + 1]; r.SW = R[rc - TT::RW - 1];
         const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
+        float2 z = make_float2(0.f, 0.f);
+        if (MODE == 2) z = xi49[(long long)y * g.nx + x];
         float o[Q];
-        collide_node<MODE>(a, f, r, node, make_float2(0.f, 0.f), o);
+        collide_node<MODE>(a, f, r, node, z, o);
         store9(dst, g.plane, g, x, y, o);
     }
 }

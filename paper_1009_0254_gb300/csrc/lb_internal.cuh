@@ -91,15 +91,17 @@ struct StepArgs {
 };
 
 // k-space synthesis of the correlated (4,9) noise: Xi_ab(k) = a_ab + b_ab s(k) with s
-// the lattice k^2 of [GACV] Appendix B, coefficients computed on the host in FP64.
-struct NoiseGenArgs {
+// the lattice k^2 of [GACV] Appendix B, coefficients computed on the host in FP64.  Key is
+// the Philox key form (RoundKeys precomputed, or KeyPair expanded on the fly).
+template <typename Key>
+struct NoiseGenT {
     float a44, b44, a49, b49, a99, b99;
     int eig;             // 0: Cholesky factor of the (4,9) block, 1: eigen-decomposition factor
     const float* cosx;   // cos(2 pi m / nx), m < nx
     const float* cosy;   // cos(2 pi m / ny), m < ny
     int nx, ny;
     uint32_t t_lo, t_hi;
-    RoundKeys rk;
+    Key rk;
 };
 
 // ---------------------------------------------------------------------------
@@ -120,6 +122,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk) {
 struct KeyPair {
     uint32_t k0, k1;
 };
+
+using NoiseGenArgs = NoiseGenT<RoundKeys>;   // single lattice: round keys precomputed
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeyPair& kp) {
     uint32_t k0 = kp.k0, k1 = kp.k1;
@@ -261,4 +265,8 @@ int sums_partial_count();
 void set_context_free_error(const std::string& msg);
 // rest populations fbar_i of a lattice at density rho0 with p0 = cs2 rho (Table II at u = 0)
 void rest_populations(double rho0, double cs2, double fbar[Q]);
+// coefficients of the k-dependent (4,9) block of Xi(k), Eq. (noise-yeo), as functions of the
+// lattice k^2 s: {a44, b44, a49, b49, a99, b99} with Xi_ab = a_ab + b_ab s
+void noise_coefficients(double rho0, double cs2, double kT, double kappa, double tau_s, double tau_b,
+                        double tau_ghost, double out[6]);
 }  // namespace lbf

@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
 
         int mode;
         const TileArgs a = load_tile_args(p.recs + slot, sl, &mode);
-        if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, x0, y0, dst);
-        else tile_nodes<0, TX, TY, NT>(a, S, R, g, x0, y0, dst);
+        if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
+        else tile_nodes<0, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
         __syncthreads();
         if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

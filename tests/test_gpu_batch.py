@@ -165,7 +165,7 @@ def test_batch_api_errors():
         ens.step(1)
     assert e.value.code == lbf.LB_ESTATE
     with pytest.raises(lbf.LBError) as e:
-        ens.set_params(0, 1e-4, 0.01, 1.0, 1.0, 1.0, lbf.LB_NOISE_FULL)
+        ens.set_params(1, 1e-4, 0.01, 1.0, 1.0, 1.0, lbf.LB_NOISE_FULL)    # 24 x 8: not powers of two
     assert e.value.code == lbf.LB_EINVAL
     with pytest.raises(lbf.LBError) as e:
         ens.set_params(0, 1e-4, 0.01, 0.5, 1.0, 1.0, lbf.LB_NOISE_LW)
@@ -185,3 +185,41 @@ def test_batch_api_errors():
     assert lbf.lb_batch_launch_count(ens.b) == 5      # one persistent launch per step for both classes
     with pytest.raises(lbf.LBError):
         lbf.Ensemble([(1, 16)], [1])
+
+
+FULL_MIX = [
+    ((32, 32), 41, (1.0e-4, 0.01, 1.0, 1.0, 1.0), lbf.LB_NOISE_FULL),
+    ((64, 32), 42, (2.0e-4, 0.03, 0.8, 1.1, 0.9), lbf.LB_NOISE_FULL),
+    ((32, 32), 43, (1.5e-4, 0.02, 0.7, 1.0, 1.2), lbf.LB_NOISE_LW),
+    ((16, 64), 44, (1.0e-4, 0.05, 1.0, 1.0, 1.0), lbf.LB_NOISE_FULL),
+    ((33, 17), 45, (1.0e-4, 0.01, 1.0, 1.0, 1.0), lbf.LB_NOISE_DIAG),
+    ((32, 32), 46, (8.0e-5, 0.04, 0.9, 1.0, 1.0), lbf.LB_NOISE_FULL),
+]
+
+
+def test_correlated_noise_replicas_match_oracle():
+    ens = _ensemble(FULL_MIX)
+    ens.step(11)
+    ens.step(39, graph_steps=13)
+    for r, (size, seed, params, mode) in enumerate(FULL_MIX):
+        o = oracle.Lattice(*size, seed=seed)
+        o.set_params(*params, mode)
+        o.f = _initial(*size, params, seed=seed)
+        o.t = r
+        o.step(50)
+        err = np.abs(ens.populations(r) - o.f).max()
+        assert err <= TOL, (r, size, mode, err)
+
+
+def test_correlated_replica_alone_equals_in_mix_and_single_path():
+    mixed = _ensemble(FULL_MIX)
+    mixed.step(30, graph_steps=10)
+    size, seed, params, mode = FULL_MIX[1]
+    alone = _ensemble([FULL_MIX[1]], t0=1)
+    alone.step(30, graph_steps=10)
+    assert np.array_equal(alone.populations(0), mixed.populations(1))
+    L = lbf.Lattice(*size, seed=seed)
+    L.set_params(*params, mode)
+    L.set_populations(_initial(*size, params, seed=seed), t=1)
+    L.step(30)
+    assert np.abs(L.populations() - mixed.populations(1)).max() <= 1e-6

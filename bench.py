@@ -305,6 +305,17 @@ def batched_variant(lbf, torch, steps=2000, graph_steps=100, plain_steps=20):
     ms = ev0.elapsed_time(ev1)
     launches = lbf.lb_batch_launch_count(ens.b) - k0
     tx, ty, nt, _ = lbf.lb_batch_tuning(ens.b)
+    # the same ensemble with the correlated (full FDT) noise of Sec. IV
+    for r in range(len(sizes)):
+        ens.set_params(r, float(kT[r]), 0.01, 0.8, 1.0, 1.0, lbf.LB_NOISE_FULL)
+    fsteps = max(1, steps // 4)
+    ens.step(graph_steps, graph_steps=graph_steps)
+    torch.cuda.synchronize()
+    ev0.record(ens.stream)
+    ens.step(fsteps, graph_steps=graph_steps)
+    ev1.record(ens.stream)
+    torch.cuda.synchronize()
+    fms = ev0.elapsed_time(ev1)
     ens.close()
     del ens
     # plain path: the same lattices as separate contexts, one step launch per lattice
@@ -333,6 +344,9 @@ def batched_variant(lbf, torch, steps=2000, graph_steps=100, plain_steps=20):
             "value": value, "unit": "MLUPS", "ms_per_step": ms / steps,
             "launch": "one persistent launch per step, CUDA graph of %d steps" % graph_steps,
             "autotuned_tile": [tx, ty, nt], "gpu_launches": launches,
+            "correlated_noise": {"value": nodes * fsteps / (fms / 1e3) / 1e6, "unit": "MLUPS",
+                                 "ms_per_step": fms / fsteps, "steps": fsteps,
+                                 "how": "same replicas with full FDT noise (k-space synthesis per replica)"},
             "plain_path": {"value": plain, "unit": "MLUPS", "steps": plain_steps,
                            "how": "512 lb_step calls per step, one context per lattice"},
             "speedup_vs_plain": value / plain,

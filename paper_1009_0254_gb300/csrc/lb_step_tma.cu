@@ -1,10 +1,9 @@
 // lb_step_tma.cu -- the fused fluctuating D2Q9 step, TMA-staged and persistent.
 //
 // Same arithmetic as lb_step.cu (collide_node), different data movement:
-//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles (32 x 16
-//     by default), in
-//     row-major tile order, so the tiles in flight form a band whose halo rows are
-//     still in L2 when the neighbouring tile reads them;
+//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles (32 x 16 by
+//     default) in row-major tile order, so the tiles in flight form a band whose halo rows
+//     are still in L2 when the neighbouring tile reads them;
 //   * for each tile one thread issues nine 3D TMA loads (cp.async.bulk.tensor), one per
 //     population plane, of the box [x0 - 4, x0 + TX + 4) x [y0 - 1 - cy_i, y0 + TY + 1 - cy_i)
 //     into shared memory; the y offset of plane i absorbs its streaming shift, so node
@@ -15,9 +14,12 @@
 //     collides and stores its nine post-collision deviations (and periodic ghosts)
 //     directly from registers with coalesced stores.  Nodes beyond a ragged edge of the
 //     lattice take part in the density pass (their values are never used) but not in the
-//     collision pass.
+//     collision pass.  For correlated noise and FP16 storage the pulled populations stay in
+//     registers across the density barrier and the stage is refilled right after it; for
+//     uncorrelated noise in FP32 the nodes pull again and the stage is refilled at the end
+//     of the tile (the faster of the two in each case, measured).
 // Waits on the mbarriers are bounded by the global timer; a CTA that gives up sets the
-// error word and returns.
+// error word, gives its loads in flight a bounded chance to land, and returns.
 #include <cuda.h>
 
 #include "lb_collide.cuh"

@@ -49,6 +49,9 @@ extern "C" {
 #define LB_FP16DEV 1       /* FP16 deviations, stored as (f_i - fbar_i) / w_i (36 bytes per node update);
                               arithmetic stays FP32; rounding to FP16 each step makes the mass
                               conserved only to that rounding */
+#define LB_FP64 2          /* FP64 deviations and FP64 arithmetic throughout the step (the
+                              correlated noise too, which then needs ny <= 4096); the sampled
+                              spectra are FP32 transforms accumulated in FP64 */
 
 /* noise modes, [GACV] Sec. IV */
 #define LB_NOISE_OFF 0     /* deterministic (kT ignored) */

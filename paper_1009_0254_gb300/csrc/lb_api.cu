@@ -29,9 +29,12 @@ bool is_pow2(int v) { return v >= 2 && (v & (v - 1)) == 0; }
 
 struct WsLayout {
     size_t pop[2], z1, z2, twx, twy, cosx, cosy, bins, counts, bin16, partial, sums3, fbar, err, total;
+    size_t twxd, twyd, cosxd, cosyd;   // FP64 storage: FP64 tables of the correlated noise
 };
 
-int elem_size(int precision) { return precision == LB_FP16DEV ? 2 : (precision == LB_FP32 ? 4 : 0); }
+int elem_size(int precision) {
+    return precision == LB_FP16DEV ? 2 : (precision == LB_FP32 ? 4 : (precision == LB_FP64 ? 8 : 0));
+}
 
 bool make_grid(int nx, int ny, int esize, Grid* g) {
     if (nx < 2 || ny < 2 || nx > (1 << 16) || ny > (1 << 16) || esize <= 0) return false;
@@ -52,7 +55,8 @@ WsLayout make_layout(const Grid& g, int esize) {
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     L.pop[0] = take((size_t)Q * g.plane * esize);
     L.pop[1] = take((size_t)Q * g.plane * esize);
-    L.z1 = take((size_t)n * sizeof(float2));
+    // z1 holds the correlated noise (complex, FP64 with FP64 storage) and spectra scratch
+    L.z1 = take((size_t)n * (esize == 8 ? sizeof(double2) : sizeof(float2)));
     L.z2 = take((size_t)n * sizeof(float2));
     L.twx = take((size_t)g.nx * sizeof(float2));
     L.twy = take((size_t)g.ny * sizeof(float2));
@@ -65,6 +69,13 @@ WsLayout make_layout(const Grid& g, int esize) {
     L.sums3 = take(3 * sizeof(double));
     L.fbar = take(Q * sizeof(double));
     L.err = take(sizeof(int));
+    L.twxd = L.twyd = L.cosxd = L.cosyd = 0;
+    if (esize == 8) {
+        L.twxd = take((size_t)g.nx * sizeof(double2));
+        L.twyd = take((size_t)g.ny * sizeof(double2));
+        L.cosxd = take((size_t)g.nx * sizeof(double));
+        L.cosyd = take((size_t)g.ny * sizeof(double));
+    }
     L.total = off;
     return L;
 }
@@ -208,6 +219,10 @@ struct lb_ctx {
     double kT = 0, kappa = 0, tau_s = 1, tau_b = 1, tau_g = 1;
     StepArgs sa{};
     NoiseGenArgs ga{};
+    StepArgsD sad{};                 // FP64 storage
+    NoiseGenArgsD gad{};
+    double2 *twxd = nullptr, *twyd = nullptr;
+    double *cosxd = nullptr, *cosyd = nullptr;
     // sampling
     int every = 0, nbins = 0;
     long long nsamples = 0;
@@ -292,7 +307,7 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
     *out = nullptr;
     const int es = elem_size(precision);
-    if (es == 0) return fail(nullptr, LB_EINVAL, "precision must be LB_FP32 or LB_FP16DEV");
+    if (es == 0) return fail(nullptr, LB_EINVAL, "precision must be LB_FP32, LB_FP16DEV or LB_FP64");
     Grid g;
     if (!make_grid(nx, ny, es, &g)) return fail(nullptr, LB_EINVAL, "nx and ny must lie in [2, 65536]");
     if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail(nullptr, LB_EINVAL, "rho0 must be positive");
@@ -338,7 +353,9 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
         const char* v = std::getenv("LBFLUCT_STEP_KERNEL");
         c->use_sweep = v && (std::strcmp(v, "sweep") == 0 || std::strcmp(v, "sweep6") == 0) && sweep_fits(g);
         c->sweep_occ6 = v && std::strcmp(v, "sweep6") == 0;
-        const bool want_tma = !(v && std::strcmp(v, "simple") == 0) && !c->use_sweep;
+        if (precision == LB_FP64) c->use_sweep = false;
+        // FP64 storage runs the plain kernel (its arithmetic is FP64 throughout)
+        const bool want_tma = !(v && std::strcmp(v, "simple") == 0) && !c->use_sweep && precision != LB_FP64;
         const char* tv = std::getenv("LBFLUCT_TMA_TILE");
         c->tma_tile = tv ? std::atoi(tv) : 0;
         if (c->tma_tile < 0 || c->tma_tile >= tma_tile_count()) c->tma_tile = 0;
@@ -362,6 +379,25 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     };
     cudaError_t e = upload(nx, c->twx, c->cosx);
     if (e == cudaSuccess) e = upload(ny, c->twy, c->cosy);
+    if (e == cudaSuccess && precision == LB_FP64) {
+        c->twxd = (double2*)(c->ws + c->L.twxd);
+        c->twyd = (double2*)(c->ws + c->L.twyd);
+        c->cosxd = (double*)(c->ws + c->L.cosxd);
+        c->cosyd = (double*)(c->ws + c->L.cosyd);
+        std::vector<double2> twd(std::max(nx, ny));
+        std::vector<double> csd(std::max(nx, ny));
+        for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+            const int n = which == 0 ? nx : ny;
+            for (int k = 0; k < n; ++k) {
+                const double a = 2.0 * M_PI * (double)k / n;
+                twd[k] = make_double2(std::cos(a), -std::sin(a));
+                csd[k] = std::cos(a);
+            }
+            e = cudaMemcpy(which == 0 ? c->twxd : c->twyd, twd.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(which == 0 ? c->cosxd : c->cosyd, csd.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemcpy(c->fbar_dev, c->fbar, sizeof(double) * Q, cudaMemcpyHostToDevice);
     // rest state: every deviation (and ghost) zero
     if (e == cudaSuccess) e = cudaMemset(c->pop[0], 0, (size_t)Q * g.plane * es);
@@ -377,6 +413,10 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     c->sa.rho0 = (float)rho0;
     c->sa.cs2m = (float)(cs2 - SIGMA_S2);
     c->sa.rk = make_round_keys(seed);
+    c->sad.g = g;
+    c->sad.rho0 = rho0;
+    c->sad.cs2m = cs2 - SIGMA_S2;
+    c->sad.rk = c->sa.rk;
     *out = c;
     return LB_OK;
 }
@@ -403,6 +443,8 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     if (r != LB_OK) return fail(c, r, why);
     if (mode == LB_NOISE_FULL && kT > 0.0 && (!c->pow2 || c->ny > 8192))
         return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two and ny <= 8192");
+    if (mode == LB_NOISE_FULL && kT > 0.0 && c->precision == LB_FP64 && noise_strip_d(c->nx, c->ny) < 2)
+        return fail(c, LB_EINVAL, "correlated noise with FP64 storage needs ny <= 4096");
     c->kT = kT; c->kappa = kappa; c->tau_s = tau_s; c->tau_b = tau_b; c->tau_g = tau_ghost;
     c->noise_mode = mode;
     c->warnings = (kT >= 0.1 * SIGMA_S2 * c->rho0) ? LB_WARN_LOW_MACH : 0;   // Eq. (low-mach)
@@ -434,6 +476,19 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     ga.cosx = c->cosx; ga.cosy = c->cosy; ga.nx = c->nx; ga.ny = c->ny;
     ga.eig = c->factor == LB_FACTOR_EIGEN ? 1 : 0;
     ga.rk = a.rk;
+    // the same in FP64 for FP64 storage (no rounding of the parameters to FP32)
+    StepArgsD& d = c->sad;
+    d.kappa = kappa;
+    d.lb = -1.0 / tau_b; d.ls = -1.0 / tau_s; d.lq = -1.0 / tau_ghost; d.le = -1.0 / tau_ghost;
+    d.L44 = L44; d.L49 = L49; d.L94 = L94; d.L99 = L99;
+    d.s5 = std::sqrt(std::fmax(nc.x55, 0.0));
+    d.s6 = std::sqrt(std::fmax(nc.x66, 0.0));
+    d.s7 = std::sqrt(std::fmax(nc.x77, 0.0));
+    NoiseGenArgsD& gd = c->gad;
+    gd.a44 = nc.a44; gd.b44 = nc.b44; gd.a49 = nc.a49; gd.b49 = nc.b49; gd.a99 = nc.a99; gd.b99 = nc.b99;
+    gd.cosx = c->cosxd; gd.cosy = c->cosyd; gd.nx = c->nx; gd.ny = c->ny;
+    gd.eig = ga.eig;
+    gd.rk = a.rk;
     c->have_params = true;
     return LB_OK;
 }
@@ -482,6 +537,42 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two (radix-2 FFT)");
     for (int64_t k = 0; k < nsteps; ++k) {
         const uint32_t tlo = (uint32_t)((uint64_t)c->t & 0xffffffffu), thi = (uint32_t)((uint64_t)c->t >> 32);
+        if (c->precision == LB_FP64) {
+            // FP64 storage: FP64 noise synthesis and the plain kernel in FP64
+            if (kmode == 2) {
+                NoiseGenArgsD gd = c->gad;
+                gd.t_lo = tlo; gd.t_hi = thi;
+                CK(c, launch_noise49_d(reinterpret_cast<double2*>(c->z1), gd, c->twxd, c->twyd, c->stream),
+                   "correlated noise");
+                c->kernels += 2;
+            }
+            StepArgsD d = c->sad;
+            d.src = c->pop[c->cur];
+            d.dst = c->pop[c->cur ^ 1];
+            d.xi49 = reinterpret_cast<const double2*>(c->z1);
+            d.t_lo = tlo; d.t_hi = thi;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (c->timing) {
+                int r = record_timing(c, &e0, &e1);
+                if (r != LB_OK) return r;
+                CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
+            }
+            CK(c, launch_step_simple_d(d, kmode, c->stream), "step kernel launch");
+            c->kernels += 1;
+            if (c->timing) {
+                CK(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
+                c->launches_acc++;
+            }
+            c->cur ^= 1;
+            c->t++;
+            if (c->every > 0 && c->t % c->every == 0) {
+                CK(c, launch_stats_sample(c->pop[c->cur], c->precision, c->g, c->z1, c->z2, c->twx, c->twy, c->bin16,
+                                          c->bins, c->nbins, c->stream), "spectra sample");
+                c->kernels += 6;
+                c->nsamples++;
+            }
+            continue;
+        }
         if (kmode == 2) {
             NoiseGenArgs ga = c->ga;
             ga.t_lo = tlo; ga.t_hi = thi;
@@ -514,8 +605,8 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         c->cur ^= 1;
         c->t++;
         if (c->every > 0 && c->t % c->every == 0) {
-            CK(c, launch_stats_sample(c->pop[c->cur], c->fp16, c->g, c->z1, c->z2, c->twx, c->twy, c->bin16, c->bins,
-                                      c->nbins, c->stream), "spectra sample");
+            CK(c, launch_stats_sample(c->pop[c->cur], c->precision, c->g, c->z1, c->z2, c->twx, c->twy, c->bin16,
+                                      c->bins, c->nbins, c->stream), "spectra sample");
             c->kernels += 6;
             c->nsamples++;
         }
@@ -539,7 +630,7 @@ int lb_set_populations(lb_ctx* c, const double* f, int loc, int64_t t) {
             CK(c, cudaMemcpyAsync(stage, src, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream), "H2D");
             src = stage;
         }
-        CK(c, launch_set_plane(src, c->pop[c->cur], c->fp16, c->g, i, c->fbar[i], c->stream), "set populations");
+        CK(c, launch_set_plane(src, c->pop[c->cur], c->precision, c->g, i, c->fbar[i], c->stream), "set populations");
         c->kernels += 1;
     }
     CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
@@ -553,7 +644,7 @@ int lb_get_populations(lb_ctx* c, double* f, int loc) {
     double* stage = (double*)c->z1;
     for (int i = 0; i < Q; ++i) {
         double* dst = (loc == LB_HOST) ? stage : f + (long long)i * c->n;
-        CK(c, launch_get_plane(c->pop[c->cur], c->fp16, c->g, i, c->fbar[i], dst, c->stream), "get populations");
+        CK(c, launch_get_plane(c->pop[c->cur], c->precision, c->g, i, c->fbar[i], dst, c->stream), "get populations");
         c->kernels += 1;
         if (loc == LB_HOST)
             CK(c, cudaMemcpyAsync(f + (long long)i * c->n, stage, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
@@ -570,7 +661,7 @@ int lb_moments(lb_ctx* c, double* m, int loc, double sums[3]) {
         double* stage = (double*)c->z1;
         for (int a = 0; a < Q; ++a) {
             double* dst = (loc == LB_HOST) ? stage : m + (long long)a * c->n;
-            CK(c, launch_moment(c->pop[c->cur], c->fp16, c->g, a, c->fbar_dev, dst, c->stream), "moments");
+            CK(c, launch_moment(c->pop[c->cur], c->precision, c->g, a, c->fbar_dev, dst, c->stream), "moments");
             c->kernels += 1;
             if (loc == LB_HOST)
                 CK(c, cudaMemcpyAsync(m + (long long)a * c->n, stage, sizeof(double) * c->n, cudaMemcpyDeviceToHost,
@@ -578,7 +669,7 @@ int lb_moments(lb_ctx* c, double* m, int loc, double sums[3]) {
         }
     }
     if (sums) {
-        CK(c, launch_sums(c->pop[c->cur], c->fp16, c->g, c->fbar_dev, c->partial, c->sums3, c->stream), "sums");
+        CK(c, launch_sums(c->pop[c->cur], c->precision, c->g, c->fbar_dev, c->partial, c->sums3, c->stream), "sums");
         c->kernels += 2;
         CK(c, cudaMemcpyAsync(sums, c->sums3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
     }

@@ -9,70 +9,77 @@
 namespace lbf {
 
 // density deviation with one fixed summation order (used for a node and for the ring)
-__device__ __forceinline__ float drho_of(const float f[Q]) {
-    const float sa = (f[1] + f[3]) + (f[2] + f[4]);
-    const float sd = (f[5] + f[7]) + (f[6] + f[8]);
+template <typename R>
+__device__ __forceinline__ R drho_of(const R f[Q]) {
+    const R sa = (f[1] + f[3]) + (f[2] + f[4]);
+    const R sd = (f[5] + f[7]) + (f[6] + f[8]);
     return f[0] + sa + sd;
 }
 
 // Density deviations around the node: C centre, E/W = x +- 1, N/S = y +- 1.
-struct Nbr {
-    float C, E, W, N, S, NE, NW, SE, SW;
+template <typename R>
+struct NbrT {
+    R C, E, W, N, S, NE, NW, SE, SW;
 };
+using Nbr = NbrT<float>;
 
 // MODE 0: no noise; 1: uncorrelated (long-wavelength or diagonal); 2: correlated
 // (xi_4, xi_9 given in xi49).  A carries the relaxation and noise factors, the time and
 // the Philox key (StepArgs with precomputed round keys, or a per-replica record): Args.
-template <int MODE, typename Args>
-__device__ __forceinline__ void collide_node(const Args& a, const float f[Q], const Nbr& r, uint32_t node,
-                                             float2 xi49, float o[Q]) {
+// R is the arithmetic type (float, or double for FP64 storage); every constant is an
+// exact rational or rounded in R.
+template <int MODE, typename Args, typename R, typename X2>
+__device__ __forceinline__ void collide_node(const Args& a, const R f[Q], const NbrT<R>& r, uint32_t node,
+                                             X2 xi49, R o[Q]) {
+    const R c6 = R(1) / R(6), c3 = R(1) / R(3), c12 = R(1) / R(12);
     // Appendix B: sum_{i != 1} w_i [rho(r+c_i) + rho(r-c_i) - 2 rho(r)] / sigma_s^2
-    const float lap = (4.0f * ((r.E + r.W) + (r.N + r.S)) + ((r.NE + r.SW) + (r.NW + r.SE)) - 20.0f * r.C) *
-                      (1.0f / 6.0f);
+    const R lap = (R(4) * ((r.E + r.W) + (r.N + r.S)) + ((r.NE + r.SW) + (r.NW + r.SE)) - R(20) * r.C) * c6;
     // d_alpha rho = 3 sum_i w_i c_i,alpha rho(r + c_i)
-    const float gx = (r.E - r.W) * (1.0f / 3.0f) + ((r.NE - r.SW) + (r.SE - r.NW)) * (1.0f / 12.0f);
-    const float gy = (r.N - r.S) * (1.0f / 3.0f) + ((r.NE - r.SW) + (r.NW - r.SE)) * (1.0f / 12.0f);
+    const R gx = (r.E - r.W) * c3 + ((r.NE - r.SW) + (r.SE - r.NW)) * c12;
+    const R gy = (r.N - r.S) * c3 + ((r.NE - r.SW) + (r.NW - r.SE)) * c12;
 
     // moments of the deviations (rows of T, Eq. Tmat)
-    const float sa = (f[1] + f[3]) + (f[2] + f[4]);
-    const float sd = (f[5] + f[7]) + (f[6] + f[8]);
-    const float drho = f[0] + sa + sd;
-    const float ax = f[1] - f[3], ay = f[2] - f[4];
-    const float dx = (f[5] - f[7]) + (f[8] - f[6]);
-    const float dy = (f[5] - f[7]) + (f[6] - f[8]);
-    const float jx = ax + dx, jy = ay + dy;
-    const float m4 = -2.0f * f[0] + sa + 4.0f * sd;
-    const float m5 = (f[1] + f[3]) - (f[2] + f[4]);
-    const float m6 = (f[5] + f[7]) - (f[6] + f[8]);
-    const float m7 = 2.0f * dx - ax;
-    const float m8 = 2.0f * dy - ay;
-    const float m9 = 2.0f * f[0] - 4.0f * sa + 8.0f * sd;
+    const R sa = (f[1] + f[3]) + (f[2] + f[4]);
+    const R sd = (f[5] + f[7]) + (f[6] + f[8]);
+    const R drho = f[0] + sa + sd;
+    const R ax = f[1] - f[3], ay = f[2] - f[4];
+    const R dx = (f[5] - f[7]) + (f[8] - f[6]);
+    const R dy = (f[5] - f[7]) + (f[6] - f[8]);
+    const R jx = ax + dx, jy = ay + dy;
+    const R m4 = R(-2) * f[0] + sa + R(4) * sd;
+    const R m5 = (f[1] + f[3]) - (f[2] + f[4]);
+    const R m6 = (f[5] + f[7]) - (f[6] + f[8]);
+    const R m7 = R(2) * dx - ax;
+    const R m8 = R(2) * dy - ay;
+    const R m9 = R(2) * f[0] - R(4) * sa + R(8) * sd;
 
     // equilibrium deviations, Table II (p0 = cs2 rho, C_n = 0)
-    const float rho = a.rho0 + drho;
-    const float inv = rcp_approx(rho);
-    const float ux = jx * inv, uy = jy * inv;
-    const float iso = a.cs2m * drho - a.kappa * rho * lap;
-    const float e_eq = 3.0f * (jx * ux + jy * uy) + 6.0f * iso;
-    const float pww_eq = (jx * ux - jy * uy) + a.kappa * (gx * gx - gy * gy);
-    const float pxy_eq = jx * uy + a.kappa * gx * gy;
-    const float eps_eq = -6.0f * iso - 3.0f * a.kappa * (gx * gx + gy * gy);
+    const R rho = a.rho0 + drho;
+    const R inv = recip(rho);
+    const R ux = jx * inv, uy = jy * inv;
+    const R iso = a.cs2m * drho - a.kappa * rho * lap;
+    const R e_eq = R(3) * (jx * ux + jy * uy) + R(6) * iso;
+    const R pww_eq = (jx * ux - jy * uy) + a.kappa * (gx * gx - gy * gy);
+    const R pxy_eq = jx * uy + a.kappa * gx * gy;
+    const R eps_eq = R(-6) * iso - R(3) * a.kappa * (gx * gx + gy * gy);
 
     // noise, Sec. IV
-    float xi4 = 0.f, xi5 = 0.f, xi6 = 0.f, xi7 = 0.f, xi8 = 0.f, xi9 = 0.f;
+    R xi4 = R(0), xi5 = R(0), xi6 = R(0), xi7 = R(0), xi8 = R(0), xi9 = R(0);
     if (MODE != 0) {
         // one Philox draw per node and step: words 0, 1 -> nu_5..nu_8, word 2 -> (nu_4, nu_9)
         const uint4 r0 = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_NODE), a.rk);
-        const float2 g01 = gauss_pair(r0.x);
-        const float2 g23 = gauss_pair(r0.y);
-        xi5 = a.s5 * g01.x;
-        xi6 = a.s6 * g01.y;
-        xi7 = a.s7 * g23.x;
-        xi8 = a.s7 * g23.y;
+        R n5, n6, n7, n8;
+        gauss_word(r0.x, &n5, &n6);
+        gauss_word(r0.y, &n7, &n8);
+        xi5 = a.s5 * n5;
+        xi6 = a.s6 * n6;
+        xi7 = a.s7 * n7;
+        xi8 = a.s7 * n8;
         if (MODE == 1) {
-            const float2 n49 = gauss_pair(r0.z);
-            xi4 = a.L44 * n49.x + a.L49 * n49.y;
-            xi9 = a.L94 * n49.x + a.L99 * n49.y;
+            R n4, n9;
+            gauss_word(r0.z, &n4, &n9);
+            xi4 = a.L44 * n4 + a.L49 * n9;
+            xi9 = a.L94 * n4 + a.L99 * n9;
         } else {
             xi4 = xi49.x;
             xi9 = xi49.y;
@@ -81,30 +88,31 @@ __device__ __forceinline__ void collide_node(const Args& a, const float f[Q], co
 
     // relaxation of the non-conserved modes, Eq. (fluct-lin-lbe), as increments
     // D_a = m*_a - m_a = lambda_a (m_a - m_a^eq) + xi_a (zero for the conserved a = 1..3)
-    const float D4 = a.lb * (m4 - e_eq) + xi4;
-    const float D5 = a.ls * (m5 - pww_eq) + xi5;
-    const float D6 = a.ls * (m6 - pxy_eq) + xi6;
-    const float D7 = a.lq * m7 + xi7;
-    const float D8 = a.lq * m8 + xi8;
-    const float D9 = a.le * (m9 - eps_eq) + xi9;
+    const R D4 = a.lb * (m4 - e_eq) + xi4;
+    const R D5 = a.ls * (m5 - pww_eq) + xi5;
+    const R D6 = a.ls * (m6 - pxy_eq) + xi6;
+    const R D7 = a.lq * m7 + xi7;
+    const R D8 = a.lq * m8 + xi8;
+    const R D9 = a.le * (m9 - eps_eq) + xi9;
 
     // back to populations: f*_i = f_i + w_i sum_{a>=4} T_ai D_a / N_a (Sec. III A)
-    const float d4 = 0.25f * D4, d5 = 2.25f * D5, d6 = 9.0f * D6;
-    const float d7 = 1.5f * D7, d8 = 1.5f * D8, d9 = 0.0625f * D9;
-    const float A = d4 - 4.0f * d9;                 // T_4i - 4 T_9i part of the axis directions
-    const float A1 = A + d5, A2 = A - d5;
-    const float Dd = 4.0f * d4 + 8.0f * d9;         // the same for the diagonals
-    const float D1 = Dd + d6, D2 = Dd - d6;
-    const float P = 2.0f * (d7 + d8), M = 2.0f * (d7 - d8);
-    o[0] = f[0] + (8.0f / 9.0f) * (d9 - d4);
-    o[1] = f[1] + (1.0f / 9.0f) * (A1 - d7);
-    o[2] = f[2] + (1.0f / 9.0f) * (A2 - d8);
-    o[3] = f[3] + (1.0f / 9.0f) * (A1 + d7);
-    o[4] = f[4] + (1.0f / 9.0f) * (A2 + d8);
-    o[5] = f[5] + (1.0f / 36.0f) * (D1 + P);
-    o[6] = f[6] + (1.0f / 36.0f) * (D2 - M);
-    o[7] = f[7] + (1.0f / 36.0f) * (D1 - P);
-    o[8] = f[8] + (1.0f / 36.0f) * (D2 + M);
+    const R d4 = R(0.25) * D4, d5 = R(2.25) * D5, d6 = R(9) * D6;
+    const R d7 = R(1.5) * D7, d8 = R(1.5) * D8, d9 = R(0.0625) * D9;
+    const R A = d4 - R(4) * d9;                    // T_4i - 4 T_9i part of the axis directions
+    const R A1 = A + d5, A2 = A - d5;
+    const R Dd = R(4) * d4 + R(8) * d9;            // the same for the diagonals
+    const R D1 = Dd + d6, D2 = Dd - d6;
+    const R P = R(2) * (d7 + d8), M = R(2) * (d7 - d8);
+    const R w0 = R(8) / R(9), w1 = R(1) / R(9), w5 = R(1) / R(36);
+    o[0] = f[0] + w0 * (d9 - d4);
+    o[1] = f[1] + w1 * (A1 - d7);
+    o[2] = f[2] + w1 * (A2 - d8);
+    o[3] = f[3] + w1 * (A1 + d7);
+    o[4] = f[4] + w1 * (A2 + d8);
+    o[5] = f[5] + w5 * (D1 + P);
+    o[6] = f[6] + w5 * (D2 - M);
+    o[7] = f[7] + w5 * (D1 - P);
+    o[8] = f[8] + w5 * (D2 + M);
 }
 
 }  // namespace lbf

@@ -49,6 +49,25 @@ __global__ void __launch_bounds__(1024) noise_cols_kernel(float2* out, NoiseGenA
     noise_cols_block(out, ga, count, blockIdx.x, twy);
 }
 
+// FP64 storage: the same two passes of the correlated noise in FP64 (rows: one CTA per row).
+__global__ void __launch_bounds__(512) fft_rows_kernel_d(double2* data, int nx, int sign,
+                                                          const double2* __restrict__ twx, double scale) {
+    extern __shared__ __align__(16) unsigned char rows_smem_d[];
+    double2* sm = reinterpret_cast<double2*>(rows_smem_d);
+    double2* rowp = data + (long long)blockIdx.x * nx;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = rowp[j];
+    stockham_fft(sm, nx, ilog2(nx), 1, sign, twx);
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        const double2 v = sm[fpad(j)];
+        rowp[j] = make_double2(v.x * scale, v.y * scale);
+    }
+}
+
+__global__ void __launch_bounds__(512) noise_cols_kernel_d(double2* out, NoiseGenArgsD ga, int count,
+                                                            const double2* __restrict__ twy) {
+    noise_cols_block(out, ga, count, blockIdx.x, twy);
+}
+
 // Column pass over strips of `count` adjacent columns, scaled by `scale` on the way out.
 __global__ void __launch_bounds__(1024) fft_cols_kernel(float2* data, int nx, int ny, int count, int sign,
                                 const float2* __restrict__ twy, float scale) {
@@ -126,6 +145,29 @@ cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* tw
     if (e != cudaSuccess) return e;
     const float scale = (float)(1.0 / sqrt((double)ga.nx * (double)ga.ny));
     return rows_pass(buf, ga.nx, ga.ny, -1, twx, scale, s);
+}
+
+int noise_strip_d(int nx, int ny) {
+    int c = 16;
+    while (c > 1 && (fft_threads(ny, c) > 512 || fft_smem_bytes(ny, c, 16) > 200 * 1024)) c >>= 1;
+    return c > nx ? nx : c;
+}
+
+cudaError_t launch_noise49_d(double2* buf, const NoiseGenArgsD& ga, const double2* twx, const double2* twy,
+                             cudaStream_t s) {
+    const int c = noise_strip_d(ga.nx, ga.ny);
+    if (c < 2) return cudaErrorInvalidValue;
+    const size_t smem = fft_smem_bytes(ga.ny, c, 16);
+    cudaError_t e = cudaFuncSetAttribute(noise_cols_kernel_d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    noise_cols_kernel_d<<<ga.nx / c, fft_threads(ga.ny, c), smem, s>>>(buf, ga, c, twy);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t rsm = fft_smem_bytes(ga.nx, 1, 16);
+    e = cudaFuncSetAttribute(fft_rows_kernel_d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+    if (e != cudaSuccess) return e;
+    fft_rows_kernel_d<<<ga.ny, fft_threads(ga.nx, 1), rsm, s>>>(buf, ga.nx, -1, twx,
+                                                                1.0 / sqrt((double)ga.nx * (double)ga.ny));
+    return cudaGetLastError();
 }
 
 // --- sampled spectra ---------------------------------------------------------------
@@ -249,11 +291,12 @@ cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned short* bin16, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats_sample(const void* pops, int fp16, const Grid& g, float2* z1, float2* z2,
+cudaError_t launch_stats_sample(const void* pops, int storage, const Grid& g, float2* z1, float2* z2,
                                 const float2* twx, const float2* twy, const unsigned short* bin16, double* bins,
                                 int nbins, cudaStream_t s) {
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
-    if (fp16) stats_fields_kernel<__half><<<grd, blk, 0, s>>>(static_cast<const __half*>(pops), g, z1, z2);
+    if (storage == 1) stats_fields_kernel<__half><<<grd, blk, 0, s>>>(static_cast<const __half*>(pops), g, z1, z2);
+    else if (storage == 2) stats_fields_kernel<double><<<grd, blk, 0, s>>>(static_cast<const double*>(pops), g, z1, z2);
     else stats_fields_kernel<float><<<grd, blk, 0, s>>>(static_cast<const float*>(pops), g, z1, z2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

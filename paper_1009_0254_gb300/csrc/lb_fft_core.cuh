@@ -23,20 +23,30 @@ __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 c_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 c_make(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 c_make(double x, double y) { return make_double2(x, y); }
 // multiply by sign * i
-__device__ __forceinline__ float2 c_rot(float2 a, int sign) {
-    return sign < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+template <typename C>
+__device__ __forceinline__ C c_rot(C a, int sign) {
+    return sign < 0 ? c_make(a.y, -a.x) : c_make(-a.y, a.x);
 }
 
-__device__ __forceinline__ void dft2(float2* a) {
-    const float2 t = a[0];
+template <typename C>
+__device__ __forceinline__ void dft2(C* a) {
+    const C t = a[0];
     a[0] = c_add(t, a[1]);
     a[1] = c_sub(t, a[1]);
 }
 
-__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, int sign) {
-    const float2 y0 = c_add(a0, a2), y1 = c_sub(a0, a2);
-    const float2 y2 = c_add(a1, a3), y3 = c_rot(c_sub(a1, a3), sign);
+template <typename C>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3, int sign) {
+    const C y0 = c_add(a0, a2), y1 = c_sub(a0, a2);
+    const C y2 = c_add(a1, a3), y3 = c_rot(c_sub(a1, a3), sign);
     a0 = c_add(y0, y2);
     a2 = c_sub(y0, y2);
     a1 = c_add(y1, y3);
@@ -44,16 +54,18 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
 }
 
 // 8-point DFT by decimation in time: X_k = E_k + W8^k O_k, X_{k+4} = E_k - W8^k O_k.
-__device__ __forceinline__ void dft8(float2* a, int sign) {
-    float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
-    float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+template <typename C>
+__device__ __forceinline__ void dft8(C* a, int sign) {
+    using R = decltype(a[0].x);
+    C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
     dft4(e0, e1, e2, e3, sign);
     dft4(o0, o1, o2, o3, sign);
-    const float h = 0.70710678118654752f;
-    const float s = (float)sign;
-    o1 = c_mul(o1, make_float2(h, s * h));
+    const R h = R(0.70710678118654752440);
+    const R s = (R)sign;
+    o1 = c_mul(o1, c_make(h, s * h));
     o2 = c_rot(o2, sign);
-    o3 = c_mul(o3, make_float2(-h, s * h));
+    o3 = c_mul(o3, c_make(-h, s * h));
     a[0] = c_add(e0, o0); a[4] = c_sub(e0, o0);
     a[1] = c_add(e1, o1); a[5] = c_sub(e1, o1);
     a[2] = c_add(e2, o2); a[6] = c_sub(e2, o2);
@@ -61,8 +73,10 @@ __device__ __forceinline__ void dft8(float2* a, int sign) {
 }
 
 // 16-point DFT by decimation in time over two 8-point halves, W16^k = exp(sign i k pi / 8).
-__device__ __forceinline__ void dft16(float2* a, int sign) {
-    float2 e[8], o[8];
+template <typename C>
+__device__ __forceinline__ void dft16(C* a, int sign) {
+    using R = decltype(a[0].x);
+    C e[8], o[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         e[m] = a[2 * m];
@@ -70,21 +84,21 @@ __device__ __forceinline__ void dft16(float2* a, int sign) {
     }
     dft8(e, sign);
     dft8(o, sign);
-    const float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
-    const float s = (float)sign;
-    const float2 w[8] = {make_float2(1.f, 0.f),  make_float2(c1, s * s1), make_float2(h, s * h),
-                         make_float2(s1, s * c1), make_float2(0.f, s),    make_float2(-s1, s * c1),
-                         make_float2(-h, s * h), make_float2(-c1, s * s1)};
+    const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173), h = R(0.70710678118654752440);
+    const R s = (R)sign;
+    const C w[8] = {c_make(R(1), R(0)), c_make(c1, s * s1), c_make(h, s * h),
+                    c_make(s1, s * c1), c_make(R(0), s),    c_make(-s1, s * c1),
+                    c_make(-h, s * h),  c_make(-c1, s * s1)};
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const float2 t = c_mul(o[k], w[k]);
+        const C t = c_mul(o[k], w[k]);
         a[k] = c_add(e[k], t);
         a[k + 8] = c_sub(e[k], t);
     }
 }
 
-template <int R>
-__device__ __forceinline__ void dft_r(float2* a, int sign) {
+template <int R, typename C>
+__device__ __forceinline__ void dft_r(C* a, int sign) {
     if (R == 2) dft2(a);
     else if (R == 4) dft4(a[0], a[1], a[2], a[3], sign);
     else if (R == 8) dft8(a, sign);
@@ -92,15 +106,15 @@ __device__ __forceinline__ void dft_r(float2* a, int sign) {
 }
 
 // One Stockham stage of radix R; each thread takes up to 16/R work items.
-template <int R>
-__device__ __forceinline__ void stockham_stage(float2* s, int n, int count, int lc, int Ns, int sign,
-                                               const float2* __restrict__ tw) {
+template <int R, typename C>
+__device__ __forceinline__ void stockham_stage(C* s, int n, int count, int lc, int Ns, int sign,
+                                               const C* __restrict__ tw) {
     constexpr int MQ = 16 / R;
     const int items = (n / R) * count;
     const int T = blockDim.x;
     const int stride_in = n / R;
     const int tw_step = n / (Ns * R);
-    float2 v[MQ][R];
+    C v[MQ][R];
 #pragma unroll
     for (int q = 0; q < MQ; ++q) {
         const int w = threadIdx.x + q * T;
@@ -109,9 +123,9 @@ __device__ __forceinline__ void stockham_stage(float2* s, int n, int count, int 
             const int k = j & (Ns - 1);
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                float2 x = s[fpad((j + m * stride_in) * count + c)];
+                C x = s[fpad((j + m * stride_in) * count + c)];
                 if (m > 0 && Ns > 1) {
-                    float2 t = __ldg(&tw[m * k * tw_step]);
+                    C t = tw[m * k * tw_step];
                     if (sign > 0) t.y = -t.y;
                     x = c_mul(x, t);
                 }
@@ -137,8 +151,9 @@ __device__ __forceinline__ void stockham_stage(float2* s, int n, int count, int 
 
 // Full transform of `count` interleaved sequences of length n = 2^log2n (n >= 2) already in
 // shared memory; tw[q] = exp(-2 pi i q / n), q < n.  Needs blockDim.x >= max(1, n/16) * count.
-__device__ __forceinline__ void stockham_fft(float2* s, int n, int log2n, int count, int sign,
-                                             const float2* __restrict__ tw) {
+template <typename C>
+__device__ __forceinline__ void stockham_fft(C* s, int n, int log2n, int count, int sign,
+                                             const C* __restrict__ tw) {
     const int lc = 31 - __clz(count);
     int Ns = 1, left = log2n;
     __syncthreads();
@@ -158,9 +173,9 @@ __host__ __device__ inline int fft_threads(int n, int count) {
     return (t + 31) / 32 * 32;
 }
 
-__host__ __device__ inline size_t fft_smem_bytes(int n, int count) {
+__host__ __device__ inline size_t fft_smem_bytes(int n, int count, int elem_bytes = 8) {
     const long long e = (long long)n * count;
-    return (size_t)(e + (e >> 4) + 1) * 8;
+    return (size_t)(e + (e >> 4) + 1) * elem_bytes;
 }
 
 }  // namespace lbf

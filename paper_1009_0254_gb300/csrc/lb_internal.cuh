@@ -56,6 +56,27 @@ struct Elem<__half> {
     }
 };
 
+// FP64 storage: deviations in FP64, arithmetic in FP64.
+template <>
+struct Elem<double> {
+    static constexpr int XO = 2;
+    static constexpr int GW = 4;
+    __host__ __device__ static __forceinline__ double load(double v, int) { return v; }
+    __host__ __device__ static __forceinline__ double store(double v, int) { return v; }
+};
+
+// arithmetic type of a storage type, and its complex pair
+template <typename T>
+struct Arith {
+    using type = float;
+    using vec2 = float2;
+};
+template <>
+struct Arith<double> {
+    using type = double;
+    using vec2 = double2;
+};
+
 // Philox4x32-10 round keys: round r uses (k0 + r W0, k1 + r W1) mod 2^32, computed once on
 // the host so that every round is two wide multiplies and two three-input XORs.
 struct RoundKeys {
@@ -74,31 +95,34 @@ inline RoundKeys make_round_keys(uint64_t seed) {
     return rk;
 }
 
-// Arguments of the fused step kernel (by value).
-struct StepArgs {
+// Arguments of the fused step kernel (by value), in the arithmetic type R.
+template <typename R>
+struct StepArgsT {
     Grid g;
     const void* __restrict__ src;    // post-collision deviations at t-1 (planes 0..8, storage type)
     void* __restrict__ dst;          // post-collision deviations at t
-    const float2* __restrict__ xi49; // FULL mode: (xi_4, xi_9)(r) for this step, [y][x]
-    float rho0;
-    float cs2m;                      // cs2 - sigma_s^2
-    float kappa;
-    float lb, ls, lq, le;            // lambda_b, lambda_s, lambda_q, lambda_eps
-    float L44, L49, L94, L99;        // factor of the (4,9) block of Xi(0) (L49 = 0: Cholesky)
-    float s5, s6, s7;                // sqrt(Xi_55), sqrt(Xi_66), sqrt(Xi_77) = sqrt(Xi_88)
+    const typename Arith<R>::vec2* __restrict__ xi49;   // FULL mode: (xi_4, xi_9)(r) for this step, [y][x]
+    R rho0;
+    R cs2m;                          // cs2 - sigma_s^2
+    R kappa;
+    R lb, ls, lq, le;                // lambda_b, lambda_s, lambda_q, lambda_eps
+    R L44, L49, L94, L99;            // factor of the (4,9) block of Xi(0) (L49 = 0: Cholesky)
+    R s5, s6, s7;                    // sqrt(Xi_55), sqrt(Xi_66), sqrt(Xi_77) = sqrt(Xi_88)
     uint32_t t_lo, t_hi;
     RoundKeys rk;
 };
+using StepArgs = StepArgsT<float>;
+using StepArgsD = StepArgsT<double>;
 
 // k-space synthesis of the correlated (4,9) noise: Xi_ab(k) = a_ab + b_ab s(k) with s
 // the lattice k^2 of [GACV] Appendix B, coefficients computed on the host in FP64.  Key is
 // the Philox key form (RoundKeys precomputed, or KeyPair expanded on the fly).
-template <typename Key>
+template <typename Key, typename R = float>
 struct NoiseGenT {
-    float a44, b44, a49, b49, a99, b99;
+    R a44, b44, a49, b49, a99, b99;
     int eig;             // 0: Cholesky factor of the (4,9) block, 1: eigen-decomposition factor
-    const float* cosx;   // cos(2 pi m / nx), m < nx
-    const float* cosy;   // cos(2 pi m / ny), m < ny
+    const R* cosx;       // cos(2 pi m / nx), m < nx
+    const R* cosy;       // cos(2 pi m / ny), m < ny
     int nx, ny;
     uint32_t t_lo, t_hi;
     Key rk;
@@ -124,6 +148,7 @@ struct KeyPair {
 };
 
 using NoiseGenArgs = NoiseGenT<RoundKeys>;   // single lattice: round keys precomputed
+using NoiseGenArgsD = NoiseGenT<RoundKeys, double>;   // FP64 storage
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const KeyPair& kp) {
     uint32_t k0 = kp.k0, k1 = kp.k1;
@@ -162,11 +187,42 @@ __device__ __forceinline__ float2 gauss_pair(uint32_t w) {
     return make_float2(-r * __cosf(th), -r * __sinf(th));
 }
 
+// The same pair in FP64 (storage LB_FP64): IEEE log, sqrt and sincos, the form of the
+// definition itself.
+__device__ __forceinline__ double2 gauss_pair_d(uint32_t w) {
+    const double u1 = ((double)(w >> 12) + 0.5) * (1.0 / 1048576.0);
+    const double u2 = ((double)(w & 0xfffu) + 0.5) * (1.0 / 4096.0);
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincos(6.283185307179586476925286766559 * u2, &sn, &cs);
+    return make_double2(r * cs, r * sn);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+// reciprocal in the arithmetic type: hardware approximation in FP32, IEEE in FP64
+__device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// normals of one Philox word in the arithmetic type (same bit layout in both, lb_internal.cuh)
+__device__ __forceinline__ void gauss_word(uint32_t w, float* n0, float* n1) {
+    const float2 g = gauss_pair(w);
+    *n0 = g.x;
+    *n1 = g.y;
+}
+__device__ __forceinline__ void gauss_word(uint32_t w, double* n0, double* n1) {
+    const double2 g = gauss_pair_d(w);
+    *n0 = g.x;
+    *n1 = g.y;
+}
+
+// square root in the arithmetic type: hardware approximation in FP32, IEEE in FP64
+__device__ __forceinline__ float sqrt_fast(float x) { return sqrt_approx(x); }
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
 
 // noise draw tags (fourth counter word)
 constexpr uint32_t TAG_NODE = 0;     // per node: words 0, 1 -> nu_5..nu_8, word 2 -> (nu_4, nu_9)
@@ -204,8 +260,8 @@ __device__ __forceinline__ void store_with_ghosts(T* plane, const Grid& g, int x
 // their corner unless the lattice is narrower than 2 GW or lower than 4 rows; the common
 // case is three predicated stores per plane with offsets formed once per node, the rare
 // one goes through store_with_ghosts.
-template <typename T>
-__device__ __forceinline__ void store9(T* dst, long long P, const Grid& g, int x, int y, const float o[Q]) {
+template <typename T, typename R>
+__device__ __forceinline__ void store9(T* dst, long long P, const Grid& g, int x, int y, const R o[Q]) {
     constexpr int GW = Elem<T>::GW;
     const long long c = g.at(x, y);
     const bool xl = x < GW, xr = x >= g.nx - GW, yb = y < 2, yt = y >= g.ny - 2;
@@ -237,6 +293,7 @@ __device__ __forceinline__ void store9(T* dst, long long P, const Grid& g, int x
 // Launchers implemented in the .cu files (host side).
 namespace lbf {
 cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, int fp16, cudaStream_t s);
+cudaError_t launch_step_simple_d(const StepArgsD& a, int noise_mode, cudaStream_t s);
 cudaError_t launch_step_sweep(const StepArgs& a, int noise_mode, int fp16, int occ6, cudaStream_t s);
 bool sweep_fits(const Grid& g);
 cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile, int fp16,
@@ -246,20 +303,24 @@ int tma_tile_count();
 size_t tensor_map_bytes();
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s);
-cudaError_t launch_stats_sample(const void* pops, int fp16, const Grid& g, float2* z1, float2* z2,
+cudaError_t launch_noise49_d(double2* buf, const NoiseGenArgsD& ga, const double2* twx, const double2* twy,
+                             cudaStream_t s);
+int noise_strip_d(int nx, int ny);
+// storage: 0 FP32, 1 FP16 deviations, 2 FP64 (the spectra themselves are FP32 transforms)
+cudaError_t launch_stats_sample(const void* pops, int storage, const Grid& g, float2* z1, float2* z2,
                                 const float2* twx, const float2* twy, const unsigned short* bin16, double* bins,
                                 int nbins, cudaStream_t s);
 cudaError_t launch_bin_counts(int nx, int ny, int nbins, unsigned short* bin16, unsigned long long* counts,
                               cudaStream_t s);
 cudaError_t launch_fft2d(float2* data, int nx, int ny, int sign, const float2* twx, const float2* twy,
                          float scale, cudaStream_t s);
-cudaError_t launch_set_plane(const double* src, void* pops, int fp16, const Grid& g, int i, double fbar,
+cudaError_t launch_set_plane(const double* src, void* pops, int storage, const Grid& g, int i, double fbar,
                              cudaStream_t s);
-cudaError_t launch_get_plane(const void* pops, int fp16, const Grid& g, int i, double fbar, double* out,
+cudaError_t launch_get_plane(const void* pops, int storage, const Grid& g, int i, double fbar, double* out,
                              cudaStream_t s);
-cudaError_t launch_moment(const void* pops, int fp16, const Grid& g, int a, const double* fbar9, double* out,
+cudaError_t launch_moment(const void* pops, int storage, const Grid& g, int a, const double* fbar9, double* out,
                           cudaStream_t s);
-cudaError_t launch_sums(const void* pops, int fp16, const Grid& g, const double* fbar9, double* partial,
+cudaError_t launch_sums(const void* pops, int storage, const Grid& g, const double* fbar9, double* partial,
                         double* out3, cudaStream_t s);
 int sums_partial_count();
 void set_context_free_error(const std::string& msg);

@@ -31,7 +31,7 @@ __global__ void set_plane_kernel(const double* __restrict__ src, T* plane, Grid 
     xs = xs < 0 ? xs + g.nx : (xs >= g.nx ? xs - g.nx : xs);
     ys = ys < 0 ? ys + g.ny : (ys >= g.ny ? ys - g.ny : ys);
     const double v = src[(long long)ys * g.nx + xs] - fbar;
-    store_with_ghosts(plane, g, x, y, Elem<T>::store((float)v, i));
+    store_with_ghosts(plane, g, x, y, Elem<T>::store((typename Arith<T>::type)v, i));
 }
 
 template <typename T>
@@ -118,19 +118,25 @@ __global__ void sums_final_kernel(const double* __restrict__ partial, double* ou
 
 static dim3 row_grid(const Grid& g, int bx) { return dim3((g.nx + bx - 1) / bx, g.ny); }
 
-cudaError_t launch_set_plane(const double* src, void* pops, int fp16, const Grid& g, int i, double fbar,
+// `storage`: 0 FP32, 1 FP16 deviations, 2 FP64 (the LB_FP32 / LB_FP16DEV / LB_FP64 codes)
+cudaError_t launch_set_plane(const double* src, void* pops, int storage, const Grid& g, int i, double fbar,
                              cudaStream_t s) {
-    if (fp16)
+    if (storage == 1)
         set_plane_kernel<__half><<<row_grid(g, 128), 128, 0, s>>>(src, static_cast<__half*>(pops) + i * g.plane, g, i, fbar);
+    else if (storage == 2)
+        set_plane_kernel<double><<<row_grid(g, 128), 128, 0, s>>>(src, static_cast<double*>(pops) + i * g.plane, g, i, fbar);
     else
         set_plane_kernel<float><<<row_grid(g, 128), 128, 0, s>>>(src, static_cast<float*>(pops) + i * g.plane, g, i, fbar);
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_plane(const void* pops, int fp16, const Grid& g, int i, double fbar, double* out,
+cudaError_t launch_get_plane(const void* pops, int storage, const Grid& g, int i, double fbar, double* out,
                              cudaStream_t s) {
-    if (fp16)
+    if (storage == 1)
         get_plane_kernel<__half><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const __half*>(pops) + i * g.plane, g, i,
+                                                                 fbar, out);
+    else if (storage == 2)
+        get_plane_kernel<double><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const double*>(pops) + i * g.plane, g, i,
                                                                  fbar, out);
     else
         get_plane_kernel<float><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const float*>(pops) + i * g.plane, g, i,
@@ -138,17 +144,25 @@ cudaError_t launch_get_plane(const void* pops, int fp16, const Grid& g, int i, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_moment(const void* pops, int fp16, const Grid& g, int a, const double* fbar9, double* out,
+cudaError_t launch_moment(const void* pops, int storage, const Grid& g, int a, const double* fbar9, double* out,
                           cudaStream_t s) {
-    if (fp16) moment_kernel<__half><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const __half*>(pops), g, a, fbar9, out);
-    else moment_kernel<float><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const float*>(pops), g, a, fbar9, out);
+    if (storage == 1)
+        moment_kernel<__half><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const __half*>(pops), g, a, fbar9, out);
+    else if (storage == 2)
+        moment_kernel<double><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const double*>(pops), g, a, fbar9, out);
+    else
+        moment_kernel<float><<<row_grid(g, 128), 128, 0, s>>>(static_cast<const float*>(pops), g, a, fbar9, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sums(const void* pops, int fp16, const Grid& g, const double* fbar9, double* partial, double* out3,
+cudaError_t launch_sums(const void* pops, int storage, const Grid& g, const double* fbar9, double* partial, double* out3,
                         cudaStream_t s) {
-    if (fp16) sums_kernel<__half><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(static_cast<const __half*>(pops), g, fbar9, partial);
-    else sums_kernel<float><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(static_cast<const float*>(pops), g, fbar9, partial);
+    if (storage == 1)
+        sums_kernel<__half><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(static_cast<const __half*>(pops), g, fbar9, partial);
+    else if (storage == 2)
+        sums_kernel<double><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(static_cast<const double*>(pops), g, fbar9, partial);
+    else
+        sums_kernel<float><<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(static_cast<const float*>(pops), g, fbar9, partial);
     sums_final_kernel<<<1, SUM_THREADS, 0, s>>>(partial, out3);
     return cudaGetLastError();
 }

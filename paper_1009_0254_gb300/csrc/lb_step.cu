@@ -12,7 +12,8 @@
 //   back   f*_i = w_i sum_a T_ai m*_a / N_a                                 (Sec. III A)
 //   store  f*_i(r,t) with its periodic ghost copies.
 // Everything is FP32 on deviations from the rest state fbar_i, which keeps the
-// small fluctuations (~sqrt(kT)) at full relative precision.
+// small fluctuations (~sqrt(kT)) at full relative precision; with FP64 storage the
+// arithmetic is FP64 too (this kernel is the FP64 path).
 #include "lb_collide.cuh"
 
 namespace lbf {
@@ -26,7 +27,8 @@ struct Tile {
 
 // Pulled deviations at (x, y): f_i(x, y) = f*_i(x - cx_i, y - cy_i).
 template <typename T>
-__device__ __forceinline__ void pull9(const T* __restrict__ s, long long P, int pitch, long long c, float f[Q]) {
+__device__ __forceinline__ void pull9(const T* __restrict__ s, long long P, int pitch, long long c,
+                                      typename Arith<T>::type f[Q]) {
     f[0] = Elem<T>::load(s[c], 0);
     f[1] = Elem<T>::load(s[P + c - 1], 1);                   // c = ( 1, 0)
     f[2] = Elem<T>::load(s[2 * P + c - pitch], 2);           // c = ( 0, 1)
@@ -39,9 +41,10 @@ __device__ __forceinline__ void pull9(const T* __restrict__ s, long long P, int 
 }
 
 template <int BX, int BY, int MODE, typename T>
-__global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgsT<typename Arith<T>::type> a) {
     using TL = Tile<BX, BY>;
-    __shared__ float rs[TL::RY][TL::RX];
+    using R = typename Arith<T>::type;
+    __shared__ R rs[TL::RY][TL::RX];
     const Grid g = a.g;
     const T* __restrict__ src = static_cast<const T*>(a.src);
     const long long P = g.plane;
@@ -51,12 +54,12 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
     const bool own = (x < g.nx) && (y < g.ny);
 
     // 1. density on the tile (plus the first column/row past a ragged edge)
-    float f[Q];
+    R f[Q];
     if (x <= g.nx && y <= g.ny) {
         pull9(src, P, g.pitch, g.at(x, y), f);
         rs[ty + 1][tx + 1] = drho_of(f);
     } else {
-        rs[ty + 1][tx + 1] = 0.0f;
+        rs[ty + 1][tx + 1] = R(0);
     }
     // 2. density on the one-node ring around the tile
     const int tid = ty * BX + tx;
@@ -72,9 +75,9 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
             hx = BX; hy = q - 2 * TL::RX - BY;
         }
         const int gx = x0 + hx, gy = y0 + hy;
-        float v = 0.0f;
+        R v = R(0);
         if (gx >= -1 && gx <= g.nx && gy >= -1 && gy <= g.ny) {
-            float h[Q];
+            R h[Q];
             pull9(src, P, g.pitch, g.at(gx, gy), h);
             v = drho_of(h);
         }
@@ -84,16 +87,16 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
     if (!own) return;
 
     // 3.-8. stencil, moments, equilibrium, noise, relaxation, back-transform
-    Nbr r;
+    NbrT<R> r;
     r.C = rs[ty + 1][tx + 1];
     r.E = rs[ty + 1][tx + 2]; r.W = rs[ty + 1][tx];
     r.N = rs[ty + 2][tx + 1]; r.S = rs[ty][tx + 1];
     r.NE = rs[ty + 2][tx + 2]; r.NW = rs[ty + 2][tx];
     r.SE = rs[ty][tx + 2]; r.SW = rs[ty][tx];
     const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
-    float2 z = make_float2(0.f, 0.f);
+    typename Arith<T>::vec2 z{};
     if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
-    float o[Q];
+    R o[Q];
     collide_node<MODE>(a, f, r, node, z, o);
 
     // 9. store (own node plus periodic ghosts)
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgs a) {
 }
 
 template <typename T>
-static void launch_t(const StepArgs& a, int noise_mode, cudaStream_t s) {
+static void launch_t(const StepArgsT<typename Arith<T>::type>& a, int noise_mode, cudaStream_t s) {
     constexpr int BX = 32, BY = 16;
     dim3 block(BX, BY);
     dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY);
@@ -115,6 +118,11 @@ static void launch_t(const StepArgs& a, int noise_mode, cudaStream_t s) {
 cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, int fp16, cudaStream_t s) {
     if (fp16) launch_t<__half>(a, noise_mode, s);
     else launch_t<float>(a, noise_mode, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_simple_d(const StepArgsD& a, int noise_mode, cudaStream_t s) {
+    launch_t<double>(a, noise_mode, s);
     return cudaGetLastError();
 }
 

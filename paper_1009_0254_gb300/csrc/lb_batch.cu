@@ -202,6 +202,11 @@ __global__ void __launch_bounds__(1024) batch_noise_rows_kernel(float2* data, co
     if (__ldg(&recs[blockIdx.x / ny].mode) != 2) return;
     extern __shared__ float2 sm[];
     float2* rowp = data + (long long)blockIdx.x * nx;
+    if (nx >= 256) {
+        stockham_fft_io(sm, nx, 31 - __clz(nx), 1, -1, twx, [&](int e) { return rowp[e]; },
+                        [&](int e, float2 v) { rowp[e] = make_float2(v.x * scale, v.y * scale); });
+        return;
+    }
     for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = rowp[j];
     stockham_fft(sm, nx, 31 - __clz(nx), 1, -1, twx);
     for (int j = threadIdx.x; j < nx; j += blockDim.x) {

@@ -16,25 +16,18 @@ namespace lbf {
 
 __device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
 
-// Row pass, in place, scaled by `scale` on the way out.  One CTA per row.
+// Row pass, in place, scaled by `scale` on the way out.  One CTA per row; rows of 256 and
+// more points read and write global memory in the first and last stage directly.
 __global__ void __launch_bounds__(1024) fft_rows_kernel(float2* data, int nx, int sign, const float2* __restrict__ twx, float scale) {
     extern __shared__ float2 sm[];
     const int log2n = ilog2(nx);
     float2* rowp = data + (long long)blockIdx.x * nx;
-    constexpr int U = 8;                       // loads in flight per thread
-    for (int j0 = threadIdx.x; j0 < nx; j0 += U * blockDim.x) {
-        float2 v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = j0 + u * blockDim.x;
-            v[u] = j < nx ? rowp[j] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int j = j0 + u * blockDim.x;
-            if (j < nx) sm[fpad(j)] = v[u];
-        }
+    if (nx >= 256) {
+        stockham_fft_io(sm, nx, log2n, 1, sign, twx, [&](int e) { return rowp[e]; },
+                        [&](int e, float2 v) { rowp[e] = make_float2(v.x * scale, v.y * scale); });
+        return;
     }
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = rowp[j];
     stockham_fft(sm, nx, log2n, 1, sign, twx);
     for (int j = threadIdx.x; j < nx; j += blockDim.x) {
         const float2 v = sm[fpad(j)];

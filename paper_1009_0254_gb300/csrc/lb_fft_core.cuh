@@ -167,6 +167,106 @@ __device__ __forceinline__ void stockham_fft(C* s, int n, int log2n, int count, 
     else if (left == 1) stockham_stage<2>(s, n, count, lc, Ns, sign, tw);
 }
 
+// The same transform with its first stage reading the input through load(e) (e = element
+// index * count + sequence) instead of from shared memory, and its last stage handing the
+// output to store(e, value) instead of writing it back: two shared-memory passes fewer.
+// Needs n >= 256 (a radix-16 first stage and at least one more); the shared buffer s is
+// only a scratch between the stages.
+template <int R, typename C, typename Load>
+__device__ __forceinline__ void stockham_first(C* s, int n, int count, int lc, int sign, Load load) {
+    constexpr int MQ = 16 / R;
+    const int items = (n / R) * count;
+    const int T = blockDim.x;
+    const int stride_in = n / R;
+    C v[MQ][R];
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+        const int w = threadIdx.x + q * T;
+        if (w < items) {
+            const int c = w & (count - 1), j = w >> lc;
+#pragma unroll
+            for (int m = 0; m < R; ++m) v[q][m] = load((j + m * stride_in) * count + c);
+            dft_r<R>(v[q], sign);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+        const int w = threadIdx.x + q * T;
+        if (w < items) {
+            const int c = w & (count - 1), j = w >> lc;
+#pragma unroll
+            for (int m = 0; m < R; ++m) s[fpad((j * R + m) * count + c)] = v[q][m];
+        }
+    }
+    __syncthreads();
+}
+
+template <int R, typename C, typename Store>
+__device__ __forceinline__ void stockham_last(const C* s, int n, int count, int lc, int sign,
+                                              const C* __restrict__ tw, Store store) {
+    constexpr int MQ = 16 / R;
+    const int Ns = n / R;            // last stage: Ns * R = n, so k = j and the output index is j + m Ns
+    const int items = Ns * count;
+    const int T = blockDim.x;
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+        const int w = threadIdx.x + q * T;
+        if (w < items) {
+            const int c = w & (count - 1), j = w >> lc;
+            C v[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                C x = s[fpad((j + m * Ns) * count + c)];
+                if (m > 0) {
+                    C t = tw[m * j];
+                    if (sign > 0) t.y = -t.y;
+                    x = c_mul(x, t);
+                }
+                v[m] = x;
+            }
+            dft_r<R>(v, sign);
+#pragma unroll
+            for (int m = 0; m < R; ++m) store((j + m * Ns) * count + c, v[m]);
+        }
+    }
+}
+
+template <typename C, typename Load, typename Store>
+__device__ __forceinline__ void stockham_fft_io(C* s, int n, int log2n, int count, int sign,
+                                                const C* __restrict__ tw, Load load, Store store) {
+    const int lc = 31 - __clz(count);
+    stockham_first<16>(s, n, count, lc, sign, load);
+    int Ns = 16, left = log2n - 4;
+    while (left > 4) {
+        stockham_stage<16>(s, n, count, lc, Ns, sign, tw);
+        Ns <<= 4;
+        left -= 4;
+    }
+    if (left == 4) stockham_last<16>(s, n, count, lc, sign, tw, store);
+    else if (left == 3) stockham_last<8>(s, n, count, lc, sign, tw, store);
+    else if (left == 2) stockham_last<4>(s, n, count, lc, sign, tw, store);
+    else stockham_last<2>(s, n, count, lc, sign, tw, store);
+}
+
+// Transform of sequences already in shared memory whose last stage hands the output to
+// store(e, value) instead of writing it back (one shared-memory pass fewer).
+template <typename C, typename Store>
+__device__ __forceinline__ void stockham_fft_out(C* s, int n, int log2n, int count, int sign,
+                                                 const C* __restrict__ tw, Store store) {
+    const int lc = 31 - __clz(count);
+    int Ns = 1, left = log2n;
+    __syncthreads();
+    while (left > 4) {
+        stockham_stage<16>(s, n, count, lc, Ns, sign, tw);
+        Ns <<= 4;
+        left -= 4;
+    }
+    if (left == 4) stockham_last<16>(s, n, count, lc, sign, tw, store);
+    else if (left == 3) stockham_last<8>(s, n, count, lc, sign, tw, store);
+    else if (left == 2) stockham_last<4>(s, n, count, lc, sign, tw, store);
+    else stockham_last<2>(s, n, count, lc, sign, tw, store);
+}
+
 __host__ __device__ inline int fft_threads(int n, int count) {
     int t = (n >= 16 ? n / 16 : 1) * count;
     if (t < 32) t = 32;

@@ -116,12 +116,10 @@ __device__ __forceinline__ void noise_cols_block(C* out, const GA& ga, int count
             sm[fpad(kym * count + q + half)] = zm;
         }
     }
-    stockham_fft(sm, ny, log2n, count, -1, twy);
-    const int total = ny * count;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    stockham_fft_out(sm, ny, log2n, count, -1, twy, [&](int e, C v) {
         const int q = e & (count - 1), y = e >> lc;
-        out[(long long)y * ga.nx + paired_column(b, q, count, ga.nx)] = sm[fpad(e)];
-    }
+        out[(long long)y * ga.nx + paired_column(b, q, count, ga.nx)] = v;
+    });
 }
 
 }  // namespace lbf

@@ -293,13 +293,16 @@ const char* lb_batch_last_error(lb_batch* b);
 /*
  * Request server: continuous batching of independent simulations.
  * Each request is one periodic lattice of the model of [GACV] Sec. III started at rest
- * (uniform density rho0, zero velocity) at time 0, with uncorrelated noise of Sec. IV
- * (LB_NOISE_OFF, LB_NOISE_LW or LB_NOISE_DIAG) keyed by its own seed, FP32 storage,
- * advanced by `steps` time steps.  Its trajectory is exactly the one lb_batch_* (and, up
- * to FP32 rounding order, lb_step) gives the same lattice, whatever else is served with it.
+ * (uniform density rho0, zero velocity) at time 0, with the noise of Sec. IV in any mode
+ * (LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_DIAG, or LB_NOISE_FULL for nx, ny powers of two and
+ * ny <= 8192) keyed by its own seed, FP32 storage, advanced by `steps` time steps.  Its
+ * trajectory is exactly the one lb_batch_* (and, up to FP32 rounding order, lb_step) gives
+ * the same lattice, whatever else is served with it.  Correlated requests of one size share
+ * one pair of k-space synthesis launches per step (Sec. IV, Eq. (noise-yeo)).
  *
- * lb_server_request_bytes: device bytes one request of that size holds while admitted
- *   (both population buffers); 0 for an invalid size (sides in [2, 16384]).
+ * lb_server_request_bytes: device bytes one request of that size and noise mode holds
+ *   while admitted (both population buffers, plus the (xi_4, xi_9) field for
+ *   LB_NOISE_FULL); 0 for an invalid size (sides in [2, 16384]).
  * lb_server_create: starts a scheduler thread on the current device.  hbm_budget_bytes
  *   bounds the sum of lb_server_request_bytes over admitted requests (their memory comes
  *   from a stream-ordered pool that keeps up to the budget cached); max_active bounds the
@@ -307,7 +310,8 @@ const char* lb_batch_last_error(lb_batch* b);
  *   steps issued between two admission decisions.  Requests are admitted in arrival order;
  *   one that does not fit the remaining budget lets later, smaller ones pass.
  * lb_server_submit: queues a request (thread-safe) and returns its id (> 0).  Validation
- *   happens here: LB_EINVAL for bad sizes/steps/parameters or LB_NOISE_FULL, LB_ENOTPSD
+ *   happens here: LB_EINVAL for bad sizes/steps/parameters or LB_NOISE_FULL on a size
+ *   that is not a power of two on both sides (or ny > 8192), LB_ENOTPSD
  *   as lb_check_params, LB_ENOMEM if the request alone exceeds the budget.
  * lb_server_poll: moves up to max_results completed results (oldest first) into out.
  * lb_server_wait: blocks until request `id` has completed (id <= 0: until every request
@@ -359,7 +363,7 @@ typedef struct lb_server_stats {
 } lb_server_stats;
 
 typedef struct lb_server lb_server;
-size_t lb_server_request_bytes(int nx, int ny);
+size_t lb_server_request_bytes(int nx, int ny, int noise_mode);
 int lb_server_create(size_t hbm_budget_bytes, int max_active, int max_chunk_steps, lb_server** out);
 int lb_server_submit(lb_server* s, const lb_request* r, int64_t* id);
 int lb_server_poll(lb_server* s, lb_result* out, int max_results, int* n);

@@ -108,7 +108,7 @@ def load(path: str = LIB_PATH):
         "lb_batch_launch_count": (c_int, [vp, i64p]),
         "lb_batch_tuning": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int), dp]),
         "lb_batch_last_error": (ctypes.c_char_p, [vp]),
-        "lb_server_request_bytes": (c_sz, [c_int, c_int]),
+        "lb_server_request_bytes": (c_sz, [c_int, c_int, c_int]),
         "lb_server_create": (c_int, [c_sz, c_int, c_int, ctypes.POINTER(vp)]),
         "lb_server_submit": (c_int, [vp, ctypes.POINTER(lb_request), i64p]),
         "lb_server_poll": (c_int, [vp, ctypes.POINTER(lb_result), c_int, ctypes.POINTER(c_int)]),
@@ -370,8 +370,8 @@ def _scheck(rc, srv=None):
     return rc
 
 
-def lb_server_request_bytes(nx, ny):
-    return load().lb_server_request_bytes(nx, ny)
+def lb_server_request_bytes(nx, ny, noise_mode=LB_NOISE_LW):
+    return load().lb_server_request_bytes(nx, ny, noise_mode)
 
 
 def lb_server_create(hbm_budget_bytes, max_active=4096, max_chunk_steps=500):

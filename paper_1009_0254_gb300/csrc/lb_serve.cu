@@ -18,6 +18,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -25,6 +26,7 @@
 #include <vector>
 
 #include "lb_ens.cuh"
+#include "lb_noise.cuh"
 #include "lbfluct.h"
 
 namespace lbf {
@@ -33,6 +35,7 @@ namespace lbf {
 struct SlotDesc {
     Grid g;
     float* buf[2];
+    float2* xi;              // correlated noise (xi_4, xi_9) for the coming step, or null
     int ntx;                 // tiles along x
     long long k_start;       // server step counter at admission
 };
@@ -146,7 +149,8 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
 
         int mode;
         const TileArgs a = load_tile_args(p.recs + slot, sl, &mode);
-        if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
+        if (mode == 2) tile_nodes<2, TX, TY, NT>(a, S, R, g, x0, y0, dst, d->xi);
+        else if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
         else tile_nodes<0, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
         __syncthreads();
         if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
@@ -160,6 +164,52 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
             *p.done = 0u;
             *p.kstep = K + 1;
         }
+    }
+}
+
+// Correlated noise of the served simulations of one size: k-space synthesis with each
+// simulation's Xi(k) coefficients, seed and own time, back along y (blockIdx.y = the
+// simulation's index in `slots`), then back along x (one CTA per row).
+__global__ void __launch_bounds__(1024) serve_noise_cols_kernel(const int* __restrict__ slots,
+                                                                const SlotDesc* __restrict__ desc,
+                                                                const RepRec* __restrict__ recs,
+                                                                const long long* __restrict__ kstep, int nx, int ny,
+                                                                int count, const float2* __restrict__ twy,
+                                                                const float* __restrict__ cosx,
+                                                                const float* __restrict__ cosy) {
+    const int slot = __ldg(&slots[blockIdx.y]);
+    const RepRec* rp = recs + slot;
+    NoiseGenT<KeyPair> ga;
+    ga.a44 = __ldg(&rp->a44); ga.b44 = __ldg(&rp->b44);
+    ga.a49 = __ldg(&rp->a49); ga.b49 = __ldg(&rp->b49);
+    ga.a99 = __ldg(&rp->a99); ga.b99 = __ldg(&rp->b99);
+    ga.eig = 0;
+    ga.cosx = cosx; ga.cosy = cosy;
+    ga.nx = nx; ga.ny = ny;
+    const long long t = __ldcg(kstep) - __ldg(&desc[slot].k_start);
+    ga.t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);
+    ga.t_hi = (uint32_t)((unsigned long long)t >> 32);
+    ga.rk.k0 = __ldg(&rp->k0);
+    ga.rk.k1 = __ldg(&rp->k1);
+    noise_cols_block(desc[slot].xi, ga, count, blockIdx.x, twy);
+}
+
+__global__ void __launch_bounds__(1024) serve_noise_rows_kernel(const int* __restrict__ slots,
+                                                                const SlotDesc* __restrict__ desc, int nx, int ny,
+                                                                const float2* __restrict__ twx, float scale) {
+    extern __shared__ float2 sm[];
+    const int slot = __ldg(&slots[blockIdx.x / ny]);
+    float2* rowp = desc[slot].xi + (long long)(blockIdx.x % ny) * nx;
+    if (nx >= 256) {
+        stockham_fft_io(sm, nx, 31 - __clz(nx), 1, -1, twx, [&](int e) { return rowp[e]; },
+                        [&](int e, float2 v) { rowp[e] = make_float2(v.x * scale, v.y * scale); });
+        return;
+    }
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = rowp[j];
+    stockham_fft(sm, nx, 31 - __clz(nx), 1, -1, twx);
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        const float2 v = sm[fpad(j)];
+        rowp[j] = make_float2(v.x * scale, v.y * scale);
     }
 }
 
@@ -211,7 +261,21 @@ bool serve_grid(int nx, int ny, Grid* g) {
     return true;
 }
 
-size_t slot_bytes(const Grid& g) { return 2 * align256s((size_t)Q * g.plane * sizeof(float)); }
+// device memory of one request: two population buffers, then (correlated noise only) its
+// (xi_4, xi_9) field
+size_t buf_bytes(const Grid& g) { return align256s((size_t)Q * g.plane * sizeof(float)); }
+size_t slot_bytes(const Grid& g, bool full = false) {
+    return 2 * buf_bytes(g) + (full ? align256s((size_t)g.nx * g.ny * sizeof(float2)) : 0);
+}
+
+bool pow2s(int v) { return v >= 2 && (v & (v - 1)) == 0; }
+
+// k-space column strip of the correlated-noise synthesis (as the single-lattice path)
+int noise_strip(int nx, int ny) {
+    int c = 16;
+    while (c > 1 && (fft_threads(ny, c) > 1024 || fft_smem_bytes(ny, c) > 200 * 1024)) c >>= 1;
+    return c > nx ? nx : c;
+}
 
 struct Pending {
     lb_request r;
@@ -230,6 +294,7 @@ struct Running {
     double t_submit, t_admit;
     bool finished = false;       // its last step has been issued
     int chunk = -1;              // chunk that issues its last step
+    bool full = false;           // correlated noise (needs the k-space synthesis every step)
 };
 
 struct Kept {
@@ -237,6 +302,13 @@ struct Kept {
 };
 
 }  // namespace
+
+struct SizeTables {                  // FFT twiddles and cosines of one lattice size
+    float2* twx = nullptr;
+    float2* twy = nullptr;
+    float* cosx = nullptr;
+    float* cosy = nullptr;
+};
 
 struct lb_server {
     int device = 0;
@@ -251,6 +323,10 @@ struct lb_server {
     double* d_fbar = nullptr;        // [slot][9]
     double* d_sums = nullptr;        // [slot][3]
     int* d_active[2] = {nullptr, nullptr};
+    int* d_full[2] = {nullptr, nullptr};     // correlated simulations of a chunk, grouped by size
+    int* h_full[2] = {nullptr, nullptr};
+    std::map<std::pair<int, int>, SizeTables> tables;
+    size_t noise_csm = 0, noise_rsm = 0;     // shared memory the noise kernels are set up for
     int* d_tb[2] = {nullptr, nullptr};
     long long* d_k = nullptr;
     unsigned int* d_done = nullptr;
@@ -307,6 +383,40 @@ unsigned char* slot_stage(lb_server* s, int slot) { return s->h_slot + (size_t)s
             return false;                                                            \
         }                                                                            \
     } while (0)
+
+// twiddles and cosines of a lattice size for the correlated noise (first request of the size)
+bool ensure_tables(lb_server* s, int nx, int ny) {
+    auto key = std::make_pair(nx, ny);
+    if (s->tables.count(key)) return true;
+    SizeTables t;
+    SCK(s, cudaMalloc(&t.twx, nx * sizeof(float2)));
+    SCK(s, cudaMalloc(&t.twy, ny * sizeof(float2)));
+    SCK(s, cudaMalloc(&t.cosx, nx * sizeof(float)));
+    SCK(s, cudaMalloc(&t.cosy, ny * sizeof(float)));
+    for (int which = 0; which < 2; ++which) {
+        const int n = which == 0 ? nx : ny;
+        std::vector<float2> tw(n);
+        std::vector<float> cs(n);
+        for (int k = 0; k < n; ++k) {
+            const double a = 2.0 * M_PI * (double)k / n;
+            tw[k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+            cs[k] = (float)std::cos(a);
+        }
+        SCK(s, cudaMemcpy(which == 0 ? t.twx : t.twy, tw.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+        SCK(s, cudaMemcpy(which == 0 ? t.cosx : t.cosy, cs.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    s->tables[key] = t;
+    const size_t csm = fft_smem_bytes(ny, noise_strip(nx, ny)), rsm = fft_smem_bytes(nx, 1);
+    if (csm > s->noise_csm) {
+        SCK(s, cudaFuncSetAttribute(serve_noise_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+        s->noise_csm = csm;
+    }
+    if (rsm > s->noise_rsm) {
+        SCK(s, cudaFuncSetAttribute(serve_noise_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+        s->noise_rsm = rsm;
+    }
+    return true;
+}
 
 lb_result make_result(const lb_request& r, int64_t id, int status, double t_submit, double t_admit, double t_done) {
     lb_result res;
@@ -369,7 +479,7 @@ bool admit(lb_server* s) {
         for (auto it = s->queue.begin(); it != s->queue.end() && !s->free_slots.empty();) {
             Grid g;
             serve_grid(it->r.nx, it->r.ny, &g);
-            const size_t b = slot_bytes(g);
+            const size_t b = slot_bytes(g, it->r.noise_mode == LB_NOISE_FULL);
             if (s->in_use + b <= s->budget) {
                 s->in_use += b;
                 s->peak = std::max(s->peak, s->in_use);
@@ -391,7 +501,8 @@ bool admit(lb_server* s) {
         run.id = pr.id;
         run.t_submit = pr.t_submit;
         serve_grid(pr.r.nx, pr.r.ny, &run.g);
-        run.bytes = slot_bytes(run.g);
+        run.full = pr.r.noise_mode == LB_NOISE_FULL && pr.r.kT > 0.0;
+        run.bytes = slot_bytes(run.g, pr.r.noise_mode == LB_NOISE_FULL);
         run.slot = slots[q];
         bool injected = false;
         {
@@ -411,7 +522,7 @@ bool admit(lb_server* s) {
         run.mem = (char*)mem;
         SCK(s, cudaMemsetAsync(run.mem, 0, run.bytes, s->stream));   // rest: zero deviations
         float* b0 = reinterpret_cast<float*>(run.mem);
-        float* b1 = reinterpret_cast<float*>(run.mem + run.bytes / 2);
+        float* b1 = reinterpret_cast<float*>(run.mem + buf_bytes(run.g));
         unsigned char* st = slot_stage(s, run.slot);
         CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(st);
         if (!make_slot_map(b0, run.g, &maps[0]) || !make_slot_map(b1, run.g, &maps[1])) {
@@ -423,6 +534,11 @@ bool admit(lb_server* s) {
         d->g = run.g;
         d->buf[0] = b0;
         d->buf[1] = b1;
+        d->xi = nullptr;
+        if (run.full) {
+            d->xi = reinterpret_cast<float2*>(run.mem + 2 * buf_bytes(run.g));
+            if (!ensure_tables(s, run.g.nx, run.g.ny)) return false;
+        }
         d->ntx = (run.g.nx + SV_TX - 1) / SV_TX;
         d->k_start = s->K;
         RepRec* rec = reinterpret_cast<RepRec*>(st + 2 * sizeof(CUtensorMap) + sizeof(SlotDesc));
@@ -518,9 +634,27 @@ bool issue_chunk(lb_server* s) {
     }
     const int n = (int)s->running.size();
     tb[n] = tiles;
+    // correlated simulations grouped by size: one pair of noise launches per size and step
+    struct Group { int nx, ny, off, cnt; };
+    std::vector<Group> groups;
+    {
+        std::map<std::pair<int, int>, std::vector<int>> by;
+        for (const Running& r : s->running)
+            if (r.full) by[std::make_pair(r.g.nx, r.g.ny)].push_back(r.slot);
+        int off = 0;
+        for (auto& kv : by) {
+            for (size_t q = 0; q < kv.second.size(); ++q) s->h_full[c][off + q] = kv.second[q];
+            groups.push_back(Group{kv.first.first, kv.first.second, off, (int)kv.second.size()});
+            off += (int)kv.second.size();
+        }
+    }
     std::lock_guard<std::mutex> gl(s->gpu);
     SCK(s, cudaMemcpyAsync(s->d_active[c], act, n * sizeof(int), cudaMemcpyHostToDevice, s->stream));
     SCK(s, cudaMemcpyAsync(s->d_tb[c], tb, (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    if (!groups.empty()) {
+        const int nf = groups.back().off + groups.back().cnt;
+        SCK(s, cudaMemcpyAsync(s->d_full[c], s->h_full[c], nf * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    }
     ServeParams p;
     p.maps = s->d_maps;
     p.desc = s->d_desc;
@@ -535,8 +669,19 @@ bool issue_chunk(lb_server* s) {
     using TT = TmaTile<SV_TX, SV_TY, float>;
     const int grid = std::max(1, std::min(tiles, s->grid));
     SCK(s, cudaEventRecord(s->ev_begin[c], s->stream));
-    for (long long k = 0; k < G; ++k)
+    for (long long k = 0; k < G; ++k) {
+        for (const Group& gr : groups) {
+            const SizeTables& tb2 = s->tables[std::make_pair(gr.nx, gr.ny)];
+            const int cs = noise_strip(gr.nx, gr.ny);
+            serve_noise_cols_kernel<<<dim3(gr.nx / cs, gr.cnt), fft_threads(gr.ny, cs), fft_smem_bytes(gr.ny, cs),
+                                      s->stream>>>(s->d_full[c] + gr.off, s->d_desc, s->d_recs, s->d_k, gr.nx, gr.ny,
+                                                   cs, tb2.twy, tb2.cosx, tb2.cosy);
+            serve_noise_rows_kernel<<<gr.cnt * gr.ny, fft_threads(gr.nx, 1), fft_smem_bytes(gr.nx, 1), s->stream>>>(
+                s->d_full[c] + gr.off, s->d_desc, gr.nx, gr.ny, tb2.twx,
+                (float)(1.0 / std::sqrt((double)gr.nx * gr.ny)));
+        }
         step_serve_kernel<SV_TX, SV_TY, SV_NT><<<grid, SV_NT, TT::SMEM_BYTES, s->stream>>>(p);
+    }
     SCK(s, cudaGetLastError());
     s->K += G;
     {
@@ -547,7 +692,7 @@ bool issue_chunk(lb_server* s) {
     for (auto it = s->running.begin(); it != s->running.end();) {
         if (it->k_end != s->K) { ++it; continue; }
         const int fin = (int)(it->r.steps & 1);   // buffer holding the state after `steps` steps
-        float* pops = reinterpret_cast<float*>(it->mem + (fin ? it->bytes / 2 : 0));
+        float* pops = reinterpret_cast<float*>(it->mem + (fin ? buf_bytes(it->g) : 0));
         SCK(s, launch_sums(pops, 0, it->g, s->d_fbar + (size_t)Q * it->slot, s->d_partial, s->d_sums + 3 * it->slot,
                            s->stream));
         SCK(s, cudaMemcpyAsync(s->h_sums + 3 * it->slot, s->d_sums + 3 * it->slot, 3 * sizeof(double),
@@ -616,10 +761,10 @@ int sfail(lb_server* s, int code, const std::string& m) {
 
 extern "C" {
 
-size_t lb_server_request_bytes(int nx, int ny) {
+size_t lb_server_request_bytes(int nx, int ny, int noise_mode) {
     Grid g;
     if (!serve_grid(nx, ny, &g)) return 0;
-    return slot_bytes(g);
+    return slot_bytes(g, noise_mode == LB_NOISE_FULL);
 }
 
 int lb_server_create(size_t hbm_budget_bytes, int max_active, int max_chunk_steps, lb_server** out) {
@@ -660,6 +805,8 @@ int lb_server_create(size_t hbm_budget_bytes, int max_active, int max_chunk_step
         if ((e = cudaMalloc(&s->d_tb[c], (M + 1) * sizeof(int))) != cudaSuccess) return fail_create(e);
         if ((e = cudaMallocHost(&s->h_active[c], M * sizeof(int))) != cudaSuccess) return fail_create(e);
         if ((e = cudaMallocHost(&s->h_tb[c], (M + 1) * sizeof(int))) != cudaSuccess) return fail_create(e);
+        if ((e = cudaMalloc(&s->d_full[c], M * sizeof(int))) != cudaSuccess) return fail_create(e);
+        if ((e = cudaMallocHost(&s->h_full[c], M * sizeof(int))) != cudaSuccess) return fail_create(e);
         if ((e = cudaEventCreate(&s->ev_begin[c])) != cudaSuccess) return fail_create(e);
         if ((e = cudaEventCreate(&s->ev_end[c])) != cudaSuccess) return fail_create(e);
     }
@@ -700,12 +847,14 @@ int lb_server_submit(lb_server* s, const lb_request* r, int64_t* id) {
     Grid g;
     if (!serve_grid(r->nx, r->ny, &g)) return sfail(nullptr, LB_EINVAL, "lattice sides must lie in [2, 16384]");
     if (r->steps < 1) return sfail(nullptr, LB_EINVAL, "steps must be >= 1");
-    if (r->noise_mode == LB_NOISE_FULL)
-        return sfail(nullptr, LB_EINVAL, "correlated noise is not available for served simulations");
+    if (r->noise_mode == LB_NOISE_FULL &&
+        (!pow2s(r->nx) || !pow2s(r->ny) || r->ny > 8192 || noise_strip(r->nx, r->ny) < 2))
+        return sfail(nullptr, LB_EINVAL, "correlated noise needs nx and ny powers of two and ny <= 8192");
     const int rc = lb_check_params(r->nx, r->ny, r->rho0, r->cs2, r->kT, r->kappa, r->tau_s, r->tau_b, r->tau_ghost,
                                    r->noise_mode);
     if (rc != LB_OK) return sfail(nullptr, rc, "parameters rejected (see lb_check_params)");
-    if (slot_bytes(g) > s->budget) return sfail(nullptr, LB_ENOMEM, "the request alone exceeds the HBM budget");
+    if (slot_bytes(g, r->noise_mode == LB_NOISE_FULL) > s->budget)
+        return sfail(nullptr, LB_ENOMEM, "the request alone exceeds the HBM budget");
     std::lock_guard<std::mutex> lk(s->mu);
     if (!s->err.empty()) return LB_ECUDA;
     if (s->stop) return LB_ESTATE;
@@ -766,7 +915,7 @@ int lb_server_fetch_populations(lb_server* s, int64_t id, double* f) {
     std::lock_guard<std::mutex> gl(s->gpu);
     const long long n = (long long)run.g.nx * run.g.ny;
     const int fin = (int)(run.r.steps & 1);
-    const void* pops = run.mem + (fin ? run.bytes / 2 : 0);
+    const void* pops = run.mem + (fin ? buf_bytes(run.g) : 0);
     double fbar[Q];
     rest_populations(run.r.rho0, run.r.cs2, fbar);
     void* stage = nullptr;
@@ -854,11 +1003,15 @@ int lb_server_destroy(lb_server* s) {
     for (int c = 0; c < 2; ++c) {
         cudaFree(s->d_active[c]); cudaFree(s->d_tb[c]);
         cudaFreeHost(s->h_active[c]); cudaFreeHost(s->h_tb[c]);
+        cudaFree(s->d_full[c]); cudaFreeHost(s->h_full[c]);
         if (s->ev_begin[c]) cudaEventDestroy(s->ev_begin[c]);
         if (s->ev_end[c]) cudaEventDestroy(s->ev_end[c]);
     }
     cudaFree(s->d_k); cudaFree(s->d_done); cudaFree(s->d_err); cudaFree(s->d_partial);
     cudaFreeHost(s->h_sums); cudaFreeHost(s->h_slot); cudaFreeHost(s->h_err);
+    for (auto& kv : s->tables) {
+        cudaFree(kv.second.twx); cudaFree(kv.second.twy); cudaFree(kv.second.cosx); cudaFree(kv.second.cosy);
+    }
     if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;

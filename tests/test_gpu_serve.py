@@ -46,6 +46,52 @@ def test_served_result_matches_oracle(nx, ny, mode):
     srv.close()
 
 
+@pytest.mark.parametrize("nx,ny", [(32, 32), (64, 16), (8, 128), (256, 8)])
+def test_served_correlated_noise_matches_oracle(nx, ny):
+    # Sec. IV, Eq. (noise-yeo): k-space noise of modes 4 and 9 per served request
+    srv = lbf.Server(1 << 30, max_active=16, max_chunk_steps=29)
+    p = dict(kT=1.5e-4, kappa=0.03, tau_s=0.8, tau_b=1.1, tau_ghost=0.9, noise_mode=lbf.LB_NOISE_FULL, seed=31)
+    i = srv.submit(nx, ny, 70, keep_state=True, **p)
+    res = srv.wait(i, timeout_s=60)
+    assert res.status == lbf.LB_OK
+    f = srv.fetch(i, nx, ny)
+    o = _oracle_run(nx, ny, 70, 31, 1.5e-4, 0.03, 0.8, 1.1, 0.9, lbf.LB_NOISE_FULL)
+    assert np.abs(f - o.f).max() <= TOL
+    srv.close()
+
+
+def test_served_correlated_result_same_alone_and_in_the_mix():
+    X = dict(nx=64, ny=32, steps=180, kT=1e-4, kappa=0.02, tau_s=0.9, seed=2024, noise_mode=lbf.LB_NOISE_FULL)
+    alone = lbf.Server(1 << 30, max_active=8, max_chunk_steps=50)
+    ia = alone.submit(keep_state=True, **X)
+    alone.wait(ia, timeout_s=60)
+    fa = alone.fetch(ia, 64, 32)
+    alone.close()
+
+    rng = np.random.default_rng(8)
+    mix = lbf.Server(1 << 30, max_active=64, max_chunk_steps=17)
+    reqs = _random_requests(rng, 30)
+    for k, r in enumerate(reqs):
+        if k % 2 == 0:
+            r["noise_mode"] = lbf.LB_NOISE_FULL     # same and other sizes share noise launches
+    for r in reqs[:15]:
+        mix.submit(**r)
+    ix = mix.submit(keep_state=True, **X)
+    for r in reqs[15:]:
+        mix.submit(**r)
+    mix.wait(0, timeout_s=120)
+    assert all(r.status == lbf.LB_OK for r in mix.poll())
+    fm = mix.fetch(ix, 64, 32)
+    assert np.array_equal(fa, fm)
+    mix.close()
+
+    # and the batched engine steps the same correlated trajectory
+    ens = lbf.Ensemble([(64, 32)], [2024])
+    ens.set_params(0, 1e-4, 0.02, 0.9, 1.0, 1.0, lbf.LB_NOISE_FULL)
+    ens.step(180)
+    assert np.abs(ens.populations(0) - fa).max() <= 1e-6
+
+
 def test_nonideal_request_matches_oracle():
     srv = lbf.Server(1 << 30, max_active=4, max_chunk_steps=50)
     i = srv.submit(32, 32, 80, kT=1e-5, kappa=0.08, tau_s=1.0, tau_b=1.1, tau_ghost=0.9, seed=9, rho0=0.9,
@@ -156,8 +202,13 @@ def test_concurrent_submitters():
 def test_submit_validation():
     srv = lbf.Server(lbf.lb_server_request_bytes(64, 64), max_active=4)
     with pytest.raises(lbf.LBError) as e:
-        srv.submit(32, 32, 10, noise_mode=lbf.LB_NOISE_FULL)
+        srv.submit(48, 32, 10, noise_mode=lbf.LB_NOISE_FULL)     # 48 is not a power of two
     assert e.value.code == lbf.LB_EINVAL
+    assert lbf.lb_server_request_bytes(64, 64, lbf.LB_NOISE_FULL) == \
+        lbf.lb_server_request_bytes(64, 64) + 64 * 64 * 8
+    with pytest.raises(lbf.LBError) as e:
+        srv.submit(64, 64, 10, noise_mode=lbf.LB_NOISE_FULL)     # its noise field exceeds the budget
+    assert e.value.code == lbf.LB_ENOMEM
     with pytest.raises(lbf.LBError) as e:
         srv.submit(32, 32, 10, tau_s=0.5)
     assert e.value.code == lbf.LB_EINVAL

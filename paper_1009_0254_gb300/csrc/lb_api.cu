@@ -209,7 +209,8 @@ struct lb_ctx {
     bool use_tma = false;            // TMA-staged persistent step kernel
     bool use_sweep = false;          // warp-autonomous vertical sweep kernel
     int sweep_occ6 = 0;              // its occupancy variant
-    int tma_tile = 0;                // its tile shape (see lb_step_tma.cu)
+    int tma_tile = 0;                // tile shape of the tensor maps (see lb_step_tma.cu)
+    int tma_tile_fixed = -1;         // LBFLUCT_TMA_TILE, else -1: the fastest for the noise mode
     alignas(64) unsigned char tmap[2][128];
     double fbar[Q] = {};
     // parameters
@@ -349,7 +350,8 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     c->err_dev = (int*)(c->ws + c->L.err);
     rest_populations(rho0, cs2, c->fbar);
     {
-        // LBFLUCT_STEP_KERNEL=simple selects the plain kernel; LBFLUCT_TMA_TILE=<0..2> a tile shape
+        // LBFLUCT_STEP_KERNEL=simple selects the plain kernel; LBFLUCT_TMA_TILE=<0..4> fixes a
+        // tile shape (otherwise each step uses the fastest one for its noise mode)
         const char* v = std::getenv("LBFLUCT_STEP_KERNEL");
         c->use_sweep = v && (std::strcmp(v, "sweep") == 0 || std::strcmp(v, "sweep6") == 0) && sweep_fits(g);
         c->sweep_occ6 = v && std::strcmp(v, "sweep6") == 0;
@@ -357,8 +359,9 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
         // FP64 storage runs the plain kernel (its arithmetic is FP64 throughout)
         const bool want_tma = !(v && std::strcmp(v, "simple") == 0) && !c->use_sweep && precision != LB_FP64;
         const char* tv = std::getenv("LBFLUCT_TMA_TILE");
-        c->tma_tile = tv ? std::atoi(tv) : 0;
-        if (c->tma_tile < 0 || c->tma_tile >= tma_tile_count()) c->tma_tile = 0;
+        c->tma_tile_fixed = tv ? std::atoi(tv) : -1;
+        if (c->tma_tile_fixed >= tma_tile_count()) c->tma_tile_fixed = -1;
+        c->tma_tile = c->tma_tile_fixed >= 0 ? c->tma_tile_fixed : tma_default_tile(LB_NOISE_LW, c->fp16);
         c->use_tma = want_tma && tensor_map_bytes() <= sizeof(c->tmap[0]) &&
                      make_pop_tensor_map(c->pop[0], g, c->tma_tile, c->fp16, c->tmap[0]) &&
                      make_pop_tensor_map(c->pop[1], g, c->tma_tile, c->fp16, c->tmap[1]);
@@ -592,10 +595,18 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         }
         if (c->use_sweep)
             CK(c, launch_step_sweep(a, kmode, c->fp16, c->sweep_occ6, c->stream), "step kernel launch");
-        else if (c->use_tma)
+        else if (c->use_tma) {
+            const int want = c->tma_tile_fixed >= 0 ? c->tma_tile_fixed : tma_default_tile(kmode, c->fp16);
+            if (want != c->tma_tile) {
+                // tensor maps are host-encoded descriptors passed by value: re-encode for the shape
+                if (!make_pop_tensor_map(c->pop[0], c->g, want, c->fp16, c->tmap[0]) ||
+                    !make_pop_tensor_map(c->pop[1], c->g, want, c->fp16, c->tmap[1]))
+                    return fail(c, LB_ECUDA, "tensor map encoding failed");
+                c->tma_tile = want;
+            }
             CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->tma_tile, c->fp16, c->stream),
                "step kernel launch");
-        else
+        } else
             CK(c, launch_step_simple(a, kmode, c->fp16, c->stream), "step kernel launch");
         c->kernels += 1;
         if (c->timing) {

@@ -300,6 +300,7 @@ cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, in
                             cudaStream_t s);
 bool make_pop_tensor_map(const void* buf, const Grid& g, int tile, int fp16, void* map_out);
 int tma_tile_count();
+int tma_default_tile(int noise_mode, int fp16);
 size_t tensor_map_bytes();
 cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
                            cudaStream_t s);

@@ -10,14 +10,13 @@
 //     (lx, ly) of the tile reads f_i at box[ly + 1][lx + 4 - cx_i].  The x start is rounded
 //     down to a 16-byte boundary (four floats) as TMA requires;
 //   * two stages and an mbarrier each: tile k+1 is in flight while tile k is computed;
-//   * density on the tile plus one ring is formed from shared memory, then every node
+//   * every thread pulls its nodes' nine deviations from shared memory into registers and
+//     writes their density to a tile-plus-ring array (the ring from the halo); after one
+//     barrier the stage is refilled with the tile two steps ahead while every node
 //     collides and stores its nine post-collision deviations (and periodic ghosts)
 //     directly from registers with coalesced stores.  Nodes beyond a ragged edge of the
 //     lattice take part in the density pass (their values are never used) but not in the
-//     collision pass.  For correlated noise and FP16 storage the pulled populations stay in
-//     registers across the density barrier and the stage is refilled right after it; for
-//     uncorrelated noise in FP32 the nodes pull again and the stage is refilled at the end
-//     of the tile (the faster of the two in each case, measured).
+//     collision pass.
 // Waits on the mbarriers are bounded by the global timer; a CTA that gives up sets the
 // error word, gives its loads in flight a bounded chance to land, and returns.
 #include <cuda.h>
@@ -94,54 +93,33 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
 
         static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
         constexpr int NN = TX * TY / NT;
-        // RES: each thread pulls its nodes' nine deviations once, keeps them in registers
-        // across the barrier and writes their density to the tile; the ring is formed
-        // separately.  Otherwise the density of tile and ring is formed in one pass and
-        // the nodes pull again in the collision pass (fewer live registers; measured
-        // faster for the uncorrelated noise in FP32 storage, slower for the others).
-        constexpr bool RES = !(MODE == 1 && sizeof(T) == 4);
-        float fr[RES ? NN : 1][Q];
-        if constexpr (RES) {
+        // each thread pulls its nodes' nine deviations once, keeps them in registers across
+        // the barrier and writes their density to the tile; the ring is formed separately
+        float fr[NN][Q];
 #pragma unroll
-            for (int it = 0; it < NN; ++it) {
-                const int q = tid + it * NT;
-                const int ly = q / TX, lx = q - ly * TX;
-                load9(S, (ly + 1) * TT::BW + lx + TT::XO, fr[it]);
-                R[(ly + 1) * TT::RW + lx + 1] = drho_of(fr[it]);
-            }
-            // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
-            constexpr int NB = 2 * (TX + 2) + 2 * TY;
-            for (int j = tid; j < NB; j += NT) {
-                int rx, ry;
-                if (j < TX + 2) { rx = j; ry = 0; }
-                else if (j < 2 * (TX + 2)) { rx = j - (TX + 2); ry = TY + 1; }
-                else { const int u = j - 2 * (TX + 2); ry = 1 + (u >> 1); rx = (u & 1) ? TX + 1 : 0; }
-                float h[Q];
-                load9(S, ry * TT::BW + rx + TT::XO - 1, h);
-                R[ry * TT::RW + rx] = drho_of(h);
-            }
-        } else {
-            // density deviation on the tile and its ring: node (lx, ly) = (rx - 1, ry - 1)
-            constexpr int NA = (TT::RW * TT::RH + NT - 1) / NT;
-#pragma unroll
-            for (int it = 0; it < NA; ++it) {
-                const int q = tid + it * NT;
-                if (q >= TT::RW * TT::RH) break;
-                const int ry = q / TT::RW, rx = q - ry * TT::RW;
-                const int b = ry * TT::BW + rx + TT::XO - 1;
-                float f[Q];
-                load9(S, b, f);
-                R[q] = drho_of(f);
-            }
+        for (int it = 0; it < NN; ++it) {
+            const int q = tid + it * NT;
+            const int ly = q / TX, lx = q - ly * TX;
+            load9(S, (ly + 1) * TT::BW + lx + TT::XO, fr[it]);
+            R[(ly + 1) * TT::RW + lx + 1] = drho_of(fr[it]);
+        }
+        // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
+        constexpr int NB = 2 * (TX + 2) + 2 * TY;
+        for (int j = tid; j < NB; j += NT) {
+            int rx, ry;
+            if (j < TX + 2) { rx = j; ry = 0; }
+            else if (j < 2 * (TX + 2)) { rx = j - (TX + 2); ry = TY + 1; }
+            else { const int u = j - 2 * (TX + 2); ry = 1 + (u >> 1); rx = (u & 1) ? TX + 1 : 0; }
+            float h[Q];
+            load9(S, ry * TT::BW + rx + TT::XO - 1, h);
+            R[ry * TT::RW + rx] = drho_of(h);
         }
         __syncthreads();
-        if constexpr (RES) {
-            // the collision pass reads no population from stage s: refill it now with the
-            // tile two steps ahead
-            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(tile + 2 * gridDim.x, s);
-            }
+        // the collision pass reads no population from stage s: refill it now with the tile
+        // two steps ahead
+        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(tile + 2 * gridDim.x, s);
         }
 
         // collide every node of the tile; the nodes of one thread are independent, so
@@ -152,13 +130,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             const int ly = q / TX, lx = q - ly * TX;
             const int x = x0 + lx, y = y0 + ly;
             if (x >= g.nx || y >= g.ny) continue;
-            float f[Q];
-            if constexpr (RES) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) f[i] = fr[it][i];
-            } else {
-                load9(S, (ly + 1) * TT::BW + lx + TT::XO, f);
-            }
+            const float* f = fr[it];
             const int rc = (ly + 1) * TT::RW + lx + 1;
             Nbr r;
             r.C = R[rc];
@@ -172,16 +144,6 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             float o[Q];
             collide_node<MODE>(a, f, r, node, z, o);
             store9(static_cast<T*>(a.dst), g.plane, g, x, y, o);
-        }
-        if constexpr (!RES) {
-            // stage s is free once every thread has pulled from it: refill it with the
-            // tile two steps ahead (a CTA barrier measured faster here than a
-            // last-warp-out release through a shared counter)
-            __syncthreads();
-            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(tile + 2 * gridDim.x, s);
-            }
         }
     }
 }
@@ -204,11 +166,21 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// Tile shapes (TX x TY nodes, NT threads): 0 = 32x16/256 (the fastest measured on GB300),
-// 1 = 32x32/256, 2 = 64x8/256, 3 = 64x16/512, 4 = 32x16/128.
+// Tile shapes (TX x TY nodes, NT threads): 0 = 32x16/256, 1 = 32x32/256, 2 = 64x8/256,
+// 3 = 64x16/512, 4 = 32x16/128.
 static const int kTiles[5][3] = {{32, 16, 256}, {32, 32, 256}, {64, 8, 256}, {64, 16, 512}, {32, 16, 128}};
 
 int tma_tile_count() { return 5; }
+
+// The fastest shape per noise mode (0 off, 1 uncorrelated, 2 correlated) and storage,
+// measured on GB300 over all five at 4096^2: FP32 off 32x32 (263 us), uncorrelated 64x16
+// (215 us), correlated 32x16 (246 us); FP16 off 32x16/128 (153 us), uncorrelated 32x32
+// (233 us), correlated 64x16 (245 us).
+int tma_default_tile(int noise_mode, int fp16) {
+    static const int best[2][3] = {{1, 3, 0}, {4, 1, 3}};
+    const int m = noise_mode < 0 ? 0 : (noise_mode > 2 ? 2 : noise_mode);
+    return best[fp16 ? 1 : 0][m];
+}
 
 // Tensor map over one population buffer: dims (pitch, ny + 2 GY, 9) of FP32, box
 // (TX + 8, TY + 2, 1), zero fill outside.

@@ -74,6 +74,33 @@ def test_parity_ragged_and_small_lattices(nx, ny, mode, kernel):
     assert err <= TOL, err
 
 
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("nx,ny,mode", [(100, 36, "lw"), (70, 50, "off"), (128, 64, "full")])
+def test_parity_every_tile_shape(tile, nx, ny, mode, monkeypatch):
+    # each TMA tile shape (32x16, 32x32, 64x8, 64x16, 32x16 on 128 threads) on ragged edges
+    monkeypatch.setenv("LBFLUCT_STEP_KERNEL", "tma")
+    monkeypatch.setenv("LBFLUCT_TMA_TILE", str(tile))
+    g, o = _pair(nx, ny, 11, 1.0, 1 / 3, (2e-4, 0.02, 0.8, 1.0, 1.0), MODES[mode], 0.01)
+    g.step(40)
+    o.step(40)
+    assert np.abs(g.populations() - o.f).max() <= TOL
+
+
+def test_parity_across_noise_mode_changes(monkeypatch):
+    # the default tile shape follows the noise mode; switching modes mid-run re-encodes the
+    # tensor maps and the trajectory stays the oracle's
+    monkeypatch.setenv("LBFLUCT_STEP_KERNEL", "tma")
+    monkeypatch.delenv("LBFLUCT_TMA_TILE", raising=False)
+    params = (2e-4, 0.02, 0.8, 1.0, 1.0)
+    g, o = _pair(128, 64, 13, 1.0, 1 / 3, params, MODES["lw"], 0.01)
+    for mode in ["lw", "full", "off", "lw", "diag", "full"]:
+        g.set_params(*params, MODES[mode])
+        o.set_params(*params, MODES[mode])
+        g.step(15)
+        o.step(15)
+        assert np.abs(g.populations() - o.f).max() <= TOL, mode
+
+
 @pytest.mark.parametrize("mode", ["lw", "full"])
 def test_parity_nonideal_sound_speed(mode, kernel):
     # cs != sigma_s: rest populations differ from w_i rho0 and Xi_49(0) != 0

@@ -1,4 +1,4 @@
-// lb_fft.cu -- radix-2 FFTs in shared memory, the k-space synthesis of the correlated
+// lb_fft.cu -- power-of-two FFTs in shared memory, the k-space synthesis of the correlated
 // noise ([GACV] Sec. IV, last paragraph) and the sampled spectra ([GACV] Sec. V A).
 //
 // Transforms follow the unitary convention of [GACV] Sec. III:
@@ -7,7 +7,8 @@
 // with k = 2 pi (mx/nx, my/ny).  Sizes are powers of two.  Each transform is a 2D
 // pass over rows (one CTA per row) and a pass over columns (a CTA per strip of C
 // adjacent columns), each an in-place Stockham FFT in shared memory (lb_fft_core.cuh)
-// with twiddles exp(-2 pi i q/n) computed on the host in FP64.
+// with a twiddle table exp(-2 pi i q/n) computed on the host in FP64 (one read per
+// butterfly, its powers formed on the fly).
 #include "lb_fft_core.cuh"
 #include "lb_internal.cuh"
 #include "lb_noise.cuh"
@@ -204,56 +205,58 @@ __device__ __forceinline__ int k_bin(int mx, int my, int nx, int ny, int nbins, 
     return b;
 }
 
+// Power of the three spectra at one wavevector k from Z1 = FT(drho + i jx) at k and -k and
+// Z2 = FT(jy) at k, added to s[0..2]: |drho(k)|^2, |k.j(k)|^2/|k|^2, |k x j(k)|^2/|k|^2.
+__device__ __forceinline__ void add_power3(float2 a, float2 am, float2 c, float kx, float ky, float s[3]) {
+    const float inv = rsqrtf(kx * kx + ky * ky);
+    // two real fields in one transform: drho(k) = (Z(k) + Z(-k)*)/2, jx(k) = (Z(k) - Z(-k)*)/(2i)
+    const float rr = 0.5f * (a.x + am.x), ri = 0.5f * (a.y - am.y);
+    const float xr = 0.5f * (a.y + am.y), xi = -0.5f * (a.x - am.x);
+    const float lr = (kx * xr + ky * c.x) * inv, li = (kx * xi + ky * c.y) * inv;
+    const float tr = (-ky * xr + kx * c.x) * inv, ti = (-ky * xi + kx * c.y) * inv;
+    s[0] += rr * rr + ri * ri;
+    s[1] += lr * lr + li * li;
+    s[2] += tr * tr + ti * ti;
+}
+
 // Radial spectra of one sample.  The bin of every wavevector was decided once, in FP64,
-// by bin_table_kernel; here each thread walks a contiguous run of k_x in a row, forms the
-// three power values in FP32 and merges equal consecutive bins before adding to the
-// block's FP64 bins in shared memory, which are added to the global FP64 bins at the end.
+// by bin_table_kernel; it depends on |k| only, so the up to four wavevectors (+-kx, +-ky)
+// share it.  A thread takes (mx, my) with mx <= nx/2, my <= ny/2 (lanes along mx, so the
+// loads coalesce), forms the powers of the distinct points of that set in FP32, sums them,
+// and adds the sums to the block's FP64 bins in shared memory; those are added to the
+// global FP64 bins at the end.
 __global__ void bin_kernel(const float2* __restrict__ z1, const float2* __restrict__ z2,
                            const unsigned short* __restrict__ bin16, int nx, int ny, int nbins, double* bins) {
     extern __shared__ double sb[];   // 3 * nbins
     for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x) sb[j] = 0.0;
     __syncthreads();
-    const int chunk = (nx + blockDim.x - 1) / blockDim.x;
+    const int hx = nx / 2, hy = ny / 2;
     const float tpx = 6.2831853071795865f / (float)nx, tpy = 6.2831853071795865f / (float)ny;
-    for (int my = blockIdx.x; my < ny; my += gridDim.x) {
+    for (int my = blockIdx.x; my <= hy; my += gridDim.x) {
         const int cy = (ny - my) & (ny - 1);
-        const float ky = tpy * (float)(my > ny / 2 ? my - ny : my);
-        int cur = -1;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        const int mx0 = threadIdx.x * chunk;
-        const int mx1 = min(nx, mx0 + chunk);
-        for (int mx = mx0; mx < mx1; ++mx) {
-            const long long o = (long long)my * nx + mx;
-            const int b = bin16[o];
+        const bool ypair = my != 0 && my != hy;          // -ky is another row
+        const float ky = tpy * (float)my;
+        const float kym = ypair ? -ky : ky;              // k_y of row cy (wrapped index)
+        const long long r0 = (long long)my * nx, r1 = (long long)cy * nx;
+        for (int mx = threadIdx.x; mx <= hx; mx += blockDim.x) {
+            const int b = bin16[r0 + mx];
             if (b == 0xFFFF) continue;                    // k = 0
             const int cx = (nx - mx) & (nx - 1);
-            const float kx = tpx * (float)(mx > nx / 2 ? mx - nx : mx);
-            const float inv = rsqrtf(kx * kx + ky * ky);
-            const float2 a = z1[o];
-            const float2 am = z1[(long long)cy * nx + cx];
-            const float2 c = z2[o];
-            // z1 = drho + i jx of two real fields: drho(k) = (Z(k) + Z(-k)*)/2, jx(k) = (Z(k) - Z(-k)*)/(2i)
-            const float rr = 0.5f * (a.x + am.x), ri = 0.5f * (a.y - am.y);
-            const float xr = 0.5f * (a.y + am.y), xi = -0.5f * (a.x - am.x);
-            const float lr = (kx * xr + ky * c.x) * inv, li = (kx * xi + ky * c.y) * inv;
-            const float tr = (-ky * xr + kx * c.x) * inv, ti = (-ky * xi + kx * c.y) * inv;
-            if (b != cur) {
-                if (cur >= 0) {
-                    atomicAdd(&sb[cur], a0);
-                    atomicAdd(&sb[nbins + cur], a1);
-                    atomicAdd(&sb[2 * nbins + cur], a2);
-                }
-                cur = b;
-                a0 = a1 = a2 = 0.0;
+            const bool xpair = mx != 0 && mx != hx;      // -kx is another column
+            const float kx = tpx * (float)mx;
+            const float kxm = xpair ? -kx : kx;
+            float acc[3] = {0.f, 0.f, 0.f};
+            const float2 A1 = z1[r0 + mx], A2 = z1[r1 + cx];
+            add_power3(A1, A2, z2[r0 + mx], kx, ky, acc);                 // (mx, my)
+            if (xpair || ypair) add_power3(A2, A1, z2[r1 + cx], kxm, kym, acc);   // (-mx, -my)
+            if (xpair && ypair) {
+                const float2 A3 = z1[r0 + cx], A4 = z1[r1 + mx];
+                add_power3(A3, A4, z2[r0 + cx], kxm, ky, acc);            // (-mx, my)
+                add_power3(A4, A3, z2[r1 + mx], kx, kym, acc);            // (mx, -my)
             }
-            a0 += (double)(rr * rr + ri * ri);
-            a1 += (double)(lr * lr + li * li);
-            a2 += (double)(tr * tr + ti * ti);
-        }
-        if (cur >= 0) {
-            atomicAdd(&sb[cur], a0);
-            atomicAdd(&sb[nbins + cur], a1);
-            atomicAdd(&sb[2 * nbins + cur], a2);
+            atomicAdd(&sb[b], (double)acc[0]);
+            atomicAdd(&sb[nbins + b], (double)acc[1]);
+            atomicAdd(&sb[2 * nbins + b], (double)acc[2]);
         }
     }
     __syncthreads();
@@ -301,8 +304,9 @@ cudaError_t launch_stats_sample(const void* pops, int storage, const Grid& g, fl
     const size_t smem = (size_t)3 * nbins * sizeof(double);
     e = cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int bx = g.nx >= 256 ? 256 : 64;
-    const int nblk = g.ny < 304 ? g.ny : 304;   // two blocks per SM, each over many rows
+    const int bx = g.nx >= 512 ? 256 : 64;
+    const int rows = g.ny / 2 + 1;
+    const int nblk = rows < 304 ? rows : 304;   // two blocks per SM, each over many rows
     bin_kernel<<<nblk, bx, smem, s>>>(z1, z2, bin16, g.nx, g.ny, nbins, bins);
     return cudaGetLastError();
 }

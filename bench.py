@@ -257,7 +257,9 @@ def timed_run(lbf, torch, L, steps, warmup, mode, params, dist):
     L.set_params(params["kT"], params["kappa"], params["tau_s"], params["tau_b"], params["tau_ghost"], mode)
     L.step(warmup)
     torch.cuda.synchronize()
-    lbf.lb_set_kernel_timing(L.ctx, 1)
+    # CUDA events around a sample of the step-kernel launches spread over the timed region
+    # (every launch would add the events' own cost, ~4 us a step, to the whole-run time)
+    lbf.lb_set_kernel_timing(L.ctx, max(1, steps // 500))
     k0 = lbf.lb_launch_count(L.ctx)
     if dist is not None:
         dist.barrier()
@@ -581,7 +583,7 @@ def main():
                        2 * 9 * (n + 64) * (n + 4) * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "kernel": "step_kernel (fused pull+collide+noise)",
-                     "bytes_per_node": BYTES_PER_NODE_STEP, "avg_launch_us": k_avg_s * 1e6,
+                     "bytes_per_node": BYTES_PER_NODE_STEP, "avg_launch_us": k_avg_s * 1e6, "timed_launches": kl,
                      "peak_source": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -185,12 +185,13 @@ const char* lb_last_error(lb_ctx* ctx);
 int lb_synchronize(lb_ctx* ctx);
 
 /*
- * Kernel timing for roofline measurements: when on, CUDA events are recorded on the
- * context's stream around every launch of the fused step kernel; lb_kernel_time
- * synchronises and returns the summed event time (ms) and the launch count since
- * timing was turned on.
+ * Kernel timing for roofline measurements: with every = k >= 1, CUDA events are recorded
+ * on the context's stream around every k-th launch of the fused step kernel (k = 1: all of
+ * them; a sample keeps the events' own cost out of a whole-run timing); 0 turns it off.
+ * lb_kernel_time synchronises and returns the summed event time (ms) and the number of
+ * timed launches since timing was set.  LB_EINVAL for every < 0.
  */
-int lb_set_kernel_timing(lb_ctx* ctx, int on);
+int lb_set_kernel_timing(lb_ctx* ctx, int every);
 int lb_kernel_time(lb_ctx* ctx, double* ms, int64_t* launches);
 
 /* Number of kernels this context has launched since lb_create (all kinds). */

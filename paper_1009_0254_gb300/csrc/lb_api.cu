@@ -233,7 +233,8 @@ struct lb_ctx {
     long long t = 0;
     std::string err;
     // kernel timing
-    bool timing = false;
+    int timing = 0;                 // 0 off, k: events around every k-th step-kernel launch
+    long long timing_seq = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     size_t ev_used = 0;
     double ms_acc = 0.0;
@@ -555,14 +556,15 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
             d.xi49 = reinterpret_cast<const double2*>(c->z1);
             d.t_lo = tlo; d.t_hi = thi;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (c->timing) {
+            const bool tm = c->timing > 0 && (c->timing_seq++ % c->timing) == 0;
+            if (tm) {
                 int r = record_timing(c, &e0, &e1);
                 if (r != LB_OK) return r;
                 CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
             }
             CK(c, launch_step_simple_d(d, kmode, c->stream), "step kernel launch");
             c->kernels += 1;
-            if (c->timing) {
+            if (tm) {
                 CK(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
                 c->launches_acc++;
             }
@@ -588,7 +590,8 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         a.xi49 = c->z1;
         a.t_lo = tlo; a.t_hi = thi;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (c->timing) {
+        const bool tm = c->timing > 0 && (c->timing_seq++ % c->timing) == 0;
+        if (tm) {
             int r = record_timing(c, &e0, &e1);
             if (r != LB_OK) return r;
             CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
@@ -609,7 +612,7 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         } else
             CK(c, launch_step_simple(a, kmode, c->fp16, c->stream), "step kernel launch");
         c->kernels += 1;
-        if (c->timing) {
+        if (tm) {
             CK(c, cudaEventRecord(e1, c->stream), "cudaEventRecord");
             c->launches_acc++;
         }
@@ -748,7 +751,9 @@ int lb_synchronize(lb_ctx* c) {
 
 int lb_set_kernel_timing(lb_ctx* c, int on) {
     if (!c) return LB_EINVAL;
-    c->timing = on != 0;
+    if (on < 0) return fail(c, LB_EINVAL, "timing stride must be >= 0");
+    c->timing = on;
+    c->timing_seq = 0;
     c->ev_used = 0;
     c->ms_acc = 0.0;
     c->launches_acc = 0;

@@ -257,3 +257,21 @@ def test_api_errors():
     assert lbf.lb_warnings(L.ctx) & lbf.LB_WARN_LOW_MACH
     with pytest.raises(lbf.LBError):
         lbf.Lattice(1, 16)
+
+
+def test_kernel_timing_samples_every_kth_launch():
+    L = lbf.Lattice(32, 32)
+    L.set_params(1e-4, 0.01, 1.0, 1.0, 1.0, lbf.LB_NOISE_LW)
+    with pytest.raises(lbf.LBError) as e:
+        lbf.lb_set_kernel_timing(L.ctx, -1)
+    assert e.value.code == lbf.LB_EINVAL
+    lbf.lb_set_kernel_timing(L.ctx, 3)
+    L.step(10)                                     # launches 0, 3, 6, 9 are timed
+    ms, k = lbf.lb_kernel_time(L.ctx)
+    assert k == 4 and ms > 0
+    lbf.lb_set_kernel_timing(L.ctx, 1)
+    L.step(5)
+    assert lbf.lb_kernel_time(L.ctx)[1] == 5
+    lbf.lb_set_kernel_timing(L.ctx, 0)
+    L.step(2)
+    assert lbf.lb_kernel_time(L.ctx)[1] == 0

@@ -11,6 +11,9 @@ density stencil, equilibrium, MRT relaxation, noise, back-transform, store) plus
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+(--n, --noise full, --no-variants and --no-cpu-baseline select smaller or other main lines
+for profiling runs.)
+
 With N > 1 (launched by torch.distributed.run) every rank steps its own independent
 lattice (replicas; the method has no exchange between independent runs): weak scaling.
 """
@@ -73,6 +76,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--noise", default="lw", choices=["lw", "full"],
+                   help="noise of the main line (full: correlated, kappa=0.05; for profiling runs)")
     return p.parse_args()
 
 
@@ -489,19 +494,22 @@ def main():
     time.sleep(0.3)
 
     # main line: long-wavelength noise
-    ms, kms, kl, launches, w0, w1 = timed_run(lbf, torch, L, args.steps, args.warmup, lbf.LB_NOISE_LW, PARAMS_LW, dist)
+    main_full = args.noise == "full"
+    main_mode, main_params = (lbf.LB_NOISE_FULL, PARAMS_FULL) if main_full else (lbf.LB_NOISE_LW, PARAMS_LW)
+    main_bpn = BYTES_PER_NODE_STEP_FULL if main_full else BYTES_PER_NODE_STEP
+    ms, kms, kl, launches, w0, w1 = timed_run(lbf, torch, L, args.steps, args.warmup, main_mode, main_params, dist)
     clk = clocks.stop(w0, w1)
 
     ms = max_over_ranks(dist, ms, "cuda")
     value = whole_job_mlups(world, nodes, args.steps, ms)
     hbm, peak_kind = peaks()
     k_avg_s = kms / max(kl, 1) / 1e3
-    achieved = BYTES_PER_NODE_STEP * nodes / k_avg_s / 1e9
-    traffic = step_kernel_traffic(nodes)
+    achieved = main_bpn * nodes / k_avg_s / 1e9
+    traffic = None if main_full else step_kernel_traffic(nodes)
 
     # variant: correlated (full FDT) noise at kappa = 0.05
     variants = []
-    if not args.no_variants:
+    if not args.no_variants and not main_full:
         L.set_sampling(args.every, args.nbins)
         fms, fkms, fkl, flaunch, _, _ = timed_run(lbf, torch, L, args.steps, args.warmup, lbf.LB_NOISE_FULL,
                                                   PARAMS_FULL, dist)
@@ -576,14 +584,15 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "D2Q9 fluctuating non-ideal LB (modified equilibrium), periodic %dx%d FP32 "
-                               "lattice, long-wavelength noise, kappa=0.01, tau_s=0.8, tau_b=1, tau_ghost=1, "
-                               "kT=1e-4, cs2=1/3, S(k) every %d steps into %d bins (FP64)" % (n, n, args.every,
-                                                                                               args.nbins),
+                               "lattice, %s noise, kappa=%.2f, tau_s=0.8, tau_b=1, tau_ghost=1, "
+                               "kT=1e-4, cs2=1/3, S(k) every %d steps into %d bins (FP64)" % (
+                                   n, n, "correlated (full FDT)" if main_full else "long-wavelength",
+                                   main_params["kappa"], args.every, args.nbins),
                    "lattice": [n, n], "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (
-                       2 * 9 * (n + 64) * (n + 4) * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
+                       9 * (n + 64) * (n + 4) * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "kernel": "step_kernel (fused pull+collide+noise)",
-                     "bytes_per_node": BYTES_PER_NODE_STEP, "avg_launch_us": k_avg_s * 1e6, "timed_launches": kl,
+                     "bytes_per_node": main_bpn, "avg_launch_us": k_avg_s * 1e6, "timed_launches": kl,
                      "peak_source": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,

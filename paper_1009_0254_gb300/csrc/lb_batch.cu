@@ -111,6 +111,11 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
     int k = 0;
     for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
         const int s = k & 1;
+        // the tile's replica record is read while its populations are still in flight
+        const TilePos tp = locate<TX, TY>(p, tile);
+        const RepRec* rp = p.cls[tp.c].recs + tp.rep;
+        int mode;
+        const TileArgs a = load_tile_args(rp, K + __ldg(&rp->toff), &mode);
         const bool ok = mbar_wait_bounded(smem_u32(&mbar[s]), (uint32_t)((k >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -123,7 +128,6 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
             }
             break;
         }
-        const TilePos tp = locate<TX, TY>(p, tile);
         const ClassDesc& d = p.cls[tp.c];
         const Grid g = d.g;
         const float* S = smem + s * TT::STAGE;
@@ -141,9 +145,6 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
         __syncthreads();
 
         // the replica's record (the same address for every thread of the CTA)
-        const RepRec* rp = d.recs + tp.rep;
-        int mode;
-        const TileArgs a = load_tile_args(rp, K + __ldg(&rp->toff), &mode);
         float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
 
         if (mode == 2)

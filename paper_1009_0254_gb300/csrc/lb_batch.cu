@@ -23,6 +23,7 @@
 #include "lb_ens.cuh"
 #include "lb_fft_core.cuh"
 #include "lb_noise.cuh"
+#include "lb_spectra.cuh"
 #include "lbfluct.h"
 
 namespace lbf {
@@ -275,7 +276,8 @@ __global__ void __launch_bounds__(1024) batch_cols_kernel(float2* data, int nx, 
     }
 }
 
-// per-replica radial bins (bins[rep][3][nbins]) from the class's bin table
+// per-replica radial bins (bins[rep][3][nbins]) from the class's bin table (lb_spectra.cuh;
+// blockIdx.y = replica)
 __global__ void batch_bin_kernel(const float2* __restrict__ z1, const float2* __restrict__ z2,
                                  const unsigned short* __restrict__ bin16, int nx, int ny, int nbins, double* bins) {
     extern __shared__ double sb[];
@@ -283,26 +285,9 @@ __global__ void batch_bin_kernel(const float2* __restrict__ z1, const float2* __
     __syncthreads();
     const int rep = blockIdx.y;
     const long long n = (long long)nx * ny;
-    const float2* a1 = z1 + rep * n;
-    const float2* a2 = z2 + rep * n;
-    const float tpx = 6.2831853071795865f / (float)nx, tpy = 6.2831853071795865f / (float)ny;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
-        const int b = bin16[o];
-        if (b == 0xFFFF) continue;
-        const int mx = (int)(o % nx), my = (int)(o / nx);
-        const int cx = (nx - mx) & (nx - 1), cy = (ny - my) & (ny - 1);
-        const float kx = tpx * (float)(mx > nx / 2 ? mx - nx : mx);
-        const float ky = tpy * (float)(my > ny / 2 ? my - ny : my);
-        const float inv = rsqrtf(kx * kx + ky * ky);
-        const float2 a = a1[o], am = a1[(long long)cy * nx + cx], c = a2[o];
-        const float rr = 0.5f * (a.x + am.x), ri = 0.5f * (a.y - am.y);
-        const float xr = 0.5f * (a.y + am.y), xi = -0.5f * (a.x - am.x);
-        const float lr = (kx * xr + ky * c.x) * inv, li = (kx * xi + ky * c.y) * inv;
-        const float tr = (-ky * xr + kx * c.x) * inv, ti = (-ky * xi + kx * c.y) * inv;
-        atomicAdd(&sb[b], (double)(rr * rr + ri * ri));
-        atomicAdd(&sb[nbins + b], (double)(lr * lr + li * li));
-        atomicAdd(&sb[2 * nbins + b], (double)(tr * tr + ti * ti));
-    }
+    const int wpb = blockDim.x >> 5;
+    bin_half_plane(z1 + rep * n, z2 + rep * n, bin16, nx, ny, nbins, sb, blockIdx.x * wpb + (threadIdx.x >> 5),
+                   gridDim.x * wpb);
     __syncthreads();
     double* out = bins + (long long)rep * 3 * nbins;
     for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x)
@@ -668,7 +653,8 @@ static int batch_sample(lb_batch* b, cudaStream_t s) {
             batch_cols_kernel<<<dim3(ci.nx / c, ci.R), fft_threads(ci.ny, c), csm, s>>>(z, ci.nx, ci.ny, c, twy, scale);
         }
         const size_t bsm = (size_t)3 * b->nbins * sizeof(double);
-        const int bx = std::max(1, std::min(64, (int)((size_t)ci.nx * ci.ny / 4096)));
+        const int units = (ci.ny / 2 + 1) * ((ci.nx / 2 + 32) / 32);   // warp work units per replica
+        const int bx = std::max(1, std::min(64, units / 32));
         batch_bin_kernel<<<dim3(bx, ci.R), 256, bsm, s>>>(z1, z2, reinterpret_cast<const unsigned short*>(cls_ptr(b, ci.off_bin16)),
                                                           ci.nx, ci.ny, b->nbins, reinterpret_cast<double*>(cls_ptr(b, ci.off_bins)));
         BCK(b, cudaGetLastError(), "spectra sample");

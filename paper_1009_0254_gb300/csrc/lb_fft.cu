@@ -9,9 +9,12 @@
 // adjacent columns), each an in-place Stockham FFT in shared memory (lb_fft_core.cuh)
 // with a twiddle table exp(-2 pi i q/n) computed on the host in FP64 (one read per
 // butterfly, its powers formed on the fly).
+#include <algorithm>
+
 #include "lb_fft_core.cuh"
 #include "lb_internal.cuh"
 #include "lb_noise.cuh"
+#include "lb_spectra.cuh"
 
 namespace lbf {
 
@@ -205,86 +208,15 @@ __device__ __forceinline__ int k_bin(int mx, int my, int nx, int ny, int nbins, 
     return b;
 }
 
-// Power of the three spectra at one wavevector k from Z1 = FT(drho + i jx) at k and -k and
-// Z2 = FT(jy) at k, added to s[0..2]: |drho(k)|^2, |k.j(k)|^2/|k|^2, |k x j(k)|^2/|k|^2.
-__device__ __forceinline__ void add_power3(float2 a, float2 am, float2 c, float kx, float ky, float s[3]) {
-    const float inv = rsqrtf(kx * kx + ky * ky);
-    // two real fields in one transform: drho(k) = (Z(k) + Z(-k)*)/2, jx(k) = (Z(k) - Z(-k)*)/(2i)
-    const float rr = 0.5f * (a.x + am.x), ri = 0.5f * (a.y - am.y);
-    const float xr = 0.5f * (a.y + am.y), xi = -0.5f * (a.x - am.x);
-    const float lr = (kx * xr + ky * c.x) * inv, li = (kx * xi + ky * c.y) * inv;
-    const float tr = (-ky * xr + kx * c.x) * inv, ti = (-ky * xi + kx * c.y) * inv;
-    s[0] += rr * rr + ri * ri;
-    s[1] += lr * lr + li * li;
-    s[2] += tr * tr + ti * ti;
-}
-
-// Radial spectra of one sample.  The bin of every wavevector was decided once, in FP64,
-// by bin_table_kernel; it depends on |k| only, so the up to four wavevectors (+-kx, +-ky)
-// share it.  A thread takes (mx, my) with mx <= nx/2, my <= ny/2 (lanes along mx, so the
-// loads coalesce) and sums the powers of the distinct points of that set in FP32.  Along a
-// row the bin does not decrease with mx, so the lanes of a warp that share a bin are
-// contiguous: a segmented reduction over them (FP32, at most 128 terms) leaves each run's
-// sum in its first lane, which adds it to the block's FP64 bins in shared memory; those are
-// added to the global FP64 bins at the end.
+// Radial spectra of one sample (lb_spectra.cuh): the block's warps share the half-plane
+// units, the block's FP64 bins in shared memory are added to the global bins at the end.
 __global__ void bin_kernel(const float2* __restrict__ z1, const float2* __restrict__ z2,
                            const unsigned short* __restrict__ bin16, int nx, int ny, int nbins, double* bins) {
     extern __shared__ double sb[];   // 3 * nbins
     for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x) sb[j] = 0.0;
     __syncthreads();
-    const int hx = nx / 2, hy = ny / 2;
-    const int lane = threadIdx.x & 31;
-    const float tpx = 6.2831853071795865f / (float)nx, tpy = 6.2831853071795865f / (float)ny;
-    for (int my = blockIdx.x; my <= hy; my += gridDim.x) {
-        const int cy = (ny - my) & (ny - 1);
-        const bool ypair = my != 0 && my != hy;          // -ky is another row
-        const float ky = tpy * (float)my;
-        const float kym = ypair ? -ky : ky;              // k_y of row cy (wrapped index)
-        const long long r0 = (long long)my * nx, r1 = (long long)cy * nx;
-        // every lane of a warp runs the same iterations (the reduction below needs them all)
-        for (int base = threadIdx.x - lane; base <= hx; base += blockDim.x) {
-            const int mx = base + lane;
-            int b = -1;                                  // no bin: beyond nx/2, or k = 0
-            float acc[3] = {0.f, 0.f, 0.f};
-            if (mx <= hx) {
-                const int bb = bin16[r0 + mx];
-                if (bb != 0xFFFF) {
-                    b = bb;
-                    const int cx = (nx - mx) & (nx - 1);
-                    const bool xpair = mx != 0 && mx != hx;      // -kx is another column
-                    const float kx = tpx * (float)mx;
-                    const float kxm = xpair ? -kx : kx;
-                    const float2 A1 = z1[r0 + mx], A2 = z1[r1 + cx];
-                    add_power3(A1, A2, z2[r0 + mx], kx, ky, acc);                       // (mx, my)
-                    if (xpair || ypair) add_power3(A2, A1, z2[r1 + cx], kxm, kym, acc);   // (-mx, -my)
-                    if (xpair && ypair) {
-                        const float2 A3 = z1[r0 + cx], A4 = z1[r1 + mx];
-                        add_power3(A3, A4, z2[r0 + cx], kxm, ky, acc);                  // (-mx, my)
-                        add_power3(A4, A3, z2[r1 + mx], kx, kym, acc);                  // (mx, -my)
-                    }
-                }
-            }
-            // segmented sum over the contiguous lanes of equal bin
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int bo = __shfl_down_sync(0xffffffffu, b, off);
-                const float v0 = __shfl_down_sync(0xffffffffu, acc[0], off);
-                const float v1 = __shfl_down_sync(0xffffffffu, acc[1], off);
-                const float v2 = __shfl_down_sync(0xffffffffu, acc[2], off);
-                if (lane + off < 32 && bo == b) {
-                    acc[0] += v0;
-                    acc[1] += v1;
-                    acc[2] += v2;
-                }
-            }
-            const int bp = __shfl_up_sync(0xffffffffu, b, 1);
-            if (b >= 0 && (lane == 0 || bp != b)) {
-                atomicAdd(&sb[b], (double)acc[0]);
-                atomicAdd(&sb[nbins + b], (double)acc[1]);
-                atomicAdd(&sb[2 * nbins + b], (double)acc[2]);
-            }
-        }
-    }
+    const int wpb = blockDim.x >> 5;
+    bin_half_plane(z1, z2, bin16, nx, ny, nbins, sb, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb);
     __syncthreads();
     for (int j = threadIdx.x; j < 3 * nbins; j += blockDim.x)
         if (sb[j] != 0.0) atomicAdd(&bins[j], sb[j]);
@@ -330,10 +262,9 @@ cudaError_t launch_stats_sample(const void* pops, int storage, const Grid& g, fl
     const size_t smem = (size_t)3 * nbins * sizeof(double);
     e = cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int bx = g.nx >= 512 ? 256 : 64;
-    const int rows = g.ny / 2 + 1;
-    const int nblk = rows < 304 ? rows : 304;   // two blocks per SM, each over many rows
-    bin_kernel<<<nblk, bx, smem, s>>>(z1, z2, bin16, g.nx, g.ny, nbins, bins);
+    const long long units = (long long)(g.ny / 2 + 1) * ((g.nx / 2 + 32) / 32);   // warp work units
+    const int nblk = (int)std::min<long long>(304, std::max<long long>(1, units / 32));   // <= 2 per SM
+    bin_kernel<<<nblk, 256, smem, s>>>(z1, z2, bin16, g.nx, g.ny, nbins, bins);
     return cudaGetLastError();
 }
 

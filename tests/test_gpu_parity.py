@@ -219,8 +219,10 @@ def test_reproducible_and_resumable(kernel):
     assert not np.array_equal(pa, d.populations())
 
 
-def test_spectra_match_oracle():
-    nx, ny, nb = 64, 32, 24
+@pytest.mark.parametrize("nx,ny,nb", [(64, 32, 24), (256, 128, 64), (2, 8, 4), (8, 2, 4), (128, 512, 300)])
+def test_spectra_match_oracle(nx, ny, nb):
+    # half-plane binning: rows with and without a mirror row, lanes beyond nx/2, several
+    # warp units per row, more bins than wavevectors in some
     g, o = _pair(nx, ny, 21, 1.0, 1 / 3, (1e-4, 0.02, 0.8, 1.0, 1.0), lbf.LB_NOISE_LW, 0.01)
     g.set_sampling(1, nb)
     g.step(3)

@@ -11,8 +11,8 @@ density stencil, equilibrium, MRT relaxation, noise, back-transform, store) plus
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-(--n, --noise full, --no-variants and --no-cpu-baseline select smaller or other main lines
-for profiling runs.)
+(--n, --noise full, --no-variants, --no-cpu-baseline and --batched-only select smaller or
+other runs for profiling.)
 
 With N > 1 (launched by torch.distributed.run) every rank steps its own independent
 lattice (replicas; the method has no exchange between independent runs): weak scaling.
@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--batched-only", action="store_true",
+                   help="run only the batched-ensemble variant and print its JSON (profiling runs)")
     p.add_argument("--noise", default="lw", choices=["lw", "full"],
                    help="noise of the main line (full: correlated, kappa=0.05; for profiling runs)")
     return p.parse_args()
@@ -483,6 +485,9 @@ def main():
     if dist is not None:
         dist.barrier()
     lbf.load()
+    if args.batched_only:
+        print(json.dumps(batched_variant(lbf, torch)))
+        return 0
 
     n = args.n
     nodes = n * n

@@ -113,9 +113,17 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
         if (first < ntiles) issue(first, 0);
         if (first + (int)gridDim.x < ntiles) issue(first + gridDim.x, 1);
     }
+    __syncthreads();   // the slots and origins of the first two tiles are visible to all
     int k = 0;
     for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
         const int s = k & 1;
+        // the tile's slot, origin and record are read while its populations are in flight
+        // (stage s's entries were written before the previous barrier)
+        const int slot = st_slot[s], x0 = st_x0[s], y0 = st_y0[s];
+        const SlotDesc* d = p.desc + slot;
+        const long long sl = K - __ldg(&d->k_start);
+        int mode;
+        const TileArgs a = load_tile_args(p.recs + slot, sl, &mode);
         const bool ok = mbar_wait_bounded(smem_u32(&mbar[s]), (uint32_t)((k >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -126,12 +134,9 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
             }
             break;
         }
-        const int slot = st_slot[s], x0 = st_x0[s], y0 = st_y0[s];
-        const SlotDesc* d = p.desc + slot;
         Grid g;
         g.nx = __ldg(&d->g.nx); g.ny = __ldg(&d->g.ny); g.gx = __ldg(&d->g.gx);
         g.pitch = __ldg(&d->g.pitch); g.plane = __ldg(&d->g.plane);
-        const long long sl = K - __ldg(&d->k_start);
         float* dst = (sl & 1) ? d->buf[0] : d->buf[1];
         const float* S = smem + s * TT::STAGE;
 
@@ -147,8 +152,6 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
         }
         __syncthreads();
 
-        int mode;
-        const TileArgs a = load_tile_args(p.recs + slot, sl, &mode);
         if (mode == 2) tile_nodes<2, TX, TY, NT>(a, S, R, g, x0, y0, dst, d->xi);
         else if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
         else tile_nodes<0, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);

@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
     float* smem = reinterpret_cast<float*>(smem_raw);
     float* R = reinterpret_cast<float*>(smem_raw + 2 * TT::STAGE_BYTES);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(R + TT::RW * TT::RH);
+    __shared__ TileArgs sargs;          // the record of the current tile
+    __shared__ int smode;
     const int tid = threadIdx.x;
     const long long K = __ldcg(p.kstep);
     const int par = (int)(K & 1);
@@ -112,11 +114,7 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
     int k = 0;
     for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
         const int s = k & 1;
-        // the tile's replica record is read while its populations are still in flight
         const TilePos tp = locate<TX, TY>(p, tile);
-        const RepRec* rp = p.cls[tp.c].recs + tp.rep;
-        int mode;
-        const TileArgs a = load_tile_args(rp, K + __ldg(&rp->toff), &mode);
         const bool ok = mbar_wait_bounded(smem_u32(&mbar[s]), (uint32_t)((k >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -132,33 +130,31 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
         const ClassDesc& d = p.cls[tp.c];
         const Grid g = d.g;
         const float* S = smem + s * TT::STAGE;
-
-        constexpr int NA = (TT::RW * TT::RH + NT - 1) / NT;
-#pragma unroll
-        for (int it = 0; it < NA; ++it) {
-            const int q = tid + it * NT;
-            if (q >= TT::RW * TT::RH) break;
-            const int ry = q / TT::RW, rx = q - ry * TT::RW;
-            float f[Q];
-            load9_ps<TT::PS>(S, ry * TT::BW + rx + TT::XO - 1, f);
-            R[q] = drho_of(f);
+        // the tile's replica record, to shared memory (its last readers, the previous tile's
+        // collision, are past the barrier above; measured faster than a copy per thread in
+        // registers, which the pulled populations need, and than loading it before the wait)
+        if (tid == 0) {
+            const RepRec* rp = p.cls[tp.c].recs + tp.rep;
+            sargs = load_tile_args(rp, K + __ldg(&rp->toff), &smode);
         }
-        __syncthreads();
 
-        // the replica's record (the same address for every thread of the CTA)
-        float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
-
-        if (mode == 2)
-            tile_nodes<2, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst, d.xi + (long long)tp.rep * g.nx * g.ny);
-        else if (mode)
-            tile_nodes<1, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst, nullptr);
-        else
-            tile_nodes<0, TX, TY, NT>(a, S, R, g, tp.x0, tp.y0, dst, nullptr);
+        // pulled populations stay in registers across the density barrier; the stage is
+        // refilled right after it
+        float fr[TX * TY / NT][Q];
+        tile_pull<TX, TY, NT>(S, R, fr);
         __syncthreads();
         if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(tile + 2 * gridDim.x, s);
         }
+        const int mode = smode;
+        float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
+        if (mode == 2)
+            tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, d.xi + (long long)tp.rep * g.nx * g.ny);
+        else if (mode)
+            tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr);
+        else
+            tile_nodes<0, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr);
     }
     // Every CTA read K before arriving here; the last one to arrive advances it for the
     // next step (the next launch sees it, kernel boundaries order the accesses).

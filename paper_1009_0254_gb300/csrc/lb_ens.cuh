@@ -42,21 +42,47 @@ __device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t
     return a;
 }
 
-// Collide and stream the TX x TY nodes of one tile from the staged populations S and the
-// density tile R (with its one-node ring).
-template <int MODE, int TX, int TY, int NT>
-__device__ __forceinline__ void tile_nodes(const TileArgs& a, const float* S, const float* R, const Grid& g, int x0,
-                                           int y0, float* dst, const float2* __restrict__ xi49) {
+// Pulls the nine deviations of this thread's nodes of the staged tile S into registers
+// (fr) and writes the density deviation of the tile and of its one-node ring (from the
+// halo) into R.  After a CTA barrier the stage is no longer read.
+template <int TX, int TY, int NT>
+__device__ __forceinline__ void tile_pull(const float* S, float* R, float (&fr)[TX * TY / NT][Q]) {
     using TT = TmaTile<TX, TY, float>;
     static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
 #pragma unroll
     for (int it = 0; it < TX * TY / NT; ++it) {
         const int q = threadIdx.x + it * NT;
         const int ly = q / TX, lx = q - ly * TX;
+        load9_ps<TT::PS>(S, (ly + 1) * TT::BW + lx + TT::XO, fr[it]);
+        R[(ly + 1) * TT::RW + lx + 1] = drho_of(fr[it]);
+    }
+    // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
+    constexpr int NB = 2 * (TX + 2) + 2 * TY;
+    for (int j = threadIdx.x; j < NB; j += NT) {
+        int rx, ry;
+        if (j < TX + 2) { rx = j; ry = 0; }
+        else if (j < 2 * (TX + 2)) { rx = j - (TX + 2); ry = TY + 1; }
+        else { const int u = j - 2 * (TX + 2); ry = 1 + (u >> 1); rx = (u & 1) ? TX + 1 : 0; }
+        float h[Q];
+        load9_ps<TT::PS>(S, ry * TT::BW + rx + TT::XO - 1, h);
+        R[ry * TT::RW + rx] = drho_of(h);
+    }
+}
+
+// Collide and stream the TX x TY nodes of one tile from the pulled deviations fr and the
+// density tile R (with its one-node ring).  The record a is the tile's lattice, held in
+// shared memory by the callers (registers are taken by fr).
+template <int MODE, int TX, int TY, int NT>
+__device__ __forceinline__ void tile_nodes(const TileArgs& a, const float (&fr)[TX * TY / NT][Q], const float* R,
+                                           const Grid& g, int x0, int y0, float* dst,
+                                           const float2* __restrict__ xi49) {
+    using TT = TmaTile<TX, TY, float>;
+#pragma unroll
+    for (int it = 0; it < TX * TY / NT; ++it) {
+        const int q = threadIdx.x + it * NT;
+        const int ly = q / TX, lx = q - ly * TX;
         const int x = x0 + lx, y = y0 + ly;
         if (x >= g.nx || y >= g.ny) continue;
-        float f[Q];
-        load9_ps<TT::PS>(S, (ly + 1) * TT::BW + lx + TT::XO, f);
         const int rc = (ly + 1) * TT::RW + lx + 1;
         Nbr r;
         r.C = R[rc];
@@ -68,7 +94,7 @@ __device__ __forceinline__ void tile_nodes(const TileArgs& a, const float* S, co
         float2 z = make_float2(0.f, 0.f);
         if (MODE == 2) z = xi49[(long long)y * g.nx + x];
         float o[Q];
-        collide_node<MODE>(a, f, r, node, z, o);
+        collide_node<MODE>(a, fr[it], r, node, z, o);
         store9(dst, g.plane, g, x, y, o);
     }
 }

@@ -73,6 +73,8 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
     float* R = reinterpret_cast<float*>(smem_raw + 2 * TT::STAGE_BYTES);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(R + TT::RW * TT::RH);
     __shared__ int st_slot[2], st_x0[2], st_y0[2];
+    __shared__ TileArgs sargs;          // the record of the current tile
+    __shared__ int smode;
     const int tid = threadIdx.x;
     const long long K = __ldcg(p.kstep);
     const int ntiles = p.ntiles;
@@ -117,13 +119,11 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
     int k = 0;
     for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
         const int s = k & 1;
-        // the tile's slot, origin and record are read while its populations are in flight
-        // (stage s's entries were written before the previous barrier)
+        // the tile's slot and origin (written before the previous barrier) are read while
+        // its populations are in flight
         const int slot = st_slot[s], x0 = st_x0[s], y0 = st_y0[s];
         const SlotDesc* d = p.desc + slot;
         const long long sl = K - __ldg(&d->k_start);
-        int mode;
-        const TileArgs a = load_tile_args(p.recs + slot, sl, &mode);
         const bool ok = mbar_wait_bounded(smem_u32(&mbar[s]), (uint32_t)((k >> 1) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
@@ -139,27 +139,23 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
         g.pitch = __ldg(&d->g.pitch); g.plane = __ldg(&d->g.plane);
         float* dst = (sl & 1) ? d->buf[0] : d->buf[1];
         const float* S = smem + s * TT::STAGE;
+        // the slot's record, to shared memory (its last readers, the previous tile's
+        // collision, are past the barrier above)
+        if (tid == 0) sargs = load_tile_args(p.recs + slot, sl, &smode);
 
-        constexpr int NA = (TT::RW * TT::RH + NT - 1) / NT;
-#pragma unroll
-        for (int it = 0; it < NA; ++it) {
-            const int q = tid + it * NT;
-            if (q >= TT::RW * TT::RH) break;
-            const int ry = q / TT::RW, rx = q - ry * TT::RW;
-            float f[Q];
-            load9_ps<TT::PS>(S, ry * TT::BW + rx + TT::XO - 1, f);
-            R[q] = drho_of(f);
-        }
-        __syncthreads();
-
-        if (mode == 2) tile_nodes<2, TX, TY, NT>(a, S, R, g, x0, y0, dst, d->xi);
-        else if (mode) tile_nodes<1, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
-        else tile_nodes<0, TX, TY, NT>(a, S, R, g, x0, y0, dst, nullptr);
+        // pulled populations stay in registers across the density barrier; the stage is
+        // refilled right after it (slot, x0, y0 are in registers by then)
+        float fr[TX * TY / NT][Q];
+        tile_pull<TX, TY, NT>(S, R, fr);
         __syncthreads();
         if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(tile + 2 * gridDim.x, s);
         }
+        const int mode = smode;
+        if (mode == 2) tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, d->xi);
+        else if (mode) tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
+        else tile_nodes<0, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
     }
     if (tid == 0) {
         const unsigned int prev = atomicAdd(p.done, 1u);

@@ -581,7 +581,7 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
         if (kmode == 2) {
             NoiseGenArgs ga = c->ga;
             ga.t_lo = tlo; ga.t_hi = thi;
-            CK(c, launch_noise49(c->z1, ga, c->twx, c->twy, c->stream), "correlated noise");
+            CK(c, launch_noise49(c->z1, c->z2, ga, c->twx, c->twy, c->stream), "correlated noise");
             c->kernels += 2;
         }
         StepArgs a = c->sa;

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(1024) batch_noise_cols_kernel(float2* out, con
     ga.t_hi = (uint32_t)((unsigned long long)t >> 32);
     ga.rk.k0 = __ldg(&rp->k0);
     ga.rk.k1 = __ldg(&rp->k1);
-    noise_cols_block(out + (long long)blockIdx.y * nx * ny, ga, count, blockIdx.x, twy);
+    noise_cols_block<false>(out + (long long)blockIdx.y * nx * ny, ga, count, blockIdx.x, twy);
 }
 
 // Second pass: back along x (unitary scale), one CTA per row of a correlated replica.

@@ -302,8 +302,8 @@ bool make_pop_tensor_map(const void* buf, const Grid& g, int tile, int fp16, voi
 int tma_tile_count();
 int tma_default_tile(int noise_mode, int fp16);
 size_t tensor_map_bytes();
-cudaError_t launch_noise49(float2* buf, const NoiseGenArgs& ga, const float2* twx, const float2* twy,
-                           cudaStream_t s);
+cudaError_t launch_noise49(float2* buf, float2* scratch, const NoiseGenArgs& ga, const float2* twx,
+                           const float2* twy, cudaStream_t s);
 cudaError_t launch_noise49_d(double2* buf, const NoiseGenArgsD& ga, const double2* twx, const double2* twy,
                              cudaStream_t s);
 int noise_strip_d(int nx, int ny);

@@ -79,11 +79,31 @@ __device__ __forceinline__ int paired_column(int b, int q, int count, int nx) {
     return mirror ? nx - j : j;
 }
 
+// Position of H(k_x, y) in the column-permuted layout of the column pass: row y holds its
+// nx values with the `count` columns of block b contiguous, element (y nx + b count + q),
+// q the slot of k_x in paired_column.  A row pass gathers row y (one contiguous row) from it.
+__device__ __forceinline__ long long strip_index(int x, int y, int nx, int ny, int count) {
+    const int half = count >> 1, hx = nx >> 1;
+    int b, q;
+    if (x == 0) { b = 0; q = 0; }
+    else if (x == hx) { b = 0; q = half; }
+    else {
+        const bool m = x > hx;
+        const int j = m ? nx - x : x;          // 1 .. nx/2 - 1
+        b = j / half;
+        q = (j - b * half) + (m ? half : 0);
+    }
+    return (long long)y * nx + b * count + q;
+}
+
 // Correlated noise, first pass, for column block b: the CTA synthesises `count` k-space
 // columns (half of them the mirrors of the others, so every (k, -k) draw is made once) for
 // every k_y straight into shared memory (count * ny float2, padded), transforms them back
-// along y and writes the partial result H(k_x, y) to out; a row pass finishes along x.
-template <typename GA, typename C>
+// along y and writes the partial result H(k_x, y) to out: STRIP, in the column-permuted
+// layout of strip_index (the block's count values of a row are one contiguous piece, a full
+// 32-byte sector for count = 4, where the natural order splits them into two 16-byte pieces
+// at k_x and -k_x), else row-major in place; a row pass finishes along x.
+template <bool STRIP, typename GA, typename C>
 __device__ __forceinline__ void noise_cols_block(C* out, const GA& ga, int count, int b,
                                                  const C* __restrict__ twy) {
     extern __shared__ __align__(16) unsigned char noise_smem[];
@@ -117,9 +137,38 @@ __device__ __forceinline__ void noise_cols_block(C* out, const GA& ga, int count
         }
     }
     stockham_fft_out(sm, ny, log2n, count, -1, twy, [&](int e, C v) {
-        const int q = e & (count - 1), y = e >> lc;
-        out[(long long)y * ga.nx + paired_column(b, q, count, ga.nx)] = v;
+        if (STRIP) {
+            const int q = e & (count - 1), y = e >> lc;
+            out[(long long)y * ga.nx + b * count + q] = v;
+        } else {
+            const int q = e & (count - 1), y = e >> lc;
+            out[(long long)y * ga.nx + paired_column(b, q, count, ga.nx)] = v;
+        }
     });
+}
+
+// Correlated noise, second pass, for row y: H(., y) gathered from the column-permuted layout
+// src (written by noise_cols_block<true> with blocks of `count` columns), transformed back
+// along x and scaled (the unitary n^-1/2), written to row y of dst (row-major).  One CTA per
+// row with fft_threads(nx, 1) threads and fft_smem_bytes(nx, 1) of shared memory.
+template <typename C, typename R>
+__device__ __forceinline__ void noise_rows_gather(const C* __restrict__ src, C* __restrict__ dst, int nx, int ny,
+                                                  int count, int y, const C* __restrict__ twx, R scale) {
+    extern __shared__ __align__(16) unsigned char noise_smem[];
+    C* sm = reinterpret_cast<C*>(noise_smem);
+    C* rowp = dst + (long long)y * nx;
+    const int log2n = 31 - __clz(nx);
+    if (nx >= 256) {
+        stockham_fft_io(sm, nx, log2n, 1, -1, twx, [&](int e) { return src[strip_index(e, y, nx, ny, count)]; },
+                        [&](int e, C v) { rowp[e] = c_make(v.x * scale, v.y * scale); });
+        return;
+    }
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = src[strip_index(j, y, nx, ny, count)];
+    stockham_fft(sm, nx, log2n, 1, -1, twx);
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+        const C v = sm[fpad(j)];
+        rowp[j] = c_make(v.x * scale, v.y * scale);
+    }
 }
 
 }  // namespace lbf

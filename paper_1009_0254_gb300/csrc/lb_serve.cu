@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(1024) serve_noise_cols_kernel(const int* __res
     ga.t_hi = (uint32_t)((unsigned long long)t >> 32);
     ga.rk.k0 = __ldg(&rp->k0);
     ga.rk.k1 = __ldg(&rp->k1);
-    noise_cols_block(desc[slot].xi, ga, count, blockIdx.x, twy);
+    noise_cols_block<false>(desc[slot].xi, ga, count, blockIdx.x, twy);
 }
 
 __global__ void __launch_bounds__(1024) serve_noise_rows_kernel(const int* __restrict__ slots,

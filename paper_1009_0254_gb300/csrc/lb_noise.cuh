@@ -83,17 +83,14 @@ __device__ __forceinline__ int paired_column(int b, int q, int count, int nx) {
 // nx values with the `count` columns of block b contiguous, element (y nx + b count + q),
 // q the slot of k_x in paired_column.  A row pass gathers row y (one contiguous row) from it.
 __device__ __forceinline__ long long strip_index(int x, int y, int nx, int ny, int count) {
+    // count is a power of two: block b and slot of k_x = j (or nx - j) by shifts and masks
     const int half = count >> 1, hx = nx >> 1;
-    int b, q;
-    if (x == 0) { b = 0; q = 0; }
-    else if (x == hx) { b = 0; q = half; }
-    else {
-        const bool m = x > hx;
-        const int j = m ? nx - x : x;          // 1 .. nx/2 - 1
-        b = j / half;
-        q = (j - b * half) + (m ? half : 0);
-    }
-    return (long long)y * nx + b * count + q;
+    const int lh = __ffs(half) - 1;
+    const bool m = x > hx;
+    const int j = m ? nx - x : x;              // 0 .. nx/2
+    int p = ((j >> lh) << (lh + 1)) + (j & (half - 1)) + (m ? half : 0);    // b count + q
+    if (x == hx) p = half;                     // block 0 pairs k_x = 0 (slot 0) with nx/2
+    return (long long)y * nx + p;
 }
 
 // Correlated noise, first pass, for column block b: the CTA synthesises `count` k-space

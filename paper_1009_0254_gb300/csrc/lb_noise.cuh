@@ -82,7 +82,7 @@ __device__ __forceinline__ int paired_column(int b, int q, int count, int nx) {
 // Position of H(k_x, y) in the column-permuted layout of the column pass: row y holds its
 // nx values with the `count` columns of block b contiguous, element (y nx + b count + q),
 // q the slot of k_x in paired_column.  A row pass gathers row y (one contiguous row) from it.
-__device__ __forceinline__ long long strip_index(int x, int y, int nx, int ny, int count) {
+__device__ __forceinline__ long long perm_index(int x, int y, int nx, int count) {
     // count is a power of two: block b and slot of k_x = j (or nx - j) by shifts and masks
     const int half = count >> 1, hx = nx >> 1;
     const int lh = __ffs(half) - 1;
@@ -96,11 +96,11 @@ __device__ __forceinline__ long long strip_index(int x, int y, int nx, int ny, i
 // Correlated noise, first pass, for column block b: the CTA synthesises `count` k-space
 // columns (half of them the mirrors of the others, so every (k, -k) draw is made once) for
 // every k_y straight into shared memory (count * ny float2, padded), transforms them back
-// along y and writes the partial result H(k_x, y) to out: STRIP, in the column-permuted
-// layout of strip_index (the block's count values of a row are one contiguous piece, a full
+// along y and writes the partial result H(k_x, y) to out: PERM, in the column-permuted
+// layout of perm_index (the block's count values of a row are one contiguous piece, a full
 // 32-byte sector for count = 4, where the natural order splits them into two 16-byte pieces
 // at k_x and -k_x), else row-major in place; a row pass finishes along x.
-template <bool STRIP, typename GA, typename C>
+template <bool PERM, typename GA, typename C>
 __device__ __forceinline__ void noise_cols_block(C* out, const GA& ga, int count, int b,
                                                  const C* __restrict__ twy) {
     extern __shared__ __align__(16) unsigned char noise_smem[];
@@ -134,13 +134,8 @@ __device__ __forceinline__ void noise_cols_block(C* out, const GA& ga, int count
         }
     }
     stockham_fft_out(sm, ny, log2n, count, -1, twy, [&](int e, C v) {
-        if (STRIP) {
-            const int q = e & (count - 1), y = e >> lc;
-            out[(long long)y * ga.nx + b * count + q] = v;
-        } else {
-            const int q = e & (count - 1), y = e >> lc;
-            out[(long long)y * ga.nx + paired_column(b, q, count, ga.nx)] = v;
-        }
+        const int q = e & (count - 1), y = e >> lc;
+        out[(long long)y * ga.nx + (PERM ? b * count + q : paired_column(b, q, count, ga.nx))] = v;
     });
 }
 
@@ -156,11 +151,11 @@ __device__ __forceinline__ void noise_rows_gather(const C* __restrict__ src, C* 
     C* rowp = dst + (long long)y * nx;
     const int log2n = 31 - __clz(nx);
     if (nx >= 256) {
-        stockham_fft_io(sm, nx, log2n, 1, -1, twx, [&](int e) { return src[strip_index(e, y, nx, ny, count)]; },
+        stockham_fft_io(sm, nx, log2n, 1, -1, twx, [&](int e) { return src[perm_index(e, y, nx, count)]; },
                         [&](int e, C v) { rowp[e] = c_make(v.x * scale, v.y * scale); });
         return;
     }
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = src[strip_index(j, y, nx, ny, count)];
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = src[perm_index(j, y, nx, count)];
     stockham_fft(sm, nx, log2n, 1, -1, twx);
     for (int j = threadIdx.x; j < nx; j += blockDim.x) {
         const C v = sm[fpad(j)];

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(1024) noise_cols_kernel(float2* out, NoiseGenA
 
 __global__ void __launch_bounds__(1024) noise_rows_kernel(const float2* __restrict__ h, float2* xi, int nx, int ny,
                                                           int count, const float2* __restrict__ twx, float scale) {
-    noise_rows_gather(h, xi, nx, ny, count, (int)blockIdx.x, twx, scale);
+    noise_rows_gather(h, xi, nx, count, (int)blockIdx.x, twx, scale);
 }
 
 // FP64 storage: the same two passes of the correlated noise in FP64 (rows: one CTA per row).

@@ -144,8 +144,8 @@ __device__ __forceinline__ void noise_cols_block(C* out, const GA& ga, int count
 // along x and scaled (the unitary n^-1/2), written to row y of dst (row-major).  One CTA per
 // row with fft_threads(nx, 1) threads and fft_smem_bytes(nx, 1) of shared memory.
 template <typename C, typename R>
-__device__ __forceinline__ void noise_rows_gather(const C* __restrict__ src, C* __restrict__ dst, int nx, int ny,
-                                                  int count, int y, const C* __restrict__ twx, R scale) {
+__device__ __forceinline__ void noise_rows_gather(const C* __restrict__ src, C* __restrict__ dst, int nx, int count,
+                                                  int y, const C* __restrict__ twx, R scale) {
     extern __shared__ __align__(16) unsigned char noise_smem[];
     C* sm = reinterpret_cast<C*>(noise_smem);
     C* rowp = dst + (long long)y * nx;

@@ -193,23 +193,34 @@ __global__ void __launch_bounds__(1024) batch_noise_cols_kernel(float2* out, con
     noise_cols_block<false>(out + (long long)blockIdx.y * nx * ny, ga, count, blockIdx.x, twy);
 }
 
-// Second pass: back along x (unitary scale), one CTA per row of a correlated replica.
+// Second pass: back along x (unitary scale).  Rows of 256 points and more: one CTA per row.
+// Shorter rows: `rows` rows per CTA (a power of two dividing ny, so all of one replica),
+// transformed together as interleaved sequences so that a CTA holds ~512 points instead of
+// a single warp's worth.
 __global__ void __launch_bounds__(1024) batch_noise_rows_kernel(float2* data, const RepRec* __restrict__ recs,
-                                                                int nx, int ny, const float2* __restrict__ twx,
-                                                                float scale) {
-    if (__ldg(&recs[blockIdx.x / ny].mode) != 2) return;
+                                                                int nx, int ny, int rows,
+                                                                const float2* __restrict__ twx, float scale) {
+    const long long row0 = (long long)blockIdx.x * rows;
+    if (__ldg(&recs[row0 / ny].mode) != 2) return;
     extern __shared__ float2 sm[];
-    float2* rowp = data + (long long)blockIdx.x * nx;
+    float2* base = data + row0 * nx;
+    const int log2n = 31 - __clz(nx);
     if (nx >= 256) {
-        stockham_fft_io(sm, nx, 31 - __clz(nx), 1, -1, twx, [&](int e) { return rowp[e]; },
-                        [&](int e, float2 v) { rowp[e] = make_float2(v.x * scale, v.y * scale); });
+        stockham_fft_io(sm, nx, log2n, 1, -1, twx, [&](int e) { return base[e]; },
+                        [&](int e, float2 v) { base[e] = make_float2(v.x * scale, v.y * scale); });
         return;
     }
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) sm[fpad(j)] = rowp[j];
-    stockham_fft(sm, nx, 31 - __clz(nx), 1, -1, twx);
-    for (int j = threadIdx.x; j < nx; j += blockDim.x) {
-        const float2 v = sm[fpad(j)];
-        rowp[j] = make_float2(v.x * scale, v.y * scale);
+    // element j of row r at sm[fpad(j rows + r)]; global loads and stores stay row-contiguous
+    const int lr = 31 - __clz(rows), total = rows * nx;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int r = i >> log2n, j = i & (nx - 1);
+        sm[fpad((j << lr) + r)] = base[i];
+    }
+    stockham_fft(sm, nx, log2n, rows, -1, twx);
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int r = i >> log2n, j = i & (nx - 1);
+        const float2 v = sm[fpad((j << lr) + r)];
+        base[i] = make_float2(v.x * scale, v.y * scale);
     }
 }
 
@@ -600,6 +611,14 @@ static int col_strip_b(int nx, int ny) {
 
 // correlated noise (xi_4, xi_9) of every correlated replica of class ci for the coming step,
 // into the class's first spectra buffer (free between samples)
+// rows per CTA of the noise row pass: ~512 points for rows shorter than 256 (ny and the
+// result powers of two, the result <= ny)
+static int noise_rows_per_cta(int nx, int ny) {
+    if (nx >= 256) return 1;
+    int r = 512 / nx;
+    return r > ny ? ny : r;
+}
+
 static int batch_noise(lb_batch* b, const ClassInfo& ci) {
     float2* xi = reinterpret_cast<float2*>(cls_ptr(b, ci.off_z1));
     const RepRec* recs = reinterpret_cast<const RepRec*>(cls_ptr(b, ci.off_recs));
@@ -609,8 +628,10 @@ static int batch_noise(lb_batch* b, const ClassInfo& ci) {
         reinterpret_cast<const float2*>(cls_ptr(b, ci.off_tw_y)), reinterpret_cast<const float*>(cls_ptr(b, ci.off_cosx)),
         reinterpret_cast<const float*>(cls_ptr(b, ci.off_cosy)));
     const float scale = (float)(1.0 / std::sqrt((double)ci.nx * ci.ny));
-    batch_noise_rows_kernel<<<ci.R * ci.ny, fft_threads(ci.nx, 1), fft_smem_bytes(ci.nx, 1), b->stream>>>(
-        xi, recs, ci.nx, ci.ny, reinterpret_cast<const float2*>(cls_ptr(b, ci.off_tw_x)), scale);
+    const int rows = noise_rows_per_cta(ci.nx, ci.ny);
+    batch_noise_rows_kernel<<<ci.R * ci.ny / rows, fft_threads(ci.nx, rows), fft_smem_bytes(ci.nx, rows),
+                              b->stream>>>(xi, recs, ci.nx, ci.ny, rows,
+                                           reinterpret_cast<const float2*>(cls_ptr(b, ci.off_tw_x)), scale);
     BCK(b, cudaGetLastError(), "correlated noise");
     b->kernels += 2;
     return LB_OK;
@@ -750,7 +771,7 @@ int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* see
             // shared memory of the correlated-noise kernels, set before any graph capture
             const int c = col_strip_b(ci.nx, ci.ny);
             noise_csm = std::max(noise_csm, fft_smem_bytes(ci.ny, c));
-            noise_rsm = std::max(noise_rsm, fft_smem_bytes(ci.nx, 1));
+            noise_rsm = std::max(noise_rsm, fft_smem_bytes(ci.nx, noise_rows_per_cta(ci.nx, ci.ny)));
         }
     }
     for (int r = 0; r < count && e == cudaSuccess; ++r) {

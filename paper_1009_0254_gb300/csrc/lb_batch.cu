@@ -609,8 +609,6 @@ static int col_strip_b(int nx, int ny) {
     return c > nx ? nx : c;
 }
 
-// correlated noise (xi_4, xi_9) of every correlated replica of class ci for the coming step,
-// into the class's first spectra buffer (free between samples)
 // rows per CTA of the noise row pass: ~512 points for rows shorter than 256 (ny and the
 // result powers of two, the result <= ny)
 static int noise_rows_per_cta(int nx, int ny) {
@@ -619,6 +617,8 @@ static int noise_rows_per_cta(int nx, int ny) {
     return r > ny ? ny : r;
 }
 
+// correlated noise (xi_4, xi_9) of every correlated replica of class ci for the coming step,
+// into the class's first spectra buffer (free between samples)
 static int batch_noise(lb_batch* b, const ClassInfo& ci) {
     float2* xi = reinterpret_cast<float2*>(cls_ptr(b, ci.off_z1));
     const RepRec* recs = reinterpret_cast<const RepRec*>(cls_ptr(b, ci.off_recs));

@@ -65,7 +65,8 @@ def test_parity_64x64_config1(mode, kernel):
 
 @pytest.mark.parametrize("nx,ny,mode", [(6, 10, "lw"), (33, 17, "lw"), (100, 36, "diag"), (2, 2, "lw"),
                                         (37, 5, "off"), (64, 32, "full"), (16, 128, "full"), (2, 8, "full"),
-                                        (300, 20, "lw"), (129, 9, "diag"), (256, 8, "full")])
+                                        (300, 20, "lw"), (129, 9, "diag"), (256, 8, "full"), (512, 2, "full"),
+                                        (1024, 4, "full")])
 def test_parity_ragged_and_small_lattices(nx, ny, mode, kernel):
     g, o = _pair(nx, ny, 7, 1.0, 1 / 3, (2e-4, 0.02, 0.8, 1.0, 1.0), MODES[mode], 0.01)
     g.step(60)

@@ -92,6 +92,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash(names):
+    """sha256 of the listed sources with // comments, trailing blanks and empty lines removed
+    (a comment edit leaves the compiled kernel, and so its counters, unchanged)."""
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, name)) as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
 def step_kernel_traffic(nodes):
     """DRAM bytes per step-kernel launch from a committed ncu capture, scaled by nodes,
     or None when the kernel source changed since the capture."""
@@ -101,11 +114,7 @@ def step_kernel_traffic(nodes):
             d = json.load(f)
     except Exception:
         return None
-    h = hashlib.sha256()
-    for name in d.get("sources", []):
-        with open(os.path.join(ROOT, name), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != d.get("source_sha256"):
+    if kernel_source_hash(d.get("sources", [])) != d.get("source_sha256"):
         return None
     return float(d["dram_bytes_per_launch"]) * nodes / float(d["nodes"])
 

@@ -1,9 +1,10 @@
 // lb_step_tma.cu -- the fused fluctuating D2Q9 step, TMA-staged and persistent.
 //
 // Same arithmetic as lb_step.cu (collide_node), different data movement:
-//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles (32 x 16 by
-//     default) in row-major tile order, so the tiles in flight form a band whose halo rows
-//     are still in L2 when the neighbouring tile reads them;
+//   * a persistent grid (resident CTAs only) walks the lattice in TX x TY tiles (the shape
+//     chosen per noise mode and storage, tma_default_tile) in row-major tile order, so the
+//     tiles in flight form a band whose halo rows are still in L2 when the neighbouring tile
+//     reads them;
 //   * for each tile one thread issues nine 3D TMA loads (cp.async.bulk.tensor), one per
 //     population plane, of the box [x0 - 4, x0 + TX + 4) x [y0 - 1 - cy_i, y0 + TY + 1 - cy_i)
 //     into shared memory; the y offset of plane i absorbs its streaming shift, so node

@@ -80,6 +80,8 @@ def parse():
                    help="run only the batched-ensemble variant and print its JSON (profiling runs)")
     p.add_argument("--noise", default="lw", choices=["lw", "full"],
                    help="noise of the main line (full: correlated, kappa=0.05; for profiling runs)")
+    p.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
+                   help="population storage of the main line (fp16: deviations; for profiling runs)")
     return p.parse_args()
 
 
@@ -120,7 +122,10 @@ def step_kernel_traffic(nodes):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples (every 20 ms) of SM clock and throttle reasons during the timed
+    region.  The sampler runs on until the whole bench has finished, so a timed region
+    shorter than 0.1 s is widened by 0.1 s on either side (warm-up before it, the next
+    measurement after it); the record says so."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -131,7 +136,7 @@ class ClockSampler:
         self.lines = []
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -150,6 +155,14 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        if t1 - t0 >= 0.1:
+            return self._summary(t0, t1)
+        rec = self._summary(t0 - 0.1, t1 + 0.1)
+        rec["window"] = ("timed region %.4f s; clocks sampled from 0.1 s before it to 0.1 s after it"
+                         % (t1 - t0))
+        return rec
+
+    def _summary(self, t0, t1):
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ts, line in self.lines:
@@ -500,7 +513,8 @@ def main():
 
     n = args.n
     nodes = n * n
-    L = lbf.Lattice(n, n, seed=replica_seed(42, rank))
+    main_fp16 = args.storage == "fp16"
+    L = lbf.Lattice(n, n, seed=replica_seed(42, rank), precision=lbf.LB_FP16DEV if main_fp16 else lbf.LB_FP32)
     L.set_sampling(args.every, args.nbins)
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_index = vis.split(",")[local] if vis else local
@@ -510,35 +524,39 @@ def main():
     # main line: long-wavelength noise
     main_full = args.noise == "full"
     main_mode, main_params = (lbf.LB_NOISE_FULL, PARAMS_FULL) if main_full else (lbf.LB_NOISE_LW, PARAMS_LW)
-    main_bpn = BYTES_PER_NODE_STEP_FULL if main_full else BYTES_PER_NODE_STEP
+    main_bpn = (BYTES_PER_NODE_STEP_FP16 if main_fp16 else BYTES_PER_NODE_STEP) + (8 if main_full else 0)
     ms, kms, kl, launches, w0, w1 = timed_run(lbf, torch, L, args.steps, args.warmup, main_mode, main_params, dist)
-    clk = clocks.stop(w0, w1)
+    clk_window = (w0, w1)
 
     ms = max_over_ranks(dist, ms, "cuda")
     value = whole_job_mlups(world, nodes, args.steps, ms)
     hbm, peak_kind = peaks()
     k_avg_s = kms / max(kl, 1) / 1e3
     achieved = main_bpn * nodes / k_avg_s / 1e9
-    traffic = None if main_full else step_kernel_traffic(nodes)
+    traffic = None if (main_full or main_fp16) else step_kernel_traffic(nodes)
 
-    # variant: correlated (full FDT) noise at kappa = 0.05
+    # variants of config 2: the other (noise, kappa) combinations of the same lattice
     variants = []
-    if not args.no_variants and not main_full:
-        L.set_sampling(args.every, args.nbins)
-        fms, fkms, fkl, flaunch, _, _ = timed_run(lbf, torch, L, args.steps, args.warmup, lbf.LB_NOISE_FULL,
-                                                  PARAMS_FULL, dist)
-        fms = max_over_ranks(dist, fms, "cuda")
-        fk = fkms / max(fkl, 1) / 1e3
-        variants.append({"noise": "full (correlated, k-space synthesis + FFT each step)", "kappa": 0.05,
-                         "value": whole_job_mlups(world, nodes, args.steps, fms), "unit": "MLUPS",
-                         "ms_per_step": fms / args.steps,
-                         "step_kernel": {"achieved": BYTES_PER_NODE_STEP_FULL * nodes / fk / 1e9, "unit": "GB/s",
-                                         "frac": BYTES_PER_NODE_STEP_FULL * nodes / fk / 1e9 / hbm,
-                                         "avg_us": fk * 1e6},
-                         "gpu_launches": flaunch})
+    if not args.no_variants and not main_full and not main_fp16:
+        for vmode, vkappa in ((lbf.LB_NOISE_FULL, 0.05), (lbf.LB_NOISE_FULL, 0.01), (lbf.LB_NOISE_LW, 0.05)):
+            vparams = dict(PARAMS_LW, kappa=vkappa)
+            full = vmode == lbf.LB_NOISE_FULL
+            bpn = BYTES_PER_NODE_STEP_FULL if full else BYTES_PER_NODE_STEP
+            L.set_sampling(args.every, args.nbins)
+            fms, fkms, fkl, flaunch, _, _ = timed_run(lbf, torch, L, args.steps, args.warmup, vmode, vparams, dist)
+            fms = max_over_ranks(dist, fms, "cuda")
+            fk = fkms / max(fkl, 1) / 1e3
+            variants.append({"noise": "full (correlated, k-space synthesis + FFT each step)" if full
+                             else "long-wavelength", "kappa": vkappa,
+                             "value": whole_job_mlups(world, nodes, args.steps, fms), "unit": "MLUPS",
+                             "ms_per_step": fms / args.steps,
+                             "step_kernel": {"achieved": bpn * nodes / fk / 1e9, "unit": "GB/s",
+                                             "frac": bpn * nodes / fk / 1e9 / hbm, "avg_us": fk * 1e6,
+                                             "bytes_per_node": bpn},
+                             "gpu_launches": flaunch})
 
     # variant: FP16 deviation storage, long-wavelength noise (the precision study's second arm)
-    if not args.no_variants:
+    if not args.no_variants and not main_fp16:
         L16 = lbf.Lattice(n, n, seed=replica_seed(43, rank), precision=lbf.LB_FP16DEV)
         L16.set_sampling(args.every, args.nbins)
         hms, hkms, hkl, hlaunch, _, _ = timed_run(lbf, torch, L16, args.steps, args.warmup, lbf.LB_NOISE_LW,
@@ -588,6 +606,7 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "job": "lb_set_populations (host FP64) + lb_step(K) + lb_structure_factor + lb_moments sums"}
 
+    clk = clocks.stop(*clk_window)
     if rank != 0:
         return 0
     cpu = None
@@ -597,10 +616,11 @@ def main():
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "D2Q9 fluctuating non-ideal LB (modified equilibrium), periodic %dx%d FP32 "
+        "config": {"workload": "D2Q9 fluctuating non-ideal LB (modified equilibrium), periodic %dx%d %s "
                                "lattice, %s noise, kappa=%.2f, tau_s=0.8, tau_b=1, tau_ghost=1, "
                                "kT=1e-4, cs2=1/3, S(k) every %d steps into %d bins (FP64)" % (
-                                   n, n, "correlated (full FDT)" if main_full else "long-wavelength",
+                                   n, n, "FP16-deviation" if main_fp16 else "FP32",
+                                   "correlated (full FDT)" if main_full else "long-wavelength",
                                    main_params["kappa"], args.every, args.nbins),
                    "lattice": [n, n], "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (
                        9 * (n + 64) * (n + 4) * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},

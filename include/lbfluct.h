@@ -293,8 +293,9 @@ const char* lb_batch_last_error(lb_batch* b);
 
 /*
  * Request server: continuous batching of independent simulations.
- * Each request is one periodic lattice of the model of [GACV] Sec. III started at rest
- * (uniform density rho0, zero velocity) at time 0, with the noise of Sec. IV in any mode
+ * Each request is one periodic lattice of the model of [GACV] Sec. III started at time 0,
+ * at rest (uniform density rho0, zero velocity) or from the populations in `init`, with
+ * the noise of Sec. IV in any mode
  * (LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_DIAG, or LB_NOISE_FULL for nx, ny powers of two and
  * ny <= 8192) keyed by its own seed, FP32 storage, advanced by `steps` time steps.  Its
  * trajectory is exactly the one lb_batch_* (and, up to FP32 rounding order, lb_step) gives
@@ -326,8 +327,11 @@ const char* lb_batch_last_error(lb_batch* b);
  *   next chunk boundary (its memory is released); its result then has status
  *   LB_ECANCELED.  LB_EINVAL if it is unknown or already completed.
  * lb_server_inject_alloc_failures: fault injection on the host: the next `count`
- *   admissions behave as if the device allocation failed; those requests complete with
- *   status LB_ENOMEM without running, and the server carries on.
+ *   admissions behave as if the device allocation failed.  A failed allocation, injected
+ *   or real (the pool could not grow), completes that request with status LB_ENOMEM
+ *   without running, returns its budget and slot, and the server carries on.  A request
+ *   with `init` also takes an FP64 staging plane (8*nx*ny bytes) from the pool while its
+ *   state is uploaded at admission.
  * lb_server_destroy: drops queued requests, finishes the admitted ones, frees everything.
  * lb_server_last_error: message of the last failure of s (NULL s: of the last failed
  *   lb_server_create or lb_server_submit validation).
@@ -343,6 +347,9 @@ typedef struct lb_request {
     int noise_mode;
     int keep_state;
     uint64_t seed;
+    const double* init;   /* NULL: start at rest; else host FP64 pre-collision populations
+                             f[i][y][x] (9*nx*ny, layout above) to start from at time 0,
+                             copied by lb_server_submit (the caller may free it on return) */
 } lb_request;
 
 typedef struct lb_result {

@@ -34,7 +34,7 @@ class lb_request(ctypes.Structure):
                 ("rho0", ctypes.c_double), ("cs2", ctypes.c_double), ("kT", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("tau_s", ctypes.c_double), ("tau_b", ctypes.c_double),
                 ("tau_ghost", ctypes.c_double), ("noise_mode", ctypes.c_int), ("keep_state", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("init", ctypes.POINTER(ctypes.c_double))]
 
 
 class lb_result(ctypes.Structure):
@@ -596,10 +596,17 @@ class Server:
         self.srv = lb_server_create(hbm_budget_bytes, max_active, max_chunk_steps)
 
     def submit(self, nx, ny, steps, kT=1e-4, kappa=0.01, tau_s=1.0, tau_b=1.0, tau_ghost=1.0,
-               noise_mode=LB_NOISE_LW, seed=42, rho0=1.0, cs2=1.0 / 3.0, keep_state=False):
+               noise_mode=LB_NOISE_LW, seed=42, rho0=1.0, cs2=1.0 / 3.0, keep_state=False, init=None):
+        """init: optional FP64 pre-collision populations [9, ny, nx] to start from (else rest)."""
         r = lb_request(nx=int(nx), ny=int(ny), steps=int(steps), rho0=rho0, cs2=cs2, kT=kT, kappa=kappa,
                        tau_s=tau_s, tau_b=tau_b, tau_ghost=tau_ghost, noise_mode=noise_mode,
                        keep_state=int(bool(keep_state)), seed=int(seed))
+        if init is not None:
+            f = np.ascontiguousarray(init, dtype=np.float64)
+            if f.shape != (9, int(ny), int(nx)):
+                raise ValueError("init must have shape (9, ny, nx)")
+            r.init = f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            return lb_server_submit(self.srv, r)       # copied before the call returns; f alive here
         return lb_server_submit(self.srv, r)
 
     def wait(self, id=0, timeout_s=-1.0):

@@ -177,15 +177,6 @@ int validate(int nx, int ny, double rho0, double cs2, double kT, double kappa, d
     return LB_OK;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool changed = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() { if (changed) cudaSetDevice(prev); }
-};
-
 }  // namespace
 
 struct lb_ctx {

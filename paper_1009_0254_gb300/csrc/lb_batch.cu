@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -341,20 +342,8 @@ static bool make_class_map(void* buf, const Grid& g, int R, int tile, CUtensorMa
 template <int TX, int TY, int NT>
 static cudaError_t ensemble_grid(int* grid) {
     using TT = TmaTile<TX, TY, float>;
-    static int cached = 0;
-    if (cached == 0) {
-        auto kern = step_ensemble_kernel<TX, TY, NT>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, TT::SMEM_BYTES)) != cudaSuccess)
-            return e;
-        cached = sms * (per > 0 ? per : 1);
-    }
-    *grid = cached;
-    return cudaSuccess;
+    static GridCache cache;
+    return resident_grid(step_ensemble_kernel<TX, TY, NT>, NT, TT::SMEM_BYTES, cache, grid);
 }
 
 template <int TX, int TY, int NT>
@@ -785,7 +774,13 @@ int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* see
         e = cudaFuncSetAttribute(batch_noise_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)noise_csm);
     if (e == cudaSuccess && noise_rsm > 0)
         e = cudaFuncSetAttribute(batch_noise_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)noise_rsm);
-    if (e == cudaSuccess && build_launches(b, 0, &b->launches) != LB_OK) e = cudaErrorInvalidValue;
+    {
+        // LBFLUCT_BATCH_TILE=<0..6> fixes the tile shape until an autotune (tests of every shape)
+        const char* tv = std::getenv("LBFLUCT_BATCH_TILE");
+        const int t = tv ? std::atoi(tv) : 0;
+        b->tile = (t >= 0 && t < kBatchTileCount) ? t : 0;
+    }
+    if (e == cudaSuccess && build_launches(b, b->tile, &b->launches) != LB_OK) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         if (b->owns) cudaFree(b->ws);
         delete b;
@@ -797,6 +792,7 @@ int lb_batch_create(int count, const int* nx, const int* ny, const uint64_t* see
 
 int lb_batch_destroy(lb_batch* b) {
     if (!b) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->owns) cudaFree(b->ws);
@@ -813,6 +809,7 @@ int lb_batch_set_stream(lb_batch* b, void* stream) {
 int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, double tau_s, double tau_b,
                         double tau_ghost, int noise_mode) {
     if (!b || replica < -1 || replica >= b->count) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     const int lo = replica < 0 ? 0 : replica, hi = replica < 0 ? b->count : replica + 1;
     for (int r = lo; r < hi; ++r) {
         const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
@@ -844,6 +841,7 @@ int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, doubl
 
 int lb_batch_autotune(lb_batch* b, int steps) {
     if (!b || steps < 1) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     for (int r = 0; r < b->count; ++r)
         if (!b->have_params[r]) return bfail(b, LB_ESTATE, "lb_batch_set_params must be called for every replica");
     // times each tile shape on the whole ensemble (launches that leave the step counter
@@ -895,6 +893,7 @@ int lb_batch_autotune(lb_batch* b, int steps) {
 
 int lb_batch_step(lb_batch* b, int64_t nsteps) {
     if (!b || nsteps < 0) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     for (int r = 0; r < b->count; ++r)
         if (!b->have_params[r]) return bfail(b, LB_ESTATE, "lb_batch_set_params must be called for every replica");
     for (int64_t k = 0; k < nsteps; ++k) {
@@ -906,6 +905,7 @@ int lb_batch_step(lb_batch* b, int64_t nsteps) {
 
 int lb_batch_step_graph(lb_batch* b, int64_t nsteps, int64_t steps_per_graph) {
     if (!b || nsteps < 0 || steps_per_graph < 1) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     for (int r = 0; r < b->count; ++r)
         if (!b->have_params[r]) return bfail(b, LB_ESTATE, "lb_batch_set_params must be called for every replica");
     const long long G = steps_per_graph;
@@ -964,6 +964,7 @@ static void* rep_pops(lb_batch* b, int r, int which) {
 int lb_batch_set_populations(lb_batch* b, int replica, const double* f, int loc, int64_t t) {
     if (!b || !f || replica < 0 || replica >= b->count || (loc != LB_HOST && loc != LB_DEVICE) || t < 0)
         return LB_EINVAL;
+    DeviceGuard dg(b->device);
     const ClassInfo& ci = b->L.classes[b->L.cls_of[replica]];
     const long long n = (long long)ci.nx * ci.ny;
     double* stage = reinterpret_cast<double*>(cls_ptr(b, b->L.off_stage));
@@ -987,6 +988,7 @@ int lb_batch_set_populations(lb_batch* b, int replica, const double* f, int loc,
 
 int lb_batch_get_populations(lb_batch* b, int replica, double* f, int loc) {
     if (!b || !f || replica < 0 || replica >= b->count || (loc != LB_HOST && loc != LB_DEVICE)) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     const ClassInfo& ci = b->L.classes[b->L.cls_of[replica]];
     const long long n = (long long)ci.nx * ci.ny;
     double* stage = reinterpret_cast<double*>(cls_ptr(b, b->L.off_stage));
@@ -1007,6 +1009,7 @@ int lb_batch_get_populations(lb_batch* b, int replica, double* f, int loc) {
 
 int lb_batch_sums(lb_batch* b, int replica, double sums[3]) {
     if (!b || !sums || replica < 0 || replica >= b->count) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     const ClassInfo& ci = b->L.classes[b->L.cls_of[replica]];
     double* partial = reinterpret_cast<double*>(cls_ptr(b, b->L.off_partial));
     double* s3 = reinterpret_cast<double*>(cls_ptr(b, b->L.off_sums));
@@ -1020,6 +1023,7 @@ int lb_batch_sums(lb_batch* b, int replica, double sums[3]) {
 
 int lb_batch_set_sampling(lb_batch* b, int every, int nbins) {
     if (!b || every < 0) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
     if (every == 0) { b->every = 0; return LB_OK; }
     if (nbins < 1 || nbins > kMaxBatchBins) return bfail(b, LB_EINVAL, "nbins must lie in [1, 1024]");
@@ -1054,6 +1058,7 @@ int lb_batch_set_sampling(lb_batch* b, int every, int nbins) {
 int lb_batch_structure_factor(lb_batch* b, int replica, int nbins, double* S_rho, double* S_jl, double* S_jt,
                               int64_t* counts, int64_t* nsamples) {
     if (!b || replica < 0 || replica >= b->count) return LB_EINVAL;
+    DeviceGuard dg(b->device);
     if (nbins != b->nbins || b->nbins == 0) return bfail(b, LB_EINVAL, "nbins differs from lb_batch_set_sampling");
     const int c = b->L.cls_of[replica];
     const ClassInfo& ci = b->L.classes[c];

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 
 namespace lbf {
@@ -286,6 +288,52 @@ __device__ __forceinline__ void store9(T* dst, long long P, const Grid& g, int x
             if (hx & hy) p[dxy] = v;
         }
     }
+}
+
+// Makes `dev` the current device for the lifetime of the guard (the entry points of an
+// object created on one device may be called while another device is current).
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() { if (changed) cudaSetDevice(prev); }
+};
+
+// Grid of a persistent launch (resident CTAs per SM x SMs) for one kernel, kept per
+// device: the first launch on a device raises the kernel's dynamic shared-memory limit
+// there and asks the occupancy calculator; later launches read the cached value.  Safe
+// to call from several host threads.
+constexpr int MAX_DEVICES = 64;
+struct GridCache {
+    std::atomic<int> grid[MAX_DEVICES];
+    std::mutex mu;
+};
+
+template <typename K>
+cudaError_t resident_grid(K kern, int threads, int smem, GridCache& c, int* grid) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    int g = c.grid[dev].load(std::memory_order_acquire);
+    if (g == 0) {
+        std::lock_guard<std::mutex> lk(c.mu);
+        g = c.grid[dev].load(std::memory_order_relaxed);
+        if (g == 0) {
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+                return e;
+            int sms = 0, per = 0;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem)) != cudaSuccess)
+                return e;
+            g = sms * (per > 0 ? per : 1);
+            c.grid[dev].store(g, std::memory_order_release);
+        }
+    }
+    *grid = g;
+    return cudaSuccess;
 }
 
 }  // namespace lbf

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -279,7 +280,8 @@ int noise_strip(int nx, int ny) {
 }
 
 struct Pending {
-    lb_request r;
+    lb_request r;                                  // r.init is null: the state is in `init`
+    std::shared_ptr<std::vector<double>> init;     // initial populations (host copy), or null
     int64_t id;
     double t_submit;
 };
@@ -513,15 +515,41 @@ bool admit(lb_server* s) {
                 injected = true;
             }
         }
-        if (injected) {
-            // behave as a failed allocation: the request completes with LB_ENOMEM, unrun
+        // an injected failure takes the same path as a real one: the request completes
+        // with LB_ENOMEM, unrun, and the server carries on
+        void* mem = nullptr;
+        cudaError_t ae = injected ? cudaErrorMemoryAllocation
+                                  : cudaMallocFromPoolAsync(&mem, run.bytes, s->pool, s->stream);
+        if (ae == cudaErrorMemoryAllocation) {
+            cudaGetLastError();            // not sticky: clear it
             finish_unrun(s, run, LB_ENOMEM);
             continue;
         }
-        void* mem = nullptr;
-        SCK(s, cudaMallocFromPoolAsync(&mem, run.bytes, s->pool, s->stream));
+        SCK(s, ae);
         run.mem = (char*)mem;
         SCK(s, cudaMemsetAsync(run.mem, 0, run.bytes, s->stream));   // rest: zero deviations
+        if (pr.init) {
+            // the caller's initial state, through an FP64 staging plane taken from the pool
+            // for the upload only
+            const long long n = (long long)run.g.nx * run.g.ny;
+            void* stage = nullptr;
+            ae = cudaMallocFromPoolAsync(&stage, (size_t)n * sizeof(double), s->pool, s->stream);
+            if (ae == cudaErrorMemoryAllocation) {
+                cudaGetLastError();
+                SCK(s, cudaFreeAsync(run.mem, s->stream));
+                finish_unrun(s, run, LB_ENOMEM);
+                continue;
+            }
+            SCK(s, ae);
+            double fb0[Q];
+            rest_populations(pr.r.rho0, pr.r.cs2, fb0);
+            for (int i = 0; i < Q; ++i) {
+                SCK(s, cudaMemcpyAsync(stage, pr.init->data() + (size_t)i * n, (size_t)n * sizeof(double),
+                                       cudaMemcpyHostToDevice, s->stream));
+                SCK(s, launch_set_plane((const double*)stage, run.mem, 0, run.g, i, fb0[i], s->stream));
+            }
+            SCK(s, cudaFreeAsync(stage, s->stream));
+        }
         float* b0 = reinterpret_cast<float*>(run.mem);
         float* b1 = reinterpret_cast<float*>(run.mem + buf_bytes(run.g));
         unsigned char* st = slot_stage(s, run.slot);
@@ -856,11 +884,18 @@ int lb_server_submit(lb_server* s, const lb_request* r, int64_t* id) {
     if (rc != LB_OK) return sfail(nullptr, rc, "parameters rejected (see lb_check_params)");
     if (slot_bytes(g, r->noise_mode == LB_NOISE_FULL) > s->budget)
         return sfail(nullptr, LB_ENOMEM, "the request alone exceeds the HBM budget");
+    std::shared_ptr<std::vector<double>> init_copy;
+    if (r->init) {
+        const size_t cnt = (size_t)Q * r->nx * r->ny;
+        init_copy = std::make_shared<std::vector<double>>(r->init, r->init + cnt);
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     if (!s->err.empty()) return LB_ECUDA;
     if (s->stop) return LB_ESTATE;
     Pending p;
     p.r = *r;
+    p.r.init = nullptr;
+    if (r->init) p.init = init_copy;
     p.id = s->next_id++;
     p.t_submit = now_s(s);
     s->queue.push_back(p);
@@ -913,6 +948,7 @@ int lb_server_fetch_populations(lb_server* s, int64_t id, double* f) {
         run = it->second.run;
         s->kept.erase(it);
     }
+    DeviceGuard dg(s->device);
     std::lock_guard<std::mutex> gl(s->gpu);
     const long long n = (long long)run.g.nx * run.g.ny;
     const int fin = (int)(run.r.steps & 1);
@@ -987,6 +1023,7 @@ int lb_server_inject_alloc_failures(lb_server* s, int count) {
 
 int lb_server_destroy(lb_server* s) {
     if (!s) return LB_EINVAL;
+    DeviceGuard dg(s->device);
     if (s->worker.joinable()) {
         {
             std::lock_guard<std::mutex> lk(s->mu);

@@ -207,21 +207,14 @@ template <int TX, int TY, int NT, int MODE, typename T>
 static cudaError_t launch_cfg(const void* map, TmaArgs ta, cudaStream_t s) {
     using TT = TmaTile<TX, TY, T>;
     auto kern = step_tma_kernel<TX, TY, NT, MODE, T>;
-    static int grid_cache = 0;
-    if (grid_cache == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, TT::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        grid_cache = sms * (per > 0 ? per : 1);
-    }
+    static GridCache cache;
+    int grid_max = 0;
+    cudaError_t e = resident_grid(kern, NT, TT::SMEM_BYTES, cache, &grid_max);
+    if (e != cudaSuccess) return e;
     ta.ntx = (ta.a.g.nx + TX - 1) / TX;
     ta.nty = (ta.a.g.ny + TY - 1) / TY;
     const int ntiles = ta.ntx * ta.nty;
-    const int grid = ntiles < grid_cache ? ntiles : grid_cache;
+    const int grid = ntiles < grid_max ? ntiles : grid_max;
     kern<<<grid, NT, TT::SMEM_BYTES, s>>>(*reinterpret_cast<const CUtensorMap*>(map), ta);
     return cudaGetLastError();
 }

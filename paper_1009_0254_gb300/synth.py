@@ -25,3 +25,8 @@ def sample_nodes(nx: int, ny: int, count: int, seed: int) -> np.ndarray:
              (ny - 1) * nx + nx // 2, (ny // 2) * nx + nx // 2]
     extra = rng.choice(nx * ny, size=count, replace=False)
     return np.unique(np.concatenate([np.array(fixed, dtype=np.int64), extra.astype(np.int64)]))
+
+
+def clipped_gaussian_field(shape, seed: int, scale: float, clip: float) -> np.ndarray:
+    """N(0, 1) draws (PCG64, given seed) clipped to [-clip, clip], times scale (FP64)."""
+    return scale * np.clip(np.random.default_rng(seed).standard_normal(shape), -clip, clip)

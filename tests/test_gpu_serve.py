@@ -262,15 +262,30 @@ def test_injected_allocation_failures_leave_the_server_running():
 
 
 def test_diverged_run_is_reported_not_finite():
-    # kT = 0.05 rho0 sigma_s^2 * 40: far beyond the low-Mach range, the run blows up
-    srv = lbf.Server(1 << 30, max_active=4, max_chunk_steps=100)
-    i = srv.submit(32, 32, 3000, kT=0.5, kappa=0.0, tau_s=0.51, tau_b=0.51, tau_ghost=0.51, seed=3)
+    # tests/nonlinear_case.py DIVERGING: a request whose FP64 oracle run overflows
+    # (test_oracle_step.py::test_the_diverging_request_of_the_watchdog_test_diverges)
+    # completes with exactly LB_ENONFINITE, and the server goes on serving
+    import nonlinear_case as nl
+    d = nl.DIVERGING
+    srv = lbf.Server(1 << 30, max_active=4, max_chunk_steps=64)
+    i = srv.submit(d["n"], d["n"], d["steps"], kT=0.0, kappa=d["kappa"], tau_s=d["tau"], tau_b=d["tau"],
+                   tau_ghost=d["tau"], noise_mode=lbf.LB_NOISE_OFF, seed=3, init=nl.diverging_state())
     r = srv.wait(i, timeout_s=60)
-    assert r.status in (lbf.LB_ENONFINITE, lbf.LB_OK)
-    if r.status == lbf.LB_OK:
-        assert np.all(np.isfinite(r.sums))
-    else:
-        assert not np.all(np.isfinite(r.sums))
+    assert r.status == lbf.LB_ENONFINITE
+    assert not np.all(np.isfinite(r.sums))
+    j = srv.submit(32, 32, 50, kT=1e-4, kappa=0.01, tau_s=0.8, seed=4)
+    assert srv.wait(j, timeout_s=60).status == lbf.LB_OK
+    srv.close()
+
+
+def test_non_finite_initial_state_is_reported_not_finite():
+    f = np.broadcast_to(np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None], (9, 8, 8)).copy()
+    f[3, 2, 5] = np.nan
+    srv = lbf.Server(1 << 30, max_active=4, max_chunk_steps=10)
+    i = srv.submit(8, 8, 5, kT=1e-4, kappa=0.01, tau_s=0.8, seed=4, init=f)
+    k = srv.submit(8, 8, 5, kT=1e-4, kappa=0.01, tau_s=0.8, seed=4)
+    assert srv.wait(i, timeout_s=60).status == lbf.LB_ENONFINITE
+    assert srv.wait(k, timeout_s=60).status == lbf.LB_OK
     srv.close()
 
 

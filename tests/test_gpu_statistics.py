@@ -1,14 +1,22 @@
-"""Statistics of the GPU path against the paper's theory (Sec. V A): equilibration ratios
-<|dm_a(k)|^2> / G_aa(k) of every mode (Figs. 3 and 4) and the device-accumulated spectra
-against Eqs. (struct-fact) and (momtm-fluct)."""
+"""Statistics of the GPU path against the paper's theory (Sec. V A), as replica tests:
+the equilibration ratios <|dm_a(k)|^2> / G_aa(k) of every mode (the Figs. 3 and 4
+set-ups) and the device-accumulated spectra against Eqs. (struct-fact) and
+(momtm-fluct).  Each estimate is the mean over R independent replicas (own seeds, one
+batched launch per step) with its standard error from the replica spread: a mode's
+ratio averaged over the wavevectors must lie within 3 standard errors of the theory,
+and every radial bin within the family-wise bound of tests/equilibration.py (a correct
+implementation fails any bin with a chance below 1 %).  The standard errors are printed."""
 import numpy as np
 import pytest
 
+import equilibration as eq
 import oracle
 import paper_1009_0254_gb300 as lbf
 from oracle import theory as th
 
 pytestmark = pytest.mark.gpu
+R = 32          # independent replicas
+NB = 8          # radial bins of the ratio tests
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -21,111 +29,122 @@ def _built():
     lbf.load()
 
 
-def _ratios(L, model, burn, samples, every, G_of_k):
-    nx, ny = L.nx, L.ny
-    KX, KY = th.lattice_k(nx, ny)
-    L.step(burn)
-    acc = np.zeros((9, ny, nx))
-    mbar = model.mbar()[:, None, None]
+def _replica_spectra(nx, ny, cs2, params, mode, seed0, burn, samples, every, model):
+    """Per-replica time averages of |dm_a(k)|^2, shape (R, 9, ny, nx)."""
+    ens = lbf.Ensemble([(nx, ny)] * R, [seed0 + 7919 * r for r in range(R)], rho0=1.0, cs2=cs2)
+    ens.set_params(-1, *params, mode)
+    ens.step(burn, graph_steps=every)
+    sp = eq.ModeSpectra(R, nx, ny, model)
     for _ in range(samples):
-        L.step(every)
-        m, _ = L.moments()
-        dm = m - mbar
-        acc += np.abs(np.fft.ifft2(dm, axes=(1, 2)) * np.sqrt(nx * ny)) ** 2
-    acc /= samples
-    G = np.empty((9, ny, nx))
-    for j in range(ny):
-        for i in range(nx):
-            G[:, j, i] = np.diag(G_of_k(KX[j, i], KY[j, i])).real
-    keep = np.ones((ny, nx), bool)
-    keep[0, 0] = keep[0, nx // 2] = keep[ny // 2, 0] = False
-    return acc / G, keep, KX, KY
+        ens.step(every, graph_steps=every)
+        for r in range(R):
+            lbf.lb_batch_get_populations(ens.b, r, sp.f[r], lbf.LB_DEVICE)
+        sp.add()
+    ens.close()
+    return sp.mean()
 
 
-def _radial(ratio, keep, KX, KY, nb=8):
-    kw = np.sqrt(np.minimum(KX, 2 * np.pi - KX) ** 2 + np.minimum(KY, 2 * np.pi - KY) ** 2)
-    edges = np.linspace(0, kw.max() + 1e-9, nb + 1)
-    out = []
-    for lo, hi in zip(edges[:-1], edges[1:]):
-        sel = keep & (kw >= lo) & (kw < hi)
-        out.append(ratio[sel].mean() if sel.any() else 1.0)
-    return np.array(out)
+def _check_ratios(name, ratio, nx, ny, z_mode=3.0):
+    """ratio: (R, 9, ny, nx) per-replica ratios against the theory; asserts the mode means
+    within z_mode standard errors of 1 and every radial bin within the family-wise bound."""
+    keep = eq.kept_wavevectors(nx, ny)
+    bins, _ = eq.radial_bins(nx, ny, NB)
+    zfw = eq.family_z(9 * NB)
+    worst = 0.0
+    for a in range(9):
+        mean, se, z = eq.replica_z(ratio[:, a][:, keep].mean(axis=1))
+        print("%s mode %d: ratio %.5f +- %.5f (z = %+.2f)" % (name, a + 1, mean, se, z))
+        assert abs(z) <= z_mode, (a, mean, se, z)
+        for b in range(NB):
+            sel = keep & (bins == b)
+            if sel.sum() < 4:
+                continue
+            mb, sb, zb = eq.replica_z(ratio[:, a][:, sel].mean(axis=1))
+            worst = max(worst, abs(zb))
+            assert abs(zb) <= zfw, (a, b, mb, sb, zb, zfw)
+    print("%s: largest radial-bin |z| = %.2f (bound %.2f over %d bins)" % (name, worst, zfw, 9 * NB))
 
 
 @pytest.mark.slow
 def test_correlated_noise_equilibrates_every_mode_fig3():
-    # Fig. 3 set-up: 128^2, kappa = 0.08, c_s = 0.265, tau = 1, T = 1e-7, 400 snapshots
+    # Fig. 3 set-up: 128^2, kappa = 0.08, c_s = 0.265, tau = 1, T = 1e-7, correlated noise
+    nx = ny = 128
     cs2 = 0.265 ** 2
-    L = lbf.Lattice(128, 128, seed=2010, rho0=1.0, cs2=cs2)
-    L.set_params(1e-7, 0.08, 1.0, 1.0, 1.0, lbf.LB_NOISE_FULL)
     m = th.Model(1.0, cs2, 0.08, 1e-7, 1.0, 1.0, 1.0)
-    ratio, keep, KX, KY = _ratios(L, m, burn=12000, samples=400, every=40, G_of_k=m.G_closed)
-    for a in range(9):
-        mean = ratio[a][keep].mean()
-        assert abs(mean - 1) < 0.03, (a, mean)
-        rad = _radial(ratio[a], keep, KX, KY)
-        assert np.all(np.abs(rad[1:] - 1) < 0.1), (a, rad)
+    acc = _replica_spectra(nx, ny, cs2, (1e-7, 0.08, 1.0, 1.0, 1.0), lbf.LB_NOISE_FULL, 2010, burn=12000,
+                           samples=200, every=40, model=m)
+    G = eq.diag_theory(nx, ny, m.G_closed)
+    _check_ratios("Fig. 3 (full FDT noise)", acc / G[None], nx, ny)
 
 
 @pytest.mark.slow
 def test_uncorrelated_noise_fig4_setup():
     # Fig. 4 set-up: kappa = 0.03, c_s = 0.15, tau = 1, long-wavelength noise.
-    # (1) Every mode follows the exact stationary theory of this noise: the solution of
-    #     G = M G M^H + A(-k) Xi(0) A(-k)^H (stationarity of Eq. lb-lang-ft).
+    # (1) Every mode follows the exact stationary theory of this noise, the solution of
+    #     G = M G M^H + A(-k) Xi(0) A(-k)^H (stationarity of Eq. lb-lang-ft), within the
+    #     replica standard errors.
     # (2) In the hydrodynamic range k <~ 0.8 the errors against G(k) of Eq. (g-mat-yeo)
-    #     are negligible (Sec. V A).  At larger k that theory itself puts the density
-    #     ratio up to ~1.2 (along the diagonal), above the paper's "< 10 %" for this figure;
-    #     the test records the measured value without asserting the paper's bound.
-    cs2 = 0.15 ** 2
+    #     are negligible (Sec. V A): within 5 %.  At larger k that theory itself puts the
+    #     density ratio up to ~1.2 (reading R15); the value is printed.
     nx = ny = 64
-    L = lbf.Lattice(nx, ny, seed=2011, rho0=1.0, cs2=cs2)
-    L.set_params(1e-7, 0.03, 1.0, 1.0, 1.0, lbf.LB_NOISE_LW)
+    cs2 = 0.15 ** 2
     m = th.Model(1.0, cs2, 0.03, 1e-7, 1.0, 1.0, 1.0)
-    ratio, keep, KX, KY = _ratios(L, m, burn=8000, samples=400, every=40, G_of_k=m.G_closed)
+    acc = _replica_spectra(nx, ny, cs2, (1e-7, 0.03, 1.0, 1.0, 1.0), lbf.LB_NOISE_LW, 2011, burn=8000,
+                           samples=200, every=40, model=m)
+    keep = eq.kept_wavevectors(nx, ny)
     X0 = m.Xi_zero()
-    Glw = np.empty((9, ny, nx))
-    Gc = np.empty((9, ny, nx))
+    KX, KY = th.lattice_k(nx, ny)
+    Gc = eq.diag_theory(nx, ny, m.G_closed)
+    Glw = Gc.copy()
     for j in range(ny):
         for i in range(nx):
-            kx, ky = KX[j, i], KY[j, i]
-            Gc[:, j, i] = np.diag(m.G_closed(kx, ky))
-            Glw[:, j, i] = Gc[:, j, i] if not keep[j, i] else np.diag(th.lyapunov_G(m, kx, ky, X0)).real
-    r2 = ratio * Gc / Glw
-    for a in range(9):
-        assert abs(r2[a][keep].mean() - 1) < 0.03, (a, r2[a][keep].mean())
-        rad = _radial(r2[a], keep, KX, KY)
-        assert np.all(np.abs(rad[1:] - 1) < 0.1), (a, rad)
-    kw = np.sqrt(np.minimum(KX, 2 * np.pi - KX) ** 2 + np.minimum(KY, 2 * np.pi - KY) ** 2)
+            if keep[j, i]:
+                Glw[:, j, i] = np.diag(th.lyapunov_G(m, KX[j, i], KY[j, i], X0)).real
+    _check_ratios("Fig. 4 (long-wavelength noise) vs its exact theory", acc / Glw[None], nx, ny)
+    ratio = acc / Gc[None]
+    bins, kw = eq.radial_bins(nx, ny, NB)
     hydro = keep & (kw <= 0.8)
     for a in range(9):
-        assert abs(ratio[a][hydro].mean() - 1) < 0.05, (a, ratio[a][hydro].mean())
-    print("Fig. 4 set-up: density ratio vs G(k) in the outermost radial bin = %.3f"
-          % _radial(ratio[0], keep, KX, KY)[-1])
+        mean, se, z = eq.replica_z(ratio[:, a][:, hydro].mean(axis=1))
+        assert abs(mean - 1) < 0.05, (a, mean, se)
+    out = keep & (bins == NB - 1)
+    print("Fig. 4 set-up: density ratio vs G(k) in the outermost radial bin = %.3f" % ratio[:, 0][:, out].mean())
 
 
 @pytest.mark.slow
 def test_device_structure_factor_against_ornstein_zernike():
-    # Eq. (struct-fact) with the lattice k^2 (Appendix B) and Eq. (momtm-fluct)
+    # Eq. (struct-fact) with the lattice k^2 (Appendix B) and Eq. (momtm-fluct), from the
+    # spectra the library accumulates in FP64 on the device, per replica
     nx = ny = 128
     nb = 16
     kT, kappa = 1e-6, 0.05
-    L = lbf.Lattice(nx, ny, seed=77)
-    L.set_params(kT, kappa, 1.0, 1.0, 1.0, lbf.LB_NOISE_FULL)
-    L.step(12000)
-    L.set_sampling(20, nb)
-    L.step(8000)
-    S, Jl, Jt, cnt, ns = L.structure_factor()
-    assert ns == 400
+    ens = lbf.Ensemble([(nx, ny)] * R, [77 + 104729 * r for r in range(R)])
+    ens.set_params(-1, kT, kappa, 1.0, 1.0, 1.0, lbf.LB_NOISE_FULL)
+    ens.step(12000, graph_steps=100)
+    ens.set_sampling(20, nb)
+    ens.step(8000, graph_steps=100)
+    spec = [ens.structure_factor(r) for r in range(R)]
+    ens.close()
+    assert all(s[4] == 400 for s in spec)
+    S = np.array([s[0] for s in spec])
+    Jl = np.array([s[1] for s in spec])
+    Jt = np.array([s[2] for s in spec])
+    cnt = spec[0][3]
     m = th.Model(1.0, 1 / 3, kappa, kT, 1.0, 1.0, 1.0)
     b, KXw, KYw, _ = oracle.k_bins(nx, ny, nb)
     Sth = m.S_k(KXw, KYw)
-    keep = b >= 0
-    keep[0, nx // 2] = keep[ny // 2, 0] = False
+    # j_l at (pi, 0) and (0, pi) is the staggered-momentum invariant (reading R12): it keeps
+    # its initial value 0, so those two wavevectors contribute 0 to their bin's <|j_l|^2>
+    frozen = np.zeros((ny, nx), bool)
+    frozen[0, nx // 2] = frozen[ny // 2, 0] = True
+    zfw = eq.family_z(3 * (nb - 1))
     for k in range(1, nb):
-        sel = keep & (b == k)
-        if sel.sum() < 50:
+        sel = b == k
+        if cnt[k] < 50:
             continue
-        th_mean = Sth[sel].mean()
-        assert abs(S[k] / th_mean - 1) < 0.08, (k, S[k], th_mean)
-        assert abs(Jl[k] / kT - 1) < 0.08, (k, Jl[k])
-        assert abs(Jt[k] / kT - 1) < 0.08, (k, Jt[k])
+        targets = [(S[:, k], Sth[sel].mean(), "S"), (Jl[:, k], kT * (1 - frozen[sel].sum() / sel.sum()), "j_l"),
+                   (Jt[:, k], kT, "j_t")]
+        for vals, target, name in targets:
+            mean, se, z = eq.replica_z(vals / target)
+            print("bin %2d %s: %.5f +- %.5f (z = %+.2f)" % (k, name, mean, se, z))
+            assert abs(z) <= zfw, (k, name, mean, se, z, zfw)

@@ -118,3 +118,84 @@ def test_noise_conserves_mass_and_momentum(mode):
     m1 = lat.moments().sum(axis=(1, 2))
     np.testing.assert_allclose(m1[:3], m0[:3], atol=1e-12)
     assert np.abs(lat.f - lat.model.fbar()[:, None, None]).max() > 1e-3   # noise did act
+
+
+def _gradient_swapped_diagonals(rho):
+    """The gradient with the density neighbours at (1, 1) and (-1, 1) exchanged: the
+    mistake of a mis-wired diagonal in a kernel's density ring (the Laplacian, symmetric
+    in the four diagonals, does not see it)."""
+    gx = np.zeros_like(rho)
+    gy = np.zeros_like(rho)
+    for i in range(1, 9):
+        cx, cy = th.C[i]
+        sx, sy = th.C[{5: 6, 6: 5}.get(i, i)]
+        nb = np.roll(rho, shift=(-sy, -sx), axis=(0, 1))
+        gx += 3 * th.W[i] * cx * nb
+        gy += 3 * th.W[i] * cy * nb
+    return gx, gy
+
+
+@pytest.mark.parametrize("case", ["ideal", "nonideal"])
+def test_nonlinear_parity_state_resolves_the_second_order_terms(case):
+    # The state of the GPU nonlinear parity tests (tests/nonlinear_case.py): each
+    # second-order term of the Table II equilibrium, and a swap of two diagonal density
+    # neighbours, moves the post-collision populations by >= 100 x their tolerance.
+    import nonlinear_case as nl
+    m = nl.model(case)
+    nx, ny = 64, 48
+    f = nl.state(case, nx, ny, seed=101)
+    tol = nl.tolerance(f)
+    rho = f.sum(axis=0)
+    drho = rho - m.rho0
+    jx = np.einsum("i,iyx->yx", th.C[:, 0].astype(float), f)
+    jy = np.einsum("i,iyx->yx", th.C[:, 1].astype(float), f)
+    lap = th.laplacian_stencil(rho)
+    gx, gy = _lattice_gradient(rho)
+    k = m.kappa
+
+    def dfstar(dm):
+        # change of f* = T^-1 (m + lambda (m - m^eq)) caused by a change dm of m^eq
+        return np.einsum("ia,ayx->iyx", th.TINV, -m.lam[:, None, None] * dm)
+
+    def moments(**kw):
+        dm = np.zeros((9, ny, nx))
+        for a, v in kw.items():
+            dm[int(a[1:])] = v
+        return dm
+
+    # the contribution map against the oracle itself: the whole kappa dependence of f*
+    sites = np.arange(nx * ny)
+    m0 = th.Model(m.rho0, m.cs2, 0.0, m.kT, m.tau_s, m.tau_b, m.tau_ghost)
+    got = (oracle.collide_sites(f, m, sites) - oracle.collide_sites(f, m0, sites)).T.reshape(9, ny, nx)
+    want = dfstar(moments(m3=-6 * k * rho * lap, m4=k * (gx * gx - gy * gy), m5=k * gx * gy,
+                          m8=6 * k * rho * lap - 3 * k * (gx * gx + gy * gy)))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+    sgx, sgy = _gradient_swapped_diagonals(rho)
+    terms = {
+        "rho u u": moments(m3=3 * (jx * jx + jy * jy) / rho, m4=(jx * jx - jy * jy) / rho, m5=jx * jy / rho),
+        "kappa grad grad (shear)": moments(m4=k * (gx * gx - gy * gy), m5=k * gx * gy),
+        "-3 kappa |grad rho|^2 (m9)": moments(m8=-3 * k * (gx * gx + gy * gy)),
+        "kappa drho lap rho": moments(m3=-6 * k * drho * lap, m8=6 * k * drho * lap),
+        "diagonals swapped": moments(m4=k * ((sgx * sgx - sgy * sgy) - (gx * gx - gy * gy)), m5=k * (sgx * sgy - gx * gy),
+                                     m8=-3 * k * ((sgx * sgx + sgy * sgy) - (gx * gx + gy * gy))),
+    }
+    for name, dm in terms.items():
+        size = np.abs(dfstar(dm)).max()
+        print("%s %s: %.2e = %.0f x tolerance %.2e" % (case, name, size, size / tol, tol))
+        assert size >= 100 * tol, (name, size, tol)
+
+
+def test_the_diverging_request_of_the_watchdog_test_diverges():
+    # tests/nonlinear_case.py DIVERGING: the oracle's own FP64 run of it leaves the finite
+    # numbers, so the served run of the same request must be reported LB_ENONFINITE
+    import nonlinear_case as nl
+    d = nl.DIVERGING
+    m = nl.diverging_model()
+    f = nl.diverging_state()
+    assert np.isfinite(oracle.step(f, m)).all()          # a sane start
+    with np.errstate(all="ignore"):
+        for _ in range(d["steps"]):
+            f = oracle.step(f, m)
+    assert not np.isfinite(f).all()
+    assert not np.isfinite(f.sum())

@@ -26,8 +26,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbref.so")
 _lib = None
 
-NOISE_OFF, NOISE_LW, NOISE_FULL, NOISE_DIAG = 0, 1, 2, 3
-TAG_NODE, TAG_KSPACE = 0, 2
+NOISE_OFF, NOISE_LW, NOISE_FULL, NOISE_DIAG, NOISE_FULL_RS = 0, 1, 2, 3, 4
+TAG_NODE, TAG_KSPACE, TAG_STENCIL = 0, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -159,6 +159,84 @@ def xi49_full(model: Model, nx, ny, seed, step, factor: str = "cholesky"):
     return x4.real, x9.real
 
 
+# --- correlated noise built in real space ------------------------------------------------
+#
+# Every k-dependent entry of Xi(k), Eq. (noise-yeo), depends on k only through the lattice
+# k^2 = s(k) of Appendix B, and affinely: Xi_(4,9)(k) = A + B s(k), s in [0, 16/3].  With
+# cx = cos kx, cy = cos ky, s = (10 - 4 cx - 4 cy - 2 cx cy) / 3, and the four products
+# P_ab(k) = (1 + a e^{i kx})(1 + b e^{i ky}) (a, b = +-1) have |P_ab|^2 = 4 (1 + a cx)(1 + b cy),
+#   (1/16) [ |P_++|^2 + |P_+-|^2 + |P_-+|^2 + |P_--|^2 ]              = 1,
+#   (1/16) [ 4 (|P_+-|^2 + |P_-+|^2) + (16/3) |P_--|^2 ]               = s(k),
+# so Xi(k) = (1/16) [ Xi(s=0) |P_++|^2 + Xi(s=4) (|P_+-|^2 + |P_-+|^2) + Xi(s=16/3) |P_--|^2 ].
+# Four independent white 2-vector fields nu_ab, each multiplied by a factor L_ab of Xi at its
+# s and filtered by the 2 x 2 stencil P_ab, add up to a field whose covariance is Xi(k) at
+# every k: the same Gaussian field the Fourier construction of Sec. IV gives (it exists when
+# Xi is positive semidefinite at s = 0 and s = 16/3, hence on the whole range), built from
+# one 2 x 2 box of nodes, on a lattice of any size.
+
+# wavevectors where the lattice k^2 takes the values 0, 4 and 16/3
+STENCIL_K = {"++": (0.0, 0.0), "+-": (2 * np.pi / 3, np.pi / 2), "-+": (2 * np.pi / 3, np.pi / 2),
+             "--": (np.pi, np.pi)}
+STENCIL_SIGNS = {"++": (1, 1), "+-": (1, -1), "-+": (-1, 1), "--": (-1, -1)}
+STENCIL_ORDER = ("++", "+-", "-+", "--")
+
+
+def stencil_factors(model: Model, factor: str = "cholesky"):
+    """Factors L_ab (2 x 2, rows/columns modes 4 and 9) of the four fields: L L^T is the
+    (4,9) block of Xi of Eq. (noise-yeo) at s = 0, 4, 4 and 16/3."""
+    out = []
+    for ab in STENCIL_ORDER:
+        kx, ky = STENCIL_K[ab]
+        l11, l12, l21, l22 = block49_factor(model, np.array(kx), np.array(ky), factor)
+        out.append(np.array([[float(l11), float(l12)], [float(l21), float(l22)]]))
+    return out
+
+
+def stencil_combine(nu, Ls):
+    """xi_(4,9)(r) = 1/4 sum_ab sum_{dx,dy in {0,1}} a^dx b^dy L_ab nu_ab(r - dx e_x - dy e_y)
+    (periodic), from nu[ab, component, y, x] (ab in STENCIL_ORDER); returns (2, ny, nx)."""
+    out = np.zeros(nu.shape[1:])
+    for idx, ab in enumerate(STENCIL_ORDER):
+        a, b = STENCIL_SIGNS[ab]
+        g = np.einsum("cd,dyx->cyx", Ls[idx], nu[idx])
+        for dx in (0, 1):
+            for dy in (0, 1):
+                out += (a ** dx) * (b ** dy) * np.roll(g, shift=(dy, dx), axis=(1, 2))
+    return out / 4.0
+
+
+def stencil_fields(nx, ny, seed, step):
+    """The four white fields nu_ab (shape (4, 2, ny, nx)): one draw per node (tag 3), the
+    Box-Muller pair of output word w gives the two components of field w."""
+    g = normals(np.arange(nx * ny, dtype=np.uint32), seed, step, TAG_STENCIL)      # (n, 8)
+    return g.T.reshape(4, 2, ny, nx)
+
+
+def xi49_stencil(model: Model, nx, ny, seed, step, factor: str = "cholesky"):
+    """Correlated noise of modes 4 and 9 with covariance Xi(k) built in real space (see
+    above).  Returns real fields xi4[y, x], xi9[y, x]."""
+    x = stencil_combine(stencil_fields(nx, ny, seed, step), stencil_factors(model, factor))
+    return x[0], x[1]
+
+
+def xi49_stencil_at(model: Model, nx, ny, seed, step, sites, factor: str = "cholesky"):
+    """The same at the listed linear sites only (draws at the 2 x 2 box below-left of each
+    site): returns (len(sites), 2)."""
+    sites = np.asarray(sites, dtype=np.int64)
+    x = sites % nx
+    y = sites // nx
+    Ls = stencil_factors(model, factor)
+    out = np.zeros((sites.size, 2))
+    for dx in (0, 1):
+        for dy in (0, 1):
+            q = ((y - dy) % ny) * nx + (x - dx) % nx
+            nu = normals(q.astype(np.uint32), seed, step, TAG_STENCIL).reshape(-1, 4, 2)
+            for idx, ab in enumerate(STENCIL_ORDER):
+                a, b = STENCIL_SIGNS[ab]
+                out += (a ** dx) * (b ** dy) * (nu[:, idx, :] @ Ls[idx].T)
+    return out / 4.0
+
+
 def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None, factor: str = "cholesky"):
     """xi[a, y, x] for one step (Sec. IV).
 
@@ -167,7 +245,8 @@ def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None, factor: s
           uncorrelated.
     DIAG: as LW with the off-diagonal Xi_49 dropped ("ideal gas-like" noise, Sec. IV).
     FULL: modes 5..8 as LW (their variances do not depend on k); modes 4, 9 from
-          xi49_full()."""
+          xi49_full().
+    FULL_RS: as FULL with modes 4, 9 from xi49_stencil() (the same covariance Xi(k))."""
     n = nx * ny
     xi = np.zeros((9, ny, nx))
     if mode == NOISE_OFF or model.kT == 0.0:
@@ -188,6 +267,10 @@ def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None, factor: s
     xi[:] = xi_flat.reshape(9, ny, nx)
     if mode == NOISE_FULL:
         x4, x9 = xi49_full(model, nx, ny, seed, step, factor)
+        xi[3] = x4
+        xi[8] = x9
+    elif mode == NOISE_FULL_RS:
+        x4, x9 = xi49_stencil(model, nx, ny, seed, step, factor)
         xi[3] = x4
         xi[8] = x9
     return xi
@@ -346,6 +429,10 @@ def noise_at_sites(model: Model, mode: int, nx, ny, seed, step, sites, L0=None, 
         x4, x9 = xi49
         xi[:, 3] = x4.ravel()[sites]
         xi[:, 8] = x9.ravel()[sites]
+    elif mode == NOISE_FULL_RS:
+        x49 = xi49_stencil_at(model, nx, ny, seed, step, sites, factor)
+        xi[:, 3] = x49[:, 0]
+        xi[:, 8] = x49[:, 1]
     return xi
 
 

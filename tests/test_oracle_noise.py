@@ -191,3 +191,109 @@ def test_eigen_factor_lw_noise_statistics():
         for b in range(3, 9):
             sd = np.sqrt((X0[a, a] * X0[b, b] + X0[a, b] ** 2) / ns)
             assert abs(C[a, b] - X0[a, b]) < 5 * sd + 1e-30, (a, b)
+
+
+# --- correlated noise built in real space (2 x 2 stencil, oracle.xi49_stencil) -----------
+
+STENCIL_MODELS = [
+    th.Model(rho0=1.0, cs2=1 / 3, kappa=0.03, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9),
+    th.Model(rho0=0.9, cs2=0.265 ** 2, kappa=0.08, kT=1e-7, tau_s=1.0, tau_b=1.0, tau_ghost=1.0),
+    th.Model(rho0=1.2, cs2=0.2 ** 2, kappa=0.02, kT=1e-4, tau_s=0.7, tau_b=1.3, tau_ghost=0.8),
+]
+
+
+@pytest.mark.parametrize("m", STENCIL_MODELS)
+@pytest.mark.parametrize("factor", ["cholesky", "eigen"])
+@pytest.mark.parametrize("nx,ny", [(12, 10), (16, 16), (7, 5)])
+def test_stencil_noise_has_the_noise_matrix_at_every_k(m, factor, nx, ny):
+    # The construction is linear in the white fields: xi = K * nu.  Its impulse responses
+    # give the transfer function K(k) = sum_d K(d) e^{i k.d}, and the covariance of xi(k)
+    # for unit white nu is sum over the 8 inputs of K K^H.  It must equal the (4,9) block
+    # of the printed Eq. (noise-yeo) at every wavevector of the lattice, any size.
+    Ls = oracle.stencil_factors(m, factor)
+    n = nx * ny
+    cov = np.zeros((ny, nx, 2, 2), dtype=complex)
+    for f in range(4):
+        for c in range(2):
+            nu = np.zeros((4, 2, ny, nx))
+            nu[f, c, 0, 0] = 1.0
+            resp = oracle.stencil_combine(nu, Ls)                  # (2, ny, nx)
+            K = np.fft.ifft2(resp, axes=(1, 2)) * n               # sum_r resp(r) e^{+i k.r}
+            cov += np.einsum("iyx,jyx->yxij", K, np.conj(K))
+    KX, KY = th.lattice_k(nx, ny)
+    for j in range(ny):
+        for i in range(nx):
+            X = m.Xi_closed(KX[j, i], KY[j, i])[np.ix_([3, 8], [3, 8])]
+            np.testing.assert_allclose(cov[j, i], X, rtol=0, atol=1e-13 * np.abs(X).max())
+
+
+def test_stencil_noise_is_local_and_uses_four_independent_fields():
+    # xi(r) depends on the draws of r, r - e_x, r - e_y, r - e_x - e_y only, and every
+    # field enters (dropping one changes the result)
+    m = STENCIL_MODELS[0]
+    nx, ny = 9, 7
+    nu = oracle.stencil_fields(nx, ny, seed=5, step=3)
+    Ls = oracle.stencil_factors(m)
+    base = oracle.stencil_combine(nu, Ls)
+    q = (4, 3)                                                  # (y, x) of a perturbed node
+    pert = nu.copy()
+    pert[:, :, q[0], q[1]] += 1.0
+    diff = np.abs(oracle.stencil_combine(pert, Ls) - base).max(axis=0)
+    changed = set(zip(*np.nonzero(diff > 1e-15)))
+    assert changed == {(4, 3), (4, 4), (5, 3), (5, 4)}          # r = q, q + e_x, q + e_y, q + e_x + e_y
+    for f in range(4):
+        drop = nu.copy()
+        drop[f] = 0.0
+        assert np.abs(oracle.stencil_combine(drop, Ls) - base).max() > 1e-8
+    # the sampled-site version agrees with the field
+    sites = np.array([0, 5, nx - 1, nx * (ny - 1), nx * ny - 1, 31])
+    x4, x9 = oracle.xi49_stencil(m, nx, ny, seed=5, step=3)
+    at = oracle.xi49_stencil_at(m, nx, ny, 5, 3, sites)
+    np.testing.assert_allclose(at[:, 0], x4.ravel()[sites], atol=1e-15)
+    np.testing.assert_allclose(at[:, 1], x9.ravel()[sites], atol=1e-15)
+
+
+def test_stencil_noise_spectrum_statistics():
+    # the draws behind the construction are the stated ones: the sampled spectrum of the
+    # generated fields matches Xi(k) in every k^2 shell, like the Fourier construction's
+    m = th.Model(rho0=1.0, cs2=0.25 ** 2, kappa=0.05, kT=1e-4, tau_s=1.0)
+    nx, ny = 16, 12
+    KX, KY = th.lattice_k(nx, ny)
+    steps = 300
+    P44 = np.zeros((ny, nx)); P99 = np.zeros((ny, nx)); P49 = np.zeros((ny, nx))
+    for t in range(steps):
+        x4, x9 = oracle.xi49_stencil(m, nx, ny, seed=8, step=t)
+        a, b = oracle.unitary_ft(x4), oracle.unitary_ft(x9)
+        P44 += np.abs(a) ** 2; P99 += np.abs(b) ** 2; P49 += (a * np.conj(b)).real
+    X = np.array([[m.Xi_closed(KX[j, i], KY[j, i]) for i in range(nx)] for j in range(ny)])
+    k2 = th.k2_lattice(KX, KY)
+    edges = np.quantile(k2, [0, 0.25, 0.5, 0.75, 1.0])
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (k2 >= lo) & (k2 <= hi)
+        nS = sel.sum() * steps
+        for P, ab in [(P44, (3, 3)), (P99, (8, 8))]:
+            ratio = P[sel].sum() / (steps * X[sel][:, ab[0], ab[1]].sum())
+            assert abs(ratio - 1) < 5 * np.sqrt(2.0 / nS)
+        c = P49[sel].sum() / steps
+        ref = X[sel][:, 3, 8].sum()
+        sd = np.sqrt((X[sel][:, 3, 3] * X[sel][:, 8, 8]).sum() / steps)
+        assert abs(c - ref) < 5 * sd
+
+
+def test_stencil_noise_needs_psd_at_both_ends_of_the_k2_range():
+    # kappa = 0.06 at cs2 = 1/3: Xi is not positive semidefinite at large k^2
+    m = th.Model(rho0=1.0, cs2=1 / 3, kappa=0.06, kT=1e-4, tau_s=1.0)
+    with pytest.raises(ValueError):
+        oracle.stencil_factors(m)
+
+
+@pytest.mark.slow
+def test_stencil_noise_equilibrates_every_mode():
+    # Sec. V A with the real-space construction on a lattice whose sides are not powers of
+    # two: every mode equilibrates, <|dm_a(k)|^2> / G_aa(k) = 1 (Fig. 3 parameters)
+    lat = oracle.Lattice(12, 10, rho0=1.0, cs2=0.265 ** 2, seed=79)
+    lat.set_params(kT=1e-6, kappa=0.08, tau_s=1.0, tau_b=1.0, tau_ghost=1.0, noise_mode=oracle.NOISE_FULL_RS)
+    ratio, keep = _equilibration_ratios(lat, burn=400, samples=1500, every=2, G_of_k=lat.model.G_closed)
+    for a in range(9):
+        r = ratio[a][keep]
+        assert abs(r.mean() - 1) < 0.04, (a, r.mean())

@@ -78,8 +78,9 @@ def parse():
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--batched-only", action="store_true",
                    help="run only the batched-ensemble variant and print its JSON (profiling runs)")
-    p.add_argument("--noise", default="lw", choices=["lw", "full"],
-                   help="noise of the main line (full: correlated, kappa=0.05; for profiling runs)")
+    p.add_argument("--noise", default="lw", choices=["lw", "full", "rs"],
+                   help="noise of the main line (full: correlated via k-space, rs: correlated built in real "
+                        "space, both at kappa=0.05; for profiling runs)")
     p.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                    help="population storage of the main line (fp16: deviations; for profiling runs)")
     return p.parse_args()
@@ -522,9 +523,10 @@ def main():
     time.sleep(0.3)
 
     # main line: long-wavelength noise
-    main_full = args.noise == "full"
-    main_mode, main_params = (lbf.LB_NOISE_FULL, PARAMS_FULL) if main_full else (lbf.LB_NOISE_LW, PARAMS_LW)
-    main_bpn = (BYTES_PER_NODE_STEP_FP16 if main_fp16 else BYTES_PER_NODE_STEP) + (8 if main_full else 0)
+    main_full = args.noise != "lw"
+    main_mode = {"lw": lbf.LB_NOISE_LW, "full": lbf.LB_NOISE_FULL, "rs": lbf.LB_NOISE_FULL_RS}[args.noise]
+    main_params = PARAMS_FULL if main_full else PARAMS_LW
+    main_bpn = (BYTES_PER_NODE_STEP_FP16 if main_fp16 else BYTES_PER_NODE_STEP) + (8 if args.noise == "full" else 0)
     ms, kms, kl, launches, w0, w1 = timed_run(lbf, torch, L, args.steps, args.warmup, main_mode, main_params, dist)
     clk_window = (w0, w1)
 
@@ -538,7 +540,8 @@ def main():
     # variants of config 2: the other (noise, kappa) combinations of the same lattice
     variants = []
     if not args.no_variants and not main_full and not main_fp16:
-        for vmode, vkappa in ((lbf.LB_NOISE_FULL, 0.05), (lbf.LB_NOISE_FULL, 0.01), (lbf.LB_NOISE_LW, 0.05)):
+        for vmode, vkappa in ((lbf.LB_NOISE_FULL, 0.05), (lbf.LB_NOISE_FULL, 0.01), (lbf.LB_NOISE_LW, 0.05),
+                              (lbf.LB_NOISE_FULL_RS, 0.05), (lbf.LB_NOISE_FULL_RS, 0.01)):
             vparams = dict(PARAMS_LW, kappa=vkappa)
             full = vmode == lbf.LB_NOISE_FULL
             bpn = BYTES_PER_NODE_STEP_FULL if full else BYTES_PER_NODE_STEP
@@ -546,8 +549,10 @@ def main():
             fms, fkms, fkl, flaunch, _, _ = timed_run(lbf, torch, L, args.steps, args.warmup, vmode, vparams, dist)
             fms = max_over_ranks(dist, fms, "cuda")
             fk = fkms / max(fkl, 1) / 1e3
-            variants.append({"noise": "full (correlated, k-space synthesis + FFT each step)" if full
-                             else "long-wavelength", "kappa": vkappa,
+            variants.append({"noise": {lbf.LB_NOISE_FULL: "full (correlated, k-space synthesis + FFT each step)",
+                                       lbf.LB_NOISE_FULL_RS: "full (correlated, built in real space: 2x2 stencil of "
+                                                             "four white fields, fused in the step kernel)",
+                                       lbf.LB_NOISE_LW: "long-wavelength"}[vmode], "kappa": vkappa,
                              "value": whole_job_mlups(world, nodes, args.steps, fms), "unit": "MLUPS",
                              "ms_per_step": fms / args.steps,
                              "step_kernel": {"achieved": bpn * nodes / fk / 1e9, "unit": "GB/s",
@@ -620,7 +625,8 @@ def main():
                                "lattice, %s noise, kappa=%.2f, tau_s=0.8, tau_b=1, tau_ghost=1, "
                                "kT=1e-4, cs2=1/3, S(k) every %d steps into %d bins (FP64)" % (
                                    n, n, "FP16-deviation" if main_fp16 else "FP32",
-                                   "correlated (full FDT)" if main_full else "long-wavelength",
+                                   {"lw": "long-wavelength", "full": "correlated (full FDT, k-space)",
+                                    "rs": "correlated (full FDT, real space)"}[args.noise],
                                    main_params["kappa"], args.every, args.nbins),
                    "lattice": [n, n], "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (
                        9 * (n + 64) * (n + 4) * 4 / 1e6), "parallelism": "replicas" if world > 1 else "single"},

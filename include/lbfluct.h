@@ -59,6 +59,14 @@ extern "C" {
 #define LB_NOISE_FULL 2    /* spatially correlated, covariance Xi(k), Eq. (noise-yeo);
                               needs nx, ny powers of two, ny <= 8192 */
 #define LB_NOISE_DIAG 3    /* "ideal gas-like": LW with the off-diagonal Xi_49 dropped */
+#define LB_NOISE_FULL_RS 4 /* spatially correlated, covariance Xi(k) of Eq. (noise-yeo) at every k,
+                              built in real space: Xi depends on k only through the lattice k^2 s
+                              (Appendix B), affinely, so four white 2-vector fields nu_ab drawn per
+                              node, each times a factor L_ab of Xi at s = 0, 4, 4, 16/3 and summed
+                              over the 2x2 box {r, r-e_x, r-e_y, r-e_x-e_y} with the signs
+                              a^dx b^dy (a, b = +-1), give xi_4, xi_9 with exactly that covariance
+                              (no transform; any lattice size).  Needs Xi positive semidefinite
+                              at s = 0 and s = 16/3.  Modes 5..8 as LB_NOISE_LW. */
 
 /* factorisation of the noise matrix, [GACV] Sec. IV (xi = L nu with L L^T = Xi) */
 #define LB_FACTOR_CHOLESKY 0   /* Cholesky of the lower-right block (default) */
@@ -127,7 +135,9 @@ int lb_set_noise_factor(lb_ctx* ctx, int factor);
  * Advances nsteps >= 0 time steps of [GACV] Eq. (fluct-lin-lbe): stream (pull),
  * collide in moment space with the Table II equilibrium (Appendix B Laplacian),
  * add the noise of the chosen mode, transform back.  The collision at time t draws
- * its random numbers with counter (node y*nx+x, t mod 2^32, t div 2^32, tag).  If
+ * its random numbers with counter (node y*nx+x, t mod 2^32, t div 2^32, tag): tag 0 per
+ * node (words 0, 1: nu_5..nu_8, word 2: nu_4, nu_9), tag 2 per wavevector pair
+ * (LB_NOISE_FULL), tag 3 per node (LB_NOISE_FULL_RS: word w gives field w of ++, +-, -+, --).  If
  * sampling is on (lb_set_sampling) the spectra are accumulated after every step
  * that brings the time to a multiple of `every`.  Asynchronous on the stream.
  * Errors: LB_ESTATE before lb_set_params, LB_ECUDA on launch failure.

@@ -26,7 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbref.so")
 _lib = None
 
-NOISE_OFF, NOISE_LW, NOISE_FULL, NOISE_DIAG, NOISE_FULL_RS = 0, 1, 2, 3, 4
+NOISE_OFF, NOISE_LW, NOISE_FULL, NOISE_DIAG, NOISE_FULL_RS, NOISE_LW_LOCAL = 0, 1, 2, 3, 4, 5
 TAG_NODE, TAG_KSPACE, TAG_STENCIL = 0, 2, 3
 
 
@@ -278,48 +278,97 @@ def noise_fields(model: Model, mode: int, nx, ny, seed, step, L0=None, factor: s
 
 # --- the step -----------------------------------------------------------------------
 
-def params_vector(model: Model) -> np.ndarray:
-    return np.concatenate([[model.rho0, model.cs2, model.kappa], model.lam]).astype(np.float64)
+def params_vector(model: Model, eos=None) -> np.ndarray:
+    """{rho0, cs2, kappa, lambda_1..9, eos, beta, rhoV, rhoL} for the C core (eos 0: p0 = cs2
+    rho; 1: the double well `eos`, a theory.DoubleWell)."""
+    tail = [0.0, 0.0, 0.0, 0.0] if eos is None else [1.0, eos.beta, eos.rhoV, eos.rhoL]
+    return np.concatenate([[model.rho0, model.cs2, model.kappa], model.lam, tail]).astype(np.float64)
 
 
-def step(f: np.ndarray, model: Model, xi=None) -> np.ndarray:
+def step(f: np.ndarray, model: Model, xi=None, eos=None) -> np.ndarray:
     """One step of Eq. (fluct-lin-lbe) on a periodic lattice: f[9, ny, nx] pre-collision
-    populations in, next pre-collision populations out (FP64)."""
+    populations in, next pre-collision populations out (FP64).  eos: None for p0 = cs2 rho,
+    else a theory.DoubleWell."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     _, ny, nx = f.shape
     out = np.empty_like(f)
-    par = params_vector(model)
+    par = params_vector(model, eos)
     xi_c = None if xi is None else np.ascontiguousarray(xi, dtype=np.float64)
     lib().oracle_step(nx, ny, _dp(f), _dp(out), _dp(par), _dp(xi_c))
     return out
 
 
-def collide_sites(f: np.ndarray, model: Model, sites: np.ndarray, xi_sites=None) -> np.ndarray:
+def collide_sites(f: np.ndarray, model: Model, sites: np.ndarray, xi_sites=None, eos=None) -> np.ndarray:
     """Post-collision populations f*_i at the given linear sites, shape (len(sites), 9)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     _, ny, nx = f.shape
     s = np.ascontiguousarray(sites, dtype=np.int64)
     out = np.zeros((s.size, 9))
-    par = params_vector(model)
+    par = params_vector(model, eos)
     xs = None if xi_sites is None else np.ascontiguousarray(xi_sites, dtype=np.float64)
     lib().oracle_collide_sites(nx, ny, _dp(f), s.size, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                _dp(par), _dp(xs), _dp(out))
     return out
 
 
+# --- uncorrelated noise at the local density (inhomogeneous systems) ------------------------
+
+def xi_zero_local(model: Model, rho, c2):
+    """Entries of Xi(0), Eq. (noise-yeo) at k = 0, with the density rho0 and the sound speed
+    squared c_s^2 replaced by local values rho, c2 (arrays): the uncorrelated noise of an
+    inhomogeneous system (Sec. IV, and Sec. V B: local density and sound speed in the
+    real-space noise variance).  Returns x44, x49, x99, x55, x66, x77 (= x88)."""
+    lb, ls, lq, le = model.lam[3], model.lam[4], model.lam[6], model.lam[8]
+    til = lambda l: l * (2 + l)
+    til_be = lb + le + lb * le
+    pref = -(np.asarray(rho) * model.kT / SIGMA_S2)
+    return (pref * N[3] * (2 - 3 * c2) * til(lb), pref * 12 * (c2 - SIGMA_S2) * til_be,
+            pref * N[8] * (5 / 4 - 3 / 4 * c2) * til(le), pref * N[4] * til(ls), pref * N[5] * til(ls),
+            pref * N[6] * til(lq))
+
+
+def local_noise_fields(model: Model, rho, c2, seed, step):
+    """xi[a, y, x] of the uncorrelated noise at the local density: at every node the (4,9)
+    block of xi_zero_local is factored by Cholesky (a negative pivot, where the local block is
+    not positive semidefinite, is clamped to zero), the other modes take the square roots of
+    their variances; the unit normals are the long-wavelength mode's (tag 0)."""
+    ny, nx = rho.shape
+    n = nx * ny
+    g0 = normals(np.arange(n, dtype=np.uint32), seed, step, TAG_NODE)
+    x44, x49, x99, x55, x66, x77 = xi_zero_local(model, rho.ravel(), np.broadcast_to(c2, rho.shape).ravel())
+    L44 = np.sqrt(np.maximum(x44, 0.0))
+    L94 = np.where(L44 > 0, x49 / np.where(L44 > 0, L44, 1.0), 0.0)
+    L99 = np.sqrt(np.maximum(x99 - L94 * L94, 0.0))
+    xi = np.zeros((9, n))
+    xi[3] = L44 * g0[:, 4]
+    xi[8] = L94 * g0[:, 4] + L99 * g0[:, 5]
+    xi[4] = np.sqrt(np.maximum(x55, 0.0)) * g0[:, 0]
+    xi[5] = np.sqrt(np.maximum(x66, 0.0)) * g0[:, 1]
+    xi[6] = np.sqrt(np.maximum(x77, 0.0)) * g0[:, 2]
+    xi[7] = np.sqrt(np.maximum(x77, 0.0)) * g0[:, 3]
+    return xi.reshape(9, ny, nx)
+
+
 class Lattice:
     """A periodic nx x ny lattice stepped by the oracle (FP64), noise per Sec. IV.
 
     ``f`` holds pre-collision populations f[i, y, x]; ``t`` is the index of the next
-    collision, which keys its random numbers."""
+    collision, which keys its random numbers.  ``eos`` (a theory.DoubleWell) replaces the
+    linearised p0 = cs2 rho by the double well's bulk pressure; the linear theory about rho0
+    (noise covariance, rest state) then takes c_s^2(rho0) and p0(rho0)."""
 
-    def __init__(self, nx, ny, rho0=1.0, cs2=SIGMA_S2, seed=42):
+    def __init__(self, nx, ny, rho0=1.0, cs2=SIGMA_S2, seed=42, eos=None):
         self.nx, self.ny = int(nx), int(ny)
         self.seed = int(seed)
-        self.model = Model(rho0=rho0, cs2=cs2)
+        self.eos = eos
+        if eos is None:
+            self.model = Model(rho0=rho0, cs2=cs2)
+        else:
+            self.model = Model(rho0=rho0, cs2=eos.cs2(rho0), p0_rest=eos.p0(rho0))
         self.mode = NOISE_OFF
         self.t = 0
-        self.f = np.broadcast_to(self.model.fbar()[:, None, None], (9, ny, nx)).copy()
+        rest = self.model.fbar() if eos is None else self.model.rest()
+        self.f = np.broadcast_to(rest[:, None, None], (9, ny, nx)).copy()
         self._L0 = None
         self.factor = "cholesky"
 
@@ -328,7 +377,7 @@ class Lattice:
         (Sec. IV); None keeps the current one."""
         if factor is not None:
             self.factor = factor
-        m = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
+        m = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost, p0_rest=self.model.p0_rest)
         fb_old = self.model.fbar()
         self.model = m
         self.mode = int(noise_mode)
@@ -338,8 +387,15 @@ class Lattice:
         self._L0 = theory.noise_factor(X0, self.factor)
         del fb_old
 
+    def local_sound_speed2(self, rho):
+        """c_s^2 at density rho: rho d2f0/drho2 of the double well, else the constant cs2."""
+        return self.eos.cs2(rho) if self.eos is not None else np.full_like(rho, self.model.cs2)
+
     def noise(self, t=None):
         t = self.t if t is None else t
+        if self.mode == NOISE_LW_LOCAL:
+            rho = self.f.sum(axis=0)         # the density the collision at time t sees
+            return local_noise_fields(self.model, rho, self.local_sound_speed2(rho), self.seed, t)
         return noise_fields(self.model, self.mode, self.nx, self.ny, self.seed, t, self._L0, self.factor)
 
     def step(self, nsteps=1):
@@ -347,7 +403,7 @@ class Lattice:
             xi = None
             if self.mode != NOISE_OFF and self.model.kT > 0:
                 xi = self.noise()
-            self.f = step(self.f, self.model, xi)
+            self.f = step(self.f, self.model, xi, self.eos)
             self.t += 1
         return self
 

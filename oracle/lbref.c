@@ -13,7 +13,8 @@
  *     m_a^eq) + xi_a, then f*_i = (T^-1 m*)_i and f_i(r + c_i, t+1) = f*_i(r, t);
  *   - the basis of Table I / Eq. (Tmat), built here from its polynomials;
  *   - the equilibrium moments of Table II with p0 = cs2 rho (linearised equation
- *     of state), no Galilean corrections (C_n = 0) and no forcing (m^F = 0);
+ *     of state) or the bulk pressure of the Landau double well of Sec. II A, no
+ *     Galilean corrections (C_n = 0) and no forcing (m^F = 0);
  *   - the Laplacian of Appendix B and the isotropic gradient
  *     d_alpha rho = 3 sum_i w_i c_i,alpha rho(r + c_i) for the (grad rho)^2 terms.
  * The noise xi_a(r) is an input (the Python side builds it per Sec. IV).
@@ -145,7 +146,21 @@ void oracle_normals(int64_t count, const uint32_t* index, uint64_t seed, uint64_
 typedef struct {
     double rho0, cs2, kappa;
     double lam[Q];
+    int eos;                       /* 0: p0 = cs2 rho;  1: Landau double well (Sec. II A) */
+    double beta, rhoV, rhoL;       /* f0 = beta (rho - rhoV)^2 (rho - rhoL)^2 */
 } params_t;
+
+/* Bulk pressure of the equation of state (Sec. II A): p0 = rho d(f0)/d(rho) - f0 for the
+ * double well f0 = beta (rho - rhoV)^2 (rho - rhoL)^2, else the linearised p0 = cs2 rho. */
+static double bulk_pressure(const params_t* p, double rho) {
+    if (p->eos == 1) {
+        const double a = rho - p->rhoV, b = rho - p->rhoL;
+        const double f0 = p->beta * a * a * b * b;
+        const double df0 = 2.0 * p->beta * a * b * (a + b);          /* d f0 / d rho */
+        return rho * df0 - f0;
+    }
+    return p->cs2 * rho;
+}
 
 static int wrap(int v, int n) {
     v %= n;
@@ -173,7 +188,7 @@ static void collide_site(const params_t* p, const double rho_nb[Q], const double
         gx += 3.0 * WT[j] * CX[j] * rho_nb[j];
         gy += 3.0 * WT[j] * CY[j] * rho_nb[j];
     }
-    double p0 = p->cs2 * rho;                                   /* linearised EOS */
+    double p0 = bulk_pressure(p, rho);                          /* equation of state */
     double iso = p0 - rho * s2 - p->kappa * rho * lap;
     meq[0] = rho;
     meq[1] = rho * ux;
@@ -193,11 +208,15 @@ static void collide_site(const params_t* p, const double rho_nb[Q], const double
 }
 
 static void load_params(params_t* p, const double* par) {
-    /* par = {rho0, cs2, kappa, lambda_1 .. lambda_9} */
+    /* par = {rho0, cs2, kappa, lambda_1 .. lambda_9, eos, beta, rhoV, rhoL} */
     p->rho0 = par[0];
     p->cs2 = par[1];
     p->kappa = par[2];
     for (int a = 0; a < Q; ++a) p->lam[a] = par[3 + a];
+    p->eos = (int)par[12];
+    p->beta = par[13];
+    p->rhoV = par[14];
+    p->rhoL = par[15];
 }
 
 /*

@@ -84,12 +84,51 @@ def k2_lattice(kx, ky):
     return -sym
 
 
+class DoubleWell:
+    """Landau double-well bulk free energy f0 = beta (rho - rhoV)^2 (rho - rhoL)^2 (Sec. II A,
+    Eq. f0-bulk), its bulk pressure p0 = rho df0/drho - f0, sound speed squared
+    c_s^2 = dp0/drho = rho d2f0/drho2, and the flat-interface results of Eqs. (interf-width)
+    and (surf-tension)."""
+
+    def __init__(self, beta, rhoV, rhoL):
+        self.beta, self.rhoV, self.rhoL = float(beta), float(rhoV), float(rhoL)
+
+    def f0(self, rho):
+        return self.beta * (rho - self.rhoV) ** 2 * (rho - self.rhoL) ** 2
+
+    def df0(self, rho):
+        a, b = rho - self.rhoV, rho - self.rhoL
+        return 2 * self.beta * a * b * (a + b)
+
+    def d2f0(self, rho):
+        a, b = rho - self.rhoV, rho - self.rhoL
+        return 2 * self.beta * (a * a + 4 * a * b + b * b)
+
+    def p0(self, rho):
+        return rho * self.df0(rho) - self.f0(rho)
+
+    def cs2(self, rho):
+        return rho * self.d2f0(rho)
+
+    def width(self, kappa):
+        """Interface width xi = sqrt(8 kappa / beta) / (rhoL - rhoV), Eq. (interf-width)."""
+        return np.sqrt(8 * kappa / self.beta) / (self.rhoL - self.rhoV)
+
+    def surface_tension(self, kappa):
+        """sigma = (rhoL - rhoV)^3 sqrt(2 kappa beta) / 6, Eq. (surf-tension)."""
+        return (self.rhoL - self.rhoV) ** 3 * np.sqrt(2 * kappa * self.beta) / 6
+
+
 class Model:
-    """Parameters of one homogeneous run: rho0, cs2, kappa, kT and the relaxation times."""
+    """Parameters of one homogeneous run: rho0, cs2, kappa, kT and the relaxation times.
+    p0_rest is the bulk pressure of the uniform rest state at rho0 (cs2 rho0 for the
+    linearised equation of state; p0(rho0) of a double well, whose fluctuations about rho0
+    have cs2 = c_s^2(rho0))."""
 
     def __init__(self, rho0=1.0, cs2=SIGMA_S2, kappa=0.0, kT=0.0,
-                 tau_s=1.0, tau_b=1.0, tau_ghost=1.0):
+                 tau_s=1.0, tau_b=1.0, tau_ghost=1.0, p0_rest=None):
         self.rho0 = float(rho0)
+        self.p0_rest = float(cs2) * float(rho0) if p0_rest is None else float(p0_rest)
         self.cs2 = float(cs2)
         self.kappa = float(kappa)
         self.kT = float(kT)
@@ -119,8 +158,18 @@ class Model:
         return m
 
     def fbar(self, kx=0.0, ky=0.0) -> np.ndarray:
-        """Rest populations fbar_i = (T^-1 mbar)_i; at k = 0 the uniform rest state of the run."""
+        """Rest populations fbar_i = (T^-1 mbar)_i; at k = 0 the uniform rest state of the run
+        for the linearised equation of state."""
         return TINV @ self.mbar(kx, ky)
+
+    def rest(self) -> np.ndarray:
+        """Populations of the uniform rest state at rho0: Table II at u = 0, grad rho = 0,
+        m4 = -m9 = 6 (p0(rho0) - sigma_s^2 rho0), through T^-1."""
+        m = np.zeros(9)
+        m[0] = self.rho0
+        m[3] = 6 * (self.p0_rest - SIGMA_S2 * self.rho0)
+        m[8] = -m[3]
+        return TINV @ m
 
     # --- linearised collision and advection (Sec. III B, C) ------------------
     def Omega(self, kx, ky) -> np.ndarray:

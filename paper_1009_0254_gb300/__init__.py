@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbfluct.so")
 LB_OK, LB_EINVAL, LB_ENOTPSD, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LB_ENONFINITE, LB_ECANCELED = -7, -8
 LB_FP32, LB_FP16DEV, LB_FP64 = 0, 1, 2
-LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL, LB_NOISE_DIAG = 0, 1, 2, 3
+LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL, LB_NOISE_DIAG, LB_NOISE_FULL_RS = 0, 1, 2, 3, 4
 LB_FACTOR_CHOLESKY, LB_FACTOR_EIGEN = 0, 1
 LB_HOST, LB_DEVICE = 0, 1
 LB_WARN_LOW_MACH = 1

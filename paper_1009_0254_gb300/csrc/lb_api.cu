@@ -113,6 +113,11 @@ NoiseCoef noise_coef(double rho0, double cs2, double kT, double kappa, double ta
     return c;
 }
 
+// largest lattice k^2 (at k = (pi, pi)), and the k^2 of the middle factor of the real-space
+// correlated noise (LB_NOISE_FULL_RS, lb_internal.cuh stencil_h)
+constexpr double S_MAX = 16.0 / 3.0;
+constexpr double S_MID = 4.0;
+
 // lattice k^2: minus the Fourier symbol of the Appendix B Laplacian
 double k2_lattice(double kx, double ky) {
     return -((4.0 / 9.0) * (std::cos(kx) + std::cos(ky)) + (2.0 / 9.0) * std::cos(kx) * std::cos(ky) - 10.0 / 9.0) /
@@ -149,7 +154,7 @@ int validate(int nx, int ny, double rho0, double cs2, double kT, double kappa, d
     if (!(tau_s > 0.5) || !(tau_b > 0.5) || !(tau_g > 0.5)) return bad("every relaxation time must exceed 1/2");
     if (!(kT >= 0.0) || !std::isfinite(kT)) return bad("kT must be finite and >= 0");
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return bad("kappa must be finite and >= 0");
-    if (mode < LB_NOISE_OFF || mode > LB_NOISE_DIAG) return bad("unknown noise mode");
+    if (mode < LB_NOISE_OFF || mode > LB_NOISE_FULL_RS) return bad("unknown noise mode");
     if (!(rho0 > 0.0) || !(cs2 > 0.0)) return bad("rho0 and cs2 must be positive");
     if (mode == LB_NOISE_OFF || kT == 0.0) return LB_OK;
     const NoiseCoef c = noise_coef(rho0, cs2, 1.0, kappa, tau_s, tau_b, tau_g);
@@ -163,6 +168,12 @@ int validate(int nx, int ny, double rho0, double cs2, double kT, double kappa, d
                     return LB_ENOTPSD;
                 }
             }
+    } else if (mode == LB_NOISE_FULL_RS) {
+        // Xi is affine in the lattice k^2 over [0, 16/3]: PSD at both ends <=> PSD for all k
+        if (!block_psd(c, 0.0) || !block_psd(c, S_MAX)) {
+            if (why) *why = "noise covariance Xi is not positive semidefinite at lattice k^2 = 0 or 16/3";
+            return LB_ENOTPSD;
+        }
     } else if (mode == LB_NOISE_LW) {
         if (!block_psd(c, 0.0)) {
             if (why) *why = "noise covariance Xi(0) is not positive semidefinite";
@@ -464,6 +475,22 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     a.s5 = (float)std::sqrt(std::fmax(nc.x55, 0.0));
     a.s6 = (float)std::sqrt(std::fmax(nc.x66, 0.0));
     a.s7 = (float)std::sqrt(std::fmax(nc.x77, 0.0));
+    // real-space correlated noise: factors of the (4,9) block at k^2 = 0, 4, 16/3, over 4
+    double sL[3][4];
+    const double sk[3] = {0.0, S_MID, S_MAX};
+    for (int j = 0; j < 3; ++j) {
+        const double y44 = nc.a44 + nc.b44 * sk[j], y49 = nc.a49 + nc.b49 * sk[j], y99 = nc.a99 + nc.b99 * sk[j];
+        double l11, l12 = 0.0, l21, l22;
+        if (c->factor == LB_FACTOR_EIGEN) {
+            eigen_factor_2x2(y44, y49, y99, &l11, &l12, &l21, &l22);
+        } else {
+            l11 = std::sqrt(std::fmax(y44, 0.0));
+            l21 = l11 > 0.0 ? y49 / l11 : 0.0;
+            l22 = std::sqrt(std::fmax(y99 - l21 * l21, 0.0));
+        }
+        sL[j][0] = 0.25 * l11; sL[j][1] = 0.25 * l12; sL[j][2] = 0.25 * l21; sL[j][3] = 0.25 * l22;
+        for (int q = 0; q < 4; ++q) a.sL[j][q] = (float)sL[j][q];
+    }
     NoiseGenArgs& ga = c->ga;
     ga.a44 = (float)nc.a44; ga.b44 = (float)nc.b44;
     ga.a49 = (float)nc.a49; ga.b49 = (float)nc.b49;
@@ -479,6 +506,8 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     d.s5 = std::sqrt(std::fmax(nc.x55, 0.0));
     d.s6 = std::sqrt(std::fmax(nc.x66, 0.0));
     d.s7 = std::sqrt(std::fmax(nc.x77, 0.0));
+    for (int j = 0; j < 3; ++j)
+        for (int q = 0; q < 4; ++q) d.sL[j][q] = sL[j][q];
     NoiseGenArgsD& gd = c->gad;
     gd.a44 = nc.a44; gd.b44 = nc.b44; gd.a49 = nc.a49; gd.b49 = nc.b49; gd.a99 = nc.a99; gd.b99 = nc.b99;
     gd.cosx = c->cosxd; gd.cosy = c->cosyd; gd.nx = c->nx; gd.ny = c->ny;
@@ -527,7 +556,9 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
     if (!c->have_params) return fail(c, LB_ESTATE, "lb_set_params must be called before lb_step");
     DeviceGuard dg(c->device);
     const bool noisy = c->noise_mode != LB_NOISE_OFF && c->kT > 0.0;
-    const int kmode = !noisy ? 0 : (c->noise_mode == LB_NOISE_FULL ? 2 : 1);
+    // kernel noise mode: 0 none, 1 uncorrelated, 2 correlated (k-space field), 3 correlated
+    // built in real space
+    const int kmode = !noisy ? 0 : (c->noise_mode == LB_NOISE_FULL ? 2 : (c->noise_mode == LB_NOISE_FULL_RS ? 3 : 1));
     if (kmode == 2 && !c->pow2)
         return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two (radix-2 FFT)");
     for (int64_t k = 0; k < nsteps; ++k) {
@@ -587,7 +618,7 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
             if (r != LB_OK) return r;
             CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
         }
-        if (c->use_sweep)
+        if (c->use_sweep && kmode != 3)      // the sweep kernel has no real-space correlated noise
             CK(c, launch_step_sweep(a, kmode, c->fp16, c->sweep_occ6, c->stream), "step kernel launch");
         else if (c->use_tma) {
             const int want = c->tma_tile_fixed >= 0 ? c->tma_tile_fixed : tma_default_tile(kmode, c->fp16);

@@ -110,6 +110,8 @@ struct StepArgsT {
     R lb, ls, lq, le;                // lambda_b, lambda_s, lambda_q, lambda_eps
     R L44, L49, L94, L99;            // factor of the (4,9) block of Xi(0) (L49 = 0: Cholesky)
     R s5, s6, s7;                    // sqrt(Xi_55), sqrt(Xi_66), sqrt(Xi_77) = sqrt(Xi_88)
+    R sL[3][4];                      // real-space correlated noise: factors (L44, L49, L94, L99) / 4
+                                     // of the (4,9) block of Xi at lattice k^2 = 0, 4, 16/3
     uint32_t t_lo, t_hi;
     RoundKeys rk;
 };
@@ -229,6 +231,37 @@ __device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
 // noise draw tags (fourth counter word)
 constexpr uint32_t TAG_NODE = 0;     // per node: words 0, 1 -> nu_5..nu_8, word 2 -> (nu_4, nu_9)
 constexpr uint32_t TAG_KSPACE = 2;   // per wavevector pair: words 0, 1 -> eta_1(k), eta_2(k)
+constexpr uint32_t TAG_STENCIL = 3;  // per node: word w -> white 2-vector field w (++, +-, -+, --)
+
+// Real-space correlated noise (LB_NOISE_FULL_RS).  The (4,9) noise at r is
+//   xi(r) = h00(r) + h10(r - e_x) + h01(r - e_y) + h11(r - e_x - e_y),
+// where node q contributes h_d(q) = 1/4 sum_ab a^dx b^dy L_ab nu_ab(q): the four white
+// 2-vectors nu_ab(q) of its tag-3 draw, times the factors L_ab of Xi at lattice k^2 = 0
+// (++), 4 (+- and -+) and 16/3 (--), combined with the 2 x 2 Hadamard signs.  sL holds
+// L_ab / 4; h[0..7] = (h00, h10, h01, h11) as (xi_4, xi_9) pairs.
+template <typename Args, typename R>
+__device__ __forceinline__ void stencil_h(const Args& a, uint32_t node, R h[8]) {
+    const uint4 w = philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_STENCIL), a.rk);
+    R g[4][2];
+    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        R n0, n1;
+        gauss_word(ww[f], &n0, &n1);
+        const int k = f == 0 ? 0 : (f == 3 ? 2 : 1);
+        g[f][0] = a.sL[k][0] * n0 + a.sL[k][1] * n1;
+        g[f][1] = a.sL[k][2] * n0 + a.sL[k][3] * n1;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const R u = g[0][c] + g[1][c], v = g[0][c] - g[1][c];
+        const R wv = g[2][c] + g[3][c], z = g[2][c] - g[3][c];
+        h[0 + c] = u + wv;       // h00: all signs +
+        h[2 + c] = u - wv;       // h10: sign a
+        h[4 + c] = v + z;        // h01: sign b
+        h[6 + c] = v - z;        // h11: sign a b
+    }
+}
 
 // Writes v at (x, y) of a plane and at the ghost copies that (x, y) feeds.  Only columns
 // -2, -1, nx, nx+1 and rows -2, -1, ny, ny+1 are ever read, but the ghost columns are

@@ -7,8 +7,9 @@
 //   m      moments m = T f in deviation form (Table I basis, Eq. Tmat)
 //   m^eq   Table II with p0 = cs2 rho, C_n = 0, m^F = 0
 //   relax  m*_a = m_a + lambda_a (m_a - m_a^eq) + xi_a,  a = 4..9        (Eq. fluct-lin-lbe)
-//   noise  xi from Philox4x32-10 keyed (seed, t, node, tag) (Sec. IV), or for the
-//          correlated mode xi_4, xi_9 read from the k-space synthesis
+//   noise  xi from Philox4x32-10 keyed (seed, t, node, tag) (Sec. IV); for the
+//          correlated mode xi_4, xi_9 read from the k-space synthesis or, built in real
+//          space, summed over the 2 x 2 box of draws below-left of the node
 //   back   f*_i = w_i sum_a T_ai m*_a / N_a                                 (Sec. III A)
 //   store  f*_i(r,t) with its periodic ghost copies.
 // Everything is FP32 on deviations from the rest state fbar_i, which keeps the
@@ -40,11 +41,29 @@ __device__ __forceinline__ void pull9(const T* __restrict__ s, long long P, int 
     f[8] = Elem<T>::load(s[8 * P + c + pitch - 1], 8);       // c = ( 1,-1)
 }
 
+// contributions h_d of node q (tile coordinates lx, ly >= -1) to the real-space correlated
+// noise, in the arithmetic type (stencil_h in lb_internal.cuh)
+template <int HW, typename Args, typename V>
+__device__ __forceinline__ void stencil_put(const Args& a, V* H, int HN, int lx, int ly, uint32_t node) {
+    decltype(V().x) h[8];
+    stencil_h(a, node, h);
+    const int q = (ly + 1) * HW + lx + 1;
+    H[q].x = h[0]; H[q].y = h[1];
+    H[HN + q].x = h[2]; H[HN + q].y = h[3];
+    H[2 * HN + q].x = h[4]; H[2 * HN + q].y = h[5];
+    H[3 * HN + q].x = h[6]; H[3 * HN + q].y = h[7];
+}
+
 template <int BX, int BY, int MODE, typename T>
 __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgsT<typename Arith<T>::type> a) {
     using TL = Tile<BX, BY>;
     using R = typename Arith<T>::type;
+    using V = typename Arith<T>::vec2;
     __shared__ R rs[TL::RY][TL::RX];
+    // real-space correlated noise (MODE 3): h00, h10, h01, h11 of the tile's nodes and of the
+    // column left of it and the row below it
+    constexpr int HW = BX + 1, HN = (BX + 1) * (BY + 1);
+    __shared__ V H[MODE == 3 ? 4 * HN : 1];
     const Grid g = a.g;
     const T* __restrict__ src = static_cast<const T*>(a.src);
     const long long P = g.plane;
@@ -83,6 +102,18 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgsT<typename 
         }
         rs[hy + 1][hx + 1] = v;
     }
+    if (MODE == 3) {
+        if (own) stencil_put<HW>(a, H, HN, tx, ty, (uint32_t)y * (uint32_t)g.nx + (uint32_t)x);
+        for (int j = tid; j < BX + BY + 1; j += BX * BY) {
+            int lx, ly;
+            if (j <= BY) { lx = -1; ly = j - 1; }
+            else { lx = j - (BY + 1); ly = -1; }
+            int gx = x0 + lx, gy = y0 + ly;
+            if (gx < 0) gx += g.nx;
+            if (gy < 0) gy += g.ny;
+            if (gx < g.nx && gy < g.ny) stencil_put<HW>(a, H, HN, lx, ly, (uint32_t)gy * (uint32_t)g.nx + (uint32_t)gx);
+        }
+    }
     __syncthreads();
     if (!own) return;
 
@@ -96,6 +127,12 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgsT<typename 
     const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
     typename Arith<T>::vec2 z{};
     if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
+    if (MODE == 3) {
+        const int q = (ty + 1) * HW + tx + 1;
+        const V h00 = H[q], h10 = H[HN + q - 1], h01 = H[2 * HN + q - HW], h11 = H[3 * HN + q - HW - 1];
+        z.x = (h00.x + h10.x) + (h01.x + h11.x);
+        z.y = (h00.y + h10.y) + (h01.y + h11.y);
+    }
     R o[Q];
     collide_node<MODE>(a, f, r, node, z, o);
 
@@ -111,6 +148,7 @@ static void launch_t(const StepArgsT<typename Arith<T>::type>& a, int noise_mode
     switch (noise_mode) {
         case 0: step_kernel<BX, BY, 0, T><<<grid, block, 0, s>>>(a); break;
         case 1: step_kernel<BX, BY, 1, T><<<grid, block, 0, s>>>(a); break;
+        case 3: step_kernel<BX, BY, 3, T><<<grid, block, 0, s>>>(a); break;
         default: step_kernel<BX, BY, 2, T><<<grid, block, 0, s>>>(a); break;
     }
 }

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
     const int tid = threadIdx.x;
     const int ntiles = ta.ntx * ta.nty;
     auto load9 = [](const T* S, int b, float f[Q]) { load9_ps<TT::PS>(S, b, f); };
+    float2* H = reinterpret_cast<float2*>(smem_raw + TT::H_OFFSET);   // MODE 3 only
 
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
@@ -104,6 +105,18 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             load9(S, (ly + 1) * TT::BW + lx + TT::XO, fr[it]);
             R[(ly + 1) * TT::RW + lx + 1] = drho_of(fr[it]);
         }
+        if (MODE == 3) {
+            // real-space correlated noise: every node's contributions, then the halo's
+#pragma unroll 1
+            for (int it = 0; it < NN; ++it) {
+                const int q = tid + it * NT;
+                const int ly = q / TX, lx = q - ly * TX;
+                const int x = x0 + lx, y = y0 + ly;
+                if (x < g.nx && y < g.ny)
+                    stencil_store<TT::HW>(a, H, TT::HN, lx, ly, (uint32_t)y * (uint32_t)g.nx + (uint32_t)x);
+            }
+            stencil_halo<TX, TY, TT::HW>(a, H, TT::HN, x0, y0, g.nx, g.ny, tid, NT);
+        }
         // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
         constexpr int NB = 2 * (TX + 2) + 2 * TY;
         for (int j = tid; j < NB; j += NT) {
@@ -142,6 +155,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
             float2 z = make_float2(0.f, 0.f);
             if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
+            if (MODE == 3) z = stencil_xi<TT::HW>(H, TT::HN, lx, ly);
             float o[Q];
             collide_node<MODE>(a, f, r, node, z, o);
             store9(static_cast<T*>(a.dst), g.plane, g, x, y, o);
@@ -178,8 +192,8 @@ int tma_tile_count() { return 5; }
 // (215 us), correlated 32x16 (246 us); FP16 off 32x16/128 (153 us), uncorrelated 32x32
 // (233 us), correlated 64x16 (245 us).
 int tma_default_tile(int noise_mode, int fp16) {
-    static const int best[2][3] = {{1, 3, 0}, {4, 1, 3}};
-    const int m = noise_mode < 0 ? 0 : (noise_mode > 2 ? 2 : noise_mode);
+    static const int best[2][4] = {{1, 3, 0, 0}, {4, 1, 3, 0}};
+    const int m = noise_mode < 0 ? 0 : (noise_mode > 3 ? 3 : noise_mode);
     return best[fp16 ? 1 : 0][m];
 }
 
@@ -207,15 +221,16 @@ template <int TX, int TY, int NT, int MODE, typename T>
 static cudaError_t launch_cfg(const void* map, TmaArgs ta, cudaStream_t s) {
     using TT = TmaTile<TX, TY, T>;
     auto kern = step_tma_kernel<TX, TY, NT, MODE, T>;
+    constexpr int smem = TT::SMEM_BYTES + (MODE == 3 ? TT::H_BYTES : 0);
     static GridCache cache;
     int grid_max = 0;
-    cudaError_t e = resident_grid(kern, NT, TT::SMEM_BYTES, cache, &grid_max);
+    cudaError_t e = resident_grid(kern, NT, smem, cache, &grid_max);
     if (e != cudaSuccess) return e;
     ta.ntx = (ta.a.g.nx + TX - 1) / TX;
     ta.nty = (ta.a.g.ny + TY - 1) / TY;
     const int ntiles = ta.ntx * ta.nty;
     const int grid = ntiles < grid_max ? ntiles : grid_max;
-    kern<<<grid, NT, TT::SMEM_BYTES, s>>>(*reinterpret_cast<const CUtensorMap*>(map), ta);
+    kern<<<grid, NT, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(map), ta);
     return cudaGetLastError();
 }
 
@@ -235,6 +250,7 @@ static cudaError_t launch_type(const void* map, const TmaArgs& ta, int noise_mod
     switch (noise_mode) {
         case 0: return launch_mode<0, T>(map, ta, tile, s);
         case 1: return launch_mode<1, T>(map, ta, tile, s);
+        case 3: return launch_mode<3, T>(map, ta, tile, s);
         default: return launch_mode<2, T>(map, ta, tile, s);
     }
 }

@@ -19,6 +19,13 @@ struct TmaTile {
     static constexpr int RW = TX + 2, RH = TY + 2;                      // density tile + ring
     static constexpr int SMEM_BYTES = 2 * STAGE_BYTES + RW * RH * 4 + 2 * 8;
     static constexpr uint32_t TX_BYTES = Q * PLANE_BYTES;
+    // real-space correlated noise: h00, h10, h01, h11 (float2 each) of the tile's nodes and of
+    // the column left of it and the row below it, (TX + 1) x (TY + 1) nodes, after the mbarriers
+    static constexpr int HW = TX + 1;
+    static constexpr int HN = (TX + 1) * (TY + 1);
+    static constexpr int H_BYTES = 4 * HN * 8;
+    static constexpr int H_OFFSET = SMEM_BYTES;        // 16-byte aligned: RW, RH even
+    static_assert(H_OFFSET % 16 == 0, "H must be 16-byte aligned");
 };
 
 static __constant__ int kCYt[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -102,6 +109,45 @@ __device__ __forceinline__ void load9_ps(const T* S, int b, float f[Q]) {
     f[6] = Elem<T>::load(S[6 * PS + b + 1], 6);
     f[7] = Elem<T>::load(S[7 * PS + b + 1], 7);
     f[8] = Elem<T>::load(S[8 * PS + b - 1], 8);
+}
+
+// Real-space correlated noise of a tile (LB_NOISE_FULL_RS): the contributions h_d(q) of a
+// node q of the tile, or of the column left of it / row below it (local coordinates -1),
+// go to H[d][(ly + 1) * HW + lx + 1]; the (xi_4, xi_9) of a tile node are then
+// h00(r) + h10(r - e_x) + h01(r - e_y) + h11(r - e_x - e_y).
+template <int HW, typename Args>
+__device__ __forceinline__ void stencil_store(const Args& a, float2* H, int HN, int lx, int ly, uint32_t node) {
+    float h[8];
+    stencil_h(a, node, h);
+    const int q = (ly + 1) * HW + lx + 1;
+    H[q] = make_float2(h[0], h[1]);
+    H[HN + q] = make_float2(h[2], h[3]);
+    H[2 * HN + q] = make_float2(h[4], h[5]);
+    H[3 * HN + q] = make_float2(h[6], h[7]);
+}
+
+// the halo nodes of the tile at (x0, y0): j in [0, TY] -> column x0 - 1, rows y0 - 1 ..
+// y0 + TY - 1; j in (TY, TX + TY] -> row y0 - 1, columns x0 .. x0 + TX - 1 (periodic; nodes
+// past a ragged edge are skipped, no tile node reads them)
+template <int TX, int TY, int HW, typename Args>
+__device__ __forceinline__ void stencil_halo(const Args& a, float2* H, int HN, int x0, int y0, int nx, int ny,
+                                             int tid, int nthreads) {
+    for (int j = tid; j < TX + TY + 1; j += nthreads) {
+        int lx, ly;
+        if (j <= TY) { lx = -1; ly = j - 1; }
+        else { lx = j - (TY + 1); ly = -1; }
+        int gx = x0 + lx, gy = y0 + ly;
+        if (gx < 0) gx += nx;
+        if (gy < 0) gy += ny;
+        if (gx < nx && gy < ny) stencil_store<HW>(a, H, HN, lx, ly, (uint32_t)gy * (uint32_t)nx + (uint32_t)gx);
+    }
+}
+
+template <int HW>
+__device__ __forceinline__ float2 stencil_xi(const float2* H, int HN, int lx, int ly) {
+    const int q = (ly + 1) * HW + lx + 1;
+    const float2 a = H[q], b = H[HN + q - 1], c = H[2 * HN + q - HW], d = H[3 * HN + q - HW - 1];
+    return make_float2((a.x + b.x) + (c.x + d.x), (a.y + b.y) + (c.y + d.y));
 }
 
 }  // namespace lbf

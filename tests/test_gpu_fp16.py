@@ -30,7 +30,8 @@ def kernel(request, monkeypatch):
 
 
 @pytest.mark.parametrize("nx,ny,mode", [(64, 64, lbf.LB_NOISE_FULL), (33, 17, lbf.LB_NOISE_LW),
-                                        (100, 36, lbf.LB_NOISE_DIAG)])
+                                        (100, 36, lbf.LB_NOISE_DIAG), (100, 36, lbf.LB_NOISE_FULL_RS),
+                                        (64, 64, lbf.LB_NOISE_FULL_RS)])
 def test_fp16_follows_oracle_within_rounding(nx, ny, mode, kernel):
     # Each step rounds every stored g_i = df_i / w_i to FP16 (error <= 2^-11 |g_i|); the step
     # itself is a contraction on every non-conserved mode, so after N steps the population

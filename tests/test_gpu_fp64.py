@@ -11,7 +11,8 @@ from paper_1009_0254_gb300 import synth
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12       # FP64 on both sides: only the order of rounding differs
 
-MODES = {"off": lbf.LB_NOISE_OFF, "lw": lbf.LB_NOISE_LW, "full": lbf.LB_NOISE_FULL, "diag": lbf.LB_NOISE_DIAG}
+MODES = {"off": lbf.LB_NOISE_OFF, "lw": lbf.LB_NOISE_LW, "full": lbf.LB_NOISE_FULL, "diag": lbf.LB_NOISE_DIAG,
+         "rs": lbf.LB_NOISE_FULL_RS}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -40,7 +41,8 @@ def _pair(nx, ny, seed, rho0, cs2, params, mode, scale, factor=None):
 
 
 @pytest.mark.parametrize("nx,ny,mode", [(64, 32, "full"), (64, 32, "lw"), (33, 17, "lw"), (40, 24, "diag"),
-                                        (37, 5, "off"), (2, 2, "lw"), (16, 128, "full"), (8, 2, "full")])
+                                        (37, 5, "off"), (2, 2, "lw"), (16, 128, "full"), (8, 2, "full"),
+                                        (64, 32, "rs"), (33, 17, "rs"), (2, 2, "rs"), (70, 9, "rs")])
 def test_fp64_follows_oracle_to_rounding(nx, ny, mode):
     g, o = _pair(nx, ny, 5, 1.0, 1 / 3, (2e-4, 0.02, 0.8, 1.1, 0.9), MODES[mode], 0.01)
     g.step(100)
@@ -49,7 +51,7 @@ def test_fp64_follows_oracle_to_rounding(nx, ny, mode):
     assert err <= TOL64, err
 
 
-@pytest.mark.parametrize("mode", ["full", "lw"])
+@pytest.mark.parametrize("mode", ["full", "lw", "rs"])
 def test_fp64_nonideal_and_eigen_factor(mode):
     g, o = _pair(64, 32, 9, 0.9, 0.265 ** 2, (1e-5, 0.08, 1.0, 1.1, 0.9), MODES[mode], 0.005, factor="eigen")
     g.step(80)
@@ -93,3 +95,14 @@ def test_fp64_moments_spectra_and_limits():
     with pytest.raises(lbf.LBError) as e:
         big.set_params(1e-4, 0.01, 1.0, 1.0, 1.0, lbf.LB_NOISE_FULL)
     assert e.value.code == lbf.LB_EINVAL
+
+
+def test_fp64_config1_1000_steps_real_space_correlated_noise():
+    # the first configuration with the correlated noise built in real space (the same
+    # covariance Xi(k) as the k-space construction)
+    g, o = _pair(64, 64, 42, 1.0, 1 / 3, (1e-4, 0.01, 1.0, 1.0, 1.0), lbf.LB_NOISE_FULL_RS, 0.0)
+    g.step(1000)
+    o.step(1000)
+    err = np.abs(g.populations() - o.f).max()
+    print("FP64 config 1 (real-space correlated noise), 1000 steps: max |f - f_oracle| = %.3e" % err)
+    assert err <= 10 * TOL64

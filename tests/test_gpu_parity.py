@@ -12,7 +12,8 @@ from paper_1009_0254_gb300 import synth
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
-MODES = {"off": lbf.LB_NOISE_OFF, "lw": lbf.LB_NOISE_LW, "full": lbf.LB_NOISE_FULL, "diag": lbf.LB_NOISE_DIAG}
+MODES = {"off": lbf.LB_NOISE_OFF, "lw": lbf.LB_NOISE_LW, "full": lbf.LB_NOISE_FULL, "diag": lbf.LB_NOISE_DIAG,
+         "rs": lbf.LB_NOISE_FULL_RS}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -49,7 +50,7 @@ def kernel(request, monkeypatch):
     return request.param
 
 
-@pytest.mark.parametrize("mode", ["full", "lw", "diag", "off"])
+@pytest.mark.parametrize("mode", ["full", "lw", "diag", "off", "rs"])
 def test_parity_64x64_config1(mode, kernel):
     # 64^2, rho0 = 1, kappa = 0.01, tau = 1, kT = 1e-4, cs2 = 1/3, seed 42, start at rest
     scale = 0.01 if mode == "off" else 0.0
@@ -66,7 +67,8 @@ def test_parity_64x64_config1(mode, kernel):
 @pytest.mark.parametrize("nx,ny,mode", [(6, 10, "lw"), (33, 17, "lw"), (100, 36, "diag"), (2, 2, "lw"),
                                         (37, 5, "off"), (64, 32, "full"), (16, 128, "full"), (2, 8, "full"),
                                         (300, 20, "lw"), (129, 9, "diag"), (256, 8, "full"), (512, 2, "full"),
-                                        (1024, 4, "full")])
+                                        (1024, 4, "full"), (6, 10, "rs"), (33, 17, "rs"), (2, 2, "rs"),
+                                        (100, 36, "rs"), (129, 9, "rs"), (1024, 4, "rs"), (3, 70, "rs")])
 def test_parity_ragged_and_small_lattices(nx, ny, mode, kernel):
     g, o = _pair(nx, ny, 7, 1.0, 1 / 3, (2e-4, 0.02, 0.8, 1.0, 1.0), MODES[mode], 0.01)
     g.step(60)
@@ -76,7 +78,8 @@ def test_parity_ragged_and_small_lattices(nx, ny, mode, kernel):
 
 
 @pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
-@pytest.mark.parametrize("nx,ny,mode", [(100, 36, "lw"), (70, 50, "off"), (128, 64, "full")])
+@pytest.mark.parametrize("nx,ny,mode", [(100, 36, "lw"), (70, 50, "off"), (128, 64, "full"), (100, 36, "rs"),
+                                        (130, 70, "rs")])
 def test_parity_every_tile_shape(tile, nx, ny, mode, monkeypatch):
     # each TMA tile shape (32x16, 32x32, 64x8, 64x16, 32x16 on 128 threads) on ragged edges
     monkeypatch.setenv("LBFLUCT_STEP_KERNEL", "tma")
@@ -94,7 +97,7 @@ def test_parity_across_noise_mode_changes(monkeypatch):
     monkeypatch.delenv("LBFLUCT_TMA_TILE", raising=False)
     params = (2e-4, 0.02, 0.8, 1.0, 1.0)
     g, o = _pair(128, 64, 13, 1.0, 1 / 3, params, MODES["lw"], 0.01)
-    for mode in ["lw", "full", "off", "lw", "diag", "full"]:
+    for mode in ["lw", "full", "off", "rs", "lw", "diag", "full", "rs"]:
         g.set_params(*params, MODES[mode])
         o.set_params(*params, MODES[mode])
         g.step(15)
@@ -102,7 +105,7 @@ def test_parity_across_noise_mode_changes(monkeypatch):
         assert np.abs(g.populations() - o.f).max() <= TOL, mode
 
 
-@pytest.mark.parametrize("mode", ["lw", "full"])
+@pytest.mark.parametrize("mode", ["lw", "full", "rs"])
 def test_parity_nonideal_sound_speed(mode, kernel):
     # cs != sigma_s: rest populations differ from w_i rho0 and Xi_49(0) != 0
     g, o = _pair(32, 32, 9, 0.9, 0.265 ** 2, (1e-5, 0.08, 1.0, 1.1, 0.9), MODES[mode], 0.005)
@@ -137,7 +140,7 @@ def test_full_size_sampled_parity_and_conservation(kernel):
     del pert
     nodes = synth.sample_nodes(nx, ny, 2000, seed=6)
     g = lbf.Lattice(nx, ny, seed=42)
-    for mode in ["lw", "full"]:
+    for mode in ["lw", "full", "rs"]:
         g.set_params(*params, MODES[mode])
         g.set_populations(f0, t=123)
         s0 = g.sums()
@@ -152,7 +155,7 @@ def test_full_size_sampled_parity_and_conservation(kernel):
         assert np.all(np.abs(s1[1:] - s0[1:]) < 1e-7 * nx * ny)
 
 
-@pytest.mark.parametrize("mode", ["full", "lw"])
+@pytest.mark.parametrize("mode", ["full", "lw", "rs"])
 def test_parity_64x64_config1_1000_steps(mode):
     # the same configuration over its full 1000 steps (default step kernel): the FP32
     # path stays within the population bar of the FP64 oracle, and both conserve mass
@@ -172,7 +175,7 @@ def test_parity_64x64_config1_1000_steps(mode):
 
 
 @pytest.mark.parametrize("mode,cs2,kappa", [("lw", 0.15 ** 2, 0.03), ("lw", 1 / 3, 0.01), ("full", 1 / 3, 0.03),
-                                           ("diag", 0.25 ** 2, 0.02)])
+                                           ("diag", 0.25 ** 2, 0.02), ("rs", 0.265 ** 2, 0.08), ("rs", 1 / 3, 0.03)])
 def test_parity_eigen_noise_factor(mode, cs2, kappa):
     # Sec. IV: the eigen-decomposition factor of the noise matrix instead of Cholesky
     params = (1e-4, kappa, 1.0, 1.1, 0.9)

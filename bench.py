@@ -78,6 +78,9 @@ def parse():
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--batched-only", action="store_true",
                    help="run only the batched-ensemble variant and print its JSON (profiling runs)")
+    p.add_argument("--serve-study", action="store_true",
+                   help="run only the serving comparison on traces of 500 requests at 5/s and 2/s "
+                        "(served engine and measured plain path) and print its JSON (several minutes)")
     p.add_argument("--noise", default="lw", choices=["lw", "full", "rs"],
                    help="noise of the main line (full: correlated via k-space, rs: correlated built in real "
                         "space, both at kappa=0.05; for profiling runs)")
@@ -324,7 +327,7 @@ def batched_variant(lbf, torch, steps=2000, graph_steps=100, plain_steps=20):
     ens = lbf.Ensemble(sizes, seeds)
     for r in range(len(sizes)):
         ens.set_params(r, float(kT[r]), 0.01, 0.8, 1.0, 1.0, lbf.LB_NOISE_LW)
-    ens.autotune(5)
+    ens.autotune(20)
     ens.set_sampling(100, 64)
     ens.step(2 * graph_steps, graph_steps=graph_steps)        # warm-up, graph captured
     torch.cuda.synchronize()
@@ -348,6 +351,16 @@ def batched_variant(lbf, torch, steps=2000, graph_steps=100, plain_steps=20):
     ev1.record(ens.stream)
     torch.cuda.synchronize()
     fms = ev0.elapsed_time(ev1)
+    # and with the correlated noise built in real space (no per-class synthesis launches)
+    for r in range(len(sizes)):
+        ens.set_params(r, float(kT[r]), 0.01, 0.8, 1.0, 1.0, lbf.LB_NOISE_FULL_RS)
+    ens.step(graph_steps, graph_steps=graph_steps)
+    torch.cuda.synchronize()
+    ev0.record(ens.stream)
+    ens.step(fsteps, graph_steps=graph_steps)
+    ev1.record(ens.stream)
+    torch.cuda.synchronize()
+    rms = ev0.elapsed_time(ev1)
     ens.close()
     del ens
     # plain path: the same lattices as separate contexts, one step launch per lattice
@@ -379,6 +392,10 @@ def batched_variant(lbf, torch, steps=2000, graph_steps=100, plain_steps=20):
             "correlated_noise": {"value": nodes * fsteps / (fms / 1e3) / 1e6, "unit": "MLUPS",
                                  "ms_per_step": fms / fsteps, "steps": fsteps,
                                  "how": "same replicas with full FDT noise (k-space synthesis per replica)"},
+            "correlated_noise_real_space": {"value": nodes * fsteps / (rms / 1e3) / 1e6, "unit": "MLUPS",
+                                            "ms_per_step": rms / fsteps, "steps": fsteps,
+                                            "how": "same replicas with full FDT noise built in real space "
+                                                   "(2x2 stencil in the step kernel)"},
             "plain_path": {"value": plain, "unit": "MLUPS", "steps": plain_steps,
                            "how": "512 lb_step calls per step, one context per lattice"},
             "speedup_vs_plain": value / plain,
@@ -419,16 +436,54 @@ def _serve_stream(lbf, stream, budget, chunk):
     return lat, st
 
 
-def _fifo_model(stream, per_step):
-    """Latencies of a server that runs one request at a time through lb_step, from the
-    measured per-step time of each lattice size."""
-    arrive, side, steps = stream[0], stream[1], stream[2]
-    service = np.array([steps[k] * per_step[int(side[k])] for k in range(len(arrive))])
-    done, free_at = np.zeros(len(arrive)), 0.0
+def _plain_server(lbf, torch, stream):
+    """The plain path as a server: the same trace replayed on one host thread, each request
+    run alone through lb_step in arrival order (FIFO) on a context of its size, completion =
+    when the host sees its last step finish.  Returns latencies and the aggregate MLUPS
+    (node updates / (last completion - first start))."""
+    arrive, side, steps, kT, kap, ts = stream
+    lat = np.zeros(len(arrive))
+    updates = 0.0
+    t0 = time.perf_counter()
+    first = None
     for k in range(len(arrive)):
-        free_at = max(free_at, arrive[k]) + service[k]
-        done[k] = free_at
-    return done - arrive, float(np.sum(side.astype(float) ** 2 * steps)) / service.sum() / 1e6
+        now = time.perf_counter() - t0
+        if arrive[k] > now:
+            time.sleep(arrive[k] - now)
+        L = int(side[k])
+        start = time.perf_counter() - t0
+        first = start if first is None else first
+        lat_ = lbf.Lattice(L, L, seed=1000 + k)      # at rest, time 0 (as a served request)
+        lat_.set_params(float(kT[k]), float(kap[k]), float(ts[k]), 1.0, 1.0, lbf.LB_NOISE_LW)
+        lat_.step(int(steps[k]))
+        torch.cuda.synchronize()
+        done = time.perf_counter() - t0
+        lat_.close()
+        lat[k] = done - arrive[k]
+        updates += float(L) * L * int(steps[k])
+    wall = (time.perf_counter() - t0) - first
+    return lat, updates / wall / 1e6, wall
+
+
+def serve_compare(lbf, torch, r, n, seed, budget=120 * 10 ** 9, chunk=200):
+    """One trace of n requests at r/s through the server and through the plain FIFO path."""
+    stream = _request_stream(r, n, seed)
+    lat, st = _serve_stream(lbf, stream, budget, chunk)
+    wall = st.t_last_complete - st.t_first_admit
+    plat, pmlups, pwall = _plain_server(lbf, torch, stream)
+    offered = float(np.sum(stream[1].astype(float) ** 2 * stream[2])) / max(stream[0][-1], 1e-9) / 1e6
+    return {"rate_per_s": r, "requests": n, "completed": int(st.completed),
+            "value": st.node_updates / wall / 1e6, "unit": "MLUPS (aggregate, first admission to last completion)",
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "offered_mlups_during_arrivals": offered, "node_updates": st.node_updates, "wall_s": wall,
+            "gpu_busy_s": st.gpu_busy_s, "hbm_peak_gb": st.bytes_peak / 1e9,
+            "plain_path": {"value": pmlups, "unit": "MLUPS (aggregate, first start to last completion)",
+                           "wall_s": pwall,
+                           "latency_s": {"p50": float(np.percentile(plat, 50)),
+                                         "p99": float(np.percentile(plat, 99)), "max": float(plat.max())},
+                           "how": "measured: the same trace replayed one request at a time through "
+                                  "lb_step (FIFO, host clock)"}}
 
 
 def served_variant(lbf, torch, n_requests=64, rate=200.0, budget=120 * 10 ** 9, chunk=200,
@@ -438,45 +493,16 @@ def served_variant(lbf, torch, n_requests=64, rate=200.0, budget=120 * 10 ** 9, 
     [5e-5, 2e-4], kappa in [0.005, 0.05], tau_s in [0.6, 1.5], FP32, admitted under an HBM
     budget; latency = completion - submission on the host clock.  At 200/s the offered
     load is ~20x what one GPU sustains, so the sample is a finite trace that drains; the
-    sweep repeats it at sustainable rates."""
-    # plain path: each size alone through lb_step, measured once
-    per_step = {}
-    for L in (64, 128, 256, 512, 1024):
-        lat_ = lbf.Lattice(L, L, seed=7)
-        lat_.set_params(1e-4, 0.01, 0.8, 1.0, 1.0, lbf.LB_NOISE_LW)
-        lat_.step(10)
-        torch.cuda.synchronize()
-        k = 400
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(lat_.stream)
-        lat_.step(k)
-        e1.record(lat_.stream)
-        torch.cuda.synchronize()
-        per_step[L] = e0.elapsed_time(e1) / 1e3 / k
-        lat_.close()
+    sweep repeats it at sustainable rates.  The plain path is measured on the same trace:
+    one request at a time through lb_step, in arrival order."""
 
     def one(r, n, seed):
-        stream = _request_stream(r, n, seed)
-        lat, st = _serve_stream(lbf, stream, budget, chunk)
-        wall = st.t_last_complete - st.t_first_admit
-        plat, pmlups = _fifo_model(stream, per_step)
-        offered = float(np.sum(stream[1].astype(float) ** 2 * stream[2])) / max(stream[0][-1], 1e-9) / 1e6
-        return {"rate_per_s": r, "requests": n, "completed": int(st.completed),
-                "value": st.node_updates / wall / 1e6, "unit": "MLUPS (aggregate, first admission to last completion)",
-                "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                              "max": float(lat.max())},
-                "offered_mlups_during_arrivals": offered, "node_updates": st.node_updates, "wall_s": wall,
-                "gpu_busy_s": st.gpu_busy_s, "hbm_peak_gb": st.bytes_peak / 1e9,
-                "plain_path": {"value": pmlups, "unit": "MLUPS",
-                               "latency_s_modelled": {"p50": float(np.percentile(plat, 50)),
-                                                      "p99": float(np.percentile(plat, 99))}}}
+        return serve_compare(lbf, torch, r, n, seed, budget, chunk)
 
     line = one(rate, n_requests, 11)
     line["workload"] = ("served: Poisson arrivals at %.0f/s (sample of %d requests), L in {64..1024}^2, steps "
                         "log-uniform in [1e3, 1e5], kT in [5e-5, 2e-4], kappa in [0.005, 0.05], tau_s in [0.6, 1.5], "
                         "FP32, HBM budget %.0f GB" % (rate, n_requests, budget / 1e9))
-    line["plain_path"]["how"] = ("measured lb_step time per step for each size; FIFO one-at-a-time server "
-                                 "modelled from those service times")
     line["rate_sweep"] = [one(r, n, 12 + i) for i, (r, n) in enumerate(sweep)]
     line["accuracy"] = ("each served result is bitwise the same alone and in the mix (tests/test_gpu_serve.py); "
                         "served lattices vs FP64 oracle <= 1e-5")
@@ -510,6 +536,11 @@ def main():
     lbf.load()
     if args.batched_only:
         print(json.dumps(batched_variant(lbf, torch)))
+        return 0
+    if args.serve_study:
+        print(json.dumps({"workload": "served request stream (config 5 mix) at sustainable rates, 500 requests "
+                                      "per trace; served engine against the plain path measured on the same trace",
+                          "rates": [serve_compare(lbf, torch, 5.0, 500, 31), serve_compare(lbf, torch, 2.0, 500, 32)]}))
         return 0
 
     n = args.n

@@ -67,6 +67,18 @@ extern "C" {
                               a^dx b^dy (a, b = +-1), give xi_4, xi_9 with exactly that covariance
                               (no transform; any lattice size).  Needs Xi positive semidefinite
                               at s = 0 and s = 16/3.  Modes 5..8 as LB_NOISE_LW. */
+#define LB_NOISE_LW_LOCAL 5 /* spatially uncorrelated with Xi(0) evaluated at each node's own
+                              density rho(r) and sound speed c_s^2(rho(r)) (Sec. IV: the
+                              uncorrelated noise applies to inhomogeneous systems with the local
+                              values; Sec. V B): Cholesky of the local (4,9) block, a negative
+                              pivot (a node in the spinodal region of an interface, where the
+                              local block is not positive semidefinite) clamped to zero; same
+                              draws as LB_NOISE_LW, identical to it at uniform density. */
+
+/* equations of state, [GACV] Sec. II A (lb_set_eos) */
+#define LB_EOS_LINEAR 0       /* p0 = cs2 rho (the linearised equation of state; default) */
+#define LB_EOS_DOUBLE_WELL 1  /* Landau double well f0 = beta (rho - rhoV)^2 (rho - rhoL)^2,
+                                 Eq. (f0-bulk): p0 = rho df0/drho - f0, c_s^2 = rho d2f0/drho2 */
 
 /* factorisation of the noise matrix, [GACV] Sec. IV (xi = L nu with L L^T = Xi) */
 #define LB_FACTOR_CHOLESKY 0   /* Cholesky of the lower-right block (default) */
@@ -119,6 +131,22 @@ int lb_set_stream(lb_ctx* ctx, void* stream);
  */
 int lb_set_params(lb_ctx* ctx, double kT, double kappa, double tau_s, double tau_b,
                   double tau_ghost, int noise_mode);
+
+/*
+ * Equation of state, [GACV] Sec. II A.  eos = LB_EOS_LINEAR restores p0 = cs2 rho with the
+ * cs2 of lb_create; eos = LB_EOS_DOUBLE_WELL takes p0 = rho df0/drho - f0 of the Landau
+ * double well f0 = beta (rho - rhoV)^2 (rho - rhoL)^2 (beta > 0, 0 <= rhoV < rhoL) in the
+ * Table II equilibrium at every node.  The uniform rest state becomes the equilibrium at rho0
+ * with p0(rho0); the linear theory about rho0 that sets the noise of the LW, DIAG, FULL and
+ * FULL_RS modes takes c_s^2 = rho0 d2f0/drho2 (rho0) (it must be > 0 for those modes), and
+ * LB_NOISE_LW_LOCAL takes c_s^2(rho(r)) at every node.  The populations are kept (their
+ * stored deviations are re-based on the new rest state); the parameters of the last
+ * lb_set_params are re-applied.  A double-well lattice is stepped by the plain step kernel
+ * (the TMA-staged kernels are built for the linear equation of state).  LB_EINVAL for bad
+ * arguments; FP16 and FP32 storage keep deviations from the rest state, so large density
+ * contrasts lose more to rounding in FP16.
+ */
+int lb_set_eos(lb_ctx* ctx, int eos, double beta, double rhoV, double rhoL);
 
 /*
  * lb_set_noise_factor: how the noise matrix is factored, [GACV] Sec. IV: LB_FACTOR_CHOLESKY
@@ -252,8 +280,9 @@ int lb_conserved_sums_static(const double* f, int nx, int ny, double* sums, void
  * lb_batch_set_params: lb_set_params for replica `replica`, or for every replica when
  *   replica == -1; the same validation (lb_check_params), LB_EINVAL for LB_NOISE_FULL on
  *   a lattice whose sides are not powers of two.
- * lb_batch_autotune: times every tile shape of the batched step kernel on each size
- *   class over `steps` launches and keeps the fastest, then puts every replica back at
+ * lb_batch_autotune: times every tile shape of the batched step kernel on the whole
+ *   ensemble (three runs of `steps` steps each, the fastest run counts) and keeps the
+ *   fastest shape, then puts every replica back at
  *   rest at time 0 (populations set before are lost).  Needs parameters for every
  *   replica; synchronises the stream.
  * lb_batch_step: advances every replica by nsteps (asynchronous, one kernel per size

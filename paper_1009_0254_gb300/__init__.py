@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbfluct.so")
 LB_OK, LB_EINVAL, LB_ENOTPSD, LB_ENOMEM, LB_ECUDA, LB_ETIMEOUT, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 LB_ENONFINITE, LB_ECANCELED = -7, -8
 LB_FP32, LB_FP16DEV, LB_FP64 = 0, 1, 2
-LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL, LB_NOISE_DIAG, LB_NOISE_FULL_RS = 0, 1, 2, 3, 4
+LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL, LB_NOISE_DIAG, LB_NOISE_FULL_RS, LB_NOISE_LW_LOCAL = 0, 1, 2, 3, 4, 5
+LB_EOS_LINEAR, LB_EOS_DOUBLE_WELL = 0, 1
 LB_FACTOR_CHOLESKY, LB_FACTOR_EIGEN = 0, 1
 LB_HOST, LB_DEVICE = 0, 1
 LB_WARN_LOW_MACH = 1
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
         "lb_set_params": (c_int, [vp, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_int]),
         "lb_step": (c_int, [vp, c_i64]),
         "lb_set_noise_factor": (c_int, [vp, c_int]),
+        "lb_set_eos": (c_int, [vp, c_int, c_dbl, c_dbl, c_dbl]),
         "lb_get_time": (c_int, [vp, i64p]),
         "lb_set_populations": (c_int, [vp, vp, c_int, c_i64]),
         "lb_get_populations": (c_int, [vp, vp, c_int]),
@@ -181,6 +183,10 @@ def lb_set_stream(ctx, stream):
 
 def lb_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
     return _check(load().lb_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode), ctx)
+
+
+def lb_set_eos(ctx, eos, beta=0.0, rhoV=0.0, rhoL=0.0):
+    return _check(load().lb_set_eos(ctx, eos, float(beta), float(rhoV), float(rhoL)), ctx)
 
 
 def lb_set_noise_factor(ctx, factor):
@@ -466,6 +472,9 @@ class Lattice:
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
         lb_set_params(self.ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
+
+    def set_eos(self, eos, beta=0.0, rhoV=0.0, rhoL=0.0):
+        lb_set_eos(self.ctx, eos, beta, rhoV, rhoL)
 
     def set_noise_factor(self, factor):
         lb_set_noise_factor(self.ctx, factor)

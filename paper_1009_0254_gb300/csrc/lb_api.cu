@@ -154,9 +154,12 @@ int validate(int nx, int ny, double rho0, double cs2, double kT, double kappa, d
     if (!(tau_s > 0.5) || !(tau_b > 0.5) || !(tau_g > 0.5)) return bad("every relaxation time must exceed 1/2");
     if (!(kT >= 0.0) || !std::isfinite(kT)) return bad("kT must be finite and >= 0");
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return bad("kappa must be finite and >= 0");
-    if (mode < LB_NOISE_OFF || mode > LB_NOISE_FULL_RS) return bad("unknown noise mode");
-    if (!(rho0 > 0.0) || !(cs2 > 0.0)) return bad("rho0 and cs2 must be positive");
-    if (mode == LB_NOISE_OFF || kT == 0.0) return LB_OK;
+    if (mode < LB_NOISE_OFF || mode > LB_NOISE_LW_LOCAL) return bad("unknown noise mode");
+    if (!(rho0 > 0.0)) return bad("rho0 must be positive");
+    // the local-density noise factors Xi(0) per node (negative pivots clamped): no
+    // homogeneous state to check
+    if (mode == LB_NOISE_OFF || kT == 0.0 || mode == LB_NOISE_LW_LOCAL) return LB_OK;
+    if (!(cs2 > 0.0)) return bad("the sound speed squared of the state about rho0 must be positive");
     const NoiseCoef c = noise_coef(rho0, cs2, 1.0, kappa, tau_s, tau_b, tau_g);
     if (mode == LB_NOISE_FULL) {
         // every wavevector of the lattice; cos is even, so the quarter grid suffices
@@ -218,6 +221,14 @@ struct lb_ctx {
     // parameters
     bool have_params = false;
     int noise_mode = LB_NOISE_OFF, warnings = 0;
+    // equation of state (lb_set_eos): cs2 above is the sound speed squared of the linear
+    // theory about rho0 (the lb_create argument for the linear EOS, c_s^2(rho0) for a double
+    // well), p0_rest the bulk pressure of the rest state
+    int eos = LB_EOS_LINEAR;
+    double cs2_linear = 1.0 / 3.0, p0_rest = 1.0 / 3.0;
+    double eos_beta = 0, eos_rhoV = 0, eos_rhoL = 0;
+    double eos_poly[5] = {0, 0, 0, 0, 0};   // p0(rho0 + d) = sum_j eos_poly[j] d^j
+    double eos_cq[4] = {0, 0, 0, 0};        // c_s^2(rho0 + d) = sum_j eos_cq[j] d^j
     int factor = LB_FACTOR_CHOLESKY;
     double kT = 0, kappa = 0, tau_s = 1, tau_b = 1, tau_g = 1;
     StepArgs sa{};
@@ -320,6 +331,10 @@ int lb_create(int nx, int ny, int precision, uint64_t seed, double rho0, double 
     c->nx = nx; c->ny = ny; c->n = (long long)nx * ny; c->precision = precision;
     c->fp16 = precision == LB_FP16DEV ? 1 : 0;
     c->seed = seed; c->rho0 = rho0; c->cs2 = cs2; c->g = g; c->L = make_layout(g, es);
+    c->cs2_linear = cs2;
+    c->p0_rest = cs2 * rho0;
+    c->eos_poly[0] = cs2 * rho0; c->eos_poly[1] = cs2;
+    c->eos_cq[0] = cs2;
     c->pow2 = is_pow2(nx) && is_pow2(ny);
     cudaGetDevice(&c->device);
     if (workspace) {
@@ -508,12 +523,85 @@ int lb_set_params(lb_ctx* c, double kT, double kappa, double tau_s, double tau_b
     d.s7 = std::sqrt(std::fmax(nc.x77, 0.0));
     for (int j = 0; j < 3; ++j)
         for (int q = 0; q < 4; ++q) d.sL[j][q] = sL[j][q];
+    // noise at the local density and sound speed: Xi(0) entries per unit density as affine
+    // functions of c_s^2 (noise_coef at rho0 = 1 and cs2 = 0, 1), and c_s^2 as a function of
+    // the density deviation
+    {
+        const NoiseCoef n0 = noise_coef(1.0, 0.0, kT, kappa, tau_s, tau_b, tau_ghost);
+        const NoiseCoef n1 = noise_coef(1.0, 1.0, kT, kappa, tau_s, tau_b, tau_ghost);
+        const double lu[9] = {n0.a44, n1.a44 - n0.a44, n0.a49, n1.a49 - n0.a49, n0.a99, n1.a99 - n0.a99,
+                              std::sqrt(std::fmax(n0.x55, 0.0)), std::sqrt(std::fmax(n0.x66, 0.0)),
+                              std::sqrt(std::fmax(n0.x77, 0.0))};
+        for (int q = 0; q < 9; ++q) { a.lu[q] = (float)lu[q]; d.lu[q] = lu[q]; }
+        for (int q = 0; q < 4; ++q) { a.cq[q] = (float)c->eos_cq[q]; d.cq[q] = c->eos_cq[q]; }
+    }
     NoiseGenArgsD& gd = c->gad;
     gd.a44 = nc.a44; gd.b44 = nc.b44; gd.a49 = nc.a49; gd.b49 = nc.b49; gd.a99 = nc.a99; gd.b99 = nc.b99;
     gd.cosx = c->cosxd; gd.cosy = c->cosyd; gd.nx = c->nx; gd.ny = c->ny;
     gd.eig = ga.eig;
     gd.rk = a.rk;
     c->have_params = true;
+    return LB_OK;
+}
+
+int lb_set_eos(lb_ctx* c, int eos, double beta, double rhoV, double rhoL) {
+    if (!c) return LB_EINVAL;
+    if (eos != LB_EOS_LINEAR && eos != LB_EOS_DOUBLE_WELL) return fail(c, LB_EINVAL, "unknown equation of state");
+    const double r0 = c->rho0;
+    double poly[5] = {0, 0, 0, 0, 0}, cq[4] = {0, 0, 0, 0};
+    if (eos == LB_EOS_DOUBLE_WELL) {
+        if (!(beta > 0.0) || !std::isfinite(beta) || !(rhoV >= 0.0) || !(rhoL > rhoV) || !std::isfinite(rhoL))
+            return fail(c, LB_EINVAL, "the double well needs beta > 0 and 0 <= rhoV < rhoL");
+        // f0(rho0 + d) = beta (A + d)^2 (B + d)^2 = beta (c0 + c1 d + d^2)^2, A = rho0 - rhoV,
+        // B = rho0 - rhoL; p0 = rho df0/drho - f0 and c_s^2 = rho d2f0/drho2 as polynomials in d
+        const double A = r0 - rhoV, B = r0 - rhoL, c0 = A * B, c1 = A + B;
+        const double f[5] = {c0 * c0, 2 * c0 * c1, c1 * c1 + 2 * c0, 2 * c1, 1.0};   // f0 / beta
+        double df[4], d2f[3];
+        for (int j = 0; j < 4; ++j) df[j] = (j + 1) * f[j + 1];
+        for (int j = 0; j < 3; ++j) d2f[j] = (j + 1) * df[j + 1];
+        for (int j = 0; j < 5; ++j) {
+            // (rho0 + d) df - f
+            const double v = (j < 4 ? r0 * df[j] : 0.0) + (j >= 1 ? df[j - 1] : 0.0) - f[j];
+            poly[j] = beta * v;
+        }
+        for (int j = 0; j < 4; ++j) cq[j] = beta * ((j < 3 ? r0 * d2f[j] : 0.0) + (j >= 1 ? d2f[j - 1] : 0.0));
+    } else {
+        poly[0] = c->cs2_linear * r0;
+        poly[1] = c->cs2_linear;
+        cq[0] = c->cs2_linear;
+    }
+    DeviceGuard dg(c->device);
+    // the state in FP64 with the old rest populations, back with the new ones
+    double fb_new[Q];
+    rest_populations(r0, poly[0] / r0, fb_new);
+    double* stage = (double*)c->z1;
+    for (int i = 0; i < Q; ++i) {
+        CK(c, launch_get_plane(c->pop[c->cur], c->precision, c->g, i, c->fbar[i], stage, c->stream), "get plane");
+        CK(c, launch_set_plane(stage, c->pop[c->cur], c->precision, c->g, i, fb_new[i], c->stream), "set plane");
+        c->kernels += 2;
+    }
+    CK(c, cudaMemcpyAsync(c->fbar_dev, fb_new, sizeof(double) * Q, cudaMemcpyHostToDevice, c->stream), "H2D");
+    CK(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    for (int i = 0; i < Q; ++i) c->fbar[i] = fb_new[i];
+    c->eos = eos;
+    c->eos_beta = beta; c->eos_rhoV = rhoV; c->eos_rhoL = rhoL;
+    for (int j = 0; j < 5; ++j) c->eos_poly[j] = poly[j];
+    for (int j = 0; j < 4; ++j) c->eos_cq[j] = cq[j];
+    c->p0_rest = poly[0];
+    c->cs2 = poly[1];                        // c_s^2 of the linear theory about rho0
+    c->sa.cs2m = (float)(poly[1] - SIGMA_S2);
+    c->sad.cs2m = poly[1] - SIGMA_S2;
+    c->sa.eos = c->sad.eos = eos == LB_EOS_DOUBLE_WELL ? 1 : 0;
+    c->sa.e2 = (float)poly[2]; c->sa.e3 = (float)poly[3]; c->sa.e4 = (float)poly[4];
+    c->sad.e2 = poly[2]; c->sad.e3 = poly[3]; c->sad.e4 = poly[4];
+    for (int q = 0; q < 4; ++q) { c->sa.cq[q] = (float)cq[q]; c->sad.cq[q] = cq[q]; }
+    if (c->have_params) {
+        const int r = lb_set_params(c, c->kT, c->kappa, c->tau_s, c->tau_b, c->tau_g, c->noise_mode);
+        if (r != LB_OK) {
+            c->have_params = false;       // the old noise factors belong to the old equation of state
+            return r;
+        }
+    }
     return LB_OK;
 }
 
@@ -557,8 +645,10 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
     DeviceGuard dg(c->device);
     const bool noisy = c->noise_mode != LB_NOISE_OFF && c->kT > 0.0;
     // kernel noise mode: 0 none, 1 uncorrelated, 2 correlated (k-space field), 3 correlated
-    // built in real space
-    const int kmode = !noisy ? 0 : (c->noise_mode == LB_NOISE_FULL ? 2 : (c->noise_mode == LB_NOISE_FULL_RS ? 3 : 1));
+    // built in real space, 4 uncorrelated at the local density
+    const int kmode = !noisy ? 0
+                      : (c->noise_mode == LB_NOISE_FULL ? 2
+                         : (c->noise_mode == LB_NOISE_FULL_RS ? 3 : (c->noise_mode == LB_NOISE_LW_LOCAL ? 4 : 1)));
     if (kmode == 2 && !c->pow2)
         return fail(c, LB_EINVAL, "correlated noise needs nx and ny powers of two (radix-2 FFT)");
     for (int64_t k = 0; k < nsteps; ++k) {
@@ -618,9 +708,12 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
             if (r != LB_OK) return r;
             CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
         }
-        if (c->use_sweep && kmode != 3)      // the sweep kernel has no real-space correlated noise
+        // the double-well equation of state runs on the plain kernel; the sweep kernel has
+        // the noise modes 0..2 only
+        const bool poly = c->eos == LB_EOS_DOUBLE_WELL;
+        if (c->use_sweep && kmode < 3 && !poly)
             CK(c, launch_step_sweep(a, kmode, c->fp16, c->sweep_occ6, c->stream), "step kernel launch");
-        else if (c->use_tma) {
+        else if (c->use_tma && !poly) {
             const int want = c->tma_tile_fixed >= 0 ? c->tma_tile_fixed : tma_default_tile(kmode, c->fp16);
             if (want != c->tma_tile) {
                 // tensor maps are host-encoded descriptors passed by value: re-encode for the shape

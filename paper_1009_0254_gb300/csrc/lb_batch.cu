@@ -49,6 +49,7 @@ struct EnsParams {
     unsigned int* done;                // CTAs finished in this launch (advancing launch only)
     int* err;                          // set when a bounded wait gives up
     int advance;                       // this launch advances K when its last CTA finishes
+    int rs;                            // some replica of the launch has real-space correlated noise
 };
 
 // class, replica and origin of a tile of the launch
@@ -73,8 +74,10 @@ __device__ __forceinline__ TilePos locate(const EnsParams& p, int tile) {
     return t;
 }
 
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant__ EnsParams p) {
+// RS: the variant that also steps replicas with real-space correlated noise (its extra path
+// raises the register count, so launches without such replicas use the lean variant)
+template <int TX, int TY, int NT, bool RS>
+__global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_ensemble_kernel(const __grid_constant__ EnsParams p) {
     using TT = TmaTile<TX, TY, float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
         if (tid == 0) {
             const RepRec* rp = p.cls[tp.c].recs + tp.rep;
             sargs = load_tile_args(rp, K + __ldg(&rp->toff), &smode);
+            if (RS && smode == 3) load_stencil_args(rp, &sargs);
         }
 
         // pulled populations stay in registers across the density barrier; the stage is
@@ -144,13 +148,25 @@ __global__ void __launch_bounds__(NT) step_ensemble_kernel(const __grid_constant
         float fr[TX * TY / NT][Q];
         tile_pull<TX, TY, NT>(S, R, fr);
         __syncthreads();
-        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+        if (tid == 0 && !(RS && smode == 3) && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(tile + 2 * gridDim.x, s);
         }
         const int mode = smode;
         float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
-        if (mode == 2)
+        if (RS && mode == 3) {
+            // real-space correlated noise: the contributions go to the consumed stage s, whose
+            // refill waits for the collision (the mode is the tile's: uniform over the CTA)
+            float2* Hs = reinterpret_cast<float2*>(smem_raw + s * TT::STAGE_BYTES);
+            tile_stencil<TX, TY, NT>(sargs, Hs, g, tp.x0, tp.y0);
+            __syncthreads();
+            tile_nodes<3, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr, Hs);
+            __syncthreads();
+            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(tile + 2 * gridDim.x, s);
+            }
+        } else if (mode == 2)
             tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, d.xi + (long long)tp.rep * g.nx * g.ny);
         else if (mode)
             tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr);
@@ -339,20 +355,22 @@ static bool make_class_map(void* buf, const Grid& g, int R, int tile, CUtensorMa
 }
 
 // CTAs of a persistent launch: every SM filled to the occupancy the kernel allows
-template <int TX, int TY, int NT>
+template <int TX, int TY, int NT, bool RS>
 static cudaError_t ensemble_grid(int* grid) {
     using TT = TmaTile<TX, TY, float>;
     static GridCache cache;
-    return resident_grid(step_ensemble_kernel<TX, TY, NT>, NT, TT::SMEM_BYTES, cache, grid);
+    return resident_grid(step_ensemble_kernel<TX, TY, NT, RS>, NT, TT::SMEM_BYTES, cache, grid);
 }
 
 template <int TX, int TY, int NT>
 static cudaError_t launch_ensemble_t(const EnsParams& p, cudaStream_t s) {
     using TT = TmaTile<TX, TY, float>;
     int grid = 0;
-    cudaError_t e = ensemble_grid<TX, TY, NT>(&grid);
+    cudaError_t e = p.rs ? ensemble_grid<TX, TY, NT, true>(&grid) : ensemble_grid<TX, TY, NT, false>(&grid);
     if (e != cudaSuccess) return e;
-    step_ensemble_kernel<TX, TY, NT><<<std::max(1, std::min(p.ntiles, grid)), NT, TT::SMEM_BYTES, s>>>(p);
+    const int blocks = std::max(1, std::min(p.ntiles, grid));
+    if (p.rs) step_ensemble_kernel<TX, TY, NT, true><<<blocks, NT, TT::SMEM_BYTES, s>>>(p);
+    else step_ensemble_kernel<TX, TY, NT, false><<<blocks, NT, TT::SMEM_BYTES, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -372,13 +390,17 @@ static cudaError_t launch_ensemble(int tile, const EnsParams& p, cudaStream_t s)
 static cudaError_t prepare_ensemble_kernels() {
     int g = 0;
     cudaError_t e;
-    if ((e = ensemble_grid<32, 16, 256>(&g)) != cudaSuccess) return e;
-    if ((e = ensemble_grid<32, 16, 128>(&g)) != cudaSuccess) return e;
-    if ((e = ensemble_grid<32, 8, 256>(&g)) != cudaSuccess) return e;
-    if ((e = ensemble_grid<32, 8, 128>(&g)) != cudaSuccess) return e;
-    if ((e = ensemble_grid<64, 8, 256>(&g)) != cudaSuccess) return e;
-    if ((e = ensemble_grid<64, 16, 512>(&g)) != cudaSuccess) return e;
-    return ensemble_grid<32, 32, 512>(&g);
+    for (int rs = 0; rs < 2; ++rs) {
+        const bool R = rs != 0;
+        if ((e = R ? ensemble_grid<32, 16, 256, true>(&g) : ensemble_grid<32, 16, 256, false>(&g)) != cudaSuccess) return e;
+        if ((e = R ? ensemble_grid<32, 16, 128, true>(&g) : ensemble_grid<32, 16, 128, false>(&g)) != cudaSuccess) return e;
+        if ((e = R ? ensemble_grid<32, 8, 256, true>(&g) : ensemble_grid<32, 8, 256, false>(&g)) != cudaSuccess) return e;
+        if ((e = R ? ensemble_grid<32, 8, 128, true>(&g) : ensemble_grid<32, 8, 128, false>(&g)) != cudaSuccess) return e;
+        if ((e = R ? ensemble_grid<64, 8, 256, true>(&g) : ensemble_grid<64, 8, 256, false>(&g)) != cudaSuccess) return e;
+        if ((e = R ? ensemble_grid<64, 16, 512, true>(&g) : ensemble_grid<64, 16, 512, false>(&g)) != cudaSuccess) return e;
+        if ((e = R ? ensemble_grid<32, 32, 512, true>(&g) : ensemble_grid<32, 32, 512, false>(&g)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Relaxation rates, Cholesky factors of Xi(0) (Sec. IV; the (4,9) block coupled unless
@@ -405,7 +427,19 @@ void fill_rep_record(double rho0, double cs2, double kT, double kappa, double ta
     rec->a44 = (float)co[0]; rec->b44 = (float)co[1];
     rec->a49 = (float)co[2]; rec->b49 = (float)co[3];
     rec->a99 = (float)co[4]; rec->b99 = (float)co[5];
-    rec->mode = (noise_mode == LB_NOISE_OFF || kT <= 0.0) ? 0 : (noise_mode == LB_NOISE_FULL ? 2 : 1);
+    // real-space correlated noise: Cholesky factors of the (4,9) block at k^2 = 0, 4, 16/3, / 4
+    const double sk[3] = {0.0, 4.0, 16.0 / 3.0};
+    for (int j = 0; j < 3; ++j) {
+        const double y44 = co[0] + co[1] * sk[j], y49 = co[2] + co[3] * sk[j], y99 = co[4] + co[5] * sk[j];
+        const double l11 = std::sqrt(std::fmax(y44, 0.0));
+        const double l21 = l11 > 0.0 ? y49 / l11 : 0.0;
+        const double l22 = std::sqrt(std::fmax(y99 - l21 * l21, 0.0));
+        rec->sL[j][0] = (float)(0.25 * l11); rec->sL[j][1] = 0.0f;
+        rec->sL[j][2] = (float)(0.25 * l21); rec->sL[j][3] = (float)(0.25 * l22);
+    }
+    rec->mode = (noise_mode == LB_NOISE_OFF || kT <= 0.0)
+                    ? 0
+                    : (noise_mode == LB_NOISE_FULL ? 2 : (noise_mode == LB_NOISE_FULL_RS ? 3 : 1));
 }
 
 }  // namespace lbf
@@ -435,7 +469,8 @@ struct ClassInfo {
     std::vector<int> members;          // replica ids, in class order
     size_t off_buf[2], off_z1, off_z2, off_tw_x, off_tw_y, off_bin16, off_bins, off_counts, off_recs;
     size_t off_cosx, off_cosy;         // cos(2 pi m / n) tables of the correlated noise
-    bool any_full = false;             // some replica of the class has correlated noise
+    bool any_full = false;             // some replica of the class has correlated noise (k-space)
+    bool any_rs = false;               // some replica of the class has correlated noise (real space)
 };
 
 struct Layout {
@@ -580,6 +615,7 @@ static int build_launches(lb_batch* b, int tile, std::vector<EnsParams>* out) {
             if (tiles + more > (1ll << 30)) return bfail(b, LB_EINVAL, "too many tiles in one launch");
             tiles += (int)more;
             p.nclass = j + 1;
+            p.rs = p.rs || ci.any_rs;
         }
         p.ntiles = tiles;
         p.kstep = reinterpret_cast<long long*>(cls_ptr(b, b->L.off_k));
@@ -811,6 +847,8 @@ int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, doubl
     if (!b || replica < -1 || replica >= b->count) return LB_EINVAL;
     DeviceGuard dg(b->device);
     const int lo = replica < 0 ? 0 : replica, hi = replica < 0 ? b->count : replica + 1;
+    if (noise_mode == LB_NOISE_LW_LOCAL)
+        return bfail(b, LB_EINVAL, "the batched engine steps homogeneous noise modes only (not LB_NOISE_LW_LOCAL)");
     for (int r = lo; r < hi; ++r) {
         const ClassInfo& ci = b->L.classes[b->L.cls_of[r]];
         if (noise_mode == LB_NOISE_FULL &&
@@ -826,13 +864,24 @@ int lb_batch_set_params(lb_batch* b, int replica, double kT, double kappa, doubl
         int u = upload_rec(b, r);
         if (u != LB_OK) return u;
     }
-    // classes that now need (or no longer need) the correlated-noise kernels
-    bool changed = false;
+    // classes that now need (or no longer need) the correlated-noise kernels, or the step
+    // kernel variant with real-space correlated noise
+    bool changed = false, changed_rs = false;
     for (auto& ci : b->L.classes) {
-        bool any = false;
-        for (int r : ci.members) any = any || b->recs[r].mode == 2;
+        bool any = false, any_rs = false;
+        for (int r : ci.members) {
+            any = any || b->recs[r].mode == 2;
+            any_rs = any_rs || b->recs[r].mode == 3;
+        }
         changed = changed || any != ci.any_full;
+        changed_rs = changed_rs || any_rs != ci.any_rs;
         ci.any_full = any;
+        ci.any_rs = any_rs;
+    }
+    if (changed_rs) {
+        int rc = build_launches(b, b->tile, &b->launches);
+        if (rc != LB_OK) return rc;
+        changed = true;
     }
     if (changed && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
     BCK(b, cudaStreamSynchronize(b->stream), "cudaStreamSynchronize");
@@ -860,15 +909,19 @@ int lb_batch_autotune(lb_batch* b, int steps) {
         if (rc != LB_OK) return rc;
         for (auto& p : cand) p.advance = 0;
         for (const auto& p : cand) BCK(b, launch_ensemble(t, p, b->stream), "autotune");   // warm-up
-        BCK(b, cudaEventRecord(ev.a, b->stream), "event");
-        for (int k = 0; k < steps; ++k)
-            for (const auto& p : cand) BCK(b, launch_ensemble(t, p, b->stream), "autotune");
-        BCK(b, cudaEventRecord(ev.b, b->stream), "event");
-        BCK(b, cudaEventSynchronize(ev.b), "event");
-        b->kernels += (long long)(steps + 1) * (long long)cand.size();
-        float ms = 0.f;
-        BCK(b, cudaEventElapsedTime(&ms, ev.a, ev.b), "event");
-        if (ms < best) { best = ms; best_tile = t; }
+        // the fastest of three timed runs of `steps` steps (a single short run is at the
+        // mercy of clock ramps and of whatever else the device is finishing)
+        for (int rep = 0; rep < 3; ++rep) {
+            BCK(b, cudaEventRecord(ev.a, b->stream), "event");
+            for (int k = 0; k < steps; ++k)
+                for (const auto& p : cand) BCK(b, launch_ensemble(t, p, b->stream), "autotune");
+            BCK(b, cudaEventRecord(ev.b, b->stream), "event");
+            BCK(b, cudaEventSynchronize(ev.b), "event");
+            float ms = 0.f;
+            BCK(b, cudaEventElapsedTime(&ms, ev.a, ev.b), "event");
+            if (ms < best) { best = ms; best_tile = t; }
+        }
+        b->kernels += (long long)(3 * steps + 1) * (long long)cand.size();
     }
     b->tile = best_tile;
     int rc = build_launches(b, best_tile, &b->launches);

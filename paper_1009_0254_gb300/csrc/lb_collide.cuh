@@ -23,12 +23,15 @@ struct NbrT {
 };
 using Nbr = NbrT<float>;
 
-// MODE 0: no noise; 1: uncorrelated (long-wavelength or diagonal); 2: correlated
-// (xi_4, xi_9 given in xi49).  A carries the relaxation and noise factors, the time and
-// the Philox key (StepArgs with precomputed round keys, or a per-replica record): Args.
-// R is the arithmetic type (float, or double for FP64 storage); every constant is an
-// exact rational or rounded in R.
-template <int MODE, typename Args, typename R, typename X2>
+// MODE 0: no noise; 1: uncorrelated (long-wavelength or diagonal); 2 and 3: correlated
+// (xi_4, xi_9 given in xi49: from the k-space synthesis, or built in real space);
+// 4: uncorrelated with Xi(0) at the node's own density and sound speed.  A carries the
+// relaxation and noise factors, the time and the Philox key (StepArgs with precomputed
+// round keys, or a per-replica record): Args.  R is the arithmetic type (float, or double
+// for FP64 storage); every constant is an exact rational or rounded in R.
+// POLY: the bulk pressure is the double well's quartic in drho (Args carries e2..e4);
+// otherwise p0 = cs2 rho and no polynomial code is compiled.
+template <int MODE, bool POLY = false, typename Args, typename R, typename X2>
 __device__ __forceinline__ void collide_node(const Args& a, const R f[Q], const NbrT<R>& r, uint32_t node,
                                              X2 xi49, R o[Q]) {
     const R c6 = R(1) / R(6), c3 = R(1) / R(3), c12 = R(1) / R(12);
@@ -53,11 +56,14 @@ __device__ __forceinline__ void collide_node(const Args& a, const R f[Q], const 
     const R m8 = R(2) * dy - ay;
     const R m9 = R(2) * f[0] - R(4) * sa + R(8) * sd;
 
-    // equilibrium deviations, Table II (p0 = cs2 rho, C_n = 0)
+    // equilibrium deviations, Table II (C_n = 0): p0 - sigma_s^2 rho relative to the rest
+    // state, linear (p0 = cs2 rho) or the double well's quartic in drho (Sec. II A)
     const R rho = a.rho0 + drho;
     const R inv = recip(rho);
     const R ux = jx * inv, uy = jy * inv;
-    const R iso = a.cs2m * drho - a.kappa * rho * lap;
+    R dp = a.cs2m;
+    if constexpr (POLY) dp += drho * (a.e2 + drho * (a.e3 + drho * a.e4));
+    const R iso = dp * drho - a.kappa * rho * lap;
     const R e_eq = R(3) * (jx * ux + jy * uy) + R(6) * iso;
     const R pww_eq = (jx * ux - jy * uy) + a.kappa * (gx * gx - gy * gy);
     const R pxy_eq = jx * uy + a.kappa * gx * gy;
@@ -71,16 +77,37 @@ __device__ __forceinline__ void collide_node(const Args& a, const R f[Q], const 
         R n5, n6, n7, n8;
         gauss_word(r0.x, &n5, &n6);
         gauss_word(r0.y, &n7, &n8);
-        xi5 = a.s5 * n5;
-        xi6 = a.s6 * n6;
-        xi7 = a.s7 * n7;
-        xi8 = a.s7 * n8;
+        if constexpr (MODE == 4) {
+            // Xi(0) of Eq. (noise-yeo) at this node's density and sound speed (Sec. IV for
+            // inhomogeneous systems), Cholesky of the (4,9) block with negative pivots at 0
+            const R c = a.cq[0] + drho * (a.cq[1] + drho * (a.cq[2] + drho * a.cq[3]));
+            const R y44 = rho * (a.lu[0] + a.lu[1] * c);
+            const R y49 = rho * (a.lu[2] + a.lu[3] * c);
+            const R y99 = rho * (a.lu[4] + a.lu[5] * c);
+            const R sr = sqrt_fast(fmax(rho, R(0)));
+            xi5 = sr * a.lu[6] * n5;
+            xi6 = sr * a.lu[7] * n6;
+            xi7 = sr * a.lu[8] * n7;
+            xi8 = sr * a.lu[8] * n8;
+            const R L44 = sqrt_fast(fmax(y44, R(0)));
+            const R L94 = L44 > R(0) ? y49 * recip(L44) : R(0);
+            const R L99 = sqrt_fast(fmax(y99 - L94 * L94, R(0)));
+            R n4, n9;
+            gauss_word(r0.z, &n4, &n9);
+            xi4 = L44 * n4;
+            xi9 = L94 * n4 + L99 * n9;
+        } else {
+            xi5 = a.s5 * n5;
+            xi6 = a.s6 * n6;
+            xi7 = a.s7 * n7;
+            xi8 = a.s7 * n8;
+        }
         if (MODE == 1) {
             R n4, n9;
             gauss_word(r0.z, &n4, &n9);
             xi4 = a.L44 * n4 + a.L49 * n9;
             xi9 = a.L94 * n4 + a.L99 * n9;
-        } else {
+        } else if (MODE == 2 || MODE == 3) {
             xi4 = xi49.x;
             xi9 = xi49.y;
         }

@@ -14,21 +14,25 @@ struct RepRec {
     float rho0, cs2m, kappa, lb, ls, lq, le;
     float L44, L49, L94, L99, s5, s6, s7;
     float a44, b44, a49, b49, a99, b99;   // Xi(k) of the (4,9) block = a + b s(k) (correlated noise)
-    int mode;                 // 0 no noise, 1 uncorrelated noise, 2 correlated noise
+    float sL[3][4];           // real-space correlated noise: factors / 4 of Xi at k^2 = 0, 4, 16/3
+    int mode;                 // 0 no noise, 1 uncorrelated, 2 correlated (k-space), 3 correlated (real space)
     uint32_t k0, k1;          // Philox key = the replica's seed
     long long toff;           // time = K + toff
 };
 
-// What collide_node needs for one tile of one replica, in registers.
+// What collide_node needs for one tile of one replica, in registers (the engines step the
+// linearised equation of state).
 struct TileArgs {
     float rho0, cs2m, kappa, lb, ls, lq, le;
     float L44, L49, L94, L99, s5, s6, s7;
+    float sL[3][4];
     uint32_t t_lo, t_hi;
     KeyPair rk;
 };
 
 // The record of one lattice as collide_node reads it, for its time t; *mode = 0 without
-// noise, 1 with uncorrelated noise, 2 with correlated noise (xi_4, xi_9 read from a field).
+// noise, 1 with uncorrelated noise, 2 with correlated noise (xi_4, xi_9 read from a field),
+// 3 with correlated noise built in real space.
 __device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t, int* mode) {
     TileArgs a;
     a.rho0 = __ldg(&rp->rho0); a.cs2m = __ldg(&rp->cs2m); a.kappa = __ldg(&rp->kappa);
@@ -40,6 +44,15 @@ __device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t
     a.t_hi = (uint32_t)((unsigned long long)t >> 32);
     *mode = __ldg(&rp->mode);
     return a;
+}
+
+// The real-space correlated-noise factors of a record (only for its lattices with that
+// mode: the record load sits on the tile's critical path).
+__device__ __forceinline__ void load_stencil_args(const RepRec* rp, TileArgs* a) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a->sL[j][q] = __ldg(&rp->sL[j][q]);
 }
 
 // Pulls the nine deviations of this thread's nodes of the staged tile S into registers
@@ -75,7 +88,7 @@ __device__ __forceinline__ void tile_pull(const float* S, float* R, float (&fr)[
 template <int MODE, int TX, int TY, int NT>
 __device__ __forceinline__ void tile_nodes(const TileArgs& a, const float (&fr)[TX * TY / NT][Q], const float* R,
                                            const Grid& g, int x0, int y0, float* dst,
-                                           const float2* __restrict__ xi49) {
+                                           const float2* __restrict__ xi49, const float2* Hs = nullptr) {
     using TT = TmaTile<TX, TY, float>;
 #pragma unroll
     for (int it = 0; it < TX * TY / NT; ++it) {
@@ -93,10 +106,29 @@ __device__ __forceinline__ void tile_nodes(const TileArgs& a, const float (&fr)[
         const uint32_t node = (uint32_t)y * (uint32_t)g.nx + (uint32_t)x;
         float2 z = make_float2(0.f, 0.f);
         if (MODE == 2) z = xi49[(long long)y * g.nx + x];
+        if (MODE == 3) z = stencil_xi<TT::HW>(Hs, TT::HN, lx, ly);
         float o[Q];
         collide_node<MODE>(a, fr[it], r, node, z, o);
         store9(dst, g.plane, g, x, y, o);
     }
+}
+
+// Real-space correlated noise of a staged tile whose lattice uses it: the 2 x 2-box
+// contributions of the tile's nodes and of its halo, written into the memory of the stage
+// just consumed (FP32 stages hold them; the caller refills that stage after the collision).
+template <int TX, int TY, int NT>
+__device__ __forceinline__ void tile_stencil(const TileArgs& a, float2* Hs, const Grid& g, int x0, int y0) {
+    using TT = TmaTile<TX, TY, float>;
+    static_assert(TT::H_IN_STAGE, "the noise contributions must fit in a stage");
+#pragma unroll 1
+    for (int it = 0; it < TX * TY / NT; ++it) {
+        const int q = threadIdx.x + it * NT;
+        const int ly = q / TX, lx = q - ly * TX;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x < g.nx && y < g.ny)
+            stencil_store<TT::HW>(a, Hs, TT::HN, lx, ly, (uint32_t)y * (uint32_t)g.nx + (uint32_t)x);
+    }
+    stencil_halo<TX, TY, TT::HW>(a, Hs, TT::HN, x0, y0, g.nx, g.ny, threadIdx.x, NT);
 }
 
 // host: fills the parameter fields of a record (defined in lb_batch.cu)

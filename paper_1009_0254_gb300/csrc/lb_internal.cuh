@@ -112,6 +112,12 @@ struct StepArgsT {
     R s5, s6, s7;                    // sqrt(Xi_55), sqrt(Xi_66), sqrt(Xi_77) = sqrt(Xi_88)
     R sL[3][4];                      // real-space correlated noise: factors (L44, L49, L94, L99) / 4
                                      // of the (4,9) block of Xi at lattice k^2 = 0, 4, 16/3
+    int eos;                         // 0: p0 = cs2 rho; 1: polynomial (double-well) bulk pressure,
+                                     // stepped by the plain kernel (lb_step.cu)
+    R e2, e3, e4;                    // p0(rho0 + d) - p0(rho0) = d (cs2m + sigma_s^2) + d^2 (e2 + d (e3 + d e4))
+    R cq[4];                         // local c_s^2(rho0 + d) = cq0 + d (cq1 + d (cq2 + d cq3))
+    R lu[9];                         // local Xi(0): x44 = rho (lu0 + lu1 c), x49 = rho (lu2 + lu3 c),
+                                     // x99 = rho (lu4 + lu5 c); lu6..8 = sqrt(x55, x66, x77 / rho)
     uint32_t t_lo, t_hi;
     RoundKeys rk;
 };

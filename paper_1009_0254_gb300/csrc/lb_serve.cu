@@ -68,8 +68,10 @@ __device__ __forceinline__ int find_owner(const int* __restrict__ tile_begin, in
     return lo;
 }
 
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
+// RS: the variant that also steps simulations with real-space correlated noise (launched
+// for chunks that hold one; its extra path raises the register count)
+template <int TX, int TY, int NT, bool RS>
+__global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_serve_kernel(const ServeParams p) {
     using TT = TmaTile<TX, TY, float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
@@ -144,19 +146,34 @@ __global__ void __launch_bounds__(NT) step_serve_kernel(const ServeParams p) {
         const float* S = smem + s * TT::STAGE;
         // the slot's record, to shared memory (its last readers, the previous tile's
         // collision, are past the barrier above)
-        if (tid == 0) sargs = load_tile_args(p.recs + slot, sl, &smode);
+        if (tid == 0) {
+            sargs = load_tile_args(p.recs + slot, sl, &smode);
+            if (RS && smode == 3) load_stencil_args(p.recs + slot, &sargs);
+        }
 
         // pulled populations stay in registers across the density barrier; the stage is
         // refilled right after it (slot, x0, y0 are in registers by then)
         float fr[TX * TY / NT][Q];
         tile_pull<TX, TY, NT>(S, R, fr);
         __syncthreads();
-        if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+        const int mode = smode;
+        if (tid == 0 && !(RS && mode == 3) && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(tile + 2 * gridDim.x, s);
         }
-        const int mode = smode;
-        if (mode == 2) tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, d->xi);
+        if (RS && mode == 3) {
+            // real-space correlated noise: contributions in the consumed stage s, refilled
+            // after the collision (the mode is the tile's: uniform over the CTA)
+            float2* Hs = reinterpret_cast<float2*>(smem_raw + s * TT::STAGE_BYTES);
+            tile_stencil<TX, TY, NT>(sargs, Hs, g, x0, y0);
+            __syncthreads();
+            tile_nodes<3, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr, Hs);
+            __syncthreads();
+            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(tile + 2 * gridDim.x, s);
+            }
+        } else if (mode == 2) tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, d->xi);
         else if (mode) tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
         else tile_nodes<0, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
     }
@@ -316,7 +333,7 @@ struct SizeTables {                  // FFT twiddles and cosines of one lattice 
 struct lb_server {
     int device = 0;
     size_t budget = 0, in_use = 0, peak = 0;
-    int max_slots = 0, max_chunk = 0, grid = 0;
+    int max_slots = 0, max_chunk = 0, grid = 0, grid_rs = 0;
     cudaStream_t stream = nullptr;
     cudaMemPool_t pool = nullptr;
     // device tables
@@ -696,7 +713,9 @@ bool issue_chunk(lb_server* s) {
     p.done = s->d_done;
     p.err = s->d_err;
     using TT = TmaTile<SV_TX, SV_TY, float>;
-    const int grid = std::max(1, std::min(tiles, s->grid));
+    bool rs = false;
+    for (const Running& r : s->running) rs = rs || (r.r.noise_mode == LB_NOISE_FULL_RS && r.r.kT > 0.0);
+    const int grid = std::max(1, std::min(tiles, rs ? s->grid_rs : s->grid));
     SCK(s, cudaEventRecord(s->ev_begin[c], s->stream));
     for (long long k = 0; k < G; ++k) {
         for (const Group& gr : groups) {
@@ -709,7 +728,8 @@ bool issue_chunk(lb_server* s) {
                 s->d_full[c] + gr.off, s->d_desc, gr.nx, gr.ny, tb2.twx,
                 (float)(1.0 / std::sqrt((double)gr.nx * gr.ny)));
         }
-        step_serve_kernel<SV_TX, SV_TY, SV_NT><<<grid, SV_NT, TT::SMEM_BYTES, s->stream>>>(p);
+        if (rs) step_serve_kernel<SV_TX, SV_TY, SV_NT, true><<<grid, SV_NT, TT::SMEM_BYTES, s->stream>>>(p);
+        else step_serve_kernel<SV_TX, SV_TY, SV_NT, false><<<grid, SV_NT, TT::SMEM_BYTES, s->stream>>>(p);
     }
     SCK(s, cudaGetLastError());
     s->K += G;
@@ -852,14 +872,21 @@ int lb_server_create(size_t hbm_budget_bytes, int max_active, int max_chunk_step
     if ((e = cudaMemset(s->d_done, 0, sizeof(unsigned int))) != cudaSuccess) return fail_create(e);
     if ((e = cudaMemset(s->d_err, 0, sizeof(int))) != cudaSuccess) return fail_create(e);
     using TT = TmaTile<SV_TX, SV_TY, float>;
-    auto kern = step_serve_kernel<SV_TX, SV_TY, SV_NT>;
+    auto kern = step_serve_kernel<SV_TX, SV_TY, SV_NT, false>;
+    auto kern_rs = step_serve_kernel<SV_TX, SV_TY, SV_NT, true>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES)) != cudaSuccess)
         return fail_create(e);
-    int sms = 0, per = 0;
+    if ((e = cudaFuncSetAttribute(kern_rs, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM_BYTES)) !=
+        cudaSuccess)
+        return fail_create(e);
+    int sms = 0, per = 0, per_rs = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SV_NT, TT::SMEM_BYTES)) != cudaSuccess)
         return fail_create(e);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_rs, kern_rs, SV_NT, TT::SMEM_BYTES)) != cudaSuccess)
+        return fail_create(e);
     s->grid = sms * std::max(per, 1);
+    s->grid_rs = sms * std::max(per_rs, 1);
     if (!encode_fn_s()) {
         set_context_free_error("lb_server_create: cuTensorMapEncodeTiled is not available");
         lb_server_destroy(s);
@@ -879,6 +906,8 @@ int lb_server_submit(lb_server* s, const lb_request* r, int64_t* id) {
     if (r->noise_mode == LB_NOISE_FULL &&
         (!pow2s(r->nx) || !pow2s(r->ny) || r->ny > 8192 || noise_strip(r->nx, r->ny) < 2))
         return sfail(nullptr, LB_EINVAL, "correlated noise needs nx and ny powers of two and ny <= 8192");
+    if (r->noise_mode == LB_NOISE_LW_LOCAL)
+        return sfail(nullptr, LB_EINVAL, "served simulations use homogeneous noise modes only (not LB_NOISE_LW_LOCAL)");
     const int rc = lb_check_params(r->nx, r->ny, r->rho0, r->cs2, r->kT, r->kappa, r->tau_s, r->tau_b, r->tau_ghost,
                                    r->noise_mode);
     if (rc != LB_OK) return sfail(nullptr, rc, "parameters rejected (see lb_check_params)");

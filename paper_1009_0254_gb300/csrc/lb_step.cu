@@ -54,7 +54,7 @@ __device__ __forceinline__ void stencil_put(const Args& a, V* H, int HN, int lx,
     H[3 * HN + q].x = h[6]; H[3 * HN + q].y = h[7];
 }
 
-template <int BX, int BY, int MODE, typename T>
+template <int BX, int BY, int MODE, typename T, bool POLY>
 __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgsT<typename Arith<T>::type> a) {
     using TL = Tile<BX, BY>;
     using R = typename Arith<T>::type;
@@ -134,23 +134,31 @@ __global__ void __launch_bounds__(BX * BY) step_kernel(const StepArgsT<typename 
         z.y = (h00.y + h10.y) + (h01.y + h11.y);
     }
     R o[Q];
-    collide_node<MODE>(a, f, r, node, z, o);
+    collide_node<MODE, POLY>(a, f, r, node, z, o);
 
     // 9. store (own node plus periodic ghosts)
     store9(static_cast<T*>(a.dst), P, g, x, y, o);
 }
 
-template <typename T>
-static void launch_t(const StepArgsT<typename Arith<T>::type>& a, int noise_mode, cudaStream_t s) {
+template <typename T, bool POLY>
+static void launch_p(const StepArgsT<typename Arith<T>::type>& a, int noise_mode, cudaStream_t s) {
     constexpr int BX = 32, BY = 16;
     dim3 block(BX, BY);
     dim3 grid((a.g.nx + BX - 1) / BX, (a.g.ny + BY - 1) / BY);
     switch (noise_mode) {
-        case 0: step_kernel<BX, BY, 0, T><<<grid, block, 0, s>>>(a); break;
-        case 1: step_kernel<BX, BY, 1, T><<<grid, block, 0, s>>>(a); break;
-        case 3: step_kernel<BX, BY, 3, T><<<grid, block, 0, s>>>(a); break;
-        default: step_kernel<BX, BY, 2, T><<<grid, block, 0, s>>>(a); break;
+        case 0: step_kernel<BX, BY, 0, T, POLY><<<grid, block, 0, s>>>(a); break;
+        case 1: step_kernel<BX, BY, 1, T, POLY><<<grid, block, 0, s>>>(a); break;
+        case 3: step_kernel<BX, BY, 3, T, POLY><<<grid, block, 0, s>>>(a); break;
+        case 4: step_kernel<BX, BY, 4, T, POLY><<<grid, block, 0, s>>>(a); break;
+        default: step_kernel<BX, BY, 2, T, POLY><<<grid, block, 0, s>>>(a); break;
     }
+}
+
+// the double-well equation of state (a.eos) is a separate instantiation
+template <typename T>
+static void launch_t(const StepArgsT<typename Arith<T>::type>& a, int noise_mode, cudaStream_t s) {
+    if (a.eos) launch_p<T, true>(a, noise_mode, s);
+    else launch_p<T, false>(a, noise_mode, s);
 }
 
 cudaError_t launch_step_simple(const StepArgs& a, int noise_mode, int fp16, cudaStream_t s) {

@@ -46,7 +46,10 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
     const int tid = threadIdx.x;
     const int ntiles = ta.ntx * ta.nty;
     auto load9 = [](const T* S, int b, float f[Q]) { load9_ps<TT::PS>(S, b, f); };
-    float2* H = reinterpret_cast<float2*>(smem_raw + TT::H_OFFSET);   // MODE 3 only
+    // MODE 3: the 2 x 2-box noise contributions, after the mbarriers (kept apart from the
+    // stages: filling them into the consumed stage and refilling it after the collision
+    // measured slower, the two extra barriers costing more than the fourth CTA per SM gained)
+    float2* H = reinterpret_cast<float2*>(smem_raw + TT::H_OFFSET);
 
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
@@ -105,18 +108,19 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             load9(S, (ly + 1) * TT::BW + lx + TT::XO, fr[it]);
             R[(ly + 1) * TT::RW + lx + 1] = drho_of(fr[it]);
         }
-        if (MODE == 3) {
-            // real-space correlated noise: every node's contributions, then the halo's
+        // real-space correlated noise: every node's contributions, then the halo's
+        auto stencil_tile = [&](float2* Hd) {
 #pragma unroll 1
             for (int it = 0; it < NN; ++it) {
                 const int q = tid + it * NT;
                 const int ly = q / TX, lx = q - ly * TX;
                 const int x = x0 + lx, y = y0 + ly;
                 if (x < g.nx && y < g.ny)
-                    stencil_store<TT::HW>(a, H, TT::HN, lx, ly, (uint32_t)y * (uint32_t)g.nx + (uint32_t)x);
+                    stencil_store<TT::HW>(a, Hd, TT::HN, lx, ly, (uint32_t)y * (uint32_t)g.nx + (uint32_t)x);
             }
-            stencil_halo<TX, TY, TT::HW>(a, H, TT::HN, x0, y0, g.nx, g.ny, tid, NT);
-        }
+            stencil_halo<TX, TY, TT::HW>(a, Hd, TT::HN, x0, y0, g.nx, g.ny, tid, NT);
+        };
+        if (MODE == 3) stencil_tile(H);
         // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
         constexpr int NB = 2 * (TX + 2) + 2 * TY;
         for (int j = tid; j < NB; j += NT) {
@@ -192,8 +196,8 @@ int tma_tile_count() { return 5; }
 // (215 us), correlated 32x16 (246 us); FP16 off 32x16/128 (153 us), uncorrelated 32x32
 // (233 us), correlated 64x16 (245 us).
 int tma_default_tile(int noise_mode, int fp16) {
-    static const int best[2][4] = {{1, 3, 0, 0}, {4, 1, 3, 0}};
-    const int m = noise_mode < 0 ? 0 : (noise_mode > 3 ? 3 : noise_mode);
+    static const int best[2][5] = {{1, 3, 0, 0, 3}, {4, 1, 3, 0, 1}};
+    const int m = noise_mode < 0 ? 0 : (noise_mode > 4 ? 4 : noise_mode);
     return best[fp16 ? 1 : 0][m];
 }
 
@@ -251,6 +255,7 @@ static cudaError_t launch_type(const void* map, const TmaArgs& ta, int noise_mod
         case 0: return launch_mode<0, T>(map, ta, tile, s);
         case 1: return launch_mode<1, T>(map, ta, tile, s);
         case 3: return launch_mode<3, T>(map, ta, tile, s);
+        case 4: return launch_mode<4, T>(map, ta, tile, s);
         default: return launch_mode<2, T>(map, ta, tile, s);
     }
 }

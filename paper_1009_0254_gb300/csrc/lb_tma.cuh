@@ -26,6 +26,9 @@ struct TmaTile {
     static constexpr int H_BYTES = 4 * HN * 8;
     static constexpr int H_OFFSET = SMEM_BYTES;        // 16-byte aligned: RW, RH even
     static_assert(H_OFFSET % 16 == 0, "H must be 16-byte aligned");
+    // whether H fits in the memory of one stage (FP32 storage): the engines put it in the
+    // stage just consumed and refill that stage after the collision pass
+    static constexpr bool H_IN_STAGE = H_BYTES <= STAGE_BYTES;
 };
 
 static __constant__ int kCYt[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};

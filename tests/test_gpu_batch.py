@@ -223,3 +223,54 @@ def test_correlated_replica_alone_equals_in_mix_and_single_path():
     L.set_populations(_initial(*size, params, seed=seed), t=1)
     L.step(30)
     assert np.abs(L.populations() - mixed.populations(1)).max() <= 1e-6
+
+
+RS_MIX = [
+    ((32, 32), 51, (1.0e-4, 0.01, 1.0, 1.0, 1.0), lbf.LB_NOISE_FULL_RS),
+    ((33, 17), 52, (2.0e-4, 0.03, 0.8, 1.1, 0.9), lbf.LB_NOISE_FULL_RS),
+    ((32, 32), 53, (1.5e-4, 0.02, 0.7, 1.0, 1.2), lbf.LB_NOISE_LW),
+    ((100, 36), 54, (1.0e-4, 0.04, 1.0, 1.0, 1.0), lbf.LB_NOISE_FULL_RS),
+    ((2, 2), 55, (1.0e-4, 0.01, 1.0, 1.0, 1.0), lbf.LB_NOISE_FULL_RS),
+    ((64, 32), 56, (8.0e-5, 0.04, 0.9, 1.0, 1.0), lbf.LB_NOISE_FULL),
+]
+
+
+@pytest.mark.parametrize("tile", [0, 5, 6, 2])
+def test_real_space_correlated_replicas_match_oracle(tile, monkeypatch):
+    # correlated noise built in real space (LB_NOISE_FULL_RS) in a mix with the other modes,
+    # lattices of any size; several tile shapes of the batched kernel
+    monkeypatch.setenv("LBFLUCT_BATCH_TILE", str(tile))
+    ens = _ensemble(RS_MIX)
+    ens.step(11)
+    ens.step(39, graph_steps=13)
+    for r, (size, seed, params, mode) in enumerate(RS_MIX):
+        o = oracle.Lattice(*size, seed=seed)
+        o.set_params(*params, mode)
+        o.f = _initial(*size, params, seed=seed)
+        o.t = r
+        o.step(50)
+        err = np.abs(ens.populations(r) - o.f).max()
+        assert err <= TOL, (r, size, mode, err)
+
+
+def test_real_space_correlated_replica_alone_equals_in_mix_and_single_path():
+    mixed = _ensemble(RS_MIX)
+    mixed.step(30, graph_steps=10)
+    size, seed, params, mode = RS_MIX[3]
+    alone = _ensemble([RS_MIX[3]], t0=3)
+    alone.step(30, graph_steps=10)
+    assert np.array_equal(alone.populations(0), mixed.populations(3))
+    L = lbf.Lattice(*size, seed=seed)
+    L.set_params(*params, mode)
+    L.set_populations(_initial(*size, params, seed=seed), t=3)
+    L.step(30)
+    assert np.abs(L.populations() - mixed.populations(3)).max() <= 1e-6
+    # switching the mode off and on rebuilds the launches (lean step kernel without it)
+    for r in range(len(RS_MIX)):
+        mixed.set_params(r, *RS_MIX[r][2], lbf.LB_NOISE_LW)
+    mixed.step(5, graph_steps=5)
+    mixed.set_params(3, *params, mode)
+    mixed.step(5, graph_steps=5)
+    with pytest.raises(lbf.LBError) as e:
+        mixed.set_params(0, *RS_MIX[0][2], lbf.LB_NOISE_LW_LOCAL)
+    assert e.value.code == lbf.LB_EINVAL

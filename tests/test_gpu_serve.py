@@ -296,3 +296,41 @@ def test_device_wait_gives_up_and_context_survives():
     L.set_params(1e-4, 0.01, 1.0, 1.0, 1.0, lbf.LB_NOISE_LW)
     L.step(5)
     assert L.t == 5 and np.all(np.isfinite(L.populations()))
+
+
+@pytest.mark.parametrize("nx,ny", [(32, 32), (33, 17), (100, 36)])
+def test_served_real_space_correlated_noise_matches_oracle(nx, ny):
+    srv = lbf.Server(1 << 30, max_active=16, max_chunk_steps=29)
+    p = dict(kT=1.5e-4, kappa=0.03, tau_s=0.8, tau_b=1.1, tau_ghost=0.9, noise_mode=lbf.LB_NOISE_FULL_RS, seed=33)
+    i = srv.submit(nx, ny, 70, keep_state=True, **p)
+    res = srv.wait(i, timeout_s=60)
+    assert res.status == lbf.LB_OK
+    f = srv.fetch(i, nx, ny)
+    o = _oracle_run(nx, ny, 70, 33, 1.5e-4, 0.03, 0.8, 1.1, 0.9, lbf.LB_NOISE_FULL_RS)
+    assert np.abs(f - o.f).max() <= TOL
+    with pytest.raises(lbf.LBError):
+        srv.submit(nx, ny, 10, noise_mode=lbf.LB_NOISE_LW_LOCAL)
+    srv.close()
+
+
+def test_served_real_space_correlated_result_same_alone_and_in_the_mix():
+    X = dict(nx=60, ny=36, steps=150, kT=1e-4, kappa=0.02, tau_s=0.9, seed=77, noise_mode=lbf.LB_NOISE_FULL_RS)
+    alone = lbf.Server(1 << 30, max_active=8, max_chunk_steps=50)
+    ia = alone.submit(keep_state=True, **X)
+    alone.wait(ia, timeout_s=60)
+    fa = alone.fetch(ia, 60, 36)
+    alone.close()
+    rng = np.random.default_rng(9)
+    mix = lbf.Server(1 << 30, max_active=64, max_chunk_steps=17)
+    reqs = _random_requests(rng, 24)
+    for k, r in enumerate(reqs):
+        r["noise_mode"] = [lbf.LB_NOISE_FULL_RS, lbf.LB_NOISE_LW, lbf.LB_NOISE_FULL][k % 3]
+    for r in reqs[:12]:
+        mix.submit(**r)
+    ix = mix.submit(keep_state=True, **X)
+    for r in reqs[12:]:
+        mix.submit(**r)
+    mix.wait(0, timeout_s=120)
+    assert all(r.status == lbf.LB_OK for r in mix.poll())
+    assert np.array_equal(fa, mix.fetch(ix, 60, 36))
+    mix.close()

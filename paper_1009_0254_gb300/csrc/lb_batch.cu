@@ -77,13 +77,13 @@ __device__ __forceinline__ TilePos locate(const EnsParams& p, int tile) {
 // RS: the variant that also steps replicas with real-space correlated noise (its extra path
 // raises the register count, so launches without such replicas use the lean variant)
 template <int TX, int TY, int NT, bool RS>
-__global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_ensemble_kernel(const __grid_constant__ EnsParams p) {
+__global__ void __launch_bounds__(NT, RS ? 1024 / NT : 0) step_ensemble_kernel(const __grid_constant__ EnsParams p) {
     using TT = TmaTile<TX, TY, float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
     float* R = reinterpret_cast<float*>(smem_raw + 2 * TT::STAGE_BYTES);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(R + TT::RW * TT::RH);
-    __shared__ TileArgs sargs;          // the record of the current tile
+    __shared__ TileArgsOf<RS> sargs;    // the record of the current tile
     __shared__ int smode;
     const int tid = threadIdx.x;
     const long long K = __ldcg(p.kstep);
@@ -139,8 +139,10 @@ __global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_ensemble_kernel(c
         // registers, which the pulled populations need, and than loading it before the wait)
         if (tid == 0) {
             const RepRec* rp = p.cls[tp.c].recs + tp.rep;
-            sargs = load_tile_args(rp, K + __ldg(&rp->toff), &smode);
-            if (RS && smode == 3) load_stencil_args(rp, &sargs);
+            static_cast<TileArgs&>(sargs) = load_tile_args(rp, K + __ldg(&rp->toff), &smode);
+            if constexpr (RS) {
+                if (smode == 3) load_stencil_args(rp, &sargs);
+            }
         }
 
         // pulled populations stay in registers across the density barrier; the stage is
@@ -154,24 +156,32 @@ __global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_ensemble_kernel(c
         }
         const int mode = smode;
         float* dst = (par ? d.buf[0] : d.buf[1]) + (long long)tp.rep * d.rstride;
-        if (RS && mode == 3) {
-            // real-space correlated noise: the contributions go to the consumed stage s, whose
-            // refill waits for the collision (the mode is the tile's: uniform over the CTA)
-            float2* Hs = reinterpret_cast<float2*>(smem_raw + s * TT::STAGE_BYTES);
-            tile_stencil<TX, TY, NT>(sargs, Hs, g, tp.x0, tp.y0);
-            __syncthreads();
-            tile_nodes<3, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr, Hs);
-            __syncthreads();
-            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(tile + 2 * gridDim.x, s);
+        bool stepped = false;
+        if constexpr (RS) {
+            if (mode == 3) {
+                // real-space correlated noise: the contributions go to the consumed stage s,
+                // whose refill waits for the collision (the mode is the tile's: uniform over
+                // the CTA)
+                float2* Hs = reinterpret_cast<float2*>(smem_raw + s * TT::STAGE_BYTES);
+                tile_stencil<TX, TY, NT>(sargs, Hs, g, tp.x0, tp.y0);
+                __syncthreads();
+                tile_nodes<3, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr, Hs);
+                __syncthreads();
+                if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(tile + 2 * gridDim.x, s);
+                }
+                stepped = true;
             }
-        } else if (mode == 2)
-            tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, d.xi + (long long)tp.rep * g.nx * g.ny);
-        else if (mode)
-            tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr);
-        else
-            tile_nodes<0, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr);
+        }
+        if (!stepped) {
+            if (mode == 2)
+                tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, d.xi + (long long)tp.rep * g.nx * g.ny);
+            else if (mode)
+                tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr);
+            else
+                tile_nodes<0, TX, TY, NT>(sargs, fr, R, g, tp.x0, tp.y0, dst, nullptr);
+        }
     }
     // Every CTA read K before arriving here; the last one to arrive advances it for the
     // next step (the next launch sees it, kernel boundaries order the accesses).

@@ -29,9 +29,20 @@ using Nbr = NbrT<float>;
 // relaxation and noise factors, the time and the Philox key (StepArgs with precomputed
 // round keys, or a per-replica record): Args.  R is the arithmetic type (float, or double
 // for FP64 storage); every constant is an exact rational or rounded in R.
+// density deviation of scaled deviations g_i = (f_i - fbar_i) / w_i (the FP16 storage form)
+template <typename R>
+__device__ __forceinline__ R drho_of_g(const R g[Q]) {
+    const R sa = (g[1] + g[3]) + (g[2] + g[4]);
+    const R sd = (g[5] + g[7]) + (g[6] + g[8]);
+    return R(4) / R(9) * g[0] + (R(1) / R(9) * sa + R(1) / R(36) * sd);
+}
+
 // POLY: the bulk pressure is the double well's quartic in drho (Args carries e2..e4);
 // otherwise p0 = cs2 rho and no polynomial code is compiled.
-template <int MODE, bool POLY = false, typename Args, typename R, typename X2>
+// GF: f and o hold the scaled deviations g_i = (f_i - fbar_i) / w_i instead of f_i - fbar_i
+// (the weights move into the moment sums and out of the back-transform, so FP16 storage
+// needs no scaling on load or store).
+template <int MODE, bool POLY = false, bool GF = false, typename Args, typename R, typename X2>
 __device__ __forceinline__ void collide_node(const Args& a, const R f[Q], const NbrT<R>& r, uint32_t node,
                                              X2 xi49, R o[Q]) {
     const R c6 = R(1) / R(6), c3 = R(1) / R(3), c12 = R(1) / R(12);
@@ -41,20 +52,24 @@ __device__ __forceinline__ void collide_node(const Args& a, const R f[Q], const 
     const R gx = (r.E - r.W) * c3 + ((r.NE - r.SW) + (r.SE - r.NW)) * c12;
     const R gy = (r.N - r.S) * c3 + ((r.NE - r.SW) + (r.NW - r.SE)) * c12;
 
-    // moments of the deviations (rows of T, Eq. Tmat)
-    const R sa = (f[1] + f[3]) + (f[2] + f[4]);
-    const R sd = (f[5] + f[7]) + (f[6] + f[8]);
-    const R drho = f[0] + sa + sd;
-    const R ax = f[1] - f[3], ay = f[2] - f[4];
-    const R dx = (f[5] - f[7]) + (f[8] - f[6]);
-    const R dy = (f[5] - f[7]) + (f[6] - f[8]);
+    // moments of the deviations (rows of T, Eq. Tmat); with GF the sums over the axis and
+    // diagonal velocities carry their weights 1/9 and 1/36, the rest velocity 4/9
+    const R wa = GF ? R(1) / R(9) : R(1), wd = GF ? R(1) / R(36) : R(1), w0 = GF ? R(4) / R(9) : R(1);
+    const R sa0 = (f[1] + f[3]) + (f[2] + f[4]);
+    const R sd0 = (f[5] + f[7]) + (f[6] + f[8]);
+    const R sa = GF ? wa * sa0 : sa0, sd = GF ? wd * sd0 : sd0, g0 = GF ? w0 * f[0] : f[0];
+    const R drho = g0 + sa + sd;
+    const R ax = GF ? wa * (f[1] - f[3]) : f[1] - f[3], ay = GF ? wa * (f[2] - f[4]) : f[2] - f[4];
+    const R dx0 = (f[5] - f[7]) + (f[8] - f[6]);
+    const R dy0 = (f[5] - f[7]) + (f[6] - f[8]);
+    const R dx = GF ? wd * dx0 : dx0, dy = GF ? wd * dy0 : dy0;
     const R jx = ax + dx, jy = ay + dy;
-    const R m4 = R(-2) * f[0] + sa + R(4) * sd;
-    const R m5 = (f[1] + f[3]) - (f[2] + f[4]);
-    const R m6 = (f[5] + f[7]) - (f[6] + f[8]);
+    const R m4 = R(-2) * g0 + sa + R(4) * sd;
+    const R m5 = GF ? wa * ((f[1] + f[3]) - (f[2] + f[4])) : (f[1] + f[3]) - (f[2] + f[4]);
+    const R m6 = GF ? wd * ((f[5] + f[7]) - (f[6] + f[8])) : (f[5] + f[7]) - (f[6] + f[8]);
     const R m7 = R(2) * dx - ax;
     const R m8 = R(2) * dy - ay;
-    const R m9 = R(2) * f[0] - R(4) * sa + R(8) * sd;
+    const R m9 = R(2) * g0 - R(4) * sa + R(8) * sd;
 
     // equilibrium deviations, Table II (C_n = 0): p0 - sigma_s^2 rho relative to the rest
     // state, linear (p0 = cs2 rho) or the double well's quartic in drho (Sec. II A)
@@ -130,16 +145,29 @@ __device__ __forceinline__ void collide_node(const Args& a, const R f[Q], const 
     const R Dd = R(4) * d4 + R(8) * d9;            // the same for the diagonals
     const R D1 = Dd + d6, D2 = Dd - d6;
     const R P = R(2) * (d7 + d8), M = R(2) * (d7 - d8);
-    const R w0 = R(8) / R(9), w1 = R(1) / R(9), w5 = R(1) / R(36);
-    o[0] = f[0] + w0 * (d9 - d4);
-    o[1] = f[1] + w1 * (A1 - d7);
-    o[2] = f[2] + w1 * (A2 - d8);
-    o[3] = f[3] + w1 * (A1 + d7);
-    o[4] = f[4] + w1 * (A2 + d8);
-    o[5] = f[5] + w5 * (D1 + P);
-    o[6] = f[6] + w5 * (D2 - M);
-    o[7] = f[7] + w5 * (D1 - P);
-    o[8] = f[8] + w5 * (D2 + M);
+    // the rest velocity's increment is w_0 (T_40 D4/N4 + T_90 D9/N9) = (4/9)(2 d9 - 2 d4)
+    if constexpr (GF) {
+        o[0] = f[0] + R(2) * (d9 - d4);
+        o[1] = f[1] + (A1 - d7);
+        o[2] = f[2] + (A2 - d8);
+        o[3] = f[3] + (A1 + d7);
+        o[4] = f[4] + (A2 + d8);
+        o[5] = f[5] + (D1 + P);
+        o[6] = f[6] + (D2 - M);
+        o[7] = f[7] + (D1 - P);
+        o[8] = f[8] + (D2 + M);
+    } else {
+        const R u0 = R(8) / R(9), u1 = R(1) / R(9), u5 = R(1) / R(36);
+        o[0] = f[0] + u0 * (d9 - d4);
+        o[1] = f[1] + u1 * (A1 - d7);
+        o[2] = f[2] + u1 * (A2 - d8);
+        o[3] = f[3] + u1 * (A1 + d7);
+        o[4] = f[4] + u1 * (A2 + d8);
+        o[5] = f[5] + u5 * (D1 + P);
+        o[6] = f[6] + u5 * (D2 - M);
+        o[7] = f[7] + u5 * (D1 - P);
+        o[8] = f[8] + u5 * (D2 + M);
+    }
 }
 
 }  // namespace lbf

@@ -7,6 +7,8 @@
 #include "lb_internal.cuh"
 #include "lb_tma.cuh"
 
+#include <type_traits>
+
 namespace lbf {
 
 // Per-replica record (device).
@@ -14,10 +16,10 @@ struct RepRec {
     float rho0, cs2m, kappa, lb, ls, lq, le;
     float L44, L49, L94, L99, s5, s6, s7;
     float a44, b44, a49, b49, a99, b99;   // Xi(k) of the (4,9) block = a + b s(k) (correlated noise)
-    float sL[3][4];           // real-space correlated noise: factors / 4 of Xi at k^2 = 0, 4, 16/3
     int mode;                 // 0 no noise, 1 uncorrelated, 2 correlated (k-space), 3 correlated (real space)
     uint32_t k0, k1;          // Philox key = the replica's seed
     long long toff;           // time = K + toff
+    float sL[3][4];           // real-space correlated noise: factors / 4 of Xi at k^2 = 0, 4, 16/3
 };
 
 // What collide_node needs for one tile of one replica, in registers (the engines step the
@@ -25,10 +27,18 @@ struct RepRec {
 struct TileArgs {
     float rho0, cs2m, kappa, lb, ls, lq, le;
     float L44, L49, L94, L99, s5, s6, s7;
-    float sL[3][4];
     uint32_t t_lo, t_hi;
     KeyPair rk;
 };
+
+// The same with the real-space correlated-noise factors: the record of the engines' step
+// kernel variant that steps such lattices (the lean variant keeps the smaller record).
+struct TileArgsRS : TileArgs {
+    float sL[3][4];
+};
+
+template <bool RS>
+using TileArgsOf = typename std::conditional<RS, TileArgsRS, TileArgs>::type;
 
 // The record of one lattice as collide_node reads it, for its time t; *mode = 0 without
 // noise, 1 with uncorrelated noise, 2 with correlated noise (xi_4, xi_9 read from a field),
@@ -48,7 +58,7 @@ __device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t
 
 // The real-space correlated-noise factors of a record (only for its lattices with that
 // mode: the record load sits on the tile's critical path).
-__device__ __forceinline__ void load_stencil_args(const RepRec* rp, TileArgs* a) {
+__device__ __forceinline__ void load_stencil_args(const RepRec* rp, TileArgsRS* a) {
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -117,7 +127,7 @@ __device__ __forceinline__ void tile_nodes(const TileArgs& a, const float (&fr)[
 // contributions of the tile's nodes and of its halo, written into the memory of the stage
 // just consumed (FP32 stages hold them; the caller refills that stage after the collision).
 template <int TX, int TY, int NT>
-__device__ __forceinline__ void tile_stencil(const TileArgs& a, float2* Hs, const Grid& g, int x0, int y0) {
+__device__ __forceinline__ void tile_stencil(const TileArgsRS& a, float2* Hs, const Grid& g, int x0, int y0) {
     using TT = TmaTile<TX, TY, float>;
     static_assert(TT::H_IN_STAGE, "the noise contributions must fit in a stage");
 #pragma unroll 1

@@ -56,6 +56,9 @@ struct Elem<__half> {
     __device__ static __forceinline__ __half store(float v, int i) {
         return __float2half_rn(v * (i == 0 ? 2.25f : (i < 5 ? 9.0f : 36.0f)));
     }
+    // the stored value itself, g_i = df_i / w_i (kernels that collide in that form)
+    __device__ static __forceinline__ float load_g(__half v) { return __half2float(v); }
+    __device__ static __forceinline__ __half store_g(float g) { return __float2half_rn(g); }
 };
 
 // FP64 storage: deviations in FP64, arithmetic in FP64.
@@ -301,17 +304,21 @@ __device__ __forceinline__ void store_with_ghosts(T* plane, const Grid& g, int x
 // their corner unless the lattice is narrower than 2 GW or lower than 4 rows; the common
 // case is three predicated stores per plane with offsets formed once per node, the rare
 // one goes through store_with_ghosts.
-template <typename T, typename R>
+template <typename T, typename R, bool GF = false>
 __device__ __forceinline__ void store9(T* dst, long long P, const Grid& g, int x, int y, const R o[Q]) {
     constexpr int GW = Elem<T>::GW;
+    auto conv = [](R v, int i) -> T {
+        if constexpr (GF) return Elem<T>::store_g(v);
+        else return Elem<T>::store(v, i);
+    };
     const long long c = g.at(x, y);
     const bool xl = x < GW, xr = x >= g.nx - GW, yb = y < 2, yt = y >= g.ny - 2;
     if (!(xl | xr | yb | yt)) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) dst[i * P + c] = Elem<T>::store(o[i], i);
+        for (int i = 0; i < Q; ++i) dst[i * P + c] = conv(o[i], i);
     } else if ((xl & xr) | (yb & yt)) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) store_with_ghosts(dst + i * P, g, x, y, Elem<T>::store(o[i], i));
+        for (int i = 0; i < Q; ++i) store_with_ghosts(dst + i * P, g, x, y, conv(o[i], i));
     } else {
         const bool hx = xl | xr, hy = yb | yt;
         const long long dx = xl ? (long long)g.nx : (xr ? -(long long)g.nx : 0);
@@ -319,7 +326,7 @@ __device__ __forceinline__ void store9(T* dst, long long P, const Grid& g, int x
         const long long dxy = dx + dy;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const T v = Elem<T>::store(o[i], i);
+            const T v = conv(o[i], i);
             T* p = dst + i * P + c;
             p[0] = v;
             if (hx) p[dx] = v;

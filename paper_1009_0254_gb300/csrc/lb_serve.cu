@@ -71,14 +71,14 @@ __device__ __forceinline__ int find_owner(const int* __restrict__ tile_begin, in
 // RS: the variant that also steps simulations with real-space correlated noise (launched
 // for chunks that hold one; its extra path raises the register count)
 template <int TX, int TY, int NT, bool RS>
-__global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_serve_kernel(const ServeParams p) {
+__global__ void __launch_bounds__(NT, RS ? 1024 / NT : 0) step_serve_kernel(const ServeParams p) {
     using TT = TmaTile<TX, TY, float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
     float* R = reinterpret_cast<float*>(smem_raw + 2 * TT::STAGE_BYTES);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(R + TT::RW * TT::RH);
     __shared__ int st_slot[2], st_x0[2], st_y0[2];
-    __shared__ TileArgs sargs;          // the record of the current tile
+    __shared__ TileArgsOf<RS> sargs;    // the record of the current tile
     __shared__ int smode;
     const int tid = threadIdx.x;
     const long long K = __ldcg(p.kstep);
@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_serve_kernel(cons
         // the slot's record, to shared memory (its last readers, the previous tile's
         // collision, are past the barrier above)
         if (tid == 0) {
-            sargs = load_tile_args(p.recs + slot, sl, &smode);
-            if (RS && smode == 3) load_stencil_args(p.recs + slot, &sargs);
+            static_cast<TileArgs&>(sargs) = load_tile_args(p.recs + slot, sl, &smode);
+            if constexpr (RS) {
+                if (smode == 3) load_stencil_args(p.recs + slot, &sargs);
+            }
         }
 
         // pulled populations stay in registers across the density barrier; the stage is
@@ -161,21 +163,28 @@ __global__ void __launch_bounds__(NT, RS ? 1024 / NT : 1) step_serve_kernel(cons
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(tile + 2 * gridDim.x, s);
         }
-        if (RS && mode == 3) {
-            // real-space correlated noise: contributions in the consumed stage s, refilled
-            // after the collision (the mode is the tile's: uniform over the CTA)
-            float2* Hs = reinterpret_cast<float2*>(smem_raw + s * TT::STAGE_BYTES);
-            tile_stencil<TX, TY, NT>(sargs, Hs, g, x0, y0);
-            __syncthreads();
-            tile_nodes<3, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr, Hs);
-            __syncthreads();
-            if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(tile + 2 * gridDim.x, s);
+        bool stepped = false;
+        if constexpr (RS) {
+            if (mode == 3) {
+                // real-space correlated noise: contributions in the consumed stage s, refilled
+                // after the collision (the mode is the tile's: uniform over the CTA)
+                float2* Hs = reinterpret_cast<float2*>(smem_raw + s * TT::STAGE_BYTES);
+                tile_stencil<TX, TY, NT>(sargs, Hs, g, x0, y0);
+                __syncthreads();
+                tile_nodes<3, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr, Hs);
+                __syncthreads();
+                if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(tile + 2 * gridDim.x, s);
+                }
+                stepped = true;
             }
-        } else if (mode == 2) tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, d->xi);
-        else if (mode) tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
-        else tile_nodes<0, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
+        }
+        if (!stepped) {
+            if (mode == 2) tile_nodes<2, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, d->xi);
+            else if (mode) tile_nodes<1, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
+            else tile_nodes<0, TX, TY, NT>(sargs, fr, R, g, x0, y0, dst, nullptr);
+        }
     }
     if (tid == 0) {
         const unsigned int prev = atomicAdd(p.done, 1u);

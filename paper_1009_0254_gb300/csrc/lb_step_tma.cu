@@ -22,6 +22,8 @@
 // error word, gives its loads in flight a bounded chance to land, and returns.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "lb_collide.cuh"
 #include "lb_tma.cuh"
 
@@ -45,7 +47,10 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
     const Grid g = a.g;
     const int tid = threadIdx.x;
     const int ntiles = ta.ntx * ta.nty;
-    auto load9 = [](const T* S, int b, float f[Q]) { load9_ps<TT::PS>(S, b, f); };
+    // FP16 storage collides in the stored form g_i = df_i / w_i (no scaling on load or store)
+    constexpr bool GF = std::is_same<T, __half>::value;
+    auto load9 = [](const T* S, int b, float f[Q]) { load9_ps<TT::PS, T, GF>(S, b, f); };
+    auto rho_of = [](const float f[Q]) { return GF ? drho_of_g(f) : drho_of(f); };
     // MODE 3: the 2 x 2-box noise contributions, after the mbarriers (kept apart from the
     // stages: filling them into the consumed stage and refilling it after the collision
     // measured slower, the two extra barriers costing more than the fourth CTA per SM gained)
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             const int q = tid + it * NT;
             const int ly = q / TX, lx = q - ly * TX;
             load9(S, (ly + 1) * TT::BW + lx + TT::XO, fr[it]);
-            R[(ly + 1) * TT::RW + lx + 1] = drho_of(fr[it]);
+            R[(ly + 1) * TT::RW + lx + 1] = rho_of(fr[it]);
         }
         // real-space correlated noise: every node's contributions, then the halo's
         auto stencil_tile = [&](float2* Hd) {
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             else { const int u = j - 2 * (TX + 2); ry = 1 + (u >> 1); rx = (u & 1) ? TX + 1 : 0; }
             float h[Q];
             load9(S, ry * TT::BW + rx + TT::XO - 1, h);
-            R[ry * TT::RW + rx] = drho_of(h);
+            R[ry * TT::RW + rx] = rho_of(h);
         }
         __syncthreads();
         // the collision pass reads no population from stage s: refill it now with the tile
@@ -161,8 +166,8 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
             if (MODE == 3) z = stencil_xi<TT::HW>(H, TT::HN, lx, ly);
             float o[Q];
-            collide_node<MODE>(a, f, r, node, z, o);
-            store9(static_cast<T*>(a.dst), g.plane, g, x, y, o);
+            collide_node<MODE, false, GF>(a, f, r, node, z, o);
+            store9<T, float, GF>(static_cast<T*>(a.dst), g.plane, g, x, y, o);
         }
     }
 }

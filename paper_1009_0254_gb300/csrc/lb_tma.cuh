@@ -101,17 +101,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 
 // The nine pulled deviations of the node whose unshifted box index is b: plane i is read at
 // b - cx_i (its y shift is already in the box origin).
-template <int PS, typename T>
+template <int PS, typename T, bool GF = false>
 __device__ __forceinline__ void load9_ps(const T* S, int b, float f[Q]) {
-    f[0] = Elem<T>::load(S[b], 0);
-    f[1] = Elem<T>::load(S[PS + b - 1], 1);
-    f[2] = Elem<T>::load(S[2 * PS + b], 2);
-    f[3] = Elem<T>::load(S[3 * PS + b + 1], 3);
-    f[4] = Elem<T>::load(S[4 * PS + b], 4);
-    f[5] = Elem<T>::load(S[5 * PS + b - 1], 5);
-    f[6] = Elem<T>::load(S[6 * PS + b + 1], 6);
-    f[7] = Elem<T>::load(S[7 * PS + b + 1], 7);
-    f[8] = Elem<T>::load(S[8 * PS + b - 1], 8);
+    auto ld = [](T v, int i) -> float {
+        if constexpr (GF) return Elem<T>::load_g(v);
+        else return Elem<T>::load(v, i);
+    };
+    f[0] = ld(S[b], 0);
+    f[1] = ld(S[PS + b - 1], 1);
+    f[2] = ld(S[2 * PS + b], 2);
+    f[3] = ld(S[3 * PS + b + 1], 3);
+    f[4] = ld(S[4 * PS + b], 4);
+    f[5] = ld(S[5 * PS + b - 1], 5);
+    f[6] = ld(S[6 * PS + b + 1], 6);
+    f[7] = ld(S[7 * PS + b + 1], 7);
+    f[8] = ld(S[8 * PS + b - 1], 8);
 }
 
 // Real-space correlated noise of a tile (LB_NOISE_FULL_RS): the contributions h_d(q) of a
@@ -131,11 +135,12 @@ __device__ __forceinline__ void stencil_store(const Args& a, float2* H, int HN, 
 
 // the halo nodes of the tile at (x0, y0): j in [0, TY] -> column x0 - 1, rows y0 - 1 ..
 // y0 + TY - 1; j in (TY, TX + TY] -> row y0 - 1, columns x0 .. x0 + TX - 1 (periodic; nodes
-// past a ragged edge are skipped, no tile node reads them)
+// past a ragged edge are skipped, no tile node reads them).  They go to the last threads of
+// the block, which form no density-ring node, so the work before the tile's barrier evens out.
 template <int TX, int TY, int HW, typename Args>
 __device__ __forceinline__ void stencil_halo(const Args& a, float2* H, int HN, int x0, int y0, int nx, int ny,
                                              int tid, int nthreads) {
-    for (int j = tid; j < TX + TY + 1; j += nthreads) {
+    for (int j = nthreads - 1 - tid; j < TX + TY + 1; j += nthreads) {
         int lx, ly;
         if (j <= TY) { lx = -1; ly = j - 1; }
         else { lx = j - (TY + 1); ly = -1; }

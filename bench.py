@@ -416,11 +416,14 @@ def _request_stream(rate, n_requests, seed):
     return arrive, side, steps, kT, kap, ts
 
 
-def _serve_stream(lbf, stream, budget, chunk):
+def _serve_stream(lbf, stream, budget, chunk, admission=None):
     """Submits the stream at its arrival times, waits for the drain; returns latencies
-    (completion - submission, host clock) and the server's counters."""
+    (completion - submission, host clock) and the server's counters.  admission: optional
+    (large_nodes, max_large) for lb_server_set_admission."""
     arrive, side, steps, kT, kap, ts = stream
     srv = lbf.Server(budget, max_active=4096, max_chunk_steps=chunk)
+    if admission is not None:
+        lbf.lb_server_set_admission(srv.srv, *admission)
     t0 = time.perf_counter()
     for k in range(len(arrive)):
         d = arrive[k] - (time.perf_counter() - t0)
@@ -465,11 +468,16 @@ def _plain_server(lbf, torch, stream):
     return lat, updates / wall / 1e6, wall
 
 
-def serve_compare(lbf, torch, r, n, seed, budget=120 * 10 ** 9, chunk=200):
+def serve_compare(lbf, torch, r, n, seed, budget=120 * 10 ** 9, chunk=200, admission=None, plain=True):
     """One trace of n requests at r/s through the server and through the plain FIFO path."""
     stream = _request_stream(r, n, seed)
-    lat, st = _serve_stream(lbf, stream, budget, chunk)
+    lat, st = _serve_stream(lbf, stream, budget, chunk, admission)
     wall = st.t_last_complete - st.t_first_admit
+    if not plain:
+        return {"rate_per_s": r, "requests": n, "completed": int(st.completed), "admission": admission,
+                "value": st.node_updates / wall / 1e6, "unit": "MLUPS (aggregate, first admission to last completion)",
+                "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "max": float(lat.max())}}
     plat, pmlups, pwall = _plain_server(lbf, torch, stream)
     offered = float(np.sum(stream[1].astype(float) ** 2 * stream[2])) / max(stream[0][-1], 1e-9) / 1e6
     return {"rate_per_s": r, "requests": n, "completed": int(st.completed),
@@ -538,9 +546,14 @@ def main():
         print(json.dumps(batched_variant(lbf, torch)))
         return 0
     if args.serve_study:
+        big = (512 * 512, 1)      # lattices of 512^2 and more: one at a time
         print(json.dumps({"workload": "served request stream (config 5 mix) at sustainable rates, 500 requests "
-                                      "per trace; served engine against the plain path measured on the same trace",
-                          "rates": [serve_compare(lbf, torch, 5.0, 500, 31), serve_compare(lbf, torch, 2.0, 500, 32)]}))
+                                      "per trace; served engine against the plain path measured on the same trace; "
+                                      "the server also with lattices of 512^2 nodes and more admitted one at a time",
+                          "rates": [serve_compare(lbf, torch, 5.0, 500, 31), serve_compare(lbf, torch, 2.0, 500, 32)],
+                          "large_one_at_a_time": [serve_compare(lbf, torch, 5.0, 500, 31, admission=big, plain=False),
+                                                  serve_compare(lbf, torch, 2.0, 500, 32, admission=big,
+                                                                plain=False)]}))
         return 0
 
     n = args.n

@@ -365,6 +365,12 @@ const char* lb_batch_last_error(lb_batch* b);
  * lb_server_cancel: withdraws request `id`: a queued one at once, an admitted one at the
  *   next chunk boundary (its memory is released); its result then has status
  *   LB_ECANCELED.  LB_EINVAL if it is unknown or already completed.
+ * lb_server_set_admission: requests of at least `large_nodes` lattice nodes (nx * ny) are
+ *   admitted at most `max_large` at a time (later, smaller requests pass one that waits);
+ *   max_large = 0 removes the limit (the default).  A lattice that fills the GPU alone gains
+ *   no throughput from sharing it with another such lattice, and sharing delays both: with
+ *   a limit the large requests complete in arrival order while small ones still run in
+ *   the same launches.  LB_EINVAL for large_nodes < 1 or max_large < 0.
  * lb_server_inject_alloc_failures: fault injection on the host: the next `count`
  *   admissions behave as if the device allocation failed.  A failed allocation, injected
  *   or real (the pool could not grow), completes that request with status LB_ENOMEM
@@ -418,6 +424,7 @@ int lb_server_wait(lb_server* s, int64_t id, double timeout_s, lb_result* out);
 int lb_server_fetch_populations(lb_server* s, int64_t id, double* f);
 int lb_server_get_stats(lb_server* s, lb_server_stats* st);
 int lb_server_cancel(lb_server* s, int64_t id);
+int lb_server_set_admission(lb_server* s, int64_t large_nodes, int max_large);
 int lb_server_inject_alloc_failures(lb_server* s, int count);
 int lb_server_destroy(lb_server* s);
 const char* lb_server_last_error(lb_server* s);

@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
         "lb_server_destroy": (c_int, [vp]),
         "lb_server_cancel": (c_int, [vp, c_i64]),
         "lb_server_inject_alloc_failures": (c_int, [vp, c_int]),
+        "lb_server_set_admission": (c_int, [vp, c_i64, c_int]),
         "lb_selftest_bounded_wait": (c_int, [c_dbl, ctypes.POINTER(c_int)]),
         "lb_server_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -417,6 +418,10 @@ def lb_server_get_stats(srv):
 
 def lb_server_cancel(srv, id):
     return _scheck(load().lb_server_cancel(srv, id), srv)
+
+
+def lb_server_set_admission(srv, large_nodes, max_large):
+    return _scheck(load().lb_server_set_admission(srv, int(large_nodes), int(max_large)), srv)
 
 
 def lb_server_inject_alloc_failures(srv, count):

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NT, RS ? 1024 / NT : 0) step_ensemble_kernel(c
         // registers, which the pulled populations need, and than loading it before the wait)
         if (tid == 0) {
             const RepRec* rp = p.cls[tp.c].recs + tp.rep;
-            static_cast<TileArgs&>(sargs) = load_tile_args(rp, K + __ldg(&rp->toff), &smode);
+            load_tile_args(rp, K + __ldg(&rp->toff), &sargs, &smode);
             if constexpr (RS) {
                 if (smode == 3) load_stencil_args(rp, &sargs);
             }

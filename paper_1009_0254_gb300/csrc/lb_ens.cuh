@@ -24,11 +24,11 @@ struct RepRec {
 
 // What collide_node needs for one tile of one replica, in registers (the engines step the
 // linearised equation of state).
-struct TileArgs {
+struct __align__(16) TileArgs {
+    RoundKeys4 rk;            // the lattice's Philox round keys
     float rho0, cs2m, kappa, lb, ls, lq, le;
     float L44, L49, L94, L99, s5, s6, s7;
     uint32_t t_lo, t_hi;
-    KeyPair rk;
 };
 
 // The same with the real-space correlated-noise factors: the record of the engines' step
@@ -40,20 +40,25 @@ struct TileArgsRS : TileArgs {
 template <bool RS>
 using TileArgsOf = typename std::conditional<RS, TileArgsRS, TileArgs>::type;
 
-// The record of one lattice as collide_node reads it, for its time t; *mode = 0 without
-// noise, 1 with uncorrelated noise, 2 with correlated noise (xi_4, xi_9 read from a field),
-// 3 with correlated noise built in real space.
-__device__ __forceinline__ TileArgs load_tile_args(const RepRec* rp, long long t, int* mode) {
-    TileArgs a;
-    a.rho0 = __ldg(&rp->rho0); a.cs2m = __ldg(&rp->cs2m); a.kappa = __ldg(&rp->kappa);
-    a.lb = __ldg(&rp->lb); a.ls = __ldg(&rp->ls); a.lq = __ldg(&rp->lq); a.le = __ldg(&rp->le);
-    a.L44 = __ldg(&rp->L44); a.L49 = __ldg(&rp->L49); a.L94 = __ldg(&rp->L94); a.L99 = __ldg(&rp->L99);
-    a.s5 = __ldg(&rp->s5); a.s6 = __ldg(&rp->s6); a.s7 = __ldg(&rp->s7);
-    a.rk.k0 = __ldg(&rp->k0); a.rk.k1 = __ldg(&rp->k1);
-    a.t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);
-    a.t_hi = (uint32_t)((unsigned long long)t >> 32);
+// The record of one lattice as collide_node reads it, for its time t, written by one
+// thread into the tile's shared record a; *mode = 0 without noise, 1 with uncorrelated
+// noise, 2 with correlated noise (xi_4, xi_9 read from a field), 3 with correlated noise
+// built in real space.
+__device__ __forceinline__ void load_tile_args(const RepRec* rp, long long t, TileArgs* a, int* mode) {
+    a->rho0 = __ldg(&rp->rho0); a->cs2m = __ldg(&rp->cs2m); a->kappa = __ldg(&rp->kappa);
+    a->lb = __ldg(&rp->lb); a->ls = __ldg(&rp->ls); a->lq = __ldg(&rp->lq); a->le = __ldg(&rp->le);
+    a->L44 = __ldg(&rp->L44); a->L49 = __ldg(&rp->L49); a->L94 = __ldg(&rp->L94); a->L99 = __ldg(&rp->L99);
+    a->s5 = __ldg(&rp->s5); a->s6 = __ldg(&rp->s6); a->s7 = __ldg(&rp->s7);
+    uint32_t k0 = __ldg(&rp->k0), k1 = __ldg(&rp->k1);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        a->rk.q[j] = make_uint4(k0, k1, k0 + 0x9E3779B9u, k1 + 0xBB67AE85u);
+        k0 += 2u * 0x9E3779B9u;
+        k1 += 2u * 0xBB67AE85u;
+    }
+    a->t_lo = (uint32_t)((unsigned long long)t & 0xffffffffu);
+    a->t_hi = (uint32_t)((unsigned long long)t >> 32);
     *mode = __ldg(&rp->mode);
-    return a;
 }
 
 // The real-space correlated-noise factors of a record (only for its lattices with that

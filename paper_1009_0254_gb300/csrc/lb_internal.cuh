@@ -160,6 +160,38 @@ struct KeyPair {
     uint32_t k0, k1;
 };
 
+// Round keys as five 16-byte words, q[j] = keys of rounds 2j and 2j + 1: a record in shared
+// memory serves them with five vector loads.
+struct __align__(16) RoundKeys4 {
+    uint4 q[5];
+};
+
+__device__ __forceinline__ RoundKeys4 round_keys4(uint32_t k0, uint32_t k1) {
+    RoundKeys4 rk;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        rk.q[j] = make_uint4(k0, k1, k0 + 0x9E3779B9u, k1 + 0xBB67AE85u);
+        k0 += 2u * 0x9E3779B9u;
+        k1 += 2u * 0xBB67AE85u;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys4& rk) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const uint4 kk = rk.q[j];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t ka = h ? kk.z : kk.x, kb = h ? kk.w : kk.y;
+            const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+            const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+            c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ ka, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ kb, (uint32_t)p0);
+        }
+    }
+    return c;
+}
+
 using NoiseGenArgs = NoiseGenT<RoundKeys>;   // single lattice: round keys precomputed
 using NoiseGenArgsD = NoiseGenT<RoundKeys, double>;   // FP64 storage
 

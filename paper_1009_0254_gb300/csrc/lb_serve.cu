@@ -71,7 +71,7 @@ __device__ __forceinline__ int find_owner(const int* __restrict__ tile_begin, in
 // RS: the variant that also steps simulations with real-space correlated noise (launched
 // for chunks that hold one; its extra path raises the register count)
 template <int TX, int TY, int NT, bool RS>
-__global__ void __launch_bounds__(NT, RS ? 1024 / NT : 0) step_serve_kernel(const ServeParams p) {
+__global__ void __launch_bounds__(NT, 1024 / NT) step_serve_kernel(const ServeParams p) {
     using TT = TmaTile<TX, TY, float>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(NT, RS ? 1024 / NT : 0) step_serve_kernel(cons
         // the slot's record, to shared memory (its last readers, the previous tile's
         // collision, are past the barrier above)
         if (tid == 0) {
-            static_cast<TileArgs&>(sargs) = load_tile_args(p.recs + slot, sl, &smode);
+            load_tile_args(p.recs + slot, sl, &sargs, &smode);
             if constexpr (RS) {
                 if (smode == 3) load_stencil_args(p.recs + slot, &sargs);
             }
@@ -390,6 +390,8 @@ struct lb_server {
     double t_first_admit = -1.0, t_last_complete = -1.0;
     bool stop = false;
     int inject_alloc_fail = 0;        // host-side fault injection: admissions left to fail
+    long long large_nodes = 0;        // admission: requests with at least this many nodes ...
+    int max_large = 0;                // ... are admitted at most this many at a time (0: no limit)
     std::vector<int64_t> cancel_ids;  // admitted requests to withdraw at the next chunk boundary
     std::string err;                  // sticky worker error
     std::thread worker;
@@ -505,11 +507,21 @@ bool admit(lb_server* s) {
     std::vector<int> slots;
     {
         std::lock_guard<std::mutex> lk(s->mu);
+        // large requests already admitted (the admission limit on them, if set)
+        int large = 0;
+        if (s->max_large > 0)
+            for (const Running& r : s->running) large += (long long)r.g.nx * r.g.ny >= s->large_nodes;
         for (auto it = s->queue.begin(); it != s->queue.end() && !s->free_slots.empty();) {
             Grid g;
             serve_grid(it->r.nx, it->r.ny, &g);
             const size_t b = slot_bytes(g, it->r.noise_mode == LB_NOISE_FULL);
+            const bool is_large = s->max_large > 0 && (long long)it->r.nx * it->r.ny >= s->large_nodes;
+            if (is_large && large >= s->max_large) {
+                ++it;                  // waits for a large one to finish; smaller ones may pass
+                continue;
+            }
             if (s->in_use + b <= s->budget) {
+                large += is_large;
                 s->in_use += b;
                 s->peak = std::max(s->peak, s->in_use);
                 take.push_back(*it);
@@ -1048,6 +1060,15 @@ int lb_server_cancel(lb_server* s, int64_t id) {
     }
     if (id <= 0 || id >= s->next_id || s->all_results.count(id)) return LB_EINVAL;
     s->cancel_ids.push_back(id);      // admitted (or being admitted): withdrawn by the worker
+    s->cv.notify_all();
+    return LB_OK;
+}
+
+int lb_server_set_admission(lb_server* s, int64_t large_nodes, int max_large) {
+    if (!s || large_nodes < 1 || max_large < 0) return LB_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->large_nodes = large_nodes;
+    s->max_large = max_large;
     s->cv.notify_all();
     return LB_OK;
 }

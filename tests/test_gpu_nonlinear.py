@@ -102,11 +102,10 @@ def _fp16_code(f, fbar):
     return g.astype(np.float16)
 
 
-def _ulp_index(h):
-    """FP16 values as integers in value order (consecutive FP16 numbers differ by one;
-    +0 and -0 are both 0)."""
-    b = h.view(np.uint16).astype(np.int64)
-    return np.where(b >= 0x8000, -(b & 0x7FFF), b)
+# FP32 arithmetic error of the collision in g units (intermediates of size up to ~1 at this
+# state, a few dozen operations): below one FP16 unit in the last place for words of order
+# one, above it for words near zero, where an FP16 unit is as small as 6e-8
+G_ARITH = 4e-6
 
 
 @pytest.mark.parametrize("kernel", ["tma", "simple", "sweep", "sweep6"])
@@ -115,8 +114,9 @@ def test_fp16_storage_resolves_the_nonlinear_terms(kernel, case, monkeypatch):
     # FP16 storage keeps g_i = (f_i - fbar_i)/w_i in FP16.  Start from a state whose g_i are
     # FP16 numbers (stored exactly), take one step, and compare the stored words with the
     # oracle's result rounded to FP16 the same way: they may differ only where the FP32
-    # arithmetic lands within its own rounding error of an FP16 rounding boundary (one unit
-    # in the last place, rare); a dropped second-order term moves many words by several.
+    # arithmetic lands within its own rounding error (G_ARITH) of an FP16 rounding boundary,
+    # i.e. by at most one unit in the last place plus G_ARITH, and rarely; a dropped
+    # second-order term moves g by 1e-3 or more (over 250 x G_ARITH).
     monkeypatch.setenv("LBFLUCT_STEP_KERNEL", kernel)
     monkeypatch.delenv("LBFLUCT_TMA_TILE", raising=False)
     rho0, cs2, p = nl.CASES[case]
@@ -131,12 +131,14 @@ def test_fp16_storage_resolves_the_nonlinear_terms(kernel, case, monkeypatch):
         g.set_populations(f0, t=0)
         assert np.array_equal(_fp16_code(g.populations(), fbar), h)      # stored exactly
         g.step(1)
-        got = _ulp_index(_fp16_code(g.populations(), fbar))
-        want = _ulp_index(_fp16_code(_oracle(case, f0, 1), fbar))
+        got = _fp16_code(g.populations(), fbar).astype(np.float64)
+        want16 = _fp16_code(_oracle(case, f0, 1), fbar)
+        want = want16.astype(np.float64)
+        ulp = np.spacing(np.abs(want16)).astype(np.float64)
         d = np.abs(got - want)
-        print("fp16 %s %s %dx%d: words off by one %d of %d, max %d" % (kernel, case, nx, ny, (d == 1).sum(), d.size,
-                                                                       d.max()))
-        assert d.max() <= 1, d.max()
+        print("fp16 %s %s %dx%d: words that differ %d of %d, largest difference %.2e (%.1f units of the word)"
+              % (kernel, case, nx, ny, (d > 0).sum(), d.size, d.max(), (d / ulp).max()))
+        assert np.all(d <= ulp + G_ARITH), (d - ulp).max()
         assert (d == 0).mean() >= 0.99
         g.close()
 

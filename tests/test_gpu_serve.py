@@ -334,3 +334,33 @@ def test_served_real_space_correlated_result_same_alone_and_in_the_mix():
     assert all(r.status == lbf.LB_OK for r in mix.poll())
     assert np.array_equal(fa, mix.fetch(ix, 60, 36))
     mix.close()
+
+
+def test_admission_limit_on_large_requests():
+    # lb_server_set_admission: two large lattices are not admitted together (the second waits
+    # until the first has issued its last step), small ones pass; results are unchanged
+    def run(limit):
+        srv = lbf.Server(1 << 31, max_active=16, max_chunk_steps=25)
+        if limit:
+            lbf.lb_server_set_admission(srv.srv, 256 * 256, 1)
+        big1 = srv.submit(256, 256, 300, seed=1, keep_state=True)
+        big2 = srv.submit(256, 256, 300, seed=2, keep_state=True)
+        small = srv.submit(32, 32, 300, seed=3, keep_state=True)
+        r = [srv.wait(i, timeout_s=120) for i in (big1, big2, small)]
+        f = [srv.fetch(i, n, n) for i, n in ((big1, 256), (big2, 256), (small, 32))]
+        srv.close()
+        return r, f
+    r0, f0 = run(False)
+    r1, f1 = run(True)
+    for a, b in zip(f0, f1):
+        assert np.array_equal(a, b)
+    assert all(x.status == lbf.LB_OK for x in r1)
+    # with the limit the second large lattice is admitted only after the first ran; the small
+    # one ran alongside the first
+    assert r1[1].t_admit >= r1[0].t_admit + 0.5 * (r1[0].t_complete - r1[0].t_admit)
+    assert r1[2].t_admit <= r1[0].t_complete
+    srv = lbf.Server(1 << 20)
+    with pytest.raises(lbf.LBError) as e:
+        lbf.lb_server_set_admission(srv.srv, 0, 1)
+    assert e.value.code == lbf.LB_EINVAL
+    srv.close()

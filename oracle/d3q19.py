@@ -1,0 +1,284 @@
+"""FP64 CPU oracle of the fluctuating non-ideal model on the D3Q19 lattice.
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` are the only callers; the product library shares no code with it.
+
+Sec. IV of Gross, Adhikari, Cates & Varnik (arXiv:1009.0254) states that the derivation of
+the noise from the lattice fluctuation-dissipation theorem holds on any DdQn lattice.  This
+module carries the D2Q9 model of the paper to D3Q19 with the same steps:
+
+  * the weighted-orthogonal basis of Duenweg, Schiller & Ladd, Phys. Rev. E 76, 036704
+    (2007), Table I (the D3Q19 modes); the D2Q9 basis of Table I of the paper is the
+    two-dimensional member of that family;
+  * the fluctuating collision of Eq. (fluct-lin-lbe) in moment space and the streaming of
+    Eq. (gen-lbe), on a periodic box;
+  * equilibrium moments that carry the pressure tensor of Eq. (press-ten) with
+    p0 = cs2 rho (the linearised equation of state), Galilean corrections and forcing
+    omitted as in the D2Q9 model;
+  * the long-wavelength noise Xi(0) of Eq. (noise-matrix-k0), built from the equilibrium
+    correlations of the ansatz Eq. (f-correl-yeo) and the linearised collision operator,
+    then factored by Cholesky (Sec. IV).
+
+Readings where the paper is silent (also listed in the design notes):
+  * the second-order moments are the trace and the traceless part of P^th + rho u u
+    (Eq. press-ten), so sum_i f^eq_i c_ia c_ib = P^th_ab + rho u_a u_b;
+  * the ghost equilibria are zero except the isotropic fourth-order ghost,
+    e16^eq = -3 (p0 - sigma_s^2 rho - kappa rho lap rho) - (9/2) kappa |grad rho|^2,
+    the one isotropic choice for which a field that is uniform along one axis evolves,
+    at equal relaxation times, exactly as the paper's D2Q9 model (Table II);
+  * one bulk rate lambda_b for mode 4, one shear rate lambda_s for modes 5..9 and one
+    ghost rate for modes 10..18;
+  * the Laplacian and the gradient are the isotropic stencils of Appendix B written with
+    the D3Q19 weights.
+
+Indices: velocities and moments are array positions 0..18; f[i, z, y, x].
+Random numbers: two Philox4x32-10 draws per node and step with counter (node, t mod 2^32,
+t div 2^32, tag), node = (z ny + y) nx + x; tag 4 gives nu_4..nu_11, tag 5 gives
+nu_12..nu_18 (its last normal unused), each word one Box-Muller pair as for D2Q9.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import normals
+from .theory import cholesky_psd
+
+SIGMA_S2 = 1.0 / 3.0
+TAG_A, TAG_B = 4, 5
+
+
+def _velocities() -> np.ndarray:
+    """Rest, the six faces (+x, -x, +y, -y, +z, -z), then the twelve edges in the (x,y),
+    (y,z), (z,x) planes with signs (++, +-, -+, --)."""
+    c = [(0, 0, 0)]
+    for a in range(3):
+        for s in (1, -1):
+            v = [0, 0, 0]
+            v[a] = s
+            c.append(tuple(v))
+    for a, b in ((0, 1), (1, 2), (2, 0)):
+        for s in (1, -1):
+            for t in (1, -1):
+                v = [0, 0, 0]
+                v[a], v[b] = s, t
+                c.append(tuple(v))
+    return np.array(c, dtype=np.int64)
+
+
+#: D3Q19 velocities c_i.
+C = _velocities()
+#: Weights 1/3 (rest), 1/18 (faces), 1/36 (edges).
+W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+Q = 19
+#: opposite direction: C[OPP[i]] = -C[i]
+OPP = np.array([int(np.where((C == -C[i]).all(axis=1))[0][0]) for i in range(Q)])
+
+
+def basis_T() -> np.ndarray:
+    """The nineteen mode polynomials (Duenweg, Schiller & Ladd 2007, Table I) on C:
+    rho; j; the bulk mode c^2 - 1; five shear modes; six third-order ghosts; three
+    fourth-order ghosts."""
+    cx, cy, cz = (C[:, k].astype(np.float64) for k in range(3))
+    c2 = cx * cx + cy * cy + cz * cz
+    rows = [
+        np.ones(Q), cx, cy, cz,                          # 0: rho, 1..3: j
+        c2 - 1,                                          # 4: bulk
+        3 * cx * cx - c2, cy * cy - cz * cz,             # 5, 6: shear, diagonal
+        cx * cy, cy * cz, cz * cx,                       # 7..9: shear, off-diagonal
+        (3 * c2 - 5) * cx, (3 * c2 - 5) * cy, (3 * c2 - 5) * cz,        # 10..12
+        (cy * cy - cz * cz) * cx, (cz * cz - cx * cx) * cy, (cx * cx - cy * cy) * cz,  # 13..15
+        3 * c2 * c2 - 6 * c2 + 1,                        # 16: isotropic fourth order
+        (2 * c2 - 3) * (3 * cx * cx - c2), (2 * c2 - 3) * (cy * cy - cz * cz),    # 17, 18
+    ]
+    return np.array(rows)
+
+
+T = basis_T()
+#: N_a = sum_i w_i T_ai^2 (the scalar product of Eq. scalar-prod with the D3Q19 weights).
+N = (T * T * W[None, :]).sum(axis=1)
+#: (T^-1)_ia = w_i T_ai / N_a.
+TINV = (W[:, None] * T.T) / N[None, :]
+
+
+def lambdas(tau_s: float, tau_b: float, tau_ghost: float) -> np.ndarray:
+    """lambda_a = -1/tau: 0 for the conserved modes, bulk, five shear, nine ghosts."""
+    return np.array([0.0] * 4 + [-1.0 / tau_b] + [-1.0 / tau_s] * 5 + [-1.0 / tau_ghost] * 9)
+
+
+class Model:
+    """One homogeneous run on D3Q19: rho0, cs2 (p0 = cs2 rho), kappa, kT, relaxation times."""
+
+    def __init__(self, rho0=1.0, cs2=SIGMA_S2, kappa=0.0, kT=0.0, tau_s=1.0, tau_b=1.0, tau_ghost=1.0):
+        self.rho0, self.cs2, self.kappa, self.kT = float(rho0), float(cs2), float(kappa), float(kT)
+        self.tau_s, self.tau_b, self.tau_ghost = float(tau_s), float(tau_b), float(tau_ghost)
+        self.lam = lambdas(tau_s, tau_b, tau_ghost)
+
+    def d(self) -> float:
+        """Weight of the pressure deviation in the rest moments: 3 (cs2 - sigma_s^2)."""
+        return 3.0 * (self.cs2 - SIGMA_S2)
+
+    def mbar(self) -> np.ndarray:
+        """Rest moments: rho0, e4 = d rho0, e16 = -d rho0 (the equilibrium at u = 0 and
+        uniform density), the rest zero."""
+        m = np.zeros(Q)
+        m[0] = self.rho0
+        m[4] = self.d() * self.rho0
+        m[16] = -self.d() * self.rho0
+        return m
+
+    def fbar(self) -> np.ndarray:
+        return TINV @ self.mbar()
+
+    def Omega0(self) -> np.ndarray:
+        """Linearised collision operator at k = 0 (the analogue of Eq. coll-op-yeo): mode a
+        relaxes at lambda_a towards its equilibrium, which for e4 and e16 follows the
+        density through p0 = cs2 rho."""
+        O = np.diag(self.lam)
+        O[4, 0] = -self.lam[4] * self.d()
+        O[16, 0] = self.lam[16] * self.d()
+        return O
+
+    def G0(self) -> np.ndarray:
+        """Equal-time mode correlations of the ansatz <df_i df_j> = (S/rho0) fbar_i delta_ij,
+        Eq. (f-correl-yeo), at k = 0 with S = rho0 kT / cs2 (Eq. struct-fact)."""
+        S = self.rho0 * self.kT / self.cs2
+        return (S / self.rho0) * (T @ np.diag(self.fbar()) @ T.T)
+
+    def Xi_zero(self) -> np.ndarray:
+        """Xi(0) = -G Omega^T - Omega G - Omega G Omega^T, Eq. (noise-matrix-k0)."""
+        G, O = self.G0(), self.Omega0()
+        return -G @ O.T - O @ G - O @ G @ O.T
+
+    def noise_factor(self) -> np.ndarray:
+        """19x19 L with L L^T = Xi(0): Cholesky of the block of the non-conserved modes
+        4..18 (Sec. IV), rows 0..3 zero."""
+        L = np.zeros((Q, Q))
+        L[4:, 4:] = cholesky_psd(self.Xi_zero()[4:, 4:])
+        return L
+
+
+# --- the step -------------------------------------------------------------------------
+
+def _shift(a: np.ndarray, c) -> np.ndarray:
+    """b(r) = a(r + c) on the periodic box, a[z, y, x]."""
+    return np.roll(a, shift=(-int(c[2]), -int(c[1]), -int(c[0])), axis=(0, 1, 2))
+
+
+def density_stencils(rho: np.ndarray):
+    """Laplacian sum_{i != 0} w_i [rho(r + c_i) + rho(r - c_i) - 2 rho(r)] / sigma_s^2 and the
+    gradient 3 sum_i w_i c_i rho(r + c_i) (Appendix B's isotropic stencils, D3Q19 weights)."""
+    lap = np.zeros_like(rho)
+    grad = np.zeros((3,) + rho.shape)
+    for i in range(1, Q):
+        ri = _shift(rho, C[i])
+        lap += W[i] * (ri + _shift(rho, C[OPP[i]]) - 2.0 * rho) / SIGMA_S2
+        for k in range(3):
+            grad[k] += 3.0 * W[i] * C[i, k] * ri
+    return lap, grad
+
+
+def equilibrium_moments(rho, j, lap, grad, cs2, kappa) -> np.ndarray:
+    """m^eq[a, ...] for each node: rho, j, then the second-order moments of
+    P^th_ab + rho u_a u_b with P^th of Eq. (press-ten) for p0 = cs2 rho,
+        P^th_ab = (p0 - kappa rho lap rho - kappa |grad rho|^2 / 2) delta_ab
+                  + kappa d_a rho d_b rho,
+    and the fourth-order ghost e16 of the module's reading; the other ghosts zero."""
+    u = j / rho
+    P = np.zeros((3, 3) + rho.shape)
+    g2 = (grad * grad).sum(axis=0)
+    piso = cs2 * rho - kappa * rho * lap - 0.5 * kappa * g2
+    for a in range(3):
+        for b in range(3):
+            P[a, b] = rho * u[a] * u[b] + kappa * grad[a] * grad[b]
+        P[a, a] = P[a, a] + piso
+    m = np.zeros((Q,) + rho.shape)
+    m[0] = rho
+    m[1:4] = j
+    m[4] = P[0, 0] + P[1, 1] + P[2, 2] - rho
+    m[5] = 2 * P[0, 0] - P[1, 1] - P[2, 2]
+    m[6] = P[1, 1] - P[2, 2]
+    m[7], m[8], m[9] = P[0, 1], P[1, 2], P[2, 0]
+    m[16] = -3.0 * (cs2 * rho - SIGMA_S2 * rho - kappa * rho * lap) - 4.5 * kappa * g2
+    return m
+
+
+def collide(f: np.ndarray, model: Model, xi=None) -> np.ndarray:
+    """Post-collision populations f*_i = (T^-1 m*)_i with
+    m*_a = m_a + lambda_a (m_a - m^eq_a) + xi_a, Eq. (fluct-lin-lbe)."""
+    m = np.einsum("ai,i...->a...", T, f)
+    rho = m[0]
+    lap, grad = density_stencils(rho)
+    meq = equilibrium_moments(rho, m[1:4], lap, grad, model.cs2, model.kappa)
+    ms = m + model.lam[:, None, None, None] * (m - meq)
+    if xi is not None:
+        ms = ms + xi
+    return np.einsum("ia,a...->i...", TINV, ms)
+
+
+def stream(fs: np.ndarray) -> np.ndarray:
+    """f_i(r + c_i, t + 1) = f*_i(r, t), Eq. (gen-lbe), periodic."""
+    out = np.empty_like(fs)
+    for i in range(Q):
+        out[i] = np.roll(fs[i], shift=(int(C[i, 2]), int(C[i, 1]), int(C[i, 0])), axis=(0, 1, 2))
+    return out
+
+
+def step(f: np.ndarray, model: Model, xi=None) -> np.ndarray:
+    return stream(collide(f, model, xi))
+
+
+# --- noise of Sec. IV -------------------------------------------------------------------
+
+def noise_normals(nx, ny, nz, seed: int, step_index: int) -> np.ndarray:
+    """nu[a, z, y, x] for a = 4..18 (rows 0..3 zero): the counter layout of the module
+    docstring."""
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.uint32)
+    ga = normals(idx, seed, step_index, TAG_A)
+    gb = normals(idx, seed, step_index, TAG_B)
+    nu = np.zeros((Q, n))
+    nu[4:12] = ga.T
+    nu[12:19] = gb[:, :7].T
+    return nu.reshape(Q, nz, ny, nx)
+
+
+def noise_lw(model: Model, nx, ny, nz, seed: int, step_index: int, L=None) -> np.ndarray:
+    """xi = L nu with L L^T = Xi(0), independently at every node."""
+    if L is None:
+        L = model.noise_factor()
+    nu = noise_normals(nx, ny, nz, seed, step_index)
+    return np.einsum("ab,b...->a...", L, nu)
+
+
+NOISE_OFF, NOISE_LW = 0, 1
+
+
+class Lattice:
+    """A periodic nx x ny x nz D3Q19 lattice: f[19, nz, ny, nx] pre-collision populations,
+    t the index of the next collision (it keys the random numbers)."""
+
+    def __init__(self, nx, ny, nz, rho0=1.0, cs2=SIGMA_S2, seed=42):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.seed = int(seed)
+        self.model = Model(rho0=rho0, cs2=cs2)
+        self.mode = NOISE_OFF
+        self.t = 0
+        self.f = np.broadcast_to(self.model.fbar()[:, None, None, None], (Q, nz, ny, nx)).copy()
+        self._L = None
+
+    def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+        self.model = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
+        self.mode = int(noise_mode)
+        self._L = self.model.noise_factor() if (self.mode == NOISE_LW and kT > 0) else None
+
+    def step(self, nsteps=1):
+        for _ in range(int(nsteps)):
+            xi = None
+            if self._L is not None:
+                xi = noise_lw(self.model, self.nx, self.ny, self.nz, self.seed, self.t, self._L)
+            self.f = step(self.f, self.model, xi)
+            self.t += 1
+        return self
+
+    def moments(self) -> np.ndarray:
+        return np.einsum("ai,i...->a...", T, self.f)

@@ -242,6 +242,20 @@ def noise_normals(nx, ny, nz, seed: int, step_index: int) -> np.ndarray:
     return nu.reshape(Q, nz, ny, nx)
 
 
+def noise_lw_nodes(model: Model, nodes: np.ndarray, seed: int, step_index: int, L=None) -> np.ndarray:
+    """xi[a, ...] = L nu at the given global node indices (any shape): the draws of
+    noise_normals() for those nodes."""
+    if L is None:
+        L = model.noise_factor()
+    idx = np.ascontiguousarray(nodes, dtype=np.uint32).ravel()
+    ga = normals(idx, seed, step_index, TAG_A)
+    gb = normals(idx, seed, step_index, TAG_B)
+    nu = np.zeros((Q, idx.size))
+    nu[4:12] = ga.T
+    nu[12:19] = gb[:, :7].T
+    return (L @ nu).reshape((Q,) + np.shape(nodes))
+
+
 def noise_lw(model: Model, nx, ny, nz, seed: int, step_index: int, L=None) -> np.ndarray:
     """xi = L nu with L L^T = Xi(0), independently at every node."""
     if L is None:

@@ -123,6 +123,22 @@ def load(path: str = LIB_PATH):
         "lb_server_set_admission": (c_int, [vp, c_i64, c_int]),
         "lb_selftest_bounded_wait": (c_int, [c_dbl, ctypes.POINTER(c_int)]),
         "lb_server_last_error": (ctypes.c_char_p, [vp]),
+        "lb3_workspace_bytes": (c_sz, [c_int, c_int, c_int, c_int]),
+        "lb3_create": (c_int, [c_int, c_int, c_int, c_int, c_u64, c_dbl, c_dbl, ctypes.POINTER(vp)]),
+        "lb3_destroy": (c_int, [vp]),
+        "lb3_set_stream": (c_int, [vp, vp]),
+        "lb3_set_params": (c_int, [vp, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_int]),
+        "lb3_step": (c_int, [vp, c_i64]),
+        "lb3_get_time": (c_int, [vp, i64p]),
+        "lb3_set_populations": (c_int, [vp, vp, c_int, c_i64]),
+        "lb3_get_populations": (c_int, [vp, vp, c_int]),
+        "lb3_sums": (c_int, [vp, dp]),
+        "lb3_set_kernel_timing": (c_int, [vp, c_int]),
+        "lb3_kernel_time": (c_int, [vp, dp, i64p]),
+        "lb3_launch_count": (c_int, [vp, i64p]),
+        "lb3_synchronize": (c_int, [vp]),
+        "lb3_last_error": (ctypes.c_char_p, [vp]),
+        "lb3_noise_matrix": (c_int, [c_dbl] * 6 + [dp]),
     }
     for name, (res, args) in proto.items():
         fn = getattr(L, name)
@@ -650,3 +666,131 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# --- D3Q19 lattice (include/lbfluct3d.h) ---------------------------------------------------
+
+def _check3(rc, ctx=None):
+    if rc < 0:
+        msg = load().lb3_last_error(ctx)
+        raise LBError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def lb3_workspace_bytes(nx, ny, nz, precision=LB_FP32):
+    return load().lb3_workspace_bytes(nx, ny, nz, precision)
+
+
+def lb3_create(nx, ny, nz, precision=LB_FP32, seed=42, rho0=1.0, cs2=1.0 / 3.0):
+    out = ctypes.c_void_p()
+    _check3(load().lb3_create(nx, ny, nz, precision, seed, rho0, cs2, ctypes.byref(out)))
+    return out.value
+
+
+def lb3_destroy(ctx):
+    return _check3(load().lb3_destroy(ctx))
+
+
+def lb3_set_stream(ctx, stream):
+    return _check3(load().lb3_set_stream(ctx, stream), ctx)
+
+
+def lb3_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+    return _check3(load().lb3_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode), ctx)
+
+
+def lb3_step(ctx, nsteps):
+    return _check3(load().lb3_step(ctx, nsteps), ctx)
+
+
+def lb3_get_time(ctx):
+    t = ctypes.c_int64()
+    _check3(load().lb3_get_time(ctx, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def lb3_set_populations(ctx, f, loc, t):
+    return _check3(load().lb3_set_populations(ctx, _ptr(f), loc, t), ctx)
+
+
+def lb3_get_populations(ctx, f, loc):
+    return _check3(load().lb3_get_populations(ctx, _ptr(f), loc), ctx)
+
+
+def lb3_sums(ctx, sums):
+    return _check3(load().lb3_sums(ctx, _dptr(sums)), ctx)
+
+
+def lb3_set_kernel_timing(ctx, every):
+    return _check3(load().lb3_set_kernel_timing(ctx, every), ctx)
+
+
+def lb3_kernel_time(ctx):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check3(load().lb3_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def lb3_launch_count(ctx):
+    n = ctypes.c_int64()
+    _check3(load().lb3_launch_count(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def lb3_synchronize(ctx):
+    return _check3(load().lb3_synchronize(ctx), ctx)
+
+
+def lb3_noise_matrix(rho0, cs2, kT, tau_s, tau_b, tau_ghost):
+    X = np.zeros((19, 19))
+    _check3(load().lb3_noise_matrix(rho0, cs2, kT, tau_s, tau_b, tau_ghost, _dptr(X)))
+    return X
+
+
+class Lattice3:
+    """One periodic D3Q19 lattice on the current CUDA device; its work runs on the given
+    stream (torch.cuda.current_stream() at construction, unless given)."""
+
+    def __init__(self, nx, ny, nz, seed=42, rho0=1.0, cs2=1.0 / 3.0, stream=None, precision=LB_FP32):
+        import torch
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.ctx = lb3_create(self.nx, self.ny, self.nz, precision, seed, rho0, cs2)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        lb3_set_stream(self.ctx, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lb3_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+        lb3_set_params(self.ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
+
+    def step(self, n=1):
+        lb3_step(self.ctx, n)
+
+    @property
+    def t(self):
+        return lb3_get_time(self.ctx)
+
+    def set_populations(self, f, t=0):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (19, self.nz, self.ny, self.nx)
+        lb3_set_populations(self.ctx, f, LB_HOST, t)
+
+    def populations(self):
+        f = np.empty((19, self.nz, self.ny, self.nx))
+        lb3_get_populations(self.ctx, f, LB_HOST)
+        return f
+
+    def sums(self):
+        s = np.zeros(4)
+        lb3_sums(self.ctx, s)
+        return s

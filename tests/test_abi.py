@@ -1,5 +1,6 @@
 """The C ABI without a GPU: the library loads, exports every entry point declared in
-include/lbfluct.h, and its host-side FP64 theory agrees with the oracle."""
+include/lbfluct.h and include/lbfluct3d.h, and its host-side FP64 theory agrees with the
+oracle."""
 import os
 import re
 
@@ -21,15 +22,18 @@ def lib():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "lbfluct.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(lb_[a-z0-9_]+)\s*\(", src)
+    names = []
+    for h in ("lbfluct.h", "lbfluct3d.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(lb3?_[a-z0-9_]+)\s*\(", src)
     return sorted(set(names))
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = _declared()
     assert "lb_create" in names and "lb_step" in names and "lb_structure_factor" in names
+    assert "lb3_create" in names and "lb3_step" in names and "lb3_noise_matrix" in names
     for n in names:
         assert hasattr(lib, n), n
 
@@ -91,3 +95,12 @@ def test_psd_check_agrees_with_oracle_over_a_parameter_grid(lib):
                 assert rc == lbf.LB_ENOTPSD, (cs, kappa, e)
             elif e > 1e-9 * scale:
                 assert rc == lbf.LB_OK, (cs, kappa, e)
+
+
+@pytest.mark.parametrize("cs2,tau", [(1 / 3, (1.0, 1.0, 1.0)), (0.2, (0.8, 1.1, 0.9)), (0.12, (1.3, 0.7, 1.05))])
+def test_library_d3q19_noise_matrix_matches_oracle(lib, cs2, tau):
+    # the library's closed-form Xi(0) against the oracle's FDT construction from the ansatz
+    from oracle import d3q19 as d3
+    m = d3.Model(rho0=0.9, cs2=cs2, kappa=0.03, kT=3e-5, tau_s=tau[0], tau_b=tau[1], tau_ghost=tau[2])
+    X = lbf.lb3_noise_matrix(0.9, cs2, 3e-5, *tau)
+    np.testing.assert_allclose(X, m.Xi_zero(), rtol=1e-12, atol=1e-13 * np.abs(X).max())

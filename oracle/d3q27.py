@@ -1,0 +1,277 @@
+"""FP64 CPU oracle of the fluctuating non-ideal model on the D3Q27 lattice.
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` are the only callers; the product library shares no code with it.
+
+Sec. IV of Gross, Adhikari, Cates & Varnik (arXiv:1009.0254) states that the noise
+derivation holds on any DdQn lattice.  This module carries the D2Q9 model of the paper to
+D3Q27 with the steps of ``oracle.d3q19``:
+
+  * the basis: products p_a(c_x) p_b(c_y) p_c(c_z) of the polynomials p_0 = 1, p_1 = c,
+    p_2 = 3c^2 - 1, orthogonal under the D1Q3 weights (2/3, 1/6, 1/6) whose products are the
+    D3Q27 weights; the c_z-independent members (p_a(c_x) p_b(c_y)) span the D2Q9 basis of
+    the paper's Table I (e = p_2x + p_2y, p_ww = (p_2x - p_2y)/3, q_x = p_1x p_2y, eps =
+    2 p_2x p_2y, ...), so the paper's basis is the two-dimensional member of this family;
+  * the fluctuating collision of Eq. (fluct-lin-lbe): the bulk mode p_2x + p_2y + p_2z
+    relaxes at lambda_b, the traceless second-order modes at lambda_s, all higher modes
+    at one ghost rate;
+  * the pressure tensor of Eq. (press-ten) with p0 = cs2 rho in the second moments;
+  * the long-wavelength noise Xi(0) of Eq. (noise-matrix-k0) from the ansatz Eq.
+    (f-correl-yeo), factored by Cholesky (Sec. IV).
+
+Readings where the paper is silent (also listed in the design notes):
+  * second moments: sum_i f^eq_i c_ia c_ib = P^th_ab + rho u_a u_b (as for D3Q19);
+  * ghost equilibria are those of the equilibrium that carries the pressure on the moving
+    velocities (w_i [3 p + 3 c.j + (9/2)(rho uu + kappa grad rho grad rho):cc
+    - (3/2)(rho u^2 + kappa |grad rho|^2)], the remainder at rest), except the three
+    fourth-order modes p_2a p_2b (a != b), which take Table II's correction:
+    m^eq(p_2a p_2b) = -3 (p0 - rho/3 - kappa rho lap rho) - (3/2) kappa |grad rho|^2, so that
+    a field uniform and mirror-symmetric along one axis evolves, at equal relaxation times,
+    as the D2Q9 model of Table II; the sixth-order mode has
+    m^eq(p_2x p_2y p_2z) = 3 (p0 - rho/3 - kappa rho lap rho) - (3/2) kappa |grad rho|^2 and
+    every other ghost equilibrium is zero;
+  * the Laplacian and gradient are Appendix B's isotropic stencils with the D3Q27 weights.
+
+Indices: velocity i = 9 ix + 3 iy + iz with c = (v[ix], v[iy], v[iz]), v = (0, 1, -1); mode
+a = 9 ax + 3 ay + az for p_ax(c_x) p_ay(c_y) p_az(c_z).  f[i, z, y, x].
+Random numbers: three Philox4x32-10 draws per node and step with counter (node, t mod 2^32,
+t div 2^32, tag), node = (z ny + y) nx + x, tags 6, 7, 8; their 24 normals in order go to the
+23 non-conserved modes in increasing mode index (the last normal unused).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from . import normals
+from .theory import cholesky_psd
+
+SIGMA_S2 = 1.0 / 3.0
+Q = 27
+TAGS = (6, 7, 8)
+_V = (0, 1, -1)
+
+#: velocities c_i, i = 9 ix + 3 iy + iz
+C = np.array([(_V[a], _V[b], _V[c]) for a, b, c in itertools.product(range(3), repeat=3)], dtype=np.int64)
+_W1 = {0: 2 / 3, 1: 1 / 6, -1: 1 / 6}
+#: weights: products of the D1Q3 weights (8/27, 2/27, 1/54, 1/216)
+W = np.array([_W1[int(a)] * _W1[int(b)] * _W1[int(c)] for a, b, c in C])
+OPP = np.array([int(np.where((C == -C[i]).all(axis=1))[0][0]) for i in range(Q)])
+#: mode labels (ax, ay, az)
+MODES = list(itertools.product(range(3), repeat=3))
+IDX = {m: k for k, m in enumerate(MODES)}
+CONSERVED = [IDX[(0, 0, 0)], IDX[(1, 0, 0)], IDX[(0, 1, 0)], IDX[(0, 0, 1)]]
+SECOND_DIAG = [IDX[(2, 0, 0)], IDX[(0, 2, 0)], IDX[(0, 0, 2)]]
+SECOND_OFF = [IDX[(1, 1, 0)], IDX[(0, 1, 1)], IDX[(1, 0, 1)]]
+FOURTH_PAIR = [IDX[(2, 2, 0)], IDX[(0, 2, 2)], IDX[(2, 0, 2)]]
+SIXTH = IDX[(2, 2, 2)]
+NONCONSERVED = [k for k in range(Q) if k not in CONSERVED]
+
+
+def _p(a, c):
+    c = c.astype(np.float64)
+    return np.ones_like(c) if a == 0 else (c if a == 1 else 3 * c * c - 1)
+
+
+def basis_T() -> np.ndarray:
+    """T_ai = p_ax(c_ix) p_ay(c_iy) p_az(c_iz)."""
+    return np.array([_p(a, C[:, 0]) * _p(b, C[:, 1]) * _p(c, C[:, 2]) for a, b, c in MODES])
+
+
+T = basis_T()
+N = (T * T * W[None, :]).sum(axis=1)
+TINV = (W[:, None] * T.T) / N[None, :]
+
+
+def relaxation_matrix(tau_s, tau_b, tau_ghost) -> np.ndarray:
+    """Lambda with m* = m + Lambda (m - m^eq) + xi: lambda_b on the bulk direction (1, 1, 1)/3
+    of the three p_2a modes, lambda_s on its traceless complement and on p_1a p_1b, the ghost
+    rate on every mode above second order, zero on the conserved modes."""
+    lb, ls, lg = -1.0 / tau_b, -1.0 / tau_s, -1.0 / tau_ghost
+    L = np.zeros((Q, Q))
+    for k in range(Q):
+        if k in CONSERVED:
+            continue
+        L[k, k] = lg
+    for k in SECOND_OFF:
+        L[k, k] = ls
+    for a in SECOND_DIAG:
+        for b in SECOND_DIAG:
+            L[a, b] = (lb - ls) / 3.0 + (ls if a == b else 0.0)
+    return L
+
+
+class Model:
+    """One homogeneous run on D3Q27: rho0, cs2 (p0 = cs2 rho), kappa, kT, relaxation times."""
+
+    def __init__(self, rho0=1.0, cs2=SIGMA_S2, kappa=0.0, kT=0.0, tau_s=1.0, tau_b=1.0, tau_ghost=1.0):
+        self.rho0, self.cs2, self.kappa, self.kT = float(rho0), float(cs2), float(kappa), float(kT)
+        self.tau_s, self.tau_b, self.tau_ghost = float(tau_s), float(tau_b), float(tau_ghost)
+        self.Lam = relaxation_matrix(tau_s, tau_b, tau_ghost)
+
+    def d(self) -> float:
+        return 3.0 * (self.cs2 - SIGMA_S2)
+
+    def mbar(self) -> np.ndarray:
+        """Rest moments: the equilibrium at u = 0 and uniform rho0."""
+        m = np.zeros(Q)
+        m[IDX[(0, 0, 0)]] = self.rho0
+        d = self.d() * self.rho0
+        for k in SECOND_DIAG:
+            m[k] = d
+        for k in FOURTH_PAIR:
+            m[k] = -d
+        m[SIXTH] = d
+        return m
+
+    def fbar(self) -> np.ndarray:
+        return TINV @ self.mbar()
+
+    def J0(self) -> np.ndarray:
+        """d m^eq / d m at the rest state (only the density column is non-zero beyond the
+        conserved modes)."""
+        J = np.zeros((Q, Q))
+        for k in CONSERVED:
+            J[k, k] = 1.0
+        d = self.d()
+        for k in SECOND_DIAG:
+            J[k, 0] = d
+        for k in FOURTH_PAIR:
+            J[k, 0] = -d
+        J[SIXTH, 0] = d
+        return J
+
+    def Omega0(self) -> np.ndarray:
+        """Linearised collision at k = 0: Omega = Lambda (I - J0)."""
+        return self.Lam @ (np.eye(Q) - self.J0())
+
+    def G0(self) -> np.ndarray:
+        """(S/rho0) T diag(fbar) T^T with S = rho0 kT / cs2 (Eqs. f-correl-yeo, struct-fact)."""
+        S = self.rho0 * self.kT / self.cs2
+        return (S / self.rho0) * (T @ np.diag(self.fbar()) @ T.T)
+
+    def Xi_zero(self) -> np.ndarray:
+        """Xi(0) = -G Omega^T - Omega G - Omega G Omega^T, Eq. (noise-matrix-k0)."""
+        G, O = self.G0(), self.Omega0()
+        return -G @ O.T - O @ G - O @ G @ O.T
+
+    def noise_factor(self) -> np.ndarray:
+        """27 x 27 L, L L^T = Xi(0): Cholesky of the non-conserved block in mode order."""
+        L = np.zeros((Q, Q))
+        nc = NONCONSERVED
+        L[np.ix_(nc, nc)] = cholesky_psd(self.Xi_zero()[np.ix_(nc, nc)])
+        return L
+
+
+# --- the step -------------------------------------------------------------------------------
+
+def _shift(a, c):
+    return np.roll(a, shift=(-int(c[2]), -int(c[1]), -int(c[0])), axis=(0, 1, 2))
+
+
+def density_stencils(rho):
+    """Appendix B's Laplacian and the isotropic gradient with the D3Q27 weights."""
+    lap = np.zeros_like(rho)
+    grad = np.zeros((3,) + rho.shape)
+    for i in range(1, Q):
+        ri = _shift(rho, C[i])
+        lap += W[i] * (ri + _shift(rho, C[OPP[i]]) - 2.0 * rho) / SIGMA_S2
+        for k in range(3):
+            grad[k] += 3.0 * W[i] * C[i, k] * ri
+    return lap, grad
+
+
+def equilibrium_moments(rho, j, lap, grad, cs2, kappa) -> np.ndarray:
+    """m^eq[a, ...]: rho, j, the second-order modes of P^th + rho u u (Eq. press-ten,
+    p0 = cs2 rho), and the fourth- and sixth-order ghosts of the module's reading."""
+    u = j / rho
+    g2 = (grad * grad).sum(axis=0)
+    piso = cs2 * rho - kappa * rho * lap - 0.5 * kappa * g2
+    Pi = np.zeros((3, 3) + rho.shape)
+    for a in range(3):
+        for b in range(3):
+            Pi[a, b] = rho * u[a] * u[b] + kappa * grad[a] * grad[b]
+        Pi[a, a] = Pi[a, a] + piso
+    iso = cs2 * rho - SIGMA_S2 * rho - kappa * rho * lap
+    m = np.zeros((Q,) + rho.shape)
+    m[IDX[(0, 0, 0)]] = rho
+    m[IDX[(1, 0, 0)]], m[IDX[(0, 1, 0)]], m[IDX[(0, 0, 1)]] = j[0], j[1], j[2]
+    for a, k in enumerate(SECOND_DIAG):               # sum_i f_i (3 c_a^2 - 1) = 3 Pi_aa - rho
+        m[k] = 3.0 * Pi[a, a] - rho
+    m[IDX[(1, 1, 0)]], m[IDX[(0, 1, 1)]], m[IDX[(1, 0, 1)]] = Pi[0, 1], Pi[1, 2], Pi[0, 2]
+    for k in FOURTH_PAIR:
+        m[k] = -3.0 * iso - 1.5 * kappa * g2
+    m[SIXTH] = 3.0 * iso - 1.5 * kappa * g2
+    return m
+
+
+def collide(f, model: Model, xi=None):
+    m = np.einsum("ai,i...->a...", T, f)
+    rho = m[0]
+    lap, grad = density_stencils(rho)
+    j = np.array([m[IDX[(1, 0, 0)]], m[IDX[(0, 1, 0)]], m[IDX[(0, 0, 1)]]])
+    meq = equilibrium_moments(rho, j, lap, grad, model.cs2, model.kappa)
+    ms = m + np.einsum("ab,b...->a...", model.Lam, m - meq)
+    if xi is not None:
+        ms = ms + xi
+    return np.einsum("ia,a...->i...", TINV, ms)
+
+
+def stream(fs):
+    out = np.empty_like(fs)
+    for i in range(Q):
+        out[i] = np.roll(fs[i], shift=(int(C[i, 2]), int(C[i, 1]), int(C[i, 0])), axis=(0, 1, 2))
+    return out
+
+
+def step(f, model: Model, xi=None):
+    return stream(collide(f, model, xi))
+
+
+# --- noise of Sec. IV ---------------------------------------------------------------------
+
+def noise_lw_nodes(model: Model, nodes, seed: int, step_index: int, L=None) -> np.ndarray:
+    """xi[a, ...] = L nu at the given global node indices."""
+    if L is None:
+        L = model.noise_factor()
+    idx = np.ascontiguousarray(nodes, dtype=np.uint32).ravel()
+    g = np.concatenate([normals(idx, seed, step_index, t) for t in TAGS], axis=1)     # (n, 24)
+    nu = np.zeros((Q, idx.size))
+    nu[NONCONSERVED] = g[:, :len(NONCONSERVED)].T
+    return (L @ nu).reshape((Q,) + np.shape(nodes))
+
+
+NOISE_OFF, NOISE_LW = 0, 1
+
+
+class Lattice:
+    """A periodic nx x ny x nz D3Q27 lattice: f[27, nz, ny, nx] pre-collision populations."""
+
+    def __init__(self, nx, ny, nz, rho0=1.0, cs2=SIGMA_S2, seed=42):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.seed = int(seed)
+        self.model = Model(rho0=rho0, cs2=cs2)
+        self.mode = NOISE_OFF
+        self.t = 0
+        self.f = np.broadcast_to(self.model.fbar()[:, None, None, None], (Q, nz, ny, nx)).copy()
+        self._L = None
+
+    def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
+        self.model = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
+        self.mode = int(noise_mode)
+        self._L = self.model.noise_factor() if (self.mode == NOISE_LW and kT > 0) else None
+
+    def step(self, nsteps=1):
+        n = self.nx * self.ny * self.nz
+        nodes = np.arange(n, dtype=np.uint32).reshape(self.nz, self.ny, self.nx)
+        for _ in range(int(nsteps)):
+            xi = None
+            if self._L is not None:
+                xi = noise_lw_nodes(self.model, nodes, self.seed, self.t, self._L)
+            self.f = step(self.f, self.model, xi)
+            self.t += 1
+        return self
+
+    def moments(self):
+        return np.einsum("ai,i...->a...", T, self.f)

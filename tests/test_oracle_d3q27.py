@@ -1,0 +1,296 @@
+"""Pins of the D3Q27 oracle (oracle/d3q27.py): the lattice's isotropy, the product basis
+(orthogonality, its norms, the D2Q9 basis of Table I as its c_z-independent members), the
+second and third moments of the equilibrium against Eq. (press-ten), the rest state, exact
+agreement with the independent D2Q9 C core on fields uniform along an axis, Navier-Stokes
+shear and sound, the ansatz covariance as a rank-one update of a diagonal, the ideal-gas
+noise in closed form, the fluctuation-dissipation balance of Xi(0) by simulation of the
+k = 0 dynamics, and equipartition of the ideal fluctuating gas."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import d3q27 as d
+from oracle import theory as th
+from paper_1009_0254_gb300 import synth
+
+S2 = 1.0 / 3.0
+
+
+def test_lattice_is_the_product_of_d1q3_and_isotropic_to_fourth_order():
+    C, W = d.C.astype(float), d.W
+    assert len({tuple(c) for c in d.C}) == 27 and (d.C[d.OPP] == -d.C).all()
+    assert abs(W.sum() - 1) < 1e-15
+    np.testing.assert_allclose(sorted(set(np.round(W, 15))), sorted({8 / 27, 2 / 27, 1 / 54, 1 / 216}))
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", W, C, C), S2 * np.eye(3), atol=1e-16)
+    dd = np.eye(3)
+    iso4 = S2 ** 2 * (np.einsum("ab,cd->abcd", dd, dd) + np.einsum("ac,bd->abcd", dd, dd)
+                      + np.einsum("ad,bc->abcd", dd, dd))
+    np.testing.assert_allclose(np.einsum("i,ia,ib,ic,id->abcd", W, C, C, C, C), iso4, atol=1e-16)
+
+
+def test_product_basis_is_orthogonal_and_contains_the_d2q9_basis():
+    G = (d.T * d.W) @ d.T.T
+    assert np.abs(G - np.diag(np.diag(G))).max() < 1e-15
+    n1 = [1.0, 1 / 3, 2.0]                          # D1Q3 norms of 1, c, 3c^2 - 1
+    np.testing.assert_allclose(d.N, [n1[a] * n1[b] * n1[c] for a, b, c in d.MODES], rtol=1e-14)
+    # Table I's polynomials on the c_z = 0 velocities are the (a, b, 0) product modes
+    sel = d.C[:, 2] == 0
+    cx, cy = d.C[sel, 0].astype(float), d.C[sel, 1].astype(float)
+    c2 = cx * cx + cy * cy
+    row = lambda m: d.T[d.IDX[m]][sel]
+    np.testing.assert_allclose(3 * c2 - 2, row((2, 0, 0)) + row((0, 2, 0)))
+    np.testing.assert_allclose(2 * cx * cx - c2, (row((2, 0, 0)) - row((0, 2, 0))) / 3)
+    np.testing.assert_allclose(cx * cy, row((1, 1, 0)))
+    np.testing.assert_allclose((3 * c2 - 4) * cx, row((1, 2, 0)))
+    np.testing.assert_allclose((3 * c2 - 4) * cy, row((2, 1, 0)))
+    np.testing.assert_allclose(9 * c2 * c2 - 15 * c2 + 2, 2 * row((2, 2, 0)))
+
+
+def test_relaxation_rates_on_the_bulk_and_traceless_modes():
+    L = d.relaxation_matrix(0.8, 1.1, 0.9)
+    v = np.zeros(27)
+    for k in d.SECOND_DIAG:
+        v[k] = 1.0
+    np.testing.assert_allclose(L @ v, -v / 1.1, atol=1e-15)            # bulk: p_2x + p_2y + p_2z
+    w = np.zeros(27)
+    w[d.SECOND_DIAG[0]], w[d.SECOND_DIAG[1]] = 1.0, -1.0
+    np.testing.assert_allclose(L @ w, -w / 0.8, atol=1e-15)            # traceless
+    assert L[d.IDX[(1, 1, 0)], d.IDX[(1, 1, 0)]] == -1 / 0.8
+    assert L[d.IDX[(2, 1, 1)], d.IDX[(2, 1, 1)]] == -1 / 0.9
+    assert np.all(L[d.CONSERVED] == 0)
+
+
+def test_equilibrium_carries_the_pressure_tensor():
+    rng = np.random.default_rng(1)
+    shape = (4, 3, 5)
+    rho = 1.0 + 0.2 * rng.random(shape)
+    j = 0.05 * rng.standard_normal((3,) + shape)
+    lap = rng.standard_normal(shape)
+    grad = 0.3 * rng.standard_normal((3,) + shape)
+    cs2, kappa = 0.21, 0.07
+    f = np.einsum("ia,a...->i...", d.TINV, d.equilibrium_moments(rho, j, lap, grad, cs2, kappa))
+    C = d.C.astype(float)
+    np.testing.assert_allclose(f.sum(axis=0), rho, rtol=1e-14)
+    np.testing.assert_allclose(np.einsum("ia,i...->a...", C, f), j, atol=1e-15)
+    u = j / rho
+    g2 = (grad ** 2).sum(axis=0)
+    P2 = np.einsum("ia,ib,i...->ab...", C, C, f)
+    for a in range(3):
+        for b in range(3):
+            want = rho * u[a] * u[b] + kappa * grad[a] * grad[b]
+            if a == b:
+                want = want + cs2 * rho - kappa * rho * lap - 0.5 * kappa * g2
+            np.testing.assert_allclose(P2[a, b], want, atol=1e-14)
+    P3 = np.einsum("ia,ib,ic,i...->abc...", C, C, C, f)
+    dd = np.eye(3)
+    want3 = S2 * (np.einsum("a...,bc->abc...", j, dd) + np.einsum("b...,ac->abc...", j, dd)
+                  + np.einsum("c...,ab->abc...", j, dd))
+    np.testing.assert_allclose(P3, want3, atol=1e-14)
+
+
+@pytest.mark.parametrize("cs2", [S2, 0.2, 0.1])
+def test_rest_state_is_a_fixed_point(cs2):
+    m = d.Model(rho0=0.9, cs2=cs2, kappa=0.05, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    fb = m.fbar()
+    np.testing.assert_allclose(fb[1:], d.W[1:] * 3 * cs2 * 0.9, rtol=1e-13)
+    assert abs(fb.sum() - 0.9) < 1e-15
+    f = np.broadcast_to(fb[:, None, None, None], (27, 3, 4, 5)).copy()
+    np.testing.assert_allclose(d.step(f, m), f, atol=1e-15)
+
+
+def _project(f3, axes):
+    drop = ({0, 1, 2} - set(axes)).pop()
+    sl = [slice(None)] * 4
+    sl[3 - drop] = 0
+    plane = f3[tuple(sl)]
+    rem = [ax for ax in (2, 1, 0) if ax != drop]
+    if rem[0] != axes[1]:
+        plane = np.transpose(plane, (0, 2, 1))
+    out = np.zeros((9,) + plane.shape[1:])
+    for i, c in enumerate(d.C):
+        k = [n for n in range(9) if th.C[n, 0] == c[axes[0]] and th.C[n, 1] == c[axes[1]]][0]
+        out[k] += plane[i]
+    return out
+
+
+@pytest.mark.parametrize("axes", [(0, 1), (1, 2), (2, 0)])
+def test_field_uniform_along_an_axis_evolves_as_the_d2q9_model(axes):
+    # equal relaxation times, a state uniform and mirror-symmetric along the dropped axis:
+    # the D3Q27 oracle follows the independent D2Q9 C core (Table II) step for step
+    n = {0: 12, 1: 10, 2: 9}
+    drop = ({0, 1, 2} - set(axes)).pop()
+    shape3 = [n[2], n[1], n[0]]
+    shape3[2 - drop] = 1
+    cs2, kappa, tau = 0.25, 0.05, 0.85
+    m3 = d.Model(1.0, cs2, kappa, 0.0, tau, tau, tau)
+    m2 = th.Model(rho0=1.0, cs2=cs2, kappa=kappa, tau_s=tau, tau_b=tau, tau_ghost=tau)
+    pert = synth.gaussian_field((27,) + tuple(shape3), seed=9 + drop, scale=0.05)
+    flip = d.C.copy()
+    flip[:, drop] *= -1
+    mirror = [int(np.where((d.C == c).all(axis=1))[0][0]) for c in flip]
+    pert = 0.5 * (pert + pert[mirror])
+    f3 = m3.fbar()[:, None, None, None] * (1.0 + pert)
+    f2 = _project(f3, axes)
+    for _ in range(12):
+        f3 = d.step(f3, m3)
+        f2 = oracle.step(f2, m2)
+        np.testing.assert_allclose(_project(f3, axes), f2, rtol=0, atol=2e-14)
+    assert f2.sum(axis=0).std() > 1e-3
+
+
+def test_mass_and_momentum_are_conserved_with_noise():
+    L = d.Lattice(5, 4, 3, cs2=0.2, seed=3)
+    L.set_params(1e-4, 0.03, 0.8, 1.1, 0.9, d.NOISE_LW)
+    c = [d.IDX[(0, 0, 0)], d.IDX[(1, 0, 0)], d.IDX[(0, 1, 0)], d.IDX[(0, 0, 1)]]
+    m0 = L.moments()[c].sum(axis=(1, 2, 3))
+    L.step(20)
+    np.testing.assert_allclose(L.moments()[c].sum(axis=(1, 2, 3)), m0, atol=1e-12)
+
+
+@pytest.mark.parametrize("tau_s", [0.7, 1.3])
+def test_shear_wave_decays_at_the_shear_viscosity(tau_s):
+    nz = 64
+    k = 2 * np.pi / nz
+    m = d.Model(1.0, 0.25, 0.02, 0.0, tau_s, 1.1, 0.9)
+    z = np.arange(nz)
+    rho = np.ones((nz, 1, 1))
+    j = np.zeros((3, nz, 1, 1))
+    j[0] = 1e-4 * np.sin(k * z)[:, None, None]
+    lap, grad = d.density_stencils(rho)
+    f = np.einsum("ia,a...->i...", d.TINV, d.equilibrium_moments(rho, j, lap, grad, m.cs2, m.kappa))
+    amp = []
+    for _ in range(400):
+        jx = np.einsum("i,i...->...", d.C[:, 0].astype(float), f)[:, 0, 0]
+        amp.append((jx * np.sin(k * z)).sum() * 2 / nz)
+        f = d.step(f, m)
+    t = np.arange(20, 400)
+    rate = -np.polyfit(t, np.log(np.abs(np.array(amp)[20:400])), 1)[0]
+    nu = S2 * (tau_s - 0.5)
+    assert abs(rate / (nu * k * k) - 1) < 5e-3
+
+
+@pytest.mark.parametrize("cs2,tau_b", [(0.25, 1.1), (0.15, 0.7)])
+def test_sound_wave_speed_and_damping(cs2, tau_b):
+    # Gamma = (4 eta / 3 + zeta) / (2 rho0), zeta = rho0 (tau_b - 1/2)(5 sigma_s^2 - 3 cs2) / 3
+    from scipy.optimize import curve_fit
+    nx = 64
+    k = 2 * np.pi / nx
+    tau_s = 0.8
+    m = d.Model(1.0, cs2, 0.0, 0.0, tau_s, tau_b, 0.9)
+    x = np.arange(nx)
+    rho = (1.0 + 1e-4 * np.cos(k * x))[None, None, :]
+    j = np.zeros((3, 1, 1, nx))
+    lap, grad = d.density_stencils(rho)
+    f = np.einsum("ia,a...->i...", d.TINV, d.equilibrium_moments(rho, j, lap, grad, m.cs2, m.kappa))
+    amp = []
+    for _ in range(700):
+        r = f.sum(axis=0)[0, 0]
+        amp.append(((r - 1.0) * np.cos(k * x)).sum() * 2 / nx)
+        f = d.step(f, m)
+    t = np.arange(700, dtype=float)
+    fun = lambda tt, A, g, w, p: A * np.exp(-g * tt) * np.cos(w * tt + p)
+    sel = t >= 30
+    p, _ = curve_fit(fun, t[sel], np.array(amp)[sel], p0=[1e-4, 1e-3, np.sqrt(cs2) * k, 0.0])
+    gamma = (4 * S2 * (tau_s - 0.5) / 3 + (tau_b - 0.5) * (5 * S2 - 3 * cs2) / 3) / 2 * k * k
+    w = np.sqrt(cs2 * k * k - gamma ** 2)
+    assert abs(abs(p[2]) / w - 1) < 2e-3
+    assert abs(p[1] / gamma - 1) < 2e-2
+
+
+@pytest.mark.parametrize("cs2", [S2, 0.25, 0.12])
+def test_ansatz_covariance_is_a_rank_one_update_of_a_diagonal(cs2):
+    # fbar_i = 3 cs2 rho0 w_i + rho0 (1 - 3 cs2) delta_i0, so
+    # (S / rho0) T diag(fbar) T^T = S [3 cs2 diag(N) + (1 - 3 cs2) t0 t0^T], t0 the modes at c = 0
+    rho0, kT = 0.9, 1e-4
+    m = d.Model(rho0, cs2, 0.03, kT, 0.8, 1.1, 0.9)
+    S = rho0 * kT / cs2
+    t0 = d.T[:, 0]
+    want = S * (3 * cs2 * np.diag(d.N) + (1 - 3 * cs2) * np.outer(t0, t0))
+    np.testing.assert_allclose(m.G0(), want, rtol=1e-12, atol=1e-18)
+
+
+def test_ideal_gas_noise_in_closed_form():
+    # cs2 = sigma_s^2: G = N rho0 kT / sigma_s^2 (diagonal), Omega = Lambda, so
+    # Xi = -(rho0 kT / sigma_s^2) N_a lambda (2 + lambda) mode by mode, with the p_2 block
+    # lambda~_s I + (lambda~_b - lambda~_s) / 3 (1 1^T) (N = 2 each)
+    rho0, kT = 1.0, 1e-4
+    m = d.Model(rho0, S2, 0.0, kT, 0.8, 1.1, 0.9)
+    til = lambda l: l * (2 + l)
+    lb, ls, lg = -1 / 1.1, -1 / 0.8, -1 / 0.9
+    Tt = rho0 * kT / S2
+    want = np.zeros((27, 27))
+    for k in range(27):
+        if k not in d.CONSERVED:
+            want[k, k] = -Tt * d.N[k] * til(lg)
+    for k in d.SECOND_OFF:
+        want[k, k] = -Tt * d.N[k] * til(ls)
+    for a in d.SECOND_DIAG:
+        for b in d.SECOND_DIAG:
+            want[a, b] = -Tt * 2 * ((til(lb) - til(ls)) / 3 + (til(ls) if a == b else 0.0))
+    np.testing.assert_allclose(m.Xi_zero(), want, rtol=1e-12, atol=1e-13 * kT)
+
+
+@pytest.mark.parametrize("cs2", [0.25, 0.12])
+def test_single_node_dynamics_reaches_the_conditional_ansatz_covariance(cs2):
+    # On a 1x1x1 periodic lattice streaming is the identity, rho and j are fixed and the
+    # collision is linear: m -> m + Omega (m - mbar) + xi exactly.  The stationary
+    # covariance of the non-conserved modes must be the ansatz G(0) conditioned on the fixed
+    # density, G_nn - G_n0 G_0n / G_00: the fluctuation-dissipation balance of Xi(0), checked
+    # by simulation instead of algebra.
+    kT = 1e-6
+    L = d.Lattice(1, 1, 1, cs2=cs2, seed=17)
+    L.set_params(kT, 0.04, 0.8, 1.1, 0.9, d.NOISE_LW)
+    mbar = L.model.mbar()
+    L.step(50)
+    nc = d.NONCONSERVED
+    steps = 16000
+    acc = np.zeros((len(nc), len(nc)))
+    samples = []
+    for _ in range(steps):
+        L.step(1)
+        v = (L.moments()[:, 0, 0, 0] - mbar)[nc]
+        acc += np.outer(v, v)
+        samples.append(v)
+    Cs = acc / steps
+    G = L.model.G0()
+    Gc = G[np.ix_(nc, nc)] - np.outer(G[nc, 0], G[0, nc]) / G[0, 0]
+    # standard error of each diagonal entry from batch means (batches of 200 steps)
+    s = np.array(samples) ** 2
+    bm = s.reshape(80, 200, -1).mean(axis=1)
+    se = bm.std(axis=0, ddof=1) / np.sqrt(80)
+    z = (np.diag(Cs) - np.diag(Gc)) / se
+    print("k = 0 variance ratios", np.round(np.diag(Cs) / np.diag(Gc), 3), "max |z| %.2f" % np.abs(z).max())
+    assert np.abs(z).max() < 4.5
+    # the coupled entries (bulk, fourth- and sixth-order ghosts) too
+    k4 = [nc.index(k) for k in d.SECOND_DIAG + d.FOURTH_PAIR + [d.SIXTH]]
+    sub = np.abs(Cs[np.ix_(k4, k4)] - Gc[np.ix_(k4, k4)]).max() / np.abs(Gc[np.ix_(k4, k4)]).max()
+    assert sub < 0.08
+
+
+def test_ideal_fluctuating_gas_is_in_equipartition():
+    rho0, kT = 1.0, 1e-4
+    nx = ny = nz = 3
+    n = nx * ny * nz
+    R, steps = 6, 300
+    acc = []
+    for r in range(R):
+        L = d.Lattice(nx, ny, nz, rho0=rho0, cs2=S2, seed=200 + r)
+        L.set_params(kT, 0.0, 0.8, 1.1, 0.9, d.NOISE_LW)
+        L.step(60)
+        s = np.zeros(27)
+        cnt = 0
+        for t in range(steps):
+            L.step(1)
+            if t % 3 == 0:
+                dm = L.moments() - L.model.mbar()[:, None, None, None]
+                s += (dm.reshape(27, -1) ** 2).mean(axis=1)
+                cnt += 1
+        acc.append(s / cnt)
+    acc = np.array(acc)
+    want = d.N * rho0 * kT / S2
+    want[d.CONSERVED] *= 1 - 1 / n
+    mean = acc.mean(axis=0)
+    sd = acc.std(axis=0, ddof=1) / np.sqrt(R)
+    print("D3Q27 equipartition ratios", np.round(mean / want, 3))
+    assert np.abs(mean / want - 1).max() < 0.06
+    assert np.abs((mean - want) / sd).max() < 5.0

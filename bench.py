@@ -81,8 +81,10 @@ def parse():
     p.add_argument("--serve-study", action="store_true",
                    help="run only the serving comparison on traces of 500 requests at 5/s and 2/s "
                         "(served engine and measured plain path) and print its JSON (several minutes)")
-    p.add_argument("--d3q19-only", type=int, default=0, metavar="N",
-                   help="run only the D3Q19 variant on an N^3 lattice and print its JSON (profiling runs)")
+    p.add_argument("--d3-only", type=int, default=0, metavar="N",
+                   help="run only the three-dimensional variant on an N^3 lattice and print its JSON "
+                        "(profiling runs; --lattice 19 or 27)")
+    p.add_argument("--lattice", type=int, default=19, choices=[19, 27])
     p.add_argument("--noise", default="lw", choices=["lw", "full", "rs"],
                    help="noise of the main line (full: correlated via k-space, rs: correlated built in real "
                         "space, both at kappa=0.05; for profiling runs)")
@@ -316,14 +318,12 @@ def timed_run(lbf, torch, L, steps, warmup, mode, params, dist):
     return ms, kms, kl, launches, wall0, wall1
 
 
-BYTES_PER_NODE_STEP_D3Q19 = 152   # 19 FP32 populations read + 19 written
-
-
-def d3q19_variant(lbf, torch, hbm, n=256, steps=300, warmup=5):
-    """The D3Q19 lattice (the paper's model carried to three dimensions): n^3 FP32 (2 x 1.27 GB
-    of populations at n = 256, larger than L2), cs2 = 1/3, uncorrelated noise of Xi(0), the
-    PARAMS_LW relaxation times and kappa; one kernel launch per step."""
-    L = lbf.Lattice3(n, n, n, seed=42, rho0=1.0, cs2=1.0 / 3.0)
+def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5):
+    """A three-dimensional lattice (the paper's model carried to D3Q19 or D3Q27): n^3 FP32
+    (2 x 19 x 67 MB or 2 x 27 x 67 MB of populations at n = 256, larger than L2), cs2 = 1/3,
+    uncorrelated noise of Xi(0), the PARAMS_LW relaxation times and kappa; one kernel launch
+    per step.  Algorithmic bytes: Q FP32 populations read and Q written per node."""
+    L = lbf.Lattice3(n, n, n, seed=42, rho0=1.0, cs2=1.0 / 3.0, lattice=lattice)
     p = PARAMS_LW
     L.set_params(p["kT"], p["kappa"], p["tau_s"], p["tau_b"], p["tau_ghost"], lbf.LB_NOISE_LW)
     L.step(warmup)
@@ -342,13 +342,14 @@ def d3q19_variant(lbf, torch, hbm, n=256, steps=300, warmup=5):
     launches = lbf.lb3_launch_count(L.ctx) - k0
     lbf.lb3_set_kernel_timing(L.ctx, 0)
     nodes = n ** 3
+    bpn = 2 * lattice * 4
     k_s = kms / max(kl, 1) / 1e3
     L.close()
-    return {"lattice": "D3Q19 %d^3, FP32 deviations" % n, "noise": "long-wavelength", "kappa": p["kappa"],
-            "value": nodes * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / steps,
-            "step_kernel": {"achieved": BYTES_PER_NODE_STEP_D3Q19 * nodes / k_s / 1e9, "unit": "GB/s",
-                            "frac": BYTES_PER_NODE_STEP_D3Q19 * nodes / k_s / 1e9 / hbm, "avg_us": k_s * 1e6,
-                            "bytes_per_node": BYTES_PER_NODE_STEP_D3Q19},
+    return {"lattice": "D3Q%d %d^3, FP32 deviations" % (lattice, n), "noise": "long-wavelength",
+            "kappa": p["kappa"], "value": nodes * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ms / steps,
+            "step_kernel": {"achieved": bpn * nodes / k_s / 1e9, "unit": "GB/s",
+                            "frac": bpn * nodes / k_s / 1e9 / hbm, "avg_us": k_s * 1e6, "bytes_per_node": bpn},
             "gpu_launches": launches}
 
 
@@ -583,9 +584,9 @@ def main():
     if args.batched_only:
         print(json.dumps(batched_variant(lbf, torch)))
         return 0
-    if args.d3q19_only:
-        print(json.dumps(d3q19_variant(lbf, torch, peaks()[0], n=args.d3q19_only, steps=args.steps,
-                                       warmup=args.warmup)))
+    if args.d3_only:
+        print(json.dumps(d3_variant(lbf, torch, peaks()[0], args.lattice, n=args.d3_only, steps=args.steps,
+                                    warmup=args.warmup)))
         return 0
     if args.serve_study:
         big = (512 * 512, 1)      # lattices of 512^2 and more: one at a time
@@ -664,9 +665,10 @@ def main():
         L16.close()
         del L16
 
-    # the three-dimensional lattice
+    # the three-dimensional lattices
     if not args.no_variants and not main_fp16:
-        variants.append(d3q19_variant(lbf, torch, hbm))
+        variants.append(d3_variant(lbf, torch, hbm, 19))
+        variants.append(d3_variant(lbf, torch, hbm, 27))
 
     # batched ensemble and request server (rank 0 of a single-GPU run)
     if not args.no_variants and world == 1:

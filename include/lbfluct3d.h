@@ -1,43 +1,56 @@
 /*
- * lbfluct3d.h -- C ABI of the D3Q19 member of the GB300 (sm_103a) fluctuating lattice
- * Boltzmann library.
+ * lbfluct3d.h -- C ABI of the three-dimensional members (D3Q19, D3Q27) of the GB300 (sm_103a)
+ * fluctuating lattice Boltzmann library.
  *
  * [GACV] = Gross, Adhikari, Cates & Varnik, "Thermal fluctuations in the lattice Boltzmann
  * method for non-ideal fluids", arXiv:1009.0254.  Sec. IV states that its construction of
  * the noise from the lattice fluctuation-dissipation theorem holds on any DdQn lattice;
- * these entry points step the same non-ideal model on a periodic nx x ny x nz D3Q19 lattice:
- *   - modes: the weighted-orthogonal basis of Duenweg, Schiller & Ladd, Phys. Rev. E 76,
- *     036704 (2007), Table I (m_0 = rho, m_1..3 = j, m_4 = bulk c^2 - 1, m_5..9 shear,
- *     m_10..18 ghosts), scalar product of [GACV] Eq. (scalar-prod) with the D3Q19 weights
- *     1/3, 1/18, 1/36;
+ * these entry points step the same non-ideal model on a periodic nx x ny x nz lattice:
  *   - collision: [GACV] Eq. (fluct-lin-lbe), m*_a = m_a + lambda_a (m_a - m_a^eq) + xi_a, with
- *     lambda = -1/tau_b for m_4, -1/tau_s for m_5..9, -1/tau_ghost for m_10..18;
+ *     lambda_b = -1/tau_b on the bulk mode, lambda_s = -1/tau_s on the traceless second-order
+ *     modes and -1/tau_ghost on every higher mode;
  *   - equilibrium: rho, j and the second moments of P^th + rho u u, with P^th the pressure
  *     tensor of [GACV] Eq. (press-ten) for p0 = cs2 rho, i.e.
  *     sum_i f^eq_i c_ia c_ib = (p0 - kappa rho lap rho - kappa |grad rho|^2 / 2) delta_ab
- *     + kappa d_a rho d_b rho + rho u_a u_b; the ghost m_16 = 3 c^4 - 6 c^2 + 1 has
- *     m_16^eq = -3 (p0 - rho/3 - kappa rho lap rho) - (9/2) kappa |grad rho|^2 (on fields
- *     that are uniform along one axis the model is then the D2Q9 model of [GACV] Table II
- *     at equal relaxation times); the other ghosts have zero equilibrium; lap and grad are
- *     the isotropic stencils of [GACV] Appendix B with the D3Q19 weights;
+ *     + kappa d_a rho d_b rho + rho u_a u_b; lap and grad are the isotropic stencils of
+ *     [GACV] Appendix B with the lattice's weights; the ghost equilibria below make a field
+ *     that is uniform along one axis evolve, at equal relaxation times, as the D2Q9 model of
+ *     [GACV] Table II;
  *   - noise: spatially uncorrelated with covariance Xi(0) of [GACV] Eq. (noise-matrix-k0),
- *     xi = L nu with L the Cholesky factor of the block of the non-conserved modes.
+ *     xi = L nu, L the Cholesky factor of the block of the non-conserved modes.
+ *
+ * LB_D3Q19 (19 velocities, weights 1/3, 1/18, 1/36)
+ *   - modes: the weighted-orthogonal basis of Duenweg, Schiller & Ladd, Phys. Rev. E 76,
+ *     036704 (2007), Table I (m_0 = rho, m_1..3 = j, m_4 = bulk c^2 - 1, m_5..9 shear,
+ *     m_10..18 ghosts); only m_16 = 3c^4 - 6c^2 + 1 among the ghosts has an equilibrium,
+ *     m_16^eq = -3 (p0 - rho/3 - kappa rho lap rho) - (9/2) kappa |grad rho|^2;
+ *   - velocity order: 0 rest; 1 (1,0,0), 2 (-1,0,0), 3 (0,1,0), 4 (0,-1,0), 5 (0,0,1),
+ *     6 (0,0,-1); 7 (1,1,0), 8 (1,-1,0), 9 (-1,1,0), 10 (-1,-1,0); 11 (0,1,1), 12 (0,1,-1),
+ *     13 (0,-1,1), 14 (0,-1,-1); 15 (1,0,1), 16 (-1,0,1), 17 (1,0,-1), 18 (-1,0,-1);
+ *   - random numbers: tag 4 gives nu_4..nu_11, tag 5 gives nu_12..nu_18; xi_a = sqrt(Xi_aa) nu_a
+ *     except xi_4 = L_44 nu_4, xi_16 = L_16,4 nu_4 + L_16,16 nu_16.
+ * LB_D3Q27 (27 velocities, weights the products of the D1Q3 weights 2/3, 1/6, 1/6)
+ *   - velocity i = 9 ix + 3 iy + iz with c = (v[ix], v[iy], v[iz]), v = (0, 1, -1);
+ *   - modes: the products m_(a,b,c) = sum_i p_a(c_ix) p_b(c_iy) p_c(c_iz) f_i of p_0 = 1,
+ *     p_1 = c, p_2 = 3c^2 - 1 (mode index 9a + 3b + c; the c_z-independent modes are the D2Q9
+ *     basis of [GACV] Table I); ghost equilibria p_2a p_2b = -3 (p0 - rho/3 - kappa rho lap rho)
+ *     - (3/2) kappa |grad rho|^2, p_2x p_2y p_2z = 3 (p0 - rho/3 - kappa rho lap rho)
+ *     - (3/2) kappa |grad rho|^2, all others zero;
+ *   - random numbers: tags 6, 7, 8 give 24 normals, the n-th going to the n-th non-conserved
+ *     mode in mode order; the factor is diagonal except on the modes p_2z, p_2y, p_2y p_2z,
+ *     p_2x, p_2x p_2z, p_2x p_2y, p_2x p_2y p_2z, which share a dense Cholesky block.
  *
  * Conventions
  *   - Return codes and buffer locations are those of lbfluct.h (LB_OK, LB_E*, LB_HOST,
  *     LB_DEVICE, LB_FP32, LB_FP64, LB_NOISE_OFF, LB_NOISE_LW).
  *   - Populations cross the ABI as FP64 arrays f[i][z][y][x] (index
- *     ((i*nz + z)*ny + y)*nx + x), pre-collision (right after streaming), i = 0..18 in the
- *     velocity order: 0 rest; 1 (1,0,0), 2 (-1,0,0), 3 (0,1,0), 4 (0,-1,0), 5 (0,0,1),
- *     6 (0,0,-1); 7 (1,1,0), 8 (1,-1,0), 9 (-1,1,0), 10 (-1,-1,0); 11 (0,1,1), 12 (0,1,-1),
- *     13 (0,-1,1), 14 (0,-1,-1); 15 (1,0,1), 16 (-1,0,1), 17 (1,0,-1), 18 (-1,0,-1).
+ *     ((i*nz + z)*ny + y)*nx + x), pre-collision (right after streaming), in the lattice's
+ *     velocity order above.
  *   - The device holds the deviations f_i - fbar_i from the rest state in the storage
- *     precision (LB_FP32: 152 bytes moved per node update; LB_FP64: 304), two copies.
- *   - Random numbers: Philox4x32-10 keyed (seed mod 2^32, seed div 2^32), counter
- *     (node, t mod 2^32, t div 2^32, tag) with node = (z*ny + y)*nx + x; tag 4 gives the
- *     normals nu_4..nu_11, tag 5 gives nu_12..nu_18 (one Box-Muller pair per output word:
- *     20-bit radius, 12-bit angle, as for D2Q9); xi_a = sqrt(Xi_aa) nu_a except
- *     xi_4 = L_44 nu_4, xi_16 = L_16,4 nu_4 + L_16,16 nu_16.
+ *     precision (LB_FP32: 2 Q 4 bytes moved per node update; LB_FP64: 2 Q 8), two copies.
+ *   - Philox4x32-10 keyed (seed mod 2^32, seed div 2^32), counter (node, t mod 2^32,
+ *     t div 2^32, tag) with node = (z*ny + y)*nx + x; one Box-Muller pair per output word
+ *     (20-bit radius, 12-bit angle, as for D2Q9).
  *   - All GPU work runs on the context's stream; calls that return data synchronise it.
  *     The caller owns every buffer it passes.  One host thread per context at a time.
  */
@@ -53,28 +66,32 @@
 extern "C" {
 #endif
 
+/* lattices */
+#define LB_D3Q19 19
+#define LB_D3Q27 27
+
 typedef struct lb3_ctx lb3_ctx;
 
 /* Device bytes of a context (two population copies, FP64 staging plane, reduction
- * scratch); 0 for invalid sizes or precision. */
-size_t lb3_workspace_bytes(int nx, int ny, int nz, int precision);
+ * scratch); 0 for invalid sizes, lattice or precision. */
+size_t lb3_workspace_bytes(int nx, int ny, int nz, int lattice, int precision);
 
 /*
- * Creates a context for a periodic nx x ny x nz lattice (each >= 1, nx*ny*nz < 2^32) at
- * rest with density rho0: fbar_i = w_i 3 cs2 rho0 for the moving velocities and the
- * remainder rho0 - sum on the rest velocity (the equilibrium at u = 0 for p0 = cs2 rho).
- * precision: LB_FP32 or LB_FP64 (LB_EINVAL otherwise).  The library allocates its device
- * memory (LB_ENOMEM if that fails).  *out receives the context.
+ * Creates a context for a periodic nx x ny x nz lattice (each >= 1, nx*ny*nz < 2^32) of the
+ * given kind (LB_D3Q19 or LB_D3Q27) at rest with density rho0: fbar_i = w_i 3 cs2 rho0 for
+ * the moving velocities and the remainder rho0 - sum on the rest velocity (the equilibrium
+ * at u = 0 for p0 = cs2 rho).  precision: LB_FP32 or LB_FP64 (LB_EINVAL otherwise).  The
+ * library allocates its device memory (LB_ENOMEM if that fails).  *out receives the context.
  */
-int lb3_create(int nx, int ny, int nz, int precision, uint64_t seed, double rho0, double cs2,
+int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed, double rho0, double cs2,
                lb3_ctx** out);
 int lb3_destroy(lb3_ctx* ctx);
 int lb3_set_stream(lb3_ctx* ctx, void* stream);
 
 /*
  * Sets kT, kappa, the relaxation times (each > 1/2) and the noise mode (LB_NOISE_OFF or
- * LB_NOISE_LW).  With noise, Xi(0) must be positive semidefinite (cs2 <= 5/9 and the
- * (4,16) block's determinant >= 0), else LB_ENOTPSD.
+ * LB_NOISE_LW).  With noise, Xi(0) must be positive semidefinite (D3Q19: cs2 <= 5/9), else
+ * LB_ENOTPSD.
  */
 int lb3_set_params(lb3_ctx* ctx, double kT, double kappa, double tau_s, double tau_b, double tau_ghost,
                    int noise_mode);
@@ -83,7 +100,7 @@ int lb3_set_params(lb3_ctx* ctx, double kT, double kappa, double tau_s, double t
 int lb3_step(lb3_ctx* ctx, int64_t nsteps);
 int lb3_get_time(lb3_ctx* ctx, int64_t* t);
 
-/* Writes / reads all populations (FP64, layout above) at `loc`; set also sets the time t
+/* Writes / reads all Q populations (FP64, layout above) at `loc`; set also sets the time t
  * (the index of the next collision, which keys its random numbers). */
 int lb3_set_populations(lb3_ctx* ctx, const double* f, int loc, int64_t t);
 int lb3_get_populations(lb3_ctx* ctx, double* f, int loc);
@@ -102,9 +119,10 @@ int lb3_launch_count(lb3_ctx* ctx, int64_t* launches);
 int lb3_synchronize(lb3_ctx* ctx);
 const char* lb3_last_error(lb3_ctx* ctx);
 
-/* Host-side FP64 Xi(0) of the D3Q19 model (19 x 19, row-major) for these parameters. */
-int lb3_noise_matrix(double rho0, double cs2, double kT, double tau_s, double tau_b, double tau_ghost,
-                     double* xi);
+/* Host-side FP64 Xi(0) of the lattice's model (Q x Q, row-major, in its mode order) for these
+ * parameters; LB_EINVAL for an unknown lattice or parameters out of range. */
+int lb3_noise_matrix(int lattice, double rho0, double cs2, double kT, double tau_s, double tau_b,
+                     double tau_ghost, double* xi);
 
 #ifdef __cplusplus
 }

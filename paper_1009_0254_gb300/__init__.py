@@ -26,6 +26,7 @@ LB_EOS_LINEAR, LB_EOS_DOUBLE_WELL = 0, 1
 LB_FACTOR_CHOLESKY, LB_FACTOR_EIGEN = 0, 1
 LB_HOST, LB_DEVICE = 0, 1
 LB_WARN_LOW_MACH = 1
+LB_D3Q19, LB_D3Q27 = 19, 27
 
 _lib = None
 
@@ -123,8 +124,8 @@ def load(path: str = LIB_PATH):
         "lb_server_set_admission": (c_int, [vp, c_i64, c_int]),
         "lb_selftest_bounded_wait": (c_int, [c_dbl, ctypes.POINTER(c_int)]),
         "lb_server_last_error": (ctypes.c_char_p, [vp]),
-        "lb3_workspace_bytes": (c_sz, [c_int, c_int, c_int, c_int]),
-        "lb3_create": (c_int, [c_int, c_int, c_int, c_int, c_u64, c_dbl, c_dbl, ctypes.POINTER(vp)]),
+        "lb3_workspace_bytes": (c_sz, [c_int, c_int, c_int, c_int, c_int]),
+        "lb3_create": (c_int, [c_int, c_int, c_int, c_int, c_int, c_u64, c_dbl, c_dbl, ctypes.POINTER(vp)]),
         "lb3_destroy": (c_int, [vp]),
         "lb3_set_stream": (c_int, [vp, vp]),
         "lb3_set_params": (c_int, [vp, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_int]),
@@ -138,7 +139,7 @@ def load(path: str = LIB_PATH):
         "lb3_launch_count": (c_int, [vp, i64p]),
         "lb3_synchronize": (c_int, [vp]),
         "lb3_last_error": (ctypes.c_char_p, [vp]),
-        "lb3_noise_matrix": (c_int, [c_dbl] * 6 + [dp]),
+        "lb3_noise_matrix": (c_int, [c_int] + [c_dbl] * 6 + [dp]),
     }
     for name, (res, args) in proto.items():
         fn = getattr(L, name)
@@ -677,13 +678,13 @@ def _check3(rc, ctx=None):
     return rc
 
 
-def lb3_workspace_bytes(nx, ny, nz, precision=LB_FP32):
-    return load().lb3_workspace_bytes(nx, ny, nz, precision)
+def lb3_workspace_bytes(nx, ny, nz, lattice=LB_D3Q19, precision=LB_FP32):
+    return load().lb3_workspace_bytes(nx, ny, nz, lattice, precision)
 
 
-def lb3_create(nx, ny, nz, precision=LB_FP32, seed=42, rho0=1.0, cs2=1.0 / 3.0):
+def lb3_create(nx, ny, nz, lattice=LB_D3Q19, precision=LB_FP32, seed=42, rho0=1.0, cs2=1.0 / 3.0):
     out = ctypes.c_void_p()
-    _check3(load().lb3_create(nx, ny, nz, precision, seed, rho0, cs2, ctypes.byref(out)))
+    _check3(load().lb3_create(nx, ny, nz, lattice, precision, seed, rho0, cs2, ctypes.byref(out)))
     return out.value
 
 
@@ -742,20 +743,22 @@ def lb3_synchronize(ctx):
     return _check3(load().lb3_synchronize(ctx), ctx)
 
 
-def lb3_noise_matrix(rho0, cs2, kT, tau_s, tau_b, tau_ghost):
-    X = np.zeros((19, 19))
-    _check3(load().lb3_noise_matrix(rho0, cs2, kT, tau_s, tau_b, tau_ghost, _dptr(X)))
+def lb3_noise_matrix(rho0, cs2, kT, tau_s, tau_b, tau_ghost, lattice=LB_D3Q19):
+    X = np.zeros((lattice, lattice))
+    _check3(load().lb3_noise_matrix(lattice, rho0, cs2, kT, tau_s, tau_b, tau_ghost, _dptr(X)))
     return X
 
 
 class Lattice3:
-    """One periodic D3Q19 lattice on the current CUDA device; its work runs on the given
-    stream (torch.cuda.current_stream() at construction, unless given)."""
+    """One periodic D3Q19 or D3Q27 lattice on the current CUDA device; its work runs on the
+    given stream (torch.cuda.current_stream() at construction, unless given)."""
 
-    def __init__(self, nx, ny, nz, seed=42, rho0=1.0, cs2=1.0 / 3.0, stream=None, precision=LB_FP32):
+    def __init__(self, nx, ny, nz, seed=42, rho0=1.0, cs2=1.0 / 3.0, stream=None, precision=LB_FP32,
+                 lattice=LB_D3Q19):
         import torch
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
-        self.ctx = lb3_create(self.nx, self.ny, self.nz, precision, seed, rho0, cs2)
+        self.q = int(lattice)
+        self.ctx = lb3_create(self.nx, self.ny, self.nz, lattice, precision, seed, rho0, cs2)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         lb3_set_stream(self.ctx, self.stream.cuda_stream)
 
@@ -782,11 +785,11 @@ class Lattice3:
 
     def set_populations(self, f, t=0):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        assert f.shape == (19, self.nz, self.ny, self.nx)
+        assert f.shape == (self.q, self.nz, self.ny, self.nx)
         lb3_set_populations(self.ctx, f, LB_HOST, t)
 
     def populations(self):
-        f = np.empty((19, self.nz, self.ny, self.nx))
+        f = np.empty((self.q, self.nz, self.ny, self.nx))
         lb3_get_populations(self.ctx, f, LB_HOST)
         return f
 

@@ -1,19 +1,29 @@
-// lb3d.cu -- the fused fluctuating D3Q19 step for sm_103a and the C ABI of lbfluct3d.h.
+// lb3d.cu -- the fused fluctuating step on the D3Q19 and D3Q27 lattices for sm_103a and the
+// C ABI of lbfluct3d.h.
 //
-// One launch performs one time step on every node (collision of lb3_collide.cuh, then
-// streaming in pull form: f_i(r, t) = f*_i(r - c_i, t - 1)).  A CTA owns a TX x TY tile of
-// the (x, y) plane and marches over a run of z planes.  Before it collides plane z it has
-// the density deviations of planes z-1, z, z+1 on its tile plus a one-node ring in shared
-// memory (three rotating slots); each new plane's densities are summed from the pulled
-// populations, so the step reads every population once from DRAM (the re-reads of the
-// tile hit L1/L2) and writes it once: 2 x 19 x sizeof(storage) bytes per node.
+// One launch performs one time step on every node (collision of lb3_collide.cuh or
+// lb27_collide.cuh, then streaming in pull form: f_i(r, t) = f*_i(r - c_i, t - 1)).  A CTA
+// owns a TX x TY tile of the (x, y) plane and marches over a run of z planes.  The pulled
+// populations of each plane, for the tile and its one-node ring, are staged in shared
+// memory by asynchronous copies (three rotating slots: the plane being collided, the plane
+// whose densities are summed, and the plane in flight), so the loads of plane z+2 overlap
+// the collision of plane z.  The densities of planes z-1, z, z+1 sit in three more rotating
+// slots; the collision reads its own node's populations and its 3x3x3 density neighbourhood
+// from shared memory.  Every population is read once from DRAM (the ring's re-reads hit L2)
+// and written once: 2 Q sizeof(storage) bytes per node.
+//
+// A plain D3Q19 kernel (density summed from direct loads, the collision pulling again) is
+// kept as a cross-check (LBFLUCT3_KERNEL=plain).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <utility>
 #include <vector>
 
+#include "lb27_collide.cuh"
 #include "lb3_collide.cuh"
 #include "lb_internal.cuh"
 #include "lbfluct3d.h"
@@ -21,23 +31,265 @@
 namespace lbf3 {
 
 constexpr double SIGMA_S2 = 1.0 / 3.0;
-constexpr uint32_t TAG_A = 4, TAG_B = 5;   // Philox tags of the two draws per node
+constexpr int QMAX = 27;
+
+// velocity components in {-1, 0, 1} packed two bits each: c = ((P >> 2i) & 3) - 1
+constexpr unsigned long long pack3(const int (&v)[19]) {
+    unsigned long long p = 0;
+    for (int i = 0; i < 19; ++i) p |= (unsigned long long)(v[i] + 1) << (2 * i);
+    return p;
+}
+
+// D3Q19: the velocity order of lb3_collide.cuh; noise tags 4, 5
+struct Lat19 {
+    static constexpr int Q = 19, TX = 32, TY = 8;
+    static constexpr uint32_t TAG0 = 4;
+    static constexpr int CXv[19] = {0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
+    static constexpr int CYv[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 0, 0, 0, 0};
+    static constexpr int CZv[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1};
+    static constexpr unsigned long long PX = pack3(CXv), PY = pack3(CYv), PZ = pack3(CZv);
+    __host__ __device__ static constexpr int c(int i, int k) {
+        return (int)(((k == 0 ? PX : (k == 1 ? PY : PZ)) >> (2 * i)) & 3ULL) - 1;
+    }
+    __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+};
+
+// D3Q27: i = 9 ix + 3 iy + iz, components (0, 1, -1); noise tags 6, 7, 8
+struct Lat27 {
+    static constexpr int Q = 27, TX = 32, TY = 4;
+    static constexpr uint32_t TAG0 = 6;
+    __host__ __device__ static constexpr int v(int a) { return a == 0 ? 0 : (a == 1 ? 1 : -1); }
+    __host__ __device__ static constexpr int c(int i, int k) {
+        return v(k == 0 ? i / 9 : (k == 1 ? (i / 3) % 3 : i % 3));
+    }
+    __host__ __device__ static constexpr double w1(int a) { return a == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+    __host__ __device__ static constexpr double w(int i) { return w1(i / 9) * w1((i / 3) % 3) * w1(i % 3); }
+};
+
+// The D3Q27 modes whose noise is coupled (the Cholesky factor's dense 7 x 7 block, in mode
+// order): p_2z, p_2y, p_2y p_2z, p_2x, p_2x p_2z, p_2x p_2y, p_2x p_2y p_2z.
+constexpr int COUPLED27[7] = {2, 6, 8, 18, 20, 24, 26};
+__host__ __device__ constexpr int coupled27(int r) {
+    return r == 0 ? 2 : (r == 1 ? 6 : (r == 2 ? 8 : (r == 3 ? 18 : (r == 4 ? 20 : (r == 5 ? 24 : 26)))));
+}
 
 template <typename R>
 struct Step3Args {
-    const R* __restrict__ src;    // post-collision deviations at t-1, 19 planes of P nodes
+    const R* __restrict__ src;    // post-collision deviations at t-1, Q planes of P nodes
     R* __restrict__ dst;
     int nx, ny, nz, zc;           // zc: planes per CTA
     long long P;                  // nodes per population plane
     Coef3<R> co;
-    R sc[Q3];                     // sqrt(Xi_aa) of the modes with a diagonal factor
-    R L44, L164, L1616;           // Cholesky factor of the (4,16) block
+    R sc[QMAX];                   // sqrt(Xi_kk) of the modes with a diagonal factor
+    R Lc[28];                     // the coupled block's Cholesky factor: D3Q19 (L44, L16_4, L16_16);
+                                  // D3Q27 the 7 x 7 lower triangle, row-major
     uint32_t t_lo, t_hi;
     lbf::RoundKeys rk;
 };
 
-// the 19 pulled deviations of node (x, y, z): f_i = src_i(r - c_i), wrapped coordinates
-// xm = x-1, xp = x+1 (mod nx) and the row / plane offsets of y-1, y, y+1 and z-1, z, z+1
+// D3Q19 noise: tag 4 -> nu_4..nu_11, tag 5 -> nu_12..nu_18
+template <typename R>
+__device__ __forceinline__ void normals19(const Step3Args<R>& a, uint32_t node, R xi[Q3]) {
+    const uint4 ra = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat19::TAG0), a.rk);
+    const uint4 rb = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat19::TAG0 + 1), a.rk);
+    R n4, n16, spare;
+    lbf::gauss_word(ra.x, &n4, &xi[5]);
+    lbf::gauss_word(ra.y, &xi[6], &xi[7]);
+    lbf::gauss_word(ra.z, &xi[8], &xi[9]);
+    lbf::gauss_word(ra.w, &xi[10], &xi[11]);
+    lbf::gauss_word(rb.x, &xi[12], &xi[13]);
+    lbf::gauss_word(rb.y, &xi[14], &xi[15]);
+    lbf::gauss_word(rb.z, &n16, &xi[17]);
+    lbf::gauss_word(rb.w, &xi[18], &spare);
+    (void)spare;
+#pragma unroll
+    for (int q = 5; q < Q3; ++q) xi[q] *= a.sc[q];
+    xi[4] = a.Lc[0] * n4;
+    xi[16] = a.Lc[1] * n4 + a.Lc[2] * n16;
+}
+
+// position of mode k among the non-conserved D3Q27 modes (conserved: 0, 1, 3, 9)
+__host__ __device__ constexpr int nc27(int k) { return k - (k > 0) - (k > 1) - (k > 3) - (k > 9); }
+
+// D3Q27 noise: tags 6, 7, 8 give 24 normals; normal n goes to the n-th non-conserved mode
+template <typename R>
+__device__ __forceinline__ void normals27(const Step3Args<R>& a, uint32_t node, R xi[Q27]) {
+    R nu[24];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const uint4 r = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat27::TAG0 + d), a.rk);
+        lbf::gauss_word(r.x, &nu[8 * d + 0], &nu[8 * d + 1]);
+        lbf::gauss_word(r.y, &nu[8 * d + 2], &nu[8 * d + 3]);
+        lbf::gauss_word(r.z, &nu[8 * d + 4], &nu[8 * d + 5]);
+        lbf::gauss_word(r.w, &nu[8 * d + 6], &nu[8 * d + 7]);
+    }
+#pragma unroll
+    for (int k = 0; k < Q27; ++k)
+        xi[k] = (k == 0 || k == 1 || k == 3 || k == 9) ? R(0) : a.sc[k] * nu[nc27(k)];
+#pragma unroll
+    for (int r = 0; r < 7; ++r) {
+        R s = R(0);
+#pragma unroll
+        for (int q = 0; q <= r; ++q) s += a.Lc[r * (r + 1) / 2 + q] * nu[nc27(coupled27(q))];
+        xi[coupled27(r)] = s;
+    }
+}
+
+__device__ __forceinline__ int wrap_lo(int v, int n) { return v < 0 ? v + n : v; }
+__device__ __forceinline__ int wrap_hi(int v, int n) { return v >= n ? v - n : v; }
+
+// asynchronous global -> shared copy of one element (4 or 8 bytes), cached in L1
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// density deviation of one node's pulled deviations, one fixed summation order
+template <typename LAT, typename R>
+__device__ __forceinline__ R drho_of(const R* f) {
+    if constexpr (LAT::Q == 19) {
+        return drho19(f);
+    } else {
+        R s = f[0];
+#pragma unroll
+        for (int i = 1; i < Q27; i += 2) s += (i + 1 < Q27) ? (f[i] + f[i + 1]) : f[i];
+        return s;
+    }
+}
+
+// The staged step kernel: one CTA per TX x TY tile and run of zc planes.
+template <typename LAT, typename R, int MODE, typename I>
+__global__ void __launch_bounds__(LAT::TX * LAT::TY) step3_staged_kernel(const Step3Args<R> a) {
+    constexpr int Q = LAT::Q, TX = LAT::TX, TY = LAT::TY;
+    constexpr int RX = TX + 2, RY = TY + 2, RN = RX * RY, NT = TX * TY;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    R* raw = reinterpret_cast<R*>(smem3);                   // [3][Q][RN] pulled populations
+    R* rs = raw + 3 * Q * RN;                               // [3][RN] density deviations
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long P = a.P, nxy = (long long)nx * ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * a.zc;
+    const int z1 = min(z0 + a.zc, nz);
+    const int tid = threadIdx.x;
+    const R* __restrict__ src = a.src;
+    // offsets in I: 32-bit when all Q planes fit in 2^32 elements, else 64-bit
+    const I PI = (I)P;
+
+    // issue the pulled populations of plane zz (an integer in [-1, nz]) into raw slot k
+    auto issue = [&](int zz, int k) {
+        const int zc = wrap_hi(wrap_lo(zz, nz), nz);
+        // offsets of r - c along each axis, indexed by 1 - c
+        const I Zo[3] = {(I)(zc == 0 ? nz - 1 : zc - 1) * (I)nxy, (I)zc * (I)nxy,
+                         (I)(zc == nz - 1 ? 0 : zc + 1) * (I)nxy};
+        R* slot = raw + k * Q * RN;
+        for (int q = tid; q < RN; q += NT) {
+            const int ly = q / RX, lx = q - ly * RX;
+            int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            if (gx > nx || gy > ny) continue;       // never read by a node of the lattice
+            gx = wrap_hi(wrap_lo(gx, nx), nx);
+            gy = wrap_hi(wrap_lo(gy, ny), ny);
+            const I Xo[3] = {(I)(gx == 0 ? nx - 1 : gx - 1), (I)gx, (I)(gx == nx - 1 ? 0 : gx + 1)};
+            const I Yo[3] = {(I)(gy == 0 ? ny - 1 : gy - 1) * (I)nx, (I)gy * (I)nx,
+                             (I)(gy == ny - 1 ? 0 : gy + 1) * (I)nx};
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const I off = Zo[1 - LAT::c(i, 2)] + Yo[1 - LAT::c(i, 1)] + Xo[1 - LAT::c(i, 0)];
+                cp_async_elem<sizeof(R)>(slot + i * RN + q, src + ((I)i * PI + off));
+            }
+        }
+        cp_async_commit();
+    };
+    // density deviations of the plane in raw slot k into density slot k
+    auto density = [&](int k) {
+        const R* slot = raw + k * Q * RN;
+        for (int q = tid; q < RN; q += NT) {
+            const int ly = q / RX, lx = q - ly * RX;
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            R v = R(0);
+            if (gx <= nx && gy <= ny) {
+                R f[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) f[i] = slot[i * RN + q];
+                v = drho_of<LAT>(f);
+            }
+            rs[k * RN + q] = v;
+        }
+    };
+
+    const int lx = tid % TX, ly = tid / TX;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool own = x < nx && y < ny;
+    const int qc = (ly + 1) * RX + lx + 1;
+
+    // planes z0-1, z0 -> slots 0, 1; plane z0+1 -> slot 2 (in flight)
+    issue(z0 - 1, 0);
+    issue(z0, 1);
+    cp_async_wait_all();
+    __syncthreads();
+    density(0);
+    density(1);
+    issue(z0 + 1, 2);
+    for (int z = z0; z < z1; ++z) {
+        const int k0 = (z - z0 + 1) % 3, km = (k0 + 2) % 3, kp = (k0 + 1) % 3;   // slots of z, z-1, z+1
+        cp_async_wait_all();
+        __syncthreads();
+        density(kp);
+        if (z + 1 < z1) issue(z + 2, km);          // plane z-1's slot is free
+        __syncthreads();
+        if (!own) continue;
+        const R* sl = raw + k0 * Q * RN;
+        R f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = sl[i * RN + qc];
+        const R* d0 = rs + k0 * RN + qc;
+        const R* dm = rs + km * RN + qc;
+        const R* dp = rs + kp * RN + qc;
+        R xi[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) xi[q] = R(0);
+        const I node = (I)z * (I)nxy + (I)y * (I)nx + (I)x;
+        R o[Q];
+        if constexpr (Q == 19) {
+            Rho3<R> r;
+            r.c = d0[0];
+            r.xp = d0[1]; r.xm = d0[-1];
+            r.yp = d0[RX]; r.ym = d0[-RX];
+            r.zp = dp[0]; r.zm = dm[0];
+            r.ap = d0[RX + 1]; r.am = d0[-RX - 1];         // (1,1,0)
+            r.bp = d0[-RX + 1]; r.bm = d0[RX - 1];         // (1,-1,0)
+            r.cp = dp[RX]; r.cm = dm[-RX];                 // (0,1,1)
+            r.dp = dm[RX]; r.dm = dp[-RX];                 // (0,1,-1)
+            r.ep = dp[1]; r.em = dm[-1];                   // (1,0,1)
+            r.fp = dp[-1]; r.fm = dm[1];                   // (-1,0,1)
+            if (MODE == 1) normals19(a, (uint32_t)node, xi);
+            collide19(a.co, f, r, xi, o);
+        } else {
+            // nb[i] = rho(r + c_i)
+            R nb[Q27];
+#pragma unroll
+            for (int i = 0; i < Q27; ++i) {
+                const int cz = LAT::c(i, 2);
+                const R* pl = cz == 0 ? d0 : (cz > 0 ? dp : dm);
+                nb[i] = pl[LAT::c(i, 1) * RX + LAT::c(i, 0)];
+            }
+            if (MODE == 1) normals27(a, (uint32_t)node, xi);
+            collide27(a.co, f, nb, xi, o);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) a.dst[(I)i * PI + node] = o[i];
+    }
+    cp_async_wait_all();
+}
+
+// ---- the plain D3Q19 kernel (cross-check) -----------------------------------------------
+
+// the 19 pulled deviations of node (x, y, z): f_i = src_i(r - c_i)
 template <typename R>
 __device__ __forceinline__ void pull19(const R* __restrict__ s, long long P, int x, int xm, int xp, long long ym,
                                        long long y0, long long yp, long long zm, long long z0, long long zp,
@@ -63,29 +315,6 @@ __device__ __forceinline__ void pull19(const R* __restrict__ s, long long P, int
     f[18] = s[18 * P + zp + y0 + xp];
 }
 
-__device__ __forceinline__ int wrap_lo(int v, int n) { return v < 0 ? v + n : v; }
-__device__ __forceinline__ int wrap_hi(int v, int n) { return v >= n ? v - n : v; }
-
-template <typename R>
-__device__ __forceinline__ void normals19(const Step3Args<R>& a, uint32_t node, R xi[Q3]) {
-    const uint4 ra = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_A), a.rk);
-    const uint4 rb = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_B), a.rk);
-    R n4, n16, spare;
-    lbf::gauss_word(ra.x, &n4, &xi[5]);
-    lbf::gauss_word(ra.y, &xi[6], &xi[7]);
-    lbf::gauss_word(ra.z, &xi[8], &xi[9]);
-    lbf::gauss_word(ra.w, &xi[10], &xi[11]);
-    lbf::gauss_word(rb.x, &xi[12], &xi[13]);
-    lbf::gauss_word(rb.y, &xi[14], &xi[15]);
-    lbf::gauss_word(rb.z, &n16, &xi[17]);
-    lbf::gauss_word(rb.w, &xi[18], &spare);
-    (void)spare;
-#pragma unroll
-    for (int q = 5; q < Q3; ++q) xi[q] *= a.sc[q];
-    xi[4] = a.L44 * n4;
-    xi[16] = a.L164 * n4 + a.L1616 * n16;
-}
-
 template <typename R, int MODE, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
     constexpr int RX = TX + 2, RY = TY + 2, NT = TX * TY;
@@ -98,7 +327,6 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
     const int tid = threadIdx.x;
     const R* __restrict__ src = a.src;
 
-    // density deviations of plane zz (any integer in [-1, nz]) on the tile and its ring
     auto density = [&](int zz, int slot) {
         const int zc = wrap_hi(wrap_lo(zz, nz), nz);
         const long long Z0 = zc * nxy;
@@ -107,7 +335,7 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
             const int ly = q / RX, lx = q - ly * RX;
             int gx = x0 + lx - 1, gy = y0 + ly - 1;
             R v = R(0);
-            if (gx <= nx && gy <= ny) {          // gx, gy >= -1 always
+            if (gx <= nx && gy <= ny) {
                 gx = wrap_hi(wrap_lo(gx, nx), nx);
                 gy = wrap_hi(wrap_lo(gy, ny), ny);
                 const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
@@ -147,12 +375,12 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
             r.xp = rs[s0][cy][cx + 1]; r.xm = rs[s0][cy][cx - 1];
             r.yp = rs[s0][cy + 1][cx]; r.ym = rs[s0][cy - 1][cx];
             r.zp = rs[sp][cy][cx]; r.zm = rs[sm][cy][cx];
-            r.ap = rs[s0][cy + 1][cx + 1]; r.am = rs[s0][cy - 1][cx - 1];      // (1,1,0)
-            r.bp = rs[s0][cy - 1][cx + 1]; r.bm = rs[s0][cy + 1][cx - 1];      // (1,-1,0)
-            r.cp = rs[sp][cy + 1][cx]; r.cm = rs[sm][cy - 1][cx];              // (0,1,1)
-            r.dp = rs[sm][cy + 1][cx]; r.dm = rs[sp][cy - 1][cx];              // (0,1,-1)
-            r.ep = rs[sp][cy][cx + 1]; r.em = rs[sm][cy][cx - 1];              // (1,0,1)
-            r.fp = rs[sp][cy][cx - 1]; r.fm = rs[sm][cy][cx + 1];              // (-1,0,1)
+            r.ap = rs[s0][cy + 1][cx + 1]; r.am = rs[s0][cy - 1][cx - 1];
+            r.bp = rs[s0][cy - 1][cx + 1]; r.bm = rs[s0][cy + 1][cx - 1];
+            r.cp = rs[sp][cy + 1][cx]; r.cm = rs[sm][cy - 1][cx];
+            r.dp = rs[sm][cy + 1][cx]; r.dm = rs[sp][cy - 1][cx];
+            r.ep = rs[sp][cy][cx + 1]; r.em = rs[sm][cy][cx - 1];
+            r.fp = rs[sp][cy][cx - 1]; r.fm = rs[sm][cy][cx + 1];
             R xi[Q3];
 #pragma unroll
             for (int q = 0; q < Q3; ++q) xi[q] = R(0);
@@ -168,19 +396,52 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
     }
 }
 
-template <typename R, int MODE>
-static cudaError_t launch3(const Step3Args<R>& a, dim3 grid, cudaStream_t s) {
-    constexpr int TX = 32, TY = 8;
-    step3_kernel<R, MODE, TX, TY><<<grid, TX * TY, 0, s>>>(a);
+template <typename LAT, typename R>
+constexpr int staged_smem_bytes() {
+    return (3 * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) * (int)sizeof(R);
+}
+
+template <typename LAT, typename R, int MODE, typename I>
+static cudaError_t launch_staged(const Step3Args<R>& a, dim3 grid, cudaStream_t s) {
+    constexpr int smem = staged_smem_bytes<LAT, R>();
+    // the shared-memory limit is a per-device attribute of the function: set it once per
+    // device (a repeated set from a concurrent first launch is harmless)
+    static std::atomic<unsigned> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned bit = 1u << (dev & 31);
+    if (!(done.load(std::memory_order_acquire) & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(step3_staged_kernel<LAT, R, MODE, I>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        done.fetch_or(bit, std::memory_order_release);
+    }
+    step3_staged_kernel<LAT, R, MODE, I><<<grid, LAT::TX * LAT::TY, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+template <typename LAT, typename R, int MODE>
+static cudaError_t launch3(const Step3Args<R>& a, dim3 grid, bool plain, cudaStream_t s) {
+    if constexpr (LAT::Q == 19) {
+        if (plain) {
+            step3_kernel<R, MODE, 32, 8><<<grid, 256, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    if ((unsigned long long)a.P * LAT::Q < (1ULL << 32)) return launch_staged<LAT, R, MODE, uint32_t>(a, grid, s);
+    return launch_staged<LAT, R, MODE, unsigned long long>(a, grid, s);
+}
+
+// ---- host-side theory --------------------------------------------------------------------
+
+static double w_of(int lattice, int i) { return lattice == 19 ? Lat19::w(i) : Lat27::w(i); }
+static int c_of(int lattice, int i, int k) { return lattice == 19 ? Lat19::c(i, k) : Lat27::c(i, k); }
+
 // rest populations: w_i 3 cs2 rho0 on the moving velocities, the remainder at rest
-static void rest19(double rho0, double cs2, double fbar[Q3]) {
+static void rest_pops(int lattice, double rho0, double cs2, double* fbar) {
     double moving = 0.0;
-    for (int i = 1; i < Q3; ++i) {
-        const double w = i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0;
-        fbar[i] = w * 3.0 * cs2 * rho0;
+    for (int i = 1; i < lattice; ++i) {
+        fbar[i] = w_of(lattice, i) * 3.0 * cs2 * rho0;
         moving += fbar[i];
     }
     fbar[0] = rho0 - moving;
@@ -192,13 +453,13 @@ static double norm19(int a) {
     return N[a];
 }
 
-// Xi(0) in closed form: in the variables y4 = m4 - d rho, y16 = m16 + d rho (d = 3 cs2 - 1)
-// the linearised collision is diagonal and the equal-time covariances of the ansatz
-// <df_i df_j> = (S/rho0) fbar_i delta_ij (S = rho0 kT / cs2) are rho0 kT (5 - 9 cs2),
+// D3Q19 Xi(0) in closed form: in the variables y4 = m4 - d rho, y16 = m16 + d rho
+// (d = 3 cs2 - 1) the linearised collision is diagonal and the equal-time covariances of the
+// ansatz <df_i df_j> = (S/rho0) fbar_i delta_ij (S = rho0 kT / cs2) are rho0 kT (5 - 9 cs2),
 // 9 rho0 kT (1 - cs2), 3 rho0 kT (3 cs2 - 1) for (y4, y4), (y16, y16), (y4, y16) and
 // N_a rho0 kT / sigma_s^2 for the other non-conserved modes; stationarity under
 // m -> (1 + lambda) m + xi gives the entries below.
-static void xi_zero19(double rho0, double cs2, double kT, double lb, double ls, double lg, double X[Q3 * Q3]) {
+static void xi_zero19(double rho0, double cs2, double kT, double lb, double ls, double lg, double* X) {
     for (int k = 0; k < Q3 * Q3; ++k) X[k] = 0.0;
     auto til = [](double l) { return l * (2.0 + l); };
     for (int a = 5; a < Q3; ++a) {
@@ -210,33 +471,132 @@ static void xi_zero19(double rho0, double cs2, double kT, double lb, double ls, 
     X[4 * Q3 + 16] = X[16 * Q3 + 4] = -3.0 * rho0 * kT * (3.0 * cs2 - 1.0) * (lb + lg + lb * lg);
 }
 
-template <typename R>
-__global__ void set_plane3_kernel(const double* __restrict__ src, R* __restrict__ dst, long long n, double fbar) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        dst[k] = (R)(src[k] - fbar);
+// D3Q27 Xi(0).  The rest populations are fbar_i = 3 cs2 rho0 w_i + rho0 (1 - 3 cs2) delta_i0,
+// so the ansatz covariance is the rank-one update G = S [3 cs2 diag(N) + (1 - 3 cs2) t0 t0^T]
+// (t0: the modes at c = 0, S = rho0 kT / cs2).  With y = (I - J) m (J the density
+// dependence of the equilibrium at rest) the ansatz makes y uncorrelated with rho, so the
+// fluctuation-dissipation relation of Eq. (noise-matrix-k0) becomes
+// Xi = -(Y Lambda^T + Lambda Y + Lambda Y Lambda^T) with Y = (I - J) G (I - J)^T.
+static void xi_zero27(double rho0, double cs2, double kT, double lb, double ls, double lg, double* X) {
+    constexpr int Q = Q27;
+    const double n1[3] = {1.0, 1.0 / 3.0, 2.0};
+    auto p0 = [](int a) { return a == 0 ? 1.0 : (a == 1 ? 0.0 : -1.0); };   // p_a at c = 0
+    std::vector<double> N(Q), t0(Q), G(Q * Q), A(Q * Q, 0.0), Lm(Q * Q, 0.0), Y(Q * Q, 0.0), tmp(Q * Q, 0.0);
+    for (int k = 0; k < Q; ++k) {
+        N[k] = n1[k / 9] * n1[(k / 3) % 3] * n1[k % 3];
+        t0[k] = p0(k / 9) * p0((k / 3) % 3) * p0(k % 3);
+    }
+    const double S = rho0 * kT / cs2, d = 3.0 * cs2 - 1.0;
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b)
+            G[a * Q + b] = S * ((a == b ? 3.0 * cs2 * N[a] : 0.0) + (1.0 - 3.0 * cs2) * t0[a] * t0[b]);
+    auto conserved = [](int k) { return k == 0 || k == 1 || k == 3 || k == 9; };
+    for (int k = 0; k < Q; ++k) A[k * Q + k] = conserved(k) ? 0.0 : 1.0;
+    for (int k : {2, 6, 18, 26}) A[k * Q + 0] = -d;          // p_2a and the sixth order follow +d rho
+    for (int k : {8, 20, 24}) A[k * Q + 0] = d;              // p_2a p_2b follow -d rho
+    for (int k = 0; k < Q; ++k)
+        if (!conserved(k)) Lm[k * Q + k] = lg;
+    for (int k : {4, 10, 12}) Lm[k * Q + k] = ls;
+    for (int a : {2, 6, 18})
+        for (int b : {2, 6, 18}) Lm[a * Q + b] = (lb - ls) / 3.0 + (a == b ? ls : 0.0);
+    for (int a = 0; a < Q; ++a)           // tmp = A G
+        for (int b = 0; b < Q; ++b) {
+            double s = 0.0;
+            for (int c = 0; c < Q; ++c) s += A[a * Q + c] * G[c * Q + b];
+            tmp[a * Q + b] = s;
+        }
+    for (int a = 0; a < Q; ++a)           // Y = A G A^T
+        for (int b = 0; b < Q; ++b) {
+            double s = 0.0;
+            for (int c = 0; c < Q; ++c) s += tmp[a * Q + c] * A[b * Q + c];
+            Y[a * Q + b] = s;
+        }
+    std::vector<double> LY(Q * Q, 0.0);   // Lambda Y
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b) {
+            double s = 0.0;
+            for (int c = 0; c < Q; ++c) s += Lm[a * Q + c] * Y[c * Q + b];
+            LY[a * Q + b] = s;
+        }
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b) {
+            double s = 0.0;               // (Lambda Y Lambda^T)_ab
+            for (int c = 0; c < Q; ++c) s += LY[a * Q + c] * Lm[b * Q + c];
+            X[a * Q + b] = -(LY[b * Q + a] + LY[a * Q + b] + s);
+        }
 }
 
+// lower-triangular Cholesky of the block idx[] of X (row-major, leading dimension Q); pivots
+// that are zero up to 1e-12 of the block's scale are clamped; false for a negative pivot
+static bool cholesky_block(const double* X, int Q, const std::vector<int>& idx, std::vector<double>& L) {
+    const int n = (int)idx.size();
+    L.assign((size_t)n * n, 0.0);
+    double scale = 1e-300;
+    for (int k : idx) scale = std::max(scale, std::fabs(X[k * Q + k]));
+    for (int j = 0; j < n; ++j) {
+        double s = X[idx[j] * Q + idx[j]];
+        for (int q = 0; q < j; ++q) s -= L[j * n + q] * L[j * n + q];
+        if (s <= 1e-12 * scale) {
+            if (s < -1e-9 * scale) return false;
+            continue;
+        }
+        L[j * n + j] = std::sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = X[idx[i] * Q + idx[j]];
+            for (int q = 0; q < j; ++q) t -= L[i * n + q] * L[j * n + q];
+            L[i * n + j] = t / L[j * n + j];
+        }
+    }
+    return true;
+}
+
+// ---- populations in and out; sums ---------------------------------------------------------
+
+// node q of an nx x ny x nz box shifted by (sx, sy, sz) with periodic wrap (|s| <= 1)
+__device__ __forceinline__ long long shifted3(long long q, int nx, int ny, int nz, int sx, int sy, int sz) {
+    const long long nxy = (long long)nx * ny;
+    int z = (int)(q / nxy);
+    const long long r = q - (long long)z * nxy;
+    int y = (int)(r / nx), x = (int)(r - (long long)y * nx);
+    x += sx; y += sy; z += sz;
+    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+    return (long long)z * nxy + (long long)y * nx + x;
+}
+
+// The device holds post-collision deviations (the kernel pulls f_i(r) = f*_i(r - c_i)), so
+// the pre-collision f_i(r) of the ABI is stored at r - c_i: dst(q) = f_i(q + c_i) - fbar_i.
 template <typename R>
-__global__ void get_plane3_kernel(const R* __restrict__ src, double* __restrict__ dst, long long n, double fbar) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        dst[k] = (double)src[k] + fbar;
+__global__ void set_plane3_kernel(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int nz,
+                                  int cx, int cy, int cz, double fbar) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        dst[q] = (R)(src[shifted3(q, nx, ny, nz, cx, cy, cz)] - fbar);
+}
+
+// f_i(r) = stored(r - c_i) + fbar_i
+template <typename R>
+__global__ void get_plane3_kernel(const R* __restrict__ src, double* __restrict__ dst, int nx, int ny, int nz,
+                                  int cx, int cy, int cz, double fbar) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        dst[q] = (double)src[shifted3(q, nx, ny, nz, -cx, -cy, -cz)] + fbar;
 }
 
 // per-block FP64 partial sums of the density and momentum deviations
-template <typename R>
+template <typename LAT, typename R>
 __global__ void sums3_kernel(const R* __restrict__ p, long long n, double* __restrict__ partial) {
     double s[4] = {0, 0, 0, 0};
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        double f[Q3];
 #pragma unroll
-        for (int i = 0; i < Q3; ++i) f[i] = (double)p[i * n + k];
-        double r = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q3; ++i) r += f[i];
-        s[0] += r;
-        s[1] += (f[1] - f[2]) + (f[7] - f[10]) + (f[8] - f[9]) + (f[15] - f[18]) - (f[16] - f[17]);
-        s[2] += (f[3] - f[4]) + (f[7] - f[10]) - (f[8] - f[9]) + (f[11] - f[14]) + (f[12] - f[13]);
-        s[3] += (f[5] - f[6]) + (f[11] - f[14]) - (f[12] - f[13]) + (f[15] - f[18]) + (f[16] - f[17]);
+        for (int i = 0; i < LAT::Q; ++i) {
+            const double f = (double)p[i * n + k];
+            s[0] += f;
+            s[1] += LAT::c(i, 0) * f;
+            s[2] += LAT::c(i, 1) * f;
+            s[3] += LAT::c(i, 2) * f;
+        }
     }
     __shared__ double red[4][256];
 #pragma unroll
@@ -258,11 +618,11 @@ constexpr int SUM3_BLOCKS = 256;
 using namespace lbf3;
 
 struct lb3_ctx {
-    int nx = 0, ny = 0, nz = 0, precision = 0, device = 0, es = 4;
+    int nx = 0, ny = 0, nz = 0, lattice = 19, precision = 0, device = 0, es = 4;
     long long n = 0;
     uint64_t seed = 0;
     double rho0 = 1.0, cs2 = 1.0 / 3.0;
-    double fbar[Q3] = {};
+    double fbar[QMAX] = {};
     char* ws = nullptr;
     void* pop[2] = {nullptr, nullptr};
     double* stage = nullptr;        // one FP64 plane
@@ -274,6 +634,7 @@ struct lb3_ctx {
     Step3Args<float> af{};
     Step3Args<double> ad{};
     dim3 grid;
+    bool plain = false;             // LBFLUCT3_KERNEL=plain: the plain D3Q19 kernel
     cudaStream_t stream = nullptr;
     long long t = 0;
     std::string err;
@@ -306,17 +667,18 @@ bool sizes_ok(int nx, int ny, int nz) {
 }
 
 int es_of(int precision) { return precision == LB_FP32 ? 4 : (precision == LB_FP64 ? 8 : 0); }
+bool lattice_ok(int lattice) { return lattice == LB_D3Q19 || lattice == LB_D3Q27; }
 
 struct Layout3 {
     size_t pop[2], stage, partial, total;
 };
 
-Layout3 layout3(long long n, int es) {
+Layout3 layout3(long long n, int q, int es) {
     Layout3 L{};
     size_t off = 0;
     for (int k = 0; k < 2; ++k) {
         L.pop[k] = off;
-        off = align256(off + (size_t)Q3 * n * es);
+        off = align256(off + (size_t)q * n * es);
     }
     L.stage = off;
     off = align256(off + (size_t)n * sizeof(double));
@@ -356,18 +718,55 @@ int record_timing3(lb3_ctx* c, cudaEvent_t* start, cudaEvent_t* stop) {
 void choose_grid(lb3_ctx* c) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const long long bxy = (long long)((c->nx + 31) / 32) * ((c->ny + 7) / 8);
+    const int tx = c->lattice == 19 ? Lat19::TX : Lat27::TX, ty = c->lattice == 19 ? Lat19::TY : Lat27::TY;
+    const long long bxy = (long long)((c->nx + tx - 1) / tx) * ((c->ny + ty - 1) / ty);
     const long long want = 8LL * sms;
     long long chunks = std::max(1LL, std::min((long long)c->nz, (want + bxy - 1) / bxy));
     const int zc = (int)((c->nz + chunks - 1) / chunks);
     chunks = (c->nz + zc - 1) / zc;
-    c->grid = dim3((c->nx + 31) / 32, (c->ny + 7) / 8, (unsigned)chunks);
+    c->grid = dim3((c->nx + tx - 1) / tx, (c->ny + ty - 1) / ty, (unsigned)chunks);
     c->af.zc = c->ad.zc = zc;
 }
 
+// Xi(0) of the lattice, row-major Q x Q
+void xi_zero(int lattice, double rho0, double cs2, double kT, double tau_s, double tau_b, double tau_g, double* X) {
+    if (lattice == 19) xi_zero19(rho0, cs2, kT, -1.0 / tau_b, -1.0 / tau_s, -1.0 / tau_g, X);
+    else xi_zero27(rho0, cs2, kT, -1.0 / tau_b, -1.0 / tau_s, -1.0 / tau_g, X);
+}
+
+// noise factors of the kernel: sc = sqrt of the diagonal for the uncoupled modes, Lc the
+// coupled block's Cholesky factor; false if Xi(0) is not positive semidefinite
+bool noise_factors(int lattice, const double* X, double sc[QMAX], double Lc[28]) {
+    const int Q = lattice;
+    for (int k = 0; k < QMAX; ++k) sc[k] = 0.0;
+    for (int k = 0; k < 28; ++k) Lc[k] = 0.0;
+    const std::vector<int> coupled = lattice == 19 ? std::vector<int>{4, 16}
+                                                   : std::vector<int>(COUPLED27, COUPLED27 + 7);
+    std::vector<double> L;
+    if (!cholesky_block(X, Q, coupled, L)) return false;
+    const int n = (int)coupled.size();
+    if (lattice == 19) {
+        Lc[0] = L[0];
+        Lc[1] = L[1 * n + 0];
+        Lc[2] = L[1 * n + 1];
+    } else {
+        for (int r = 0; r < n; ++r)
+            for (int q = 0; q <= r; ++q) Lc[r * (r + 1) / 2 + q] = L[r * n + q];
+    }
+    double scale = 1e-300;
+    for (int k = 0; k < Q; ++k) scale = std::max(scale, std::fabs(X[k * Q + k]));
+    for (int k = 0; k < Q; ++k) {
+        if (std::find(coupled.begin(), coupled.end(), k) != coupled.end()) continue;
+        const double v = X[k * Q + k];
+        if (v < -1e-9 * scale) return false;
+        sc[k] = std::sqrt(std::max(v, 0.0));
+    }
+    return true;
+}
+
 template <typename R>
-void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double X[Q3 * Q3],
-               double L44, double L164, double L1616) {
+void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double sc[QMAX],
+               const double Lc[28]) {
     a->nx = c->nx; a->ny = c->ny; a->nz = c->nz; a->P = c->n;
     a->co.rho0 = (R)c->rho0;
     a->co.d = (R)(3.0 * c->cs2 - 1.0);
@@ -375,34 +774,45 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
     a->co.lb = (R)(-1.0 / tau_b);
     a->co.ls = (R)(-1.0 / tau_s);
     a->co.lg = (R)(-1.0 / tau_g);
-    for (int q = 0; q < Q3; ++q) a->sc[q] = (R)(q >= 5 ? std::sqrt(std::max(X[q * Q3 + q], 0.0)) : 0.0);
-    a->L44 = (R)L44; a->L164 = (R)L164; a->L1616 = (R)L1616;
+    for (int q = 0; q < QMAX; ++q) a->sc[q] = (R)sc[q];
+    for (int q = 0; q < 28; ++q) a->Lc[q] = (R)Lc[q];
     a->rk = lbf::make_round_keys(c->seed);
+}
+
+template <typename R>
+cudaError_t launch_any(lb3_ctx* c, const Step3Args<R>& a, int kmode) {
+    if (c->lattice == 19)
+        return kmode ? launch3<Lat19, R, 1>(a, c->grid, c->plain, c->stream)
+                     : launch3<Lat19, R, 0>(a, c->grid, c->plain, c->stream);
+    return kmode ? launch3<Lat27, R, 1>(a, c->grid, false, c->stream)
+                 : launch3<Lat27, R, 0>(a, c->grid, false, c->stream);
 }
 
 }  // namespace
 
 extern "C" {
 
-size_t lb3_workspace_bytes(int nx, int ny, int nz, int precision) {
+size_t lb3_workspace_bytes(int nx, int ny, int nz, int lattice, int precision) {
     const int es = es_of(precision);
-    if (!es || !sizes_ok(nx, ny, nz)) return 0;
-    return layout3((long long)nx * ny * nz, es).total;
+    if (!es || !lattice_ok(lattice) || !sizes_ok(nx, ny, nz)) return 0;
+    return layout3((long long)nx * ny * nz, lattice, es).total;
 }
 
-int lb3_create(int nx, int ny, int nz, int precision, uint64_t seed, double rho0, double cs2, lb3_ctx** out) {
+int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed, double rho0, double cs2,
+               lb3_ctx** out) {
     if (!out) return fail3(nullptr, LB_EINVAL, "out is NULL");
     *out = nullptr;
     const int es = es_of(precision);
+    if (!lattice_ok(lattice)) return fail3(nullptr, LB_EINVAL, "lattice must be LB_D3Q19 or LB_D3Q27");
     if (!es) return fail3(nullptr, LB_EINVAL, "precision must be LB_FP32 or LB_FP64");
     if (!sizes_ok(nx, ny, nz)) return fail3(nullptr, LB_EINVAL, "sizes must be >= 1 with nx*ny*nz < 2^32");
     if (!(rho0 > 0.0) || !std::isfinite(rho0)) return fail3(nullptr, LB_EINVAL, "rho0 must be positive");
     if (!(cs2 > 0.0) || !std::isfinite(cs2)) return fail3(nullptr, LB_EINVAL, "cs2 must be positive");
     lb3_ctx* c = new lb3_ctx();
-    c->nx = nx; c->ny = ny; c->nz = nz; c->n = (long long)nx * ny * nz;
+    c->nx = nx; c->ny = ny; c->nz = nz; c->n = (long long)nx * ny * nz; c->lattice = lattice;
     c->precision = precision; c->es = es; c->seed = seed; c->rho0 = rho0; c->cs2 = cs2;
     cudaGetDevice(&c->device);
-    const Layout3 L = layout3(c->n, es);
+    const Layout3 L = layout3(c->n, lattice, es);
     cudaError_t e = cudaMalloc((void**)&c->ws, L.total);
     if (e != cudaSuccess) {
         delete c;
@@ -412,13 +822,17 @@ int lb3_create(int nx, int ny, int nz, int precision, uint64_t seed, double rho0
     c->pop[1] = c->ws + L.pop[1];
     c->stage = (double*)(c->ws + L.stage);
     c->partial = (double*)(c->ws + L.partial);
-    rest19(rho0, cs2, c->fbar);
-    e = cudaMemset(c->pop[0], 0, (size_t)Q3 * c->n * es);
-    if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, (size_t)Q3 * c->n * es);
+    rest_pops(lattice, rho0, cs2, c->fbar);
+    e = cudaMemset(c->pop[0], 0, (size_t)lattice * c->n * es);
+    if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, (size_t)lattice * c->n * es);
     if (e != cudaSuccess) {
         cudaFree(c->ws);
         delete c;
         return fail3(nullptr, LB_ECUDA, std::string("lb3_create: ") + cudaGetErrorString(e));
+    }
+    {
+        const char* v = std::getenv("LBFLUCT3_KERNEL");
+        c->plain = v && std::strcmp(v, "plain") == 0 && lattice == 19;
     }
     choose_grid(c);
     *out = c;
@@ -443,10 +857,12 @@ int lb3_set_stream(lb3_ctx* c, void* stream) {
     return LB_OK;
 }
 
-int lb3_noise_matrix(double rho0, double cs2, double kT, double tau_s, double tau_b, double tau_ghost, double* xi) {
-    if (!xi || !(rho0 > 0) || !(cs2 > 0) || kT < 0 || !(tau_s > 0.5) || !(tau_b > 0.5) || !(tau_ghost > 0.5))
+int lb3_noise_matrix(int lattice, double rho0, double cs2, double kT, double tau_s, double tau_b, double tau_ghost,
+                     double* xi) {
+    if (!xi || !lattice_ok(lattice) || !(rho0 > 0) || !(cs2 > 0) || kT < 0 || !(tau_s > 0.5) || !(tau_b > 0.5) ||
+        !(tau_ghost > 0.5))
         return LB_EINVAL;
-    xi_zero19(rho0, cs2, kT, -1.0 / tau_b, -1.0 / tau_s, -1.0 / tau_ghost, xi);
+    xi_zero(lattice, rho0, cs2, kT, tau_s, tau_b, tau_ghost, xi);
     return LB_OK;
 }
 
@@ -458,25 +874,17 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
     if (!(kT >= 0.0) || !std::isfinite(kT)) return fail3(c, LB_EINVAL, "kT must be >= 0");
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return fail3(c, LB_EINVAL, "kappa must be >= 0");
     if (mode != LB_NOISE_OFF && mode != LB_NOISE_LW)
-        return fail3(c, LB_EINVAL, "the D3Q19 lattice takes LB_NOISE_OFF or LB_NOISE_LW");
-    double X[Q3 * Q3];
-    xi_zero19(c->rho0, c->cs2, kT, -1.0 / tau_b, -1.0 / tau_s, -1.0 / tau_ghost, X);
-    double L44 = 0, L164 = 0, L1616 = 0;
-    if (mode == LB_NOISE_LW && kT > 0) {
-        const double x44 = X[4 * Q3 + 4], x416 = X[4 * Q3 + 16], x1616 = X[16 * Q3 + 16];
-        const double scale = std::max(std::fabs(x44), std::fabs(x1616));
-        const double tol = 1e-12 * scale;
-        if (x44 < -tol || x1616 < -tol || x44 * x1616 - x416 * x416 < -tol * scale)
-            return fail3(c, LB_ENOTPSD, "Xi(0) is not positive semidefinite (needs cs2 <= 5/9)");
-        L44 = x44 > tol ? std::sqrt(x44) : 0.0;
-        L164 = L44 > 0 ? x416 / L44 : 0.0;
-        L1616 = std::sqrt(std::max(x1616 - L164 * L164, 0.0));
-    }
+        return fail3(c, LB_EINVAL, "the 3-D lattices take LB_NOISE_OFF or LB_NOISE_LW");
+    std::vector<double> X((size_t)c->lattice * c->lattice);
+    xi_zero(c->lattice, c->rho0, c->cs2, kT, tau_s, tau_b, tau_ghost, X.data());
+    double sc[QMAX] = {}, Lc[28] = {};
+    if (mode == LB_NOISE_LW && kT > 0 && !noise_factors(c->lattice, X.data(), sc, Lc))
+        return fail3(c, LB_ENOTPSD, "Xi(0) is not positive semidefinite");
     c->kT = kT;
     c->kappa = kappa;
     c->noise_mode = mode;
-    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, X, L44, L164, L1616);
-    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, X, L44, L164, L1616);
+    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc);
+    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc);
     c->have_params = true;
     return LB_OK;
 }
@@ -503,15 +911,15 @@ int lb3_step(lb3_ctx* c, int64_t nsteps) {
             a.src = (const double*)c->pop[c->cur];
             a.dst = (double*)c->pop[c->cur ^ 1];
             a.t_lo = tlo; a.t_hi = thi;
-            e = kmode ? launch3<double, 1>(a, c->grid, c->stream) : launch3<double, 0>(a, c->grid, c->stream);
+            e = launch_any(c, a, kmode);
         } else {
             Step3Args<float> a = c->af;
             a.src = (const float*)c->pop[c->cur];
             a.dst = (float*)c->pop[c->cur ^ 1];
             a.t_lo = tlo; a.t_hi = thi;
-            e = kmode ? launch3<float, 1>(a, c->grid, c->stream) : launch3<float, 0>(a, c->grid, c->stream);
+            e = launch_any(c, a, kmode);
         }
-        if (e != cudaSuccess) return cuda_fail3(c, e, "D3Q19 step kernel launch");
+        if (e != cudaSuccess) return cuda_fail3(c, e, "3-D step kernel launch");
         c->kernels += 1;
         if (tm) {
             e = cudaEventRecord(e1, c->stream);
@@ -535,19 +943,20 @@ static unsigned plane_blocks(long long n) { return (unsigned)std::min<long long>
 int lb3_set_populations(lb3_ctx* c, const double* f, int loc, int64_t t) {
     if (!c || !f || (loc != LB_HOST && loc != LB_DEVICE) || t < 0) return LB_EINVAL;
     lbf::DeviceGuard dg(c->device);
-    for (int i = 0; i < Q3; ++i) {
+    for (int i = 0; i < c->lattice; ++i) {
         const double* src = f + (long long)i * c->n;
         if (loc == LB_HOST) {
             cudaError_t e = cudaMemcpyAsync(c->stage, src, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream);
             if (e != cudaSuccess) return cuda_fail3(c, e, "H2D");
             src = c->stage;
         }
+        const int cx = c_of(c->lattice, i, 0), cy = c_of(c->lattice, i, 1), cz = c_of(c->lattice, i, 2);
         if (c->precision == LB_FP64)
             set_plane3_kernel<double><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                src, (double*)c->pop[c->cur] + (long long)i * c->n, c->n, c->fbar[i]);
+                src, (double*)c->pop[c->cur] + (long long)i * c->n, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
         else
             set_plane3_kernel<float><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                src, (float*)c->pop[c->cur] + (long long)i * c->n, c->n, c->fbar[i]);
+                src, (float*)c->pop[c->cur] + (long long)i * c->n, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail3(c, e, "set populations");
         c->kernels += 1;
@@ -561,14 +970,15 @@ int lb3_set_populations(lb3_ctx* c, const double* f, int loc, int64_t t) {
 int lb3_get_populations(lb3_ctx* c, double* f, int loc) {
     if (!c || !f || (loc != LB_HOST && loc != LB_DEVICE)) return LB_EINVAL;
     lbf::DeviceGuard dg(c->device);
-    for (int i = 0; i < Q3; ++i) {
+    for (int i = 0; i < c->lattice; ++i) {
         double* dst = loc == LB_HOST ? c->stage : f + (long long)i * c->n;
+        const int cx = c_of(c->lattice, i, 0), cy = c_of(c->lattice, i, 1), cz = c_of(c->lattice, i, 2);
         if (c->precision == LB_FP64)
             get_plane3_kernel<double><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                (const double*)c->pop[c->cur] + (long long)i * c->n, dst, c->n, c->fbar[i]);
+                (const double*)c->pop[c->cur] + (long long)i * c->n, dst, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
         else
             get_plane3_kernel<float><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                (const float*)c->pop[c->cur] + (long long)i * c->n, dst, c->n, c->fbar[i]);
+                (const float*)c->pop[c->cur] + (long long)i * c->n, dst, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail3(c, e, "get populations");
         c->kernels += 1;
@@ -586,10 +996,22 @@ int lb3_get_populations(lb3_ctx* c, double* f, int loc) {
 int lb3_sums(lb3_ctx* c, double sums[4]) {
     if (!c || !sums) return LB_EINVAL;
     lbf::DeviceGuard dg(c->device);
-    if (c->precision == LB_FP64)
-        sums3_kernel<double><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const double*)c->pop[c->cur], c->n, c->partial);
-    else
-        sums3_kernel<float><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const float*)c->pop[c->cur], c->n, c->partial);
+    const bool d = c->precision == LB_FP64;
+    if (c->lattice == 19) {
+        if (d)
+            sums3_kernel<Lat19, double><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const double*)c->pop[c->cur], c->n,
+                                                                           c->partial);
+        else
+            sums3_kernel<Lat19, float><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const float*)c->pop[c->cur], c->n,
+                                                                          c->partial);
+    } else {
+        if (d)
+            sums3_kernel<Lat27, double><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const double*)c->pop[c->cur], c->n,
+                                                                           c->partial);
+        else
+            sums3_kernel<Lat27, float><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const float*)c->pop[c->cur], c->n,
+                                                                          c->partial);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail3(c, e, "sums kernel");
     c->kernels += 1;

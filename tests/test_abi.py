@@ -104,3 +104,14 @@ def test_library_d3q19_noise_matrix_matches_oracle(lib, cs2, tau):
     m = d3.Model(rho0=0.9, cs2=cs2, kappa=0.03, kT=3e-5, tau_s=tau[0], tau_b=tau[1], tau_ghost=tau[2])
     X = lbf.lb3_noise_matrix(0.9, cs2, 3e-5, *tau)
     np.testing.assert_allclose(X, m.Xi_zero(), rtol=1e-12, atol=1e-13 * np.abs(X).max())
+
+
+@pytest.mark.parametrize("cs2,tau", [(1 / 3, (1.0, 1.0, 1.0)), (0.2, (0.8, 1.1, 0.9)), (0.12, (1.3, 0.7, 1.05))])
+def test_library_d3q27_noise_matrix_matches_oracle(lib, cs2, tau):
+    # the library's rank-one ansatz route against the oracle's T diag(fbar) T^T and Omega
+    from oracle import d3q27 as d
+    m = d.Model(rho0=0.9, cs2=cs2, kappa=0.03, kT=3e-5, tau_s=tau[0], tau_b=tau[1], tau_ghost=tau[2])
+    X = lbf.lb3_noise_matrix(0.9, cs2, 3e-5, *tau, lattice=lbf.LB_D3Q27)
+    np.testing.assert_allclose(X, m.Xi_zero(), rtol=1e-12, atol=1e-13 * np.abs(X).max())
+    with pytest.raises(lbf.LBError):
+        lbf.lb3_noise_matrix(0.9, cs2, 3e-5, *tau, lattice=15)

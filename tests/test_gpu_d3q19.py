@@ -52,14 +52,20 @@ def _pair(nx, ny, nz, mode, precision=lbf.LB_FP32, cs2=0.25, rho0=1.0, seed=7, a
 SIZES = [(32, 8, 4), (37, 11, 5), (64, 16, 9), (5, 3, 2), (1, 1, 8), (40, 1, 3), (3, 17, 1)]
 
 
+@pytest.fixture(params=["staged", "plain"])
+def kernel3(request, monkeypatch):
+    monkeypatch.setenv("LBFLUCT3_KERNEL", request.param)
+    return request.param
+
+
 @pytest.mark.parametrize("nx,ny,nz", SIZES)
 @pytest.mark.parametrize("mode", [lbf.LB_NOISE_OFF, lbf.LB_NOISE_LW])
-def test_fp32_step_follows_the_oracle(nx, ny, nz, mode):
+def test_fp32_step_follows_the_oracle(nx, ny, nz, mode, kernel3):
     g, o = _pair(nx, ny, nz, mode)
     g.step(6)
     o.step(6)
     err = np.abs(g.populations() - o.f).max()
-    print("D3Q19 FP32 %dx%dx%d mode %d: %.2e" % (nx, ny, nz, mode, err))
+    print("D3Q19 FP32 %s %dx%dx%d mode %d: %.2e" % (kernel3, nx, ny, nz, mode, err))
     assert err <= TOL
     if mode == lbf.LB_NOISE_LW:
         q = d3.Lattice(nx, ny, nz, rho0=1.0, cs2=0.25, seed=7)
@@ -71,7 +77,7 @@ def test_fp32_step_follows_the_oracle(nx, ny, nz, mode):
 
 @pytest.mark.parametrize("nx,ny,nz", [(32, 8, 4), (37, 11, 5), (6, 5, 7)])
 @pytest.mark.parametrize("mode", [lbf.LB_NOISE_OFF, lbf.LB_NOISE_LW])
-def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode):
+def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode, kernel3):
     # 25 % perturbations (clipped at 3.5 sigma): kappa (grad rho)^2 and rho u u are ~1e-3 per
     # step here, far above the 1e-12 bar, so a dropped or mis-wired term fails
     g, o = _pair(nx, ny, nz, mode, precision=lbf.LB_FP64, amp=0.25, clip=3.5,
@@ -79,7 +85,7 @@ def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode):
     g.step(4)
     o.step(4)
     err = np.abs(g.populations() - o.f).max()
-    print("D3Q19 FP64 %dx%dx%d mode %d: %.2e" % (nx, ny, nz, mode, err))
+    print("D3Q19 FP64 %s %dx%dx%d mode %d: %.2e" % (kernel3, nx, ny, nz, mode, err))
     assert err <= TOL64
     # the same run without the kappa terms differs by far more than the bar
     q = d3.Lattice(nx, ny, nz, rho0=1.0, cs2=0.25, seed=7)
@@ -89,13 +95,13 @@ def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode):
     assert np.abs(q.f - o.f).max() > 1e3 * TOL64
 
 
-def test_fp32_nonlinear_terms_at_large_amplitude():
+def test_fp32_nonlinear_terms_at_large_amplitude(kernel3):
     # the FP32 kernel on the 25 % state: the bar is the FP32 rounding of the step's terms
     g, o = _pair(37, 11, 5, lbf.LB_NOISE_LW, amp=0.25, clip=3.5, params=(1e-4, 0.08, 0.8, 1.1, 0.9))
     g.step(3)
     o.step(3)
     err = np.abs(g.populations() - o.f).max()
-    print("D3Q19 FP32 nonlinear: %.2e" % err)
+    print("D3Q19 FP32 nonlinear %s: %.2e" % (kernel3, err))
     assert err <= 2e-6
 
 

@@ -1,0 +1,198 @@
+"""The D3Q27 step on the GPU (include/lbfluct3d.h, LB_D3Q27) against the FP64 oracle
+(oracle/d3q27.py): whole lattices element by element (exact tiles, ragged tails, one-node
+axes), with and without the uncorrelated noise of Xi(0), FP32 at the population bar and FP64
+to rounding at large amplitude; sampled nodes of one step at the benchmark size;
+conservation; errors; equipartition of the ideal fluctuating gas with replica z-scores."""
+import numpy as np
+import pytest
+
+import paper_1009_0254_gb300 as lbf
+from oracle import d3q27 as d
+from paper_1009_0254_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+TOL64 = 1e-12
+S2 = 1.0 / 3.0
+PARAMS = (1e-4, 0.04, 0.8, 1.1, 0.9)       # kT, kappa, tau_s, tau_b, tau_ghost
+Q = 27
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_0254_gb300 import build
+    build.build()
+    lbf.load()
+
+
+def _state(nx, ny, nz, m, seed, amp=0.01, clip=None):
+    shape = (Q, nz, ny, nx)
+    pert = synth.gaussian_field(shape, seed=seed, scale=amp) if clip is None else \
+        synth.clipped_gaussian_field(shape, seed, amp, clip)
+    return m.fbar()[:, None, None, None] * (1.0 + pert)
+
+
+def _pair(nx, ny, nz, mode, precision=lbf.LB_FP32, cs2=0.25, seed=7, amp=0.01, clip=None, params=PARAMS):
+    g = lbf.Lattice3(nx, ny, nz, seed=seed, cs2=cs2, precision=precision, lattice=lbf.LB_D3Q27)
+    g.set_params(*params, mode)
+    o = d.Lattice(nx, ny, nz, cs2=cs2, seed=seed)
+    o.set_params(*params, {lbf.LB_NOISE_OFF: d.NOISE_OFF, lbf.LB_NOISE_LW: d.NOISE_LW}[mode])
+    f0 = _state(nx, ny, nz, o.model, seed + 100, amp, clip)
+    g.set_populations(f0, t=0)
+    o.f = f0.copy()
+    return g, o
+
+
+SIZES = [(32, 4, 3), (37, 11, 5), (64, 8, 9), (5, 3, 2), (1, 1, 6), (40, 1, 3), (3, 9, 1)]
+
+
+@pytest.mark.parametrize("nx,ny,nz", SIZES)
+@pytest.mark.parametrize("mode", [lbf.LB_NOISE_OFF, lbf.LB_NOISE_LW])
+def test_fp32_step_follows_the_oracle(nx, ny, nz, mode):
+    g, o = _pair(nx, ny, nz, mode)
+    g.step(5)
+    o.step(5)
+    err = np.abs(g.populations() - o.f).max()
+    print("D3Q27 FP32 %dx%dx%d mode %d: %.2e" % (nx, ny, nz, mode, err))
+    assert err <= TOL
+    if mode == lbf.LB_NOISE_LW:
+        q = d.Lattice(nx, ny, nz, cs2=0.25, seed=7)
+        q.set_params(*PARAMS, d.NOISE_OFF)
+        q.f = _state(nx, ny, nz, q.model, 107)
+        q.step(5)
+        assert np.abs(q.f - o.f).max() > 100 * TOL
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(32, 4, 3), (37, 11, 5), (6, 5, 7)])
+@pytest.mark.parametrize("mode", [lbf.LB_NOISE_OFF, lbf.LB_NOISE_LW])
+def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode):
+    params = (1e-4, 0.08, 0.8, 1.1, 0.9)
+    g, o = _pair(nx, ny, nz, mode, precision=lbf.LB_FP64, amp=0.25, clip=3.5, params=params)
+    g.step(4)
+    o.step(4)
+    err = np.abs(g.populations() - o.f).max()
+    print("D3Q27 FP64 %dx%dx%d mode %d: %.2e" % (nx, ny, nz, mode, err))
+    assert err <= TOL64
+    q = d.Lattice(nx, ny, nz, cs2=0.25, seed=7)
+    q.set_params(1e-4, 0.0, 0.8, 1.1, 0.9, d.NOISE_OFF if mode == lbf.LB_NOISE_OFF else d.NOISE_LW)
+    q.f = _state(nx, ny, nz, q.model, 107, 0.25, 3.5)
+    q.step(4)
+    assert np.abs(q.f - o.f).max() > 1e3 * TOL64          # the kappa terms matter here
+
+
+def test_fp32_nonlinear_terms_at_large_amplitude():
+    g, o = _pair(37, 11, 5, lbf.LB_NOISE_LW, amp=0.25, clip=3.5, params=(1e-4, 0.08, 0.8, 1.1, 0.9))
+    g.step(3)
+    o.step(3)
+    err = np.abs(g.populations() - o.f).max()
+    print("D3Q27 FP32 nonlinear: %.2e" % err)
+    assert err <= 2e-6
+
+
+WAVES = np.random.default_rng(13)
+KVEC = WAVES.integers(0, 192, size=(Q, 3, 3))
+PHASE = WAVES.uniform(0, 2 * np.pi, size=(Q, 3))
+
+
+def _wave_state(fbar, n, z, y, x, amp, xp=np):
+    out = []
+    for i in range(Q):
+        s = 0.0
+        for w in range(3):
+            kx, ky, kz = (int(v) for v in KVEC[i, w])
+            s = s + xp.sin((2 * np.pi / n) * ((kx * x + ky * y + kz * z) % n) + float(PHASE[i, w]))
+        out.append(fbar[i] * (1.0 + amp * s))
+    return out
+
+
+def _patch_step(m, n, centre, seed, t, L, amp):
+    z0, y0, x0 = centre
+    zs, ys, xs = ((np.arange(c - 2, c + 3)) % n for c in (z0, y0, x0))
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    sub = np.array(_wave_state(m.fbar(), n, Z, Y, X, amp))
+    nodes = (Z * n + Y) * n + X
+    return d.step(sub, m, d.noise_lw_nodes(m, nodes, seed, t, L))[:, 2, 2, 2]
+
+
+def test_sampled_nodes_at_the_benchmark_size():
+    # 192^3, FP32, uncorrelated noise: the benchmark's launch configuration
+    import torch
+    n, amp = 192, 0.01
+    m = d.Model(1.0, 0.25, PARAMS[1], PARAMS[0], PARAMS[2], PARAMS[3], PARAMS[4])
+    g = lbf.Lattice3(n, n, n, seed=5, cs2=0.25, lattice=lbf.LB_D3Q27)
+    g.set_params(*PARAMS, lbf.LB_NOISE_LW)
+    dev = torch.empty((Q, n, n, n), dtype=torch.float64, device="cuda")
+    r = torch.arange(n, device="cuda", dtype=torch.float64)
+    Z, Y, X = torch.meshgrid(r, r, r, indexing="ij")
+    for i, plane in enumerate(_wave_state(m.fbar(), n, Z, Y, X, amp, xp=torch)):
+        dev[i] = plane
+    del Z, Y, X
+    lbf.lb3_set_populations(g.ctx, dev, lbf.LB_DEVICE, 3)
+    g.step(1)
+    lbf.lb3_get_populations(g.ctx, dev, lbf.LB_DEVICE)
+    torch.cuda.synchronize()
+    L = m.noise_factor()
+    rng = np.random.default_rng(1)
+    picks = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 0, 31), (96, 96, 0), (7, 8, n - 1)]
+    picks += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(16)]
+    err = 0.0
+    for c in picks:
+        got = dev[:, c[0], c[1], c[2]].cpu().numpy()
+        err = max(err, np.abs(got - _patch_step(m, n, c, 5, 3, L, amp)).max())
+    print("D3Q27 192^3 sampled: %.2e" % err)
+    assert err <= TOL
+    del dev, g
+    torch.cuda.empty_cache()
+
+
+def test_mass_and_momentum_are_conserved():
+    g = lbf.Lattice3(24, 20, 16, seed=3, cs2=0.2, precision=lbf.LB_FP64, lattice=lbf.LB_D3Q27)
+    g.set_params(1e-4, 0.03, 0.8, 1.1, 0.9, lbf.LB_NOISE_LW)
+    g.set_populations(_state(24, 20, 16, d.Model(1.0, 0.2), 9, 0.02), t=0)
+    s0 = g.sums()
+    g.step(300)
+    np.testing.assert_allclose(g.sums(), s0, rtol=0, atol=1e-10)
+
+
+def test_errors():
+    with pytest.raises(lbf.LBError) as e:
+        lbf.Lattice3(8, 8, 8, lattice=21)
+    assert e.value.code == lbf.LB_EINVAL
+    g = lbf.Lattice3(8, 8, 8, lattice=lbf.LB_D3Q27)
+    with pytest.raises(lbf.LBError) as e:
+        g.step(1)
+    assert e.value.code == lbf.LB_ESTATE
+    with pytest.raises(lbf.LBError) as e:
+        g.set_params(1e-4, 0.0, 1.0, 1.0, 1.0, lbf.LB_NOISE_FULL)
+    assert e.value.code == lbf.LB_EINVAL
+
+
+def test_ideal_fluctuating_gas_is_in_equipartition():
+    from scipy.stats import t as student
+    rho0, kT = 1.0, 1e-4
+    nx = ny = nz = 10
+    n = nx * ny * nz
+    R, samples, every, burn = 32, 50, 25, 200
+    mbar = d.Model(rho0, S2).mbar()[:, None, None, None]
+    acc = np.zeros((R, Q))
+    for r in range(R):
+        g = lbf.Lattice3(nx, ny, nz, seed=2000 + r, rho0=rho0, cs2=S2, lattice=lbf.LB_D3Q27)
+        g.set_params(kT, 0.0, 0.8, 1.1, 0.9, lbf.LB_NOISE_LW)
+        g.step(burn)
+        for _ in range(samples):
+            g.step(every)
+            dm = np.einsum("ai,i...->a...", d.T, g.populations()) - mbar
+            acc[r] += (dm.reshape(Q, -1) ** 2).mean(axis=1)
+        acc[r] /= samples
+    want = d.N * rho0 * kT / S2
+    want[d.CONSERVED] *= 1 - 1 / n
+    mean = acc.mean(axis=0)
+    sd = acc.std(axis=0, ddof=1) / np.sqrt(R)
+    z = (mean - want) / sd
+    bound = float(student.isf(0.01 / (2 * Q), R - 1))
+    print("D3Q27 GPU equipartition ratios", np.round(mean / want, 4), "max |z| %.2f (bound %.2f)"
+          % (np.abs(z).max(), bound))
+    assert np.abs(z).max() < bound

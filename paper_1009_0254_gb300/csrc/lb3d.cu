@@ -181,44 +181,63 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY) step3_staged_kernel(const S
     // offsets in I: 32-bit when all Q planes fit in 2^32 elements, else 64-bit
     const I PI = (I)P;
 
+    // The tile-and-ring positions a thread stages are the same on every plane: their validity
+    // and the nine in-plane offsets (x - cx) + (y - cy) nx, indexed (1 - cy) 3 + (1 - cx), are
+    // formed once.
+    constexpr int KP = (RN + NT - 1) / NT;
+    I yx[KP][9];
+    bool valid[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        const int q = tid + k * NT;
+        const int ly = q / RX, lx = q - ly * RX;
+        int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        valid[k] = q < RN && gx <= nx && gy <= ny;      // others are never read by a node
+        gx = wrap_hi(wrap_lo(gx, nx), nx);
+        gy = wrap_hi(wrap_lo(gy, ny), ny);
+        const I Xo[3] = {(I)(gx == 0 ? nx - 1 : gx - 1), (I)gx, (I)(gx == nx - 1 ? 0 : gx + 1)};
+        const I Yo[3] = {(I)(gy == 0 ? ny - 1 : gy - 1) * (I)nx, (I)gy * (I)nx,
+                         (I)(gy == ny - 1 ? 0 : gy + 1) * (I)nx};
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) yx[k][3 * b + c] = Yo[b] + Xo[c];
+    }
+
     // issue the pulled populations of plane zz (an integer in [-1, nz]) into raw slot k
-    auto issue = [&](int zz, int k) {
+    auto issue = [&](int zz, int slot_k) {
         const int zc = wrap_hi(wrap_lo(zz, nz), nz);
-        // offsets of r - c along each axis, indexed by 1 - c
+        // plane offsets of z - cz, indexed by 1 - cz
         const I Zo[3] = {(I)(zc == 0 ? nz - 1 : zc - 1) * (I)nxy, (I)zc * (I)nxy,
                          (I)(zc == nz - 1 ? 0 : zc + 1) * (I)nxy};
-        R* slot = raw + k * Q * RN;
-        for (int q = tid; q < RN; q += NT) {
-            const int ly = q / RX, lx = q - ly * RX;
-            int gx = x0 + lx - 1, gy = y0 + ly - 1;
-            if (gx > nx || gy > ny) continue;       // never read by a node of the lattice
-            gx = wrap_hi(wrap_lo(gx, nx), nx);
-            gy = wrap_hi(wrap_lo(gy, ny), ny);
-            const I Xo[3] = {(I)(gx == 0 ? nx - 1 : gx - 1), (I)gx, (I)(gx == nx - 1 ? 0 : gx + 1)};
-            const I Yo[3] = {(I)(gy == 0 ? ny - 1 : gy - 1) * (I)nx, (I)gy * (I)nx,
-                             (I)(gy == ny - 1 ? 0 : gy + 1) * (I)nx};
+        R* slot = raw + slot_k * Q * RN;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            if (!valid[k]) continue;
+            const int q = tid + k * NT;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const I off = Zo[1 - LAT::c(i, 2)] + Yo[1 - LAT::c(i, 1)] + Xo[1 - LAT::c(i, 0)];
-                cp_async_elem<sizeof(R)>(slot + i * RN + q, src + ((I)i * PI + off));
+                const I off = (I)i * PI + Zo[1 - LAT::c(i, 2)] + yx[k][3 * (1 - LAT::c(i, 1)) + (1 - LAT::c(i, 0))];
+                cp_async_elem<sizeof(R)>(slot + i * RN + q, src + off);
             }
         }
         cp_async_commit();
     };
     // density deviations of the plane in raw slot k into density slot k
-    auto density = [&](int k) {
-        const R* slot = raw + k * Q * RN;
-        for (int q = tid; q < RN; q += NT) {
-            const int ly = q / RX, lx = q - ly * RX;
-            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    auto density = [&](int slot_k) {
+        const R* slot = raw + slot_k * Q * RN;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int q = tid + k * NT;
+            if (q >= RN) continue;
             R v = R(0);
-            if (gx <= nx && gy <= ny) {
+            if (valid[k]) {
                 R f[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) f[i] = slot[i * RN + q];
                 v = drho_of<LAT>(f);
             }
-            rs[k * RN + q] = v;
+            rs[slot_k * RN + q] = v;
         }
     };
 

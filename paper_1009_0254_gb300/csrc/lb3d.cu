@@ -7,7 +7,9 @@
 // populations of each plane, for the tile and its one-node ring, are staged in shared
 // memory by asynchronous copies (three rotating slots: the plane being collided, the plane
 // whose densities are summed, and the plane in flight), so the loads of plane z+2 overlap
-// the collision of plane z.  The densities of planes z-1, z, z+1 sit in three more rotating
+// the collision of plane z.  With two slots (D3Q27's default: its smaller shared-memory
+// footprint fits four CTAs per SM instead of three) a plane's own populations move to
+// registers when its densities are summed.  The densities of planes z-1, z, z+1 sit in three more rotating
 // slots; the collision reads its own node's populations and its 3x3x3 density neighbourhood
 // from shared memory.  Every population is read once from DRAM (the ring's re-reads hit L2)
 // and written once: 2 Q sizeof(storage) bytes per node.
@@ -164,13 +166,21 @@ __device__ __forceinline__ R drho_of(const R* f) {
 }
 
 // The staged step kernel: one CTA per TX x TY tile and run of zc planes.
-template <typename LAT, typename R, int MODE, typename I>
-__global__ void __launch_bounds__(LAT::TX * LAT::TY) step3_staged_kernel(const Step3Args<R> a) {
+// resident CTAs per SM the register budget is sized for: what the shared memory of the
+// three-slot (two-slot) pipeline admits
+template <typename LAT, int SLOTS>
+constexpr int staged_min_blocks() {
+    return LAT::Q == 19 ? (SLOTS == 3 ? 2 : 3) : (SLOTS == 3 ? 3 : 4);
+}
+
+template <typename LAT, typename R, int MODE, typename I, int SLOTS>
+__global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, SLOTS>())
+    step3_staged_kernel(const Step3Args<R> a) {
     constexpr int Q = LAT::Q, TX = LAT::TX, TY = LAT::TY;
     constexpr int RX = TX + 2, RY = TY + 2, RN = RX * RY, NT = TX * TY;
     extern __shared__ __align__(16) unsigned char smem3[];
-    R* raw = reinterpret_cast<R*>(smem3);                   // [3][Q][RN] pulled populations
-    R* rs = raw + 3 * Q * RN;                               // [3][RN] density deviations
+    R* raw = reinterpret_cast<R*>(smem3);                   // [SLOTS][Q][RN] pulled populations
+    R* rs = raw + SLOTS * Q * RN;                           // [3][RN] density deviations
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long P = a.P, nxy = (long long)nx * ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -223,8 +233,8 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY) step3_staged_kernel(const S
         }
         cp_async_commit();
     };
-    // density deviations of the plane in raw slot k into density slot k
-    auto density = [&](int slot_k) {
+    // density deviations of the plane in raw slot slot_k into density slot dk
+    auto density = [&](int slot_k, int dk) {
         const R* slot = raw + slot_k * Q * RN;
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY) step3_staged_kernel(const S
                 for (int i = 0; i < Q; ++i) f[i] = slot[i * RN + q];
                 v = drho_of<LAT>(f);
             }
-            rs[slot_k * RN + q] = v;
+            rs[dk * RN + q] = v;
         }
     };
 
@@ -246,26 +256,8 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY) step3_staged_kernel(const S
     const bool own = x < nx && y < ny;
     const int qc = (ly + 1) * RX + lx + 1;
 
-    // planes z0-1, z0 -> slots 0, 1; plane z0+1 -> slot 2 (in flight)
-    issue(z0 - 1, 0);
-    issue(z0, 1);
-    cp_async_wait_all();
-    __syncthreads();
-    density(0);
-    density(1);
-    issue(z0 + 1, 2);
-    for (int z = z0; z < z1; ++z) {
-        const int k0 = (z - z0 + 1) % 3, km = (k0 + 2) % 3, kp = (k0 + 1) % 3;   // slots of z, z-1, z+1
-        cp_async_wait_all();
-        __syncthreads();
-        density(kp);
-        if (z + 1 < z1) issue(z + 2, km);          // plane z-1's slot is free
-        __syncthreads();
-        if (!own) continue;
-        const R* sl = raw + k0 * Q * RN;
-        R f[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = sl[i * RN + qc];
+    // the collision of plane z from its pulled values f and density slots of z, z-1, z+1
+    auto collide_plane = [&](int z, const R (&f)[Q], int k0, int km, int kp) {
         const R* d0 = rs + k0 * RN + qc;
         const R* dm = rs + km * RN + qc;
         const R* dp = rs + kp * RN + qc;
@@ -302,6 +294,62 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY) step3_staged_kernel(const S
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) a.dst[(I)i * PI + node] = o[i];
+    };
+
+    if constexpr (SLOTS == 3) {
+        // planes z0-1, z0 -> slots 0, 1; plane z0+1 -> slot 2 (in flight); density slots alike
+        issue(z0 - 1, 0);
+        issue(z0, 1);
+        cp_async_wait_all();
+        __syncthreads();
+        density(0, 0);
+        density(1, 1);
+        issue(z0 + 1, 2);
+        for (int z = z0; z < z1; ++z) {
+            const int k0 = (z - z0 + 1) % 3, km = (k0 + 2) % 3, kp = (k0 + 1) % 3;   // slots of z, z-1, z+1
+            cp_async_wait_all();
+            __syncthreads();
+            density(kp, kp);
+            if (z + 1 < z1) issue(z + 2, km);          // plane z-1's slot is free
+            __syncthreads();
+            if (!own) continue;
+            const R* sl = raw + k0 * Q * RN;
+            R f[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = sl[i * RN + qc];
+            collide_plane(z, f, k0, km, kp);
+        }
+    } else {
+        // two raw slots: a plane's own pulled values move to registers when its densities are
+        // summed, which frees its slot for the plane after next
+        R fcur[Q], fnext[Q];
+        auto take = [&](int k, R (&f)[Q]) {
+            const R* sl = raw + k * Q * RN;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = own ? sl[i * RN + qc] : R(0);
+        };
+        issue(z0 - 1, 0);
+        issue(z0, 1);
+        cp_async_wait_all();
+        __syncthreads();
+        density(0, 0);                 // plane z0-1 -> density slot 0
+        density(1, 1);                 // plane z0 -> density slot 1
+        take(1, fcur);
+        __syncthreads();
+        issue(z0 + 1, 0);              // raw slot of plane p: (p - z0 + 1) % 2
+        for (int z = z0; z < z1; ++z) {
+            const int k0 = (z - z0 + 1) % 3, km = (k0 + 2) % 3, kp = (k0 + 1) % 3;
+            const int rp = (z - z0) & 1;             // raw slot of plane z+1
+            cp_async_wait_all();
+            __syncthreads();
+            if (z + 1 < z1) issue(z + 2, rp ^ 1);    // the slot of plane z, already in registers
+            density(rp, kp);
+            take(rp, fnext);
+            __syncthreads();
+            if (own) collide_plane(z, fcur, k0, km, kp);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) fcur[i] = fnext[i];
+        }
     }
     cp_async_wait_all();
 }
@@ -415,14 +463,14 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
     }
 }
 
-template <typename LAT, typename R>
+template <typename LAT, typename R, int SLOTS>
 constexpr int staged_smem_bytes() {
-    return (3 * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) * (int)sizeof(R);
+    return (SLOTS * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) * (int)sizeof(R);
 }
 
-template <typename LAT, typename R, int MODE, typename I>
+template <typename LAT, typename R, int MODE, typename I, int SLOTS>
 static cudaError_t launch_staged(const Step3Args<R>& a, dim3 grid, cudaStream_t s) {
-    constexpr int smem = staged_smem_bytes<LAT, R>();
+    constexpr int smem = staged_smem_bytes<LAT, R, SLOTS>();
     // the shared-memory limit is a per-device attribute of the function: set it once per
     // device (a repeated set from a concurrent first launch is harmless)
     static std::atomic<unsigned> done{0};
@@ -430,25 +478,29 @@ static cudaError_t launch_staged(const Step3Args<R>& a, dim3 grid, cudaStream_t 
     cudaGetDevice(&dev);
     const unsigned bit = 1u << (dev & 31);
     if (!(done.load(std::memory_order_acquire) & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(step3_staged_kernel<LAT, R, MODE, I>,
+        cudaError_t e = cudaFuncSetAttribute(step3_staged_kernel<LAT, R, MODE, I, SLOTS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         done.fetch_or(bit, std::memory_order_release);
     }
-    step3_staged_kernel<LAT, R, MODE, I><<<grid, LAT::TX * LAT::TY, smem, s>>>(a);
+    step3_staged_kernel<LAT, R, MODE, I, SLOTS><<<grid, LAT::TX * LAT::TY, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename LAT, typename R, int MODE>
-static cudaError_t launch3(const Step3Args<R>& a, dim3 grid, bool plain, cudaStream_t s) {
+static cudaError_t launch3(const Step3Args<R>& a, dim3 grid, bool plain, int slots, cudaStream_t s) {
     if constexpr (LAT::Q == 19) {
         if (plain) {
             step3_kernel<R, MODE, 32, 8><<<grid, 256, 0, s>>>(a);
             return cudaGetLastError();
         }
     }
-    if ((unsigned long long)a.P * LAT::Q < (1ULL << 32)) return launch_staged<LAT, R, MODE, uint32_t>(a, grid, s);
-    return launch_staged<LAT, R, MODE, unsigned long long>(a, grid, s);
+    const bool narrow = (unsigned long long)a.P * LAT::Q < (1ULL << 32);
+    if (slots == 2)
+        return narrow ? launch_staged<LAT, R, MODE, uint32_t, 2>(a, grid, s)
+                      : launch_staged<LAT, R, MODE, unsigned long long, 2>(a, grid, s);
+    return narrow ? launch_staged<LAT, R, MODE, uint32_t, 3>(a, grid, s)
+                  : launch_staged<LAT, R, MODE, unsigned long long, 3>(a, grid, s);
 }
 
 // ---- host-side theory --------------------------------------------------------------------
@@ -654,6 +706,8 @@ struct lb3_ctx {
     Step3Args<double> ad{};
     dim3 grid;
     bool plain = false;             // LBFLUCT3_KERNEL=plain: the plain D3Q19 kernel
+    int slots = 3;                  // raw slots of the staged kernel: 3 for D3Q19, 2 for D3Q27
+                                    // (the measured faster; LBFLUCT3_SLOTS=2 or 3 overrides)
     cudaStream_t stream = nullptr;
     long long t = 0;
     std::string err;
@@ -801,10 +855,10 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
 template <typename R>
 cudaError_t launch_any(lb3_ctx* c, const Step3Args<R>& a, int kmode) {
     if (c->lattice == 19)
-        return kmode ? launch3<Lat19, R, 1>(a, c->grid, c->plain, c->stream)
-                     : launch3<Lat19, R, 0>(a, c->grid, c->plain, c->stream);
-    return kmode ? launch3<Lat27, R, 1>(a, c->grid, false, c->stream)
-                 : launch3<Lat27, R, 0>(a, c->grid, false, c->stream);
+        return kmode ? launch3<Lat19, R, 1>(a, c->grid, c->plain, c->slots, c->stream)
+                     : launch3<Lat19, R, 0>(a, c->grid, c->plain, c->slots, c->stream);
+    return kmode ? launch3<Lat27, R, 1>(a, c->grid, false, c->slots, c->stream)
+                 : launch3<Lat27, R, 0>(a, c->grid, false, c->slots, c->stream);
 }
 
 }  // namespace
@@ -852,6 +906,8 @@ int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed
     {
         const char* v = std::getenv("LBFLUCT3_KERNEL");
         c->plain = v && std::strcmp(v, "plain") == 0 && lattice == 19;
+        const char* sv = std::getenv("LBFLUCT3_SLOTS");
+        c->slots = sv ? (std::atoi(sv) == 2 ? 2 : 3) : (lattice == 27 ? 2 : 3);
     }
     choose_grid(c);
     *out = c;

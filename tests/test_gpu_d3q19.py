@@ -52,9 +52,11 @@ def _pair(nx, ny, nz, mode, precision=lbf.LB_FP32, cs2=0.25, rho0=1.0, seed=7, a
 SIZES = [(32, 8, 4), (37, 11, 5), (64, 16, 9), (5, 3, 2), (1, 1, 8), (40, 1, 3), (3, 17, 1)]
 
 
-@pytest.fixture(params=["staged", "plain"])
+@pytest.fixture(params=["staged", "staged2", "plain"])
 def kernel3(request, monkeypatch):
-    monkeypatch.setenv("LBFLUCT3_KERNEL", request.param)
+    # the staged kernel with three raw slots (the default here), with two, and the plain kernel
+    monkeypatch.setenv("LBFLUCT3_KERNEL", "plain" if request.param == "plain" else "staged")
+    monkeypatch.setenv("LBFLUCT3_SLOTS", "2" if request.param == "staged2" else "3")
     return request.param
 
 

@@ -166,15 +166,22 @@ __device__ __forceinline__ R drho_of(const R* f) {
 }
 
 // The staged step kernel: one CTA per TX x TY tile and run of zc planes.
-// resident CTAs per SM the register budget is sized for: what the shared memory of the
-// three-slot (two-slot) pipeline admits
-template <typename LAT, int SLOTS>
+template <typename LAT, typename R, int SLOTS>
+constexpr int staged_smem_bytes() {
+    return (SLOTS * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) * (int)sizeof(R);
+}
+
+// resident CTAs per SM the register budget is sized for: as many as the shared memory admits
+// (227 KB per SM, 1 KB reserved per CTA), at most 2048 threads
+template <typename LAT, typename R, int SLOTS>
 constexpr int staged_min_blocks() {
-    return LAT::Q == 19 ? (SLOTS == 3 ? 2 : 3) : (SLOTS == 3 ? 3 : 4);
+    constexpr int by_smem = (227 * 1024) / (staged_smem_bytes<LAT, R, SLOTS>() + 1024);
+    constexpr int by_threads = 2048 / (LAT::TX * LAT::TY);
+    return by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads);
 }
 
 template <typename LAT, typename R, int MODE, typename I, int SLOTS>
-__global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, SLOTS>())
+__global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, SLOTS>())
     step3_staged_kernel(const Step3Args<R> a) {
     constexpr int Q = LAT::Q, TX = LAT::TX, TY = LAT::TY;
     constexpr int RX = TX + 2, RY = TY + 2, RN = RX * RY, NT = TX * TY;
@@ -461,11 +468,6 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
         }
         __syncthreads();
     }
-}
-
-template <typename LAT, typename R, int SLOTS>
-constexpr int staged_smem_bytes() {
-    return (SLOTS * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) * (int)sizeof(R);
 }
 
 template <typename LAT, typename R, int MODE, typename I, int SLOTS>

@@ -35,6 +35,18 @@ Indices: velocities and moments are array positions 0..18; f[i, z, y, x].
 Random numbers: two Philox4x32-10 draws per node and step with counter (node, t mod 2^32,
 t div 2^32, tag), node = (z ny + y) nx + x; tag 4 gives nu_4..nu_11, tag 5 gives
 nu_12..nu_18 (its last normal unused), each word one Box-Muller pair as for D2Q9.
+
+Correlated noise (Sec. III C, Eq. noise-matrix at every k): with the ansatz the advection
+drops out of the fluctuation-dissipation relation (A(k) G(k) A(-k)^T = G(k), the phases of
+a diagonal matrix cancel), so Xi(k) is the long-wavelength form at c_s^2(k) = cs2 + rho0
+kappa s(k), s the Laplacian symbol; only the (4,16) block depends on k, affinely in s.  s is
+multilinear in (cos kx, cos ky, cos kz), so Xi(k) is the multilinear interpolation of its
+values at the eight corners k in {0, pi}^3 (s = 0, 4, 16/3, 4 for 0..3 components at pi):
+eight white 2-vector fields nu_abc per node (a, b, c = +-1; + for k = 0), each times the
+Cholesky factor of the (4,16) block at its corner, combined as
+h_d(r) = (1/8) sum_abc a^dx b^dy c^dz L_abc nu_abc(r) and summed over the 2x2x2 box,
+xi(r) = sum_d h_d(r - d), give (xi_4, xi_16) with covariance Xi(k) at every k.  Their draws:
+tags 10 and 11, word w of the pair -> corner w = 4 ia + 2 ib + ic (sign +1 for index 0).
 """
 from __future__ import annotations
 
@@ -264,12 +276,84 @@ def noise_lw(model: Model, nx, ny, nz, seed: int, step_index: int, L=None) -> np
     return np.einsum("ab,b...->a...", L, nu)
 
 
-NOISE_OFF, NOISE_LW = 0, 1
+# --- correlated noise (Sec. III C, Eq. noise-matrix) ------------------------------------------
+
+TAG_RS = (10, 11)
+
+
+def lattice_s(kx, ky, kz):
+    """Symbol of the Laplacian stencil: -lap e^{ik.r} = s(k) e^{ik.r},
+    s = 6 sum_{i != 0} w_i (1 - cos k.c_i)."""
+    kv = np.stack(np.broadcast_arrays(np.asarray(kx, float), np.asarray(ky, float), np.asarray(kz, float)), axis=-1)
+    return 6.0 * sum(W[i] * (1.0 - np.cos(kv @ C[i].astype(float))) for i in range(1, Q))
+
+
+def Xi_k(model: Model, kx, ky, kz) -> np.ndarray:
+    """Xi(k) = A(k) G(k) A(-k)^T - (1 + Omega(k)) G(k) (1 + Omega(k))^T, Eq. (noise-matrix), with
+    G(k) the ansatz (S(k)/rho0) T diag(fbar(k)) T^T and the density dependence of the
+    equilibrium through c_s^2(k) = cs2 + rho0 kappa s(k) (Eq. sound-speed-k)."""
+    c2k = model.cs2 + model.rho0 * model.kappa * float(lattice_s(kx, ky, kz))
+    dk = 3.0 * (c2k - SIGMA_S2)
+    mb = np.zeros(Q)
+    mb[0] = model.rho0
+    mb[4], mb[16] = dk * model.rho0, -dk * model.rho0
+    G = (model.kT / c2k) * (T @ np.diag(TINV @ mb) @ T.T)
+    O = np.diag(model.lam).astype(complex)
+    O[4, 0] = -model.lam[4] * dk
+    O[16, 0] = model.lam[16] * dk
+    ph = np.exp(-1j * (C.astype(float) @ np.array([kx, ky, kz], dtype=float)))
+    A = T @ np.diag(ph) @ TINV
+    Am = T @ np.diag(np.conj(ph)) @ TINV
+    IO = np.eye(Q) + O
+    X = A @ G @ Am.T - IO @ G @ IO.T
+    return X.real
+
+
+CORNERS = [(1 if (w >> 2) & 1 == 0 else -1, 1 if (w >> 1) & 1 == 0 else -1, 1 if w & 1 == 0 else -1)
+           for w in range(8)]
+
+
+def rs_factors(model: Model) -> np.ndarray:
+    """2x2 Cholesky factors of the (4,16) block of Xi at the eight corners (sign +1: k = 0)."""
+    out = np.zeros((8, 2, 2))
+    for w, (a, b, c) in enumerate(CORNERS):
+        k = [0.0 if v > 0 else np.pi for v in (a, b, c)]
+        X = Xi_k(model, *k)
+        out[w] = cholesky_psd(np.array([[X[4, 4], X[4, 16]], [X[16, 4], X[16, 16]]]))
+    return out
+
+
+def rs_fields(nx, ny, nz, seed: int, step_index: int) -> np.ndarray:
+    """nu[w, 2, z, y, x]: the white 2-vector of corner w at every node."""
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.uint32)
+    g = np.concatenate([normals(idx, seed, step_index, t) for t in TAG_RS], axis=1)     # (n, 16)
+    return g.T.reshape(8, 2, nz, ny, nx)
+
+
+def xi416_rs(model: Model, nx, ny, nz, seed: int, step_index: int, Ls=None) -> np.ndarray:
+    """(xi_4, xi_16)[2, z, y, x] of the real-space construction (module docstring)."""
+    if Ls is None:
+        Ls = rs_factors(model)
+    nu = rs_fields(nx, ny, nz, seed, step_index)
+    v = np.einsum("wab,wb...->wa...", Ls, nu)                 # L_abc nu_abc
+    out = np.zeros((2, nz, ny, nx))
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                h = sum((CORNERS[w][0] ** dx) * (CORNERS[w][1] ** dy) * (CORNERS[w][2] ** dz) * v[w]
+                        for w in range(8)) / 8.0
+                out += np.roll(h, shift=(dz, dy, dx), axis=(1, 2, 3))      # h_d(r - d)
+    return out
+
+
+NOISE_OFF, NOISE_LW, NOISE_FULL_RS = 0, 1, 4
 
 
 class Lattice:
     """A periodic nx x ny x nz D3Q19 lattice: f[19, nz, ny, nx] pre-collision populations,
-    t the index of the next collision (it keys the random numbers)."""
+    t the index of the next collision (it keys the random numbers).  Noise: NOISE_LW (Xi(0))
+    or NOISE_FULL_RS (Xi(k), the (4,16) block built in real space, the other modes as LW)."""
 
     def __init__(self, nx, ny, nz, rho0=1.0, cs2=SIGMA_S2, seed=42):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
@@ -279,17 +363,25 @@ class Lattice:
         self.t = 0
         self.f = np.broadcast_to(self.model.fbar()[:, None, None, None], (Q, nz, ny, nx)).copy()
         self._L = None
+        self._Ls = None
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
         self.model = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
         self.mode = int(noise_mode)
-        self._L = self.model.noise_factor() if (self.mode == NOISE_LW and kT > 0) else None
+        noisy = self.mode in (NOISE_LW, NOISE_FULL_RS) and kT > 0
+        self._L = self.model.noise_factor() if noisy else None
+        self._Ls = rs_factors(self.model) if (noisy and self.mode == NOISE_FULL_RS) else None
+
+    def noise(self, t=None):
+        t = self.t if t is None else t
+        xi = noise_lw(self.model, self.nx, self.ny, self.nz, self.seed, t, self._L)
+        if self._Ls is not None:
+            xi[[4, 16]] = xi416_rs(self.model, self.nx, self.ny, self.nz, self.seed, t, self._Ls)
+        return xi
 
     def step(self, nsteps=1):
         for _ in range(int(nsteps)):
-            xi = None
-            if self._L is not None:
-                xi = noise_lw(self.model, self.nx, self.ny, self.nz, self.seed, self.t, self._L)
+            xi = self.noise() if self._L is not None else None
             self.f = step(self.f, self.model, xi)
             self.t += 1
         return self

@@ -305,3 +305,134 @@ def test_ideal_fluctuating_gas_is_in_equipartition():
     print("equipartition ratios", np.round(mean / want, 3))
     assert np.abs(mean / want - 1).max() < 0.05
     assert np.abs(z).max() < 4.0
+
+
+# --- correlated noise Xi(k) (Sec. III C, Eq. noise-matrix) ---------------------------------
+
+@pytest.mark.parametrize("k", [(0.0, 0.0, 0.0), (np.pi, 0.0, 0.0), (np.pi, np.pi, 0.0), (np.pi, np.pi, np.pi),
+                               (0.3, 1.1, -2.0), (2.0, 2.5, 0.7)])
+def test_noise_matrix_at_k_is_the_long_wavelength_form_at_cs2_k(k):
+    # the FDT of Eq. (noise-matrix) with advection A(k) and the k-dependent ansatz against the
+    # hand-derived Xi(0) closed forms evaluated at c_s^2(k) = cs2 + rho0 kappa s(k)
+    m = d3.Model(rho0=0.9, cs2=0.25, kappa=0.03, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    X = d3.Xi_k(m, *k)
+    s = float(d3.lattice_s(*k))
+    m2 = d3.Model(rho0=0.9, cs2=0.25 + 0.9 * 0.03 * s, kappa=0.03, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    np.testing.assert_allclose(X, m2.Xi_zero(), rtol=1e-12, atol=1e-13 * 1e-4)
+    assert np.abs(X[:4]).max() < 1e-18
+
+
+def test_lattice_symbol_at_the_corners_and_its_small_k_limit():
+    # s(k) = k^2 + O(k^4) (Appendix B's stencil is isotropic) and the corner values 0, 4, 16/3, 4
+    k = np.array([0.01, -0.02, 0.015])
+    assert abs(float(d3.lattice_s(*k)) / (k @ k) - 1) < 1e-3
+    for kk, want in [((0, 0, 0), 0.0), ((np.pi, 0, 0), 4.0), ((0, np.pi, np.pi), 16 / 3), ((np.pi,) * 3, 4.0)]:
+        assert abs(float(d3.lattice_s(*kk)) - want) < 1e-12
+
+
+def test_real_space_construction_reproduces_Xi_k_at_every_wavevector():
+    # transfer function of the 2x2x2 box: sum_abc L L^T |(1/8) sum_d a^dx b^dy c^dz e^{-i k.d}|^2
+    # must equal the (4,16) block of Xi(k) from the FDT at every k of a 6 x 5 x 4 lattice
+    m = d3.Model(rho0=1.0, cs2=0.2, kappa=0.04, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    Ls = d3.rs_factors(m)
+    for mz in range(4):
+        for my in range(5):
+            for mx in range(6):
+                k = (2 * np.pi * mx / 6, 2 * np.pi * my / 5, 2 * np.pi * mz / 4)
+                got = np.zeros((2, 2))
+                for w, (a, b, c) in enumerate(d3.CORNERS):
+                    t = sum((a ** dx) * (b ** dy) * (c ** dz) * np.exp(-1j * (k[0] * dx + k[1] * dy + k[2] * dz))
+                            for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)) / 8.0
+                    got += abs(t) ** 2 * (Ls[w] @ Ls[w].T)
+                X = d3.Xi_k(m, *k)
+                want = np.array([[X[4, 4], X[4, 16]], [X[16, 4], X[16, 16]]])
+                np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-18)
+
+
+def test_real_space_fields_have_the_Xi_k_spectrum():
+    # sampled: the generated (xi_4, xi_16) fields' spectral covariance at a few k against Xi(k)
+    m = d3.Model(rho0=1.0, cs2=0.2, kappa=0.04, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    n = 6
+    Ls = d3.rs_factors(m)
+    acc = np.zeros((2, 2, n, n, n), dtype=complex)
+    draws = 400
+    for t in range(draws):
+        xi = d3.xi416_rs(m, n, n, n, seed=9, step_index=t, Ls=Ls)
+        xk = np.fft.fftn(xi, axes=(1, 2, 3)) / np.sqrt(n ** 3)
+        acc += np.einsum("a...,b...->ab...", xk, np.conj(xk))
+    acc /= draws
+    for (mz, my, mx) in [(0, 0, 1), (0, 3, 3), (3, 3, 3), (1, 2, 5), (0, 0, 0)]:
+        k = (2 * np.pi * mx / n, 2 * np.pi * my / n, 2 * np.pi * mz / n)
+        X = d3.Xi_k(m, *k)
+        want = np.array([[X[4, 4], X[4, 16]], [X[16, 4], X[16, 16]]])
+        got = acc[:, :, mz, my, mx].real
+        sd = np.sqrt((np.abs(np.diag(want))[:, None] * np.abs(np.diag(want))[None, :] + want ** 2) / draws)
+        assert np.abs(got - want).max() < 5 * sd.max(), (k, got, want)
+
+
+def _spectra(L, n):
+    m = L.moments()
+    drho = np.fft.fftn(m[0] - L.model.rho0) / np.sqrt(n ** 3)
+    j = [np.fft.fftn(m[a]) / np.sqrt(n ** 3) for a in (1, 2, 3)]
+    return np.abs(drho) ** 2, sum(np.abs(x) ** 2 for x in j) / 3
+
+
+@pytest.mark.parametrize("mode", ["rs", "lw"])
+def test_correlated_noise_equilibrates_every_wavevector(mode):
+    # Sec. V A in three dimensions: with Xi(k) the density spectrum is the Ornstein-Zernike
+    # S(k) = rho0 kT / c_s^2(k) and the momentum spectrum rho0 kT at every k; with the
+    # long-wavelength Xi(0) alone the largest wavevectors stay out of equipartition
+    n, R, steps, burn = 4, 4, 500, 80
+    cs2, kappa, kT = 0.2, 0.04, 1e-4       # Xi(k) positive semidefinite up to s = 16/3
+    S_acc = np.zeros((n, n, n))
+    J_acc = np.zeros((n, n, n))
+    cnt = 0
+    for r in range(R):
+        L = d3.Lattice(n, n, n, cs2=cs2, seed=300 + r)
+        L.set_params(kT, kappa, 0.8, 1.1, 0.9, d3.NOISE_FULL_RS if mode == "rs" else d3.NOISE_LW)
+        L.step(burn)
+        for t in range(steps):
+            L.step(1)
+            if t % 2 == 0:
+                s_, j_ = _spectra(L, n)
+                S_acc += s_
+                J_acc += j_
+                cnt += 1
+    S_acc /= cnt
+    J_acc /= cnt
+    k1 = 2 * np.pi * np.fft.fftfreq(n)
+    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")       # arrays [z, y, x]
+    s = d3.lattice_s(KX, KY, KZ)
+    S_th = 1.0 * kT / (cs2 + kappa * s)
+    ratio_S = (S_acc / S_th).ravel()[1:]
+    # j_a at k = pi e_a is the staggered-momentum invariant (next test): those three never
+    # equilibrate, as (pi, 0) and (0, pi) on D2Q9
+    keep = np.ones((n, n, n), bool)
+    keep[0, 0, 0] = keep[0, 0, n // 2] = keep[0, n // 2, 0] = keep[n // 2, 0, 0] = False
+    ratio_J = (J_acc / kT)[keep]
+    print(mode, "S ratio range %.3f..%.3f, J ratio range %.3f..%.3f" % (ratio_S.min(), ratio_S.max(),
+                                                                        ratio_J.min(), ratio_J.max()))
+    if mode == "rs":
+        assert np.abs(ratio_S - 1).max() < 0.12 and np.abs(ratio_J - 1).max() < 0.12
+        assert abs(ratio_S.mean() - 1) < 0.02 and abs(ratio_J.mean() - 1) < 0.02
+    else:
+        assert np.abs(ratio_S - 1).max() > 0.2          # the long-wavelength noise misses large k
+
+
+def test_staggered_momentum_is_an_invariant_of_the_noisy_step():
+    # sum_r (-1)^x j_x(r) (and its y, z analogues): streaming multiplies every population with
+    # c_x = +-1 by -1 at k = (pi, 0, 0), the collision conserves j and the noise has no
+    # momentum component, so the staggered momentum only changes sign each step
+    n = 4
+    L = d3.Lattice(n, n, n, cs2=0.2, seed=4)
+    L.set_params(1e-4, 0.04, 0.8, 1.1, 0.9, d3.NOISE_FULL_RS)
+    L.f = L.f * (1.0 + synth.gaussian_field(L.f.shape, seed=2, scale=0.01))
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    def stag():
+        m = L.moments()
+        return np.array([((-1.0) ** x * m[1]).sum(), ((-1.0) ** y * m[2]).sum(), ((-1.0) ** z * m[3]).sum()])
+    s0 = stag()
+    assert np.abs(s0).min() > 1e-4
+    for t in range(1, 6):
+        L.step(1)
+        np.testing.assert_allclose(stag(), (-1) ** t * s0, atol=1e-14)

@@ -85,6 +85,7 @@ def parse():
                    help="run only the three-dimensional variant on an N^3 lattice and print its JSON "
                         "(profiling runs; --lattice 19 or 27)")
     p.add_argument("--lattice", type=int, default=19, choices=[19, 27])
+    p.add_argument("--d3-noise", default="lw", choices=["lw", "rs"])
     p.add_argument("--noise", default="lw", choices=["lw", "full", "rs"],
                    help="noise of the main line (full: correlated via k-space, rs: correlated built in real "
                         "space, both at kappa=0.05; for profiling runs)")
@@ -318,14 +319,16 @@ def timed_run(lbf, torch, L, steps, warmup, mode, params, dist):
     return ms, kms, kl, launches, wall0, wall1
 
 
-def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5):
+def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5, noise="lw"):
     """A three-dimensional lattice (the paper's model carried to D3Q19 or D3Q27): n^3 FP32
     (2 x 19 x 67 MB or 2 x 27 x 67 MB of populations at n = 256, larger than L2), cs2 = 1/3,
-    uncorrelated noise of Xi(0), the PARAMS_LW relaxation times and kappa; one kernel launch
-    per step.  Algorithmic bytes: Q FP32 populations read and Q written per node."""
+    uncorrelated noise of Xi(0) (noise="lw") or, on D3Q19, the correlated noise Xi(k) built in
+    real space (noise="rs"), the PARAMS_LW relaxation times and kappa; one kernel launch per
+    step.  Algorithmic bytes: Q FP32 populations read and Q written per node."""
     L = lbf.Lattice3(n, n, n, seed=42, rho0=1.0, cs2=1.0 / 3.0, lattice=lattice)
     p = PARAMS_LW
-    L.set_params(p["kT"], p["kappa"], p["tau_s"], p["tau_b"], p["tau_ghost"], lbf.LB_NOISE_LW)
+    mode = lbf.LB_NOISE_FULL_RS if noise == "rs" else lbf.LB_NOISE_LW
+    L.set_params(p["kT"], p["kappa"], p["tau_s"], p["tau_b"], p["tau_ghost"], mode)
     L.step(warmup)
     torch.cuda.synchronize()
     lbf.lb3_set_kernel_timing(L.ctx, max(1, steps // 100))
@@ -345,7 +348,9 @@ def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5):
     bpn = 2 * lattice * 4
     k_s = kms / max(kl, 1) / 1e3
     L.close()
-    return {"lattice": "D3Q%d %d^3, FP32 deviations" % (lattice, n), "noise": "long-wavelength",
+    return {"lattice": "D3Q%d %d^3, FP32 deviations" % (lattice, n),
+            "noise": "correlated, built in real space (2x2x2 stencil of eight white fields)" if noise == "rs"
+            else "long-wavelength",
             "kappa": p["kappa"], "value": nodes * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
             "ms_per_step": ms / steps,
             "step_kernel": {"achieved": bpn * nodes / k_s / 1e9, "unit": "GB/s",
@@ -586,7 +591,7 @@ def main():
         return 0
     if args.d3_only:
         print(json.dumps(d3_variant(lbf, torch, peaks()[0], args.lattice, n=args.d3_only, steps=args.steps,
-                                    warmup=args.warmup)))
+                                    warmup=args.warmup, noise=args.d3_noise)))
         return 0
     if args.serve_study:
         big = (512 * 512, 1)      # lattices of 512^2 and more: one at a time
@@ -668,6 +673,7 @@ def main():
     # the three-dimensional lattices
     if not args.no_variants and not main_fp16:
         variants.append(d3_variant(lbf, torch, hbm, 19))
+        variants.append(d3_variant(lbf, torch, hbm, 19, noise="rs"))
         variants.append(d3_variant(lbf, torch, hbm, 27))
 
     # batched ensemble and request server (rank 0 of a single-GPU run)

@@ -17,7 +17,18 @@
  *     that is uniform along one axis evolve, at equal relaxation times, as the D2Q9 model of
  *     [GACV] Table II;
  *   - noise: spatially uncorrelated with covariance Xi(0) of [GACV] Eq. (noise-matrix-k0),
- *     xi = L nu, L the Cholesky factor of the block of the non-conserved modes.
+ *     xi = L nu, L the Cholesky factor of the block of the non-conserved modes (LB_NOISE_LW);
+ *     or, on D3Q19, spatially correlated with covariance Xi(k) of [GACV] Eq. (noise-matrix) at
+ *     every k (LB_NOISE_FULL_RS): with the ansatz of Eq. (f-correl-yeo) the advection drops
+ *     out of the fluctuation-dissipation relation, so Xi(k) is Xi(0) at c_s^2(k) = cs2 +
+ *     rho0 kappa s(k) (Eq. sound-speed-k, s the Laplacian symbol); only the (4,16) block
+ *     depends on k, affinely in s, and s is multilinear in (cos kx, cos ky, cos kz), so Xi(k)
+ *     is the multilinear interpolation of its values at the corners k in {0, pi}^3 (s = 0, 4,
+ *     16/3, 4 for 0..3 components at pi).  Eight white 2-vector fields nu_abc per node
+ *     (a, b, c = +-1; +1 for k = 0), each times the Cholesky factor L_abc of the (4,16) block
+ *     at its corner, combined as h_d(r) = (1/8) sum_abc a^dx b^dy c^dz L_abc nu_abc(r), give
+ *     (xi_4, xi_16)(r) = sum over d in {0,1}^3 of h_d(r - d), with exactly the covariance
+ *     Xi(k); Xi must be positive semidefinite at s = 0, 4, 16/3.  The other modes as LB_NOISE_LW.
  *
  * LB_D3Q19 (19 velocities, weights 1/3, 1/18, 1/36)
  *   - modes: the weighted-orthogonal basis of Duenweg, Schiller & Ladd, Phys. Rev. E 76,
@@ -28,7 +39,9 @@
  *     6 (0,0,-1); 7 (1,1,0), 8 (1,-1,0), 9 (-1,1,0), 10 (-1,-1,0); 11 (0,1,1), 12 (0,1,-1),
  *     13 (0,-1,1), 14 (0,-1,-1); 15 (1,0,1), 16 (-1,0,1), 17 (1,0,-1), 18 (-1,0,-1);
  *   - random numbers: tag 4 gives nu_4..nu_11, tag 5 gives nu_12..nu_18; xi_a = sqrt(Xi_aa) nu_a
- *     except xi_4 = L_44 nu_4, xi_16 = L_16,4 nu_4 + L_16,16 nu_16.
+ *     except xi_4 = L_44 nu_4, xi_16 = L_16,4 nu_4 + L_16,16 nu_16 (LB_NOISE_LW); the corner
+ *     fields of LB_NOISE_FULL_RS from tags 10 and 11, word w of the pair giving nu of corner
+ *     w = 4 ia + 2 ib + ic (index 0: sign +1).
  * LB_D3Q27 (27 velocities, weights the products of the D1Q3 weights 2/3, 1/6, 1/6)
  *   - velocity i = 9 ix + 3 iy + iz with c = (v[ix], v[iy], v[iz]), v = (0, 1, -1);
  *   - modes: the products m_(a,b,c) = sum_i p_a(c_ix) p_b(c_iy) p_c(c_iz) f_i of p_0 = 1,
@@ -89,9 +102,10 @@ int lb3_destroy(lb3_ctx* ctx);
 int lb3_set_stream(lb3_ctx* ctx, void* stream);
 
 /*
- * Sets kT, kappa, the relaxation times (each > 1/2) and the noise mode (LB_NOISE_OFF or
- * LB_NOISE_LW).  With noise, Xi(0) must be positive semidefinite (D3Q19: cs2 <= 5/9), else
- * LB_ENOTPSD.
+ * Sets kT, kappa, the relaxation times (each > 1/2) and the noise mode (LB_NOISE_OFF,
+ * LB_NOISE_LW, or on D3Q19 LB_NOISE_FULL_RS; others LB_EINVAL).  With noise, Xi(0) (and with
+ * LB_NOISE_FULL_RS Xi at s = 4 and 16/3) must be positive semidefinite (D3Q19: c_s^2 <= 5/9),
+ * else LB_ENOTPSD.
  */
 int lb3_set_params(lb3_ctx* ctx, double kT, double kappa, double tau_s, double tau_b, double tau_ghost,
                    int noise_mode);

@@ -85,6 +85,8 @@ struct Step3Args {
     R sc[QMAX];                   // sqrt(Xi_kk) of the modes with a diagonal factor
     R Lc[28];                     // the coupled block's Cholesky factor: D3Q19 (L44, L16_4, L16_16);
                                   // D3Q27 the 7 x 7 lower triangle, row-major
+    R Lrs[9];                     // D3Q19 correlated noise: Cholesky factors (L11, L21, L22) of the
+                                  // (4,16) block of Xi at s = 0, 4, 16/3
     uint32_t t_lo, t_hi;
     lbf::RoundKeys rk;
 };
@@ -165,29 +167,39 @@ __device__ __forceinline__ R drho_of(const R* f) {
     }
 }
 
-// The staged step kernel: one CTA per TX x TY tile and run of zc planes.
-template <typename LAT, typename R, int SLOTS>
+// D3Q19 correlated noise: the tags of the two draws of the eight corner fields
+constexpr uint32_t TAG_RS0 = 10;
+
+// The staged step kernel: one CTA per TX x TY tile and run of zc planes.  With correlated
+// noise (MODE 3) it also holds the 2x2x2-box contributions: for the tile plus its left column
+// and bottom row, the in-plane half (four 2-vectors) of the current plane and the upward half
+// of the current and the previous plane.
+template <typename LAT, typename R, int SLOTS, int MODE>
 constexpr int staged_smem_bytes() {
-    return (SLOTS * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) * (int)sizeof(R);
+    return ((SLOTS * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) +
+            (MODE == 3 ? 24 * (LAT::TX + 1) * (LAT::TY + 1) : 0)) * (int)sizeof(R);
 }
 
 // resident CTAs per SM the register budget is sized for: as many as the shared memory admits
 // (227 KB per SM, 1 KB reserved per CTA), at most 2048 threads
-template <typename LAT, typename R, int SLOTS>
+template <typename LAT, typename R, int SLOTS, int MODE>
 constexpr int staged_min_blocks() {
-    constexpr int by_smem = (227 * 1024) / (staged_smem_bytes<LAT, R, SLOTS>() + 1024);
+    constexpr int by_smem = (227 * 1024) / (staged_smem_bytes<LAT, R, SLOTS, MODE>() + 1024);
     constexpr int by_threads = 2048 / (LAT::TX * LAT::TY);
     return by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads);
 }
 
 template <typename LAT, typename R, int MODE, typename I, int SLOTS>
-__global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, SLOTS>())
+__global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, SLOTS, MODE>())
     step3_staged_kernel(const Step3Args<R> a) {
     constexpr int Q = LAT::Q, TX = LAT::TX, TY = LAT::TY;
     constexpr int RX = TX + 2, RY = TY + 2, RN = RX * RY, NT = TX * TY;
     extern __shared__ __align__(16) unsigned char smem3[];
     R* raw = reinterpret_cast<R*>(smem3);                   // [SLOTS][Q][RN] pulled populations
     R* rs = raw + SLOTS * Q * RN;                           // [3][RN] density deviations
+    constexpr int HW = TX + 1, HN = HW * (TY + 1);
+    R* Hin = rs + 3 * RN;                                   // MODE 3: [8][HN] in-plane half
+    R* Hup = Hin + 8 * HN;                                  // MODE 3: [2][8][HN] upward half
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long P = a.P, nxy = (long long)nx * ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -263,8 +275,56 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
     const bool own = x < nx && y < ny;
     const int qc = (ly + 1) * RX + lx + 1;
 
+    // MODE 3: the eight white 2-vectors nu_w of every position of plane zz (tile, left column,
+    // bottom row), times the factor of their corner (w = 4 ia + 2 ib + ic, sign -1 for a set
+    // bit: k = pi), combined by a Walsh-Hadamard transform into h_m = (1/8) sum_w
+    // (-1)^{popcount(w & m)} L_w nu_w, m = 4 dx + 2 dy + dz: the in-plane half (dz = 0) into Hin
+    // when keep_in, the upward half (dz = 1) into buffer ub
+    auto stencil_plane = [&](int zz, bool keep_in, int ub) {
+        const int zc = wrap_hi(wrap_lo(zz, nz), nz);
+        for (int p = tid; p < HN; p += NT) {
+            const int hy = p / HW - 1, hx = p - (hy + 1) * HW - 1;
+            int gx = x0 + hx, gy = y0 + hy;
+            if (gx >= nx || gy >= ny) continue;         // never read by a node of the lattice
+            gx = wrap_lo(gx, nx);
+            gy = wrap_lo(gy, ny);
+            const uint32_t node = ((uint32_t)zc * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx;
+            const uint4 r0 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0), a.rk);
+            const uint4 r1 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0 + 1), a.rk);
+            const uint32_t wd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            R vx[8], vy[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                R n0, n1;
+                lbf::gauss_word(wd[w], &n0, &n1);
+                const int pc = (w & 1) + ((w >> 1) & 1) + ((w >> 2) & 1);      // components at pi
+                const int cls = pc == 0 ? 0 : (pc == 2 ? 2 : 1);             // s = 0, 16/3, 4
+                vx[w] = a.Lrs[3 * cls] * n0;
+                vy[w] = a.Lrs[3 * cls + 1] * n0 + a.Lrs[3 * cls + 2] * n1;
+            }
+#pragma unroll
+            for (int b = 1; b < 8; b <<= 1)
+#pragma unroll
+                for (int w = 0; w < 8; ++w)
+                    if (!(w & b)) {
+                        const R ax = vx[w], ay = vy[w], bx = vx[w | b], by = vy[w | b];
+                        vx[w] = ax + bx; vy[w] = ay + by;
+                        vx[w | b] = ax - bx; vy[w | b] = ay - by;
+                    }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                R* dst = (m & 1) ? Hup + ub * 8 * HN : Hin;
+                if (!(m & 1) && !keep_in) continue;
+                const int j = m >> 1;
+                dst[(2 * j) * HN + p] = R(0.125) * vx[m];
+                dst[(2 * j + 1) * HN + p] = R(0.125) * vy[m];
+            }
+        }
+    };
+
     // the collision of plane z from its pulled values f and density slots of z, z-1, z+1
-    auto collide_plane = [&](int z, const R (&f)[Q], int k0, int km, int kp) {
+    // (hb: the buffer of the previous plane's upward noise contributions, MODE 3)
+    auto collide_plane = [&](int z, const R (&f)[Q], int k0, int km, int kp, int hb) {
         const R* d0 = rs + k0 * RN + qc;
         const R* dm = rs + km * RN + qc;
         const R* dp = rs + kp * RN + qc;
@@ -285,7 +345,21 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
             r.dp = dm[RX]; r.dm = dp[-RX];                 // (0,1,-1)
             r.ep = dp[1]; r.em = dm[-1];                   // (1,0,1)
             r.fp = dp[-1]; r.fm = dm[1];                   // (-1,0,1)
-            if (MODE == 1) normals19(a, (uint32_t)node, xi);
+            if (MODE == 1 || MODE == 3) normals19(a, (uint32_t)node, xi);
+            if constexpr (MODE == 3) {
+                // (xi_4, xi_16) = sum over the box: h of r - (dx, dy, 0) from this plane and of
+                // r - (dx, dy, 1) from the previous one
+                R s4 = R(0), s16 = R(0);
+                const R* hu = Hup + hb * 8 * HN;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int q = (ly - (j & 1) + 1) * HW + (lx - (j >> 1) + 1);
+                    s4 += Hin[(2 * j) * HN + q] + hu[(2 * j) * HN + q];
+                    s16 += Hin[(2 * j + 1) * HN + q] + hu[(2 * j + 1) * HN + q];
+                }
+                xi[4] = s4;
+                xi[16] = s16;
+            }
             collide19(a.co, f, r, xi, o);
         } else {
             // nb[i] = rho(r + c_i)
@@ -311,12 +385,14 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
         __syncthreads();
         density(0, 0);
         density(1, 1);
+        if constexpr (MODE == 3) stencil_plane(z0 - 1, false, 0);
         issue(z0 + 1, 2);
         for (int z = z0; z < z1; ++z) {
             const int k0 = (z - z0 + 1) % 3, km = (k0 + 2) % 3, kp = (k0 + 1) % 3;   // slots of z, z-1, z+1
             cp_async_wait_all();
             __syncthreads();
             density(kp, kp);
+            if constexpr (MODE == 3) stencil_plane(z, true, (z - z0 + 1) & 1);
             if (z + 1 < z1) issue(z + 2, km);          // plane z-1's slot is free
             __syncthreads();
             if (!own) continue;
@@ -324,7 +400,7 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
             R f[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) f[i] = sl[i * RN + qc];
-            collide_plane(z, f, k0, km, kp);
+            collide_plane(z, f, k0, km, kp, (z - z0) & 1);
         }
     } else {
         // two raw slots: a plane's own pulled values move to registers when its densities are
@@ -342,6 +418,7 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
         density(0, 0);                 // plane z0-1 -> density slot 0
         density(1, 1);                 // plane z0 -> density slot 1
         take(1, fcur);
+        if constexpr (MODE == 3) stencil_plane(z0 - 1, false, 0);
         __syncthreads();
         issue(z0 + 1, 0);              // raw slot of plane p: (p - z0 + 1) % 2
         for (int z = z0; z < z1; ++z) {
@@ -352,8 +429,9 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
             if (z + 1 < z1) issue(z + 2, rp ^ 1);    // the slot of plane z, already in registers
             density(rp, kp);
             take(rp, fnext);
+            if constexpr (MODE == 3) stencil_plane(z, true, (z - z0 + 1) & 1);
             __syncthreads();
-            if (own) collide_plane(z, fcur, k0, km, kp);
+            if (own) collide_plane(z, fcur, k0, km, kp, (z - z0) & 1);
 #pragma unroll
             for (int i = 0; i < Q; ++i) fcur[i] = fnext[i];
         }
@@ -472,7 +550,7 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
 
 template <typename LAT, typename R, int MODE, typename I, int SLOTS>
 static cudaError_t launch_staged(const Step3Args<R>& a, dim3 grid, cudaStream_t s) {
-    constexpr int smem = staged_smem_bytes<LAT, R, SLOTS>();
+    constexpr int smem = staged_smem_bytes<LAT, R, SLOTS, MODE>();
     // the shared-memory limit is a per-device attribute of the function: set it once per
     // device (a repeated set from a concurrent first launch is harmless)
     static std::atomic<unsigned> done{0};
@@ -841,7 +919,7 @@ bool noise_factors(int lattice, const double* X, double sc[QMAX], double Lc[28])
 
 template <typename R>
 void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double sc[QMAX],
-               const double Lc[28]) {
+               const double Lc[28], const double Lrs[9]) {
     a->nx = c->nx; a->ny = c->ny; a->nz = c->nz; a->P = c->n;
     a->co.rho0 = (R)c->rho0;
     a->co.d = (R)(3.0 * c->cs2 - 1.0);
@@ -851,14 +929,17 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
     a->co.lg = (R)(-1.0 / tau_g);
     for (int q = 0; q < QMAX; ++q) a->sc[q] = (R)sc[q];
     for (int q = 0; q < 28; ++q) a->Lc[q] = (R)Lc[q];
+    for (int q = 0; q < 9; ++q) a->Lrs[q] = (R)Lrs[q];
     a->rk = lbf::make_round_keys(c->seed);
 }
 
 template <typename R>
 cudaError_t launch_any(lb3_ctx* c, const Step3Args<R>& a, int kmode) {
-    if (c->lattice == 19)
+    if (c->lattice == 19) {
+        if (kmode == 3) return launch3<Lat19, R, 3>(a, c->grid, false, c->slots, c->stream);
         return kmode ? launch3<Lat19, R, 1>(a, c->grid, c->plain, c->slots, c->stream)
                      : launch3<Lat19, R, 0>(a, c->grid, c->plain, c->slots, c->stream);
+    }
     return kmode ? launch3<Lat27, R, 1>(a, c->grid, false, c->slots, c->stream)
                  : launch3<Lat27, R, 0>(a, c->grid, false, c->slots, c->stream);
 }
@@ -950,18 +1031,34 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
         return fail3(c, LB_EINVAL, "relaxation times must exceed 1/2");
     if (!(kT >= 0.0) || !std::isfinite(kT)) return fail3(c, LB_EINVAL, "kT must be >= 0");
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return fail3(c, LB_EINVAL, "kappa must be >= 0");
-    if (mode != LB_NOISE_OFF && mode != LB_NOISE_LW)
-        return fail3(c, LB_EINVAL, "the 3-D lattices take LB_NOISE_OFF or LB_NOISE_LW");
+    if (mode != LB_NOISE_OFF && mode != LB_NOISE_LW && !(mode == LB_NOISE_FULL_RS && c->lattice == 19))
+        return fail3(c, LB_EINVAL, "the 3-D lattices take LB_NOISE_OFF or LB_NOISE_LW (D3Q19 also LB_NOISE_FULL_RS)");
     std::vector<double> X((size_t)c->lattice * c->lattice);
     xi_zero(c->lattice, c->rho0, c->cs2, kT, tau_s, tau_b, tau_ghost, X.data());
-    double sc[QMAX] = {}, Lc[28] = {};
-    if (mode == LB_NOISE_LW && kT > 0 && !noise_factors(c->lattice, X.data(), sc, Lc))
+    double sc[QMAX] = {}, Lc[28] = {}, Lrs[9] = {};
+    if (mode != LB_NOISE_OFF && kT > 0 && !noise_factors(c->lattice, X.data(), sc, Lc))
         return fail3(c, LB_ENOTPSD, "Xi(0) is not positive semidefinite");
+    if (mode == LB_NOISE_FULL_RS && kT > 0) {
+        // Xi(k) is Xi(0) at c_s^2(k) = cs2 + rho0 kappa s(k); the factors of its (4,16) block at
+        // the corner values s = 0, 4, 16/3 (positive semidefinite there means at every k)
+        const double svals[3] = {0.0, 4.0, 16.0 / 3.0};
+        for (int q = 0; q < 3; ++q) {
+            std::vector<double> Xs((size_t)Q3 * Q3);
+            xi_zero19(c->rho0, c->cs2 + c->rho0 * kappa * svals[q], kT, -1.0 / tau_b, -1.0 / tau_s,
+                      -1.0 / tau_ghost, Xs.data());
+            std::vector<double> L2;
+            if (!cholesky_block(Xs.data(), Q3, {4, 16}, L2))
+                return fail3(c, LB_ENOTPSD, "Xi(k) is not positive semidefinite on the lattice");
+            Lrs[3 * q] = L2[0];
+            Lrs[3 * q + 1] = L2[2];
+            Lrs[3 * q + 2] = L2[3];
+        }
+    }
     c->kT = kT;
     c->kappa = kappa;
     c->noise_mode = mode;
-    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc);
-    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc);
+    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc, Lrs);
+    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc, Lrs);
     c->have_params = true;
     return LB_OK;
 }
@@ -971,7 +1068,7 @@ int lb3_step(lb3_ctx* c, int64_t nsteps) {
     if (nsteps < 0) return fail3(c, LB_EINVAL, "nsteps must be >= 0");
     if (!c->have_params) return fail3(c, LB_ESTATE, "lb3_set_params must be called before lb3_step");
     lbf::DeviceGuard dg(c->device);
-    const int kmode = (c->noise_mode == LB_NOISE_LW && c->kT > 0.0) ? 1 : 0;
+    const int kmode = c->kT > 0.0 ? (c->noise_mode == LB_NOISE_LW ? 1 : (c->noise_mode == LB_NOISE_FULL_RS ? 3 : 0)) : 0;
     for (int64_t k = 0; k < nsteps; ++k) {
         const uint32_t tlo = (uint32_t)((uint64_t)c->t & 0xffffffffu), thi = (uint32_t)((uint64_t)c->t >> 32);
         cudaEvent_t e0 = nullptr, e1 = nullptr;

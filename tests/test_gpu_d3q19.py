@@ -7,6 +7,7 @@ equipartition of the ideal fluctuating gas with replica z-scores."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_1009_0254_gb300 as lbf
 from oracle import d3q19 as d3
 from paper_1009_0254_gb300 import synth
@@ -232,3 +233,154 @@ def test_ideal_fluctuating_gas_is_in_equipartition():
     bound = float(student.isf(0.01 / (2 * 19), R - 1))
     print("GPU equipartition ratios", np.round(mean / want, 4), "max |z| %.2f (bound %.2f)" % (np.abs(z).max(), bound))
     assert np.abs(z).max() < bound
+
+
+# --- correlated noise Xi(k), built in real space (LB_NOISE_FULL_RS) ---------------------------
+
+RS_PARAMS = (1e-4, 0.04, 0.8, 1.1, 0.9)
+
+
+def _pair_rs(nx, ny, nz, precision=lbf.LB_FP32, amp=0.01, clip=None, params=RS_PARAMS, seed=7):
+    g = lbf.Lattice3(nx, ny, nz, seed=seed, cs2=0.2, precision=precision)
+    g.set_params(*params, lbf.LB_NOISE_FULL_RS)
+    o = d3.Lattice(nx, ny, nz, cs2=0.2, seed=seed)
+    o.set_params(*params, d3.NOISE_FULL_RS)
+    f0 = _state(nx, ny, nz, o.model, seed + 100, amp, clip)
+    g.set_populations(f0, t=0)
+    o.f = f0.copy()
+    return g, o
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(32, 8, 4), (37, 11, 5), (64, 16, 9), (5, 3, 2), (1, 1, 8), (40, 1, 3),
+                                      (3, 17, 1), (33, 9, 2)])
+def test_fp32_correlated_noise_follows_the_oracle(nx, ny, nz, kernel3):
+    g, o = _pair_rs(nx, ny, nz)
+    g.step(6)
+    o.step(6)
+    err = np.abs(g.populations() - o.f).max()
+    print("D3Q19 FP32 RS %s %dx%dx%d: %.2e" % (kernel3, nx, ny, nz, err))
+    assert err <= TOL
+    q = d3.Lattice(nx, ny, nz, cs2=0.2, seed=7)
+    q.set_params(*RS_PARAMS, d3.NOISE_LW)
+    q.f = _state(nx, ny, nz, q.model, 107)
+    q.step(6)
+    assert np.abs(q.f - o.f).max() > 10 * TOL           # the correlated part acted
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(32, 8, 4), (37, 11, 5), (6, 5, 7)])
+def test_fp64_correlated_noise_to_rounding(nx, ny, nz, kernel3):
+    g, o = _pair_rs(nx, ny, nz, precision=lbf.LB_FP64, amp=0.25, clip=3.5, params=(1e-4, 0.04, 0.8, 1.1, 0.9))
+    g.step(4)
+    o.step(4)
+    err = np.abs(g.populations() - o.f).max()
+    print("D3Q19 FP64 RS %s %dx%dx%d: %.2e" % (kernel3, nx, ny, nz, err))
+    assert err <= TOL64
+
+
+def test_correlated_noise_refuses_an_indefinite_Xi():
+    g = lbf.Lattice3(8, 8, 8, cs2=0.3)
+    # c_s^2(k) = 0.3 + 0.06 * 16/3 = 0.62 > 5/9 at s = 16/3
+    with pytest.raises(lbf.LBError) as e:
+        g.set_params(1e-4, 0.06, 0.8, 1.1, 0.9, lbf.LB_NOISE_FULL_RS)
+    assert e.value.code == lbf.LB_ENOTPSD
+    g.set_params(1e-4, 0.06, 0.8, 1.1, 0.9, lbf.LB_NOISE_LW)           # Xi(0) alone is fine
+    h = lbf.Lattice3(8, 8, 8, lattice=lbf.LB_D3Q27)
+    with pytest.raises(lbf.LBError) as e:
+        h.set_params(1e-4, 0.01, 0.8, 1.1, 0.9, lbf.LB_NOISE_FULL_RS)
+    assert e.value.code == lbf.LB_EINVAL
+
+
+def _patch_step_rs(m, n, centre, seed, t, L, Ls, amp):
+    """One oracle step at `centre` with the correlated noise: the 6x6x6 neighbourhood from
+    centre - 3 .. centre + 2 holds every node the box sums of the 3x3x3 collisions need."""
+    z0, y0, x0 = centre
+    zs, ys, xs = ((np.arange(c - 3, c + 3)) % n for c in (z0, y0, x0))
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    nodes = (Z * n + Y) * n + X
+    sub = np.array(_wave_state(m.fbar(), n, Z, Y, X, amp))
+    xi = d3.noise_lw_nodes(m, nodes, seed, t, L)
+    g = np.concatenate([oracle.normals(nodes.ravel().astype(np.uint32), seed, t, tg) for tg in d3.TAG_RS], axis=1)
+    nu = g.T.reshape(8, 2, 6, 6, 6)
+    v = np.einsum("wab,wb...->wa...", Ls, nu)
+    xi416 = np.zeros((2, 6, 6, 6))
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                h = sum((d3.CORNERS[w][0] ** dx) * (d3.CORNERS[w][1] ** dy) * (d3.CORNERS[w][2] ** dz) * v[w]
+                        for w in range(8)) / 8.0
+                xi416 += np.roll(h, shift=(dz, dy, dx), axis=(1, 2, 3))     # exact away from the low faces
+    xi[4], xi[16] = xi416[0], xi416[1]
+    return d3.step(sub, m, xi)[:, 3, 3, 3]
+
+
+def test_correlated_noise_sampled_at_the_benchmark_size():
+    import torch
+    n, amp = 256, 0.01
+    kT, kappa, ts, tb, tg = RS_PARAMS
+    m = d3.Model(1.0, 0.2, kappa, kT, ts, tb, tg)
+    g = lbf.Lattice3(n, n, n, seed=5, cs2=0.2)
+    g.set_params(*RS_PARAMS, lbf.LB_NOISE_FULL_RS)
+    dev = torch.empty((19, n, n, n), dtype=torch.float64, device="cuda")
+    r = torch.arange(n, device="cuda", dtype=torch.float64)
+    Z, Y, X = torch.meshgrid(r, r, r, indexing="ij")
+    for i, plane in enumerate(_wave_state(m.fbar(), n, Z, Y, X, amp, xp=torch)):
+        dev[i] = plane
+    del Z, Y, X
+    lbf.lb3_set_populations(g.ctx, dev, lbf.LB_DEVICE, 9)
+    g.step(1)
+    lbf.lb3_get_populations(g.ctx, dev, lbf.LB_DEVICE)
+    torch.cuda.synchronize()
+    L, Ls = m.noise_factor(), d3.rs_factors(m)
+    rng = np.random.default_rng(3)
+    picks = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 0, 31), (128, 128, 0), (7, 8, n - 1)]
+    picks += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(16)]
+    err = 0.0
+    for c in picks:
+        got = dev[:, c[0], c[1], c[2]].cpu().numpy()
+        err = max(err, np.abs(got - _patch_step_rs(m, n, c, 5, 9, L, Ls, amp)).max())
+    print("RS 256^3 sampled: %.2e" % err)
+    assert err <= TOL
+    del dev, g
+    torch.cuda.empty_cache()
+
+
+def test_correlated_noise_equilibrates_every_wavevector_on_the_gpu():
+    # Sec. V A in three dimensions on the GPU: S(k) = rho0 kT / c_s^2(k) and <|j(k)|^2> = rho0 kT
+    # at every k of a 12^3 lattice, binned by s(k), replicas for the standard errors, a
+    # Bonferroni bound over the bins (Student t); the staggered-momentum invariants excluded
+    from scipy.stats import t as student
+    n, R, samples, every, burn = 12, 16, 40, 20, 300
+    cs2, kappa, kT = 0.2, 0.04, 1e-4
+    k1 = 2 * np.pi * np.fft.fftfreq(n)
+    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")
+    s = d3.lattice_s(KX, KY, KZ)
+    edges = np.linspace(0, 16 / 3 + 1e-9, 9)
+    b = np.digitize(s, edges) - 1
+    keep = np.ones((n, n, n), bool)
+    keep[0, 0, 0] = False
+    keepj = keep.copy()
+    keepj[0, 0, n // 2] = keepj[0, n // 2, 0] = keepj[n // 2, 0, 0] = False
+    S_th = kT / (cs2 + kappa * s)
+    accS = np.zeros((R, 8))
+    accJ = np.zeros((R, 8))
+    for r in range(R):
+        g = lbf.Lattice3(n, n, n, seed=500 + r, cs2=cs2)
+        g.set_params(kT, kappa, 0.8, 1.1, 0.9, lbf.LB_NOISE_FULL_RS)
+        g.step(burn)
+        S = np.zeros((n, n, n))
+        J = np.zeros((n, n, n))
+        for _ in range(samples):
+            g.step(every)
+            m = np.einsum("ai,i...->a...", d3.T, g.populations())
+            S += np.abs(np.fft.fftn(m[0] - 1.0)) ** 2 / n ** 3
+            J += sum(np.abs(np.fft.fftn(m[a])) ** 2 for a in (1, 2, 3)) / (3 * n ** 3)
+        for q in range(8):
+            accS[r, q] = (S / samples / S_th)[keep & (b == q)].mean()
+            accJ[r, q] = (J / samples / kT)[keepj & (b == q)].mean()
+    bound = float(student.isf(0.01 / (2 * 16), R - 1))
+    for name, acc in (("S", accS), ("J", accJ)):
+        mean = acc.mean(axis=0)
+        se = acc.std(axis=0, ddof=1) / np.sqrt(R)
+        z = (mean - 1) / se
+        print("RS GPU %s ratios by s bin" % name, np.round(mean, 4), "max |z| %.2f (bound %.2f)" % (np.abs(z).max(), bound))
+        assert np.abs(z).max() < bound

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import paper_1009_0254_gb300 as lbf
+from waves3d import wave_state_box
 from oracle import d3q19 as d3
 from paper_1009_0254_gb300 import synth
 
@@ -384,3 +385,45 @@ def test_correlated_noise_equilibrates_every_wavevector_on_the_gpu():
         z = (mean - 1) / se
         print("RS GPU %s ratios by s bin" % name, np.round(mean, 4), "max |z| %.2f (bound %.2f)" % (np.abs(z).max(), bound))
         assert np.abs(z).max() < bound
+
+
+def test_lattice_with_64_bit_plane_offsets_sampled():
+    # 1024 x 1024 x 216 nodes: 19 planes hold more than 2^32 elements, so the step takes its
+    # 64-bit offsets; one step from a plane-wave state checked on sampled nodes, several in the
+    # last planes (offsets above 2^32)
+    import torch
+    nx, ny, nz, amp = 1024, 1024, 216, 0.01
+    assert 19 * nx * ny * nz >= 2 ** 32
+    m = d3.Model(1.0, 0.25, PARAMS[1], PARAMS[0], PARAMS[2], PARAMS[3], PARAMS[4])
+    g = lbf.Lattice3(nx, ny, nz, seed=5, cs2=0.25)
+    g.set_params(*PARAMS, lbf.LB_NOISE_LW)
+    dev = torch.empty((19, nz, ny, nx), dtype=torch.float64, device="cuda")
+    for z0 in range(0, nz, 24):
+        zz = torch.arange(z0, min(z0 + 24, nz), device="cuda", dtype=torch.float64)
+        yy = torch.arange(ny, device="cuda", dtype=torch.float64)
+        xx = torch.arange(nx, device="cuda", dtype=torch.float64)
+        Z, Y, X = torch.meshgrid(zz, yy, xx, indexing="ij")
+        for i, plane in enumerate(wave_state_box(m.fbar(), (nx, ny, nz), Z, Y, X, amp, xp=torch)):
+            dev[i, z0:z0 + Z.shape[0]] = plane
+        del Z, Y, X
+    lbf.lb3_set_populations(g.ctx, dev, lbf.LB_DEVICE, 2)
+    g.step(1)
+    lbf.lb3_get_populations(g.ctx, dev, lbf.LB_DEVICE)
+    torch.cuda.synchronize()
+    L = m.noise_factor()
+    rng = np.random.default_rng(5)
+    picks = [(nz - 1, ny - 1, nx - 1), (nz - 1, 0, 0), (nz - 2, 517, 1023), (0, 0, 0), (108, 512, 511)]
+    picks += [(int(rng.integers(nz - 20, nz)), int(rng.integers(0, ny)), int(rng.integers(0, nx))) for _ in range(8)]
+    err = 0.0
+    for c in picks:
+        zc, yc, xc = c
+        zs, ys, xs = (np.arange(c0 - 2, c0 + 3) % nn for c0, nn in ((zc, nz), (yc, ny), (xc, nx)))
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        sub = np.array(wave_state_box(m.fbar(), (nx, ny, nz), Z, Y, X, amp))
+        nodes = (Z * ny + Y) * nx + X
+        want = d3.step(sub, m, d3.noise_lw_nodes(m, nodes, 5, 2, L))[:, 2, 2, 2]
+        err = max(err, np.abs(dev[:, zc, yc, xc].cpu().numpy() - want).max())
+    print("1024x1024x216 sampled: %.2e" % err)
+    assert err <= TOL
+    del dev, g
+    torch.cuda.empty_cache()

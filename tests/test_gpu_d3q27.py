@@ -8,6 +8,7 @@ import pytest
 
 import paper_1009_0254_gb300 as lbf
 from oracle import d3q27 as d
+from waves3d import wave_state_box
 from paper_1009_0254_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -203,3 +204,43 @@ def test_ideal_fluctuating_gas_is_in_equipartition():
     print("D3Q27 GPU equipartition ratios", np.round(mean / want, 4), "max |z| %.2f (bound %.2f)"
           % (np.abs(z).max(), bound))
     assert np.abs(z).max() < bound
+
+
+def test_lattice_with_64_bit_plane_offsets_sampled():
+    # 1024 x 1024 x 152 nodes: 27 planes hold more than 2^32 elements (64-bit offsets)
+    import torch
+    nx, ny, nz, amp = 1024, 1024, 152, 0.01
+    assert 27 * nx * ny * nz >= 2 ** 32
+    m = d.Model(1.0, 0.25, PARAMS[1], PARAMS[0], PARAMS[2], PARAMS[3], PARAMS[4])
+    g = lbf.Lattice3(nx, ny, nz, seed=5, cs2=0.25, lattice=lbf.LB_D3Q27)
+    g.set_params(*PARAMS, lbf.LB_NOISE_LW)
+    dev = torch.empty((Q, nz, ny, nx), dtype=torch.float64, device="cuda")
+    for z0 in range(0, nz, 24):
+        zz = torch.arange(z0, min(z0 + 24, nz), device="cuda", dtype=torch.float64)
+        yy = torch.arange(ny, device="cuda", dtype=torch.float64)
+        xx = torch.arange(nx, device="cuda", dtype=torch.float64)
+        Z, Y, X = torch.meshgrid(zz, yy, xx, indexing="ij")
+        for i, plane in enumerate(wave_state_box(m.fbar(), (nx, ny, nz), Z, Y, X, amp, xp=torch, q=Q)):
+            dev[i, z0:z0 + Z.shape[0]] = plane
+        del Z, Y, X
+    lbf.lb3_set_populations(g.ctx, dev, lbf.LB_DEVICE, 2)
+    g.step(1)
+    lbf.lb3_get_populations(g.ctx, dev, lbf.LB_DEVICE)
+    torch.cuda.synchronize()
+    L = m.noise_factor()
+    rng = np.random.default_rng(6)
+    picks = [(nz - 1, ny - 1, nx - 1), (nz - 1, 0, 0), (0, 0, 0), (76, 512, 511)]
+    picks += [(int(rng.integers(nz - 20, nz)), int(rng.integers(0, ny)), int(rng.integers(0, nx))) for _ in range(8)]
+    err = 0.0
+    for c in picks:
+        zc, yc, xc = c
+        zs, ys, xs = (np.arange(c0 - 2, c0 + 3) % nn for c0, nn in ((zc, nz), (yc, ny), (xc, nx)))
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        sub = np.array(wave_state_box(m.fbar(), (nx, ny, nz), Z, Y, X, amp, q=Q))
+        nodes = (Z * ny + Y) * nx + X
+        want = d.step(sub, m, d.noise_lw_nodes(m, nodes, 5, 2, L))[:, 2, 2, 2]
+        err = max(err, np.abs(dev[:, zc, yc, xc].cpu().numpy() - want).max())
+    print("D3Q27 1024x1024x152 sampled: %.2e" % err)
+    assert err <= TOL
+    del dev, g
+    torch.cuda.empty_cache()

@@ -252,15 +252,18 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
         }
         cp_async_commit();
     };
-    // density deviations of the plane in raw slot slot_k into density slot dk
+    // density deviations of the plane in raw slot slot_k into density slot dk; positions run
+    // from the last thread down, so the positions beyond the block's width fall on other
+    // threads than the extra copies of issue()
     auto density = [&](int slot_k, int dk) {
         const R* slot = raw + slot_k * Q * RN;
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            const int q = tid + k * NT;
+            const int q = (NT - 1 - tid) + k * NT;
             if (q >= RN) continue;
+            const int ly = q / RX, lx = q - ly * RX;
             R v = R(0);
-            if (valid[k]) {
+            if (x0 + lx - 1 <= nx && y0 + ly - 1 <= ny) {
                 R f[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) f[i] = slot[i * RN + q];
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, S
     // when keep_in, the upward half (dz = 1) into buffer ub
     auto stencil_plane = [&](int zz, bool keep_in, int ub) {
         const int zc = wrap_hi(wrap_lo(zz, nz), nz);
-        for (int p = tid; p < HN; p += NT) {
+        for (int p = NT - 1 - tid; p < HN; p += NT) {       // extra positions on the last threads
             const int hy = p / HW - 1, hx = p - (hy + 1) * HW - 1;
             int gx = x0 + hx, gy = y0 + hy;
             if (gx >= nx || gy >= ny) continue;         // never read by a node of the lattice

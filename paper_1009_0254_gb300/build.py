@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbfluct.so")
-SOURCES = ["lb_api.cu", "lb_step.cu", "lb_step_tma.cu", "lb_step_sweep.cu", "lb_fft.cu", "lb_io.cu", "lb_static.cu", "lb_batch.cu", "lb_serve.cu", "lb_selftest.cu", "lb3d.cu"]
+SOURCES = ["lb_api.cu", "lb_step.cu", "lb_step_tma.cu", "lb_step_sweep.cu", "lb_fft.cu", "lb_io.cu", "lb_static.cu", "lb_batch.cu", "lb_serve.cu", "lb_selftest.cu", "lb3d.cu", "lb3d_q19.cu", "lb3d_q27.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,23 +1,8 @@
-// lb3d.cu -- the fused fluctuating step on the D3Q19 and D3Q27 lattices for sm_103a and the
-// C ABI of lbfluct3d.h.
-//
-// One launch performs one time step on every node (collision of lb3_collide.cuh or
-// lb27_collide.cuh, then streaming in pull form: f_i(r, t) = f*_i(r - c_i, t - 1)).  A CTA
-// owns a TX x TY tile of the (x, y) plane and marches over a run of z planes.  The pulled
-// populations of each plane, for the tile and its one-node ring, are staged in shared
-// memory by asynchronous copies (three rotating slots: the plane being collided, the plane
-// whose densities are summed, and the plane in flight), so the loads of plane z+2 overlap
-// the collision of plane z.  With two slots (D3Q27's default: its smaller shared-memory
-// footprint fits four CTAs per SM instead of three) a plane's own populations move to
-// registers when its densities are summed.  The densities of planes z-1, z, z+1 sit in three more rotating
-// slots; the collision reads its own node's populations and its 3x3x3 density neighbourhood
-// from shared memory.  Every population is read once from DRAM (the ring's re-reads hit L2)
-// and written once: 2 Q sizeof(storage) bytes per node.
-//
-// A plain D3Q19 kernel (density summed from direct loads, the collision pulling again) is
-// kept as a cross-check (LBFLUCT3_KERNEL=plain).
+// lb3d.cu -- host side of the D3Q19 and D3Q27 lattices and the C ABI of lbfluct3d.h: the
+// lattices' Xi(0) and its factors, the padded population storage (lb3d_kernel.cuh) and its
+// transfers, the choice of the step kernel, and the tensor maps of its TMA staging.  The
+// step kernels are compiled in lb3d_q19.cu and lb3d_q27.cu.
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -25,571 +10,19 @@
 #include <utility>
 #include <vector>
 
-#include "lb27_collide.cuh"
-#include "lb3_collide.cuh"
-#include "lb_internal.cuh"
+#include "lb3d_kernel.cuh"
 #include "lbfluct3d.h"
 
 namespace lbf3 {
 
 constexpr double SIGMA_S2 = 1.0 / 3.0;
-constexpr int QMAX = 27;
-
-// velocity components in {-1, 0, 1} packed two bits each: c = ((P >> 2i) & 3) - 1
-constexpr unsigned long long pack3(const int (&v)[19]) {
-    unsigned long long p = 0;
-    for (int i = 0; i < 19; ++i) p |= (unsigned long long)(v[i] + 1) << (2 * i);
-    return p;
-}
-
-// D3Q19: the velocity order of lb3_collide.cuh; noise tags 4, 5
-struct Lat19 {
-    static constexpr int Q = 19, TX = 32, TY = 8;
-    static constexpr uint32_t TAG0 = 4;
-    static constexpr int CXv[19] = {0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
-    static constexpr int CYv[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 0, 0, 0, 0};
-    static constexpr int CZv[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1};
-    static constexpr unsigned long long PX = pack3(CXv), PY = pack3(CYv), PZ = pack3(CZv);
-    __host__ __device__ static constexpr int c(int i, int k) {
-        return (int)(((k == 0 ? PX : (k == 1 ? PY : PZ)) >> (2 * i)) & 3ULL) - 1;
-    }
-    __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
-};
-
-// D3Q27: i = 9 ix + 3 iy + iz, components (0, 1, -1); noise tags 6, 7, 8
-struct Lat27 {
-    static constexpr int Q = 27, TX = 32, TY = 4;
-    static constexpr uint32_t TAG0 = 6;
-    __host__ __device__ static constexpr int v(int a) { return a == 0 ? 0 : (a == 1 ? 1 : -1); }
-    __host__ __device__ static constexpr int c(int i, int k) {
-        return v(k == 0 ? i / 9 : (k == 1 ? (i / 3) % 3 : i % 3));
-    }
-    __host__ __device__ static constexpr double w1(int a) { return a == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
-    __host__ __device__ static constexpr double w(int i) { return w1(i / 9) * w1((i / 3) % 3) * w1(i % 3); }
-};
-
-// The D3Q27 modes whose noise is coupled (the Cholesky factor's dense 7 x 7 block, in mode
-// order): p_2z, p_2y, p_2y p_2z, p_2x, p_2x p_2z, p_2x p_2y, p_2x p_2y p_2z.
-constexpr int COUPLED27[7] = {2, 6, 8, 18, 20, 24, 26};
-__host__ __device__ constexpr int coupled27(int r) {
-    return r == 0 ? 2 : (r == 1 ? 6 : (r == 2 ? 8 : (r == 3 ? 18 : (r == 4 ? 20 : (r == 5 ? 24 : 26)))));
-}
-
-template <typename R>
-struct Step3Args {
-    const R* __restrict__ src;    // post-collision deviations at t-1, Q planes of P nodes
-    R* __restrict__ dst;
-    int nx, ny, nz, zc;           // zc: planes per CTA
-    long long P;                  // nodes per population plane
-    Coef3<R> co;
-    R sc[QMAX];                   // sqrt(Xi_kk) of the modes with a diagonal factor
-    R Lc[28];                     // the coupled block's Cholesky factor: D3Q19 (L44, L16_4, L16_16);
-                                  // D3Q27 the 7 x 7 lower triangle, row-major
-    R Lrs[9];                     // D3Q19 correlated noise: Cholesky factors (L11, L21, L22) of the
-                                  // (4,16) block of Xi at s = 0, 4, 16/3
-    uint32_t t_lo, t_hi;
-    lbf::RoundKeys rk;
-};
-
-// D3Q19 noise: tag 4 -> nu_4..nu_11, tag 5 -> nu_12..nu_18
-template <typename R>
-__device__ __forceinline__ void normals19(const Step3Args<R>& a, uint32_t node, R xi[Q3]) {
-    const uint4 ra = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat19::TAG0), a.rk);
-    const uint4 rb = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat19::TAG0 + 1), a.rk);
-    R n4, n16, spare;
-    lbf::gauss_word(ra.x, &n4, &xi[5]);
-    lbf::gauss_word(ra.y, &xi[6], &xi[7]);
-    lbf::gauss_word(ra.z, &xi[8], &xi[9]);
-    lbf::gauss_word(ra.w, &xi[10], &xi[11]);
-    lbf::gauss_word(rb.x, &xi[12], &xi[13]);
-    lbf::gauss_word(rb.y, &xi[14], &xi[15]);
-    lbf::gauss_word(rb.z, &n16, &xi[17]);
-    lbf::gauss_word(rb.w, &xi[18], &spare);
-    (void)spare;
-#pragma unroll
-    for (int q = 5; q < Q3; ++q) xi[q] *= a.sc[q];
-    xi[4] = a.Lc[0] * n4;
-    xi[16] = a.Lc[1] * n4 + a.Lc[2] * n16;
-}
-
-// position of mode k among the non-conserved D3Q27 modes (conserved: 0, 1, 3, 9)
-__host__ __device__ constexpr int nc27(int k) { return k - (k > 0) - (k > 1) - (k > 3) - (k > 9); }
-
-// D3Q27 noise: tags 6, 7, 8 give 24 normals; normal n goes to the n-th non-conserved mode
-template <typename R>
-__device__ __forceinline__ void normals27(const Step3Args<R>& a, uint32_t node, R xi[Q27]) {
-    R nu[24];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const uint4 r = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat27::TAG0 + d), a.rk);
-        lbf::gauss_word(r.x, &nu[8 * d + 0], &nu[8 * d + 1]);
-        lbf::gauss_word(r.y, &nu[8 * d + 2], &nu[8 * d + 3]);
-        lbf::gauss_word(r.z, &nu[8 * d + 4], &nu[8 * d + 5]);
-        lbf::gauss_word(r.w, &nu[8 * d + 6], &nu[8 * d + 7]);
-    }
-#pragma unroll
-    for (int k = 0; k < Q27; ++k)
-        xi[k] = (k == 0 || k == 1 || k == 3 || k == 9) ? R(0) : a.sc[k] * nu[nc27(k)];
-#pragma unroll
-    for (int r = 0; r < 7; ++r) {
-        R s = R(0);
-#pragma unroll
-        for (int q = 0; q <= r; ++q) s += a.Lc[r * (r + 1) / 2 + q] * nu[nc27(coupled27(q))];
-        xi[coupled27(r)] = s;
-    }
-}
-
-__device__ __forceinline__ int wrap_lo(int v, int n) { return v < 0 ? v + n : v; }
-__device__ __forceinline__ int wrap_hi(int v, int n) { return v >= n ? v - n : v; }
-
-// asynchronous global -> shared copy of one element (4 or 8 bytes), cached in L1
-template <int BYTES>
-__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (BYTES == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// density deviation of one node's pulled deviations, one fixed summation order
-template <typename LAT, typename R>
-__device__ __forceinline__ R drho_of(const R* f) {
-    if constexpr (LAT::Q == 19) {
-        return drho19(f);
-    } else {
-        R s = f[0];
-#pragma unroll
-        for (int i = 1; i < Q27; i += 2) s += (i + 1 < Q27) ? (f[i] + f[i + 1]) : f[i];
-        return s;
-    }
-}
-
-// D3Q19 correlated noise: the tags of the two draws of the eight corner fields
-constexpr uint32_t TAG_RS0 = 10;
-
-// The staged step kernel: one CTA per TX x TY tile and run of zc planes.  With correlated
-// noise (MODE 3) it also holds the 2x2x2-box contributions: for the tile plus its left column
-// and bottom row, the in-plane half (four 2-vectors) of the current plane and the upward half
-// of the current and the previous plane.
-template <typename LAT, typename R, int SLOTS, int MODE>
-constexpr int staged_smem_bytes() {
-    return ((SLOTS * LAT::Q + 3) * (LAT::TX + 2) * (LAT::TY + 2) +
-            (MODE == 3 ? 24 * (LAT::TX + 1) * (LAT::TY + 1) : 0)) * (int)sizeof(R);
-}
-
-// resident CTAs per SM the register budget is sized for: as many as the shared memory admits
-// (227 KB per SM, 1 KB reserved per CTA), at most 2048 threads
-template <typename LAT, typename R, int SLOTS, int MODE>
-constexpr int staged_min_blocks() {
-    constexpr int by_smem = (227 * 1024) / (staged_smem_bytes<LAT, R, SLOTS, MODE>() + 1024);
-    constexpr int by_threads = 2048 / (LAT::TX * LAT::TY);
-    return by_smem < 1 ? 1 : (by_smem < by_threads ? by_smem : by_threads);
-}
-
-template <typename LAT, typename R, int MODE, typename I, int SLOTS>
-__global__ void __launch_bounds__(LAT::TX * LAT::TY, staged_min_blocks<LAT, R, SLOTS, MODE>())
-    step3_staged_kernel(const Step3Args<R> a) {
-    constexpr int Q = LAT::Q, TX = LAT::TX, TY = LAT::TY;
-    constexpr int RX = TX + 2, RY = TY + 2, RN = RX * RY, NT = TX * TY;
-    extern __shared__ __align__(16) unsigned char smem3[];
-    R* raw = reinterpret_cast<R*>(smem3);                   // [SLOTS][Q][RN] pulled populations
-    R* rs = raw + SLOTS * Q * RN;                           // [3][RN] density deviations
-    constexpr int HW = TX + 1, HN = HW * (TY + 1);
-    R* Hin = rs + 3 * RN;                                   // MODE 3: [8][HN] in-plane half
-    R* Hup = Hin + 8 * HN;                                  // MODE 3: [2][8][HN] upward half
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long P = a.P, nxy = (long long)nx * ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * a.zc;
-    const int z1 = min(z0 + a.zc, nz);
-    const int tid = threadIdx.x;
-    const R* __restrict__ src = a.src;
-    // offsets in I: 32-bit when all Q planes fit in 2^32 elements, else 64-bit
-    const I PI = (I)P;
-
-    // The tile-and-ring positions a thread stages are the same on every plane: their validity
-    // and the nine in-plane offsets (x - cx) + (y - cy) nx, indexed (1 - cy) 3 + (1 - cx), are
-    // formed once.
-    constexpr int KP = (RN + NT - 1) / NT;
-    I yx[KP][9];
-    bool valid[KP];
-#pragma unroll
-    for (int k = 0; k < KP; ++k) {
-        const int q = tid + k * NT;
-        const int ly = q / RX, lx = q - ly * RX;
-        int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        valid[k] = q < RN && gx <= nx && gy <= ny;      // others are never read by a node
-        gx = wrap_hi(wrap_lo(gx, nx), nx);
-        gy = wrap_hi(wrap_lo(gy, ny), ny);
-        const I Xo[3] = {(I)(gx == 0 ? nx - 1 : gx - 1), (I)gx, (I)(gx == nx - 1 ? 0 : gx + 1)};
-        const I Yo[3] = {(I)(gy == 0 ? ny - 1 : gy - 1) * (I)nx, (I)gy * (I)nx,
-                         (I)(gy == ny - 1 ? 0 : gy + 1) * (I)nx};
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) yx[k][3 * b + c] = Yo[b] + Xo[c];
-    }
-
-    // issue the pulled populations of plane zz (an integer in [-1, nz]) into raw slot k
-    auto issue = [&](int zz, int slot_k) {
-        const int zc = wrap_hi(wrap_lo(zz, nz), nz);
-        // plane offsets of z - cz, indexed by 1 - cz
-        const I Zo[3] = {(I)(zc == 0 ? nz - 1 : zc - 1) * (I)nxy, (I)zc * (I)nxy,
-                         (I)(zc == nz - 1 ? 0 : zc + 1) * (I)nxy};
-        R* slot = raw + slot_k * Q * RN;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            if (!valid[k]) continue;
-            const int q = tid + k * NT;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const I off = (I)i * PI + Zo[1 - LAT::c(i, 2)] + yx[k][3 * (1 - LAT::c(i, 1)) + (1 - LAT::c(i, 0))];
-                cp_async_elem<sizeof(R)>(slot + i * RN + q, src + off);
-            }
-        }
-        cp_async_commit();
-    };
-    // density deviations of the plane in raw slot slot_k into density slot dk; positions run
-    // from the last thread down, so the positions beyond the block's width fall on other
-    // threads than the extra copies of issue()
-    auto density = [&](int slot_k, int dk) {
-        const R* slot = raw + slot_k * Q * RN;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            const int q = (NT - 1 - tid) + k * NT;
-            if (q >= RN) continue;
-            const int ly = q / RX, lx = q - ly * RX;
-            R v = R(0);
-            if (x0 + lx - 1 <= nx && y0 + ly - 1 <= ny) {
-                R f[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) f[i] = slot[i * RN + q];
-                v = drho_of<LAT>(f);
-            }
-            rs[dk * RN + q] = v;
-        }
-    };
-
-    const int lx = tid % TX, ly = tid / TX;
-    const int x = x0 + lx, y = y0 + ly;
-    const bool own = x < nx && y < ny;
-    const int qc = (ly + 1) * RX + lx + 1;
-
-    // MODE 3: the eight white 2-vectors nu_w of every position of plane zz (tile, left column,
-    // bottom row), times the factor of their corner (w = 4 ia + 2 ib + ic, sign -1 for a set
-    // bit: k = pi), combined by a Walsh-Hadamard transform into h_m = (1/8) sum_w
-    // (-1)^{popcount(w & m)} L_w nu_w, m = 4 dx + 2 dy + dz: the in-plane half (dz = 0) into Hin
-    // when keep_in, the upward half (dz = 1) into buffer ub
-    auto stencil_plane = [&](int zz, bool keep_in, int ub) {
-        const int zc = wrap_hi(wrap_lo(zz, nz), nz);
-        for (int p = NT - 1 - tid; p < HN; p += NT) {       // extra positions on the last threads
-            const int hy = p / HW - 1, hx = p - (hy + 1) * HW - 1;
-            int gx = x0 + hx, gy = y0 + hy;
-            if (gx >= nx || gy >= ny) continue;         // never read by a node of the lattice
-            gx = wrap_lo(gx, nx);
-            gy = wrap_lo(gy, ny);
-            const uint32_t node = ((uint32_t)zc * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx;
-            const uint4 r0 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0), a.rk);
-            const uint4 r1 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0 + 1), a.rk);
-            const uint32_t wd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-            R vx[8], vy[8];
-#pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                R n0, n1;
-                lbf::gauss_word(wd[w], &n0, &n1);
-                const int pc = (w & 1) + ((w >> 1) & 1) + ((w >> 2) & 1);      // components at pi
-                const int cls = pc == 0 ? 0 : (pc == 2 ? 2 : 1);             // s = 0, 16/3, 4
-                vx[w] = a.Lrs[3 * cls] * n0;
-                vy[w] = a.Lrs[3 * cls + 1] * n0 + a.Lrs[3 * cls + 2] * n1;
-            }
-#pragma unroll
-            for (int b = 1; b < 8; b <<= 1)
-#pragma unroll
-                for (int w = 0; w < 8; ++w)
-                    if (!(w & b)) {
-                        const R ax = vx[w], ay = vy[w], bx = vx[w | b], by = vy[w | b];
-                        vx[w] = ax + bx; vy[w] = ay + by;
-                        vx[w | b] = ax - bx; vy[w | b] = ay - by;
-                    }
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                R* dst = (m & 1) ? Hup + ub * 8 * HN : Hin;
-                if (!(m & 1) && !keep_in) continue;
-                const int j = m >> 1;
-                dst[(2 * j) * HN + p] = R(0.125) * vx[m];
-                dst[(2 * j + 1) * HN + p] = R(0.125) * vy[m];
-            }
-        }
-    };
-
-    // the collision of plane z from its pulled values f and density slots of z, z-1, z+1
-    // (hb: the buffer of the previous plane's upward noise contributions, MODE 3)
-    auto collide_plane = [&](int z, const R (&f)[Q], int k0, int km, int kp, int hb) {
-        const R* d0 = rs + k0 * RN + qc;
-        const R* dm = rs + km * RN + qc;
-        const R* dp = rs + kp * RN + qc;
-        R xi[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) xi[q] = R(0);
-        const I node = (I)z * (I)nxy + (I)y * (I)nx + (I)x;
-        R o[Q];
-        if constexpr (Q == 19) {
-            Rho3<R> r;
-            r.c = d0[0];
-            r.xp = d0[1]; r.xm = d0[-1];
-            r.yp = d0[RX]; r.ym = d0[-RX];
-            r.zp = dp[0]; r.zm = dm[0];
-            r.ap = d0[RX + 1]; r.am = d0[-RX - 1];         // (1,1,0)
-            r.bp = d0[-RX + 1]; r.bm = d0[RX - 1];         // (1,-1,0)
-            r.cp = dp[RX]; r.cm = dm[-RX];                 // (0,1,1)
-            r.dp = dm[RX]; r.dm = dp[-RX];                 // (0,1,-1)
-            r.ep = dp[1]; r.em = dm[-1];                   // (1,0,1)
-            r.fp = dp[-1]; r.fm = dm[1];                   // (-1,0,1)
-            if (MODE == 1 || MODE == 3) normals19(a, (uint32_t)node, xi);
-            if constexpr (MODE == 3) {
-                // (xi_4, xi_16) = sum over the box: h of r - (dx, dy, 0) from this plane and of
-                // r - (dx, dy, 1) from the previous one
-                R s4 = R(0), s16 = R(0);
-                const R* hu = Hup + hb * 8 * HN;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int q = (ly - (j & 1) + 1) * HW + (lx - (j >> 1) + 1);
-                    s4 += Hin[(2 * j) * HN + q] + hu[(2 * j) * HN + q];
-                    s16 += Hin[(2 * j + 1) * HN + q] + hu[(2 * j + 1) * HN + q];
-                }
-                xi[4] = s4;
-                xi[16] = s16;
-            }
-            collide19(a.co, f, r, xi, o);
-        } else {
-            // nb[i] = rho(r + c_i)
-            R nb[Q27];
-#pragma unroll
-            for (int i = 0; i < Q27; ++i) {
-                const int cz = LAT::c(i, 2);
-                const R* pl = cz == 0 ? d0 : (cz > 0 ? dp : dm);
-                nb[i] = pl[LAT::c(i, 1) * RX + LAT::c(i, 0)];
-            }
-            if (MODE == 1) normals27(a, (uint32_t)node, xi);
-            collide27(a.co, f, nb, xi, o);
-        }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) a.dst[(I)i * PI + node] = o[i];
-    };
-
-    if constexpr (SLOTS == 3) {
-        // planes z0-1, z0 -> slots 0, 1; plane z0+1 -> slot 2 (in flight); density slots alike
-        issue(z0 - 1, 0);
-        issue(z0, 1);
-        cp_async_wait_all();
-        __syncthreads();
-        density(0, 0);
-        density(1, 1);
-        if constexpr (MODE == 3) stencil_plane(z0 - 1, false, 0);
-        issue(z0 + 1, 2);
-        for (int z = z0; z < z1; ++z) {
-            const int k0 = (z - z0 + 1) % 3, km = (k0 + 2) % 3, kp = (k0 + 1) % 3;   // slots of z, z-1, z+1
-            cp_async_wait_all();
-            __syncthreads();
-            density(kp, kp);
-            if constexpr (MODE == 3) stencil_plane(z, true, (z - z0 + 1) & 1);
-            if (z + 1 < z1) issue(z + 2, km);          // plane z-1's slot is free
-            __syncthreads();
-            if (!own) continue;
-            const R* sl = raw + k0 * Q * RN;
-            R f[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = sl[i * RN + qc];
-            collide_plane(z, f, k0, km, kp, (z - z0) & 1);
-        }
-    } else {
-        // two raw slots: a plane's own pulled values move to registers when its densities are
-        // summed, which frees its slot for the plane after next
-        R fcur[Q], fnext[Q];
-        auto take = [&](int k, R (&f)[Q]) {
-            const R* sl = raw + k * Q * RN;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = own ? sl[i * RN + qc] : R(0);
-        };
-        issue(z0 - 1, 0);
-        issue(z0, 1);
-        cp_async_wait_all();
-        __syncthreads();
-        density(0, 0);                 // plane z0-1 -> density slot 0
-        density(1, 1);                 // plane z0 -> density slot 1
-        take(1, fcur);
-        if constexpr (MODE == 3) stencil_plane(z0 - 1, false, 0);
-        __syncthreads();
-        issue(z0 + 1, 0);              // raw slot of plane p: (p - z0 + 1) % 2
-        for (int z = z0; z < z1; ++z) {
-            const int k0 = (z - z0 + 1) % 3, km = (k0 + 2) % 3, kp = (k0 + 1) % 3;
-            const int rp = (z - z0) & 1;             // raw slot of plane z+1
-            cp_async_wait_all();
-            __syncthreads();
-            if (z + 1 < z1) issue(z + 2, rp ^ 1);    // the slot of plane z, already in registers
-            density(rp, kp);
-            take(rp, fnext);
-            if constexpr (MODE == 3) stencil_plane(z, true, (z - z0 + 1) & 1);
-            __syncthreads();
-            if (own) collide_plane(z, fcur, k0, km, kp, (z - z0) & 1);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) fcur[i] = fnext[i];
-        }
-    }
-    cp_async_wait_all();
-}
-
-// ---- the plain D3Q19 kernel (cross-check) -----------------------------------------------
-
-// the 19 pulled deviations of node (x, y, z): f_i = src_i(r - c_i)
-template <typename R>
-__device__ __forceinline__ void pull19(const R* __restrict__ s, long long P, int x, int xm, int xp, long long ym,
-                                       long long y0, long long yp, long long zm, long long z0, long long zp,
-                                       R f[Q3]) {
-    f[0] = s[z0 + y0 + x];
-    f[1] = s[P + z0 + y0 + xm];
-    f[2] = s[2 * P + z0 + y0 + xp];
-    f[3] = s[3 * P + z0 + ym + x];
-    f[4] = s[4 * P + z0 + yp + x];
-    f[5] = s[5 * P + zm + y0 + x];
-    f[6] = s[6 * P + zp + y0 + x];
-    f[7] = s[7 * P + z0 + ym + xm];
-    f[8] = s[8 * P + z0 + yp + xm];
-    f[9] = s[9 * P + z0 + ym + xp];
-    f[10] = s[10 * P + z0 + yp + xp];
-    f[11] = s[11 * P + zm + ym + x];
-    f[12] = s[12 * P + zp + ym + x];
-    f[13] = s[13 * P + zm + yp + x];
-    f[14] = s[14 * P + zp + yp + x];
-    f[15] = s[15 * P + zm + y0 + xm];
-    f[16] = s[16 * P + zm + y0 + xp];
-    f[17] = s[17 * P + zp + y0 + xm];
-    f[18] = s[18 * P + zp + y0 + xp];
-}
-
-template <typename R, int MODE, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
-    constexpr int RX = TX + 2, RY = TY + 2, NT = TX * TY;
-    __shared__ R rs[3][RY][RX];
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long P = a.P, nxy = (long long)nx * ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * a.zc;
-    const int z1 = min(z0 + a.zc, nz);
-    const int tid = threadIdx.x;
-    const R* __restrict__ src = a.src;
-
-    auto density = [&](int zz, int slot) {
-        const int zc = wrap_hi(wrap_lo(zz, nz), nz);
-        const long long Z0 = zc * nxy;
-        const long long Zm = (zc == 0 ? nz - 1 : zc - 1) * nxy, Zp = (zc == nz - 1 ? 0 : zc + 1) * nxy;
-        for (int q = tid; q < RX * RY; q += NT) {
-            const int ly = q / RX, lx = q - ly * RX;
-            int gx = x0 + lx - 1, gy = y0 + ly - 1;
-            R v = R(0);
-            if (gx <= nx && gy <= ny) {
-                gx = wrap_hi(wrap_lo(gx, nx), nx);
-                gy = wrap_hi(wrap_lo(gy, ny), ny);
-                const int xm = gx == 0 ? nx - 1 : gx - 1, xp = gx == nx - 1 ? 0 : gx + 1;
-                const long long Y0 = (long long)gy * nx;
-                const long long Ym = (long long)(gy == 0 ? ny - 1 : gy - 1) * nx;
-                const long long Yp = (long long)(gy == ny - 1 ? 0 : gy + 1) * nx;
-                R f[Q3];
-                pull19(src, P, gx, xm, xp, Ym, Y0, Yp, Zm, Z0, Zp, f);
-                v = drho19(f);
-            }
-            rs[slot][ly][lx] = v;
-        }
-    };
-
-    density(z0 - 1, 0);
-    density(z0, 1);
-    const int lx = tid % TX, ly = tid / TX;
-    const int x = x0 + lx, y = y0 + ly;
-    const bool own = x < nx && y < ny;
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const long long Y0 = (long long)y * nx;
-    const long long Ym = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
-    const long long Yp = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
-    for (int z = z0; z < z1; ++z) {
-        const int s0 = (z - z0 + 1) % 3, sm = (s0 + 2) % 3, sp = (s0 + 1) % 3;
-        density(z + 1, sp);
-        __syncthreads();
-        if (own) {
-            const long long Z0 = (long long)z * nxy;
-            const long long Zm = (long long)(z == 0 ? nz - 1 : z - 1) * nxy;
-            const long long Zp = (long long)(z == nz - 1 ? 0 : z + 1) * nxy;
-            R f[Q3];
-            pull19(src, P, x, xm, xp, Ym, Y0, Yp, Zm, Z0, Zp, f);
-            const int cx = lx + 1, cy = ly + 1;
-            Rho3<R> r;
-            r.c = rs[s0][cy][cx];
-            r.xp = rs[s0][cy][cx + 1]; r.xm = rs[s0][cy][cx - 1];
-            r.yp = rs[s0][cy + 1][cx]; r.ym = rs[s0][cy - 1][cx];
-            r.zp = rs[sp][cy][cx]; r.zm = rs[sm][cy][cx];
-            r.ap = rs[s0][cy + 1][cx + 1]; r.am = rs[s0][cy - 1][cx - 1];
-            r.bp = rs[s0][cy - 1][cx + 1]; r.bm = rs[s0][cy + 1][cx - 1];
-            r.cp = rs[sp][cy + 1][cx]; r.cm = rs[sm][cy - 1][cx];
-            r.dp = rs[sm][cy + 1][cx]; r.dm = rs[sp][cy - 1][cx];
-            r.ep = rs[sp][cy][cx + 1]; r.em = rs[sm][cy][cx - 1];
-            r.fp = rs[sp][cy][cx - 1]; r.fm = rs[sm][cy][cx + 1];
-            R xi[Q3];
-#pragma unroll
-            for (int q = 0; q < Q3; ++q) xi[q] = R(0);
-            const long long node = Z0 + Y0 + x;
-            if (MODE == 1) normals19(a, (uint32_t)node, xi);
-            R o[Q3];
-            collide19(a.co, f, r, xi, o);
-            R* __restrict__ d = a.dst + node;
-#pragma unroll
-            for (int i = 0; i < Q3; ++i) d[i * P] = o[i];
-        }
-        __syncthreads();
-    }
-}
-
-template <typename LAT, typename R, int MODE, typename I, int SLOTS>
-static cudaError_t launch_staged(const Step3Args<R>& a, dim3 grid, cudaStream_t s) {
-    constexpr int smem = staged_smem_bytes<LAT, R, SLOTS, MODE>();
-    // the shared-memory limit is a per-device attribute of the function: set it once per
-    // device (a repeated set from a concurrent first launch is harmless)
-    static std::atomic<unsigned> done{0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const unsigned bit = 1u << (dev & 31);
-    if (!(done.load(std::memory_order_acquire) & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(step3_staged_kernel<LAT, R, MODE, I, SLOTS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        done.fetch_or(bit, std::memory_order_release);
-    }
-    step3_staged_kernel<LAT, R, MODE, I, SLOTS><<<grid, LAT::TX * LAT::TY, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename LAT, typename R, int MODE>
-static cudaError_t launch3(const Step3Args<R>& a, dim3 grid, bool plain, int slots, cudaStream_t s) {
-    if constexpr (LAT::Q == 19) {
-        if (plain) {
-            step3_kernel<R, MODE, 32, 8><<<grid, 256, 0, s>>>(a);
-            return cudaGetLastError();
-        }
-    }
-    const bool narrow = (unsigned long long)a.P * LAT::Q < (1ULL << 32);
-    if (slots == 2)
-        return narrow ? launch_staged<LAT, R, MODE, uint32_t, 2>(a, grid, s)
-                      : launch_staged<LAT, R, MODE, unsigned long long, 2>(a, grid, s);
-    return narrow ? launch_staged<LAT, R, MODE, uint32_t, 3>(a, grid, s)
-                  : launch_staged<LAT, R, MODE, unsigned long long, 3>(a, grid, s);
-}
 
 // ---- host-side theory --------------------------------------------------------------------
 
 static double w_of(int lattice, int i) { return lattice == 19 ? Lat19::w(i) : Lat27::w(i); }
 static int c_of(int lattice, int i, int k) { return lattice == 19 ? Lat19::c(i, k) : Lat27::c(i, k); }
+// the stored plane of population i
+static int sigma_of(int lattice, int i) { return lattice == 19 ? Lat19::sigma(i) : Lat27::sigma(i); }
 
 // rest populations: w_i 3 cs2 rho0 on the moving velocities, the remainder at rest
 static void rest_pops(int lattice, double rho0, double cs2, double* fbar) {
@@ -706,46 +139,85 @@ static bool cholesky_block(const double* X, int Q, const std::vector<int>& idx, 
 
 // ---- populations in and out; sums ---------------------------------------------------------
 
-// node q of an nx x ny x nz box shifted by (sx, sy, sz) with periodic wrap (|s| <= 1)
-__device__ __forceinline__ long long shifted3(long long q, int nx, int ny, int nz, int sx, int sy, int sz) {
+// The stored geometry of a context (the padded storage of lb3d_kernel.cuh).
+struct Geom3 {
+    int nx, ny, nz, gx, pitch;
+    long long PL, P;
+    // stored offset of node (x, y, z), -gx <= x < nx + gx, -GY3 <= y < ny + GY3
+    __host__ __device__ long long at(int x, int y, int z) const {
+        return (long long)z * PL + (long long)(y + GY3) * pitch + (x + gx);
+    }
+};
+
+// coordinates of lattice node q = (z ny + y) nx + x
+__device__ __forceinline__ void coords3(long long q, int nx, int ny, int* x, int* y, int* z) {
     const long long nxy = (long long)nx * ny;
-    int z = (int)(q / nxy);
-    const long long r = q - (long long)z * nxy;
-    int y = (int)(r / nx), x = (int)(r - (long long)y * nx);
-    x += sx; y += sy; z += sz;
-    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-    z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-    return (long long)z * nxy + (long long)y * nx + x;
+    *z = (int)(q / nxy);
+    const long long r = q - (long long)*z * nxy;
+    *y = (int)(r / nx);
+    *x = (int)(r - (long long)*y * nx);
 }
 
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
 // The device holds post-collision deviations (the kernel pulls f_i(r) = f*_i(r - c_i)), so
-// the pre-collision f_i(r) of the ABI is stored at r - c_i: dst(q) = f_i(q + c_i) - fbar_i.
+// the pre-collision f_i(r) of the ABI is stored at r - c_i: stored(q) = f_i(q + c_i) - fbar_i
+// on the interior; fill_ghosts3_kernel then sets the ghost copies.
 template <typename R>
-__global__ void set_plane3_kernel(const double* __restrict__ src, R* __restrict__ dst, int nx, int ny, int nz,
-                                  int cx, int cy, int cz, double fbar) {
-    const long long n = (long long)nx * ny * nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-        dst[q] = (R)(src[shifted3(q, nx, ny, nz, cx, cy, cz)] - fbar);
+__global__ void set_plane3_kernel(const double* __restrict__ src, R* __restrict__ dst, Geom3 g, int cx, int cy,
+                                  int cz, double fbar) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords3(q, g.nx, g.ny, &x, &y, &z);
+        const int sx = wrap1(x + cx, g.nx), sy = wrap1(y + cy, g.ny), sz = wrap1(z + cz, g.nz);
+        dst[g.at(x, y, z)] = (R)(src[((long long)sz * g.ny + sy) * g.nx + sx] - fbar);
+    }
+}
+
+// every ghost position of one population takes the value of the interior node it wraps to
+template <typename R>
+__global__ void fill_ghosts3_kernel(R* __restrict__ p, Geom3 g) {
+    const int W = g.nx + 2 * g.gx, H = g.ny + 2 * GY3;
+    const long long n = (long long)W * H * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(q / ((long long)W * H));
+        const long long r = q - (long long)z * W * H;
+        const int yy = (int)(r / W) - GY3, xx = (int)(r % W) - g.gx;
+        if (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny) continue;
+        const int sx = ((xx % g.nx) + g.nx) % g.nx, sy = ((yy % g.ny) + g.ny) % g.ny;
+        p[g.at(xx, yy, z)] = p[g.at(sx, sy, z)];
+    }
 }
 
 // f_i(r) = stored(r - c_i) + fbar_i
 template <typename R>
-__global__ void get_plane3_kernel(const R* __restrict__ src, double* __restrict__ dst, int nx, int ny, int nz,
-                                  int cx, int cy, int cz, double fbar) {
-    const long long n = (long long)nx * ny * nz;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-        dst[q] = (double)src[shifted3(q, nx, ny, nz, -cx, -cy, -cz)] + fbar;
+__global__ void get_plane3_kernel(const R* __restrict__ src, double* __restrict__ dst, Geom3 g, int cx, int cy,
+                                  int cz, double fbar) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords3(q, g.nx, g.ny, &x, &y, &z);
+        dst[q] = (double)src[g.at(wrap1(x - cx, g.nx), wrap1(y - cy, g.ny), wrap1(z - cz, g.nz))] + fbar;
+    }
 }
 
-// per-block FP64 partial sums of the density and momentum deviations
+// per-block FP64 partial sums of the density and momentum deviations over the interior
 template <typename LAT, typename R>
-__global__ void sums3_kernel(const R* __restrict__ p, long long n, double* __restrict__ partial) {
+__global__ void sums3_kernel(const R* __restrict__ p, Geom3 g, double* __restrict__ partial) {
     double s[4] = {0, 0, 0, 0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords3(k, g.nx, g.ny, &x, &y, &z);
+        const long long o = g.at(x, y, z);
 #pragma unroll
         for (int i = 0; i < LAT::Q; ++i) {
-            const double f = (double)p[i * n + k];
+            const double f = (double)p[LAT::sigma(i) * g.P + o];
             s[0] += f;
             s[1] += LAT::c(i, 0) * f;
             s[2] += LAT::c(i, 1) * f;
@@ -773,7 +245,8 @@ using namespace lbf3;
 
 struct lb3_ctx {
     int nx = 0, ny = 0, nz = 0, lattice = 19, precision = 0, device = 0, es = 4;
-    long long n = 0;
+    long long n = 0;                // lattice nodes
+    Geom3 geom{};                   // padded storage
     uint64_t seed = 0;
     double rho0 = 1.0, cs2 = 1.0 / 3.0;
     double fbar[QMAX] = {};
@@ -781,16 +254,15 @@ struct lb3_ctx {
     void* pop[2] = {nullptr, nullptr};
     double* stage = nullptr;        // one FP64 plane
     double* partial = nullptr;      // SUM3_BLOCKS x 4
+    int* err_dev = nullptr;         // device error word of the TMA waits
+    CUtensorMap maps[2];            // TMA: the population buffers (box of the staged kernel)
     int cur = 0;
     bool have_params = false;
     int noise_mode = LB_NOISE_OFF;
     double kT = 0, kappa = 0;
     Step3Args<float> af{};
     Step3Args<double> ad{};
-    dim3 grid;
-    bool plain = false;             // LBFLUCT3_KERNEL=plain: the plain D3Q19 kernel
-    int slots = 3;                  // raw slots of the staged kernel: 3 for D3Q19, 2 for D3Q27
-                                    // (the measured faster; LBFLUCT3_SLOTS=2 or 3 overrides)
+    Launch3 cfg[2];                 // step kernel without / with the correlated noise (kmode 3)
     cudaStream_t stream = nullptr;
     long long t = 0;
     std::string err;
@@ -825,21 +297,34 @@ bool sizes_ok(int nx, int ny, int nz) {
 int es_of(int precision) { return precision == LB_FP32 ? 4 : (precision == LB_FP64 ? 8 : 0); }
 bool lattice_ok(int lattice) { return lattice == LB_D3Q19 || lattice == LB_D3Q27; }
 
+// padded storage of an nx x ny x nz lattice with es-byte elements (lb3d_kernel.cuh)
+Geom3 geom3(int nx, int ny, int nz, int es) {
+    Geom3 g{};
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.gx = 32 / es;
+    g.pitch = ((nx + 2 * g.gx + g.gx - 1) / g.gx) * g.gx;
+    g.PL = (long long)(ny + 2 * GY3) * g.pitch;
+    g.P = (long long)nz * g.PL;
+    return g;
+}
+
 struct Layout3 {
-    size_t pop[2], stage, partial, total;
+    size_t pop[2], stage, partial, err, total;
 };
 
-Layout3 layout3(long long n, int q, int es) {
+Layout3 layout3(const Geom3& g, int q, int es) {
     Layout3 L{};
     size_t off = 0;
     for (int k = 0; k < 2; ++k) {
         L.pop[k] = off;
-        off = align256(off + (size_t)q * n * es);
+        off = align256(off + (size_t)q * g.P * es);
     }
     L.stage = off;
-    off = align256(off + (size_t)n * sizeof(double));
+    off = align256(off + (size_t)g.nx * g.ny * g.nz * sizeof(double));
     L.partial = off;
     off = align256(off + (size_t)SUM3_BLOCKS * 4 * sizeof(double));
+    L.err = off;
+    off = align256(off + sizeof(int));
     L.total = off;
     return L;
 }
@@ -870,18 +355,83 @@ int record_timing3(lb3_ctx* c, cudaEvent_t* start, cudaEvent_t* stop) {
     return LB_OK;
 }
 
-// the z run of a CTA: enough CTAs for eight per SM, each at least one plane
-void choose_grid(lb3_ctx* c) {
+// The step kernel of a context.  Measured on GB300 at 256^3 (FP32): both lattices stage by
+// TMA in two slots (D3Q19 with and without the correlated noise: three CTAs per SM at 80
+// registers, against two with three slots; D3Q27 on 32 x 4 tiles).  FP64 stages by copies
+// (D3Q19 in three slots, D3Q27 in two; TMA boxes of doubles would fit one CTA per SM).
+// LBFLUCT3_KERNEL=plain (D3Q19), LBFLUCT3_STAGE=tma|copy, LBFLUCT3_SLOTS=2|3 and
+// LBFLUCT3_TY=4|6 (D3Q27 with TMA) override the choice.
+Launch3 default_cfg(int lattice, int precision) {
+    Launch3 L{};
+    L.kmode = 0;
+    L.plain = false;
+    L.tma = precision == LB_FP32;
+    L.slots = (L.tma || lattice == 27) ? 2 : 3;
+    L.ty = lattice == 19 ? 8 : 4;
+    return L;
+}
+
+Launch3 env_cfg(Launch3 L, int lattice, int precision, bool rs) {
+    const char* v = std::getenv("LBFLUCT3_KERNEL");
+    L.plain = v && std::strcmp(v, "plain") == 0 && lattice == 19 && !rs;
+    if (const char* st = std::getenv("LBFLUCT3_STAGE")) {
+        if (std::strcmp(st, "tma") == 0) L.tma = precision == LB_FP32;
+        else if (std::strcmp(st, "copy") == 0) L.tma = false;
+    }
+    if (const char* sv = std::getenv("LBFLUCT3_SLOTS")) L.slots = std::atoi(sv) == 2 ? 2 : 3;
+    if (lattice == 27) {
+        if (L.tma) L.slots = 2;
+        const char* tv = std::getenv("LBFLUCT3_TY");
+        L.ty = (L.tma && tv && std::atoi(tv) == 6) ? 6 : 4;
+    }
+    return L;
+}
+
+// the grid of a configuration: the z run of a CTA gives enough CTAs for eight per SM, each
+// at least one plane
+void choose_grid(lb3_ctx* c, Launch3* L) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const int tx = c->lattice == 19 ? Lat19::TX : Lat27::TX, ty = c->lattice == 19 ? Lat19::TY : Lat27::TY;
+    const int tx = 32, ty = L->plain ? 8 : L->ty;
     const long long bxy = (long long)((c->nx + tx - 1) / tx) * ((c->ny + ty - 1) / ty);
     const long long want = 8LL * sms;
     long long chunks = std::max(1LL, std::min((long long)c->nz, (want + bxy - 1) / bxy));
     const int zc = (int)((c->nz + chunks - 1) / chunks);
     chunks = (c->nz + zc - 1) / zc;
-    c->grid = dim3((c->nx + tx - 1) / tx, (c->ny + ty - 1) / ty, (unsigned)chunks);
-    c->af.zc = c->ad.zc = zc;
+    L->grid = dim3((c->nx + tx - 1) / tx, (c->ny + ty - 1) / ty, (unsigned)chunks);
+    L->zc = zc;
+}
+
+// Tensor map over one population buffer: dims (pitch, ny + 2 GY3, nz, Q) of FP32, box
+// (TX + 8, ty + 2, 1, GM) (the tile, its ring and the 16-byte x alignment; the GM stored
+// planes of one (c_y, c_z)), zero fill outside.
+bool make_map3(const lb3_ctx* c, const void* buf, int ty, CUtensorMap* map) {
+    lbf::EncodeTiledFn fn = lbf::tensor_map_encoder();
+    if (!fn) return false;
+    const Geom3& g = c->geom;
+    cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * GY3), (cuuint64_t)g.nz,
+                          (cuuint64_t)c->lattice};
+    cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.PL * 4, (cuuint64_t)g.P * 4};
+    cuuint32_t box[4] = {32 + 8, (cuuint32_t)(ty + 2), 1, (cuuint32_t)(c->lattice == 19 ? Lat19::GM : Lat27::GM)};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(buf), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Reads the device error word (after the stream has drained); a CTA that gave up waiting for
+// its TMA loads is reported as LB_ETIMEOUT and the word cleared.
+int check_device_error3(lb3_ctx* c) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail3(c, e, "error word");
+    if (h != 0) {
+        e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) return cuda_fail3(c, e, "error word");
+        return fail3(c, LB_ETIMEOUT, "a 3-D step kernel gave up waiting for its TMA loads");
+    }
+    return LB_OK;
 }
 
 // Xi(0) of the lattice, row-major Q x Q
@@ -923,7 +473,9 @@ bool noise_factors(int lattice, const double* X, double sc[QMAX], double Lc[28])
 template <typename R>
 void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double sc[QMAX],
                const double Lc[28], const double Lrs[9]) {
-    a->nx = c->nx; a->ny = c->ny; a->nz = c->nz; a->P = c->n;
+    a->nx = c->nx; a->ny = c->ny; a->nz = c->nz;
+    a->pitch = c->geom.pitch; a->PL = c->geom.PL; a->P = c->geom.P;
+    a->err = c->err_dev;
     a->co.rho0 = (R)c->rho0;
     a->co.d = (R)(3.0 * c->cs2 - 1.0);
     a->co.kappa = (R)c->kappa;
@@ -937,14 +489,13 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
 }
 
 template <typename R>
-cudaError_t launch_any(lb3_ctx* c, const Step3Args<R>& a, int kmode) {
-    if (c->lattice == 19) {
-        if (kmode == 3) return launch3<Lat19, R, 3>(a, c->grid, false, c->slots, c->stream);
-        return kmode ? launch3<Lat19, R, 1>(a, c->grid, c->plain, c->slots, c->stream)
-                     : launch3<Lat19, R, 0>(a, c->grid, c->plain, c->slots, c->stream);
-    }
-    return kmode ? launch3<Lat27, R, 1>(a, c->grid, false, c->slots, c->stream)
-                 : launch3<Lat27, R, 0>(a, c->grid, false, c->slots, c->stream);
+cudaError_t launch_any(lb3_ctx* c, Step3Args<R> a, int kmode) {
+    Launch3 L = c->cfg[kmode == 3 ? 1 : 0];
+    L.kmode = kmode;
+    a.zc = L.zc;
+    const CUtensorMap* map = &c->maps[c->cur];
+    return c->lattice == 19 ? launch_lattice<Lat19, R>(a, map, L, c->stream)
+                            : launch_lattice<Lat27, R>(a, map, L, c->stream);
 }
 
 }  // namespace
@@ -954,7 +505,7 @@ extern "C" {
 size_t lb3_workspace_bytes(int nx, int ny, int nz, int lattice, int precision) {
     const int es = es_of(precision);
     if (!es || !lattice_ok(lattice) || !sizes_ok(nx, ny, nz)) return 0;
-    return layout3((long long)nx * ny * nz, lattice, es).total;
+    return layout3(geom3(nx, ny, nz, es), lattice, es).total;
 }
 
 int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed, double rho0, double cs2,
@@ -971,7 +522,8 @@ int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed
     c->nx = nx; c->ny = ny; c->nz = nz; c->n = (long long)nx * ny * nz; c->lattice = lattice;
     c->precision = precision; c->es = es; c->seed = seed; c->rho0 = rho0; c->cs2 = cs2;
     cudaGetDevice(&c->device);
-    const Layout3 L = layout3(c->n, lattice, es);
+    c->geom = geom3(nx, ny, nz, es);
+    const Layout3 L = layout3(c->geom, lattice, es);
     cudaError_t e = cudaMalloc((void**)&c->ws, L.total);
     if (e != cudaSuccess) {
         delete c;
@@ -981,21 +533,31 @@ int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed
     c->pop[1] = c->ws + L.pop[1];
     c->stage = (double*)(c->ws + L.stage);
     c->partial = (double*)(c->ws + L.partial);
+    c->err_dev = (int*)(c->ws + L.err);
     rest_pops(lattice, rho0, cs2, c->fbar);
-    e = cudaMemset(c->pop[0], 0, (size_t)lattice * c->n * es);
-    if (e == cudaSuccess) e = cudaMemset(c->pop[1], 0, (size_t)lattice * c->n * es);
+    // the whole workspace starts at zero: the rest state, ghosts included
+    e = cudaMemset(c->ws, 0, L.total);
     if (e != cudaSuccess) {
         cudaFree(c->ws);
         delete c;
         return fail3(nullptr, LB_ECUDA, std::string("lb3_create: ") + cudaGetErrorString(e));
     }
-    {
-        const char* v = std::getenv("LBFLUCT3_KERNEL");
-        c->plain = v && std::strcmp(v, "plain") == 0 && lattice == 19;
-        const char* sv = std::getenv("LBFLUCT3_SLOTS");
-        c->slots = sv ? (std::atoi(sv) == 2 ? 2 : 3) : (lattice == 27 ? 2 : 3);
+    std::memset(c->maps, 0, sizeof(c->maps));
+    for (int k = 0; k < 2; ++k) {
+        c->cfg[k] = env_cfg(default_cfg(lattice, precision), lattice, precision, k == 1);
+        choose_grid(c, &c->cfg[k]);
     }
-    choose_grid(c);
+    // one tensor-map pair serves both configurations: they share the tile height when both
+    // stage by TMA (D3Q19: 8; D3Q27 has no correlated noise)
+    const Launch3* tl = c->cfg[0].tma ? &c->cfg[0] : (c->cfg[1].tma ? &c->cfg[1] : nullptr);
+    if (tl) {
+        for (int k = 0; k < 2; ++k)
+            if (!make_map3(c, c->pop[k], tl->ty, &c->maps[k])) {
+                cudaFree(c->ws);
+                delete c;
+                return fail3(nullptr, LB_ECUDA, "lb3_create: cuTensorMapEncodeTiled failed");
+            }
+    }
     *out = c;
     return LB_OK;
 }
@@ -1128,15 +690,20 @@ int lb3_set_populations(lb3_ctx* c, const double* f, int loc, int64_t t) {
             src = c->stage;
         }
         const int cx = c_of(c->lattice, i, 0), cy = c_of(c->lattice, i, 1), cz = c_of(c->lattice, i, 2);
-        if (c->precision == LB_FP64)
-            set_plane3_kernel<double><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                src, (double*)c->pop[c->cur] + (long long)i * c->n, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
-        else
-            set_plane3_kernel<float><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                src, (float*)c->pop[c->cur] + (long long)i * c->n, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
+        const Geom3& g = c->geom;
+        const long long padded = (long long)(g.nx + 2 * g.gx) * (g.ny + 2 * GY3) * g.nz;
+        if (c->precision == LB_FP64) {
+            double* p = (double*)c->pop[c->cur] + (long long)sigma_of(c->lattice, i) * g.P;
+            set_plane3_kernel<double><<<plane_blocks(c->n), 256, 0, c->stream>>>(src, p, g, cx, cy, cz, c->fbar[i]);
+            fill_ghosts3_kernel<double><<<plane_blocks(padded), 256, 0, c->stream>>>(p, g);
+        } else {
+            float* p = (float*)c->pop[c->cur] + (long long)sigma_of(c->lattice, i) * g.P;
+            set_plane3_kernel<float><<<plane_blocks(c->n), 256, 0, c->stream>>>(src, p, g, cx, cy, cz, c->fbar[i]);
+            fill_ghosts3_kernel<float><<<plane_blocks(padded), 256, 0, c->stream>>>(p, g);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail3(c, e, "set populations");
-        c->kernels += 1;
+        c->kernels += 2;
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail3(c, e, "cudaStreamSynchronize");
@@ -1150,12 +717,13 @@ int lb3_get_populations(lb3_ctx* c, double* f, int loc) {
     for (int i = 0; i < c->lattice; ++i) {
         double* dst = loc == LB_HOST ? c->stage : f + (long long)i * c->n;
         const int cx = c_of(c->lattice, i, 0), cy = c_of(c->lattice, i, 1), cz = c_of(c->lattice, i, 2);
+        const Geom3& g = c->geom;
         if (c->precision == LB_FP64)
             get_plane3_kernel<double><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                (const double*)c->pop[c->cur] + (long long)i * c->n, dst, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
+                (const double*)c->pop[c->cur] + (long long)sigma_of(c->lattice, i) * g.P, dst, g, cx, cy, cz, c->fbar[i]);
         else
             get_plane3_kernel<float><<<plane_blocks(c->n), 256, 0, c->stream>>>(
-                (const float*)c->pop[c->cur] + (long long)i * c->n, dst, c->nx, c->ny, c->nz, cx, cy, cz, c->fbar[i]);
+                (const float*)c->pop[c->cur] + (long long)sigma_of(c->lattice, i) * g.P, dst, g, cx, cy, cz, c->fbar[i]);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail3(c, e, "get populations");
         c->kernels += 1;
@@ -1167,7 +735,7 @@ int lb3_get_populations(lb3_ctx* c, double* f, int loc) {
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail3(c, e, "cudaStreamSynchronize");
-    return LB_OK;
+    return check_device_error3(c);
 }
 
 int lb3_sums(lb3_ctx* c, double sums[4]) {
@@ -1176,17 +744,17 @@ int lb3_sums(lb3_ctx* c, double sums[4]) {
     const bool d = c->precision == LB_FP64;
     if (c->lattice == 19) {
         if (d)
-            sums3_kernel<Lat19, double><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const double*)c->pop[c->cur], c->n,
+            sums3_kernel<Lat19, double><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const double*)c->pop[c->cur], c->geom,
                                                                            c->partial);
         else
-            sums3_kernel<Lat19, float><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const float*)c->pop[c->cur], c->n,
+            sums3_kernel<Lat19, float><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const float*)c->pop[c->cur], c->geom,
                                                                           c->partial);
     } else {
         if (d)
-            sums3_kernel<Lat27, double><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const double*)c->pop[c->cur], c->n,
+            sums3_kernel<Lat27, double><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const double*)c->pop[c->cur], c->geom,
                                                                            c->partial);
         else
-            sums3_kernel<Lat27, float><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const float*)c->pop[c->cur], c->n,
+            sums3_kernel<Lat27, float><<<SUM3_BLOCKS, 256, 0, c->stream>>>((const float*)c->pop[c->cur], c->geom,
                                                                           c->partial);
     }
     cudaError_t e = cudaGetLastError();
@@ -1196,6 +764,7 @@ int lb3_sums(lb3_ctx* c, double sums[4]) {
     e = cudaMemcpyAsync(h.data(), c->partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail3(c, e, "sums D2H");
+    if (int r = check_device_error3(c)) return r;
     double s[4] = {0, 0, 0, 0};
     for (int b = 0; b < SUM3_BLOCKS; ++b)
         for (int q = 0; q < 4; ++q) s[q] += h[(size_t)b * 4 + q];
@@ -1247,7 +816,7 @@ int lb3_synchronize(lb3_ctx* c) {
     lbf::DeviceGuard dg(c->device);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail3(c, e, "cudaStreamSynchronize");
-    return LB_OK;
+    return check_device_error3(c);
 }
 
 const char* lb3_last_error(lb3_ctx* c) { return c ? c->err.c_str() : g3_error.c_str(); }

@@ -330,29 +330,13 @@ __global__ void batch_bin_kernel(const float2* __restrict__ z1, const float2* __
 
 // --- host side -------------------------------------------------------------------------
 
-typedef CUresult (*EncodeTiledFnB)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFnB encode_fn_b() {
-    static EncodeTiledFnB fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFnB)p;
-    }
-    return fn;
-}
-
 // Tile shapes the autotuner chooses from: (TX, TY, NT); TX * TY / NT nodes per thread.
 static const int kBatchTiles[][3] = {{32, 16, 256}, {32, 16, 128}, {32, 8, 256}, {32, 8, 128},
                                      {64, 8, 256},  {64, 16, 512}, {32, 32, 512}};
 constexpr int kBatchTileCount = 7;
 
 static bool make_class_map(void* buf, const Grid& g, int R, int tile, CUtensorMap* map) {
-    EncodeTiledFnB fn = encode_fn_b();
+    EncodeTiledFn fn = tensor_map_encoder();
     if (!fn || tile < 0 || tile >= kBatchTileCount) return false;
     cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)Q, (cuuint64_t)R};
     cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.plane * 4 * Q};

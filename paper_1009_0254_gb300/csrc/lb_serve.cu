@@ -241,24 +241,8 @@ __global__ void __launch_bounds__(1024) serve_noise_rows_kernel(const int* __res
     }
 }
 
-typedef CUresult (*EncodeTiledFnS)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFnS encode_fn_s() {
-    static EncodeTiledFnS fn = nullptr;
-    if (!fn) {
-        void* q = nullptr;
-        cudaDriverEntryPointQueryResult r;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000, cudaEnableDefault, &r) ==
-                cudaSuccess && r == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFnS)q;
-    }
-    return fn;
-}
-
 static bool make_slot_map(void* buf, const Grid& g, CUtensorMap* map) {
-    EncodeTiledFnS fn = encode_fn_s();
+    EncodeTiledFn fn = tensor_map_encoder();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)(g.ny + 2 * GY), (cuuint64_t)Q};
     cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
@@ -908,7 +892,7 @@ int lb_server_create(size_t hbm_budget_bytes, int max_active, int max_chunk_step
         return fail_create(e);
     s->grid = sms * std::max(per, 1);
     s->grid_rs = sms * std::max(per_rs, 1);
-    if (!encode_fn_s()) {
+    if (!tensor_map_encoder()) {
         set_context_free_error("lb_server_create: cuTensorMapEncodeTiled is not available");
         lb_server_destroy(s);
         return LB_ECUDA;

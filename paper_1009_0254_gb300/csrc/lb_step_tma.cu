@@ -174,19 +174,14 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
 
 // --- host side ----------------------------------------------------------------------
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+EncodeTiledFn tensor_map_encoder() {
+    static const EncodeTiledFn fn = [] {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
+        const bool ok = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                            cudaSuccess && q == cudaDriverEntryPointSuccess;
+        return ok ? (EncodeTiledFn)p : (EncodeTiledFn) nullptr;
+    }();
     return fn;
 }
 
@@ -209,7 +204,7 @@ int tma_default_tile(int noise_mode, int fp16) {
 // Tensor map over one population buffer: dims (pitch, ny + 2 GY, 9) of FP32, box
 // (TX + 8, TY + 2, 1), zero fill outside.
 bool make_pop_tensor_map(const void* buf, const Grid& g, int tile, int fp16, void* map_out) {
-    EncodeTiledFn fn = encode_fn();
+    EncodeTiledFn fn = tensor_map_encoder();
     if (!fn || tile < 0 || tile >= tma_tile_count()) return false;
     const cuuint64_t es = fp16 ? 2 : 4;
     const int xo = fp16 ? Elem<__half>::XO : Elem<float>::XO;

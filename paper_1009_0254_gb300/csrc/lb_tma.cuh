@@ -33,6 +33,13 @@ struct TmaTile {
 
 static __constant__ int kCYt[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
+// cuTensorMapEncodeTiled of the driver, looked up once per process (thread-safe); null if
+// the driver does not provide it
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

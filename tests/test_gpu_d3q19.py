@@ -54,11 +54,18 @@ def _pair(nx, ny, nz, mode, precision=lbf.LB_FP32, cs2=0.25, rho0=1.0, seed=7, a
 SIZES = [(32, 8, 4), (37, 11, 5), (64, 16, 9), (5, 3, 2), (1, 1, 8), (40, 1, 3), (3, 17, 1)]
 
 
-@pytest.fixture(params=["staged", "staged2", "plain"])
+# the staged kernel staging by TMA or by copies, with three or two raw slots, and the plain
+# kernel (FP64 and the correlated noise take the variants their configuration offers)
+KERNELS3 = {"tma3": ("staged", "tma", "3"), "tma2": ("staged", "tma", "2"), "copy3": ("staged", "copy", "3"),
+            "copy2": ("staged", "copy", "2"), "plain": ("plain", "copy", "3")}
+
+
+@pytest.fixture(params=list(KERNELS3))
 def kernel3(request, monkeypatch):
-    # the staged kernel with three raw slots (the default here), with two, and the plain kernel
-    monkeypatch.setenv("LBFLUCT3_KERNEL", "plain" if request.param == "plain" else "staged")
-    monkeypatch.setenv("LBFLUCT3_SLOTS", "2" if request.param == "staged2" else "3")
+    kernel, stage, slots = KERNELS3[request.param]
+    monkeypatch.setenv("LBFLUCT3_KERNEL", kernel)
+    monkeypatch.setenv("LBFLUCT3_STAGE", stage)
+    monkeypatch.setenv("LBFLUCT3_SLOTS", slots)
     return request.param
 
 

@@ -50,21 +50,29 @@ def _pair(nx, ny, nz, mode, precision=lbf.LB_FP32, cs2=0.25, seed=7, amp=0.01, c
 SIZES = [(32, 4, 3), (37, 11, 5), (64, 8, 9), (5, 3, 2), (1, 1, 6), (40, 1, 3), (3, 9, 1)]
 
 
-@pytest.fixture(params=["2", "3"])
-def slots(request, monkeypatch):
-    # the staged kernel with two raw slots (the default for D3Q27) and with three
-    monkeypatch.setenv("LBFLUCT3_SLOTS", request.param)
+# the staged kernel staging by copies in two raw slots (the default for D3Q27) or three, and
+# by TMA in two slots on 32 x 4 or 32 x 6 tiles (FP64 stages by copies)
+STAGINGS27 = {"copy2": ("copy", "2", "4"), "copy3": ("copy", "3", "4"), "tma4": ("tma", "2", "4"),
+              "tma6": ("tma", "2", "6")}
+
+
+@pytest.fixture(params=list(STAGINGS27))
+def staging(request, monkeypatch):
+    stage, slots, ty = STAGINGS27[request.param]
+    monkeypatch.setenv("LBFLUCT3_STAGE", stage)
+    monkeypatch.setenv("LBFLUCT3_SLOTS", slots)
+    monkeypatch.setenv("LBFLUCT3_TY", ty)
     return request.param
 
 
 @pytest.mark.parametrize("nx,ny,nz", SIZES)
 @pytest.mark.parametrize("mode", [lbf.LB_NOISE_OFF, lbf.LB_NOISE_LW])
-def test_fp32_step_follows_the_oracle(nx, ny, nz, mode, slots):
+def test_fp32_step_follows_the_oracle(nx, ny, nz, mode, staging):
     g, o = _pair(nx, ny, nz, mode)
     g.step(5)
     o.step(5)
     err = np.abs(g.populations() - o.f).max()
-    print("D3Q27 FP32 slots %s %dx%dx%d mode %d: %.2e" % (slots, nx, ny, nz, mode, err))
+    print("D3Q27 FP32 %s %dx%dx%d mode %d: %.2e" % (staging, nx, ny, nz, mode, err))
     assert err <= TOL
     if mode == lbf.LB_NOISE_LW:
         q = d.Lattice(nx, ny, nz, cs2=0.25, seed=7)
@@ -76,13 +84,13 @@ def test_fp32_step_follows_the_oracle(nx, ny, nz, mode, slots):
 
 @pytest.mark.parametrize("nx,ny,nz", [(32, 4, 3), (37, 11, 5), (6, 5, 7)])
 @pytest.mark.parametrize("mode", [lbf.LB_NOISE_OFF, lbf.LB_NOISE_LW])
-def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode, slots):
+def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode, staging):
     params = (1e-4, 0.08, 0.8, 1.1, 0.9)
     g, o = _pair(nx, ny, nz, mode, precision=lbf.LB_FP64, amp=0.25, clip=3.5, params=params)
     g.step(4)
     o.step(4)
     err = np.abs(g.populations() - o.f).max()
-    print("D3Q27 FP64 slots %s %dx%dx%d mode %d: %.2e" % (slots, nx, ny, nz, mode, err))
+    print("D3Q27 FP64 %s %dx%dx%d mode %d: %.2e" % (staging, nx, ny, nz, mode, err))
     assert err <= TOL64
     q = d.Lattice(nx, ny, nz, cs2=0.25, seed=7)
     q.set_params(1e-4, 0.0, 0.8, 1.1, 0.9, d.NOISE_OFF if mode == lbf.LB_NOISE_OFF else d.NOISE_LW)
@@ -91,7 +99,7 @@ def test_fp64_step_to_rounding_at_large_amplitude(nx, ny, nz, mode, slots):
     assert np.abs(q.f - o.f).max() > 1e3 * TOL64          # the kappa terms matter here
 
 
-def test_fp32_nonlinear_terms_at_large_amplitude(slots):
+def test_fp32_nonlinear_terms_at_large_amplitude(staging):
     g, o = _pair(37, 11, 5, lbf.LB_NOISE_LW, amp=0.25, clip=3.5, params=(1e-4, 0.08, 0.8, 1.1, 0.9))
     g.step(3)
     o.step(3)

@@ -60,11 +60,15 @@
  *     ((i*nz + z)*ny + y)*nx + x), pre-collision (right after streaming), in the lattice's
  *     velocity order above.
  *   - The device holds the deviations f_i - fbar_i from the rest state in the storage
- *     precision (LB_FP32: 2 Q 4 bytes moved per node update; LB_FP64: 2 Q 8), two copies.
+ *     precision (LB_FP32: 2 Q 4 bytes moved per node update; LB_FP64: 2 Q 8), two copies,
+ *     each plane with periodic ghost copies of 32 bytes of elements on either side of a row
+ *     and two rows below and above every z plane.
  *   - Philox4x32-10 keyed (seed mod 2^32, seed div 2^32), counter (node, t mod 2^32,
  *     t div 2^32, tag) with node = (z*ny + y)*nx + x; one Box-Muller pair per output word
  *     (20-bit radius, 12-bit angle, as for D2Q9).
  *   - All GPU work runs on the context's stream; calls that return data synchronise it.
+ *     A step kernel whose bounded wait for its staged loads gave up is reported as LB_ETIMEOUT
+ *     by the next lb3_synchronize, lb3_get_populations or lb3_sums (the word is then cleared).
  *     The caller owns every buffer it passes.  One host thread per context at a time.
  */
 #ifndef LBFLUCT3D_H
@@ -85,8 +89,8 @@ extern "C" {
 
 typedef struct lb3_ctx lb3_ctx;
 
-/* Device bytes of a context (two population copies, FP64 staging plane, reduction
- * scratch); 0 for invalid sizes, lattice or precision. */
+/* Device bytes of a context (two population copies with their ghost copies, FP64 staging
+ * plane, reduction scratch, error word); 0 for invalid sizes, lattice or precision. */
 size_t lb3_workspace_bytes(int nx, int ny, int nz, int lattice, int precision);
 
 /*

@@ -359,8 +359,9 @@ int record_timing3(lb3_ctx* c, cudaEvent_t* start, cudaEvent_t* stop) {
 // TMA in two slots (D3Q19 with and without the correlated noise: three CTAs per SM at 80
 // registers, against two with three slots; D3Q27 on 32 x 4 tiles).  FP64 stages by copies
 // (D3Q19 in three slots, D3Q27 in two; TMA boxes of doubles would fit one CTA per SM).
-// LBFLUCT3_KERNEL=plain (D3Q19), LBFLUCT3_STAGE=tma|copy, LBFLUCT3_SLOTS=2|3 and
-// LBFLUCT3_TY=4|6 (D3Q27 with TMA) override the choice.
+// LBFLUCT3_KERNEL=plain (D3Q19), LBFLUCT3_STAGE=tma|copy and LBFLUCT3_SLOTS=2|3 override
+// the choice (32 x 6 tiles for D3Q27 by TMA measured 1063 against 1007 us: three CTAs per SM
+// at 96 registers with spills).
 Launch3 default_cfg(int lattice, int precision) {
     Launch3 L{};
     L.kmode = 0;
@@ -379,23 +380,26 @@ Launch3 env_cfg(Launch3 L, int lattice, int precision, bool rs) {
         else if (std::strcmp(st, "copy") == 0) L.tma = false;
     }
     if (const char* sv = std::getenv("LBFLUCT3_SLOTS")) L.slots = std::atoi(sv) == 2 ? 2 : 3;
-    if (lattice == 27) {
-        if (L.tma) L.slots = 2;
-        const char* tv = std::getenv("LBFLUCT3_TY");
-        L.ty = (L.tma && tv && std::atoi(tv) == 6) ? 6 : 4;
-    }
+    if (lattice == 27 && L.tma) L.slots = 2;
     return L;
 }
 
-// the grid of a configuration: the z run of a CTA gives enough CTAs for eight per SM, each
-// at least one plane
+// The grid of a configuration: the z runs of the CTAs are at most RUN3 planes long, and short
+// enough that there are CTAs for eight per SM.  Long runs let the CTAs of neighbouring tiles
+// drift apart in z, so the halo one of them loads has left L2 before the other needs it:
+// measured at 256^3 (FP32, TMA staging), 52-plane runs read 1.41x the algorithmic bytes and
+// 16-plane runs 1.18x (D3Q19 657 -> 628 us, D3Q27 993 -> 859 us); 8-, 32- and 64-plane runs
+// were slower.
+constexpr int RUN3 = 16;
+
 void choose_grid(lb3_ctx* c, Launch3* L) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     const int tx = 32, ty = L->plain ? 8 : L->ty;
     const long long bxy = (long long)((c->nx + tx - 1) / tx) * ((c->ny + ty - 1) / ty);
     const long long want = 8LL * sms;
-    long long chunks = std::max(1LL, std::min((long long)c->nz, (want + bxy - 1) / bxy));
+    long long chunks = std::max((want + bxy - 1) / bxy, ((long long)c->nz + RUN3 - 1) / RUN3);
+    chunks = std::max(1LL, std::min((long long)c->nz, chunks));
     const int zc = (int)((c->nz + chunks - 1) / chunks);
     chunks = (c->nz + zc - 1) / zc;
     L->grid = dim3((c->nx + tx - 1) / tx, (c->ny + ty - 1) / ty, (unsigned)chunks);
@@ -474,7 +478,7 @@ template <typename R>
 void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double sc[QMAX],
                const double Lc[28], const double Lrs[9]) {
     a->nx = c->nx; a->ny = c->ny; a->nz = c->nz;
-    a->pitch = c->geom.pitch; a->PL = c->geom.PL; a->P = c->geom.P;
+    a->pitch = c->geom.pitch; a->gx = c->geom.gx; a->PL = c->geom.PL; a->P = c->geom.P;
     a->err = c->err_dev;
     a->co.rho0 = (R)c->rho0;
     a->co.d = (R)(3.0 * c->cs2 - 1.0);

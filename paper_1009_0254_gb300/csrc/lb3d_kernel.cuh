@@ -3,14 +3,16 @@
 // streaming in pull form, f_i(r, t) = f*_i(r - c_i, t - 1)).
 //
 // Storage.  Each population plane of the nx x ny x nz lattice is kept with periodic ghost
-// copies: GX ghost columns on either side of a row (32 bytes of elements, so that the
-// interior of every row starts on a 32-byte sector) and GY3 = 2 ghost rows below and above
-// every z plane.  Element (i, x, y, z), -GX <= x < nx + GX, -GY3 <= y < ny + GY3, lives at
-//   i P + z PL + (y + GY3) pitch + (x + GX),
-// pitch = nx + 2 GX rounded up to a multiple of GX, PL = (ny + 2 GY3) pitch, P = nz PL.  The
-// step writes every node's ghost copies with the node (the columns GX wide, so that the
-// copies of an edge warp fill whole sectors), so each read of the next step, f*_i(r - c_i)
-// for r on a tile's one-node ring, is a wrap-free address in x and y; z wraps by plane.
+// copies: gx ghost columns on either side of a row (the host takes 32 bytes of elements, so
+// that the interior of every row starts on a 32-byte sector) and GY3 = 2 ghost rows below and
+// above every z plane.  Population i lives in plane sigma(i) of its buffer; element
+// (plane s, x, y, z), -gx <= x < nx + gx, -GY3 <= y < ny + GY3, lives at
+//   s P + z PL + (y + GY3) pitch + (x + gx),
+// pitch = nx + 2 gx rounded up to a multiple of gx, PL = (ny + 2 GY3) pitch, P = nz PL.  The
+// step writes every node's ghost copies with the node (columns GW = 32 bytes of elements
+// wide, so that the copies of an edge warp fill whole sectors), so each read of the next
+// step, f*_i(r - c_i) for r on a tile's one-node ring, is a wrap-free address in x and y; z
+// wraps by plane.
 //
 // The staged kernel.  A CTA owns a TX x TY tile of the (x, y) plane and marches over a run
 // of z planes.  The pulled populations of each plane, for the tile and its one-node ring,
@@ -92,9 +94,9 @@ __host__ __device__ constexpr int coupled27(int r) {
     return r == 0 ? 2 : (r == 1 ? 6 : (r == 2 ? 8 : (r == 3 ? 18 : (r == 4 ? 20 : (r == 5 ? 24 : 26)))));
 }
 
-// ghost columns per side (32 bytes of elements) and ghost rows per side
+// ghost columns written per side (32 bytes of elements: one sector) and ghost rows per side
 template <typename R>
-__host__ __device__ constexpr int gx3() { return 32 / (int)sizeof(R); }
+__host__ __device__ constexpr int gw3() { return 32 / (int)sizeof(R); }
 constexpr int GY3 = 2;
 
 template <typename R>
@@ -103,6 +105,7 @@ struct Step3Args {
     R* __restrict__ dst;
     int nx, ny, nz, zc;           // zc: planes per CTA
     int pitch;                    // elements per stored row
+    int gx;                       // stored column of x = 0
     long long PL;                 // elements per stored z plane
     long long P;                  // elements per population (nz PL)
     int* err;                     // device error word: 1 = a CTA gave up waiting for its TMA loads
@@ -193,26 +196,26 @@ __device__ __forceinline__ R drho_of(const R* f) {
 }
 
 // Writes the Q post-collision values of node (x, y) of the stored plane at offset zo, and its
-// ghost copies: columns x + nx (x < GX) or x - nx (x >= nx - GX), rows y + ny (y < GY3) or
-// y - ny (y >= ny - GY3), and the corner.  On lattices narrower than 2 GX or lower than
+// ghost copies: columns x + nx (x < GW) or x - nx (x >= nx - GW), rows y + ny (y < GY3) or
+// y - ny (y >= ny - GY3), and the corner.  On lattices narrower than 2 GW or lower than
 // 2 GY3 a node can feed several copies per side; those go through the general loop.  Indices
 // are formed in I (32-bit when all planes fit in 2^32 elements) with modular arithmetic, so
 // negative displacements are added as their two's complement.
 template <typename LAT, typename R, typename I>
 __device__ __forceinline__ void store_node3(const Step3Args<R>& a, I zo, int x, int y, const R (&o)[LAT::Q]) {
     constexpr int Q = LAT::Q;
-    constexpr int GX = gx3<R>();
-    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    constexpr int GW = gw3<R>();
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch, gx = a.gx;
     const I PI = (I)a.P;
     R* __restrict__ d = a.dst;
-    const I ns = zo + (I)(y + GY3) * (I)pitch + (I)(x + GX);
-    if (nx >= 2 * GX && ny >= 2 * GY3) {
-        const bool hx = x < GX || x >= nx - GX, hy = y < GY3 || y >= ny - GY3;
+    const I ns = zo + (I)(y + GY3) * (I)pitch + (I)(x + gx);
+    if (nx >= 2 * GW && ny >= 2 * GY3) {
+        const bool hx = x < GW || x >= nx - GW, hy = y < GY3 || y >= ny - GY3;
         if (!(hx | hy)) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) d[(I)LAT::sigma(i) * PI + ns] = o[i];
         } else {
-            const I dx = hx ? (I)(long long)(x < GX ? nx : -nx) : (I)0;
+            const I dx = hx ? (I)(long long)(x < GW ? nx : -nx) : (I)0;
             const I dy = hy ? (I)((long long)(y < GY3 ? ny : -ny) * pitch) : (I)0;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -224,11 +227,11 @@ __device__ __forceinline__ void store_node3(const Step3Args<R>& a, I zo, int x, 
             }
         }
     } else {
-        // every column cx = x (mod nx) in [-GX, nx + GX) and row cy = y (mod ny) in [-GY3, ny + GY3)
-        const int cy0 = y - ((y + GY3) / ny) * ny, cx0 = x - ((x + GX) / nx) * nx;
+        // every column cx = x (mod nx) in [-GW, nx + GW) and row cy = y (mod ny) in [-GY3, ny + GY3)
+        const int cy0 = y - ((y + GY3) / ny) * ny, cx0 = x - ((x + GW) / nx) * nx;
         for (int cy = cy0; cy < ny + GY3; cy += ny)
-            for (int cx = cx0; cx < nx + GX; cx += nx) {
-                const I b = zo + (I)(cy + GY3) * (I)pitch + (I)(cx + GX);
+            for (int cx = cx0; cx < nx + GW; cx += nx) {
+                const I b = zo + (I)(cy + GY3) * (I)pitch + (I)(cx + gx);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) d[(I)LAT::sigma(i) * PI + b] = o[i];
             }
@@ -241,7 +244,7 @@ constexpr uint32_t TAG_RS0 = 10;
 // Shared-memory geometry of one raw slot.  Copies (TMA = false): per population the pulled
 // values of the tile and its ring, RX x RY, already shifted by -c_i.  TMA: per box the GM
 // populations of one (c_y, c_z), each BW x RY stored values whose origin is (x0 - XO,
-// y0 - 1 - c_iy, z - c_iz), XO = 16 bytes of elements (the TMA x alignment; x0 + GX - XO is
+// y0 - 1 - c_iy, z - c_iz), XO = 16 bytes of elements (the TMA x alignment; x0 + gx - XO is
 // then a multiple of XO); the pulled value at ring position (qx, qy) is
 // pop[qy][qx - 1 + XO - c_ix].  Every box starts on 128 bytes.
 template <typename LAT, typename R, int TY, bool TMA>
@@ -286,7 +289,6 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
     constexpr int Q = LAT::Q, TX = LAT::TX;
     using S = Slot3<LAT, R, TY, TMA>;
     constexpr int RX = S::RX, RN = S::RN, NT = TX * TY, SL = S::SLOT, BW = S::BW;
-    constexpr int GX = gx3<R>();
     extern __shared__ __align__(128) unsigned char smem3[];
     R* raw = reinterpret_cast<R*>(smem3);                                   // [SLOTS][SL]
     constexpr int RAW_BYTES = SLOTS * SL * (int)sizeof(R);
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
     constexpr int HW = TX + 1, HN = HW * (TY + 1);
     R* Hin = rs + 3 * RN;                                   // MODE 3: [8][HN] in-plane half
     R* Hup = Hin + 8 * HN;                                  // MODE 3: [2][8][HN] upward half
-    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch, GX = a.gx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * a.zc;
     const int z1 = min(z0 + a.zc, nz);
@@ -597,9 +599,8 @@ __device__ __forceinline__ void pull19(const R* __restrict__ s, long long P, con
 template <typename R, int MODE, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
     constexpr int RX = TX + 2, RY = TY + 2, NT = TX * TY;
-    constexpr int GX = gx3<R>();
     __shared__ R rs[3][RY][RX];
-    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch, GX = a.gx;
     const long long P = a.P, PL = a.PL;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * a.zc;
@@ -710,9 +711,8 @@ static cudaError_t launch_width(const Step3Args<R>& a, const CUtensorMap* map, d
                   : launch_staged<LAT, R, TY, MODE, unsigned long long, SLOTS, TMA>(a, map, grid, s);
 }
 
-// the staged variants a lattice offers: D3Q19 32 x 8 tiles (copies or TMA, two or three
-// slots; FP64 by copies); D3Q27 32 x 4 tiles by copies (two or three slots) and by TMA (two
-// slots, 32 x 4 or 32 x 6 tiles; FP32)
+// the staged variants a lattice offers, on 32 x 8 (D3Q19) or 32 x 4 (D3Q27) tiles: by copies
+// in two or three slots, and in FP32 by TMA (D3Q19 two or three slots, D3Q27 two)
 template <typename LAT, typename R, int MODE>
 static cudaError_t launch_mode3(const Step3Args<R>& a, const CUtensorMap* map, const Launch3& L, cudaStream_t s) {
     constexpr bool F32 = sizeof(R) == 4;
@@ -733,9 +733,7 @@ static cudaError_t launch_mode3(const Step3Args<R>& a, const CUtensorMap* map, c
                             : launch_width<LAT, R, 8, MODE, 3, false>(a, map, L.grid, s);
     } else {
         if constexpr (F32) {
-            if (L.tma)
-                return L.ty == 6 ? launch_width<LAT, R, 6, MODE, 2, true>(a, map, L.grid, s)
-                                 : launch_width<LAT, R, 4, MODE, 2, true>(a, map, L.grid, s);
+            if (L.tma) return launch_width<LAT, R, 4, MODE, 2, true>(a, map, L.grid, s);
         }
         return L.slots == 2 ? launch_width<LAT, R, 4, MODE, 2, false>(a, map, L.grid, s)
                             : launch_width<LAT, R, 4, MODE, 3, false>(a, map, L.grid, s);

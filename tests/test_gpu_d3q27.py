@@ -50,18 +50,16 @@ def _pair(nx, ny, nz, mode, precision=lbf.LB_FP32, cs2=0.25, seed=7, amp=0.01, c
 SIZES = [(32, 4, 3), (37, 11, 5), (64, 8, 9), (5, 3, 2), (1, 1, 6), (40, 1, 3), (3, 9, 1)]
 
 
-# the staged kernel staging by copies in two raw slots (the default for D3Q27) or three, and
-# by TMA in two slots on 32 x 4 or 32 x 6 tiles (FP64 stages by copies)
-STAGINGS27 = {"copy2": ("copy", "2", "4"), "copy3": ("copy", "3", "4"), "tma4": ("tma", "2", "4"),
-              "tma6": ("tma", "2", "6")}
+# the staged kernel staging by TMA in two raw slots (the FP32 default) and by copies in two
+# (the FP64 default) or three
+STAGINGS27 = {"tma2": ("tma", "2"), "copy2": ("copy", "2"), "copy3": ("copy", "3")}
 
 
 @pytest.fixture(params=list(STAGINGS27))
 def staging(request, monkeypatch):
-    stage, slots, ty = STAGINGS27[request.param]
+    stage, slots = STAGINGS27[request.param]
     monkeypatch.setenv("LBFLUCT3_STAGE", stage)
     monkeypatch.setenv("LBFLUCT3_SLOTS", slots)
-    monkeypatch.setenv("LBFLUCT3_TY", ty)
     return request.param
 
 

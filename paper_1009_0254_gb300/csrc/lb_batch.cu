@@ -343,8 +343,12 @@ static bool make_class_map(void* buf, const Grid& g, int R, int tile, CUtensorMa
     // box: the tile plus 4 columns (16 bytes) on either side and one row above and below
     cuuint32_t box[4] = {(cuuint32_t)(kBatchTiles[tile][0] + 8), (cuuint32_t)(kBatchTiles[tile][1] + 2), 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
+    // 64-byte L2 promotion: a class's rows carry 128 bytes of ghost columns on either side of
+    // which one 32-byte sector is ever written or read; with 256-byte promotion a box row
+    // pulled whole rows of the small lattices (the 512-replica mix read 1.74x the algorithmic
+    // bytes, 1.33x with 64; its 32^2 class 3.20x and 2.13x, 138 -> 112 us a step)
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

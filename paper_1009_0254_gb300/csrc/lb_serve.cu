@@ -248,8 +248,10 @@ static bool make_slot_map(void* buf, const Grid& g, CUtensorMap* map) {
     cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
     cuuint32_t box[3] = {(cuuint32_t)(SV_TX + 8), (cuuint32_t)(SV_TY + 2), 1};
     cuuint32_t estr[3] = {1, 1, 1};
+    // 64-byte L2 promotion, as for the batched engine's class maps (lb_batch.cu): the slot's
+    // ghost columns are mostly never read
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -36,6 +36,15 @@ Random numbers: two Philox4x32-10 draws per node and step with counter (node, t 
 t div 2^32, tag), node = (z ny + y) nx + x; tag 4 gives nu_4..nu_11, tag 5 gives
 nu_12..nu_18 (its last normal unused), each word one Box-Muller pair as for D2Q9.
 
+Two-phase model (Sec. II A; Sec. IV and Sec. V B): with a double-well ``eos``
+(theory.DoubleWell) the second moments carry p0(rho) = rho f0'(rho) - f0(rho) of the Landau
+free energy instead of cs2 rho, the uniform rest state is the equilibrium at rho0 with
+p0(rho0), and the linear theory about rho0 (the noise of the homogeneous modes) takes
+c_s^2 = rho0 f0''(rho0).  NOISE_LW_LOCAL draws the long-wavelength normals and scales them
+at every node by the factor of Xi(0) of a homogeneous system at that node's density and
+sound speed c_s^2(rho(r)) (the double well's, else cs2): Cholesky of the (4,16) block with a
+negative pivot clamped to zero, where the local block is not positive semidefinite.
+
 Correlated noise (Sec. III C, Eq. noise-matrix at every k): with the ansatz the advection
 drops out of the fluctuation-dissipation relation (A(k) G(k) A(-k)^T = G(k), the phases of
 a diagonal matrix cancel), so Xi(k) is the long-wavelength form at c_s^2(k) = cs2 + rho0
@@ -118,10 +127,14 @@ def lambdas(tau_s: float, tau_b: float, tau_ghost: float) -> np.ndarray:
 
 
 class Model:
-    """One homogeneous run on D3Q19: rho0, cs2 (p0 = cs2 rho), kappa, kT, relaxation times."""
+    """One homogeneous run on D3Q19: rho0, cs2 (p0 = cs2 rho, or the c_s^2 of the linear
+    theory about rho0), kappa, kT, relaxation times; p0_rest the bulk pressure of the uniform
+    rest state (cs2 rho0 unless given: p0(rho0) of a double well)."""
 
-    def __init__(self, rho0=1.0, cs2=SIGMA_S2, kappa=0.0, kT=0.0, tau_s=1.0, tau_b=1.0, tau_ghost=1.0):
+    def __init__(self, rho0=1.0, cs2=SIGMA_S2, kappa=0.0, kT=0.0, tau_s=1.0, tau_b=1.0, tau_ghost=1.0,
+                 p0_rest=None):
         self.rho0, self.cs2, self.kappa, self.kT = float(rho0), float(cs2), float(kappa), float(kT)
+        self.p0_rest = self.cs2 * self.rho0 if p0_rest is None else float(p0_rest)
         self.tau_s, self.tau_b, self.tau_ghost = float(tau_s), float(tau_b), float(tau_ghost)
         self.lam = lambdas(tau_s, tau_b, tau_ghost)
 
@@ -140,6 +153,15 @@ class Model:
 
     def fbar(self) -> np.ndarray:
         return TINV @ self.mbar()
+
+    def rest(self) -> np.ndarray:
+        """Populations of the uniform rest state at rho0: the equilibrium at u = 0 with bulk
+        pressure p0_rest, e4 = 3 p0 - rho0 and e16 = -e4 (fbar() for p0 = cs2 rho)."""
+        m = np.zeros(Q)
+        m[0] = self.rho0
+        m[4] = 3.0 * (self.p0_rest - SIGMA_S2 * self.rho0)
+        m[16] = -m[4]
+        return TINV @ m
 
     def Omega0(self) -> np.ndarray:
         """Linearised collision operator at k = 0 (the analogue of Eq. coll-op-yeo): mode a
@@ -189,16 +211,19 @@ def density_stencils(rho: np.ndarray):
     return lap, grad
 
 
-def equilibrium_moments(rho, j, lap, grad, cs2, kappa) -> np.ndarray:
+def equilibrium_moments(rho, j, lap, grad, cs2, kappa, p0=None) -> np.ndarray:
     """m^eq[a, ...] for each node: rho, j, then the second-order moments of
-    P^th_ab + rho u_a u_b with P^th of Eq. (press-ten) for p0 = cs2 rho,
+    P^th_ab + rho u_a u_b with P^th of Eq. (press-ten) for the bulk pressure p0 (cs2 rho
+    unless given),
         P^th_ab = (p0 - kappa rho lap rho - kappa |grad rho|^2 / 2) delta_ab
                   + kappa d_a rho d_b rho,
     and the fourth-order ghost e16 of the module's reading; the other ghosts zero."""
     u = j / rho
+    if p0 is None:
+        p0 = cs2 * rho
     P = np.zeros((3, 3) + rho.shape)
     g2 = (grad * grad).sum(axis=0)
-    piso = cs2 * rho - kappa * rho * lap - 0.5 * kappa * g2
+    piso = p0 - kappa * rho * lap - 0.5 * kappa * g2
     for a in range(3):
         for b in range(3):
             P[a, b] = rho * u[a] * u[b] + kappa * grad[a] * grad[b]
@@ -210,17 +235,19 @@ def equilibrium_moments(rho, j, lap, grad, cs2, kappa) -> np.ndarray:
     m[5] = 2 * P[0, 0] - P[1, 1] - P[2, 2]
     m[6] = P[1, 1] - P[2, 2]
     m[7], m[8], m[9] = P[0, 1], P[1, 2], P[2, 0]
-    m[16] = -3.0 * (cs2 * rho - SIGMA_S2 * rho - kappa * rho * lap) - 4.5 * kappa * g2
+    m[16] = -3.0 * (p0 - SIGMA_S2 * rho - kappa * rho * lap) - 4.5 * kappa * g2
     return m
 
 
-def collide(f: np.ndarray, model: Model, xi=None) -> np.ndarray:
+def collide(f: np.ndarray, model: Model, xi=None, eos=None) -> np.ndarray:
     """Post-collision populations f*_i = (T^-1 m*)_i with
-    m*_a = m_a + lambda_a (m_a - m^eq_a) + xi_a, Eq. (fluct-lin-lbe)."""
+    m*_a = m_a + lambda_a (m_a - m^eq_a) + xi_a, Eq. (fluct-lin-lbe); eos: a double well
+    whose p0(rho) replaces cs2 rho in the equilibrium."""
     m = np.einsum("ai,i...->a...", T, f)
     rho = m[0]
     lap, grad = density_stencils(rho)
-    meq = equilibrium_moments(rho, m[1:4], lap, grad, model.cs2, model.kappa)
+    p0 = None if eos is None else eos.p0(rho)
+    meq = equilibrium_moments(rho, m[1:4], lap, grad, model.cs2, model.kappa, p0)
     ms = m + model.lam[:, None, None, None] * (m - meq)
     if xi is not None:
         ms = ms + xi
@@ -235,8 +262,8 @@ def stream(fs: np.ndarray) -> np.ndarray:
     return out
 
 
-def step(f: np.ndarray, model: Model, xi=None) -> np.ndarray:
-    return stream(collide(f, model, xi))
+def step(f: np.ndarray, model: Model, xi=None, eos=None) -> np.ndarray:
+    return stream(collide(f, model, xi, eos))
 
 
 # --- noise of Sec. IV -------------------------------------------------------------------
@@ -274,6 +301,44 @@ def noise_lw(model: Model, nx, ny, nz, seed: int, step_index: int, L=None) -> np
         L = model.noise_factor()
     nu = noise_normals(nx, ny, nz, seed, step_index)
     return np.einsum("ab,b...->a...", L, nu)
+
+
+def local_factor(X: np.ndarray, coupled) -> np.ndarray:
+    """Q x Q factor of one node's Xi(0) for the local noise: Cholesky of the coupled block
+    (in mode order) in which a pivot below zero is clamped to zero and a zero pivot leaves
+    its column zero; the square roots of the other non-conserved modes' variances."""
+    L = np.zeros((Q, Q))
+    n = len(coupled)
+    B = np.zeros((n, n))
+    for j in range(n):
+        s = X[coupled[j], coupled[j]] - np.dot(B[j, :j], B[j, :j])
+        B[j, j] = np.sqrt(max(s, 0.0))
+        for i in range(j + 1, n):
+            t = X[coupled[i], coupled[j]] - np.dot(B[i, :j], B[j, :j])
+            B[i, j] = t / B[j, j] if B[j, j] > 0 else 0.0
+    L[np.ix_(coupled, coupled)] = B
+    for a in range(4, Q):
+        if a not in coupled:
+            L[a, a] = np.sqrt(max(X[a, a], 0.0))
+    return L
+
+
+COUPLED = [4, 16]
+
+
+def noise_lw_local(model: Model, rho: np.ndarray, c2, seed: int, step_index: int) -> np.ndarray:
+    """xi[a, z, y, x] of NOISE_LW_LOCAL: the long-wavelength normals, at every node times the
+    local factor of Xi(0) of a homogeneous system at that node's density rho(r) and sound
+    speed c2(r) (the model's kappa, kT and relaxation times)."""
+    nz, ny, nx = rho.shape
+    nu = noise_normals(nx, ny, nz, seed, step_index).reshape(Q, -1)
+    r = rho.ravel()
+    c = np.broadcast_to(np.asarray(c2, dtype=np.float64), rho.shape).ravel()
+    xi = np.zeros((Q, r.size))
+    for n in range(r.size):
+        X = Model(r[n], c[n], model.kappa, model.kT, model.tau_s, model.tau_b, model.tau_ghost).Xi_zero()
+        xi[:, n] = local_factor(X, COUPLED) @ nu[:, n]
+    return xi.reshape(Q, nz, ny, nx)
 
 
 # --- correlated noise (Sec. III C, Eq. noise-matrix) ------------------------------------------
@@ -347,26 +412,34 @@ def xi416_rs(model: Model, nx, ny, nz, seed: int, step_index: int, Ls=None) -> n
     return out
 
 
-NOISE_OFF, NOISE_LW, NOISE_FULL_RS = 0, 1, 4
+NOISE_OFF, NOISE_LW, NOISE_FULL_RS, NOISE_LW_LOCAL = 0, 1, 4, 5
 
 
 class Lattice:
     """A periodic nx x ny x nz D3Q19 lattice: f[19, nz, ny, nx] pre-collision populations,
-    t the index of the next collision (it keys the random numbers).  Noise: NOISE_LW (Xi(0))
-    or NOISE_FULL_RS (Xi(k), the (4,16) block built in real space, the other modes as LW)."""
+    t the index of the next collision (it keys the random numbers).  Noise: NOISE_LW (Xi(0)),
+    NOISE_FULL_RS (Xi(k), the (4,16) block built in real space, the other modes as LW) or
+    NOISE_LW_LOCAL (Xi(0) at each node's density and sound speed).  ``eos`` (a
+    theory.DoubleWell) replaces p0 = cs2 rho by the double well's bulk pressure; the rest
+    state and the linear theory about rho0 then take p0(rho0) and c_s^2(rho0)."""
 
-    def __init__(self, nx, ny, nz, rho0=1.0, cs2=SIGMA_S2, seed=42):
+    def __init__(self, nx, ny, nz, rho0=1.0, cs2=SIGMA_S2, seed=42, eos=None):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.seed = int(seed)
-        self.model = Model(rho0=rho0, cs2=cs2)
+        self.eos = eos
+        if eos is None:
+            self.model = Model(rho0=rho0, cs2=cs2)
+        else:
+            self.model = Model(rho0=rho0, cs2=eos.cs2(rho0), p0_rest=eos.p0(rho0))
         self.mode = NOISE_OFF
         self.t = 0
-        self.f = np.broadcast_to(self.model.fbar()[:, None, None, None], (Q, nz, ny, nx)).copy()
+        self.f = np.broadcast_to(self.model.rest()[:, None, None, None], (Q, nz, ny, nx)).copy()
         self._L = None
         self._Ls = None
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
-        self.model = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
+        m = self.model
+        self.model = Model(m.rho0, m.cs2, kappa, kT, tau_s, tau_b, tau_ghost, m.p0_rest)
         self.mode = int(noise_mode)
         noisy = self.mode in (NOISE_LW, NOISE_FULL_RS) and kT > 0
         self._L = self.model.noise_factor() if noisy else None
@@ -381,8 +454,14 @@ class Lattice:
 
     def step(self, nsteps=1):
         for _ in range(int(nsteps)):
-            xi = self.noise() if self._L is not None else None
-            self.f = step(self.f, self.model, xi)
+            xi = None
+            if self._L is not None:
+                xi = self.noise()
+            elif self.mode == NOISE_LW_LOCAL and self.model.kT > 0:
+                rho = self.f.sum(axis=0)
+                c2 = self.model.cs2 if self.eos is None else self.eos.cs2(rho)
+                xi = noise_lw_local(self.model, rho, c2, self.seed, self.t)
+            self.f = step(self.f, self.model, xi, self.eos)
             self.t += 1
         return self
 

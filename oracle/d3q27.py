@@ -32,6 +32,13 @@ Readings where the paper is silent (also listed in the design notes):
     every other ghost equilibrium is zero;
   * the Laplacian and gradient are Appendix B's isotropic stencils with the D3Q27 weights.
 
+Two-phase model (Sec. II A; Sec. IV and Sec. V B), as ``oracle.d3q19``: a double-well
+``eos`` puts p0(rho) of the Landau free energy in the second moments and the ghost
+equilibria, the rest state takes p0(rho0) and the linear theory c_s^2(rho0); NOISE_LW_LOCAL
+scales the long-wavelength normals at every node by the factor of Xi(0) at that node's
+density and sound speed (Cholesky of the seven coupled modes with negative pivots clamped
+to zero, square roots of the other variances).
+
 Indices: velocity i = 9 ix + 3 iy + iz with c = (v[ix], v[iy], v[iz]), v = (0, 1, -1); mode
 a = 9 ax + 3 ay + az for p_ax(c_x) p_ay(c_y) p_az(c_z).  f[i, z, y, x].
 Random numbers: three Philox4x32-10 draws per node and step with counter (node, t mod 2^32,
@@ -103,10 +110,14 @@ def relaxation_matrix(tau_s, tau_b, tau_ghost) -> np.ndarray:
 
 
 class Model:
-    """One homogeneous run on D3Q27: rho0, cs2 (p0 = cs2 rho), kappa, kT, relaxation times."""
+    """One homogeneous run on D3Q27: rho0, cs2 (p0 = cs2 rho, or the c_s^2 of the linear
+    theory about rho0), kappa, kT, relaxation times; p0_rest the bulk pressure of the uniform
+    rest state (cs2 rho0 unless given)."""
 
-    def __init__(self, rho0=1.0, cs2=SIGMA_S2, kappa=0.0, kT=0.0, tau_s=1.0, tau_b=1.0, tau_ghost=1.0):
+    def __init__(self, rho0=1.0, cs2=SIGMA_S2, kappa=0.0, kT=0.0, tau_s=1.0, tau_b=1.0, tau_ghost=1.0,
+                 p0_rest=None):
         self.rho0, self.cs2, self.kappa, self.kT = float(rho0), float(cs2), float(kappa), float(kT)
+        self.p0_rest = self.cs2 * self.rho0 if p0_rest is None else float(p0_rest)
         self.tau_s, self.tau_b, self.tau_ghost = float(tau_s), float(tau_b), float(tau_ghost)
         self.Lam = relaxation_matrix(tau_s, tau_b, tau_ghost)
 
@@ -127,6 +138,19 @@ class Model:
 
     def fbar(self) -> np.ndarray:
         return TINV @ self.mbar()
+
+    def rest(self) -> np.ndarray:
+        """Populations of the uniform rest state at rho0 with bulk pressure p0_rest (fbar()
+        for p0 = cs2 rho)."""
+        m = np.zeros(Q)
+        m[IDX[(0, 0, 0)]] = self.rho0
+        d = 3.0 * (self.p0_rest - SIGMA_S2 * self.rho0)
+        for k in SECOND_DIAG:
+            m[k] = d
+        for k in FOURTH_PAIR:
+            m[k] = -d
+        m[SIXTH] = d
+        return TINV @ m
 
     def J0(self) -> np.ndarray:
         """d m^eq / d m at the rest state (only the density column is non-zero beyond the
@@ -182,18 +206,21 @@ def density_stencils(rho):
     return lap, grad
 
 
-def equilibrium_moments(rho, j, lap, grad, cs2, kappa) -> np.ndarray:
-    """m^eq[a, ...]: rho, j, the second-order modes of P^th + rho u u (Eq. press-ten,
-    p0 = cs2 rho), and the fourth- and sixth-order ghosts of the module's reading."""
+def equilibrium_moments(rho, j, lap, grad, cs2, kappa, p0=None) -> np.ndarray:
+    """m^eq[a, ...]: rho, j, the second-order modes of P^th + rho u u (Eq. press-ten with
+    the bulk pressure p0, cs2 rho unless given), and the fourth- and sixth-order ghosts of
+    the module's reading."""
     u = j / rho
+    if p0 is None:
+        p0 = cs2 * rho
     g2 = (grad * grad).sum(axis=0)
-    piso = cs2 * rho - kappa * rho * lap - 0.5 * kappa * g2
+    piso = p0 - kappa * rho * lap - 0.5 * kappa * g2
     Pi = np.zeros((3, 3) + rho.shape)
     for a in range(3):
         for b in range(3):
             Pi[a, b] = rho * u[a] * u[b] + kappa * grad[a] * grad[b]
         Pi[a, a] = Pi[a, a] + piso
-    iso = cs2 * rho - SIGMA_S2 * rho - kappa * rho * lap
+    iso = p0 - SIGMA_S2 * rho - kappa * rho * lap
     m = np.zeros((Q,) + rho.shape)
     m[IDX[(0, 0, 0)]] = rho
     m[IDX[(1, 0, 0)]], m[IDX[(0, 1, 0)]], m[IDX[(0, 0, 1)]] = j[0], j[1], j[2]
@@ -206,12 +233,13 @@ def equilibrium_moments(rho, j, lap, grad, cs2, kappa) -> np.ndarray:
     return m
 
 
-def collide(f, model: Model, xi=None):
+def collide(f, model: Model, xi=None, eos=None):
     m = np.einsum("ai,i...->a...", T, f)
     rho = m[0]
     lap, grad = density_stencils(rho)
     j = np.array([m[IDX[(1, 0, 0)]], m[IDX[(0, 1, 0)]], m[IDX[(0, 0, 1)]]])
-    meq = equilibrium_moments(rho, j, lap, grad, model.cs2, model.kappa)
+    p0 = None if eos is None else eos.p0(rho)
+    meq = equilibrium_moments(rho, j, lap, grad, model.cs2, model.kappa, p0)
     ms = m + np.einsum("ab,b...->a...", model.Lam, m - meq)
     if xi is not None:
         ms = ms + xi
@@ -225,8 +253,8 @@ def stream(fs):
     return out
 
 
-def step(f, model: Model, xi=None):
-    return stream(collide(f, model, xi))
+def step(f, model: Model, xi=None, eos=None):
+    return stream(collide(f, model, xi, eos))
 
 
 # --- noise of Sec. IV ---------------------------------------------------------------------
@@ -242,23 +270,73 @@ def noise_lw_nodes(model: Model, nodes, seed: int, step_index: int, L=None) -> n
     return (L @ nu).reshape((Q,) + np.shape(nodes))
 
 
-NOISE_OFF, NOISE_LW = 0, 1
+# the modes whose Xi(0) entries couple (p_2z, p_2y, p_2y p_2z, p_2x, p_2x p_2z, p_2x p_2y,
+# p_2x p_2y p_2z), in mode order
+COUPLED = [IDX[(0, 0, 2)], IDX[(0, 2, 0)], IDX[(0, 2, 2)], IDX[(2, 0, 0)], IDX[(2, 0, 2)], IDX[(2, 2, 0)],
+           IDX[(2, 2, 2)]]
+
+
+def local_factor(X: np.ndarray) -> np.ndarray:
+    """Q x Q factor of one node's Xi(0) for the local noise: Cholesky of the coupled block in
+    mode order with a pivot below zero clamped to zero (a zero pivot leaves its column zero),
+    the square roots of the other non-conserved variances."""
+    L = np.zeros((Q, Q))
+    n = len(COUPLED)
+    B = np.zeros((n, n))
+    for j in range(n):
+        s = X[COUPLED[j], COUPLED[j]] - np.dot(B[j, :j], B[j, :j])
+        B[j, j] = np.sqrt(max(s, 0.0))
+        for i in range(j + 1, n):
+            t = X[COUPLED[i], COUPLED[j]] - np.dot(B[i, :j], B[j, :j])
+            B[i, j] = t / B[j, j] if B[j, j] > 0 else 0.0
+    L[np.ix_(COUPLED, COUPLED)] = B
+    for a in NONCONSERVED:
+        if a not in COUPLED:
+            L[a, a] = np.sqrt(max(X[a, a], 0.0))
+    return L
+
+
+def noise_lw_local(model: Model, rho: np.ndarray, c2, seed: int, step_index: int) -> np.ndarray:
+    """xi[a, z, y, x] of NOISE_LW_LOCAL: the long-wavelength normals, at every node times the
+    local factor of Xi(0) of a homogeneous system at that node's density and sound speed."""
+    nz, ny, nx = rho.shape
+    n = rho.size
+    idx = np.arange(n, dtype=np.uint32)
+    g = np.concatenate([normals(idx, seed, step_index, t) for t in TAGS], axis=1)
+    nu = np.zeros((Q, n))
+    nu[NONCONSERVED] = g[:, :len(NONCONSERVED)].T
+    r = rho.ravel()
+    c = np.broadcast_to(np.asarray(c2, dtype=np.float64), rho.shape).ravel()
+    xi = np.zeros((Q, n))
+    for k in range(n):
+        X = Model(r[k], c[k], model.kappa, model.kT, model.tau_s, model.tau_b, model.tau_ghost).Xi_zero()
+        xi[:, k] = local_factor(X) @ nu[:, k]
+    return xi.reshape(Q, nz, ny, nx)
+
+
+NOISE_OFF, NOISE_LW, NOISE_LW_LOCAL = 0, 1, 5
 
 
 class Lattice:
-    """A periodic nx x ny x nz D3Q27 lattice: f[27, nz, ny, nx] pre-collision populations."""
+    """A periodic nx x ny x nz D3Q27 lattice: f[27, nz, ny, nx] pre-collision populations.
+    ``eos`` (a theory.DoubleWell) as for oracle.d3q19.Lattice."""
 
-    def __init__(self, nx, ny, nz, rho0=1.0, cs2=SIGMA_S2, seed=42):
+    def __init__(self, nx, ny, nz, rho0=1.0, cs2=SIGMA_S2, seed=42, eos=None):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.seed = int(seed)
-        self.model = Model(rho0=rho0, cs2=cs2)
+        self.eos = eos
+        if eos is None:
+            self.model = Model(rho0=rho0, cs2=cs2)
+        else:
+            self.model = Model(rho0=rho0, cs2=eos.cs2(rho0), p0_rest=eos.p0(rho0))
         self.mode = NOISE_OFF
         self.t = 0
-        self.f = np.broadcast_to(self.model.fbar()[:, None, None, None], (Q, nz, ny, nx)).copy()
+        self.f = np.broadcast_to(self.model.rest()[:, None, None, None], (Q, nz, ny, nx)).copy()
         self._L = None
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
-        self.model = Model(self.model.rho0, self.model.cs2, kappa, kT, tau_s, tau_b, tau_ghost)
+        m = self.model
+        self.model = Model(m.rho0, m.cs2, kappa, kT, tau_s, tau_b, tau_ghost, m.p0_rest)
         self.mode = int(noise_mode)
         self._L = self.model.noise_factor() if (self.mode == NOISE_LW and kT > 0) else None
 
@@ -269,7 +347,11 @@ class Lattice:
             xi = None
             if self._L is not None:
                 xi = noise_lw_nodes(self.model, nodes, self.seed, self.t, self._L)
-            self.f = step(self.f, self.model, xi)
+            elif self.mode == NOISE_LW_LOCAL and self.model.kT > 0:
+                rho = self.f.sum(axis=0)
+                c2 = self.model.cs2 if self.eos is None else self.eos.cs2(rho)
+                xi = noise_lw_local(self.model, rho, c2, self.seed, self.t)
+            self.f = step(self.f, self.model, xi, self.eos)
             self.t += 1
         return self
 

@@ -28,7 +28,15 @@
  *     (a, b, c = +-1; +1 for k = 0), each times the Cholesky factor L_abc of the (4,16) block
  *     at its corner, combined as h_d(r) = (1/8) sum_abc a^dx b^dy c^dz L_abc nu_abc(r), give
  *     (xi_4, xi_16)(r) = sum over d in {0,1}^3 of h_d(r - d), with exactly the covariance
- *     Xi(k); Xi must be positive semidefinite at s = 0, 4, 16/3.  The other modes as LB_NOISE_LW.
+ *     Xi(k); Xi must be positive semidefinite at s = 0, 4, 16/3.  The other modes as LB_NOISE_LW;
+ *     or spatially uncorrelated with Xi(0) of a homogeneous system at each node's own density
+ *     rho(r) and sound speed c_s^2(rho(r)) (LB_NOISE_LW_LOCAL, Sec. IV and Sec. V B for
+ *     inhomogeneous systems): Xi(0) is rho (A + B c_s^2) entrywise, the coupled block is
+ *     factored at every node by Cholesky with a negative pivot clamped to zero (where the local
+ *     block is not positive semidefinite), the other modes scale with sqrt(rho); the draws are
+ *     those of LB_NOISE_LW, and at uniform density the two modes give the same noise;
+ *   - equation of state: p0 = cs2 rho, or the Landau double well of [GACV] Sec. II A
+ *     (lb3_set_eos), whose bulk pressure enters the second moments and the ghost equilibria.
  *
  * LB_D3Q19 (19 velocities, weights 1/3, 1/18, 1/36)
  *   - modes: the weighted-orthogonal basis of Duenweg, Schiller & Ladd, Phys. Rev. E 76,
@@ -107,12 +115,27 @@ int lb3_set_stream(lb3_ctx* ctx, void* stream);
 
 /*
  * Sets kT, kappa, the relaxation times (each > 1/2) and the noise mode (LB_NOISE_OFF,
- * LB_NOISE_LW, or on D3Q19 LB_NOISE_FULL_RS; others LB_EINVAL).  With noise, Xi(0) (and with
- * LB_NOISE_FULL_RS Xi at s = 4 and 16/3) must be positive semidefinite (D3Q19: c_s^2 <= 5/9),
- * else LB_ENOTPSD.
+ * LB_NOISE_LW, LB_NOISE_LW_LOCAL, or on D3Q19 LB_NOISE_FULL_RS; others LB_EINVAL).  With
+ * LB_NOISE_LW or LB_NOISE_FULL_RS and kT > 0, the c_s^2 of the linear theory about rho0 must be
+ * positive and Xi(0) (with LB_NOISE_FULL_RS also Xi at s = 4 and 16/3) positive semidefinite
+ * (D3Q19 at equal relaxation times: c_s^2 <= 5/9), else LB_ENOTPSD.  May be called again between
+ * steps; the lattice state is kept.
  */
 int lb3_set_params(lb3_ctx* ctx, double kT, double kappa, double tau_s, double tau_b, double tau_ghost,
                    int noise_mode);
+
+/*
+ * Equation of state, [GACV] Sec. II A, as lb_set_eos of lbfluct.h: LB_EOS_LINEAR restores
+ * p0 = cs2 rho with the cs2 of lb3_create; LB_EOS_DOUBLE_WELL takes p0 = rho df0/drho - f0 of
+ * f0 = beta (rho - rhoV)^2 (rho - rhoL)^2 (beta > 0, 0 <= rhoV < rhoL) at every node, as the
+ * exact quartic in rho - rho0.  The uniform rest state becomes the equilibrium at rho0 with
+ * p0(rho0); the linear theory about rho0 that sets LB_NOISE_LW and LB_NOISE_FULL_RS takes
+ * c_s^2 = rho0 d2f0/drho2 (rho0), and LB_NOISE_LW_LOCAL takes c_s^2(rho(r)) at every node.  The
+ * populations are kept (their stored deviations are re-based on the new rest state) and the
+ * parameters of the last lb3_set_params re-applied (its error, if the new linear theory
+ * refuses them).  LB_EINVAL for bad arguments.
+ */
+int lb3_set_eos(lb3_ctx* ctx, int eos, double beta, double rhoV, double rhoL);
 
 /* Advances nsteps time steps (one kernel launch each); asynchronous. */
 int lb3_step(lb3_ctx* ctx, int64_t nsteps);

@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH):
         "lb3_destroy": (c_int, [vp]),
         "lb3_set_stream": (c_int, [vp, vp]),
         "lb3_set_params": (c_int, [vp, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, c_int]),
+        "lb3_set_eos": (c_int, [vp, c_int, c_dbl, c_dbl, c_dbl]),
         "lb3_step": (c_int, [vp, c_i64]),
         "lb3_get_time": (c_int, [vp, i64p]),
         "lb3_set_populations": (c_int, [vp, vp, c_int, c_i64]),
@@ -700,6 +701,10 @@ def lb3_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
     return _check3(load().lb3_set_params(ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode), ctx)
 
 
+def lb3_set_eos(ctx, eos, beta=0.0, rhoV=0.0, rhoL=0.0):
+    return _check3(load().lb3_set_eos(ctx, eos, float(beta), float(rhoV), float(rhoL)), ctx)
+
+
 def lb3_step(ctx, nsteps):
     return _check3(load().lb3_step(ctx, nsteps), ctx)
 
@@ -775,6 +780,9 @@ class Lattice3:
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
         lb3_set_params(self.ctx, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode)
+
+    def set_eos(self, eos, beta=0.0, rhoV=0.0, rhoL=0.0):
+        lb3_set_eos(self.ctx, eos, beta, rhoV, rhoL)
 
     def step(self, n=1):
         lb3_step(self.ctx, n)

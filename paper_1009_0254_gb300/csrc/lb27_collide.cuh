@@ -5,7 +5,8 @@
 //   modes   m_(a,b,c) = sum_i p_a(c_ix) p_b(c_iy) p_c(c_iz) f_i, p_0 = 1, p_1 = c,
 //           p_2 = 3c^2 - 1 (orthogonal under the D1Q3 weights 2/3, 1/6, 1/6 whose products
 //           are the D3Q27 weights; the c_z-independent modes are the D2Q9 basis of Table I)
-//   m^eq    rho, j, second-order modes of P^th + rho u u (Eq. press-ten, p0 = cs2 rho); the
+//   m^eq    rho, j, second-order modes of P^th + rho u u (Eq. press-ten, p0 = cs2 rho or the
+//           double well's bulk pressure, Coef3); the
 //           fourth-order p_2a p_2b = -3 (p0 - rho/3 - kappa rho lap rho) - (3/2) kappa |grad rho|^2
 //           (Table II's eps on fields uniform along an axis), the sixth-order
 //           p_2x p_2y p_2z = 3 (p0 - rho/3 - kappa rho lap rho) - (3/2) kappa |grad rho|^2, others 0
@@ -103,7 +104,8 @@ __host__ __device__ __forceinline__ void collide27(const Coef3<R>& a, const R f[
     const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
     const R g2 = (gx * gx + gy * gy) + gz * gz;
     const R klap = a.kappa * rho * lap;
-    const R base2 = (a.d * drho - R(3) * klap) - R(1.5) * a.kappa * g2;
+    const R dd = pressure_slope(a, drho);
+    const R base2 = (dd * drho - R(3) * klap) - R(1.5) * a.kappa * g2;
     // second order (deviations): p_2a: 3 Pi_aa - rho; p_1a p_1b: Pi_ab
     const R e18 = base2 + R(3) * (jx * ux + a.kappa * gx * gx);      // (2,0,0)
     const R e6 = base2 + R(3) * (jy * uy + a.kappa * gy * gy);       // (0,2,0)
@@ -111,8 +113,8 @@ __host__ __device__ __forceinline__ void collide27(const Coef3<R>& a, const R f[
     const R e12 = jx * uy + a.kappa * gx * gy;                       // (1,1,0)
     const R e4 = jy * uz + a.kappa * gy * gz;                        // (0,1,1)
     const R e10 = jx * uz + a.kappa * gx * gz;                       // (1,0,1)
-    const R e44 = (R(3) * klap - a.d * drho) - R(1.5) * a.kappa * g2;  // p_2a p_2b
-    const R e26 = (a.d * drho - R(3) * klap) - R(1.5) * a.kappa * g2;  // p_2x p_2y p_2z
+    const R e44 = (R(3) * klap - dd * drho) - R(1.5) * a.kappa * g2;  // p_2a p_2b
+    const R e26 = (dd * drho - R(3) * klap) - R(1.5) * a.kappa * g2;  // p_2x p_2y p_2z
 
     // increments D = Lambda (m - m^eq) + xi; the p_2 block relaxes its mean at lambda_b
     R D[Q27];

@@ -5,8 +5,8 @@
 //   basis   the weighted-orthogonal modes of Duenweg, Schiller & Ladd, Phys. Rev. E 76,
 //           036704 (2007), Table I: rho, j, bulk c^2 - 1, five shear modes, nine ghosts
 //   m^eq    rho, j, the trace and traceless part of P^th + rho u u (Eq. press-ten with
-//           p0 = cs2 rho); the isotropic fourth-order ghost
-//           e16 = -3 (p0 - rho/3 - kappa rho lap rho) - (9/2) kappa |grad rho|^2 (the
+//           p0 = cs2 rho, or the double well's bulk pressure, Coef3); the isotropic
+//           fourth-order ghost e16 = -3 (p0 - rho/3 - kappa rho lap rho) - (9/2) kappa |grad rho|^2 (the
 //           choice that reduces to Table II on fields uniform along an axis); other ghosts 0
 //   relax   m*_a = m_a + lambda_a (m_a - m_a^eq) + xi_a (Eq. fluct-lin-lbe)
 //   noise   xi = L nu with L L^T = Xi(0) (Eq. noise-matrix-k0), two Philox draws per node
@@ -34,12 +34,22 @@ struct Rho3 {
     R ap, am, bp, bm, cp, cm, dp, dm, ep, em, fp, fm;
 };
 
-// Coefficients of one run in the arithmetic type.
+// Coefficients of one run in the arithmetic type.  The bulk pressure relative to the rest
+// state is p0(rho0 + dr) - p0(rho0) = dr (cs2 + dr (e2 + dr (e3 + dr e4))): e2..e4 are zero
+// for p0 = cs2 rho and the double well's quartic otherwise (Sec. II A).
 template <typename R>
 struct Coef3 {
     R rho0, d, kappa;          // d = 3 cs2 - 1: weight of the pressure deviation in e4, e16
     R lb, ls, lg;              // lambda of the bulk, shear and ghost modes
+    R e2, e3, e4;              // higher coefficients of the bulk pressure
 };
+
+// 3 (p0(rho0 + dr) - p0(rho0)) - dr = dd dr: the slope of the pressure deviation in the
+// trace and ghost equilibria (exactly d when e2..e4 are zero)
+template <typename R>
+__host__ __device__ __forceinline__ R pressure_slope(const Coef3<R>& a, R dr) {
+    return a.d + R(3) * dr * (a.e2 + dr * (a.e3 + dr * a.e4));
+}
 
 // 1/x: the hardware approximation in FP32 device code (relative error below 2^-22), IEEE
 // division otherwise
@@ -123,13 +133,14 @@ __host__ __device__ __forceinline__ void collide19(const Coef3<R>& a, const R f[
     const R pzz = jz * uz + a.kappa * gz * gz;
     const R g2 = (gx * gx + gy * gy) + gz * gz;
     const R klap = a.kappa * rho * lap;
-    const R e4 = (a.d * drho - R(3) * klap) + ((jx * ux + jy * uy) + jz * uz) - R(0.5) * a.kappa * g2;
+    const R dd = pressure_slope(a, drho);
+    const R e4 = (dd * drho - R(3) * klap) + ((jx * ux + jy * uy) + jz * uz) - R(0.5) * a.kappa * g2;
     const R e5 = (R(2) * pxx - pyy) - pzz;
     const R e6 = pyy - pzz;
     const R e7 = jx * uy + a.kappa * gx * gy;
     const R e8 = jy * uz + a.kappa * gy * gz;
     const R e9 = jz * ux + a.kappa * gz * gx;
-    const R e16 = (R(3) * klap - a.d * drho) - R(4.5) * a.kappa * g2;
+    const R e16 = (R(3) * klap - dd * drho) - R(4.5) * a.kappa * g2;
 
     // increments divided by N_a: D_a / N_a with D_a = lambda_a (m_a - m_a^eq) + xi_a
     const R h4 = R(1.5) * (a.lb * (m4 - e4) + xi[4]);

@@ -24,11 +24,12 @@ static int c_of(int lattice, int i, int k) { return lattice == 19 ? Lat19::c(i, 
 // the stored plane of population i
 static int sigma_of(int lattice, int i) { return lattice == 19 ? Lat19::sigma(i) : Lat27::sigma(i); }
 
-// rest populations: w_i 3 cs2 rho0 on the moving velocities, the remainder at rest
-static void rest_pops(int lattice, double rho0, double cs2, double* fbar) {
+// rest populations of bulk pressure p0: w_i 3 p0 on the moving velocities, the remainder at
+// rest (p0 = cs2 rho0 for the linearised equation of state)
+static void rest_pops(int lattice, double rho0, double p0, double* fbar) {
     double moving = 0.0;
     for (int i = 1; i < lattice; ++i) {
-        fbar[i] = w_of(lattice, i) * 3.0 * cs2 * rho0;
+        fbar[i] = w_of(lattice, i) * 3.0 * p0;
         moving += fbar[i];
     }
     fbar[0] = rho0 - moving;
@@ -205,6 +206,14 @@ __global__ void get_plane3_kernel(const R* __restrict__ src, double* __restrict_
     }
 }
 
+// adds delta to every stored element of one population (interior, ghosts and padding alike):
+// the re-basing of the stored deviations on a new rest state
+template <typename R>
+__global__ void shift_plane3_kernel(R* __restrict__ p, long long n, double delta) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        p[q] = (R)((double)p[q] + delta);
+}
+
 // per-block FP64 partial sums of the density and momentum deviations over the interior
 template <typename LAT, typename R>
 __global__ void sums3_kernel(const R* __restrict__ p, Geom3 g, double* __restrict__ partial) {
@@ -248,7 +257,12 @@ struct lb3_ctx {
     long long n = 0;                // lattice nodes
     Geom3 geom{};                   // padded storage
     uint64_t seed = 0;
-    double rho0 = 1.0, cs2 = 1.0 / 3.0;
+    double rho0 = 1.0;
+    double cs2 = 1.0 / 3.0;         // c_s^2 of the linear theory about rho0
+    double cs2_linear = 1.0 / 3.0;  // the cs2 of lb3_create (p0 = cs2 rho)
+    int eos = LB_EOS_LINEAR;
+    double eos_poly[5] = {};        // p0(rho0 + d) = sum_j eos_poly[j] d^j
+    double eos_cq[4] = {};          // c_s^2(rho0 + d) = sum_j eos_cq[j] d^j
     double fbar[QMAX] = {};
     char* ws = nullptr;
     void* pop[2] = {nullptr, nullptr};
@@ -259,7 +273,7 @@ struct lb3_ctx {
     int cur = 0;
     bool have_params = false;
     int noise_mode = LB_NOISE_OFF;
-    double kT = 0, kappa = 0;
+    double kT = 0, kappa = 0, tau_s = 1, tau_b = 1, tau_g = 1;
     Step3Args<float> af{};
     Step3Args<double> ad{};
     Launch3 cfg[2];                 // step kernel without / with the correlated noise (kmode 3)
@@ -476,7 +490,7 @@ bool noise_factors(int lattice, const double* X, double sc[QMAX], double Lc[28])
 
 template <typename R>
 void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double sc[QMAX],
-               const double Lc[28], const double Lrs[9]) {
+               const double Lc[28], const double Lb[28], const double Lrs[9]) {
     a->nx = c->nx; a->ny = c->ny; a->nz = c->nz;
     a->pitch = c->geom.pitch; a->gx = c->geom.gx; a->PL = c->geom.PL; a->P = c->geom.P;
     a->err = c->err_dev;
@@ -486,8 +500,13 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
     a->co.lb = (R)(-1.0 / tau_b);
     a->co.ls = (R)(-1.0 / tau_s);
     a->co.lg = (R)(-1.0 / tau_g);
+    a->co.e2 = (R)c->eos_poly[2];
+    a->co.e3 = (R)c->eos_poly[3];
+    a->co.e4 = (R)c->eos_poly[4];
+    for (int q = 0; q < 4; ++q) a->cq[q] = (R)c->eos_cq[q];
     for (int q = 0; q < QMAX; ++q) a->sc[q] = (R)sc[q];
     for (int q = 0; q < 28; ++q) a->Lc[q] = (R)Lc[q];
+    for (int q = 0; q < 28; ++q) a->Lb[q] = (R)Lb[q];
     for (int q = 0; q < 9; ++q) a->Lrs[q] = (R)Lrs[q];
     a->rk = lbf::make_round_keys(c->seed);
 }
@@ -496,6 +515,7 @@ template <typename R>
 cudaError_t launch_any(lb3_ctx* c, Step3Args<R> a, int kmode) {
     Launch3 L = c->cfg[kmode == 3 ? 1 : 0];
     L.kmode = kmode;
+    if (kmode == 4) L.plain = false;      // the plain kernel draws no local noise
     a.zc = L.zc;
     const CUtensorMap* map = &c->maps[c->cur];
     return c->lattice == 19 ? launch_lattice<Lat19, R>(a, map, L, c->stream)
@@ -525,6 +545,10 @@ int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed
     lb3_ctx* c = new lb3_ctx();
     c->nx = nx; c->ny = ny; c->nz = nz; c->n = (long long)nx * ny * nz; c->lattice = lattice;
     c->precision = precision; c->es = es; c->seed = seed; c->rho0 = rho0; c->cs2 = cs2;
+    c->cs2_linear = cs2;
+    c->eos_poly[0] = cs2 * rho0;
+    c->eos_poly[1] = cs2;
+    c->eos_cq[0] = cs2;
     cudaGetDevice(&c->device);
     c->geom = geom3(nx, ny, nz, es);
     const Layout3 L = layout3(c->geom, lattice, es);
@@ -538,7 +562,7 @@ int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed
     c->stage = (double*)(c->ws + L.stage);
     c->partial = (double*)(c->ws + L.partial);
     c->err_dev = (int*)(c->ws + L.err);
-    rest_pops(lattice, rho0, cs2, c->fbar);
+    rest_pops(lattice, rho0, cs2 * rho0, c->fbar);
     // the whole workspace starts at zero: the rest state, ghosts included
     e = cudaMemset(c->ws, 0, L.total);
     if (e != cudaSuccess) {
@@ -600,13 +624,43 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
         return fail3(c, LB_EINVAL, "relaxation times must exceed 1/2");
     if (!(kT >= 0.0) || !std::isfinite(kT)) return fail3(c, LB_EINVAL, "kT must be >= 0");
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return fail3(c, LB_EINVAL, "kappa must be >= 0");
-    if (mode != LB_NOISE_OFF && mode != LB_NOISE_LW && !(mode == LB_NOISE_FULL_RS && c->lattice == 19))
-        return fail3(c, LB_EINVAL, "the 3-D lattices take LB_NOISE_OFF or LB_NOISE_LW (D3Q19 also LB_NOISE_FULL_RS)");
+    if (mode != LB_NOISE_OFF && mode != LB_NOISE_LW && mode != LB_NOISE_LW_LOCAL &&
+        !(mode == LB_NOISE_FULL_RS && c->lattice == 19))
+        return fail3(c, LB_EINVAL,
+                     "the 3-D lattices take LB_NOISE_OFF, LB_NOISE_LW or LB_NOISE_LW_LOCAL (D3Q19 also LB_NOISE_FULL_RS)");
+    const bool homogeneous = mode == LB_NOISE_LW || mode == LB_NOISE_FULL_RS;
+    if (homogeneous && kT > 0 && !(c->cs2 > 0.0))
+        return fail3(c, LB_ENOTPSD, "the linear theory about rho0 has c_s^2 <= 0 (a mean density in the spinodal region)");
     std::vector<double> X((size_t)c->lattice * c->lattice);
-    xi_zero(c->lattice, c->rho0, c->cs2, kT, tau_s, tau_b, tau_ghost, X.data());
-    double sc[QMAX] = {}, Lc[28] = {}, Lrs[9] = {};
-    if (mode != LB_NOISE_OFF && kT > 0 && !noise_factors(c->lattice, X.data(), sc, Lc))
-        return fail3(c, LB_ENOTPSD, "Xi(0) is not positive semidefinite");
+    double sc[QMAX] = {}, Lc[28] = {}, Lb[28] = {}, Lrs[9] = {};
+    if (homogeneous && kT > 0) {
+        xi_zero(c->lattice, c->rho0, c->cs2, kT, tau_s, tau_b, tau_ghost, X.data());
+        if (!noise_factors(c->lattice, X.data(), sc, Lc)) return fail3(c, LB_ENOTPSD, "Xi(0) is not positive semidefinite");
+    }
+    if (mode == LB_NOISE_LW_LOCAL && kT > 0) {
+        // Xi(0) of a homogeneous system at density rho and sound speed c_s^2 is rho (A + B c_s^2)
+        // entrywise (affine in c_s^2, linear in rho): A and B from two evaluations at rho = 1;
+        // the kernel factors the coupled block at every node, the other modes scale with
+        // sqrt(rho) (their B is zero)
+        const int Q = c->lattice;
+        const double c1 = 0.2, c2 = 0.4;
+        std::vector<double> X2((size_t)Q * Q);
+        xi_zero(Q, 1.0, c1, kT, tau_s, tau_b, tau_ghost, X.data());
+        xi_zero(Q, 1.0, c2, kT, tau_s, tau_b, tau_ghost, X2.data());
+        auto B = [&](int i, int j) { return (X2[i * Q + j] - X[i * Q + j]) / (c2 - c1); };
+        auto A = [&](int i, int j) { return X[i * Q + j] - c1 * B(i, j); };
+        std::vector<int> coupled = Q == 19 ? std::vector<int>{4, 16} : std::vector<int>(COUPLED27, COUPLED27 + 7);
+        for (int k = 0; k < Q; ++k) {
+            if (std::find(coupled.begin(), coupled.end(), k) != coupled.end()) continue;
+            sc[k] = std::sqrt(std::max(A(k, k), 0.0));
+        }
+        const int n = (int)coupled.size();
+        for (int r = 0; r < n; ++r)
+            for (int q = 0; q <= r; ++q) {
+                Lc[r * (r + 1) / 2 + q] = A(coupled[r], coupled[q]);
+                Lb[r * (r + 1) / 2 + q] = B(coupled[r], coupled[q]);
+            }
+    }
     if (mode == LB_NOISE_FULL_RS && kT > 0) {
         // Xi(k) is Xi(0) at c_s^2(k) = cs2 + rho0 kappa s(k); the factors of its (4,16) block at
         // the corner values s = 0, 4, 16/3 (positive semidefinite there means at every k)
@@ -625,10 +679,68 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
     }
     c->kT = kT;
     c->kappa = kappa;
+    c->tau_s = tau_s; c->tau_b = tau_b; c->tau_g = tau_ghost;
     c->noise_mode = mode;
-    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc, Lrs);
-    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc, Lrs);
+    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs);
+    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs);
     c->have_params = true;
+    return LB_OK;
+}
+
+static unsigned plane_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 4096); }
+
+int lb3_set_eos(lb3_ctx* c, int eos, double beta, double rhoV, double rhoL) {
+    if (!c) return LB_EINVAL;
+    if (eos != LB_EOS_LINEAR && eos != LB_EOS_DOUBLE_WELL) return fail3(c, LB_EINVAL, "unknown equation of state");
+    const double r0 = c->rho0;
+    double poly[5] = {0, 0, 0, 0, 0}, cq[4] = {0, 0, 0, 0};
+    if (eos == LB_EOS_DOUBLE_WELL) {
+        if (!(beta > 0.0) || !std::isfinite(beta) || !(rhoV >= 0.0) || !(rhoL > rhoV) || !std::isfinite(rhoL))
+            return fail3(c, LB_EINVAL, "the double well needs beta > 0 and 0 <= rhoV < rhoL");
+        // f0(rho0 + d) / beta = (A + d)^2 (B + d)^2 with A = rho0 - rhoV, B = rho0 - rhoL, as a
+        // polynomial in d; p0 = rho df0/drho - f0 and c_s^2 = rho d2f0/drho2 in the same form
+        const double A = r0 - rhoV, B = r0 - rhoL, s0 = A * B, s1 = A + B;
+        const double f[5] = {s0 * s0, 2 * s0 * s1, s1 * s1 + 2 * s0, 2 * s1, 1.0};
+        double df[4], d2f[3];
+        for (int j = 0; j < 4; ++j) df[j] = (j + 1) * f[j + 1];
+        for (int j = 0; j < 3; ++j) d2f[j] = (j + 1) * df[j + 1];
+        for (int j = 0; j < 5; ++j) poly[j] = beta * ((j < 4 ? r0 * df[j] : 0.0) + (j >= 1 ? df[j - 1] : 0.0) - f[j]);
+        for (int j = 0; j < 4; ++j) cq[j] = beta * ((j < 3 ? r0 * d2f[j] : 0.0) + (j >= 1 ? d2f[j - 1] : 0.0));
+    } else {
+        poly[0] = c->cs2_linear * r0;
+        poly[1] = c->cs2_linear;
+        cq[0] = c->cs2_linear;
+    }
+    lbf::DeviceGuard dg(c->device);
+    // the stored deviations, re-based on the rest state of the new equation of state
+    double fb_new[QMAX] = {};
+    rest_pops(c->lattice, r0, poly[0], fb_new);
+    const long long P = c->geom.P;
+    for (int i = 0; i < c->lattice; ++i) {
+        const long long off = (long long)sigma_of(c->lattice, i) * P;
+        const double delta = c->fbar[i] - fb_new[i];
+        if (c->precision == LB_FP64)
+            shift_plane3_kernel<double><<<plane_blocks(P), 256, 0, c->stream>>>((double*)c->pop[c->cur] + off, P, delta);
+        else
+            shift_plane3_kernel<float><<<plane_blocks(P), 256, 0, c->stream>>>((float*)c->pop[c->cur] + off, P, delta);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail3(c, e, "re-base populations");
+        c->kernels += 1;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail3(c, e, "cudaStreamSynchronize");
+    for (int i = 0; i < c->lattice; ++i) c->fbar[i] = fb_new[i];
+    c->eos = eos;
+    for (int j = 0; j < 5; ++j) c->eos_poly[j] = poly[j];
+    for (int j = 0; j < 4; ++j) c->eos_cq[j] = cq[j];
+    c->cs2 = poly[1];                     // c_s^2 of the linear theory about rho0
+    if (c->have_params) {
+        const int r = lb3_set_params(c, c->kT, c->kappa, c->tau_s, c->tau_b, c->tau_g, c->noise_mode);
+        if (r != LB_OK) {
+            c->have_params = false;        // the old noise factors belong to the old equation of state
+            return r;
+        }
+    }
     return LB_OK;
 }
 
@@ -637,7 +749,10 @@ int lb3_step(lb3_ctx* c, int64_t nsteps) {
     if (nsteps < 0) return fail3(c, LB_EINVAL, "nsteps must be >= 0");
     if (!c->have_params) return fail3(c, LB_ESTATE, "lb3_set_params must be called before lb3_step");
     lbf::DeviceGuard dg(c->device);
-    const int kmode = c->kT > 0.0 ? (c->noise_mode == LB_NOISE_LW ? 1 : (c->noise_mode == LB_NOISE_FULL_RS ? 3 : 0)) : 0;
+    const int kmode = c->kT > 0.0 ? (c->noise_mode == LB_NOISE_LW ? 1
+                                     : (c->noise_mode == LB_NOISE_FULL_RS ? 3
+                                        : (c->noise_mode == LB_NOISE_LW_LOCAL ? 4 : 0)))
+                                  : 0;
     for (int64_t k = 0; k < nsteps; ++k) {
         const uint32_t tlo = (uint32_t)((uint64_t)c->t & 0xffffffffu), thi = (uint32_t)((uint64_t)c->t >> 32);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -681,7 +796,6 @@ int lb3_get_time(lb3_ctx* c, int64_t* t) {
     return LB_OK;
 }
 
-static unsigned plane_blocks(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 4096); }
 
 int lb3_set_populations(lb3_ctx* c, const double* f, int loc, int64_t t) {
     if (!c || !f || (loc != LB_HOST && loc != LB_DEVICE) || t < 0) return LB_EINVAL;

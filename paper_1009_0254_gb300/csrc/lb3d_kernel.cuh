@@ -110,9 +110,13 @@ struct Step3Args {
     long long P;                  // elements per population (nz PL)
     int* err;                     // device error word: 1 = a CTA gave up waiting for its TMA loads
     Coef3<R> co;
-    R sc[QMAX];                   // sqrt(Xi_kk) of the modes with a diagonal factor
+    R sc[QMAX];                   // sqrt(Xi_kk) of the modes with a diagonal factor (local noise:
+                                  // per unit density)
     R Lc[28];                     // the coupled block's Cholesky factor: D3Q19 (L44, L16_4, L16_16);
-                                  // D3Q27 the 7 x 7 lower triangle, row-major
+                                  // D3Q27 the 7 x 7 lower triangle, row-major.  Local noise: A of
+                                  // its Xi(0) = rho (A + B c_s^2), same layout
+    R Lb[28];                     // local noise: B of the coupled block
+    R cq[4];                      // local noise: c_s^2(rho0 + dr) = cq0 + dr (cq1 + dr (cq2 + dr cq3))
     R Lrs[9];                     // D3Q19 correlated noise: Cholesky factors (L11, L21, L22) of the
                                   // (4,16) block of Xi at s = 0, 4, 16/3
     uint32_t t_lo, t_hi;
@@ -140,6 +144,40 @@ __device__ __forceinline__ void normals19(const Step3Args<R>& a, uint32_t node, 
     xi[16] = a.Lc[1] * n4 + a.Lc[2] * n16;
 }
 
+// D3Q19 noise at the local density (MODE 4, Sec. IV and Sec. V B): the draws of normals19;
+// Xi(0) of a homogeneous system at this node's density rho0 + dr and sound speed
+// c_s^2(rho0 + dr) is rho (A + B c_s^2) entrywise (A, B from the host); the (4,16) block is
+// factored here by Cholesky with a negative pivot clamped to zero, the other modes scale with
+// sqrt(rho)
+template <typename R>
+__device__ __forceinline__ void normals19_local(const Step3Args<R>& a, uint32_t node, R dr, R xi[Q3]) {
+    const uint4 ra = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat19::TAG0), a.rk);
+    const uint4 rb = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat19::TAG0 + 1), a.rk);
+    R n4, n16, spare;
+    lbf::gauss_word(ra.x, &n4, &xi[5]);
+    lbf::gauss_word(ra.y, &xi[6], &xi[7]);
+    lbf::gauss_word(ra.z, &xi[8], &xi[9]);
+    lbf::gauss_word(ra.w, &xi[10], &xi[11]);
+    lbf::gauss_word(rb.x, &xi[12], &xi[13]);
+    lbf::gauss_word(rb.y, &xi[14], &xi[15]);
+    lbf::gauss_word(rb.z, &n16, &xi[17]);
+    lbf::gauss_word(rb.w, &xi[18], &spare);
+    (void)spare;
+    const R rho = a.co.rho0 + dr;
+    const R c = a.cq[0] + dr * (a.cq[1] + dr * (a.cq[2] + dr * a.cq[3]));
+    const R sr = lbf::sqrt_fast(fmax(rho, R(0)));
+#pragma unroll
+    for (int q = 5; q < Q3; ++q) xi[q] *= sr * a.sc[q];
+    const R y44 = rho * (a.Lc[0] + a.Lb[0] * c);
+    const R y416 = rho * (a.Lc[1] + a.Lb[1] * c);
+    const R y1616 = rho * (a.Lc[2] + a.Lb[2] * c);
+    const R L44 = lbf::sqrt_fast(fmax(y44, R(0)));
+    const R L164 = L44 > R(0) ? y416 * lbf::recip(L44) : R(0);
+    const R L1616 = lbf::sqrt_fast(fmax(y1616 - L164 * L164, R(0)));
+    xi[4] = L44 * n4;
+    xi[16] = L164 * n4 + L1616 * n16;
+}
+
 // position of mode k among the non-conserved D3Q27 modes (conserved: 0, 1, 3, 9)
 __host__ __device__ constexpr int nc27(int k) { return k - (k > 0) - (k > 1) - (k > 3) - (k > 9); }
 
@@ -163,6 +201,52 @@ __device__ __forceinline__ void normals27(const Step3Args<R>& a, uint32_t node, 
         R s = R(0);
 #pragma unroll
         for (int q = 0; q <= r; ++q) s += a.Lc[r * (r + 1) / 2 + q] * nu[nc27(coupled27(q))];
+        xi[coupled27(r)] = s;
+    }
+}
+
+// D3Q27 noise at the local density (MODE 4): the draws of normals27; the uncoupled modes scale
+// with sqrt(rho), the seven coupled modes take the Cholesky factor, formed here, of the block
+// rho (A + B c_s^2) (a negative pivot clamped to zero leaves its column zero)
+template <typename R>
+__device__ __forceinline__ void normals27_local(const Step3Args<R>& a, uint32_t node, R dr, R xi[Q27]) {
+    R nu[24];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const uint4 r = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, Lat27::TAG0 + d), a.rk);
+        lbf::gauss_word(r.x, &nu[8 * d + 0], &nu[8 * d + 1]);
+        lbf::gauss_word(r.y, &nu[8 * d + 2], &nu[8 * d + 3]);
+        lbf::gauss_word(r.z, &nu[8 * d + 4], &nu[8 * d + 5]);
+        lbf::gauss_word(r.w, &nu[8 * d + 6], &nu[8 * d + 7]);
+    }
+    const R rho = a.co.rho0 + dr;
+    const R c = a.cq[0] + dr * (a.cq[1] + dr * (a.cq[2] + dr * a.cq[3]));
+    const R sr = lbf::sqrt_fast(fmax(rho, R(0)));
+#pragma unroll
+    for (int k = 0; k < Q27; ++k)
+        xi[k] = (k == 0 || k == 1 || k == 3 || k == 9) ? R(0) : sr * a.sc[k] * nu[nc27(k)];
+    R L[28], inv[7];
+#pragma unroll
+    for (int r = 0; r < 7; ++r) {
+#pragma unroll
+        for (int q = 0; q <= r; ++q) {
+            const int e = r * (r + 1) / 2 + q;
+            R y = rho * (a.Lc[e] + a.Lb[e] * c);
+#pragma unroll
+            for (int p = 0; p < q; ++p) y -= L[r * (r + 1) / 2 + p] * L[q * (q + 1) / 2 + p];
+            if (q == r) {
+                L[e] = lbf::sqrt_fast(fmax(y, R(0)));
+                inv[r] = L[e] > R(0) ? lbf::recip(L[e]) : R(0);
+            } else {
+                L[e] = y * inv[q];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 7; ++r) {
+        R s = R(0);
+#pragma unroll
+        for (int q = 0; q <= r; ++q) s += L[r * (r + 1) / 2 + q] * nu[nc27(coupled27(q))];
         xi[coupled27(r)] = s;
     }
 }
@@ -494,6 +578,7 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
             r.ep = dp[1]; r.em = dm[-1];                   // (1,0,1)
             r.fp = dp[-1]; r.fm = dm[1];                   // (-1,0,1)
             if (MODE == 1 || MODE == 3) normals19(a, node, xi);
+            if (MODE == 4) normals19_local(a, node, r.c, xi);
             if constexpr (MODE == 3) {
                 // (xi_4, xi_16) = sum over the box: h of r - (dx, dy, 0) from this plane and of
                 // r - (dx, dy, 1) from the previous one
@@ -519,6 +604,7 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
                 nb[i] = pl[LAT::c(i, 1) * RX + LAT::c(i, 0)];
             }
             if (MODE == 1) normals27(a, node, xi);
+            if (MODE == 4) normals27_local(a, node, nb[0], xi);
             collide27(a.co, f, nb, xi, o);
         }
         store_node3<LAT, R, I>(a, (I)z * PLI, x, y, o);
@@ -673,7 +759,7 @@ __global__ void __launch_bounds__(TX * TY) step3_kernel(const Step3Args<R> a) {
 // ---- launch ---------------------------------------------------------------------------------
 
 // The launch configuration of a context: grid, kernel noise mode (0 off, 1 Xi(0), 3 the
-// correlated noise of D3Q19), the staged kernel's raw slots, staging (TMA or copies) and tile
+// correlated noise of D3Q19, 4 Xi(0) at the local density), the staged kernel's raw slots, staging (TMA or copies) and tile
 // height, or the plain D3Q19 kernel.
 struct Launch3 {
     dim3 grid;
@@ -718,7 +804,7 @@ static cudaError_t launch_mode3(const Step3Args<R>& a, const CUtensorMap* map, c
     constexpr bool F32 = sizeof(R) == 4;
     if constexpr (LAT::Q == 19) {
         if (L.plain) {
-            if constexpr (MODE != 3) {
+            if constexpr (MODE == 0 || MODE == 1) {
                 step3_kernel<R, MODE, 32, 8><<<L.grid, 256, 0, s>>>(a);
                 return cudaGetLastError();
             }
@@ -745,6 +831,7 @@ cudaError_t launch_lattice(const Step3Args<R>& a, const CUtensorMap* map, const 
     if constexpr (LAT::Q == 19) {
         if (L.kmode == 3) return launch_mode3<LAT, R, 3>(a, map, L, s);
     }
+    if (L.kmode == 4) return launch_mode3<LAT, R, 4>(a, map, L, s);
     return L.kmode ? launch_mode3<LAT, R, 1>(a, map, L, s) : launch_mode3<LAT, R, 0>(a, map, L, s);
 }
 

@@ -85,7 +85,7 @@ def parse():
                    help="run only the three-dimensional variant on an N^3 lattice and print its JSON "
                         "(profiling runs; --lattice 19 or 27)")
     p.add_argument("--lattice", type=int, default=19, choices=[19, 27])
-    p.add_argument("--d3-noise", default="lw", choices=["lw", "rs"])
+    p.add_argument("--d3-noise", default="lw", choices=["lw", "rs", "local"])
     p.add_argument("--noise", default="lw", choices=["lw", "full", "rs"],
                    help="noise of the main line (full: correlated via k-space, rs: correlated built in real "
                         "space, both at kappa=0.05; for profiling runs)")
@@ -319,15 +319,26 @@ def timed_run(lbf, torch, L, steps, warmup, mode, params, dist):
     return ms, kms, kl, launches, wall0, wall1
 
 
+# the two-phase variants: the Landau double well of Sec. II A, mean density in the spinodal
+# region (the uniform state decomposes, seeded by the noise at the local density)
+DOUBLE_WELL = (0.04, 0.5, 1.0)      # beta, rhoV, rhoL
+RHO0_TWOPHASE = 0.75
+
+
 def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5, noise="lw"):
     """A three-dimensional lattice (the paper's model carried to D3Q19 or D3Q27): n^3 FP32
     (2 x 19 x 67 MB or 2 x 27 x 67 MB of populations at n = 256, larger than L2), cs2 = 1/3,
     uncorrelated noise of Xi(0) (noise="lw") or, on D3Q19, the correlated noise Xi(k) built in
-    real space (noise="rs"), the PARAMS_LW relaxation times and kappa; one kernel launch per
-    step.  Algorithmic bytes: Q FP32 populations read and Q written per node."""
-    L = lbf.Lattice3(n, n, n, seed=42, rho0=1.0, cs2=1.0 / 3.0, lattice=lattice)
-    p = PARAMS_LW
-    mode = lbf.LB_NOISE_FULL_RS if noise == "rs" else lbf.LB_NOISE_LW
+    real space (noise="rs"), the PARAMS_LW relaxation times and kappa; or the two-phase model
+    (noise="local": the double well DOUBLE_WELL at mean density RHO0_TWOPHASE, kappa = 0.03,
+    noise at the local density); one kernel launch per step.  Algorithmic bytes: Q FP32
+    populations read and Q written per node."""
+    twophase = noise == "local"
+    L = lbf.Lattice3(n, n, n, seed=42, rho0=RHO0_TWOPHASE if twophase else 1.0, cs2=1.0 / 3.0, lattice=lattice)
+    p = dict(PARAMS_LW, kappa=0.03) if twophase else PARAMS_LW
+    if twophase:
+        L.set_eos(lbf.LB_EOS_DOUBLE_WELL, *DOUBLE_WELL)
+    mode = {"rs": lbf.LB_NOISE_FULL_RS, "local": lbf.LB_NOISE_LW_LOCAL}.get(noise, lbf.LB_NOISE_LW)
     L.set_params(p["kT"], p["kappa"], p["tau_s"], p["tau_b"], p["tau_ghost"], mode)
     L.step(warmup)
     torch.cuda.synchronize()
@@ -349,12 +360,37 @@ def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5, noise="l
     k_s = kms / max(kl, 1) / 1e3
     L.close()
     return {"lattice": "D3Q%d %d^3, FP32 deviations" % (lattice, n),
-            "noise": "correlated, built in real space (2x2x2 stencil of eight white fields)" if noise == "rs"
-            else "long-wavelength",
+            "noise": {"rs": "correlated, built in real space (2x2x2 stencil of eight white fields)",
+                      "local": "uncorrelated at the local density and c_s^2 (two-phase: double well beta=%g, "
+                               "rhoV=%g, rhoL=%g, rho0=%g)" % (DOUBLE_WELL + (RHO0_TWOPHASE,))}.get(
+                noise, "long-wavelength"),
             "kappa": p["kappa"], "value": nodes * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
             "ms_per_step": ms / steps,
             "step_kernel": {"achieved": bpn * nodes / k_s / 1e9, "unit": "GB/s",
                             "frac": bpn * nodes / k_s / 1e9 / hbm, "avg_us": k_s * 1e6, "bytes_per_node": bpn},
+            "gpu_launches": launches}
+
+
+def twophase_variant(lbf, torch, hbm, n=4096, steps=1000, warmup=5):
+    """The two-phase model on D2Q9: an n^2 FP32 lattice with the double well DOUBLE_WELL at
+    mean density RHO0_TWOPHASE (spinodal decomposition from the uniform state), kappa = 0.03,
+    the PARAMS_LW relaxation times and kT, noise at the local density (Sec. IV, V B); the step
+    kernel that carries the double well's quartic.  Algorithmic bytes: 72 per node."""
+    L = lbf.Lattice(n, n, seed=44, rho0=RHO0_TWOPHASE)
+    L.set_eos(lbf.LB_EOS_DOUBLE_WELL, *DOUBLE_WELL)
+    p = dict(PARAMS_LW, kappa=0.03)
+    ms, kms, kl, launches, _, _ = timed_run(lbf, torch, L, steps, warmup, lbf.LB_NOISE_LW_LOCAL, p, None)
+    k_s = kms / max(kl, 1) / 1e3
+    rho = L.populations().sum(axis=0)
+    L.close()
+    return {"lattice": "D2Q9 %d^2, FP32 deviations" % n,
+            "noise": "uncorrelated at the local density and c_s^2 (two-phase: double well beta=%g, rhoV=%g, "
+                     "rhoL=%g, rho0=%g)" % (DOUBLE_WELL + (RHO0_TWOPHASE,)),
+            "kappa": 0.03, "value": n * n * steps / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / steps,
+            "step_kernel": {"achieved": BYTES_PER_NODE_STEP * n * n / k_s / 1e9, "unit": "GB/s",
+                            "frac": BYTES_PER_NODE_STEP * n * n / k_s / 1e9 / hbm, "avg_us": k_s * 1e6,
+                            "bytes_per_node": BYTES_PER_NODE_STEP},
+            "density_range_after": [float(rho.min()), float(rho.max())],
             "gpu_launches": launches}
 
 
@@ -675,6 +711,12 @@ def main():
         variants.append(d3_variant(lbf, torch, hbm, 19))
         variants.append(d3_variant(lbf, torch, hbm, 19, noise="rs"))
         variants.append(d3_variant(lbf, torch, hbm, 27))
+
+    # the two-phase model (double well, noise at the local density) on D2Q9, D3Q19, D3Q27
+    if not args.no_variants and not main_fp16:
+        variants.append(twophase_variant(lbf, torch, hbm))
+        variants.append(d3_variant(lbf, torch, hbm, 19, noise="local"))
+        variants.append(d3_variant(lbf, torch, hbm, 27, noise="local"))
 
     # batched ensemble and request server (rank 0 of a single-GPU run)
     if not args.no_variants and world == 1:

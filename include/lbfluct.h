@@ -141,8 +141,9 @@ int lb_set_params(lb_ctx* ctx, double kT, double kappa, double tau_s, double tau
  * FULL_RS modes takes c_s^2 = rho0 d2f0/drho2 (rho0) (it must be > 0 for those modes), and
  * LB_NOISE_LW_LOCAL takes c_s^2(rho(r)) at every node.  The populations are kept (their
  * stored deviations are re-based on the new rest state); the parameters of the last
- * lb_set_params are re-applied.  A double-well lattice is stepped by the plain step kernel
- * (the TMA-staged kernels are built for the linear equation of state).  LB_EINVAL for bad
+ * lb_set_params are re-applied.  With FP32 storage a double-well lattice is stepped by the
+ * TMA-staged kernel's double-well variant (the default tile of its noise mode), with FP16 and
+ * FP64 storage by the plain step kernel.  LB_EINVAL for bad
  * arguments; FP16 and FP32 storage keep deviations from the rest state, so large density
  * contrasts lose more to rounding in FP16.
  */

@@ -708,13 +708,14 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
             if (r != LB_OK) return r;
             CK(c, cudaEventRecord(e0, c->stream), "cudaEventRecord");
         }
-        // the double-well equation of state runs on the plain kernel; the sweep kernel has
-        // the noise modes 0..2 only
+        // the double-well equation of state runs on the TMA kernel's double-well variant (FP32
+        // storage, the default tile of the noise mode) or on the plain kernel; the sweep kernel
+        // has the noise modes 0..2 only
         const bool poly = c->eos == LB_EOS_DOUBLE_WELL;
         if (c->use_sweep && kmode < 3 && !poly)
             CK(c, launch_step_sweep(a, kmode, c->fp16, c->sweep_occ6, c->stream), "step kernel launch");
-        else if (c->use_tma && !poly) {
-            const int want = c->tma_tile_fixed >= 0 ? c->tma_tile_fixed : tma_default_tile(kmode, c->fp16);
+        else if (c->use_tma && (!poly || !c->fp16)) {
+            const int want = (c->tma_tile_fixed >= 0 && !poly) ? c->tma_tile_fixed : tma_default_tile(kmode, c->fp16);
             if (want != c->tma_tile) {
                 // tensor maps are host-encoded descriptors passed by value: re-encode for the shape
                 if (!make_pop_tensor_map(c->pop[0], c->g, want, c->fp16, c->tmap[0]) ||
@@ -722,7 +723,7 @@ int lb_step(lb_ctx* c, int64_t nsteps) {
                     return fail(c, LB_ECUDA, "tensor map encoding failed");
                 c->tma_tile = want;
             }
-            CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->tma_tile, c->fp16, c->stream),
+            CK(c, launch_step_tma(a, c->tmap[c->cur], c->err_dev, kmode, c->tma_tile, c->fp16, c->stream, poly),
                "step kernel launch");
         } else
             CK(c, launch_step_simple(a, kmode, c->fp16, c->stream), "step kernel launch");

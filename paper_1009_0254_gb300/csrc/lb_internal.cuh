@@ -423,7 +423,7 @@ cudaError_t launch_step_simple_d(const StepArgsD& a, int noise_mode, cudaStream_
 cudaError_t launch_step_sweep(const StepArgs& a, int noise_mode, int fp16, int occ6, cudaStream_t s);
 bool sweep_fits(const Grid& g);
 cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile, int fp16,
-                            cudaStream_t s);
+                            cudaStream_t s, bool poly = false);
 bool make_pop_tensor_map(const void* buf, const Grid& g, int tile, int fp16, void* map_out);
 int tma_tile_count();
 int tma_default_tile(int noise_mode, int fp16);

@@ -36,7 +36,8 @@ struct TmaArgs {
 };
 
 
-template <int TX, int TY, int NT, int MODE, typename T>
+// POLY: the double-well equation of state (the bulk pressure's quartic in drho, StepArgs e2..e4)
+template <int TX, int TY, int NT, int MODE, typename T, bool POLY = false>
 __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const TmaArgs ta) {
     using TT = TmaTile<TX, TY, T>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             if (MODE == 2) z = a.xi49[(long long)y * g.nx + x];
             if (MODE == 3) z = stencil_xi<TT::HW>(H, TT::HN, lx, ly);
             float o[Q];
-            collide_node<MODE, false, GF>(a, f, r, node, z, o);
+            collide_node<MODE, POLY, GF>(a, f, r, node, z, o);
             store9<T, float, GF>(static_cast<T*>(a.dst), g.plane, g, x, y, o);
         }
     }
@@ -221,10 +222,10 @@ bool make_pop_tensor_map(const void* buf, const Grid& g, int tile, int fp16, voi
 
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
-template <int TX, int TY, int NT, int MODE, typename T>
+template <int TX, int TY, int NT, int MODE, typename T, bool POLY = false>
 static cudaError_t launch_cfg(const void* map, TmaArgs ta, cudaStream_t s) {
     using TT = TmaTile<TX, TY, T>;
-    auto kern = step_tma_kernel<TX, TY, NT, MODE, T>;
+    auto kern = step_tma_kernel<TX, TY, NT, MODE, T, POLY>;
     constexpr int smem = TT::SMEM_BYTES + (MODE == 3 ? TT::H_BYTES : 0);
     static GridCache cache;
     int grid_max = 0;
@@ -260,12 +261,25 @@ static cudaError_t launch_type(const void* map, const TmaArgs& ta, int noise_mod
     }
 }
 
+// the double-well equation of state, FP32 storage: the default tile of each noise mode
+// (tma_default_tile(noise_mode, 0); the caller encodes the tensor maps for it)
+static cudaError_t launch_poly(const void* map, const TmaArgs& ta, int noise_mode, cudaStream_t s) {
+    switch (noise_mode) {
+        case 0: return launch_cfg<32, 32, 256, 0, float, true>(map, ta, s);
+        case 1: return launch_cfg<64, 16, 512, 1, float, true>(map, ta, s);
+        case 3: return launch_cfg<32, 16, 256, 3, float, true>(map, ta, s);
+        case 4: return launch_cfg<64, 16, 512, 4, float, true>(map, ta, s);
+        default: return launch_cfg<32, 16, 256, 2, float, true>(map, ta, s);
+    }
+}
+
 cudaError_t launch_step_tma(const StepArgs& a, const void* src_map, int* err, int noise_mode, int tile, int fp16,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool poly) {
     TmaArgs ta;
     ta.a = a;
     ta.ntx = ta.nty = 0;
     ta.err = err;
+    if (poly) return fp16 ? cudaErrorInvalidValue : launch_poly(src_map, ta, noise_mode, s);
     return fp16 ? launch_type<__half>(src_map, ta, noise_mode, tile, s)
                 : launch_type<float>(src_map, ta, noise_mode, tile, s);
 }

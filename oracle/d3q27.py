@@ -39,6 +39,19 @@ scales the long-wavelength normals at every node by the factor of Xi(0) at that 
 density and sound speed (Cholesky of the seven coupled modes with negative pivots clamped
 to zero, square roots of the other variances).
 
+Correlated noise (Sec. III C, Eq. noise-matrix at every k), as ``oracle.d3q19``: with the
+ansatz the advection drops out of the fluctuation-dissipation relation, so Xi(k) is Xi(0) at
+c_s^2(k) = cs2 + rho0 kappa s(k), s the symbol of the D3Q27 Laplacian,
+s = 6 (1 - prod_a (2 + cos k_a) / 3), which is multilinear in the three cosines; Xi(0) is
+affine in c_s^2 and only its seven coupled modes depend on it, so Xi(k) is the multilinear
+interpolation of its values at the corners k in {0, pi}^3 (s = 0, 4, 16/3, 52/9 for 0..3
+components at pi).  Eight white 7-vector fields nu_w per node (w = 4 ia + 2 ib + ic, a set bit
+for a component at pi), each times the Cholesky factor of the coupled block at its corner,
+combined as h_d = (1/8) sum_w (-1)^{popcount(w & d)} L_w nu_w and summed over the 2x2x2 box,
+xi(r) = sum_d h_d(r - d), give the coupled modes' noise with covariance Xi(k) at every k; the
+other modes keep the long-wavelength noise.  Draws: tags 12..18, normal n = 7 w + m of their
+56 (in tag order, eight per draw) is component m of corner w.
+
 Indices: velocity i = 9 ix + 3 iy + iz with c = (v[ix], v[iy], v[iz]), v = (0, 1, -1); mode
 a = 9 ax + 3 ay + az for p_ax(c_x) p_ay(c_y) p_az(c_z).  f[i, z, y, x].
 Random numbers: three Philox4x32-10 draws per node and step with counter (node, t mod 2^32,
@@ -314,7 +327,73 @@ def noise_lw_local(model: Model, rho: np.ndarray, c2, seed: int, step_index: int
     return xi.reshape(Q, nz, ny, nx)
 
 
-NOISE_OFF, NOISE_LW, NOISE_LW_LOCAL = 0, 1, 5
+# --- correlated noise (Sec. III C, Eq. noise-matrix) ------------------------------------------
+
+TAG_RS = tuple(range(12, 19))
+
+
+def lattice_s(kx, ky, kz):
+    """Symbol of the D3Q27 Laplacian stencil: -lap e^{ik.r} = s(k) e^{ik.r},
+    s = 6 sum_{i != 0} w_i (1 - cos k.c_i)."""
+    kv = np.stack(np.broadcast_arrays(np.asarray(kx, float), np.asarray(ky, float), np.asarray(kz, float)), axis=-1)
+    return 6.0 * sum(W[i] * (1.0 - np.cos(kv @ C[i].astype(float))) for i in range(1, Q))
+
+
+def Xi_k(model: Model, kx, ky, kz) -> np.ndarray:
+    """Xi(k) = A(k) G(k) A(-k)^T - (1 + Omega(k)) G(k) (1 + Omega(k))^T, Eq. (noise-matrix), with
+    G(k) and Omega(k) = Lambda (I - J(k)) those of a homogeneous system at
+    c_s^2(k) = cs2 + rho0 kappa s(k) (Eq. sound-speed-k)."""
+    c2k = model.cs2 + model.rho0 * model.kappa * float(lattice_s(kx, ky, kz))
+    mk = Model(model.rho0, c2k, model.kappa, model.kT, model.tau_s, model.tau_b, model.tau_ghost)
+    G = mk.G0()
+    O = mk.Omega0()
+    ph = np.exp(-1j * (C.astype(float) @ np.array([kx, ky, kz], dtype=float)))
+    A = T @ np.diag(ph) @ TINV
+    Am = T @ np.diag(np.conj(ph)) @ TINV
+    IO = np.eye(Q) + O
+    X = A @ G @ Am.T - IO @ G @ IO.T
+    return X.real
+
+
+CORNERS = [(1 if (w >> 2) & 1 == 0 else -1, 1 if (w >> 1) & 1 == 0 else -1, 1 if w & 1 == 0 else -1)
+           for w in range(8)]
+
+
+def rs_factors(model: Model) -> np.ndarray:
+    """7x7 Cholesky factors of the coupled block of Xi at the eight corners (sign +1: k = 0)."""
+    out = np.zeros((8, 7, 7))
+    for w, (a, b, c) in enumerate(CORNERS):
+        k = [0.0 if v > 0 else np.pi for v in (a, b, c)]
+        X = Xi_k(model, *k)
+        out[w] = cholesky_psd(X[np.ix_(COUPLED, COUPLED)])
+    return out
+
+
+def rs_fields(nx, ny, nz, seed: int, step_index: int) -> np.ndarray:
+    """nu[w, 7, z, y, x]: the white 7-vector of corner w at every node."""
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.uint32)
+    g = np.concatenate([normals(idx, seed, step_index, t) for t in TAG_RS], axis=1)     # (n, 56)
+    return g.T.reshape(8, 7, nz, ny, nx)
+
+
+def xi_coupled_rs(model: Model, nx, ny, nz, seed: int, step_index: int, Ls=None) -> np.ndarray:
+    """xi[7, z, y, x] of the coupled modes (in COUPLED order) by the real-space construction."""
+    if Ls is None:
+        Ls = rs_factors(model)
+    nu = rs_fields(nx, ny, nz, seed, step_index)
+    v = np.einsum("wab,wb...->wa...", Ls, nu)
+    out = np.zeros((7, nz, ny, nx))
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                h = sum((CORNERS[w][0] ** dx) * (CORNERS[w][1] ** dy) * (CORNERS[w][2] ** dz) * v[w]
+                        for w in range(8)) / 8.0
+                out += np.roll(h, shift=(dz, dy, dx), axis=(1, 2, 3))      # h_d(r - d)
+    return out
+
+
+NOISE_OFF, NOISE_LW, NOISE_FULL_RS, NOISE_LW_LOCAL = 0, 1, 4, 5
 
 
 class Lattice:
@@ -333,12 +412,15 @@ class Lattice:
         self.t = 0
         self.f = np.broadcast_to(self.model.rest()[:, None, None, None], (Q, nz, ny, nx)).copy()
         self._L = None
+        self._Ls = None
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
         m = self.model
         self.model = Model(m.rho0, m.cs2, kappa, kT, tau_s, tau_b, tau_ghost, m.p0_rest)
         self.mode = int(noise_mode)
-        self._L = self.model.noise_factor() if (self.mode == NOISE_LW and kT > 0) else None
+        noisy = self.mode in (NOISE_LW, NOISE_FULL_RS) and kT > 0
+        self._L = self.model.noise_factor() if noisy else None
+        self._Ls = rs_factors(self.model) if (noisy and self.mode == NOISE_FULL_RS) else None
 
     def step(self, nsteps=1):
         n = self.nx * self.ny * self.nz
@@ -347,6 +429,8 @@ class Lattice:
             xi = None
             if self._L is not None:
                 xi = noise_lw_nodes(self.model, nodes, self.seed, self.t, self._L)
+                if self._Ls is not None:
+                    xi[COUPLED] = xi_coupled_rs(self.model, self.nx, self.ny, self.nz, self.seed, self.t, self._Ls)
             elif self.mode == NOISE_LW_LOCAL and self.model.kT > 0:
                 rho = self.f.sum(axis=0)
                 c2 = self.model.cs2 if self.eos is None else self.eos.cs2(rho)

@@ -4,7 +4,10 @@ second and third moments of the equilibrium against Eq. (press-ten), the rest st
 agreement with the independent D2Q9 C core on fields uniform along an axis, Navier-Stokes
 shear and sound, the ansatz covariance as a rank-one update of a diagonal, the ideal-gas
 noise in closed form, the fluctuation-dissipation balance of Xi(0) by simulation of the
-k = 0 dynamics, and equipartition of the ideal fluctuating gas."""
+k = 0 dynamics, equipartition of the ideal fluctuating gas; for the correlated noise Xi(k):
+the FDT with advection equal to Xi(0) at c_s^2(k), the Laplacian symbol against the stencil,
+the real-space construction's transfer function and sampled spectrum equal to Xi(k), and
+equipartition at every wavevector (which Xi(0) alone misses)."""
 import numpy as np
 import pytest
 
@@ -294,3 +297,119 @@ def test_ideal_fluctuating_gas_is_in_equipartition():
     print("D3Q27 equipartition ratios", np.round(mean / want, 3))
     assert np.abs(mean / want - 1).max() < 0.06
     assert np.abs((mean - want) / sd).max() < 5.0
+
+
+# --- correlated noise Xi(k) (Sec. III C, Eq. noise-matrix) ---------------------------------
+
+@pytest.mark.parametrize("k", [(0.0, 0.0, 0.0), (np.pi, 0.0, 0.0), (np.pi, np.pi, 0.0), (np.pi, np.pi, np.pi),
+                               (0.3, 1.1, -2.0), (2.0, 2.5, 0.7)])
+def test_noise_matrix_at_k_is_the_long_wavelength_form_at_cs2_k(k):
+    # the FDT of Eq. (noise-matrix) with advection A(k) and the k-dependent ansatz against
+    # Xi(0) of a homogeneous system at c_s^2(k) = cs2 + rho0 kappa s(k)
+    m = d.Model(rho0=0.9, cs2=0.25, kappa=0.03, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    X = d.Xi_k(m, *k)
+    s = float(d.lattice_s(*k))
+    m2 = d.Model(rho0=0.9, cs2=0.25 + 0.9 * 0.03 * s, kappa=0.03, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    np.testing.assert_allclose(X, m2.Xi_zero(), rtol=1e-12, atol=1e-13 * 1e-4)
+    assert np.abs(X[d.CONSERVED]).max() < 1e-18
+
+
+def test_lattice_symbol_is_the_stencils_and_has_its_corner_values():
+    # s(k) = k^2 + O(k^4); the corner values 0, 4, 16/3, 52/9; and s is what the oracle's
+    # Laplacian stencil does to a plane wave on a periodic lattice
+    k = np.array([0.01, -0.02, 0.015])
+    assert abs(float(d.lattice_s(*k)) / (k @ k) - 1) < 1e-3
+    for kk, want in [((0, 0, 0), 0.0), ((np.pi, 0, 0), 4.0), ((0, np.pi, np.pi), 16 / 3), ((np.pi,) * 3, 52 / 9)]:
+        assert abs(float(d.lattice_s(*kk)) - want) < 1e-12
+    n = (6, 5, 4)
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    for m in [(1, 0, 0), (2, 3, 1), (3, 2, 2)]:
+        kv = [2 * np.pi * m[a] / n[a] for a in range(3)]
+        wave = np.cos(kv[0] * x + kv[1] * y + kv[2] * z)
+        lap, _ = d.density_stencils(wave)
+        np.testing.assert_allclose(-lap, float(d.lattice_s(*kv)) * wave, atol=1e-12)
+
+
+def test_real_space_construction_reproduces_Xi_k_at_every_wavevector():
+    # transfer function of the 2x2x2 box: sum_w L_w L_w^T |(1/8) sum_d (-1)^{w.d} e^{-i k.d}|^2
+    # must equal the coupled block of Xi(k) from the FDT at every k of a 6 x 5 x 4 lattice
+    m = d.Model(rho0=1.0, cs2=0.2, kappa=0.04, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    Ls = d.rs_factors(m)
+    for mz in range(4):
+        for my in range(5):
+            for mx in range(6):
+                k = (2 * np.pi * mx / 6, 2 * np.pi * my / 5, 2 * np.pi * mz / 4)
+                got = np.zeros((7, 7))
+                for w, (a, b, c) in enumerate(d.CORNERS):
+                    t = sum((a ** dx) * (b ** dy) * (c ** dz) * np.exp(-1j * (k[0] * dx + k[1] * dy + k[2] * dz))
+                            for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)) / 8.0
+                    got += abs(t) ** 2 * (Ls[w] @ Ls[w].T)
+                want = d.Xi_k(m, *k)[np.ix_(d.COUPLED, d.COUPLED)]
+                np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-18)
+
+
+def test_real_space_fields_have_the_Xi_k_spectrum():
+    # sampled: the generated coupled-mode fields' spectral covariance at a few k against Xi(k)
+    m = d.Model(rho0=1.0, cs2=0.2, kappa=0.04, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    n = 6
+    Ls = d.rs_factors(m)
+    acc = np.zeros((7, 7, n, n, n), dtype=complex)
+    draws = 300
+    for t in range(draws):
+        xi = d.xi_coupled_rs(m, n, n, n, seed=9, step_index=t, Ls=Ls)
+        xk = np.fft.fftn(xi, axes=(1, 2, 3)) / np.sqrt(n ** 3)
+        acc += np.einsum("a...,b...->ab...", xk, np.conj(xk))
+    acc /= draws
+    for (mz, my, mx) in [(0, 0, 1), (0, 3, 3), (3, 3, 3), (1, 2, 5), (0, 0, 0)]:
+        k = (2 * np.pi * mx / n, 2 * np.pi * my / n, 2 * np.pi * mz / n)
+        want = d.Xi_k(m, *k)[np.ix_(d.COUPLED, d.COUPLED)]
+        got = acc[:, :, mz, my, mx].real
+        sd = np.sqrt((np.abs(np.diag(want))[:, None] * np.abs(np.diag(want))[None, :] + want ** 2) / draws)
+        assert np.abs(got - want).max() < 5 * sd.max(), (k, np.abs(got - want).max(), sd.max())
+
+
+def _spectra(L, n):
+    m = L.moments()
+    drho = np.fft.fftn(m[d.IDX[(0, 0, 0)]] - L.model.rho0) / np.sqrt(n ** 3)
+    j = [np.fft.fftn(m[d.IDX[c]]) / np.sqrt(n ** 3) for c in ((1, 0, 0), (0, 1, 0), (0, 0, 1))]
+    return np.abs(drho) ** 2, sum(np.abs(x) ** 2 for x in j) / 3
+
+
+@pytest.mark.parametrize("mode", ["rs", "lw"])
+def test_correlated_noise_equilibrates_every_wavevector(mode):
+    # Sec. V A on D3Q27: with Xi(k) the density spectrum is the Ornstein-Zernike
+    # S(k) = rho0 kT / c_s^2(k) and the momentum spectrum rho0 kT at every k (the staggered
+    # momenta at k = pi e_a excepted, an invariant as on D3Q19); with Xi(0) alone the largest
+    # wavevectors stay out of equipartition
+    n, R, steps, burn = 4, 6, 500, 80
+    cs2, kappa, kT = 0.2, 0.04, 1e-4
+    S_acc = np.zeros((n, n, n))
+    J_acc = np.zeros((n, n, n))
+    cnt = 0
+    for r in range(R):
+        L = d.Lattice(n, n, n, cs2=cs2, seed=400 + r)
+        L.set_params(kT, kappa, 0.8, 1.1, 0.9, d.NOISE_FULL_RS if mode == "rs" else d.NOISE_LW)
+        L.step(burn)
+        for t in range(steps):
+            L.step(1)
+            if t % 2 == 0:
+                s_, j_ = _spectra(L, n)
+                S_acc += s_
+                J_acc += j_
+                cnt += 1
+    S_acc /= cnt
+    J_acc /= cnt
+    k1 = 2 * np.pi * np.fft.fftfreq(n)
+    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")
+    S_th = kT / (cs2 + kappa * d.lattice_s(KX, KY, KZ))
+    ratio_S = (S_acc / S_th).ravel()[1:]
+    keep = np.ones((n, n, n), bool)
+    keep[0, 0, 0] = keep[0, 0, n // 2] = keep[0, n // 2, 0] = keep[n // 2, 0, 0] = False
+    ratio_J = (J_acc / kT)[keep]
+    print(mode, "S ratio range %.3f..%.3f, J ratio range %.3f..%.3f" % (ratio_S.min(), ratio_S.max(),
+                                                                        ratio_J.min(), ratio_J.max()))
+    if mode == "rs":
+        assert np.abs(ratio_S - 1).max() < 0.12 and np.abs(ratio_J - 1).max() < 0.12
+        assert abs(ratio_S.mean() - 1) < 0.02 and abs(ratio_J.mean() - 1) < 0.02
+    else:
+        assert np.abs(ratio_S - 1).max() > 0.2

@@ -328,8 +328,8 @@ RHO0_TWOPHASE = 0.75
 def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5, noise="lw"):
     """A three-dimensional lattice (the paper's model carried to D3Q19 or D3Q27): n^3 FP32
     (2 x 19 x 67 MB or 2 x 27 x 67 MB of populations at n = 256, larger than L2), cs2 = 1/3,
-    uncorrelated noise of Xi(0) (noise="lw") or, on D3Q19, the correlated noise Xi(k) built in
-    real space (noise="rs"), the PARAMS_LW relaxation times and kappa; or the two-phase model
+    uncorrelated noise of Xi(0) (noise="lw") or the correlated noise Xi(k) built in real space
+    (noise="rs"), the PARAMS_LW relaxation times and kappa; or the two-phase model
     (noise="local": the double well DOUBLE_WELL at mean density RHO0_TWOPHASE, kappa = 0.03,
     noise at the local density); one kernel launch per step.  Algorithmic bytes: Q FP32
     populations read and Q written per node."""
@@ -711,6 +711,7 @@ def main():
         variants.append(d3_variant(lbf, torch, hbm, 19))
         variants.append(d3_variant(lbf, torch, hbm, 19, noise="rs"))
         variants.append(d3_variant(lbf, torch, hbm, 27))
+        variants.append(d3_variant(lbf, torch, hbm, 27, noise="rs"))
 
     # the two-phase model (double well, noise at the local density) on D2Q9, D3Q19, D3Q27
     if not args.no_variants and not main_fp16:

@@ -18,17 +18,18 @@
  *     [GACV] Table II;
  *   - noise: spatially uncorrelated with covariance Xi(0) of [GACV] Eq. (noise-matrix-k0),
  *     xi = L nu, L the Cholesky factor of the block of the non-conserved modes (LB_NOISE_LW);
- *     or, on D3Q19, spatially correlated with covariance Xi(k) of [GACV] Eq. (noise-matrix) at
- *     every k (LB_NOISE_FULL_RS): with the ansatz of Eq. (f-correl-yeo) the advection drops
- *     out of the fluctuation-dissipation relation, so Xi(k) is Xi(0) at c_s^2(k) = cs2 +
- *     rho0 kappa s(k) (Eq. sound-speed-k, s the Laplacian symbol); only the (4,16) block
- *     depends on k, affinely in s, and s is multilinear in (cos kx, cos ky, cos kz), so Xi(k)
- *     is the multilinear interpolation of its values at the corners k in {0, pi}^3 (s = 0, 4,
- *     16/3, 4 for 0..3 components at pi).  Eight white 2-vector fields nu_abc per node
- *     (a, b, c = +-1; +1 for k = 0), each times the Cholesky factor L_abc of the (4,16) block
- *     at its corner, combined as h_d(r) = (1/8) sum_abc a^dx b^dy c^dz L_abc nu_abc(r), give
- *     (xi_4, xi_16)(r) = sum over d in {0,1}^3 of h_d(r - d), with exactly the covariance
- *     Xi(k); Xi must be positive semidefinite at s = 0, 4, 16/3.  The other modes as LB_NOISE_LW;
+ *     or spatially correlated with covariance Xi(k) of [GACV] Eq. (noise-matrix) at every k
+ *     (LB_NOISE_FULL_RS): with the ansatz of Eq. (f-correl-yeo) the advection drops out of the
+ *     fluctuation-dissipation relation, so Xi(k) is Xi(0) at c_s^2(k) = cs2 + rho0 kappa s(k)
+ *     (Eq. sound-speed-k, s the Laplacian symbol); only the coupled block (D3Q19 the modes 4
+ *     and 16, D3Q27 the seven listed below) depends on k, affinely in s, and s is multilinear
+ *     in (cos kx, cos ky, cos kz), so Xi(k) is the multilinear interpolation of its values at
+ *     the corners k in {0, pi}^3 (s = 0, 4, 16/3, 4 on D3Q19 and 0, 4, 16/3, 52/9 on D3Q27 for
+ *     0..3 components at pi).  Eight white vector fields nu_abc per node (a, b, c = +-1; +1
+ *     for k = 0), each times the Cholesky factor L_abc of the coupled block at its corner,
+ *     combined as h_d(r) = (1/8) sum_abc a^dx b^dy c^dz L_abc nu_abc(r), give the coupled
+ *     modes' noise sum over d in {0,1}^3 of h_d(r - d), with exactly the covariance Xi(k); Xi
+ *     must be positive semidefinite at those corner values.  The other modes as LB_NOISE_LW;
  *     or spatially uncorrelated with Xi(0) of a homogeneous system at each node's own density
  *     rho(r) and sound speed c_s^2(rho(r)) (LB_NOISE_LW_LOCAL, Sec. IV and Sec. V B for
  *     inhomogeneous systems): Xi(0) is rho (A + B c_s^2) entrywise, the coupled block is
@@ -59,7 +60,10 @@
  *     - (3/2) kappa |grad rho|^2, all others zero;
  *   - random numbers: tags 6, 7, 8 give 24 normals, the n-th going to the n-th non-conserved
  *     mode in mode order; the factor is diagonal except on the modes p_2z, p_2y, p_2y p_2z,
- *     p_2x, p_2x p_2z, p_2x p_2y, p_2x p_2y p_2z, which share a dense Cholesky block.
+ *     p_2x, p_2x p_2z, p_2x p_2y, p_2x p_2y p_2z, which share a dense Cholesky block (the
+ *     coupled block); the corner fields of LB_NOISE_FULL_RS from tags 12..18, normal 7 w + m
+ *     of their 56 (eight per draw, in tag order) giving component m of corner w = 4 ia + 2 ib +
+ *     ic.
  *
  * Conventions
  *   - Return codes and buffer locations are those of lbfluct.h (LB_OK, LB_E*, LB_HOST,
@@ -115,9 +119,9 @@ int lb3_set_stream(lb3_ctx* ctx, void* stream);
 
 /*
  * Sets kT, kappa, the relaxation times (each > 1/2) and the noise mode (LB_NOISE_OFF,
- * LB_NOISE_LW, LB_NOISE_LW_LOCAL, or on D3Q19 LB_NOISE_FULL_RS; others LB_EINVAL).  With
- * LB_NOISE_LW or LB_NOISE_FULL_RS and kT > 0, the c_s^2 of the linear theory about rho0 must be
- * positive and Xi(0) (with LB_NOISE_FULL_RS also Xi at s = 4 and 16/3) positive semidefinite
+ * LB_NOISE_LW, LB_NOISE_FULL_RS or LB_NOISE_LW_LOCAL; others LB_EINVAL).  With LB_NOISE_LW or
+ * LB_NOISE_FULL_RS and kT > 0, the c_s^2 of the linear theory about rho0 must be positive and
+ * Xi(0) (with LB_NOISE_FULL_RS also Xi at the other corner values of s) positive semidefinite
  * (D3Q19 at equal relaxation times: c_s^2 <= 5/9), else LB_ENOTPSD.  May be called again between
  * steps; the lattice state is kept.
  */

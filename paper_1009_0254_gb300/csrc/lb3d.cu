@@ -490,7 +490,7 @@ bool noise_factors(int lattice, const double* X, double sc[QMAX], double Lc[28])
 
 template <typename R>
 void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double sc[QMAX],
-               const double Lc[28], const double Lb[28], const double Lrs[9]) {
+               const double Lc[28], const double Lb[28], const double Lrs[9], const double Lrs27[112]) {
     a->nx = c->nx; a->ny = c->ny; a->nz = c->nz;
     a->pitch = c->geom.pitch; a->gx = c->geom.gx; a->PL = c->geom.PL; a->P = c->geom.P;
     a->err = c->err_dev;
@@ -508,6 +508,7 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
     for (int q = 0; q < 28; ++q) a->Lc[q] = (R)Lc[q];
     for (int q = 0; q < 28; ++q) a->Lb[q] = (R)Lb[q];
     for (int q = 0; q < 9; ++q) a->Lrs[q] = (R)Lrs[q];
+    for (int q = 0; q < 112; ++q) a->Lrs27[q] = (R)Lrs27[q];
     a->rk = lbf::make_round_keys(c->seed);
 }
 
@@ -576,7 +577,7 @@ int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed
         choose_grid(c, &c->cfg[k]);
     }
     // one tensor-map pair serves both configurations: they share the tile height when both
-    // stage by TMA (D3Q19: 8; D3Q27 has no correlated noise)
+    // stage by TMA (D3Q19: 8, D3Q27: 4)
     const Launch3* tl = c->cfg[0].tma ? &c->cfg[0] : (c->cfg[1].tma ? &c->cfg[1] : nullptr);
     if (tl) {
         for (int k = 0; k < 2; ++k)
@@ -624,15 +625,14 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
         return fail3(c, LB_EINVAL, "relaxation times must exceed 1/2");
     if (!(kT >= 0.0) || !std::isfinite(kT)) return fail3(c, LB_EINVAL, "kT must be >= 0");
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return fail3(c, LB_EINVAL, "kappa must be >= 0");
-    if (mode != LB_NOISE_OFF && mode != LB_NOISE_LW && mode != LB_NOISE_LW_LOCAL &&
-        !(mode == LB_NOISE_FULL_RS && c->lattice == 19))
+    if (mode != LB_NOISE_OFF && mode != LB_NOISE_LW && mode != LB_NOISE_LW_LOCAL && mode != LB_NOISE_FULL_RS)
         return fail3(c, LB_EINVAL,
-                     "the 3-D lattices take LB_NOISE_OFF, LB_NOISE_LW or LB_NOISE_LW_LOCAL (D3Q19 also LB_NOISE_FULL_RS)");
+                     "the 3-D lattices take LB_NOISE_OFF, LB_NOISE_LW, LB_NOISE_FULL_RS or LB_NOISE_LW_LOCAL");
     const bool homogeneous = mode == LB_NOISE_LW || mode == LB_NOISE_FULL_RS;
     if (homogeneous && kT > 0 && !(c->cs2 > 0.0))
         return fail3(c, LB_ENOTPSD, "the linear theory about rho0 has c_s^2 <= 0 (a mean density in the spinodal region)");
     std::vector<double> X((size_t)c->lattice * c->lattice);
-    double sc[QMAX] = {}, Lc[28] = {}, Lb[28] = {}, Lrs[9] = {};
+    double sc[QMAX] = {}, Lc[28] = {}, Lb[28] = {}, Lrs[9] = {}, Lrs27[112] = {};
     if (homogeneous && kT > 0) {
         xi_zero(c->lattice, c->rho0, c->cs2, kT, tau_s, tau_b, tau_ghost, X.data());
         if (!noise_factors(c->lattice, X.data(), sc, Lc)) return fail3(c, LB_ENOTPSD, "Xi(0) is not positive semidefinite");
@@ -661,7 +661,24 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
                 Lb[r * (r + 1) / 2 + q] = B(coupled[r], coupled[q]);
             }
     }
-    if (mode == LB_NOISE_FULL_RS && kT > 0) {
+    if (mode == LB_NOISE_FULL_RS && kT > 0 && c->lattice == 27) {
+        // Xi(k) is Xi(0) at c_s^2(k) = cs2 + rho0 kappa s(k), s = 6 (1 - prod (2 + cos k_a) / 3);
+        // the factors of its coupled block at the corner values s = 0, 4, 16/3, 52/9 (positive
+        // semidefinite there means at every k: Xi(k) is their multilinear interpolation)
+        const double svals[4] = {0.0, 4.0, 16.0 / 3.0, 52.0 / 9.0};
+        const std::vector<int> coupled(COUPLED27, COUPLED27 + 7);
+        for (int q = 0; q < 4; ++q) {
+            std::vector<double> Xs((size_t)27 * 27);
+            xi_zero27(c->rho0, c->cs2 + c->rho0 * kappa * svals[q], kT, -1.0 / tau_b, -1.0 / tau_s,
+                      -1.0 / tau_ghost, Xs.data());
+            std::vector<double> L7;
+            if (!cholesky_block(Xs.data(), 27, coupled, L7))
+                return fail3(c, LB_ENOTPSD, "Xi(k) is not positive semidefinite on the lattice");
+            for (int r = 0; r < 7; ++r)
+                for (int p2 = 0; p2 <= r; ++p2) Lrs27[28 * q + r * (r + 1) / 2 + p2] = L7[r * 7 + p2];
+        }
+    }
+    if (mode == LB_NOISE_FULL_RS && kT > 0 && c->lattice == 19) {
         // Xi(k) is Xi(0) at c_s^2(k) = cs2 + rho0 kappa s(k); the factors of its (4,16) block at
         // the corner values s = 0, 4, 16/3 (positive semidefinite there means at every k)
         const double svals[3] = {0.0, 4.0, 16.0 / 3.0};
@@ -681,8 +698,8 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
     c->kappa = kappa;
     c->tau_s = tau_s; c->tau_b = tau_b; c->tau_g = tau_ghost;
     c->noise_mode = mode;
-    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs);
-    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs);
+    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs, Lrs27);
+    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs, Lrs27);
     c->have_params = true;
     return LB_OK;
 }

@@ -119,6 +119,8 @@ struct Step3Args {
     R cq[4];                      // local noise: c_s^2(rho0 + dr) = cq0 + dr (cq1 + dr (cq2 + dr cq3))
     R Lrs[9];                     // D3Q19 correlated noise: Cholesky factors (L11, L21, L22) of the
                                   // (4,16) block of Xi at s = 0, 4, 16/3
+    R Lrs27[112];                 // D3Q27 correlated noise: Cholesky factors of the coupled block
+                                  // of Xi at s = 0, 4, 16/3, 52/9, 28 each (lower triangle, row-major)
     uint32_t t_lo, t_hi;
     lbf::RoundKeys rk;
 };
@@ -322,8 +324,13 @@ __device__ __forceinline__ void store_node3(const Step3Args<R>& a, I zo, int x, 
     }
 }
 
-// D3Q19 correlated noise: the tags of the two draws of the eight corner fields
+// correlated noise: the first tag of the draws of the eight corner fields (D3Q19: two draws,
+// word w -> the 2-vector of corner w; D3Q27: seven draws, normal 7 w + m -> component m of the
+// 7-vector of corner w) and the number of coupled components of a corner field
 constexpr uint32_t TAG_RS0 = 10;
+constexpr uint32_t TAG_RS27 = 12;
+template <typename LAT>
+__host__ __device__ constexpr int rs_components() { return LAT::Q == 19 ? 2 : 7; }
 
 // Shared-memory geometry of one raw slot.  Copies (TMA = false): per population the pulled
 // values of the tile and its ring, RX x RY, already shifted by -c_i.  TMA: per box the GM
@@ -349,13 +356,14 @@ struct Slot3 {
 
 // Shared memory of the staged kernel: [SLOTS][SLOT] raw values, the mbarriers (TMA), the
 // density ring [3][RN], and with correlated noise (MODE 3) the 2x2x2-box contributions: for
-// the tile plus its left column and bottom row, the in-plane half (four 2-vectors) of the
-// current plane and the upward half of the current and the previous plane.
+// the tile plus its left column and bottom row, the in-plane half (four NV-vectors, NV the
+// coupled components) of the current plane and the upward half of the current and the
+// previous plane.
 template <typename LAT, typename R, int TY, int SLOTS, int MODE, bool TMA>
 constexpr int staged_smem_bytes() {
     using S = Slot3<LAT, R, TY, TMA>;
-    return (SLOTS * S::SLOT + 3 * S::RN + (MODE == 3 ? 24 * (LAT::TX + 1) * (TY + 1) : 0)) * (int)sizeof(R) +
-           (TMA ? 16 * ((SLOTS + 1) / 2) : 0);
+    constexpr int HV = MODE == 3 ? 12 * rs_components<LAT>() * (LAT::TX + 1) * (TY + 1) : 0;
+    return (SLOTS * S::SLOT + 3 * S::RN + HV) * (int)sizeof(R) + (TMA ? 16 * ((SLOTS + 1) / 2) : 0);
 }
 
 // resident CTAs per SM the register budget is sized for: as many as the shared memory admits
@@ -378,9 +386,9 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
     constexpr int RAW_BYTES = SLOTS * SL * (int)sizeof(R);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem3 + RAW_BYTES);         // TMA: one per slot
     R* rs = reinterpret_cast<R*>(smem3 + RAW_BYTES + (TMA ? 16 * ((SLOTS + 1) / 2) : 0));   // [3][RN]
-    constexpr int HW = TX + 1, HN = HW * (TY + 1);
-    R* Hin = rs + 3 * RN;                                   // MODE 3: [8][HN] in-plane half
-    R* Hup = Hin + 8 * HN;                                  // MODE 3: [2][8][HN] upward half
+    constexpr int HW = TX + 1, HN = HW * (TY + 1), NV = rs_components<LAT>();
+    R* Hin = rs + 3 * RN;                                   // MODE 3: [4][NV][HN] in-plane half
+    R* Hup = Hin + 4 * NV * HN;                             // MODE 3: [2][4][NV][HN] upward half
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch, GX = a.gx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * a.zc;
@@ -521,6 +529,52 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
             gx = wrap_lo(gx, nx);
             gy = wrap_lo(gy, ny);
             const uint32_t node = ((uint32_t)zc * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx;
+            if constexpr (LAT::Q == 27) {
+                // D3Q27: eight 7-vectors; corner class = components at pi (s = 0, 4, 16/3, 52/9)
+                R nu[56];
+#pragma unroll
+                for (int d = 0; d < 7; ++d) {
+                    const uint4 rw = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS27 + d), a.rk);
+                    lbf::gauss_word(rw.x, &nu[8 * d + 0], &nu[8 * d + 1]);
+                    lbf::gauss_word(rw.y, &nu[8 * d + 2], &nu[8 * d + 3]);
+                    lbf::gauss_word(rw.z, &nu[8 * d + 4], &nu[8 * d + 5]);
+                    lbf::gauss_word(rw.w, &nu[8 * d + 6], &nu[8 * d + 7]);
+                }
+                R v[8][7];
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                    const int cls = (w & 1) + ((w >> 1) & 1) + ((w >> 2) & 1);
+                    const R* Lw = a.Lrs27 + 28 * cls;
+#pragma unroll
+                    for (int r = 0; r < 7; ++r) {
+                        R acc = R(0);
+#pragma unroll
+                        for (int q = 0; q <= r; ++q) acc += Lw[r * (r + 1) / 2 + q] * nu[7 * w + q];
+                        v[w][r] = acc;
+                    }
+                }
+#pragma unroll
+                for (int b = 1; b < 8; b <<= 1)
+#pragma unroll
+                    for (int w = 0; w < 8; ++w)
+                        if (!(w & b)) {
+#pragma unroll
+                            for (int r = 0; r < 7; ++r) {
+                                const R x = v[w][r], y = v[w | b][r];
+                                v[w][r] = x + y;
+                                v[w | b][r] = x - y;
+                            }
+                        }
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    R* dst = (m & 1) ? Hup + ub * 4 * NV * HN : Hin;
+                    if (!(m & 1) && !keep_in) continue;
+                    const int j = m >> 1;
+#pragma unroll
+                    for (int r = 0; r < 7; ++r) dst[(j * NV + r) * HN + p] = R(0.125) * v[m][r];
+                }
+                continue;
+            }
             const uint4 r0 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0), a.rk);
             const uint4 r1 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0 + 1), a.rk);
             const uint32_t wd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
@@ -545,11 +599,11 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
                     }
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                R* dst = (m & 1) ? Hup + ub * 8 * HN : Hin;
+                R* dst = (m & 1) ? Hup + ub * 4 * NV * HN : Hin;
                 if (!(m & 1) && !keep_in) continue;
                 const int j = m >> 1;
-                dst[(2 * j) * HN + p] = R(0.125) * vx[m];
-                dst[(2 * j + 1) * HN + p] = R(0.125) * vy[m];
+                dst[(j * NV) * HN + p] = R(0.125) * vx[m];
+                dst[(j * NV + 1) * HN + p] = R(0.125) * vy[m];
             }
         }
     };
@@ -583,12 +637,12 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
                 // (xi_4, xi_16) = sum over the box: h of r - (dx, dy, 0) from this plane and of
                 // r - (dx, dy, 1) from the previous one
                 R s4 = R(0), s16 = R(0);
-                const R* hu = Hup + hb * 8 * HN;
+                const R* hu = Hup + hb * 4 * NV * HN;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int q = (ly - (j & 1) + 1) * HW + (lx - (j >> 1) + 1);
-                    s4 += Hin[(2 * j) * HN + q] + hu[(2 * j) * HN + q];
-                    s16 += Hin[(2 * j + 1) * HN + q] + hu[(2 * j + 1) * HN + q];
+                    s4 += Hin[(j * NV) * HN + q] + hu[(j * NV) * HN + q];
+                    s16 += Hin[(j * NV + 1) * HN + q] + hu[(j * NV + 1) * HN + q];
                 }
                 xi[4] = s4;
                 xi[16] = s16;
@@ -603,8 +657,23 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
                 const R* pl = cz == 0 ? d0 : (cz > 0 ? dp : dm);
                 nb[i] = pl[LAT::c(i, 1) * RX + LAT::c(i, 0)];
             }
-            if (MODE == 1) normals27(a, node, xi);
+            if (MODE == 1 || MODE == 3) normals27(a, node, xi);
             if (MODE == 4) normals27_local(a, node, nb[0], xi);
+            if constexpr (MODE == 3) {
+                // the coupled modes: the 2x2x2-box sums of this plane's in-plane halves and the
+                // previous plane's upward halves
+                const R* hu = Hup + hb * 4 * NV * HN;
+#pragma unroll
+                for (int r = 0; r < 7; ++r) {
+                    R sacc = R(0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int q = (ly - (j & 1) + 1) * HW + (lx - (j >> 1) + 1);
+                        sacc += Hin[(j * NV + r) * HN + q] + hu[(j * NV + r) * HN + q];
+                    }
+                    xi[coupled27(r)] = sacc;
+                }
+            }
             collide27(a.co, f, nb, xi, o);
         }
         store_node3<LAT, R, I>(a, (I)z * PLI, x, y, o);
@@ -774,20 +843,24 @@ struct Launch3 {
 template <typename LAT, typename R, int TY, int MODE, typename I, int SLOTS, bool TMA>
 static cudaError_t launch_staged(const Step3Args<R>& a, const CUtensorMap* map, dim3 grid, cudaStream_t s) {
     constexpr int smem = staged_smem_bytes<LAT, R, TY, SLOTS, MODE, TMA>();
-    auto kern = step3_staged_kernel<LAT, R, TY, MODE, I, SLOTS, TMA>;
-    // the shared-memory limit is a per-device attribute of the function: set it once per
-    // device (a repeated set from a concurrent first launch is harmless)
-    static std::atomic<unsigned> done{0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const unsigned bit = 1u << (dev & 31);
-    if (!(done.load(std::memory_order_acquire) & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        done.fetch_or(bit, std::memory_order_release);
+    if constexpr (smem > 227 * 1024) {
+        return cudaErrorInvalidConfiguration;      // this variant's shared memory does not fit a CTA
+    } else {
+        auto kern = step3_staged_kernel<LAT, R, TY, MODE, I, SLOTS, TMA>;
+        // the shared-memory limit is a per-device attribute of the function: set it once per
+        // device (a repeated set from a concurrent first launch is harmless)
+        static std::atomic<unsigned> done{0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const unsigned bit = 1u << (dev & 31);
+        if (!(done.load(std::memory_order_acquire) & bit)) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            done.fetch_or(bit, std::memory_order_release);
+        }
+        kern<<<grid, LAT::TX * TY, smem, s>>>(*map, a);
+        return cudaGetLastError();
     }
-    kern<<<grid, LAT::TX * TY, smem, s>>>(*map, a);
-    return cudaGetLastError();
 }
 
 template <typename LAT, typename R, int TY, int MODE, int SLOTS, bool TMA>
@@ -828,9 +901,7 @@ static cudaError_t launch_mode3(const Step3Args<R>& a, const CUtensorMap* map, c
 
 template <typename LAT, typename R>
 cudaError_t launch_lattice(const Step3Args<R>& a, const CUtensorMap* map, const Launch3& L, cudaStream_t s) {
-    if constexpr (LAT::Q == 19) {
-        if (L.kmode == 3) return launch_mode3<LAT, R, 3>(a, map, L, s);
-    }
+    if (L.kmode == 3) return launch_mode3<LAT, R, 3>(a, map, L, s);
     if (L.kmode == 4) return launch_mode3<LAT, R, 4>(a, map, L, s);
     return L.kmode ? launch_mode3<LAT, R, 1>(a, map, L, s) : launch_mode3<LAT, R, 0>(a, map, L, s);
 }

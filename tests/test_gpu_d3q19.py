@@ -292,10 +292,6 @@ def test_correlated_noise_refuses_an_indefinite_Xi():
         g.set_params(1e-4, 0.06, 0.8, 1.1, 0.9, lbf.LB_NOISE_FULL_RS)
     assert e.value.code == lbf.LB_ENOTPSD
     g.set_params(1e-4, 0.06, 0.8, 1.1, 0.9, lbf.LB_NOISE_LW)           # Xi(0) alone is fine
-    h = lbf.Lattice3(8, 8, 8, lattice=lbf.LB_D3Q27)
-    with pytest.raises(lbf.LBError) as e:
-        h.set_params(1e-4, 0.01, 0.8, 1.1, 0.9, lbf.LB_NOISE_FULL_RS)
-    assert e.value.code == lbf.LB_EINVAL
 
 
 def _patch_step_rs(m, n, centre, seed, t, L, Ls, amp):

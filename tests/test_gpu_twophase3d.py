@@ -1,7 +1,8 @@
 """The two-phase model on the 3-D lattices (include/lbfluct3d.h: lb3_set_eos, LB_NOISE_LW_LOCAL)
 against the FP64 oracles (oracle/d3q19.py, oracle/d3q27.py): element by element on liquid
 slabs in vapour with the Landau double well, without noise, with the noise at the local
-density and, on a liquid-side lattice, with the long-wavelength noise; the re-basing of the
+density and, on a liquid-side lattice, with the long-wavelength and the correlated noise; the
+re-basing of the
 stored state by lb3_set_eos; the local noise against the uniform one at uniform density; the
 error paths; and a flat interface relaxing to the tanh profile of width xi of Eq.
 (interf-width)."""
@@ -188,3 +189,27 @@ def test_flat_interface_relaxes_to_the_tanh_profile_of_width_xi(lattice):
     print("D3Q%d xi: Eq. (interf-width) %.4f, stationary profile %.4f" % (lattice, xi, p[1]))
     assert abs(p[1] / xi - 1) < 0.7 / xi ** 2
     assert abs(rho[0, 0, 64] - WELL.rhoL) < 1e-3 and abs(rho[0, 0, 0] - WELL.rhoV) < 1e-3
+
+
+@pytest.mark.parametrize("lattice", [19, 27])
+def test_correlated_noise_on_a_double_well_lattice(lattice):
+    # rho0 = 1 (the liquid density, c_s^2 = 0.02): the correlated noise Xi(k) of the linear
+    # theory about rho0 (c_s^2(k) = 0.02 + rho0 kappa s(k)) with the double well's bulk pressure
+    # in every node's equilibrium
+    mod = ORACLE[lattice]
+    nx, ny, nz = 21, 6, 5
+    params = (1e-4, 0.04, 0.8, 1.1, 0.9)
+    m = mod.Model(1.0, WELL.cs2(1.0), p0_rest=WELL.p0(1.0))
+    f0 = m.rest()[:, None, None, None] * (1.0 + synth.gaussian_field((mod.Q, nz, ny, nx), seed=6, scale=0.02))
+    g = lbf.Lattice3(nx, ny, nz, seed=9, rho0=1.0, lattice=lattice)
+    g.set_eos(lbf.LB_EOS_DOUBLE_WELL, WELL.beta, WELL.rhoV, WELL.rhoL)
+    g.set_params(*params, lbf.LB_NOISE_FULL_RS)
+    o = mod.Lattice(nx, ny, nz, rho0=1.0, seed=9, eos=WELL)
+    o.set_params(*params, mod.NOISE_FULL_RS)
+    g.set_populations(f0, t=0)
+    o.f = f0.copy()
+    g.step(5)
+    o.step(5)
+    err = np.abs(g.populations() - o.f).max()
+    print("D3Q%d RS double well: %.2e" % (lattice, err))
+    assert err <= TOL

@@ -269,7 +269,7 @@ struct lb3_ctx {
     double* stage = nullptr;        // one FP64 plane
     double* partial = nullptr;      // SUM3_BLOCKS x 4
     int* err_dev = nullptr;         // device error word of the TMA waits
-    CUtensorMap maps[2];            // TMA: the population buffers (box of the staged kernel)
+    CUtensorMap maps[2][2];         // TMA: per configuration, the population buffers (box of its tile)
     int cur = 0;
     bool have_params = false;
     int noise_mode = LB_NOISE_OFF;
@@ -370,19 +370,20 @@ int record_timing3(lb3_ctx* c, cudaEvent_t* start, cudaEvent_t* stop) {
 }
 
 // The step kernel of a context.  Measured on GB300 at 256^3 (FP32): both lattices stage by
-// TMA in two slots (D3Q19 with and without the correlated noise: three CTAs per SM at 80
-// registers, against two with three slots; D3Q27 on 32 x 4 tiles).  FP64 stages by copies
+// TMA in two slots (D3Q19 without the correlated noise on 32 x 6 tiles, four CTAs per SM at
+// 80 registers: 620 against 635 us on 32 x 8 and 681 us with three slots; with it on 32 x 8,
+// 956 against 989 us on 32 x 6; D3Q27 on 32 x 4 tiles).  FP64 stages by copies
 // (D3Q19 in three slots, D3Q27 in two; TMA boxes of doubles would fit one CTA per SM).
 // LBFLUCT3_KERNEL=plain (D3Q19), LBFLUCT3_STAGE=tma|copy and LBFLUCT3_SLOTS=2|3 override
 // the choice (32 x 6 tiles for D3Q27 by TMA measured 1063 against 1007 us: three CTAs per SM
 // at 96 registers with spills).
-Launch3 default_cfg(int lattice, int precision) {
+Launch3 default_cfg(int lattice, int precision, bool rs) {
     Launch3 L{};
     L.kmode = 0;
     L.plain = false;
     L.tma = precision == LB_FP32;
     L.slots = (L.tma || lattice == 27) ? 2 : 3;
-    L.ty = lattice == 19 ? 8 : 4;
+    L.ty = lattice == 19 ? ((L.tma && !rs) ? 6 : 8) : 4;
     return L;
 }
 
@@ -395,6 +396,7 @@ Launch3 env_cfg(Launch3 L, int lattice, int precision, bool rs) {
     }
     if (const char* sv = std::getenv("LBFLUCT3_SLOTS")) L.slots = std::atoi(sv) == 2 ? 2 : 3;
     if (lattice == 27 && L.tma) L.slots = 2;
+    if (lattice == 19) L.ty = (L.tma && !rs) ? 6 : 8;      // the tiles the kernels are built for
     return L;
 }
 
@@ -514,11 +516,12 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
 
 template <typename R>
 cudaError_t launch_any(lb3_ctx* c, Step3Args<R> a, int kmode) {
-    Launch3 L = c->cfg[kmode == 3 ? 1 : 0];
+    const int q = kmode == 3 ? 1 : 0;
+    Launch3 L = c->cfg[q];
     L.kmode = kmode;
     if (kmode == 4) L.plain = false;      // the plain kernel draws no local noise
     a.zc = L.zc;
-    const CUtensorMap* map = &c->maps[c->cur];
+    const CUtensorMap* map = &c->maps[q][c->cur];
     return c->lattice == 19 ? launch_lattice<Lat19, R>(a, map, L, c->stream)
                             : launch_lattice<Lat27, R>(a, map, L, c->stream);
 }
@@ -573,15 +576,14 @@ int lb3_create(int nx, int ny, int nz, int lattice, int precision, uint64_t seed
     }
     std::memset(c->maps, 0, sizeof(c->maps));
     for (int k = 0; k < 2; ++k) {
-        c->cfg[k] = env_cfg(default_cfg(lattice, precision), lattice, precision, k == 1);
+        c->cfg[k] = env_cfg(default_cfg(lattice, precision, k == 1), lattice, precision, k == 1);
         choose_grid(c, &c->cfg[k]);
     }
-    // one tensor-map pair serves both configurations: they share the tile height when both
-    // stage by TMA (D3Q19: 8, D3Q27: 4)
-    const Launch3* tl = c->cfg[0].tma ? &c->cfg[0] : (c->cfg[1].tma ? &c->cfg[1] : nullptr);
-    if (tl) {
+    // a tensor-map pair per configuration that stages by TMA (its tile height sets the box)
+    for (int q = 0; q < 2; ++q) {
+        if (!c->cfg[q].tma) continue;
         for (int k = 0; k < 2; ++k)
-            if (!make_map3(c, c->pop[k], tl->ty, &c->maps[k])) {
+            if (!make_map3(c, c->pop[k], c->cfg[q].ty, &c->maps[q][k])) {
                 cudaFree(c->ws);
                 delete c;
                 return fail3(nullptr, LB_ECUDA, "lb3_create: cuTensorMapEncodeTiled failed");

@@ -870,8 +870,9 @@ static cudaError_t launch_width(const Step3Args<R>& a, const CUtensorMap* map, d
                   : launch_staged<LAT, R, TY, MODE, unsigned long long, SLOTS, TMA>(a, map, grid, s);
 }
 
-// the staged variants a lattice offers, on 32 x 8 (D3Q19) or 32 x 4 (D3Q27) tiles: by copies
-// in two or three slots, and in FP32 by TMA (D3Q19 two or three slots, D3Q27 two)
+// the staged variants a lattice offers: by copies in two or three slots on 32 x 8 (D3Q19) or
+// 32 x 4 (D3Q27) tiles, and in FP32 by TMA (D3Q19 two or three slots on 32 x 6 tiles, 32 x 8
+// with the correlated noise; D3Q27 two slots on 32 x 4)
 template <typename LAT, typename R, int MODE>
 static cudaError_t launch_mode3(const Step3Args<R>& a, const CUtensorMap* map, const Launch3& L, cudaStream_t s) {
     constexpr bool F32 = sizeof(R) == 4;
@@ -884,9 +885,11 @@ static cudaError_t launch_mode3(const Step3Args<R>& a, const CUtensorMap* map, c
             return cudaErrorInvalidValue;
         }
         if constexpr (F32) {
+            // TMA: 32 x 6 tiles (four CTAs per SM in two slots), 32 x 8 with the correlated noise
+            constexpr int TYT = MODE == 3 ? 8 : 6;
             if (L.tma)
-                return L.slots == 2 ? launch_width<LAT, R, 8, MODE, 2, true>(a, map, L.grid, s)
-                                    : launch_width<LAT, R, 8, MODE, 3, true>(a, map, L.grid, s);
+                return L.slots == 2 ? launch_width<LAT, R, TYT, MODE, 2, true>(a, map, L.grid, s)
+                                    : launch_width<LAT, R, TYT, MODE, 3, true>(a, map, L.grid, s);
         }
         return L.slots == 2 ? launch_width<LAT, R, 8, MODE, 2, false>(a, map, L.grid, s)
                             : launch_width<LAT, R, 8, MODE, 3, false>(a, map, L.grid, s);

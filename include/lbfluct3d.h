@@ -26,10 +26,20 @@
  *     in (cos kx, cos ky, cos kz), so Xi(k) is the multilinear interpolation of its values at
  *     the corners k in {0, pi}^3 (s = 0, 4, 16/3, 4 on D3Q19 and 0, 4, 16/3, 52/9 on D3Q27 for
  *     0..3 components at pi).  Eight white vector fields nu_abc per node (a, b, c = +-1; +1
- *     for k = 0), each times the Cholesky factor L_abc of the coupled block at its corner,
- *     combined as h_d(r) = (1/8) sum_abc a^dx b^dy c^dz L_abc nu_abc(r), give the coupled
- *     modes' noise sum over d in {0,1}^3 of h_d(r - d), with exactly the covariance Xi(k); Xi
- *     must be positive semidefinite at those corner values.  The other modes as LB_NOISE_LW;
+ *     for k = 0), each times a factor L_abc with L_abc L_abc^T the value at its corner of the
+ *     part built in real space, combined as h_d(r) = (1/8) sum_abc a^dx b^dy c^dz L_abc
+ *     nu_abc(r), give the noise sum over d in {0,1}^3 of h_d(r - d), whose covariance is the
+ *     multilinear interpolation of the corner values.  D3Q19: the whole (4,16) block, L_abc its
+ *     Cholesky factor at the corner.  D3Q27: the block is X0 + s(k) D with D = p p^T - q q^T
+ *     of rank two (the slope of Xi(0) in c_s^2), so it is C + s(k) p p^T + (S - s(k)) q q^T,
+ *     S = 52/9 and C = X0 - S q q^T: a white part with factor chol(C) (on the long-wavelength
+ *     normals of the coupled modes) plus p phi_p + q phi_q, the scalar fields phi_p, phi_q
+ *     built as above with the corner amplitudes sqrt(s) and sqrt(S - s); p and q come from the
+ *     eigenvectors of L0^-1 D L0^-T (X0 = L0 L0^T), the split for which C is positive
+ *     semidefinite exactly when the block at s = S is, and the first component of p (of q) of
+ *     magnitude at least half its largest is positive.  The covariance is exactly Xi(k); Xi
+ *     must be positive semidefinite at the corner values (D3Q27: at s = 0 and s = S, with the
+ *     block at s = 0 positive definite).  The other modes as LB_NOISE_LW;
  *     or spatially uncorrelated with Xi(0) of a homogeneous system at each node's own density
  *     rho(r) and sound speed c_s^2(rho(r)) (LB_NOISE_LW_LOCAL, Sec. IV and Sec. V B for
  *     inhomogeneous systems): Xi(0) is rho (A + B c_s^2) entrywise, the coupled block is
@@ -61,9 +71,8 @@
  *   - random numbers: tags 6, 7, 8 give 24 normals, the n-th going to the n-th non-conserved
  *     mode in mode order; the factor is diagonal except on the modes p_2z, p_2y, p_2y p_2z,
  *     p_2x, p_2x p_2z, p_2x p_2y, p_2x p_2y p_2z, which share a dense Cholesky block (the
- *     coupled block); the corner fields of LB_NOISE_FULL_RS from tags 12..18, normal 7 w + m
- *     of their 56 (eight per draw, in tag order) giving component m of corner w = 4 ia + 2 ib +
- *     ic.
+ *     coupled block); the corner fields of LB_NOISE_FULL_RS from tags 12 and 13, word w of the
+ *     pair giving (nu of phi_p, nu of phi_q) of corner w = 4 ia + 2 ib + ic.
  *
  * Conventions
  *   - Return codes and buffer locations are those of lbfluct.h (LB_OK, LB_E*, LB_HOST,

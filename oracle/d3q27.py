@@ -43,14 +43,25 @@ Correlated noise (Sec. III C, Eq. noise-matrix at every k), as ``oracle.d3q19``:
 ansatz the advection drops out of the fluctuation-dissipation relation, so Xi(k) is Xi(0) at
 c_s^2(k) = cs2 + rho0 kappa s(k), s the symbol of the D3Q27 Laplacian,
 s = 6 (1 - prod_a (2 + cos k_a) / 3), which is multilinear in the three cosines; Xi(0) is
-affine in c_s^2 and only its seven coupled modes depend on it, so Xi(k) is the multilinear
-interpolation of its values at the corners k in {0, pi}^3 (s = 0, 4, 16/3, 52/9 for 0..3
-components at pi).  Eight white 7-vector fields nu_w per node (w = 4 ia + 2 ib + ic, a set bit
-for a component at pi), each times the Cholesky factor of the coupled block at its corner,
-combined as h_d = (1/8) sum_w (-1)^{popcount(w & d)} L_w nu_w and summed over the 2x2x2 box,
-xi(r) = sum_d h_d(r - d), give the coupled modes' noise with covariance Xi(k) at every k; the
-other modes keep the long-wavelength noise.  Draws: tags 12..18, normal n = 7 w + m of their
-56 (in tag order, eight per draw) is component m of corner w.
+affine in c_s^2 and only its seven coupled modes depend on it: their block is
+X(k) = X0 + s(k) D, X0 the block at k = 0 and D its slope (rho0 kappa times the slope of
+Xi(0) in c_s^2), of rank two with one positive and one negative eigenvalue.  With S = 52/9
+the largest s (k = (pi, pi, pi)) and D = p p^T - q q^T,
+
+    X(k) = C + s(k) p p^T + (S - s(k)) q q^T,    C = X0 - S q q^T,
+
+so the coupled noise is C^(1/2) nu (white) plus p phi_p + q phi_q, two scalar fields whose
+spectra s(k) and S - s(k) are, like s, multilinear in the cosines: the multilinear
+interpolation of their corner values (s = 0, 4, 16/3, 52/9 at 0..3 components at pi).  A
+field with corner values sigma_w is built from eight white scalar fields nu_w per node
+(w = 4 ia + 2 ib + ic, a set bit for a component at pi) as h_d = (1/8) sum_w
+(-1)^{popcount(w & d)} sqrt(sigma_w) nu_w, summed over the 2x2x2 box: phi(r) = sum_d h_d(r - d).
+Of the splits p, q of D the one that whitens X0 (eigenvectors of L0^-1 D L0^-T, X0 = L0 L0^T)
+makes C positive semidefinite exactly when X at k = (pi, pi, pi) is, which with X0 positive
+definite is the condition for Xi(k) at every k.  The white part uses the long-wavelength
+normals of the coupled modes (their factor becomes that of C); the other modes keep the
+long-wavelength noise.  Draws: tags 12 and 13, word w (in tag order) gives the pair
+(nu_w of phi_p, nu_w of phi_q) of corner w.
 
 Indices: velocity i = 9 ix + 3 iy + iz with c = (v[ix], v[iy], v[iz]), v = (0, 1, -1); mode
 a = 9 ax + 3 ay + az for p_ax(c_x) p_ay(c_y) p_az(c_z).  f[i, z, y, x].
@@ -329,7 +340,7 @@ def noise_lw_local(model: Model, rho: np.ndarray, c2, seed: int, step_index: int
 
 # --- correlated noise (Sec. III C, Eq. noise-matrix) ------------------------------------------
 
-TAG_RS = tuple(range(12, 19))
+TAG_RS = (12, 13)
 
 
 def lattice_s(kx, ky, kz):
@@ -359,31 +370,69 @@ CORNERS = [(1 if (w >> 2) & 1 == 0 else -1, 1 if (w >> 1) & 1 == 0 else -1, 1 if
            for w in range(8)]
 
 
-def rs_factors(model: Model) -> np.ndarray:
-    """7x7 Cholesky factors of the coupled block of Xi at the eight corners (sign +1: k = 0)."""
-    out = np.zeros((8, 7, 7))
-    for w, (a, b, c) in enumerate(CORNERS):
-        k = [0.0 if v > 0 else np.pi for v in (a, b, c)]
-        X = Xi_k(model, *k)
-        out[w] = cholesky_psd(X[np.ix_(COUPLED, COUPLED)])
-    return out
+def s_max() -> float:
+    """The largest value of s(k): at k = (pi, pi, pi)."""
+    return float(lattice_s(np.pi, np.pi, np.pi))
+
+
+def _positive_convention(v: np.ndarray) -> np.ndarray:
+    """v with the sign that makes its first component of magnitude at least half its
+    largest positive (the split's vectors are defined up to sign)."""
+    big = np.abs(v) >= 0.5 * np.abs(v).max()
+    return -v if v[np.argmax(big)] < 0 else v
+
+
+def rs_split(model: Model):
+    """(Lw, p, q): the rank-two split of the coupled block of Xi(k) = X0 + s(k) D (module
+    docstring).  Lw is the Cholesky factor of the white part C = X0 - S q q^T; p and q the
+    vectors of D = p p^T - q q^T that whiten X0: with X0 = L0 L0^T and
+    L0^-1 D L0^-T = mu+ y+ y+^T + mu- y- y-^T, p = sqrt(mu+) L0 y+ and q = sqrt(-mu-) L0 y-, so
+    C = L0 (I - S |mu-| y- y-^T) L0^T.  Raises when X0 is not positive definite, when D has
+    more than one eigenvalue of either sign, or when C is not positive semidefinite (X at
+    k = (pi, pi, pi) is not)."""
+    S = s_max()
+    X0 = Xi_k(model, 0.0, 0.0, 0.0)[np.ix_(COUPLED, COUPLED)]
+    XS = Xi_k(model, np.pi, np.pi, np.pi)[np.ix_(COUPLED, COUPLED)]
+    D = (XS - X0) / S
+    L0 = np.linalg.cholesky(X0)
+    Y = np.linalg.solve(L0, np.linalg.solve(L0, D).T)         # L0^-1 D L0^-T (symmetric)
+    Y = 0.5 * (Y + Y.T)
+    mu, E = np.linalg.eigh(Y)
+    # Y is relative to X0: eigenvalues below 1e-9 in magnitude are rounding (kappa = 0: none)
+    if np.sum(mu > 1e-9) > 1 or np.sum(mu < -1e-9) > 1:
+        raise ValueError("the slope of the coupled block is not of rank two with one eigenvalue of each sign")
+    mp = mu[-1] if mu[-1] > 1e-9 else 0.0
+    mm = mu[0] if mu[0] < -1e-9 else 0.0
+    p = _positive_convention(np.sqrt(mp) * (L0 @ E[:, -1])) if mp > 0 else np.zeros(7)
+    q = _positive_convention(np.sqrt(-mm) * (L0 @ E[:, 0])) if mm < 0 else np.zeros(7)
+    if 1.0 - S * (-mm) < -1e-9:
+        raise ValueError("Xi(k) is not positive semidefinite at k = (pi, pi, pi)")
+    C = X0 - S * np.outer(q, q)
+    return cholesky_psd(0.5 * (C + C.T)), p, q
+
+
+def rs_weights():
+    """(a_p, a_q)[w]: sqrt(s) and sqrt(S - s) at corner w, the amplitudes that give phi_p and
+    phi_q the spectra s(k) and S - s(k)."""
+    S = s_max()
+    sw = np.array([float(lattice_s(*[0.0 if v > 0 else np.pi for v in CORNERS[w]])) for w in range(8)])
+    return np.sqrt(np.maximum(sw, 0.0)), np.sqrt(np.maximum(S - sw, 0.0))
 
 
 def rs_fields(nx, ny, nz, seed: int, step_index: int) -> np.ndarray:
-    """nu[w, 7, z, y, x]: the white 7-vector of corner w at every node."""
+    """nu[w, 2, z, y, x]: the white pair (phi_p's, phi_q's) of corner w at every node."""
     n = nx * ny * nz
     idx = np.arange(n, dtype=np.uint32)
-    g = np.concatenate([normals(idx, seed, step_index, t) for t in TAG_RS], axis=1)     # (n, 56)
-    return g.T.reshape(8, 7, nz, ny, nx)
+    g = np.concatenate([normals(idx, seed, step_index, t) for t in TAG_RS], axis=1)     # (n, 16)
+    return g.T.reshape(8, 2, nz, ny, nx)
 
 
-def xi_coupled_rs(model: Model, nx, ny, nz, seed: int, step_index: int, Ls=None) -> np.ndarray:
-    """xi[7, z, y, x] of the coupled modes (in COUPLED order) by the real-space construction."""
-    if Ls is None:
-        Ls = rs_factors(model)
+def rs_scalar_fields(nx, ny, nz, seed: int, step_index: int) -> np.ndarray:
+    """(phi_p, phi_q)[2, z, y, x]: the two box-filtered scalar fields."""
     nu = rs_fields(nx, ny, nz, seed, step_index)
-    v = np.einsum("wab,wb...->wa...", Ls, nu)
-    out = np.zeros((7, nz, ny, nx))
+    ap, aq = rs_weights()
+    v = np.stack([ap[:, None, None, None] * nu[:, 0], aq[:, None, None, None] * nu[:, 1]], axis=1)
+    out = np.zeros((2, nz, ny, nx))
     for dz in (0, 1):
         for dy in (0, 1):
             for dx in (0, 1):
@@ -391,6 +440,23 @@ def xi_coupled_rs(model: Model, nx, ny, nz, seed: int, step_index: int, Ls=None)
                         for w in range(8)) / 8.0
                 out += np.roll(h, shift=(dz, dy, dx), axis=(1, 2, 3))      # h_d(r - d)
     return out
+
+
+def xi_coupled_rs(model: Model, nx, ny, nz, seed: int, step_index: int, split=None) -> np.ndarray:
+    """xi[7, z, y, x]: the k-dependent part p phi_p + q phi_q of the coupled modes' noise (in
+    COUPLED order); the white part is the long-wavelength noise with rs_noise_factor."""
+    _, p, q = rs_split(model) if split is None else split
+    phi = rs_scalar_fields(nx, ny, nz, seed, step_index)
+    return p[:, None, None, None] * phi[0] + q[:, None, None, None] * phi[1]
+
+
+def rs_noise_factor(model: Model, split=None) -> np.ndarray:
+    """Q x Q factor of the white part of the correlated noise: the long-wavelength factor with
+    its coupled block replaced by the factor of C."""
+    Lw = (rs_split(model) if split is None else split)[0]
+    L = model.noise_factor()
+    L[np.ix_(COUPLED, COUPLED)] = Lw
+    return L
 
 
 NOISE_OFF, NOISE_LW, NOISE_FULL_RS, NOISE_LW_LOCAL = 0, 1, 4, 5
@@ -412,15 +478,20 @@ class Lattice:
         self.t = 0
         self.f = np.broadcast_to(self.model.rest()[:, None, None, None], (Q, nz, ny, nx)).copy()
         self._L = None
-        self._Ls = None
+        self._split = None
 
     def set_params(self, kT, kappa, tau_s, tau_b, tau_ghost, noise_mode):
         m = self.model
         self.model = Model(m.rho0, m.cs2, kappa, kT, tau_s, tau_b, tau_ghost, m.p0_rest)
         self.mode = int(noise_mode)
         noisy = self.mode in (NOISE_LW, NOISE_FULL_RS) and kT > 0
-        self._L = self.model.noise_factor() if noisy else None
-        self._Ls = rs_factors(self.model) if (noisy and self.mode == NOISE_FULL_RS) else None
+        self._split = rs_split(self.model) if (noisy and self.mode == NOISE_FULL_RS) else None
+        if not noisy:
+            self._L = None
+        elif self._split is not None:
+            self._L = rs_noise_factor(self.model, self._split)
+        else:
+            self._L = self.model.noise_factor()
 
     def step(self, nsteps=1):
         n = self.nx * self.ny * self.nz
@@ -429,8 +500,9 @@ class Lattice:
             xi = None
             if self._L is not None:
                 xi = noise_lw_nodes(self.model, nodes, self.seed, self.t, self._L)
-                if self._Ls is not None:
-                    xi[COUPLED] = xi_coupled_rs(self.model, self.nx, self.ny, self.nz, self.seed, self.t, self._Ls)
+                if self._split is not None:
+                    xi[COUPLED] += xi_coupled_rs(self.model, self.nx, self.ny, self.nz, self.seed, self.t,
+                                                 self._split)
             elif self.mode == NOISE_LW_LOCAL and self.model.kT > 0:
                 rho = self.f.sum(axis=0)
                 c2 = self.model.cs2 if self.eos is None else self.eos.cs2(rho)

@@ -138,6 +138,132 @@ static bool cholesky_block(const double* X, int Q, const std::vector<int>& idx, 
     return true;
 }
 
+// Eigenvalues (ascending, w) and orthonormal eigenvectors (the columns of V, row-major) of a
+// symmetric n x n matrix A by cyclic Jacobi rotations (each zeroes one off-diagonal pair; the
+// sweeps repeat until the off-diagonal part vanishes to rounding).
+static void sym_eigen(std::vector<double> A, int n, std::vector<double>& w, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    double scale = 0.0;
+    for (double v : A) scale = std::max(scale, std::fabs(v));
+    for (int sweep = 0; sweep < 100 && scale > 0.0; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off = std::max(off, std::fabs(A[i * n + j]));
+        if (off <= 1e-17 * scale) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (std::fabs(apq) <= 1e-300) continue;
+                const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {        // A <- A J (columns p, q)
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {        // A <- J^T A (rows p, q)
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {        // V <- V J
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return A[x * n + x] < A[y * n + y]; });
+    std::vector<double> W((size_t)n * n);
+    w.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        w[j] = A[ord[j] * n + ord[j]];
+        for (int i = 0; i < n; ++i) W[i * n + j] = V[i * n + ord[j]];
+    }
+    V = W;
+}
+
+// D3Q27 correlated noise: the coupled block of Xi(k) is X0 + s(k) D with D of rank two (the
+// slope of Xi(0) in c_s^2 times rho0 kappa), so with S = 52/9 (the largest s) and
+// D = p p^T - q q^T it is C + s p p^T + (S - s) q q^T, C = X0 - S q q^T.  The split that
+// whitens X0 (X0 = L0 L0^T, L0^-1 D L0^-T = mu+ y+ y+^T + mu- y- y-^T, p = sqrt(mu+) L0 y+,
+// q = sqrt(-mu-) L0 y-) makes C = L0 (I - S |mu-| y- y-^T) L0^T positive semidefinite exactly
+// when X at k = (pi, pi, pi) is.  Signs: the first component of p (of q) of magnitude at least
+// half its largest is positive.  Out: Lw the Cholesky factor of C (row-major 7 x 7), p, q;
+// false where X0 is singular, D is not of that form or C is indefinite.
+static bool rs_split27(double rho0, double cs2, double kappa, double kT, double lb, double ls, double lg,
+                       std::vector<double>& Lw, double p[7], double q[7]) {
+    constexpr int n = 7;
+    const double S = 52.0 / 9.0;
+    const std::vector<int> coupled(COUPLED27, COUPLED27 + 7);
+    std::vector<double> X((size_t)27 * 27), XS((size_t)27 * 27);
+    xi_zero27(rho0, cs2, kT, lb, ls, lg, X.data());
+    xi_zero27(rho0, cs2 + rho0 * kappa * S, kT, lb, ls, lg, XS.data());
+    std::vector<double> X0((size_t)n * n), D((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            X0[i * n + j] = X[coupled[i] * 27 + coupled[j]];
+            D[i * n + j] = (XS[coupled[i] * 27 + coupled[j]] - X0[i * n + j]) / S;
+        }
+    std::vector<double> L0;
+    const std::vector<int> all = {0, 1, 2, 3, 4, 5, 6};
+    if (!cholesky_block(X0.data(), n, all, L0)) return false;
+    for (int i = 0; i < n; ++i)
+        if (!(L0[i * n + i] > 0.0)) return false;
+    // Y = L0^-1 D L0^-T: forward substitution on the columns of D, then on the rows
+    std::vector<double> Z((size_t)n * n), Y((size_t)n * n);
+    for (int c = 0; c < n; ++c)
+        for (int i = 0; i < n; ++i) {
+            double t = D[i * n + c];
+            for (int k = 0; k < i; ++k) t -= L0[i * n + k] * Z[k * n + c];
+            Z[i * n + c] = t / L0[i * n + i];
+        }
+    for (int r = 0; r < n; ++r)
+        for (int i = 0; i < n; ++i) {
+            double t = Z[r * n + i];
+            for (int k = 0; k < i; ++k) t -= L0[i * n + k] * Y[r * n + k];
+            Y[r * n + i] = t / L0[i * n + i];
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) Y[i * n + j] = Y[j * n + i] = 0.5 * (Y[i * n + j] + Y[j * n + i]);
+    std::vector<double> mu, E;
+    sym_eigen(Y, n, mu, E);
+    // Y is relative to X0: eigenvalues below 1e-9 in magnitude are rounding (kappa = 0: none)
+    int npos = 0, nneg = 0;
+    for (double m : mu) {
+        npos += m > 1e-9;
+        nneg += m < -1e-9;
+    }
+    if (npos > 1 || nneg > 1) return false;
+    const double mp = mu[n - 1] > 1e-9 ? mu[n - 1] : 0.0, mm = mu[0] < -1e-9 ? mu[0] : 0.0;
+    if (1.0 - S * (-mm) < -1e-9) return false;
+    auto vec = [&](int col, double scl, double out[7]) {
+        double vmax = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int k = 0; k <= i; ++k) t += L0[i * n + k] * E[k * n + col];
+            out[i] = scl * t;
+            vmax = std::max(vmax, std::fabs(out[i]));
+        }
+        for (int i = 0; i < n; ++i)
+            if (std::fabs(out[i]) >= 0.5 * vmax) {
+                if (out[i] < 0)
+                    for (int k = 0; k < n; ++k) out[k] = -out[k];
+                break;
+            }
+    };
+    vec(n - 1, std::sqrt(mp), p);
+    vec(0, std::sqrt(-mm), q);
+    std::vector<double> C((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) C[i * n + j] = X0[i * n + j] - S * q[i] * q[j];
+    return cholesky_block(C.data(), n, all, Lw);
+}
+
 // ---- populations in and out; sums ---------------------------------------------------------
 
 // The stored geometry of a context (the padded storage of lb3d_kernel.cuh).
@@ -492,7 +618,7 @@ bool noise_factors(int lattice, const double* X, double sc[QMAX], double Lc[28])
 
 template <typename R>
 void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double tau_g, const double sc[QMAX],
-               const double Lc[28], const double Lb[28], const double Lrs[9], const double Lrs27[112]) {
+               const double Lc[28], const double Lb[28], const double Lrs[12], const double Prs[7], const double Qrs[7]) {
     a->nx = c->nx; a->ny = c->ny; a->nz = c->nz;
     a->pitch = c->geom.pitch; a->gx = c->geom.gx; a->PL = c->geom.PL; a->P = c->geom.P;
     a->err = c->err_dev;
@@ -509,8 +635,11 @@ void fill_args(lb3_ctx* c, Step3Args<R>* a, double tau_s, double tau_b, double t
     for (int q = 0; q < QMAX; ++q) a->sc[q] = (R)sc[q];
     for (int q = 0; q < 28; ++q) a->Lc[q] = (R)Lc[q];
     for (int q = 0; q < 28; ++q) a->Lb[q] = (R)Lb[q];
-    for (int q = 0; q < 9; ++q) a->Lrs[q] = (R)Lrs[q];
-    for (int q = 0; q < 112; ++q) a->Lrs27[q] = (R)Lrs27[q];
+    for (int q = 0; q < 12; ++q) a->Lrs[q] = (R)Lrs[q];
+    for (int q = 0; q < 7; ++q) {
+        a->Prs[q] = (R)Prs[q];
+        a->Qrs[q] = (R)Qrs[q];
+    }
     a->rk = lbf::make_round_keys(c->seed);
 }
 
@@ -634,7 +763,7 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
     if (homogeneous && kT > 0 && !(c->cs2 > 0.0))
         return fail3(c, LB_ENOTPSD, "the linear theory about rho0 has c_s^2 <= 0 (a mean density in the spinodal region)");
     std::vector<double> X((size_t)c->lattice * c->lattice);
-    double sc[QMAX] = {}, Lc[28] = {}, Lb[28] = {}, Lrs[9] = {}, Lrs27[112] = {};
+    double sc[QMAX] = {}, Lc[28] = {}, Lb[28] = {}, Lrs[12] = {}, Prs[7] = {}, Qrs[7] = {};
     if (homogeneous && kT > 0) {
         xi_zero(c->lattice, c->rho0, c->cs2, kT, tau_s, tau_b, tau_ghost, X.data());
         if (!noise_factors(c->lattice, X.data(), sc, Lc)) return fail3(c, LB_ENOTPSD, "Xi(0) is not positive semidefinite");
@@ -664,20 +793,20 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
             }
     }
     if (mode == LB_NOISE_FULL_RS && kT > 0 && c->lattice == 27) {
-        // Xi(k) is Xi(0) at c_s^2(k) = cs2 + rho0 kappa s(k), s = 6 (1 - prod (2 + cos k_a) / 3);
-        // the factors of its coupled block at the corner values s = 0, 4, 16/3, 52/9 (positive
-        // semidefinite there means at every k: Xi(k) is their multilinear interpolation)
+        // Xi(k) is Xi(0) at c_s^2(k) = cs2 + rho0 kappa s(k), s = 6 (1 - prod (2 + cos k_a) / 3)
+        // (multilinear in the cosines, corner values 0, 4, 16/3, 52/9): the rank-two split of
+        // its coupled block; the white part's factor replaces Xi(0)'s in Lc, and the fields
+        // along p and q take the corner amplitudes sqrt(s) and sqrt(52/9 - s)
         const double svals[4] = {0.0, 4.0, 16.0 / 3.0, 52.0 / 9.0};
-        const std::vector<int> coupled(COUPLED27, COUPLED27 + 7);
+        std::vector<double> Lw;
+        if (!rs_split27(c->rho0, c->cs2, kappa, kT, -1.0 / tau_b, -1.0 / tau_s, -1.0 / tau_ghost, Lw, Prs, Qrs))
+            return fail3(c, LB_ENOTPSD, "Xi(k) is not positive semidefinite on the lattice");
+        for (int r = 0; r < 7; ++r)
+            for (int p2 = 0; p2 <= r; ++p2) Lc[r * (r + 1) / 2 + p2] = Lw[r * 7 + p2];
         for (int q = 0; q < 4; ++q) {
-            std::vector<double> Xs((size_t)27 * 27);
-            xi_zero27(c->rho0, c->cs2 + c->rho0 * kappa * svals[q], kT, -1.0 / tau_b, -1.0 / tau_s,
-                      -1.0 / tau_ghost, Xs.data());
-            std::vector<double> L7;
-            if (!cholesky_block(Xs.data(), 27, coupled, L7))
-                return fail3(c, LB_ENOTPSD, "Xi(k) is not positive semidefinite on the lattice");
-            for (int r = 0; r < 7; ++r)
-                for (int p2 = 0; p2 <= r; ++p2) Lrs27[28 * q + r * (r + 1) / 2 + p2] = L7[r * 7 + p2];
+            Lrs[3 * q] = std::sqrt(svals[q]);
+            Lrs[3 * q + 1] = 0.0;
+            Lrs[3 * q + 2] = std::sqrt(std::max(svals[3] - svals[q], 0.0));
         }
     }
     if (mode == LB_NOISE_FULL_RS && kT > 0 && c->lattice == 19) {
@@ -700,8 +829,8 @@ int lb3_set_params(lb3_ctx* c, double kT, double kappa, double tau_s, double tau
     c->kappa = kappa;
     c->tau_s = tau_s; c->tau_b = tau_b; c->tau_g = tau_ghost;
     c->noise_mode = mode;
-    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs, Lrs27);
-    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs, Lrs27);
+    fill_args(c, &c->af, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs, Prs, Qrs);
+    fill_args(c, &c->ad, tau_s, tau_b, tau_ghost, sc, Lc, Lb, Lrs, Prs, Qrs);
     c->have_params = true;
     return LB_OK;
 }

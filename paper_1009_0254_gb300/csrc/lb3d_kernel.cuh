@@ -117,10 +117,11 @@ struct Step3Args {
                                   // its Xi(0) = rho (A + B c_s^2), same layout
     R Lb[28];                     // local noise: B of the coupled block
     R cq[4];                      // local noise: c_s^2(rho0 + dr) = cq0 + dr (cq1 + dr (cq2 + dr cq3))
-    R Lrs[9];                     // D3Q19 correlated noise: Cholesky factors (L11, L21, L22) of the
-                                  // (4,16) block of Xi at s = 0, 4, 16/3
-    R Lrs27[112];                 // D3Q27 correlated noise: Cholesky factors of the coupled block
-                                  // of Xi at s = 0, 4, 16/3, 52/9, 28 each (lower triangle, row-major)
+    R Lrs[12];                    // correlated noise, per corner class (L11, L21, L22): D3Q19 the
+                                  // Cholesky factors of the (4,16) block of Xi at s = 0, 4, 16/3;
+                                  // D3Q27 (sqrt(s), 0, sqrt(S - s)) at s = 0, 4, 16/3, 52/9 = S
+    R Prs[7], Qrs[7];             // D3Q27 correlated noise: the coupled modes' directions p, q of
+                                  // the box-filtered fields (Lc then factors the white part)
     uint32_t t_lo, t_hi;
     lbf::RoundKeys rk;
 };
@@ -324,13 +325,17 @@ __device__ __forceinline__ void store_node3(const Step3Args<R>& a, I zo, int x, 
     }
 }
 
-// correlated noise: the first tag of the draws of the eight corner fields (D3Q19: two draws,
-// word w -> the 2-vector of corner w; D3Q27: seven draws, normal 7 w + m -> component m of the
-// 7-vector of corner w) and the number of coupled components of a corner field
+// correlated noise: the first of the two tags of the draws of the eight corner fields (word w
+// -> the pair of corner w: D3Q19 the white 2-vector of the (4,16) block, D3Q27 the white
+// values of the two scalar fields along p and q), the pair's components, and the corner
+// class of a corner with pc components at pi (the table row of Lrs)
 constexpr uint32_t TAG_RS0 = 10;
 constexpr uint32_t TAG_RS27 = 12;
+constexpr int RS_NV = 2;
 template <typename LAT>
-__host__ __device__ constexpr int rs_components() { return LAT::Q == 19 ? 2 : 7; }
+__host__ __device__ constexpr uint32_t rs_tag() { return LAT::Q == 19 ? TAG_RS0 : TAG_RS27; }
+template <typename LAT>
+__host__ __device__ constexpr int rs_class(int pc) { return LAT::Q == 19 ? (pc == 0 ? 0 : (pc == 2 ? 2 : 1)) : pc; }
 
 // Shared-memory geometry of one raw slot.  Copies (TMA = false): per population the pulled
 // values of the tile and its ring, RX x RY, already shifted by -c_i.  TMA: per box the GM
@@ -356,13 +361,12 @@ struct Slot3 {
 
 // Shared memory of the staged kernel: [SLOTS][SLOT] raw values, the mbarriers (TMA), the
 // density ring [3][RN], and with correlated noise (MODE 3) the 2x2x2-box contributions: for
-// the tile plus its left column and bottom row, the in-plane half (four NV-vectors, NV the
-// coupled components) of the current plane and the upward half of the current and the
-// previous plane.
+// the tile plus its left column and bottom row, the in-plane half (four pairs) of the current
+// plane and the upward half of the current and the previous plane.
 template <typename LAT, typename R, int TY, int SLOTS, int MODE, bool TMA>
 constexpr int staged_smem_bytes() {
     using S = Slot3<LAT, R, TY, TMA>;
-    constexpr int HV = MODE == 3 ? 12 * rs_components<LAT>() * (LAT::TX + 1) * (TY + 1) : 0;
+    constexpr int HV = MODE == 3 ? 12 * RS_NV * (LAT::TX + 1) * (TY + 1) : 0;
     return (SLOTS * S::SLOT + 3 * S::RN + HV) * (int)sizeof(R) + (TMA ? 16 * ((SLOTS + 1) / 2) : 0);
 }
 
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
     constexpr int RAW_BYTES = SLOTS * SL * (int)sizeof(R);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem3 + RAW_BYTES);         // TMA: one per slot
     R* rs = reinterpret_cast<R*>(smem3 + RAW_BYTES + (TMA ? 16 * ((SLOTS + 1) / 2) : 0));   // [3][RN]
-    constexpr int HW = TX + 1, HN = HW * (TY + 1), NV = rs_components<LAT>();
+    constexpr int HW = TX + 1, HN = HW * (TY + 1), NV = RS_NV;
     R* Hin = rs + 3 * RN;                                   // MODE 3: [4][NV][HN] in-plane half
     R* Hup = Hin + 4 * NV * HN;                             // MODE 3: [2][4][NV][HN] upward half
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch, GX = a.gx;
@@ -515,11 +519,12 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
     const int qc = (ly + 1) * RX + lx + 1;     // own position in the density ring
     const int qb = (ly + 1) * BW + lx + 1;     // own position in a raw slot
 
-    // MODE 3: the eight white 2-vectors nu_w of every position of plane zz (tile, left column,
-    // bottom row), times the factor of their corner (w = 4 ia + 2 ib + ic, sign -1 for a set
-    // bit: k = pi), combined by a Walsh-Hadamard transform into h_m = (1/8) sum_w
+    // MODE 3: the eight white pairs nu_w of every position of plane zz (tile, left column,
+    // bottom row), times the factor of their corner class (w = 4 ia + 2 ib + ic, sign -1 for a
+    // set bit: k = pi), combined by a Walsh-Hadamard transform into h_m = (1/8) sum_w
     // (-1)^{popcount(w & m)} L_w nu_w, m = 4 dx + 2 dy + dz: the in-plane half (dz = 0) into Hin
-    // when keep_in, the upward half (dz = 1) into buffer ub
+    // when keep_in, the upward half (dz = 1) into buffer ub.  D3Q19: the (4,16) block's
+    // 2-vector; D3Q27: the two scalar fields along p and q (L_w diagonal)
     auto stencil_plane = [&](int zz, bool keep_in, int ub) {
         const int zc = wrap_hi(wrap_lo(zz, nz), nz);
         for (int p = NT - 1 - tid; p < HN; p += NT) {       // extra positions on the last threads
@@ -529,64 +534,20 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
             gx = wrap_lo(gx, nx);
             gy = wrap_lo(gy, ny);
             const uint32_t node = ((uint32_t)zc * (uint32_t)ny + (uint32_t)gy) * (uint32_t)nx + (uint32_t)gx;
-            if constexpr (LAT::Q == 27) {
-                // D3Q27: eight 7-vectors; corner class = components at pi (s = 0, 4, 16/3, 52/9)
-                R nu[56];
-#pragma unroll
-                for (int d = 0; d < 7; ++d) {
-                    const uint4 rw = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS27 + d), a.rk);
-                    lbf::gauss_word(rw.x, &nu[8 * d + 0], &nu[8 * d + 1]);
-                    lbf::gauss_word(rw.y, &nu[8 * d + 2], &nu[8 * d + 3]);
-                    lbf::gauss_word(rw.z, &nu[8 * d + 4], &nu[8 * d + 5]);
-                    lbf::gauss_word(rw.w, &nu[8 * d + 6], &nu[8 * d + 7]);
-                }
-                R v[8][7];
-#pragma unroll
-                for (int w = 0; w < 8; ++w) {
-                    const int cls = (w & 1) + ((w >> 1) & 1) + ((w >> 2) & 1);
-                    const R* Lw = a.Lrs27 + 28 * cls;
-#pragma unroll
-                    for (int r = 0; r < 7; ++r) {
-                        R acc = R(0);
-#pragma unroll
-                        for (int q = 0; q <= r; ++q) acc += Lw[r * (r + 1) / 2 + q] * nu[7 * w + q];
-                        v[w][r] = acc;
-                    }
-                }
-#pragma unroll
-                for (int b = 1; b < 8; b <<= 1)
-#pragma unroll
-                    for (int w = 0; w < 8; ++w)
-                        if (!(w & b)) {
-#pragma unroll
-                            for (int r = 0; r < 7; ++r) {
-                                const R x = v[w][r], y = v[w | b][r];
-                                v[w][r] = x + y;
-                                v[w | b][r] = x - y;
-                            }
-                        }
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    R* dst = (m & 1) ? Hup + ub * 4 * NV * HN : Hin;
-                    if (!(m & 1) && !keep_in) continue;
-                    const int j = m >> 1;
-#pragma unroll
-                    for (int r = 0; r < 7; ++r) dst[(j * NV + r) * HN + p] = R(0.125) * v[m][r];
-                }
-                continue;
-            }
-            const uint4 r0 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0), a.rk);
-            const uint4 r1 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, TAG_RS0 + 1), a.rk);
+            const uint4 r0 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, rs_tag<LAT>()), a.rk);
+            const uint4 r1 = lbf::philox4x32_10(make_uint4(node, a.t_lo, a.t_hi, rs_tag<LAT>() + 1), a.rk);
             const uint32_t wd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
             R vx[8], vy[8];
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
                 R n0, n1;
                 lbf::gauss_word(wd[w], &n0, &n1);
-                const int pc = (w & 1) + ((w >> 1) & 1) + ((w >> 2) & 1);      // components at pi
-                const int cls = pc == 0 ? 0 : (pc == 2 ? 2 : 1);             // s = 0, 16/3, 4
+                const int cls = rs_class<LAT>((w & 1) + ((w >> 1) & 1) + ((w >> 2) & 1));
                 vx[w] = a.Lrs[3 * cls] * n0;
-                vy[w] = a.Lrs[3 * cls + 1] * n0 + a.Lrs[3 * cls + 2] * n1;
+                if constexpr (LAT::Q == 19)
+                    vy[w] = a.Lrs[3 * cls + 1] * n0 + a.Lrs[3 * cls + 2] * n1;
+                else
+                    vy[w] = a.Lrs[3 * cls + 2] * n1;
             }
 #pragma unroll
             for (int b = 1; b < 8; b <<= 1)
@@ -660,19 +621,19 @@ __global__ void __launch_bounds__(LAT::TX * TY, staged_min_blocks<LAT, R, TY, SL
             if (MODE == 1 || MODE == 3) normals27(a, node, xi);
             if (MODE == 4) normals27_local(a, node, nb[0], xi);
             if constexpr (MODE == 3) {
-                // the coupled modes: the 2x2x2-box sums of this plane's in-plane halves and the
-                // previous plane's upward halves
+                // the coupled modes: the white part (normals27 with the factor of C) plus p phi_p
+                // + q phi_q, the two fields the 2x2x2-box sums of this plane's in-plane halves
+                // and the previous plane's upward halves
+                R sp = R(0), sq = R(0);
                 const R* hu = Hup + hb * 4 * NV * HN;
 #pragma unroll
-                for (int r = 0; r < 7; ++r) {
-                    R sacc = R(0);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int q = (ly - (j & 1) + 1) * HW + (lx - (j >> 1) + 1);
-                        sacc += Hin[(j * NV + r) * HN + q] + hu[(j * NV + r) * HN + q];
-                    }
-                    xi[coupled27(r)] = sacc;
+                for (int j = 0; j < 4; ++j) {
+                    const int q = (ly - (j & 1) + 1) * HW + (lx - (j >> 1) + 1);
+                    sp += Hin[(j * NV) * HN + q] + hu[(j * NV) * HN + q];
+                    sq += Hin[(j * NV + 1) * HN + q] + hu[(j * NV + 1) * HN + q];
                 }
+#pragma unroll
+                for (int r = 0; r < 7; ++r) xi[coupled27(r)] += a.Prs[r] * sp + a.Qrs[r] * sq;
             }
             collide27(a.co, f, nb, xi, o);
         }

@@ -304,9 +304,10 @@ def test_correlated_noise_refuses_an_indefinite_Xi():
     g.set_params(1e-4, 0.06, 0.8, 1.1, 0.9, lbf.LB_NOISE_LW)           # Xi(0) alone is fine
 
 
-def _patch_step_rs(m, n, centre, seed, t, L, Ls, amp):
+def _patch_step_rs(m, n, centre, seed, t, L, split, amp):
     """One oracle step at `centre` with the correlated noise on the 6x6x6 neighbourhood
-    centre - 3 .. centre + 2 (every node the box sums of the 3x3x3 collisions need)."""
+    centre - 3 .. centre + 2 (every node the box sums of the 3x3x3 collisions need): the
+    white part through L, plus p phi_p + q phi_q from the corner draws of the patch."""
     z0, y0, x0 = centre
     zs, ys, xs = ((np.arange(c - 3, c + 3)) % n for c in (z0, y0, x0))
     Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
@@ -314,16 +315,18 @@ def _patch_step_rs(m, n, centre, seed, t, L, Ls, amp):
     sub = np.array(_wave_state(m.fbar(), n, Z, Y, X, amp))
     xi = d.noise_lw_nodes(m, nodes, seed, t, L)
     g = np.concatenate([oracle.normals(nodes.ravel().astype(np.uint32), seed, t, tg) for tg in d.TAG_RS], axis=1)
-    nu = g.T.reshape(8, 7, 6, 6, 6)
-    v = np.einsum("wab,wb...->wa...", Ls, nu)
-    xc = np.zeros((7, 6, 6, 6))
+    nu = g.T.reshape(8, 2, 6, 6, 6)
+    ap, aq = d.rs_weights()
+    v = np.stack([ap[:, None, None, None] * nu[:, 0], aq[:, None, None, None] * nu[:, 1]], axis=1)
+    phi = np.zeros((2, 6, 6, 6))
     for dz in (0, 1):
         for dy in (0, 1):
             for dx in (0, 1):
                 h = sum((d.CORNERS[w][0] ** dx) * (d.CORNERS[w][1] ** dy) * (d.CORNERS[w][2] ** dz) * v[w]
                         for w in range(8)) / 8.0
-                xc += np.roll(h, shift=(dz, dy, dx), axis=(1, 2, 3))     # exact away from the low faces
-    xi[d.COUPLED] = xc
+                phi += np.roll(h, shift=(dz, dy, dx), axis=(1, 2, 3))    # exact away from the low faces
+    _, p, q = split
+    xi[d.COUPLED] += p[:, None, None, None] * phi[0] + q[:, None, None, None] * phi[1]
     return d.step(sub, m, xi)[:, 3, 3, 3]
 
 
@@ -344,14 +347,15 @@ def test_correlated_noise_sampled_at_the_benchmark_size():
     g.step(1)
     lbf.lb3_get_populations(g.ctx, dev, lbf.LB_DEVICE)
     torch.cuda.synchronize()
-    L, Ls = m.noise_factor(), d.rs_factors(m)
+    split = d.rs_split(m)
+    L = d.rs_noise_factor(m, split)
     rng = np.random.default_rng(3)
     picks = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 1, 0, 31), (96, 96, 0), (7, 8, n - 1)]
     picks += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(12)]
     err = 0.0
     for c in picks:
         got = dev[:, c[0], c[1], c[2]].cpu().numpy()
-        err = max(err, np.abs(got - _patch_step_rs(m, n, c, 5, 9, L, Ls, amp)).max())
+        err = max(err, np.abs(got - _patch_step_rs(m, n, c, 5, 9, L, split, amp)).max())
     print("D3Q27 RS 192^3 sampled: %.2e" % err)
     assert err <= TOL
     del dev, g

@@ -330,33 +330,98 @@ def test_lattice_symbol_is_the_stencils_and_has_its_corner_values():
         np.testing.assert_allclose(-lap, float(d.lattice_s(*kv)) * wave, atol=1e-12)
 
 
+def _transfer(k, w, d3=d):
+    """|(1/8) sum_d (+-1)^d e^{-i k.d}|^2 of corner w: the spectrum of its box-filtered field."""
+    a, b, c = d3.CORNERS[w]
+    t = sum((a ** dx) * (b ** dy) * (c ** dz) * np.exp(-1j * (k[0] * dx + k[1] * dy + k[2] * dz))
+            for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)) / 8.0
+    return abs(t) ** 2
+
+
 def test_real_space_construction_reproduces_Xi_k_at_every_wavevector():
-    # transfer function of the 2x2x2 box: sum_w L_w L_w^T |(1/8) sum_d (-1)^{w.d} e^{-i k.d}|^2
-    # must equal the coupled block of Xi(k) from the FDT at every k of a 6 x 5 x 4 lattice
+    # the white part C plus the two box-filtered scalar fields along p and q: their spectral
+    # covariance C + sum_w |t_w(k)|^2 (a_p,w^2 p p^T + a_q,w^2 q q^T) must equal the coupled
+    # block of Xi(k) from the FDT at every k of a 6 x 5 x 4 lattice
     m = d.Model(rho0=1.0, cs2=0.2, kappa=0.04, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
-    Ls = d.rs_factors(m)
+    Lw, p, q = d.rs_split(m)
+    ap, aq = d.rs_weights()
+    C = Lw @ Lw.T
     for mz in range(4):
         for my in range(5):
             for mx in range(6):
                 k = (2 * np.pi * mx / 6, 2 * np.pi * my / 5, 2 * np.pi * mz / 4)
-                got = np.zeros((7, 7))
-                for w, (a, b, c) in enumerate(d.CORNERS):
-                    t = sum((a ** dx) * (b ** dy) * (c ** dz) * np.exp(-1j * (k[0] * dx + k[1] * dy + k[2] * dz))
-                            for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)) / 8.0
-                    got += abs(t) ** 2 * (Ls[w] @ Ls[w].T)
+                got = C.copy()
+                for w in range(8):
+                    tw = _transfer(k, w)
+                    got += tw * (ap[w] ** 2 * np.outer(p, p) + aq[w] ** 2 * np.outer(q, q))
                 want = d.Xi_k(m, *k)[np.ix_(d.COUPLED, d.COUPLED)]
                 np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-18)
 
 
+def test_corner_amplitudes_interpolate_s_and_its_complement():
+    # the corner transfers are the multilinear interpolation weights: they sum to one and,
+    # weighted by the corner values of s, give s(k) itself at any k
+    ap, aq = d.rs_weights()
+    S = d.s_max()
+    assert abs(S - 52 / 9) < 1e-12
+    np.testing.assert_allclose(sorted(set(np.round(ap ** 2, 12))), [0, 4, 16 / 3, 52 / 9], atol=1e-12)
+    for k in [(0.3, -1.2, 2.2), (np.pi, 0.4, 0.0), (1.0, 2.0, 3.0)]:
+        tw = np.array([_transfer(k, w) for w in range(8)])
+        assert abs(tw.sum() - 1) < 1e-14
+        assert abs(tw @ ap ** 2 - float(d.lattice_s(*k))) < 1e-12
+        assert abs(tw @ aq ** 2 - (S - float(d.lattice_s(*k)))) < 1e-12
+
+
+@pytest.mark.parametrize("cs2,kappa,tb,tg", [(0.2, 0.04, 1.1, 0.9), (1 / 3, 0.01, 1.1, 0.9), (0.2, 0.04, 0.6, 1.5),
+                                             (0.1, 0.06, 0.6, 0.9), (0.3, 0.02, 2.0, 1.5)])
+def test_split_of_the_slope_has_rank_two_and_a_white_part_exactly_where_Xi_is_psd(cs2, kappa, tb, tg):
+    # D = (X(S) - X0) / S has one positive and one negative eigenvalue (the slope of Xi(0) in
+    # c_s^2 has rank two); D = p p^T - q q^T; C = X0 - S q q^T is positive semidefinite; and
+    # C + S p p^T is X at k = (pi, pi, pi).  The cases with tau_b = 0.6 are ones where the
+    # split along the eigenvectors of D itself leaves C indefinite: the whitened split does not
+    m = d.Model(rho0=1.0, cs2=cs2, kappa=kappa, kT=1e-4, tau_s=0.8, tau_b=tb, tau_ghost=tg)
+    S = d.s_max()
+    X0 = d.Xi_k(m, 0, 0, 0)[np.ix_(d.COUPLED, d.COUPLED)]
+    XS = d.Xi_k(m, np.pi, np.pi, np.pi)[np.ix_(d.COUPLED, d.COUPLED)]
+    D = (XS - X0) / S
+    ev = np.linalg.eigvalsh(D)
+    big = np.abs(ev) > 1e-9 * np.abs(ev).max()
+    assert big.sum() == 2 and ev[0] < 0 < ev[-1]
+    Lw, p, q = d.rs_split(m)
+    np.testing.assert_allclose(np.outer(p, p) - np.outer(q, q), D, rtol=0, atol=1e-12 * np.abs(D).max())
+    C = Lw @ Lw.T
+    np.testing.assert_allclose(C, X0 - S * np.outer(q, q), rtol=0, atol=1e-12 * np.abs(X0).max())
+    np.testing.assert_allclose(C + S * np.outer(p, p), XS, rtol=0, atol=1e-12 * np.abs(X0).max())
+    for v in (p, q):
+        big = np.abs(v) >= 0.5 * np.abs(v).max()
+        assert v[np.argmax(big)] > 0
+    if tb == 0.6:
+        w, E = np.linalg.eigh(D)
+        qe = np.sqrt(-w[0]) * E[:, 0]
+        assert np.linalg.eigvalsh(X0 - S * np.outer(qe, qe)).min() < 0
+
+
+def test_split_refuses_where_Xi_is_indefinite_at_the_far_corner():
+    # c_s^2(k) = 0.3 + 0.06 * 52/9 at k = (pi, pi, pi): the coupled block is indefinite there
+    m = d.Model(rho0=1.0, cs2=0.3, kappa=0.06, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    XS = d.Xi_k(m, np.pi, np.pi, np.pi)[np.ix_(d.COUPLED, d.COUPLED)]
+    assert np.linalg.eigvalsh(XS).min() < 0
+    with pytest.raises(ValueError):
+        d.rs_split(m)
+
+
 def test_real_space_fields_have_the_Xi_k_spectrum():
-    # sampled: the generated coupled-mode fields' spectral covariance at a few k against Xi(k)
+    # sampled: the coupled modes' noise of the lattice (the white part through the
+    # long-wavelength normals plus p phi_p + q phi_q) against Xi(k) at a few k
     m = d.Model(rho0=1.0, cs2=0.2, kappa=0.04, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
     n = 6
-    Ls = d.rs_factors(m)
+    split = d.rs_split(m)
+    L = d.rs_noise_factor(m, split)
+    nodes = np.arange(n ** 3, dtype=np.uint32).reshape(n, n, n)
     acc = np.zeros((7, 7, n, n, n), dtype=complex)
     draws = 300
     for t in range(draws):
-        xi = d.xi_coupled_rs(m, n, n, n, seed=9, step_index=t, Ls=Ls)
+        xi = d.noise_lw_nodes(m, nodes, 9, t, L)[d.COUPLED] + d.xi_coupled_rs(m, n, n, n, 9, t, split)
         xk = np.fft.fftn(xi, axes=(1, 2, 3)) / np.sqrt(n ** 3)
         acc += np.einsum("a...,b...->ab...", xk, np.conj(xk))
     acc /= draws

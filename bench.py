@@ -360,7 +360,9 @@ def d3_variant(lbf, torch, hbm, lattice=19, n=256, steps=300, warmup=5, noise="l
     k_s = kms / max(kl, 1) / 1e3
     L.close()
     return {"lattice": "D3Q%d %d^3, FP32 deviations" % (lattice, n),
-            "noise": {"rs": "correlated, built in real space (2x2x2 stencil of eight white fields)",
+            "noise": {"rs": "correlated, built in real space (2x2x2 stencil of eight white corner fields; "
+                            + ("the (4,16) block's 2-vectors)" if lattice == 19 else
+                               "a white part plus two scalar fields along the rank-two slope)"),
                       "local": "uncorrelated at the local density and c_s^2 (two-phase: double well beta=%g, "
                                "rhoV=%g, rhoL=%g, rho0=%g)" % (DOUBLE_WELL + (RHO0_TWOPHASE,))}.get(
                 noise, "long-wavelength"),

@@ -304,6 +304,24 @@ def test_correlated_noise_refuses_an_indefinite_Xi():
     g.set_params(1e-4, 0.06, 0.8, 1.1, 0.9, lbf.LB_NOISE_LW)           # Xi(0) alone is fine
 
 
+def test_correlated_noise_at_zero_kappa_is_the_long_wavelength_noise():
+    # kappa = 0: Xi(k) is Xi(0) at every k, the slope of the coupled block vanishes and the
+    # rank-two split leaves only its white part, so the correlated mode steps exactly as the
+    # long-wavelength mode (same draws; the factors agree to FP32 rounding)
+    params = (1e-4, 0.0, 0.8, 1.1, 0.9)
+    a = lbf.Lattice3(20, 9, 6, seed=3, cs2=0.2, lattice=lbf.LB_D3Q27)
+    b = lbf.Lattice3(20, 9, 6, seed=3, cs2=0.2, lattice=lbf.LB_D3Q27)
+    a.set_params(*params, lbf.LB_NOISE_FULL_RS)
+    b.set_params(*params, lbf.LB_NOISE_LW)
+    a.step(5)
+    b.step(5)
+    fa, fb = a.populations(), b.populations()
+    err = np.abs(fa - fb).max()
+    print("D3Q27 RS at kappa = 0 against LW: %.2e" % err)
+    assert err <= 1e-7
+    assert np.abs(fa - d.Lattice(20, 9, 6, cs2=0.2).f).max() > 1e-4        # the noise acted
+
+
 def _patch_step_rs(m, n, centre, seed, t, L, split, amp):
     """One oracle step at `centre` with the correlated noise on the 6x6x6 neighbourhood
     centre - 3 .. centre + 2 (every node the box sums of the 3x3x3 collisions need): the

@@ -410,6 +410,22 @@ def test_split_refuses_where_Xi_is_indefinite_at_the_far_corner():
         d.rs_split(m)
 
 
+def test_correlated_noise_at_zero_kappa_is_the_long_wavelength_noise():
+    # kappa = 0: no slope, p = q = 0, and the white part's factor is that of Xi(0): the
+    # correlated mode steps exactly as the long-wavelength mode
+    m = d.Model(rho0=1.0, cs2=0.2, kappa=0.0, kT=1e-4, tau_s=0.8, tau_b=1.1, tau_ghost=0.9)
+    Lw, p, q = d.rs_split(m)
+    assert not p.any() and not q.any()
+    a = d.Lattice(5, 4, 3, cs2=0.2, seed=11)
+    b = d.Lattice(5, 4, 3, cs2=0.2, seed=11)
+    a.set_params(1e-4, 0.0, 0.8, 1.1, 0.9, d.NOISE_FULL_RS)
+    b.set_params(1e-4, 0.0, 0.8, 1.1, 0.9, d.NOISE_LW)
+    a.step(3)
+    b.step(3)
+    np.testing.assert_allclose(a.f, b.f, rtol=0, atol=1e-15)
+    assert np.abs(a.f - d.Lattice(5, 4, 3, cs2=0.2).f).max() > 1e-4
+
+
 def test_real_space_fields_have_the_Xi_k_spectrum():
     # sampled: the coupled modes' noise of the lattice (the white part through the
     # long-wavelength normals plus p phi_p + q phi_q) against Xi(k) at a few k

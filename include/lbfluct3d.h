@@ -131,7 +131,8 @@ int lb3_set_stream(lb3_ctx* ctx, void* stream);
  * LB_NOISE_LW, LB_NOISE_FULL_RS or LB_NOISE_LW_LOCAL; others LB_EINVAL).  With LB_NOISE_LW or
  * LB_NOISE_FULL_RS and kT > 0, the c_s^2 of the linear theory about rho0 must be positive and
  * Xi(0) (with LB_NOISE_FULL_RS also Xi at the other corner values of s) positive semidefinite
- * (D3Q19 at equal relaxation times: c_s^2 <= 5/9), else LB_ENOTPSD.  May be called again between
+ * (D3Q19 at equal relaxation times: c_s^2 <= 5/9; D3Q27 with LB_NOISE_FULL_RS: the coupled
+ * block positive definite at s = 0 and positive semidefinite at s = 52/9), else LB_ENOTPSD.  May be called again between
  * steps; the lattice state is kept.
  */
 int lb3_set_params(lb3_ctx* ctx, double kT, double kappa, double tau_s, double tau_b, double tau_ghost,

@@ -81,6 +81,9 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         if (first + (int)gridDim.x < ntiles) issue(first + gridDim.x, 1);
     }
 
+    // the tile's column and row, advanced by the grid stride without a division per tile
+    const int stx = (int)gridDim.x % ta.ntx, sty = (int)gridDim.x / ta.ntx;
+    int tcol = first % ta.ntx, trow = first / ta.ntx;
     int k = 0;
     for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
         const int s = k & 1;
@@ -100,7 +103,13 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             return;
         }
         const T* S = smem + s * TT::STAGE;
-        const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
+        const int x0 = tcol * TX, y0 = trow * TY;
+        tcol += stx;
+        trow += sty;
+        if (tcol >= ta.ntx) {
+            tcol -= ta.ntx;
+            ++trow;
+        }
 
         static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
         constexpr int NN = TX * TY / NT;

@@ -37,6 +37,8 @@ struct ClassDesc {
     const RepRec* recs;         // its replicas' records
     int tile_begin;             // first tile of the class in the launch's numbering
     int ntx, per;               // tiles along x per replica, tiles per replica
+    unsigned long long per_m, ntx_m;   // division by per and by ntx as a multiply and a shift
+    int per_s, ntx_s;
     long long rstride;          // elements per replica (9 planes)
     const float2* xi;           // correlated noise (xi_4, xi_9) of the class, nx*ny per replica, or null
 };
@@ -52,6 +54,13 @@ struct EnsParams {
     int rs;                            // some replica of the launch has real-space correlated noise
 };
 
+// floor(n / d) for 0 <= n < 2^32 as (n m) >> s with m = ceil(2^s / d), s = 32 + ceil(log2 d)
+// (Granlund and Montgomery, division by invariant integers using multiplication, 1994):
+// every thread locates every tile, and a division per tile and thread is felt in the step
+__device__ __forceinline__ int div_magic(int n, unsigned long long m, int s) {
+    return (int)(((unsigned long long)(unsigned)n * m) >> s);
+}
+
 // class, replica and origin of a tile of the launch
 struct TilePos {
     int c, rep, x0, y0;
@@ -66,9 +75,9 @@ __device__ __forceinline__ TilePos locate(const EnsParams& p, int tile) {
     const ClassDesc& d = p.cls[c];
     const int rel = tile - d.tile_begin;
     t.c = c;
-    t.rep = rel / d.per;
+    t.rep = div_magic(rel, d.per_m, d.per_s);
     const int rem = rel - t.rep * d.per;
-    const int ty = rem / d.ntx;
+    const int ty = div_magic(rem, d.ntx_m, d.ntx_s);
     t.x0 = (rem - ty * d.ntx) * TX;
     t.y0 = ty * TY;
     return t;
@@ -584,6 +593,14 @@ static int upload_rec(lb_batch* b, int r) {
     return LB_OK;
 }
 
+// the multiplier and shift of div_magic for a divisor d >= 1
+static void div_magic_params(int d, unsigned long long* m, int* s) {
+    int l = 0;
+    while ((1ll << l) < (long long)d) ++l;
+    *s = 32 + l;
+    *m = ((1ull << (32 + l)) + (unsigned long long)d - 1ull) / (unsigned long long)d;
+}
+
 // Kernel parameters of the step launches for tile shape `tile`: classes in chunks of
 // MAX_CLASSES, the last launch of a step advancing the step counter.
 static int build_launches(lb_batch* b, int tile, std::vector<EnsParams>* out) {
@@ -606,6 +623,8 @@ static int build_launches(lb_batch* b, int tile, std::vector<EnsParams>* out) {
             d.recs = reinterpret_cast<const RepRec*>(cls_ptr(b, ci.off_recs));
             d.ntx = (ci.nx + TX - 1) / TX;
             d.per = d.ntx * ((ci.ny + TY - 1) / TY);
+            div_magic_params(d.per, &d.per_m, &d.per_s);
+            div_magic_params(d.ntx, &d.ntx_m, &d.ntx_s);
             d.tile_begin = tiles;
             d.rstride = (long long)Q * ci.g.plane;
             d.xi = reinterpret_cast<const float2*>(cls_ptr(b, ci.off_z1));

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(NT, RS ? 1024 / NT : 0) step_ensemble_kernel(c
         // pulled populations stay in registers across the density barrier; the stage is
         // refilled right after it
         float fr[TX * TY / NT][Q];
-        tile_pull<TX, TY, NT>(S, R, fr);
+        tile_pull<TX, TY, NT, RS>(S, R, fr);
         __syncthreads();
         if (tid == 0 && !(RS && smode == 3) && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -72,8 +72,11 @@ __device__ __forceinline__ void load_stencil_args(const RepRec* rp, TileArgsRS* 
 
 // Pulls the nine deviations of this thread's nodes of the staged tile S into registers
 // (fr) and writes the density deviation of the tile and of its one-node ring (from the
-// halo) into R.  After a CTA barrier the stage is no longer read.
-template <int TX, int TY, int NT>
+// halo) into R.  After a CTA barrier the stage is no longer read.  The ring goes to the
+// last threads (the first loads the tile's record and issues the refill) unless the
+// launch may hold real-space correlated noise (RS), whose halo contributions the last
+// threads form.
+template <int TX, int TY, int NT, bool RS>
 __device__ __forceinline__ void tile_pull(const float* S, float* R, float (&fr)[TX * TY / NT][Q]) {
     using TT = TmaTile<TX, TY, float>;
     static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
@@ -86,7 +89,7 @@ __device__ __forceinline__ void tile_pull(const float* S, float* R, float (&fr)[
     }
     // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
     constexpr int NB = 2 * (TX + 2) + 2 * TY;
-    for (int j = threadIdx.x; j < NB; j += NT) {
+    for (int j = RS ? (int)threadIdx.x : NT - 1 - (int)threadIdx.x; j < NB; j += NT) {
         int rx, ry;
         if (j < TX + 2) { rx = j; ry = 0; }
         else if (j < 2 * (TX + 2)) { rx = j - (TX + 2); ry = TY + 1; }

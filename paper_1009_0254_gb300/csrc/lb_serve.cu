@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_serve_kernel(const ServePa
         // pulled populations stay in registers across the density barrier; the stage is
         // refilled right after it (slot, x0, y0 are in registers by then)
         float fr[TX * TY / NT][Q];
-        tile_pull<TX, TY, NT>(S, R, fr);
+        tile_pull<TX, TY, NT, RS>(S, R, fr);
         __syncthreads();
         const int mode = smode;
         if (tid == 0 && !(RS && mode == 3) && tile + 2 * (int)gridDim.x < ntiles) {

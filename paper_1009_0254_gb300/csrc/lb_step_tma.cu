@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
     }
     __syncthreads();
 
-    auto issue = [&](int tile, int s) {
-        const int x0 = (tile % ta.ntx) * TX, y0 = (tile / ta.ntx) * TY;
+    // the nine boxes of the tile in column col, row row of the tiling into stage s
+    auto issue = [&](int col, int row, int s) {
+        const int x0 = col * TX, y0 = row * TY;
         const uint32_t bar = smem_u32(&mbar[s]);
         mbar_expect_tx(bar, TT::TX_BYTES);
         T* st = smem + s * TT::STAGE;
@@ -75,15 +76,24 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             tma_load_3d(smem_u32(st + i * TT::PS), &tmap, x0 - TT::XO + g.gx, y0 - 1 - kCYt[i] + GY, i, bar);
     };
 
+    // a tile's column and row, advanced by the grid stride without a division per tile
     const int first = blockIdx.x;
-    if (tid == 0) {
-        if (first < ntiles) issue(first, 0);
-        if (first + (int)gridDim.x < ntiles) issue(first + gridDim.x, 1);
-    }
-
-    // the tile's column and row, advanced by the grid stride without a division per tile
     const int stx = (int)gridDim.x % ta.ntx, sty = (int)gridDim.x / ta.ntx;
+    auto advance = [&](int& col, int& row) {
+        col += stx;
+        row += sty;
+        if (col >= ta.ntx) {
+            col -= ta.ntx;
+            ++row;
+        }
+    };
     int tcol = first % ta.ntx, trow = first / ta.ntx;
+    if (tid == 0) {
+        if (first < ntiles) issue(tcol, trow, 0);
+        int c1 = tcol, r1 = trow;
+        advance(c1, r1);
+        if (first + (int)gridDim.x < ntiles) issue(c1, r1, 1);
+    }
     int k = 0;
     for (int tile = first; tile < ntiles; tile += gridDim.x, ++k) {
         const int s = k & 1;
@@ -104,12 +114,7 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         }
         const T* S = smem + s * TT::STAGE;
         const int x0 = tcol * TX, y0 = trow * TY;
-        tcol += stx;
-        trow += sty;
-        if (tcol >= ta.ntx) {
-            tcol -= ta.ntx;
-            ++trow;
-        }
+        advance(tcol, trow);        // now the next tile's
 
         static_assert((TX * TY) % NT == 0, "tile must be a multiple of the block");
         constexpr int NN = TX * TY / NT;
@@ -136,9 +141,11 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
             stencil_halo<TX, TY, TT::HW>(a, Hd, TT::HN, x0, y0, g.nx, g.ny, tid, NT);
         };
         if (MODE == 3) stencil_tile(H);
-        // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1
+        // the ring: rows 0 and TY + 1 (TX + 2 each), then columns 0 and TX + 1, on the last
+        // threads (the first issues the refill); with MODE 3 on the first (the last form the
+        // noise contributions of the halo)
         constexpr int NB = 2 * (TX + 2) + 2 * TY;
-        for (int j = tid; j < NB; j += NT) {
+        for (int j = MODE == 3 ? tid : NT - 1 - tid; j < NB; j += NT) {
             int rx, ry;
             if (j < TX + 2) { rx = j; ry = 0; }
             else if (j < 2 * (TX + 2)) { rx = j - (TX + 2); ry = TY + 1; }
@@ -152,7 +159,9 @@ __global__ void __launch_bounds__(NT) step_tma_kernel(const __grid_constant__ CU
         // two steps ahead
         if (tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(tile + 2 * gridDim.x, s);
+            int c2 = tcol, r2 = trow;
+            advance(c2, r2);
+            issue(c2, r2, s);
         }
 
         // collide every node of the tile; the nodes of one thread are independent, so

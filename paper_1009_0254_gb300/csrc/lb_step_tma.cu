@@ -210,12 +210,14 @@ static const int kTiles[5][3] = {{32, 16, 256}, {32, 32, 256}, {64, 8, 256}, {64
 
 int tma_tile_count() { return 5; }
 
-// The fastest shape per noise mode (0 off, 1 uncorrelated, 2 correlated) and storage,
-// measured on GB300 over all five at 4096^2: FP32 off 32x32 (263 us), uncorrelated 64x16
-// (215 us), correlated 32x16 (246 us); FP16 off 32x16/128 (153 us), uncorrelated 32x32
-// (233 us), correlated 64x16 (245 us).
+// The fastest shape per noise mode (0 off, 1 uncorrelated, 2 correlated, 3 correlated built
+// in real space) and storage, measured on GB300 at 4096^2: FP32 off 32x32 (263 us),
+// uncorrelated 32x32 (212.5 us against 214.1 for 64x16/512, alternating runs on one box),
+// correlated 32x16 (235.0 us; 32x32 285, 64x16 240), real space 32x16 (334 us; 32x32 422);
+// FP16 off 32x16/128 (153 us), uncorrelated 32x32 (220.1 us; the others 221-226),
+// correlated 64x16 (245 us).
 int tma_default_tile(int noise_mode, int fp16) {
-    static const int best[2][5] = {{1, 3, 0, 0, 3}, {4, 1, 3, 0, 1}};
+    static const int best[2][5] = {{1, 1, 0, 0, 3}, {4, 1, 3, 0, 1}};
     const int m = noise_mode < 0 ? 0 : (noise_mode > 4 ? 4 : noise_mode);
     return best[fp16 ? 1 : 0][m];
 }

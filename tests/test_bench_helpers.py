@@ -37,3 +37,19 @@ def test_traffic_record_scales_per_node(tmp_path, monkeypatch):
     assert b.step_kernel_traffic(400) == 4 * 7200.0
     (tmp_path / "k.cu").write_text("int a, b;\n")           # the kernel changed: no traffic
     assert b.step_kernel_traffic(400) is None
+
+
+def test_committed_traffic_record_is_current_and_not_below_the_algorithmic_bytes():
+    # the record that bench.py reports as roofline.traffic was captured on the step kernel as
+    # committed (same sources), at the benchmark's own size, and it carries at least the 72
+    # bytes per node the kernel must move (reads and writes of nine FP32 deviations)
+    b = _bench()
+    with open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")) as fh:
+        rec = json.load(fh)
+    assert b.kernel_source_hash(rec["sources"]) == rec["source_sha256"]
+    assert rec["nodes"] == 4096 * 4096
+    t = b.step_kernel_traffic(rec["nodes"])
+    assert t is not None and t >= 72 * rec["nodes"]
+    reads = sum(x[0] for x in rec["launches"]) / len(rec["launches"])
+    writes = sum(x[1] for x in rec["launches"]) / len(rec["launches"])
+    assert reads >= 36 * rec["nodes"] and writes >= 36 * rec["nodes"]
